@@ -1,0 +1,742 @@
+/*
+ * cm_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU implementation of the explicit MacCormack
+ * predictor-corrector step with TVD correction for the nondimensional fully
+ * compressible Navier-Stokes-energy equations of arXiv 2411.10372
+ * (Tiwari, Sharma & Verma), plus the Nusselt / Reynolds diagnostics.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+ * leg may load this library.  The product path (paper_2411_10372_gb300) never
+ * calls it; the two share no code, headers or tables.
+ *
+ * Everything is written as separate whole-grid arrays (X, F, X^P, F^P, X^C,
+ * TVD fluxes) and plain nested loops, in the order the paper states the
+ * scheme, so that it can be checked against the paper by eye.
+ *
+ * Passages followed (paper sections / equations):
+ *   Sec. 2, nondimensional continuity / momentum / energy equations and the
+ *     closures for p, E and tau ........................ prims(), flux()
+ *   Sec. 2, Eq. volume_Nu (bulk Nu), Eq. mean_Nu (plate Nu), Eq. Re ... orc_diag()
+ *   Sec. 3.1, vector form X_t + sum_a dF_a/dx_a = sum_a S_a ........ flux()
+ *   Sec. 3.1, Eq. time_step (operator splitting) ................... orc_step()
+ *   Sec. 3.1, predictor / corrector / average + TVD term, limiter G,
+ *     minmod phi, coefficient C(Co) ........................ sweep_z(), sweep_h()
+ *   Sec. 3.1, "second-order forward and backward differences at the
+ *     plates" ................................................ orc_diag() (plate Nu)
+ *
+ * Readings where the paper is silent, ambiguous or garbled (each listed in
+ * the design doc with its justification):
+ *   - stress tensor: the divergence term enters with coefficient cfg->stokes
+ *     (default -2/3, Stokes' hypothesis; the paper prints +2/3);
+ *   - corrector uses F^P at both k+1 and k (the printed F^(n)_{k+1} is
+ *     inconsistent);
+ *   - pressure sits in the alpha-momentum row of F_alpha (p delta_{i alpha});
+ *   - derivatives inside F: along the sweep direction forward in the
+ *     predictor and backward in the corrector, cross derivatives central;
+ *   - TVD: cfg->tvd_form selects G(r+)+G(r-) (Davis form, default, chosen
+ *     by the total-variation test) or the literal G(r+ + r-), or none;
+ *   - plates: no-slip, fixed temperature; plate density advanced as a half
+ *     cell with zero wall mass flux; TVD fluxes through the two interfaces
+ *     next to each plate are zero; horizontal sweeps leave plate rows alone;
+ *   - time step dt = cfl * min over nodes and directions of h/(|u|+c), from
+ *     the state at the start of the step; local Courant number of interface
+ *     k+1/2 uses the larger |u|+c of its two nodes and the sweep's dt/2;
+ *   - initial state: exact conduction/hydrostatic profile for constant K,
+ *     isobaric temperature perturbation at interior nodes.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- configuration (mirrored by oracle/__init__.py, field for field) ---- */
+typedef struct {
+    int ndim;            /* 2 or 3 */
+    int nx, ny, nz;      /* nodes; ny = 1 in 2D; nz counts both plates */
+    int tvd_form;        /* 0: G(r+)+G(r-), 1: G(r+ + r-), 2: no TVD term */
+    int pad_;
+    double aspect;       /* Gamma = L/d */
+    double Ra, Pr, gamma, eps, D;
+    double cfl;          /* dt = cfl * min h/(|u|+c) */
+    double dt_fixed;     /* > 0 overrides the CFL rule */
+    double gravity;      /* multiplies g = 1/eps (1 = the paper) */
+    double t_bot, t_top; /* plate temperatures (paper: 1 and 1-eps-D) */
+    double pert_amp;     /* amplitude of the temperature perturbation */
+    double stokes;       /* coefficient of (div u) delta_ij inside tau/mu */
+    uint64_t seed;
+} orc_cfg;
+
+/* derived constants */
+typedef struct {
+    int ndim, nx, ny, nz, tvd_form;
+    size_t n;
+    double h[3];         /* dx, dy, dz */
+    double a;            /* p = a rho T,        a = (gamma-1)/(gamma eps D) */
+    double b;            /* T = b (E/rho - u^2/2 - g z), b = gamma eps D     */
+    double g;            /* gravity / eps                                    */
+    double mu;           /* sqrt(Pr/Ra)                                      */
+    double kth;          /* 1/(eps D sqrt(Ra Pr))                            */
+    double stokes, gam;
+    double t_bot, t_top;
+    double cfl, dt_fixed;
+    double Ra, Pr, eps, D, aspect;
+} P;
+
+static void derive(const orc_cfg* c, P* p)
+{
+    p->ndim = c->ndim;
+    p->nx = c->nx;
+    p->ny = (c->ndim == 3) ? c->ny : 1;
+    p->nz = c->nz;
+    p->tvd_form = c->tvd_form;
+    p->n = (size_t)p->nx * p->ny * p->nz;
+    p->h[0] = c->aspect / c->nx;
+    p->h[1] = c->aspect / p->ny;
+    p->h[2] = 1.0 / (c->nz - 1);
+    p->gam = c->gamma;
+    p->a = (c->gamma - 1.0) / (c->gamma * c->eps * c->D);
+    p->b = c->gamma * c->eps * c->D;
+    p->g = c->gravity / c->eps;
+    p->mu = sqrt(c->Pr / c->Ra);
+    p->kth = 1.0 / (c->eps * c->D * sqrt(c->Ra * c->Pr));
+    p->stokes = c->stokes;
+    p->t_bot = c->t_bot;
+    p->t_top = c->t_top;
+    p->cfl = c->cfl;
+    p->dt_fixed = c->dt_fixed;
+    p->Ra = c->Ra; p->Pr = c->Pr; p->eps = c->eps; p->D = c->D;
+    p->aspect = c->aspect;
+}
+
+/* z of plane k: nodes on both plates, z_0 = 0 and z_{nz-1} = 1 */
+static double zk(const P* p, int k) { return (double)k / (double)(p->nz - 1); }
+
+static size_t idx(const P* p, int i, int j, int k)
+{
+    return ((size_t)k * p->ny + j) * p->nx + i;
+}
+
+/* neighbour of (i,j,k) one step along direction d (s = +1 or -1);
+ * x and y are periodic, z is only asked for interior neighbours. */
+static size_t nbr(const P* p, int i, int j, int k, int d, int s)
+{
+    if (d == 0) i = (i + s + p->nx) % p->nx;
+    else if (d == 1) j = (j + s + p->ny) % p->ny;
+    else k = k + s;
+    return idx(p, i, j, k);
+}
+
+/* Internal state: 5 components (rho, m_x, m_y, m_z, E), component c of node n
+ * at X[c*N + n].  In 2D m_y stays identically zero. */
+
+/* Primitive variables from the closures of Sec. 2:
+ * u = m/rho, T = gamma eps D (E/rho - u^2/2 - z/eps), p = (gamma-1)/(gamma eps D) rho T */
+static void prims(const P* p, const double* X, double* U, double* T, double* Pr)
+{
+    size_t N = p->n;
+    for (int k = 0; k < p->nz; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                size_t n = idx(p, i, j, k);
+                double rho = X[n];
+                double u = X[1 * N + n] / rho;
+                double v = X[2 * N + n] / rho;
+                double w = X[3 * N + n] / rho;
+                U[0 * N + n] = u;
+                U[1 * N + n] = v;
+                U[2 * N + n] = w;
+                T[n] = p->b * (X[4 * N + n] / rho - 0.5 * (u * u + v * v + w * w) - p->g * zk(p, k));
+                Pr[n] = p->a * rho * T[n];
+            }
+}
+
+/* Velocity and temperature gradients at node (i,j,k) for a sweep along al:
+ * along al a one-sided difference (forward if fwd, else backward), across
+ * al central differences.  du[c][d] = d u_c / d x_d. */
+static void grad(const P* p, const double* U, const double* T, int i, int j, int k,
+                 int al, int fwd, double du[3][3], double dT[3])
+{
+    size_t N = p->n;
+    size_t self = idx(p, i, j, k);
+    for (int d = 0; d < 3; d++) {
+        size_t np, nm;
+        double span;
+        if (d == al) {
+            np = fwd ? nbr(p, i, j, k, d, +1) : self;
+            nm = fwd ? self : nbr(p, i, j, k, d, -1);
+            span = p->h[d];
+        } else {
+            np = nbr(p, i, j, k, d, +1);
+            nm = nbr(p, i, j, k, d, -1);
+            span = 2.0 * p->h[d];
+        }
+        for (int c = 0; c < 3; c++)
+            du[c][d] = (U[c * N + np] - U[c * N + nm]) / span;
+        dT[d] = (T[np] - T[nm]) / span;
+    }
+}
+
+/* Flux F_al of Sec. 3.1 at one node:
+ *   [ rho u_al ;
+ *     m_i u_al - tau_{i al} + p delta_{i al}  (i = x, y, z) ;
+ *     u_al (E + p) - K dT/dx_al - sum_b u_b tau_{b al} ]
+ * with tau_ij = mu (d_j u_i + d_i u_j + stokes (div u) delta_ij). */
+static void flux(const P* p, int al, const double q[5], const double u[3], double pr,
+                 double du[3][3], const double dT[3], double F[5])
+{
+    double div = du[0][0] + du[1][1] + du[2][2];
+    double tau[3];
+    for (int i = 0; i < 3; i++)
+        tau[i] = p->mu * (du[i][al] + du[al][i] + (i == al ? p->stokes * div : 0.0));
+    F[0] = q[1 + al];
+    for (int i = 0; i < 3; i++)
+        F[1 + i] = q[1 + i] * u[al] - tau[i] + (i == al ? pr : 0.0);
+    double work = u[0] * tau[0] + u[1] * tau[1] + u[2] * tau[2];
+    F[4] = u[al] * (q[4] + pr) - p->kth * dT[al] - work;
+}
+
+static void node_flux(const P* p, int al, int fwd, const double* X, const double* U,
+                      const double* T, const double* Pr, int i, int j, int k, double F[5])
+{
+    size_t N = p->n, n = idx(p, i, j, k);
+    double q[5], u[3], du[3][3], dT[3];
+    for (int c = 0; c < 5; c++) q[c] = X[c * N + n];
+    for (int c = 0; c < 3; c++) u[c] = U[c * N + n];
+    grad(p, U, T, i, j, k, al, fwd, du, dT);
+    flux(p, al, q, u, Pr[n], du, dT, F);
+}
+
+/* ---- TVD limiter (Sec. 3.1) ---- */
+static double phi_minmod(double r) { return fmax(0.0, fmin(2.0 * r, 1.0)); }
+static double coefC(double Co) { return Co <= 0.5 ? Co * (1.0 - Co) : 0.25; }
+static double Gfun(double r, double C) { return 0.5 * C * (1.0 - phi_minmod(r)); }
+
+/* TVD flux through the interface between nodes n0 and n1 = n0 + e_al, with
+ * nm = n0 - e_al and n2 = n1 + e_al, from the sweep's INPUT state X:
+ *   D = [G(r+_{n0}) + G(r-_{n1})] dX_{n0+1/2}   (tvd_form 0)
+ *   D =  G(r+_{n0} + r-_{n1})     dX_{n0+1/2}   (tvd_form 1)
+ * r+_{n0} = (dX_{n0-1/2}, dX_{n0+1/2}) / (dX_{n0+1/2}, dX_{n0+1/2})
+ * r-_{n1} = (dX_{n0+1/2}, dX_{n0+3/2}) / (dX_{n0+1/2}, dX_{n0+1/2})
+ * Co = (dt/2) max(|u_al|+c over n0, n1) / h_al. */
+static void tvd_flux(const P* p, const double* X, const double* A, double Delta, int al,
+                     size_t nm, size_t n0, size_t n1, size_t n2, double D[5])
+{
+    size_t N = p->n;
+    double dm[5], d0[5], dp[5];
+    for (int c = 0; c < 5; c++) {
+        dm[c] = X[c * N + n0] - X[c * N + nm];
+        d0[c] = X[c * N + n1] - X[c * N + n0];
+        dp[c] = X[c * N + n2] - X[c * N + n1];
+    }
+    double s_plus = 0.0, s_minus = 0.0, dd = 0.0;
+    for (int c = 0; c < 5; c++) {
+        s_plus += dm[c] * d0[c];
+        s_minus += d0[c] * dp[c];
+        dd += d0[c] * d0[c];
+    }
+    for (int c = 0; c < 5; c++) D[c] = 0.0;
+    if (p->tvd_form == 2 || dd == 0.0) return;
+    double rp = s_plus / dd, rm = s_minus / dd;
+    double Co = Delta * fmax(A[n0], A[n1]) / p->h[al];
+    double C = coefC(Co);
+    double G = (p->tvd_form == 0) ? Gfun(rp, C) + Gfun(rm, C) : Gfun(rp + rm, C);
+    for (int c = 0; c < 5; c++) D[c] = G * d0[c];
+}
+
+/* |u_al| + c at every node, c^2 = gamma p / rho = gamma a T */
+static void wave_speed(const P* p, int al, const double* U, const double* T, double* A)
+{
+    size_t N = p->n;
+    for (size_t n = 0; n < N; n++) A[n] = fabs(U[al * N + n]) + sqrt(p->gam * p->a * T[n]);
+}
+
+typedef struct {
+    double *U, *T, *Pr, *A, *F, *XP, *UP, *TP, *PP, *FP, *XC, *D;
+} Work;
+
+static void work_alloc(const P* p, Work* w)
+{
+    size_t N = p->n;
+    w->U = malloc(3 * N * sizeof(double));
+    w->T = malloc(N * sizeof(double));
+    w->Pr = malloc(N * sizeof(double));
+    w->A = malloc(N * sizeof(double));
+    w->F = calloc(5 * N, sizeof(double));
+    w->XP = malloc(5 * N * sizeof(double));
+    w->UP = malloc(3 * N * sizeof(double));
+    w->TP = malloc(N * sizeof(double));
+    w->PP = malloc(N * sizeof(double));
+    w->FP = calloc(5 * N, sizeof(double));
+    w->XC = malloc(5 * N * sizeof(double));
+    w->D = calloc(5 * N, sizeof(double));
+}
+
+static void work_free(Work* w)
+{
+    free(w->U); free(w->T); free(w->Pr); free(w->A); free(w->F); free(w->XP);
+    free(w->UP); free(w->TP); free(w->PP); free(w->FP); free(w->XC); free(w->D);
+}
+
+/* Plate values: no slip (m = 0) and fixed temperature T_w, so
+ * E = rho (T_w / (gamma eps D) + z_w / eps). */
+static void set_plate(const P* p, double* X, size_t n, int top)
+{
+    size_t N = p->n;
+    double Tw = top ? p->t_top : p->t_bot;
+    double zw = top ? 1.0 : 0.0;
+    X[1 * N + n] = 0.0;
+    X[2 * N + n] = 0.0;
+    X[3 * N + n] = 0.0;
+    X[4 * N + n] = X[n] * (Tw / p->b + p->g * zw);
+}
+
+/* L_z(Delta): one predictor-corrector-TVD sweep along z (Sec. 3.1) */
+static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* w)
+{
+    size_t N = p->n;
+    int nz = p->nz, K = nz - 1;
+    double lam = Delta / p->h[2];
+
+    prims(p, X, w->U, w->T, w->Pr);
+    wave_speed(p, 2, w->U, w->T, w->A);
+
+    /* predictor fluxes F^n_k, k = 0..nz-2 (forward z-derivatives) */
+    for (int k = 0; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                double F[5];
+                node_flux(p, 2, 1, X, w->U, w->T, w->Pr, i, j, k, F);
+                size_t n = idx(p, i, j, k);
+                for (int c = 0; c < 5; c++) w->F[c * N + n] = F[c];
+            }
+    /* predictor at interior nodes: X^P = X - (Delta/dz)(F_k - F_{k-1}) + Delta S,
+     * S = (0, 0, 0, -g rho, 0) */
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                size_t n = idx(p, i, j, k), nm = idx(p, i, j, k - 1);
+                for (int c = 0; c < 5; c++) {
+                    double S = (c == 3) ? -p->g * X[n] : 0.0;
+                    w->XP[c * N + n] = X[c * N + n] - lam * (w->F[c * N + n] - w->F[c * N + nm]) + Delta * S;
+                }
+            }
+    /* plates: half cell with zero wall mass flux; m = 0; T = T_w */
+    for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++) {
+            size_t n0 = idx(p, i, j, 0), nK = idx(p, i, j, K), nK1 = idx(p, i, j, K - 1);
+            w->XP[n0] = X[n0] - 2.0 * lam * w->F[n0];
+            w->XP[nK] = X[nK] + 2.0 * lam * w->F[nK1];
+            set_plate(p, w->XP, n0, 0);
+            set_plate(p, w->XP, nK, 1);
+        }
+
+    prims(p, w->XP, w->UP, w->TP, w->PP);
+
+    /* corrector fluxes F^P_k, k = 1..nz-1 (backward z-derivatives) */
+    for (int k = 1; k < nz; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                double F[5];
+                node_flux(p, 2, 0, w->XP, w->UP, w->TP, w->PP, i, j, k, F);
+                size_t n = idx(p, i, j, k);
+                for (int c = 0; c < 5; c++) w->FP[c * N + n] = F[c];
+            }
+    /* corrector at interior nodes: X^C = X - (Delta/dz)(F^P_{k+1} - F^P_k) + Delta S^P;
+     * then the average (X^P + X^C)/2 */
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                size_t n = idx(p, i, j, k), np = idx(p, i, j, k + 1);
+                for (int c = 0; c < 5; c++) {
+                    double S = (c == 3) ? -p->g * w->XP[n] : 0.0;
+                    w->XC[c * N + n] = X[c * N + n] - lam * (w->FP[c * N + np] - w->FP[c * N + n]) + Delta * S;
+                    Y[c * N + n] = (w->XP[c * N + n] + w->XC[c * N + n]) / 2.0;
+                }
+            }
+    /* plate densities: corrector half cells, then average */
+    for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++) {
+            size_t n0 = idx(p, i, j, 0), n1 = idx(p, i, j, 1), nK = idx(p, i, j, K);
+            double rc0 = X[n0] - 2.0 * lam * w->FP[n1];
+            double rcK = X[nK]; /* F^P at the top plate is m_z = 0 */
+            Y[n0] = (w->XP[n0] + rc0) / 2.0;
+            Y[nK] = (w->XP[nK] + rcK) / 2.0;
+        }
+
+    /* TVD fluxes D_{k+1/2} for k = 1..nz-3 (zero at the two plate-adjacent interfaces) */
+    memset(w->D, 0, 5 * N * sizeof(double));
+    for (int k = 1; k <= nz - 3; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                double D[5];
+                tvd_flux(p, X, w->A, Delta, 2, idx(p, i, j, k - 1), idx(p, i, j, k),
+                         idx(p, i, j, k + 1), idx(p, i, j, k + 2), D);
+                size_t n = idx(p, i, j, k);
+                for (int c = 0; c < 5; c++) w->D[c * N + n] = D[c];
+            }
+    /* X^{new} = (X^P + X^C)/2 + (D_{k+1/2} - D_{k-1/2}) */
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                size_t n = idx(p, i, j, k), nm = idx(p, i, j, k - 1);
+                for (int c = 0; c < 5; c++)
+                    Y[c * N + n] = Y[c * N + n] + (w->D[c * N + n] - w->D[c * N + nm]);
+            }
+    for (int j = 0; j < p->ny; j++)
+        for (int i = 0; i < p->nx; i++) {
+            set_plate(p, Y, idx(p, i, j, 0), 0);
+            set_plate(p, Y, idx(p, i, j, K), 1);
+        }
+}
+
+/* L_x(Delta) or L_y(Delta): a periodic horizontal sweep on the interior
+ * rows; the plate rows pass through unchanged (no mass flux along a no-slip
+ * wall). */
+static void sweep_h(const P* p, int al, double Delta, const double* X, double* Y, Work* w)
+{
+    size_t N = p->n;
+    int nz = p->nz, K = nz - 1;
+    double lam = Delta / p->h[al];
+
+    prims(p, X, w->U, w->T, w->Pr);
+    wave_speed(p, al, w->U, w->T, w->A);
+
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                double F[5];
+                node_flux(p, al, 1, X, w->U, w->T, w->Pr, i, j, k, F);
+                size_t n = idx(p, i, j, k);
+                for (int c = 0; c < 5; c++) w->F[c * N + n] = F[c];
+            }
+    memcpy(w->XP, X, 5 * N * sizeof(double));
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                size_t n = idx(p, i, j, k), nm = nbr(p, i, j, k, al, -1);
+                for (int c = 0; c < 5; c++)
+                    w->XP[c * N + n] = X[c * N + n] - lam * (w->F[c * N + n] - w->F[c * N + nm]);
+            }
+
+    prims(p, w->XP, w->UP, w->TP, w->PP);
+
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                double F[5];
+                node_flux(p, al, 0, w->XP, w->UP, w->TP, w->PP, i, j, k, F);
+                size_t n = idx(p, i, j, k);
+                for (int c = 0; c < 5; c++) w->FP[c * N + n] = F[c];
+            }
+    memcpy(Y, X, 5 * N * sizeof(double));
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                size_t n = idx(p, i, j, k), np = nbr(p, i, j, k, al, +1);
+                for (int c = 0; c < 5; c++) {
+                    w->XC[c * N + n] = X[c * N + n] - lam * (w->FP[c * N + np] - w->FP[c * N + n]);
+                    Y[c * N + n] = (w->XP[c * N + n] + w->XC[c * N + n]) / 2.0;
+                }
+            }
+    /* TVD flux D at interface n+1/2 stored at n; all interfaces of interior rows */
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                size_t n0 = idx(p, i, j, k);
+                size_t nm = nbr(p, i, j, k, al, -1);
+                size_t n1 = nbr(p, i, j, k, al, +1);
+                int i1 = (al == 0) ? (i + 1) % p->nx : i;
+                int j1 = (al == 1) ? (j + 1) % p->ny : j;
+                size_t n2 = nbr(p, i1, j1, k, al, +1);
+                double D[5];
+                tvd_flux(p, X, w->A, Delta, al, nm, n0, n1, n2, D);
+                for (int c = 0; c < 5; c++) w->D[c * N + n0] = D[c];
+            }
+    for (int k = 1; k < K; k++)
+        for (int j = 0; j < p->ny; j++)
+            for (int i = 0; i < p->nx; i++) {
+                size_t n = idx(p, i, j, k), nm = nbr(p, i, j, k, al, -1);
+                for (int c = 0; c < 5; c++)
+                    Y[c * N + n] = Y[c * N + n] + (w->D[c * N + n] - w->D[c * N + nm]);
+            }
+}
+
+/* ---- conversion between the external layout and the 5-component one ----
+ * external 2D: [rho, m_x, m_z, E]; external 3D: [rho, m_x, m_y, m_z, E];
+ * field f is the contiguous block f*N .. f*N+N-1, node index ((k*ny)+j)*nx+i */
+static void to_internal(const P* p, const double* ext, double* X)
+{
+    size_t N = p->n;
+    if (p->ndim == 3) { memcpy(X, ext, 5 * N * sizeof(double)); return; }
+    memcpy(X, ext, 2 * N * sizeof(double));
+    memset(X + 2 * N, 0, N * sizeof(double));
+    memcpy(X + 3 * N, ext + 2 * N, 2 * N * sizeof(double));
+}
+
+static void to_external(const P* p, const double* X, double* ext)
+{
+    size_t N = p->n;
+    if (p->ndim == 3) { memcpy(ext, X, 5 * N * sizeof(double)); return; }
+    memcpy(ext, X, 2 * N * sizeof(double));
+    memcpy(ext + 2 * N, X + 3 * N, 2 * N * sizeof(double));
+}
+
+/* ---- time step ---- */
+static double dt_of(const P* p, const double* X, Work* w)
+{
+    if (p->dt_fixed > 0.0) return p->dt_fixed;
+    prims(p, X, w->U, w->T, w->Pr);
+    size_t N = p->n;
+    double best = INFINITY;
+    for (size_t n = 0; n < N; n++) {
+        double c = sqrt(p->gam * p->a * w->T[n]);
+        for (int d = 0; d < 3; d++) {
+            if (d == 1 && p->ndim == 2) continue;
+            double v = p->h[d] / (fabs(w->U[d * N + n]) + c);
+            if (v < best) best = v;
+        }
+    }
+    return p->cfl * best;
+}
+
+/* ======================= exported entry points ======================= */
+
+int orc_nfields(const orc_cfg* c) { return c->ndim == 3 ? 5 : 4; }
+
+/* Conduction / hydrostatic profile for constant K (reading of the paper's
+ * "hydrostatic base state"): T_c = t_bot + (t_top - t_bot) z, dp/dz = -g rho,
+ * p = a rho T, rho(0) = 1, so p_c = a t_bot (T_c/t_bot)^(g/(a Lambda)),
+ * Lambda = t_bot - t_top; isothermal limit p_c = a t_bot exp(-g z /(a t_bot)). */
+void orc_profile(const orc_cfg* c, double* Tc, double* pc, double* rhoc)
+{
+    P p;
+    derive(c, &p);
+    double Lam = p.t_bot - p.t_top;
+    for (int k = 0; k < p.nz; k++) {
+        double z = zk(&p, k);
+        double T = p.t_bot - Lam * z;
+        double pr;
+        if (Lam != 0.0)
+            pr = p.a * p.t_bot * pow(T / p.t_bot, p.g / (p.a * Lam));
+        else
+            pr = p.a * p.t_bot * exp(-p.g * z / (p.a * p.t_bot));
+        if (Tc) Tc[k] = T;
+        if (pc) pc[k] = pr;
+        if (rhoc) rhoc[k] = pr / (p.a * T);
+    }
+}
+
+/* SplitMix64 (Steele, Lea & Flood 2014): output number idx+1 of the
+ * generator seeded with `seed`, i.e. the mix of seed + (idx+1)*golden_gamma. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t idx)
+{
+    uint64_t z = seed + (idx + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* uniform in [-1, 1): 53 high bits scaled to [0,1), then 2u - 1 */
+static double xi_of(uint64_t seed, uint64_t idx)
+{
+    double u = (double)(orc_splitmix64(seed, idx) >> 11) * 0x1.0p-53;
+    return 2.0 * u - 1.0;
+}
+
+/* Initial state: the conduction profile with an isobaric temperature
+ * perturbation pert_amp * xi at interior nodes, u = 0; plates unperturbed. */
+void orc_init(const orc_cfg* c, double* ext)
+{
+    P p;
+    derive(c, &p);
+    size_t N = p.n;
+    double* Tc = malloc(p.nz * sizeof(double));
+    double* pc = malloc(p.nz * sizeof(double));
+    orc_profile(c, Tc, pc, NULL);
+    double* X = calloc(5 * N, sizeof(double));
+    for (int k = 0; k < p.nz; k++)
+        for (int j = 0; j < p.ny; j++)
+            for (int i = 0; i < p.nx; i++) {
+                size_t n = idx(&p, i, j, k);
+                double T = Tc[k];
+                if (k > 0 && k < p.nz - 1) T = Tc[k] + c->pert_amp * xi_of(c->seed, n);
+                double rho = pc[k] / (p.a * T);
+                X[n] = rho;
+                X[4 * N + n] = rho * (T / p.b + p.g * zk(&p, k));
+            }
+    to_external(&p, X, ext);
+    free(X); free(Tc); free(pc);
+}
+
+/* one directional sweep L_dir(Delta) applied to ext (in place); dir 0=x 1=y 2=z */
+void orc_sweep(const orc_cfg* c, int dir, double Delta, double* ext)
+{
+    P p;
+    derive(c, &p);
+    size_t N = p.n;
+    double* X = malloc(5 * N * sizeof(double));
+    double* Y = malloc(5 * N * sizeof(double));
+    Work w;
+    work_alloc(&p, &w);
+    to_internal(&p, ext, X);
+    if (dir == 2) sweep_z(&p, Delta, X, Y, &w);
+    else sweep_h(&p, dir, Delta, X, Y, &w);
+    to_external(&p, Y, ext);
+    work_free(&w);
+    free(X); free(Y);
+}
+
+double orc_dt(const orc_cfg* c, const double* ext)
+{
+    P p;
+    derive(c, &p);
+    double* X = malloc(5 * p.n * sizeof(double));
+    Work w;
+    work_alloc(&p, &w);
+    to_internal(&p, ext, X);
+    double dt = dt_of(&p, X, &w);
+    work_free(&w);
+    free(X);
+    return dt;
+}
+
+/* nsteps full steps of Eq. time_step:
+ * X^{n+1} = L_x L_y L_z L_x L_y L_z X^n with every L at dt/2 (rightmost first);
+ * dt from the state at the start of each step.  Writes each step's dt to dts
+ * (if not NULL) and advances *t. */
+void orc_step(const orc_cfg* c, double* ext, int nsteps, double* t, double* dts)
+{
+    P p;
+    derive(c, &p);
+    size_t N = p.n;
+    double* X = malloc(5 * N * sizeof(double));
+    double* Y = malloc(5 * N * sizeof(double));
+    Work w;
+    work_alloc(&p, &w);
+    to_internal(&p, ext, X);
+    for (int s = 0; s < nsteps; s++) {
+        double dt = dt_of(&p, X, &w);
+        double Delta = 0.5 * dt;
+        for (int half = 0; half < 2; half++) {
+            sweep_z(&p, Delta, X, Y, &w);              /* X -> Y */
+            if (p.ndim == 3) {
+                sweep_h(&p, 1, Delta, Y, X, &w);       /* Y -> X */
+                sweep_h(&p, 0, Delta, X, Y, &w);       /* X -> Y */
+                memcpy(X, Y, 5 * N * sizeof(double));
+            } else {
+                sweep_h(&p, 0, Delta, Y, X, &w);       /* Y -> X */
+            }
+        }
+        if (dts) dts[s] = dt;
+        if (t) *t += dt;
+    }
+    to_external(&p, X, ext);
+    work_free(&w);
+    free(X); free(Y);
+}
+
+/* Diagnostics (Sec. 2).  Volume averages use the trapezoid rule in z (half
+ * weight on the plate planes) and the plain mean in x, y.
+ * out[0]  Nu      = 1 + Nu_conv + Nu_K                       (Eq. volume_Nu)
+ * out[1]  Nu_conv = sqrt(Ra Pr)/eps <rho u_z T_sa>_V
+ * out[2]  Nu_K    = D sqrt(Ra Pr)/2 <rho u_z u^2>_V
+ * out[3]  Nu_bot  = -(1/eps) d<T_sa>_A/dz at z=0, second-order forward difference
+ * out[4]  Nu_top  = same at z=1, second-order backward difference   (Eq. mean_Nu)
+ * out[5]  Nu_bar  = (Nu_bot + Nu_top)/2
+ * out[6]  Re      = sqrt(Ra/Pr) sqrt(<u^2>_V)  (instantaneous; Eq. Re before the time mean)
+ * out[7]  KE      = <rho u^2 / 2>_V
+ * out[8]  mass    = <rho>_V
+ * out[9]  energy  = <E>_V
+ * out[10] max Mach number |u|/c
+ * T_sa = T - (1 - D z) (superadiabatic temperature). */
+void orc_diag(const orc_cfg* c, const double* ext, double* out)
+{
+    P p;
+    derive(c, &p);
+    size_t N = p.n;
+    double* X = malloc(5 * N * sizeof(double));
+    to_internal(&p, ext, X);
+    double s_conv = 0, s_k = 0, s_u2 = 0, s_ke = 0, s_m = 0, s_e = 0, mach = 0;
+    double* TA = calloc(p.nz, sizeof(double));
+    for (int k = 0; k < p.nz; k++) {
+        double wgt = (k == 0 || k == p.nz - 1) ? 0.5 : 1.0;
+        double z = zk(&p, k);
+        for (int j = 0; j < p.ny; j++)
+            for (int i = 0; i < p.nx; i++) {
+                size_t n = idx(&p, i, j, k);
+                double rho = X[n];
+                double u = X[1 * N + n] / rho, v = X[2 * N + n] / rho, w = X[3 * N + n] / rho;
+                double u2 = u * u + v * v + w * w;
+                double T = p.b * (X[4 * N + n] / rho - 0.5 * u2 - p.g * z);
+                double Tsa = T - (1.0 - p.D * z);
+                s_conv += wgt * rho * w * Tsa;
+                s_k += wgt * rho * w * u2;
+                s_u2 += wgt * u2;
+                s_ke += wgt * 0.5 * rho * u2;
+                s_m += wgt * rho;
+                s_e += wgt * X[4 * N + n];
+                TA[k] += T;
+                double M = sqrt(u2) / sqrt(p.gam * p.a * T);
+                if (M > mach) mach = M;
+            }
+    }
+    double vol = (double)p.nx * p.ny * (p.nz - 1);
+    double sRP = sqrt(p.Ra * p.Pr);
+    out[1] = sRP / p.eps * (s_conv / vol);
+    out[2] = p.D * sRP / 2.0 * (s_k / vol);
+    out[0] = 1.0 + out[1] + out[2];
+    double f[3], g[3];
+    int K = p.nz - 1;
+    for (int q = 0; q < 3; q++) {
+        f[q] = TA[q] / ((double)p.nx * p.ny) - (1.0 - p.D * zk(&p, q));
+        g[q] = TA[K - q] / ((double)p.nx * p.ny) - (1.0 - p.D * zk(&p, K - q));
+    }
+    double dz = p.h[2];
+    out[3] = -(1.0 / p.eps) * (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz);
+    out[4] = -(1.0 / p.eps) * (3.0 * g[0] - 4.0 * g[1] + g[2]) / (2.0 * dz);
+    out[5] = (out[3] + out[4]) / 2.0;
+    out[6] = sqrt(p.Ra / p.Pr) * sqrt(s_u2 / vol);
+    out[7] = s_ke / vol;
+    out[8] = s_m / vol;
+    out[9] = s_e / vol;
+    out[10] = mach;
+    free(TA);
+    free(X);
+}
+
+/* 1D scalar periodic linear advection u_t + a u_x = 0 (a > 0) with the same
+ * predictor / corrector / average / TVD sequence (Sec. 3.1) and the same
+ * limiter, for the total-variation test of the TVD-term reading.  Here the
+ * dot products are plain products, F = a u, and Co = a dt/h. */
+void orc_advect1d(int n, double a, double dt, double h, int nsteps, int tvd_form, double* u)
+{
+    double* F = malloc(n * sizeof(double));
+    double* uP = malloc(n * sizeof(double));
+    double* FP = malloc(n * sizeof(double));
+    double* y = malloc(n * sizeof(double));
+    double* D = malloc(n * sizeof(double));
+    double lam = dt / h, Co = a * dt / h, C = coefC(Co);
+    for (int s = 0; s < nsteps; s++) {
+        for (int i = 0; i < n; i++) F[i] = a * u[i];
+        for (int i = 0; i < n; i++) uP[i] = u[i] - lam * (F[i] - F[(i - 1 + n) % n]);
+        for (int i = 0; i < n; i++) FP[i] = a * uP[i];
+        for (int i = 0; i < n; i++) {
+            double uC = u[i] - lam * (FP[(i + 1) % n] - FP[i]);
+            y[i] = (uP[i] + uC) / 2.0;
+        }
+        for (int i = 0; i < n; i++) {
+            double dm = u[i] - u[(i - 1 + n) % n];
+            double d0 = u[(i + 1) % n] - u[i];
+            double dp = u[(i + 2) % n] - u[(i + 1) % n];
+            double dd = d0 * d0;
+            D[i] = 0.0;
+            if (tvd_form == 2 || dd == 0.0) continue;
+            double rp = dm * d0 / dd, rm = d0 * dp / dd;
+            double G = (tvd_form == 0) ? Gfun(rp, C) + Gfun(rm, C) : Gfun(rp + rm, C);
+            D[i] = G * d0;
+        }
+        for (int i = 0; i < n; i++) u[i] = y[i] + (D[i] - D[(i - 1 + n) % n]);
+    }
+    free(F); free(uP); free(FP); free(y); free(D);
+}

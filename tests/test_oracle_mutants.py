@@ -1,0 +1,109 @@
+"""Mutation test of the oracle's pins.
+
+Each case plants one plausible mistake (a dropped term, a wrong sign, index or
+factor, a transposed operand) in a copy of oracle/cm_oracle.c, builds it, and
+checks that at least one pin of tests/test_oracle_pins.py fails on it.  The
+mistakes are planted in the oracle, on the CPU; the CUDA path is not involved.
+"""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle as O
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(O.__file__), "cm_oracle.c")
+
+# (name, text in cm_oracle.c, replacement)
+MUTANTS = [
+    ("stokes_sign", "(i == al ? p->stokes * div : 0.0)", "(i == al ? -p->stokes * div : 0.0)"),
+    ("no_pressure_in_flux", "(i == al ? pr : 0.0)", "0.0"),
+    ("pressure_in_z_row_only", "(i == al ? pr : 0.0)", "(i == 2 ? pr : 0.0)"),
+    ("gravity_sign", "double S = (c == 3) ? -p->g * X[n] : 0.0;", "double S = (c == 3) ? p->g * X[n] : 0.0;"),
+    ("no_viscous_work", "p->kth * dT[al] - work", "p->kth * dT[al]"),
+    ("heat_flux_sign", "- p->kth * dT[al]", "+ p->kth * dT[al]"),
+    ("tau_transposed", "du[i][al] + du[al][i]", "du[i][al] + du[i][al]"),
+    ("corrector_uses_Fn_literal",
+     "X[c * N + n] - lam * (w->FP[c * N + np] - w->FP[c * N + n]) + Delta * S;",
+     "X[c * N + n] - lam * (w->F[c * N + np] - w->FP[c * N + n]) + Delta * S;"),
+    ("no_average", "Y[c * N + n] = (w->XP[c * N + n] + w->XC[c * N + n]) / 2.0;\n                }\n            }\n    /* TVD flux D at",
+     "Y[c * N + n] = w->XC[c * N + n];\n                }\n            }\n    /* TVD flux D at"),
+    ("wall_half_cell_factor", "X[nK] + 2.0 * lam * w->F[nK1]", "X[nK] + lam * w->F[nK1]"),
+    ("plate_temperatures_swapped", "double Tw = top ? p->t_top : p->t_bot;", "double Tw = top ? p->t_bot : p->t_top;"),
+    ("tvd_sum_form", "(p->tvd_form == 0) ? Gfun(rp, C) + Gfun(rm, C) : Gfun(rp + rm, C)",
+     "(p->tvd_form == 1) ? Gfun(rp, C) + Gfun(rm, C) : Gfun(rp + rm, C)"),
+    ("tvd_sign", "Y[c * N + n] + (w->D[c * N + n] - w->D[c * N + nm]);\n            }\n}",
+     "Y[c * N + n] - (w->D[c * N + n] - w->D[c * N + nm]);\n            }\n}"),
+    ("tvd_rminus_index", "dp[c] = X[c * N + n2] - X[c * N + n1];", "dp[c] = X[c * N + n0] - X[c * N + nm];"),
+    ("courant_full_dt", "double Co = Delta * fmax(A[n0], A[n1]) / p->h[al];",
+     "double Co = 2.0 * Delta * fmax(A[n0], A[n1]) / p->h[al];"),
+    ("split_order_x_first", "sweep_z(&p, Delta, X, Y, &w);              /* X -> Y */",
+     "sweep_h(&p, 0, Delta, X, Y, &w);"),
+    ("limiter_phi_no_factor2", "fmin(2.0 * r, 1.0)", "fmin(r, 1.0)"),
+    ("nu_conv_coefficient", "out[1] = sRP / p.eps * (s_conv / vol);", "out[1] = sRP * (s_conv / vol);"),
+    ("nu_k_coefficient", "out[2] = p.D * sRP / 2.0 * (s_k / vol);", "out[2] = p.D * sRP * (s_k / vol);"),
+    ("tsa_sign", "double Tsa = T - (1.0 - p.D * z);", "double Tsa = T - (1.0 + p.D * z);"),
+    ("plate_nu_first_order", "(-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz)", "(f[1] - f[0]) / dz"),
+    ("re_missing_sqrt", "sqrt(p.Ra / p.Pr) * sqrt(s_u2 / vol)", "sqrt(p.Ra / p.Pr) * (s_u2 / vol)"),
+    ("sound_speed_missing_gamma", "double c = sqrt(p->gam * p->a * w->T[n]);", "double c = sqrt(p->a * w->T[n]);"),
+    ("perturb_plates", "if (k > 0 && k < p.nz - 1) T = Tc[k]", "T = Tc[k]"),
+    ("potential_missing_in_T", "- p->g * zk(p, k));", ");"),
+]
+
+
+def _pin_calls():
+    calls = []
+    for name in dir(pins):
+        fn = getattr(pins, name)
+        if not name.startswith("test_") or not callable(fn):
+            continue
+        marks = [m.name for m in getattr(fn, "pytestmark", [])]
+        if "slow" in marks:
+            continue
+        if name == "test_tvd_reading_davis_split_form_is_tvd":
+            calls += [(f"{name}[{c}]", (lambda c=c, fn=fn: fn(c))) for c in (0.1, 0.2, 0.25, 0.4)]
+        elif name == "test_sound_damping_pins_stokes_reading":
+            calls += [(f"{name}[-]", lambda fn=fn: fn(-2.0 / 3.0, True)),
+                      (f"{name}[+]", lambda fn=fn: fn(2.0 / 3.0, False))]
+        else:
+            calls.append((name, fn))
+    return calls
+
+
+def test_pins_pass_on_unmutated_oracle_copy(tmp_path):
+    lib = _build(tmp_path, open(SRC).read(), "clean")
+    with O.library(lib):
+        failed = [n for n, fn in _pin_calls() if not _passes(fn)]
+    assert failed == []
+
+
+def _build(tmp, src, tag):
+    c = os.path.join(tmp, f"m_{tag}.c")
+    so = os.path.join(tmp, f"m_{tag}.so")
+    with open(c, "w") as f:
+        f.write(src)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, c, "-lm"],
+                   check=True)
+    return so
+
+
+def _passes(fn):
+    try:
+        fn()
+        return True
+    except (AssertionError, FloatingPointError, ValueError, OverflowError, ZeroDivisionError):
+        return False
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    lib = _build(tmp_path, src.replace(old, new), name)
+    import numpy as np
+    with O.library(lib), np.errstate(all="ignore"):
+        caught = [n for n, fn in _pin_calls() if not _passes(fn)]
+    print(name, "caught by", caught)
+    assert caught, f"no pin fails on mutant {name}"
