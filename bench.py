@@ -1,0 +1,284 @@
+#!/usr/bin/env python
+"""Throughput of the MacCormack-TVD step (cell-updates/s) on GB300.
+
+Workload: 2D compressible convection, aspect ratio 4, 4096 x 1024 nodes,
+Ra = 1e10, Pr = 1, gamma = 5/3, eps = 0.1, D = 0.5, seeded isobaric
+temperature perturbation of amplitude 1e-3 (synthetic input).  FP32 state
+with FP64 dt and reductions is the timed line; an FP64-state run is reported
+beside it.  A step is one full time step of the scheme (z, x, z, x sweeps)
+over the whole grid; one cell-update is one node advanced by one step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank advances its own independent replica (the method
+has no exchange between independent boxes); timing is the max over ranks and
+the value counts the cells of all ranks.  L2 is flushed (256 MiB memset)
+before every timed step; durations come from CUDA events on the solver's
+stream.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NZ, RA, PR, GAMMA = 4096, 1024, 1e10, 1.0, 5.0 / 3.0
+WORKLOAD = "2d_aspect4_4096x1024_Ra1e10"
+METRIC = "cell-updates/s per MacCormack-TVD step"
+UNIT = "cell-updates/s"
+FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.window = None  # (start, end) host wall-clock of the timed region
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for t, line in self.lines:
+            if self.window and not (self.window[0] <= t <= self.window[1]):
+                continue
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2411_10372_gb300 as cm
+
+    stream = torch.cuda.Stream()
+    cells = NX * NZ
+    hbm, peak_kind = peaks()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def measure(precision: str, K: int, W: int, clocks: bool):
+        s = cm.Solver(NX, NZ, RA, PR, GAMMA, precision=precision, stream=stream, seed=12345 + rank)
+        s.step(W)
+        s.sync()
+        barrier()
+        launches0 = cm.cm_launch_count()
+        clk = Clocks(local)
+        if clocks:
+            with clk:
+                time.sleep(0.5)  # let nvidia-smi start; only samples inside the window count
+                t_start = time.time()
+                sweep_ms, step_ms = cm.cm_profile_steps(K, FLUSH_BYTES)
+                clk.window = (t_start, time.time())
+        else:
+            sweep_ms, step_ms = cm.cm_profile_steps(K, FLUSH_BYTES)
+        barrier()
+        launches = cm.cm_launch_count() - launches0
+        s.sync()
+        total_ms = max_over_ranks(sum(step_ms))
+        out = dict(total_ms=total_ms, sweep_ms=sweep_ms, launches=launches, clocks=clk.summary() if clocks else None,
+                   w=8 if precision == "fp64" else 4)
+        return s, out
+
+    # ---- FP32 state: the timed line ----
+    s, r32 = measure("fp32", args.steps, args.warmup, clocks=True)
+    # end to end through the public C ABI with host buffers: every step
+    # uploads the state from pinned host memory (dense float64), steps once
+    # and reads one diagnostics sample back
+    host = torch.empty((4, NZ, NX), dtype=torch.float64, pin_memory=True)
+    hostnp = host.numpy()
+    cm.cm_get_state(hostnp)
+    n_e2e = max(3, min(args.steps, 30))
+    cm.cm_run_host(hostnp, 1, None, True)
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        cm.cm_run_host(hostnp, 1, None, True)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    s.close()
+
+    # ---- FP64 state, same workload ----
+    k64 = max(3, min(args.steps, 20))
+    s64, r64 = measure("fp64", k64, min(args.warmup, 3), clocks=False)
+    s64.close()
+
+    def roofline(r):
+        nf, w = 4, r["w"]
+        kinds = {"sweep_z2d": r["sweep_ms"][0] + r["sweep_ms"][2], "sweep_x2d": r["sweep_ms"][1] + r["sweep_ms"][3]}
+        dom = max(kinds, key=kinds.get)
+        per_launch_ms = kinds[dom] / 2.0
+        bytes_per_launch = 2 * nf * w * cells
+        achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "traffic": None,
+                "bytes_per_launch": bytes_per_launch, "ms_per_launch": round(per_launch_ms, 5)}
+
+    K = args.steps
+    value = world * cells * K / (r32["total_ms"] * 1e-3)
+    value64 = world * cells * k64 / (r64["total_ms"] * 1e-3)
+    e2e_value = world * cells * n_e2e / e2e_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": r32["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD + "_fp32", "nx": NX, "nz": NZ, "Ra": RA, "Pr": PR, "gamma": GAMMA,
+                   "eps": 0.1, "D": 0.5, "cfl": 0.5, "state": "fp32, fp64 dt and reductions",
+                   "l2": "flushed before every timed step (256 MiB memset)", "parallelism": f"replicas x{world}"},
+        "roofline": roofline(r32),
+        "sweep_ms": [round(x, 5) for x in r32["sweep_ms"]],
+        "gpu_launches": r32["launches"],
+        "clocks": r32["clocks"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * cells * 8,
+                "d2h_bytes_per_step": 128, "steps": n_e2e},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": r64["total_ms"] / k64, "steps": k64,
+                 "sweep_ms": [round(x, 5) for x in r64["sweep_ms"]], "gpu_launches": r64["launches"],
+                 "roofline_hbm": roofline(r64)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(steps=args.cpu_steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(steps: int, nx: int = NX):
+    """The FP64 oracle as it stands, one thread, on a bounded sample of the
+    workload: `steps` full steps of the nx x 1024 grid from the seeded state."""
+    import oracle as O
+    cfg = O.Config(nx=nx, nz=NZ, Ra=RA, Pr=PR, gamma=GAMMA)
+    X = O.init(cfg)
+    t0 = time.perf_counter()
+    O.step(cfg, X, steps)
+    dt = time.perf_counter() - t0
+    return {"value": nx * NZ * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 steps of the {nx}x{NZ} grid, single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, timed as it stands on the
+    host cores, on this workload; each step is a bounded sample (all nz rows,
+    nx columns sized so the whole run stays within a few minutes)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    # one full-width step costs ~0.55 us per node on one core: size nx
+    budget_s = 150.0
+    est_node_s = 0.6e-6
+    nx = NX
+    while nx > 32 and (args.steps + args.warmup) * nx * NZ * est_node_s > budget_s:
+        nx //= 2
+    cfg = O.Config(nx=nx, nz=NZ, Ra=RA, Pr=PR, gamma=GAMMA)
+    X = O.init(cfg)
+    X, _, _ = O.step(cfg, X, args.warmup)
+    t0 = time.perf_counter()
+    O.step(cfg, X, args.steps)
+    dt = time.perf_counter() - t0
+    value = nx * NZ * args.steps / dt
+    sample = f"{args.steps} FP64 steps of a {nx}x{NZ} slice of the workload (same per-node work), single thread"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "nx": nx, "nz": NZ, "Ra": RA, "Pr": PR, "gamma": GAMMA},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

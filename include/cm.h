@@ -1,0 +1,204 @@
+/*
+ * cm.h -- C ABI of the GB300 MacCormack-TVD compressible-convection solver.
+ *
+ * The library advances the nondimensional, fully compressible Navier-Stokes-
+ * energy equations of arXiv 2411.10372 (Sec. 2: continuity, momentum with
+ * gravity -rho/eps, energy with conduction 1/(eps D sqrt(Ra Pr)) and viscous
+ * work; ideal gas p = (gamma-1)/(gamma eps D) rho T) in a box of aspect ratio
+ * Gamma with periodic side walls and no-slip, fixed-temperature plates, with
+ * the operator-split MacCormack predictor-corrector scheme plus TVD correction
+ * of Sec. 3.1 (Eq. time_step), on a uniform grid, on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: CM_OK (0) or a negative CM_E* code;
+ *    cm_last_error() gives a one-line message for the last failure.  No C++
+ *    exception crosses this boundary.
+ *  - There is one implicit solver context per process (not thread-safe).
+ *    cm_init() creates it (replacing any previous one), cm_finalize() frees it.
+ *  - Pointers marked "host" are ordinary CPU memory owned by the caller;
+ *    pointers marked "device" are CUDA device memory.
+ *  - Dense host state arrays are float64, field-major: field f, plane k
+ *    (z, k = 0 bottom plate .. nz-1 top plate), row j (y, 3D only), column i
+ *    (x) at ((f*nz + k)*ny + j)*nx + i.  2D fields: rho, m_x, m_z, E.
+ *    3D fields: rho, m_x, m_y, m_z, E.  (m = rho u, E total energy density.)
+ *  - Work is queued on the stream given in cm_params.stream (NULL = the
+ *    legacy default stream) and runs asynchronously unless stated.
+ *  - After any error other than CM_EINVAL from argument checks, call
+ *    cm_finalize() and cm_init() again.
+ */
+#ifndef CM_H
+#define CM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CM_OK 0
+#define CM_EINVAL (-1)      /* bad argument */
+#define CM_ECUDA (-2)       /* a CUDA runtime call failed */
+#define CM_ENOTINIT (-3)    /* no context: call cm_init first */
+#define CM_ENAN (-4)        /* non-finite value met in a reduction */
+#define CM_EUNSTABLE (-7)   /* explicit diffusion number above 1/2 at init */
+#define CM_ENOMEM (-8)      /* device allocation failed */
+#define CM_EBADCKPT (-9)    /* checkpoint file unreadable or for another grid */
+
+/* arithmetic of the state and of the stencil (reductions are always FP64) */
+#define CM_FP64 0
+#define CM_FP32 1
+
+/* form of the TVD term of Sec. 3.1 */
+#define CM_TVD_DAVIS 0      /* [G(r+_k) + G(r-_{k+1})] dX_{k+1/2}: default   */
+#define CM_TVD_SUM 1        /* G(r+_k + r-_{k+1}) dX_{k+1/2}: as printed     */
+#define CM_TVD_OFF 2        /* no TVD term (plain MacCormack; tests only)    */
+
+typedef struct cm_grid {
+    int ndim;       /* 2 or 3 */
+    int nx, ny, nz; /* nodes; x (and y) periodic; nz counts both plates (ny ignored in 2D) */
+    double aspect;  /* Gamma = L/d: the box is Gamma (x Gamma) x 1 */
+} cm_grid;
+
+typedef struct cm_params {
+    double eps;          /* superadiabaticity epsilon (Sec. 2); default 0.1 */
+    double D;            /* dissipation number (Sec. 2); default 0.5 */
+    double cfl;          /* dt = cfl * min over nodes, directions of h/(|u|+c); default 0.5 */
+    double dt_fixed;     /* > 0: use this dt instead of the CFL rule */
+    double gravity;      /* factor on g = 1/eps; 1 = the paper, 0 = no gravity */
+    double t_bot, t_top; /* plate temperatures; default 1 and 1 - eps - D (Sec. 2) */
+    double pert_amp;     /* amplitude A of the initial temperature perturbation; default 1e-3 */
+    double stokes;       /* coefficient of (div u) delta_ij in tau/mu; default -2/3 */
+    unsigned long long seed; /* seed of the SplitMix64 perturbation field */
+    int precision;       /* CM_FP64 or CM_FP32 */
+    int tvd_form;        /* CM_TVD_* */
+    int diag_every;      /* queue a diagnostics sample every n steps (0 = never) */
+    int diag_capacity;   /* samples kept on the device between cm_diagnostics calls */
+    void* stream;        /* cudaStream_t to queue work on (NULL = legacy default stream) */
+    void* state_buf;     /* optional caller-owned device memory for the two state
+                            buffers (>= cm_state_bytes bytes, 256-byte aligned);
+                            NULL = the library allocates.  Must outlive cm_finalize. */
+} cm_params;
+
+/* One diagnostics sample (Sec. 2, Eqs. volume_Nu, mean_Nu, Re), FP64.
+ * Volume averages <.>_V use the trapezoid rule in z (half weight on the
+ * plates) and the plain mean in x, y; T_sa = T - (1 - D z). */
+typedef struct cm_diag {
+    long long step;   /* steps completed when sampled */
+    double t;         /* simulated time */
+    double dt;        /* time step of the next step */
+    double Nu;        /* 1 + Nu_conv + Nu_K */
+    double Nu_conv;   /* sqrt(Ra Pr)/eps <rho u_z T_sa>_V */
+    double Nu_K;      /* D sqrt(Ra Pr)/2 <rho u_z u^2>_V */
+    double Nu_bot;    /* -(1/eps) d<T_sa>_A/dz at z = 0 (second-order forward difference) */
+    double Nu_top;    /* same at z = 1 (second-order backward difference) */
+    double Nu_bar;    /* (Nu_bot + Nu_top)/2 */
+    double Re;        /* sqrt(Ra/Pr) sqrt(<u^2>_V) (instantaneous) */
+    double KE;        /* <rho u^2/2>_V */
+    double mass;      /* <rho>_V (conserved to round-off) */
+    double energy;    /* <E>_V */
+    double mach_max;  /* max |u|/c */
+    int status;       /* CM_OK, or CM_ENAN if a non-finite value was met */
+    int pad_;
+} cm_diag;
+
+/* Fill *p with the defaults listed in cm_params.  Never fails for p != NULL. */
+int cm_default_params(cm_params* p);
+
+/* Bytes of device memory the two state buffers need (for cm_params.state_buf).
+ * grid: host; precision: CM_FP64 or CM_FP32; bytes: host out. */
+int cm_state_bytes(const cm_grid* grid, int precision, unsigned long long* bytes);
+
+/* Create the context and write the initial state: the
+ * conduction / hydrostatic profile of constant K (T linear between the plate
+ * temperatures, dp/dz = -g rho, rho(0) = 1) plus an isobaric temperature
+ * perturbation A*xi at interior nodes, xi uniform in [-1, 1) from SplitMix64
+ * of (seed, dense node index); u = 0.  Also computes the first dt.
+ * grid, params: host (params may be NULL for the defaults).  Ra, Pr, gamma:
+ * Rayleigh and Prandtl numbers and cp/cv (Sec. 2).  Returns CM_EINVAL for a
+ * bad grid or parameter, CM_EUNSTABLE if the explicit diffusion number at the
+ * first dt exceeds 1/2, CM_ENOMEM / CM_ECUDA on device failures. */
+int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_params* params);
+
+/* Queue n full time steps (Sec. 3.1, Eq. time_step):
+ *   X^{n+1} = L_x L_y L_z L_x L_y L_z X^n, each L_alpha at dt/2 (rightmost first),
+ * where L_alpha is the fused predictor / plate fill / corrector / average /
+ * TVD sweep along alpha and dt comes from the state at the start of the step
+ * (computed on the device by the previous step; the host never reads it).
+ * Asynchronous on the context's stream.  n >= 0. */
+int cm_step(int n);
+
+/* Queue one diagnostics sample of the current state now (Sec. 2 definitions). */
+int cm_sample(void);
+
+/* Wait for the stream, then copy up to max queued samples (oldest first) to
+ * out (host, max entries) and drop them; *n_out (host) receives the count.
+ * Returns CM_ENAN if any copied sample saw a non-finite value. */
+int cm_diagnostics(cm_diag* out, int max, int* n_out);
+
+/* Device pointer to field f (0 <= f < nfields) of the current state, or NULL
+ * if there is no context or f is out of range.  Layout: see cm_state_layout. */
+void* cm_state_ptr(int field);
+
+/* Layout of the current state on the device: element (k, j, i) of field f is
+ * at cm_state_ptr(f)[(k*ny + j)*pitch + i]; elem_bytes is 8 (FP64) or 4 (FP32).
+ * All arguments are host out-pointers; any may be NULL. */
+int cm_state_layout(int* pitch, int* nfields, int* elem_bytes);
+
+/* Wait for the stream and copy the current state into host (dense float64,
+ * nfields*nz*ny*nx values, layout in the header comment). */
+int cm_get_state(double* host);
+
+/* Replace the current state by host (dense float64, same layout; converted
+ * to the context's precision) and recompute dt from it.  Blocking. */
+int cm_set_state(const double* host);
+
+/* End-to-end call with host buffers: upload state_in (host, dense float64,
+ * may be NULL to keep the device state), run nsteps steps, then write the
+ * final state to state_out (host, may be NULL) and one diagnostics sample of
+ * the final state to diag_out (host, may be NULL).  Blocking. */
+int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* diag_out);
+
+/* Queue exactly one directional sweep L_dir(Delta) (dir 0 = x, 1 = y, 2 = z)
+ * on the current state (Sec. 3.1 predictor, corrector, average and TVD term),
+ * without touching dt or time.  For tests of single operators. */
+int cm_sweep(int dir, double Delta);
+
+/* Wait for the stream; *dt (host) = the dt the next step will use. */
+int cm_get_dt(double* dt);
+
+/* Wait for the stream; simulated time and completed steps (host out). */
+int cm_get_time(double* t, long long* steps);
+
+/* Measurement: queue n steps exactly as cm_step does, with CUDA events
+ * recorded on the context's stream around every sweep launch.  Before each
+ * step (outside the event brackets) a device buffer of flush_bytes is
+ * overwritten with cudaMemsetAsync to evict the L2 cache (0 = no flush).
+ * Waits once at the end.  ms_out (host, 4 entries in 2D: positions z, x, z,
+ * x of a step) receives the mean device duration in ms of the sweeps at each
+ * position; step_ms (host, n entries, may be NULL) the device duration of
+ * each step.  n >= 1. */
+int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, double* step_ms);
+
+/* Number of CUDA kernel launches this context has queued since cm_init. */
+long long cm_launch_count(void);
+
+/* Wait for all queued work of the context. */
+int cm_sync(void);
+
+/* Write / read a checkpoint: a header {magic, version, grid, precision,
+ * parameter hash, step, t} followed by the dense state in the context's
+ * precision.  cm_load needs a context created with the same grid, precision
+ * and parameters; it returns CM_EBADCKPT otherwise.  Blocking.  path: host. */
+int cm_save(const char* path);
+int cm_load(const char* path);
+
+/* Free the context and its device memory (not caller-owned state_buf). */
+int cm_finalize(void);
+
+/* Message of the last failure (static storage; never NULL). */
+const char* cm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CM_H */

@@ -1,0 +1,86 @@
+"""GB300-native MacCormack-TVD solver for fully compressible convection
+(arXiv 2411.10372, Sec. 2 equations, Sec. 3.1 scheme).
+
+The compute path is libcm.so (hand-written sm_103a CUDA kernels behind the C
+ABI of include/cm.h); this package is its thin Python binding.  `Solver` is a
+convenience wrapper that fills the C structs and moves numpy arrays; it does
+no arithmetic of the method.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from ._binding import (CM_EBADCKPT, CM_ECUDA, CM_EINVAL, CM_ENAN, CM_ENOMEM, CM_ENOTINIT, CM_EUNSTABLE,
+                       CM_FP32, CM_FP64, CM_OK, CM_TVD_DAVIS, CM_TVD_OFF, CM_TVD_SUM, CMError, cm_default_params,
+                       cm_diag, cm_diagnostics, cm_finalize, cm_get_dt, cm_get_state, cm_get_time, cm_grid,
+                       cm_init, cm_last_error, cm_launch_count, cm_load, cm_profile_steps, cm_params, cm_run_host, cm_sample,
+                       cm_save, cm_set_state, cm_state_bytes, cm_state_layout, cm_state_ptr, cm_step, cm_sweep,
+                       cm_sync, lib)
+
+__all__ = [n for n in dir() if n.startswith("cm_") or n.startswith("CM")] + ["Solver", "lib"]
+
+
+class Solver:
+    """One solver context (the library keeps a single context per process).
+
+    Parameters follow cm_params; `precision` is "fp64" or "fp32".  `stream`
+    may be a torch.cuda.Stream (its handle is passed to the library)."""
+
+    def __init__(self, nx: int, nz: int, Ra: float, Pr: float = 1.0, gamma: float = 5.0 / 3.0, *,
+                 ny: int = 1, ndim: int = 2, aspect: float = 4.0, precision: str = "fp64", stream=None, **params):
+        self.grid = cm_grid(ndim, nx, ny if ndim == 3 else 1, nz, aspect)
+        p = cm_default_params()
+        t_top_given = "t_top" in params
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        if not t_top_given:
+            p.t_top = 1.0 - p.eps - p.D
+        p.precision = CM_FP64 if precision == "fp64" else CM_FP32
+        if stream is not None:
+            p.stream = getattr(stream, "cuda_stream", stream)
+        self.params = p
+        self.Ra, self.Pr, self.gamma = Ra, Pr, gamma
+        self.nf = 5 if ndim == 3 else 4
+        cm_init(self.grid, Ra, Pr, gamma, p)
+
+    @property
+    def shape(self) -> tuple:
+        g = self.grid
+        if g.ndim == 3:
+            return (5, g.nz, g.ny, g.nx)
+        return (4, g.nz, g.nx)
+
+    def state(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float64)
+        return cm_get_state(out)
+
+    def set_state(self, X: np.ndarray):
+        cm_set_state(np.ascontiguousarray(X, dtype=np.float64).reshape(self.shape))
+
+    def step(self, n: int = 1):
+        cm_step(n)
+
+    def sweep(self, direction: int, Delta: float):
+        cm_sweep(direction, Delta)
+
+    def sample(self) -> dict:
+        cm_diagnostics(1 << 16)  # drop anything queued before
+        cm_sample()
+        return cm_diagnostics(1)[0]
+
+    def diagnostics(self, max_samples: int = 1 << 16) -> list[dict]:
+        return cm_diagnostics(max_samples)
+
+    def dt(self) -> float:
+        return cm_get_dt()
+
+    def time(self) -> tuple[float, int]:
+        return cm_get_time()
+
+    def sync(self):
+        cm_sync()
+
+    def close(self):
+        cm_finalize()

@@ -1,0 +1,221 @@
+"""ctypes binding of include/cm.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; all
+arithmetic of the solver runs in the CUDA kernels of libcm.so.  There is no
+fallback: if libcm.so cannot be loaded, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcm.so")
+
+CM_OK, CM_EINVAL, CM_ECUDA, CM_ENOTINIT, CM_ENAN = 0, -1, -2, -3, -4
+CM_EUNSTABLE, CM_ENOMEM, CM_EBADCKPT = -7, -8, -9
+CM_FP64, CM_FP32 = 0, 1
+CM_TVD_DAVIS, CM_TVD_SUM, CM_TVD_OFF = 0, 1, 2
+
+
+class cm_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("aspect", ctypes.c_double)]
+
+
+class cm_params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("D", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("dt_fixed", ctypes.c_double), ("gravity", ctypes.c_double), ("t_bot", ctypes.c_double),
+                ("t_top", ctypes.c_double), ("pert_amp", ctypes.c_double), ("stokes", ctypes.c_double),
+                ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int), ("tvd_form", ctypes.c_int),
+                ("diag_every", ctypes.c_int), ("diag_capacity", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("state_buf", ctypes.c_void_p)]
+
+
+class cm_diag(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("t", ctypes.c_double), ("dt", ctypes.c_double),
+                ("Nu", ctypes.c_double), ("Nu_conv", ctypes.c_double), ("Nu_K", ctypes.c_double),
+                ("Nu_bot", ctypes.c_double), ("Nu_top", ctypes.c_double), ("Nu_bar", ctypes.c_double),
+                ("Re", ctypes.c_double), ("KE", ctypes.c_double), ("mass", ctypes.c_double),
+                ("energy", ctypes.c_double), ("mach_max", ctypes.c_double), ("status", ctypes.c_int),
+                ("pad_", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
+
+
+class CMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_SIGS = {
+    "cm_default_params": (ctypes.c_int, [ctypes.POINTER(cm_params)]),
+    "cm_state_bytes": (ctypes.c_int, [ctypes.POINTER(cm_grid), ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "cm_init": (ctypes.c_int, [ctypes.POINTER(cm_grid), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.POINTER(cm_params)]),
+    "cm_step": (ctypes.c_int, [ctypes.c_int]),
+    "cm_sample": (ctypes.c_int, []),
+    "cm_diagnostics": (ctypes.c_int, [ctypes.POINTER(cm_diag), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "cm_state_ptr": (ctypes.c_void_p, [ctypes.c_int]),
+    "cm_state_layout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)] * 3),
+    "cm_get_state": (ctypes.c_int, [ctypes.c_void_p]),
+    "cm_set_state": (ctypes.c_int, [ctypes.c_void_p]),
+    "cm_run_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cm_diag)]),
+    "cm_sweep": (ctypes.c_int, [ctypes.c_int, ctypes.c_double]),
+    "cm_get_dt": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "cm_get_time": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "cm_profile_steps": (ctypes.c_int, [ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "cm_launch_count": (ctypes.c_longlong, []),
+    "cm_sync": (ctypes.c_int, []),
+    "cm_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "cm_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cm_finalize": (ctypes.c_int, []),
+    "cm_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load libcm.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            from . import build as _build
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != CM_OK:
+        raise CMError(rc, lib().cm_last_error().decode())
+    return rc
+
+
+def _dp(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ---- the C entry points, same names -----------------------------------------
+
+def cm_default_params() -> cm_params:
+    p = cm_params()
+    _check(lib().cm_default_params(ctypes.byref(p)))
+    return p
+
+
+def cm_state_bytes(grid: cm_grid, precision: int) -> int:
+    b = ctypes.c_ulonglong()
+    _check(lib().cm_state_bytes(ctypes.byref(grid), precision, ctypes.byref(b)))
+    return b.value
+
+
+def cm_init(grid: cm_grid, Ra: float, Pr: float, gamma: float, params: cm_params | None = None):
+    _check(lib().cm_init(ctypes.byref(grid), Ra, Pr, gamma, ctypes.byref(params) if params is not None else None))
+
+
+def cm_step(n: int):
+    _check(lib().cm_step(int(n)))
+
+
+def cm_sample():
+    _check(lib().cm_sample())
+
+
+def cm_diagnostics(max_samples: int = 4096) -> list[dict]:
+    buf = (cm_diag * max(max_samples, 1))()
+    n = ctypes.c_int()
+    rc = lib().cm_diagnostics(buf, max_samples, ctypes.byref(n))
+    out = [buf[i].as_dict() for i in range(n.value)]
+    _check(rc)
+    return out
+
+
+def cm_state_ptr(field: int) -> int:
+    return lib().cm_state_ptr(field) or 0
+
+
+def cm_state_layout() -> tuple[int, int, int]:
+    p, n, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().cm_state_layout(ctypes.byref(p), ctypes.byref(n), ctypes.byref(e)))
+    return p.value, n.value, e.value
+
+
+def cm_get_state(out: np.ndarray) -> np.ndarray:
+    _check(lib().cm_get_state(_dp(out)))
+    return out
+
+
+def cm_set_state(state: np.ndarray):
+    _check(lib().cm_set_state(_dp(np.ascontiguousarray(state, dtype=np.float64))))
+
+
+def cm_run_host(state_in: np.ndarray | None, nsteps: int, state_out: np.ndarray | None = None,
+                want_diag: bool = True):
+    d = cm_diag()
+    _check(lib().cm_run_host(_dp(state_in), int(nsteps), _dp(state_out), ctypes.byref(d) if want_diag else None))
+    return d.as_dict() if want_diag else None
+
+
+def cm_sweep(direction: int, Delta: float):
+    _check(lib().cm_sweep(int(direction), float(Delta)))
+
+
+def cm_get_dt() -> float:
+    v = ctypes.c_double()
+    _check(lib().cm_get_dt(ctypes.byref(v)))
+    return v.value
+
+
+def cm_get_time() -> tuple[float, int]:
+    t, s = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib().cm_get_time(ctypes.byref(t), ctypes.byref(s)))
+    return t.value, s.value
+
+
+def cm_profile_steps(n: int, flush_bytes: int = 0) -> tuple[list[float], list[float]]:
+    """(mean ms per sweep position, ms of each step) of n profiled steps."""
+    ms = (ctypes.c_double * 4)()
+    steps = (ctypes.c_double * n)()
+    _check(lib().cm_profile_steps(int(n), int(flush_bytes), ms, steps))
+    return list(ms), list(steps)
+
+
+def cm_launch_count() -> int:
+    return int(lib().cm_launch_count())
+
+
+def cm_sync():
+    _check(lib().cm_sync())
+
+
+def cm_save(path: str):
+    _check(lib().cm_save(path.encode()))
+
+
+def cm_load(path: str):
+    _check(lib().cm_load(path.encode()))
+
+
+def cm_finalize():
+    _check(lib().cm_finalize())
+
+
+def cm_last_error() -> str:
+    return lib().cm_last_error().decode()

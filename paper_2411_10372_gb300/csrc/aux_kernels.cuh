@@ -1,0 +1,194 @@
+// aux_kernels.cuh -- initial state, standalone dt reduction and the FP64
+// diagnostics reduction (Sec. 2: Eqs. volume_Nu, mean_Nu, Re).
+#pragma once
+#include "cm_device.cuh"
+#include "../../include/cm.h"
+
+namespace cm {
+
+// SplitMix64 (Steele, Lea & Flood 2014): output idx+1 of the generator seeded
+// with `seed`, i.e. the finaliser applied to seed + (idx+1) * golden gamma.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long idx)
+{
+    unsigned long long z = seed + (idx + 1ULL) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+
+// Initial state: T = T_c(z) + A xi at interior nodes (plates unperturbed),
+// rho = p_c(z)/(a T) (isobaric), u = 0, E = rho (T/b + g z).  FP64, then
+// rounded to the state precision.  Grid: x-threads over (i, j), y-blocks over k.
+template <class R>
+__global__ void init_state(R* X, Coef<R> C, InitArgs A)
+{
+    const int k = blockIdx.y;
+    const long long row = (long long)C.nx * C.ny;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < row; n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % C.nx);
+        const int j = (int)(n / C.nx);
+        const unsigned long long dense = ((unsigned long long)k * C.ny + j) * C.nx + i;
+        double T = A.Tc[k];
+        if (k > 0 && k < C.nz - 1) {
+            const double u = (double)(splitmix64(A.seed, dense) >> 11) * 0x1.0p-53;
+            T = A.Tc[k] + A.amp * (2.0 * u - 1.0);
+        }
+        const double rho = A.pc[k] / (A.a * T);
+        const double E = rho * (T / A.b + A.g * A.zt[k]);
+        R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
+        const long long fs = C.fstride;
+        p[0] = (R)rho;
+        p[fs] = R(0);
+        p[2 * fs] = R(0);
+        if (C.ndim == 3) {
+            p[3 * fs] = R(0);
+            p[4 * fs] = (R)E;
+        } else {
+            p[3 * fs] = (R)E;
+        }
+    }
+}
+
+// min over nodes and directions of h/(|u|+c) into a dt slot (used at init and
+// after cm_set_state; during stepping the last sweep does this reduction)
+template <class R>
+__global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int slot)
+{
+    double vmin = 1e308;
+    int bad = 0;
+    const long long plane = (long long)C.nx * C.ny;
+    const long long total = plane * C.nz;
+    const long long fs = C.fstride;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total; n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % C.nx);
+        const long long jk = n / C.nx;
+        const int j = (int)(jk % C.ny);
+        const int k = (int)(jk / C.ny);
+        const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
+        const R rho = p[0];
+        const R ri = R(1) / rho;
+        R ux = p[fs] * ri, uy = R(0), uz, E;
+        if (C.ndim == 3) { uy = p[2 * fs] * ri; uz = p[3 * fs] * ri; E = p[4 * fs]; }
+        else { uz = p[2 * fs] * ri; E = p[3 * fs]; }
+        const R T = C.b * (E * ri - R(0.5) * ((ux * ux + uy * uy) + uz * uz) - C.g * zt[k]);
+        const double c = sqrt((double)C.cs2 * (double)T);
+        double v = fmin(C.dx / (fabs((double)ux) + c), C.dz / (fabs((double)uz) + c));
+        if (C.ndim == 3) v = fmin(v, C.dy / (fabs((double)uy) + c));
+        if (!(v > 0.0) || !(v < 1e300)) bad = 1;
+        vmin = fmin(vmin, v);
+    }
+    block_dt_reduce(vmin, bad, ctl, slot);
+}
+
+// ---- diagnostics ---------------------------------------------------------
+
+// deterministic block sum of kDiagQ doubles (fixed tree); result in thread 0
+__device__ __forceinline__ void block_sum_q(double (&v)[kDiagQ], double* out)
+{
+    __shared__ double sh[kDiagThreads / 32][kDiagQ];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int q = 0; q < kDiagQ; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = (q == kDiagQ - 1) ? fmax(x, y) : x + y;
+        }
+        if (l == 0) sh[w][q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kDiagQ; ++q) {
+            double x = sh[0][q];
+            for (int ww = 1; ww < kDiagThreads / 32; ++ww) x = (q == kDiagQ - 1) ? fmax(x, sh[ww][q]) : x + sh[ww][q];
+            out[q] = x;
+        }
+    }
+}
+
+// per-plane FP64 sums of the diagnostics integrands; one block per plane k,
+// results in scratch[k*kDiagQ + q]
+template <class R>
+__global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> C, DiagArgs A, double* scratch, DevCtl* ctl)
+{
+    const int k = blockIdx.x;
+    const double z = A.zt[k];
+    const long long plane = (long long)C.nx * C.ny;
+    const long long fs = C.fstride;
+    double v[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int bad = 0;
+    for (long long n = threadIdx.x; n < plane; n += kDiagThreads) {
+        const int i = (int)(n % C.nx);
+        const int j = (int)(n / C.nx);
+        const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
+        const double rho = (double)p[0];
+        const double u = (double)p[fs] / rho;
+        double vy = 0.0, w, E;
+        if (C.ndim == 3) { vy = (double)p[2 * fs] / rho; w = (double)p[3 * fs] / rho; E = (double)p[4 * fs]; }
+        else { w = (double)p[2 * fs] / rho; E = (double)p[3 * fs]; }
+        const double u2 = u * u + vy * vy + w * w;
+        const double T = A.b * (E / rho - 0.5 * u2 - A.g * z);
+        const double Tsa = T - (1.0 - A.D * z);
+        v[0] += rho;
+        v[1] += E;
+        v[2] += rho * w * Tsa;
+        v[3] += rho * w * u2;
+        v[4] += u2;
+        v[5] += 0.5 * rho * u2;
+        v[6] += T;
+        const double M = sqrt(u2) / sqrt(A.cs2 * T);
+        v[7] = fmax(v[7], M);
+        if (!isfinite(E + rho + T + u2)) bad = 1;
+    }
+    block_sum_q(v, scratch + (size_t)k * kDiagQ);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, 1);
+}
+
+
+#ifdef CM_DEFINE_DIAG_FINAL  // one definition, in kernels_f64.cu
+// combine the plane sums (trapezoid weights, fixed order) into one cm_diag
+// record: Eq. volume_Nu, Eq. mean_Nu (second-order one-sided differences of
+// <T_sa>_A at the plates), Eq. Re (instantaneous), KE, mass, energy
+__global__ void __launch_bounds__(kDiagThreads) diag_final(const double* scratch, const double* zt, DiagFinal F, DevCtl* ctl, cm_diag* rec)
+{
+    double v[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < F.nz; k += kDiagThreads) {
+        const double w = (k == 0 || k == F.nz - 1) ? 0.5 : 1.0;
+        for (int q = 0; q < 6; ++q) v[q] += w * scratch[(size_t)k * kDiagQ + q];
+        v[7] = fmax(v[7], scratch[(size_t)k * kDiagQ + 7]);
+    }
+    __shared__ double tot[kDiagQ];
+    block_sum_q(v, tot);
+    if (threadIdx.x == 0) {
+        const double vol = F.cells * (double)(F.nz - 1);
+        const double sRP = sqrt(F.Ra * F.Pr);
+        cm_diag d;
+        d.Nu_conv = sRP / F.eps * (tot[2] / vol);
+        d.Nu_K = F.D * sRP / 2.0 * (tot[3] / vol);
+        d.Nu = 1.0 + d.Nu_conv + d.Nu_K;
+        const int K = F.nz - 1;
+        const double dz = 1.0 / (double)K;
+        double f[3], g[3];
+        for (int q = 0; q < 3; ++q) {
+            f[q] = scratch[(size_t)q * kDiagQ + 6] / F.cells - (1.0 - F.D * zt[q]);
+            g[q] = scratch[(size_t)(K - q) * kDiagQ + 6] / F.cells - (1.0 - F.D * zt[K - q]);
+        }
+        d.Nu_bot = -(1.0 / F.eps) * (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz);
+        d.Nu_top = -(1.0 / F.eps) * (3.0 * g[0] - 4.0 * g[1] + g[2]) / (2.0 * dz);
+        d.Nu_bar = (d.Nu_bot + d.Nu_top) / 2.0;
+        d.Re = sqrt(F.Ra / F.Pr) * sqrt(tot[4] / vol);
+        d.KE = tot[5] / vol;
+        d.mass = tot[0] / vol;
+        d.energy = tot[1] / vol;
+        d.mach_max = tot[7];
+        d.step = (long long)ctl->steps;
+        d.t = ctl->t;
+        d.dt = F.dt_fixed > 0.0 ? F.dt_fixed : F.cfl * __longlong_as_double((long long)ctl->dt_slot[F.slot]);
+        d.status = (ctl->status & 1) || !isfinite(d.Nu + d.Nu_bar + d.Re + d.energy) ? CM_ENAN : CM_OK;
+        d.pad_ = 0;
+        *rec = d;
+    }
+}
+#endif
+
+}  // namespace cm

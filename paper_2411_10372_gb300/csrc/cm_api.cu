@@ -1,0 +1,726 @@
+// cm_api.cu -- the C ABI of include/cm.h: context, stepping driver,
+// diagnostics ring, host transfers, checkpoints.
+//
+// A step (Sec. 3.1, Eq. time_step) is 4 sweep launches in 2D (z, x, z, x).
+// The dt of a step is produced on the device by the previous step's last
+// sweep (an FP64 atomic min of h/(|u|+c) over the new state into one of two
+// slots) and read by the next step's sweeps, so the host never waits on it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/cm.h"
+#include "kernels.h"
+
+using namespace cm;
+
+namespace {
+
+struct Ctx {
+    cm_grid grid;
+    cm_params prm;
+    double Ra, Pr, gamma;
+    int nf, ny, pitch, prec;
+    long long fstride;          // elements between fields
+    size_t elem;                // bytes per element
+    size_t buf_bytes;           // bytes of one state buffer
+    void* buf[2];
+    bool own_buf;
+    int cur;                    // buffer holding the current state
+    void* zt_r;                 // z table in the state precision
+    double* zt_d;               // z table, FP64
+    double* Tc_d;
+    double* pc_d;
+    DevCtl* ctl;
+    double* scratch;            // per-plane diagnostics sums (nz * kDiagQ)
+    double* dense;              // dense FP64 staging for host transfers (lazy)
+    cm_diag* ring;
+    int ring_cap, ring_head, ring_count;
+    cudaStream_t stream;
+    long long step;
+    long long launches;
+    int seg_rows;
+    Coef<double> cd;
+    Coef<float> cf;
+    double a, b, g, cs2;
+};
+
+Ctx* g_ctx = nullptr;
+char g_err[512] = "no error";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(CM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define NEED_CTX() \
+    do { if (!g_ctx) return fail(CM_ENOTINIT, "no context: call cm_init first"); } while (0)
+
+template <class R>
+void fill_coef(Coef<R>& C, const Ctx& c)
+{
+    const cm_grid& G = c.grid;
+    const cm_params& P = c.prm;
+    double dx = G.aspect / G.nx, dy = G.aspect / c.ny, dz = 1.0 / (G.nz - 1);
+    C.a = (R)c.a;
+    C.b = (R)c.b;
+    C.g = (R)c.g;
+    C.mu = (R)std::sqrt(c.Pr / c.Ra);
+    C.kth = (R)(1.0 / (P.eps * P.D * std::sqrt(c.Ra * c.Pr)));
+    C.cs2 = (R)c.cs2;
+    C.stokes = (R)P.stokes;
+    C.inv_dx = (R)(1.0 / dx);
+    C.inv_dy = (R)(1.0 / dy);
+    C.inv_dz = (R)(1.0 / dz);
+    C.inv_2dx = (R)(1.0 / (2.0 * dx));
+    C.inv_2dy = (R)(1.0 / (2.0 * dy));
+    C.inv_2dz = (R)(1.0 / (2.0 * dz));
+    C.ebot = (R)(P.t_bot / c.b + c.g * 0.0);
+    C.etop = (R)(P.t_top / c.b + c.g * 1.0);
+    C.dx = dx;
+    C.dy = dy;
+    C.dz = dz;
+    C.cfl = P.cfl;
+    C.dt_fixed = P.dt_fixed;
+    C.nx = G.nx;
+    C.ny = c.ny;
+    C.nz = G.nz;
+    C.pitch = c.pitch;
+    C.fstride = c.fstride;
+    C.tvd_form = P.tvd_form;
+    C.ndim = G.ndim;
+}
+
+void free_ctx(Ctx* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->own_buf && c->buf[0]) cudaFree(c->buf[0]);
+    cudaFree(c->zt_r);
+    cudaFree(c->zt_d);
+    cudaFree(c->Tc_d);
+    cudaFree(c->pc_d);
+    cudaFree(c->ctl);
+    cudaFree(c->scratch);
+    cudaFree(c->dense);
+    cudaFree(c->ring);
+    delete c;
+}
+
+int check_grid(const cm_grid* G)
+{
+    if (!G) return fail(CM_EINVAL, "grid is NULL");
+    if (G->ndim != 2) return fail(CM_EINVAL, "ndim = %d: this build steps 2D grids", G->ndim);
+    if (G->nx < 4 || G->nz < 5) return fail(CM_EINVAL, "grid too small: nx >= 4 and nz >= 5 needed (got %d, %d)", G->nx, G->nz);
+    if ((long long)G->nx * G->nz > (1LL << 31)) return fail(CM_EINVAL, "grid too large");
+    if (!(G->aspect > 0)) return fail(CM_EINVAL, "aspect must be > 0");
+    return CM_OK;
+}
+
+int pitch_of(int nx, int prec)
+{
+    const int align = prec == CM_FP64 ? 32 : 64;  // 256-byte rows
+    return (nx + align - 1) / align * align;
+}
+
+// queue one sweep on the current buffer and swap buffers
+int sweep(Ctx* c, int dir, const SweepCtl& sc)
+{
+    cudaError_t e;
+    if (c->prec == CM_FP64)
+        e = Launch<double>::sweep(dir, (const double*)c->buf[c->cur], (double*)c->buf[c->cur ^ 1],
+                                  (const double*)c->zt_r, c->cd, sc, c->seg_rows, c->stream);
+    else
+        e = Launch<float>::sweep(dir, (const float*)c->buf[c->cur], (float*)c->buf[c->cur ^ 1],
+                                 (const float*)c->zt_r, c->cf, sc, c->seg_rows, c->stream);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+    c->launches++;
+    c->cur ^= 1;
+    return CM_OK;
+}
+
+int recompute_dt(Ctx* c, int slot)
+{
+    unsigned long long inf = 0x7FF0000000000000ULL;
+    CK(cudaMemcpyAsync(&c->ctl->dt_slot[slot], &inf, sizeof inf, cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = c->prec == CM_FP64
+        ? Launch<double>::dt((const double*)c->buf[c->cur], (const double*)c->zt_r, c->cd, c->ctl, slot, c->stream)
+        : Launch<float>::dt((const float*)c->buf[c->cur], (const float*)c->zt_r, c->cf, c->ctl, slot, c->stream);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "dt launch: %s", cudaGetErrorString(e));
+    c->launches++;
+    return CM_OK;
+}
+
+int sample(Ctx* c)
+{
+    int slot;
+    if (c->ring_count == c->ring_cap) {  // full: drop the oldest
+        c->ring_head = (c->ring_head + 1) % c->ring_cap;
+        c->ring_count--;
+    }
+    slot = (c->ring_head + c->ring_count) % c->ring_cap;
+    DiagArgs A;
+    A.zt = c->zt_d;
+    A.a = c->a;
+    A.b = c->b;
+    A.g = c->g;
+    A.D = c->prm.D;
+    A.cs2 = c->cs2;
+    cudaError_t e = c->prec == CM_FP64
+        ? Launch<double>::diag_planes((const double*)c->buf[c->cur], c->cd, A, c->scratch, c->ctl, c->stream)
+        : Launch<float>::diag_planes((const float*)c->buf[c->cur], c->cf, A, c->scratch, c->ctl, c->stream);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "diagnostics launch: %s", cudaGetErrorString(e));
+    DiagFinal F;
+    F.Ra = c->Ra;
+    F.Pr = c->Pr;
+    F.eps = c->prm.eps;
+    F.D = c->prm.D;
+    F.cfl = c->prm.cfl;
+    F.dt_fixed = c->prm.dt_fixed;
+    F.cells = (double)c->grid.nx * c->ny;
+    F.nz = c->grid.nz;
+    F.slot = (int)(c->step & 1);
+    e = launch_diag_final(c->scratch, c->zt_d, F, c->ctl, c->ring + slot, c->stream);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "diagnostics launch: %s", cudaGetErrorString(e));
+    c->launches += 2;
+    c->ring_count++;
+    return CM_OK;
+}
+
+int ensure_dense(Ctx* c)
+{
+    if (c->dense) return CM_OK;
+    size_t n = (size_t)c->nf * c->grid.nz * c->ny * c->grid.nx;
+    if (cudaMalloc(&c->dense, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CM_ENOMEM, "cudaMalloc of %zu bytes (host transfer staging) failed", n * sizeof(double));
+    }
+    return CM_OK;
+}
+
+size_t dense_count(const Ctx* c) { return (size_t)c->nf * c->grid.nz * c->ny * c->grid.nx; }
+
+int upload(Ctx* c, const double* host)
+{
+    int rc = ensure_dense(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->dense, host, dense_count(c) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = c->prec == CM_FP64
+        ? Launch<double>::pack(c->dense, (double*)c->buf[c->cur], c->cd, c->nf, c->stream)
+        : Launch<float>::pack(c->dense, (float*)c->buf[c->cur], c->cf, c->nf, c->stream);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "pack launch: %s", cudaGetErrorString(e));
+    c->launches++;
+    return recompute_dt(c, (int)(c->step & 1));
+}
+
+int download(Ctx* c, double* host)
+{
+    int rc = ensure_dense(c);
+    if (rc) return rc;
+    cudaError_t e = c->prec == CM_FP64
+        ? Launch<double>::unpack((const double*)c->buf[c->cur], c->dense, c->cd, c->nf, c->stream)
+        : Launch<float>::unpack((const float*)c->buf[c->cur], c->dense, c->cf, c->nf, c->stream);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "unpack launch: %s", cudaGetErrorString(e));
+    c->launches++;
+    CK(cudaMemcpyAsync(host, c->dense, dense_count(c) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return CM_OK;
+}
+
+// queue n steps; with ev != NULL (5 events per step), record ev[5s+q]
+// before sweep q of step s and ev[5s+4] after its last sweep; with flush,
+// overwrite flush_bytes of it before each step, outside the brackets
+int queue_steps(Ctx* c, int n, cudaEvent_t* ev = nullptr, void* flush = nullptr, size_t flush_bytes = 0)
+{
+    for (int s = 0; s < n; ++s) {
+        const int slot = (int)(c->step & 1);
+        SweepCtl sc;
+        sc.ctl = c->ctl;
+        sc.slot_in = slot;
+        sc.Delta = 0.0;
+        const int order[4] = {2, 0, 2, 0};  // z, x, z, x: L_x L_z L_x L_z applied right to left
+        if (flush) CK(cudaMemsetAsync(flush, s & 0xff, flush_bytes, c->stream));
+        for (int q = 0; q < 4; ++q) {
+            sc.first = (q == 0);
+            sc.last = (q == 3);
+            if (ev) CK(cudaEventRecord(ev[5 * s + q], c->stream));
+            int rc = sweep(c, order[q], sc);
+            if (rc) return rc;
+        }
+        if (ev) CK(cudaEventRecord(ev[5 * s + 4], c->stream));
+        c->step++;
+        if (c->prm.diag_every > 0 && c->step % c->prm.diag_every == 0) {
+            int rc = sample(c);
+            if (rc) return rc;
+        }
+    }
+    return CM_OK;
+}
+
+unsigned long long fnv1a(const void* p, size_t n, unsigned long long h = 1469598103934665603ULL)
+{
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ULL; }
+    return h;
+}
+
+unsigned long long param_hash(const Ctx* c)
+{
+    double v[12] = {c->Ra, c->Pr, c->gamma, c->prm.eps, c->prm.D, c->prm.cfl, c->prm.dt_fixed,
+                    c->prm.gravity, c->prm.t_bot, c->prm.t_top, c->prm.stokes, (double)c->prm.tvd_form};
+    return fnv1a(v, sizeof v);
+}
+
+struct CkptHeader {
+    char magic[8];
+    int version, ndim, nx, ny, nz, precision;
+    long long step;
+    double t;
+    unsigned long long hash;
+};
+
+}  // namespace
+
+extern "C" {
+
+int cm_default_params(cm_params* p)
+{
+    if (!p) return fail(CM_EINVAL, "params is NULL");
+    std::memset(p, 0, sizeof *p);
+    p->eps = 0.1;
+    p->D = 0.5;
+    p->cfl = 0.5;
+    p->dt_fixed = 0.0;
+    p->gravity = 1.0;
+    p->t_bot = 1.0;
+    p->t_top = 1.0 - p->eps - p->D;
+    p->pert_amp = 1e-3;
+    p->stokes = -2.0 / 3.0;
+    p->seed = 12345ULL;
+    p->precision = CM_FP64;
+    p->tvd_form = CM_TVD_DAVIS;
+    p->diag_every = 0;
+    p->diag_capacity = 1024;
+    p->stream = nullptr;
+    p->state_buf = nullptr;
+    return CM_OK;
+}
+
+int cm_state_bytes(const cm_grid* grid, int precision, unsigned long long* bytes)
+{
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    if (precision != CM_FP64 && precision != CM_FP32) return fail(CM_EINVAL, "precision must be CM_FP64 or CM_FP32");
+    if (!bytes) return fail(CM_EINVAL, "bytes is NULL");
+    const int nf = grid->ndim == 3 ? 5 : 4;
+    const int ny = grid->ndim == 3 ? grid->ny : 1;
+    const size_t elem = precision == CM_FP64 ? 8 : 4;
+    *bytes = 2ULL * nf * (unsigned long long)grid->nz * ny * pitch_of(grid->nx, precision) * elem;
+    return CM_OK;
+}
+
+int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_params* params)
+{
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    cm_params P;
+    if (params) P = *params;
+    else cm_default_params(&P);
+    if (!(Ra > 0) || !(Pr > 0) || !(gamma > 1)) return fail(CM_EINVAL, "need Ra > 0, Pr > 0, gamma > 1");
+    if (!(P.eps > 0) || !(P.D > 0)) return fail(CM_EINVAL, "need eps > 0 and D > 0");
+    if (!(P.cfl > 0) || P.cfl > 1.0) return fail(CM_EINVAL, "cfl must be in (0, 1]");
+    if (!(P.t_bot > 0) || !(P.t_top > 0)) return fail(CM_EINVAL, "plate temperatures must be > 0");
+    if (P.precision != CM_FP64 && P.precision != CM_FP32) return fail(CM_EINVAL, "precision must be CM_FP64 or CM_FP32");
+    if (P.tvd_form < 0 || P.tvd_form > 2) return fail(CM_EINVAL, "tvd_form must be 0, 1 or 2");
+    if (P.diag_capacity < 1) P.diag_capacity = 1024;
+    if (P.state_buf && ((uintptr_t)P.state_buf & 255)) return fail(CM_EINVAL, "state_buf must be 256-byte aligned");
+
+    if (g_ctx) { free_ctx(g_ctx); g_ctx = nullptr; }
+    Ctx* c = new Ctx();
+    std::memset((void*)c, 0, sizeof *c);
+    c->grid = *grid;
+    c->prm = P;
+    c->Ra = Ra;
+    c->Pr = Pr;
+    c->gamma = gamma;
+    c->prec = P.precision;
+    c->nf = grid->ndim == 3 ? 5 : 4;
+    c->ny = grid->ndim == 3 ? grid->ny : 1;
+    c->pitch = pitch_of(grid->nx, c->prec);
+    c->elem = c->prec == CM_FP64 ? 8 : 4;
+    c->fstride = (long long)grid->nz * c->ny * c->pitch;
+    c->buf_bytes = (size_t)c->nf * c->fstride * c->elem;
+    c->stream = (cudaStream_t)P.stream;
+    c->ring_cap = P.diag_capacity;
+    c->a = (gamma - 1.0) / (gamma * P.eps * P.D);
+    c->b = gamma * P.eps * P.D;
+    c->g = P.gravity / P.eps;
+    c->cs2 = gamma * c->a;
+    // rows per warp segment: long segments amortise the 4-row pipeline
+    // ramp; shorter ones when the grid has too few strips to fill the GPU
+    {
+        const long long strips = (grid->nx + kOutW - 1) / kOutW;
+        int seg = 64;
+        while (seg > 16 && strips * ((grid->nz + seg - 1) / seg) < 152LL * 16) seg /= 2;
+        c->seg_rows = seg;
+    }
+    fill_coef(c->cd, *c);
+    fill_coef(c->cf, *c);
+
+    auto bail = [&](int code) { free_ctx(c); return code; };
+    const int nz = grid->nz;
+    if (P.state_buf) {
+        c->buf[0] = P.state_buf;
+        c->own_buf = false;
+    } else {
+        if (cudaMalloc(&c->buf[0], 2 * c->buf_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(CM_ENOMEM, "cudaMalloc of %zu bytes (state) failed", 2 * c->buf_bytes));
+        }
+        c->own_buf = true;
+    }
+    c->buf[1] = (char*)c->buf[0] + c->buf_bytes;
+    if (cudaMalloc(&c->zt_r, nz * c->elem) != cudaSuccess || cudaMalloc(&c->zt_d, nz * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->Tc_d, nz * sizeof(double)) != cudaSuccess || cudaMalloc(&c->pc_d, nz * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->ctl, sizeof(DevCtl)) != cudaSuccess ||
+        cudaMalloc(&c->scratch, (size_t)nz * kDiagQ * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->ring, (size_t)c->ring_cap * sizeof(cm_diag)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(CM_ENOMEM, "cudaMalloc of the work arrays failed"));
+    }
+
+    // conduction / hydrostatic profile of constant K, FP64 on the host (nz values)
+    std::vector<double> z(nz), Tc(nz), pc(nz), rhoc(nz);
+    const double Lam = P.t_bot - P.t_top;
+    double rho_min = 1e300;
+    for (int k = 0; k < nz; ++k) {
+        z[k] = (double)k / (double)(nz - 1);
+        Tc[k] = P.t_bot - Lam * z[k];
+        if (Lam != 0.0) pc[k] = c->a * P.t_bot * std::pow(Tc[k] / P.t_bot, c->g / (c->a * Lam));
+        else pc[k] = c->a * P.t_bot * std::exp(-c->g * z[k] / (c->a * P.t_bot));
+        rhoc[k] = pc[k] / (c->a * Tc[k]);
+        rho_min = std::fmin(rho_min, rhoc[k]);
+    }
+    std::vector<float> zf(nz);
+    for (int k = 0; k < nz; ++k) zf[k] = (float)z[k];
+    cudaStream_t s = c->stream;
+    if (cudaMemcpyAsync(c->zt_d, z.data(), nz * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->zt_r, c->prec == CM_FP64 ? (const void*)z.data() : (const void*)zf.data(), nz * c->elem,
+                        cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->Tc_d, Tc.data(), nz * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->pc_d, pc.data(), nz * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(c->buf[0], 0, 2 * c->buf_bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(CM_ECUDA, "upload of the profile tables failed"));
+    }
+    DevCtl h;
+    std::memset(&h, 0, sizeof h);
+    h.dt_slot[0] = h.dt_slot[1] = 0x7FF0000000000000ULL;
+    if (cudaMemcpyAsync(c->ctl, &h, sizeof h, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(CM_ECUDA, "upload of the control block failed"));
+    }
+    InitArgs A;
+    A.Tc = c->Tc_d;
+    A.pc = c->pc_d;
+    A.zt = c->zt_d;
+    A.a = c->a;
+    A.b = c->b;
+    A.g = c->g;
+    A.amp = P.pert_amp;
+    A.seed = P.seed;
+    cudaError_t e = c->prec == CM_FP64 ? Launch<double>::init((double*)c->buf[0], c->cd, A, s)
+                                        : Launch<float>::init((float*)c->buf[0], c->cf, A, s);
+    if (e != cudaSuccess) return bail(fail(CM_ECUDA, "init launch: %s", cudaGetErrorString(e)));
+    c->launches = 1;
+    c->cur = 0;
+    c->step = 0;
+    rc = recompute_dt(c, 0);
+    if (rc) return bail(rc);
+    // diffusion number of the explicit viscous / conduction terms at the first dt
+    if (cudaMemcpyAsync(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(CM_ECUDA, "init failed on the device: %s", cudaGetErrorString(cudaGetLastError())));
+    }
+    double hmin;
+    std::memcpy(&hmin, &h.dt_slot[0], sizeof hmin);
+    const double dt0 = P.dt_fixed > 0 ? P.dt_fixed : P.cfl * hmin;
+    if (!(dt0 > 0) || !std::isfinite(dt0) || (h.status & 1)) return bail(fail(CM_ENAN, "non-finite initial state"));
+    const double mu = std::sqrt(Pr / Ra), K = 1.0 / (P.eps * P.D * std::sqrt(Ra * Pr));
+    const double nu = std::fmax(4.0 / 3.0 * mu, K * c->b) / rho_min;
+    const double hh = std::fmin(grid->aspect / grid->nx, 1.0 / (nz - 1));
+    const double dnum = nu * 0.5 * dt0 / (hh * hh);
+    if (dnum > 0.5)
+        return bail(fail(CM_EUNSTABLE, "explicit diffusion number %.3g > 0.5 at dt = %.3g: refine dt (dt_fixed) or raise Ra", dnum, dt0));
+    g_ctx = c;
+    return CM_OK;
+}
+
+int cm_step(int n)
+{
+    NEED_CTX();
+    if (n < 0) return fail(CM_EINVAL, "n must be >= 0");
+    return queue_steps(g_ctx, n);
+}
+
+int cm_sample(void)
+{
+    NEED_CTX();
+    return sample(g_ctx);
+}
+
+int cm_diagnostics(cm_diag* out, int max, int* n_out)
+{
+    NEED_CTX();
+    if (n_out) *n_out = 0;
+    if (max < 0 || (max > 0 && !out)) return fail(CM_EINVAL, "bad output buffer");
+    Ctx* c = g_ctx;
+    CK(cudaStreamSynchronize(c->stream));
+    const int n = c->ring_count < max ? c->ring_count : max;
+    int status = CM_OK;
+    for (int q = 0; q < n; ++q) {
+        const int slot = (c->ring_head + q) % c->ring_cap;
+        CK(cudaMemcpy(out + q, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost));
+        if (out[q].status != CM_OK) status = CM_ENAN;
+    }
+    c->ring_head = (c->ring_head + n) % c->ring_cap;
+    c->ring_count -= n;
+    if (n_out) *n_out = n;
+    if (status) return fail(status, "a diagnostics sample met a non-finite value");
+    return CM_OK;
+}
+
+void* cm_state_ptr(int field)
+{
+    if (!g_ctx || field < 0 || field >= g_ctx->nf) return nullptr;
+    return (char*)g_ctx->buf[g_ctx->cur] + (size_t)field * g_ctx->fstride * g_ctx->elem;
+}
+
+int cm_state_layout(int* pitch, int* nfields, int* elem_bytes)
+{
+    NEED_CTX();
+    if (pitch) *pitch = g_ctx->pitch;
+    if (nfields) *nfields = g_ctx->nf;
+    if (elem_bytes) *elem_bytes = (int)g_ctx->elem;
+    return CM_OK;
+}
+
+int cm_get_state(double* host)
+{
+    NEED_CTX();
+    if (!host) return fail(CM_EINVAL, "host is NULL");
+    int rc = download(g_ctx, host);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(g_ctx->stream));
+    return CM_OK;
+}
+
+int cm_set_state(const double* host)
+{
+    NEED_CTX();
+    if (!host) return fail(CM_EINVAL, "host is NULL");
+    int rc = upload(g_ctx, host);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(g_ctx->stream));
+    return CM_OK;
+}
+
+int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* diag_out)
+{
+    NEED_CTX();
+    if (nsteps < 0) return fail(CM_EINVAL, "nsteps must be >= 0");
+    Ctx* c = g_ctx;
+    int rc;
+    if (state_in && (rc = upload(c, state_in))) return rc;
+    if ((rc = queue_steps(c, nsteps))) return rc;
+    if (state_out && (rc = download(c, state_out))) return rc;
+    if (diag_out) {
+        // a sample of the final state, outside the ring
+        if ((rc = sample(c))) return rc;
+        c->ring_count--;
+        const int slot = (c->ring_head + c->ring_count) % c->ring_cap;
+        CK(cudaMemcpyAsync(diag_out, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    if (diag_out && diag_out->status != CM_OK) return fail(CM_ENAN, "non-finite value in the final state");
+    return CM_OK;
+}
+
+int cm_sweep(int dir, double Delta)
+{
+    NEED_CTX();
+    if (dir != 0 && dir != 2) return fail(CM_EINVAL, "dir must be 0 (x) or 2 (z) for a 2D grid");
+    if (!(Delta > 0)) return fail(CM_EINVAL, "Delta must be > 0");
+    SweepCtl sc;
+    sc.ctl = g_ctx->ctl;
+    sc.slot_in = (int)(g_ctx->step & 1);
+    sc.first = 0;
+    sc.last = 0;
+    sc.Delta = Delta;
+    return sweep(g_ctx, dir, sc);
+}
+
+int cm_get_dt(double* dt)
+{
+    NEED_CTX();
+    if (!dt) return fail(CM_EINVAL, "dt is NULL");
+    DevCtl h;
+    CK(cudaMemcpyAsync(&h, g_ctx->ctl, sizeof h, cudaMemcpyDeviceToHost, g_ctx->stream));
+    CK(cudaStreamSynchronize(g_ctx->stream));
+    double m;
+    std::memcpy(&m, &h.dt_slot[g_ctx->step & 1], sizeof m);
+    *dt = g_ctx->prm.dt_fixed > 0 ? g_ctx->prm.dt_fixed : g_ctx->prm.cfl * m;
+    return CM_OK;
+}
+
+int cm_get_time(double* t, long long* steps)
+{
+    NEED_CTX();
+    DevCtl h;
+    CK(cudaMemcpyAsync(&h, g_ctx->ctl, sizeof h, cudaMemcpyDeviceToHost, g_ctx->stream));
+    CK(cudaStreamSynchronize(g_ctx->stream));
+    if (t) *t = h.t;
+    if (steps) *steps = (long long)h.steps;
+    return CM_OK;
+}
+
+int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, double* step_ms)
+{
+    NEED_CTX();
+    if (n < 1 || !ms_out) return fail(CM_EINVAL, "need n >= 1 and ms_out");
+    Ctx* c = g_ctx;
+    void* flush = nullptr;
+    if (flush_bytes) {
+        if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CM_ENOMEM, "cudaMalloc of the %llu-byte flush buffer failed", flush_bytes);
+        }
+    }
+    std::vector<cudaEvent_t> ev(5 * (size_t)n, nullptr);
+    int rc = CM_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { rc = fail(CM_ECUDA, "cudaEventCreate failed"); break; }
+    if (!rc) rc = queue_steps(c, n, ev.data(), flush, flush_bytes);
+    if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess)
+        rc = fail(CM_ECUDA, "profiled steps failed: %s", cudaGetErrorString(cudaGetLastError()));
+    double ms[4] = {0, 0, 0, 0};
+    for (int s = 0; !rc && s < n; ++s) {
+        double tot = 0;
+        for (int q = 0; q < 4; ++q) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[5 * s + q], ev[5 * s + q + 1]) != cudaSuccess) {
+                rc = fail(CM_ECUDA, "cudaEventElapsedTime failed");
+                break;
+            }
+            ms[q] += t;
+            tot += t;
+        }
+        if (step_ms) step_ms[s] = tot;
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (flush) cudaFree(flush);
+    if (rc) return rc;
+    for (int q = 0; q < 4; ++q) ms_out[q] = ms[q] / n;
+    return CM_OK;
+}
+
+long long cm_launch_count(void) { return g_ctx ? g_ctx->launches : 0; }
+
+int cm_sync(void)
+{
+    NEED_CTX();
+    CK(cudaStreamSynchronize(g_ctx->stream));
+    DevCtl h;
+    CK(cudaMemcpy(&h, g_ctx->ctl, sizeof h, cudaMemcpyDeviceToHost));
+    if (h.status & 1) return fail(CM_ENAN, "a non-finite value was met while stepping");
+    return CM_OK;
+}
+
+int cm_save(const char* path)
+{
+    NEED_CTX();
+    if (!path) return fail(CM_EINVAL, "path is NULL");
+    Ctx* c = g_ctx;
+    std::vector<double> host(dense_count(c));
+    int rc = download(c, host.data());
+    if (rc) return rc;
+    DevCtl h;
+    CK(cudaMemcpyAsync(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CkptHeader H;
+    std::memset(&H, 0, sizeof H);
+    std::memcpy(H.magic, "CMCKPT1", 8);
+    H.version = 1;
+    H.ndim = c->grid.ndim;
+    H.nx = c->grid.nx;
+    H.ny = c->ny;
+    H.nz = c->grid.nz;
+    H.precision = c->prec;
+    H.step = c->step;
+    H.t = h.t;
+    H.hash = param_hash(c);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(CM_EINVAL, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&H, sizeof H, 1, f) == 1 && std::fwrite(host.data(), sizeof(double), host.size(), f) == host.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? CM_OK : fail(CM_EINVAL, "write to %s failed", path);
+}
+
+int cm_load(const char* path)
+{
+    NEED_CTX();
+    if (!path) return fail(CM_EINVAL, "path is NULL");
+    Ctx* c = g_ctx;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(CM_EBADCKPT, "cannot open %s", path);
+    CkptHeader H;
+    std::vector<double> host(dense_count(c));
+    bool ok = std::fread(&H, sizeof H, 1, f) == 1;
+    ok = ok && std::memcmp(H.magic, "CMCKPT1", 8) == 0 && H.version == 1 && H.ndim == c->grid.ndim &&
+         H.nx == c->grid.nx && H.ny == c->ny && H.nz == c->grid.nz && H.precision == c->prec && H.hash == param_hash(c);
+    ok = ok && std::fread(host.data(), sizeof(double), host.size(), f) == host.size();
+    std::fclose(f);
+    if (!ok) return fail(CM_EBADCKPT, "%s is not a checkpoint of this grid, precision and parameter set", path);
+    for (double v : host)
+        if (!std::isfinite(v)) return fail(CM_EBADCKPT, "%s holds non-finite values", path);
+    c->step = H.step;
+    int rc = upload(c, host.data());
+    if (rc) return rc;
+    DevCtl h;
+    CK(cudaMemcpyAsync(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    h.t = H.t;
+    h.steps = (double)H.step;
+    CK(cudaMemcpyAsync(c->ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+int cm_finalize(void)
+{
+    if (g_ctx) {
+        free_ctx(g_ctx);
+        g_ctx = nullptr;
+    }
+    return CM_OK;
+}
+
+const char* cm_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,30 @@
+// kernels.h -- host-side launchers of the device kernels, one instantiation
+// per state precision (kernels_f64.cu, kernels_f32.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "cm_device.cuh"
+#include "../../include/cm.h"
+
+namespace cm {
+
+template <class R>
+struct Launch {
+    // one sweep L_dir (dir 0 = x, 2 = z; 2D)
+    static cudaError_t sweep(int dir, const R* in, R* out, const R* zt, const Coef<R>& C, const SweepCtl& sc,
+                             int seg_rows, cudaStream_t s);
+    static cudaError_t init(R* X, const Coef<R>& C, const InitArgs& A, cudaStream_t s);
+    static cudaError_t dt(const R* X, const R* zt, const Coef<R>& C, DevCtl* ctl, int slot, cudaStream_t s);
+    static cudaError_t diag_planes(const R* X, const Coef<R>& C, const DiagArgs& A, double* scratch, DevCtl* ctl,
+                                   cudaStream_t s);
+    // dense float64 [nf][nz][ny][nx] <-> pitched state in R
+    static cudaError_t pack(const double* dense, R* X, const Coef<R>& C, int nf, cudaStream_t s);
+    static cudaError_t unpack(const R* X, double* dense, const Coef<R>& C, int nf, cudaStream_t s);
+};
+
+cudaError_t launch_diag_final(const double* scratch, const double* zt, const DiagFinal& F, DevCtl* ctl, cm_diag* rec,
+                              cudaStream_t s);
+
+extern template struct Launch<double>;
+extern template struct Launch<float>;
+
+}  // namespace cm

@@ -1,0 +1,312 @@
+// sweep2d.cuh -- fused 2D sweep kernels L_z(Delta) and L_x(Delta) of Sec. 3.1.
+//
+// One warp owns a strip of 32 columns and marches along z through a segment
+// of rows, keeping the rows in flight in registers.  Lanes 2..29 produce the
+// strip's 28 output columns; lanes 0,1,30,31 are the halo the x-stencil and
+// the cross derivatives need (outputs of the neighbouring strips, recomputed).
+// Columns are periodic, so lane columns wrap modulo nx.  Neighbour values
+// across x travel by warp shuffle: no shared memory, no block barrier in the
+// march.  Per node and sweep the kernel reads the input state once and
+// writes the output state once (2 nf w bytes, the algorithmic minimum of a
+// sweep); everything in between -- primitives, F^n, predictor, plate fill,
+// F^P, corrector, average, TVD term, plate values -- stays in registers.
+#pragma once
+#include "cm_device.cuh"
+
+namespace cm {
+
+
+template <class R>
+struct SweepIO {
+    const R* in;
+    R* out;
+    const R* zt;     // z of each plane, in R
+    int seg_rows;    // rows per warp segment
+    int nstrips;     // ceil(nx / kOutW)
+};
+
+template <class R>
+__device__ __forceinline__ St<R> load_row(const R* __restrict__ base, long long fs, int row, int pitch, int ic)
+{
+    const R* s = base + (size_t)row * pitch + ic;
+    return {__ldg(s), __ldg(s + fs), __ldg(s + 2 * fs), __ldg(s + 3 * fs)};
+}
+
+template <class R>
+__device__ __forceinline__ void store_row(R* __restrict__ base, long long fs, int row, int pitch, int i, const St<R>& q)
+{
+    R* d = base + (size_t)row * pitch + i;
+    d[0] = q.r;
+    d[fs] = q.mx;
+    d[2 * fs] = q.mz;
+    d[3 * fs] = q.E;
+}
+
+// dt candidate of one node of the new state: min over x, z of h/(|u|+c)
+template <class R>
+__device__ __forceinline__ double dt_candidate(const St<R>& q, R z, const Coef<R>& C, int& bad)
+{
+    R ux, uz, T, p;
+    prims(q, z, C, ux, uz, T, p);
+    double c = sqrt((double)C.cs2 * (double)T);
+    double vx = C.dx / (fabs((double)ux) + c);
+    double vz = C.dz / (fabs((double)uz) + c);
+    double v = fmin(vx, vz);
+    if (!(v > 0.0) || !(v < 1e300)) bad = 1;
+    return v;
+}
+
+// L_z(Delta): predictor with backward flux differences, plate fill of X^P,
+// corrector with forward differences of F^P, average, TVD term from the
+// input state, plate values.  Row pipeline at step j (row j just loaded):
+//   F^n_{j-1}, X^P_{j-1}, F^P_{j-1}, average at j-2, TVD flux at (j-2,j-1),
+//   output row j-2.
+template <class R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int strip = gw % io.nstrips;
+    const int ks = (gw / io.nstrips) * io.seg_rows;
+    const int nz = C.nz, nx = C.nx, pitch = C.pitch;
+    const long long fs = C.fstride;
+    const int ke = min(ks + io.seg_rows, nz);
+    const int i = strip * kOutW - 2 + lane;
+    int ic = i % nx;
+    if (ic < 0) ic += nx;
+    const bool own = lane >= 2 && lane < 2 + kOutW && i < nx;
+
+    const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
+    const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
+    const R lam = (R)(Delta / C.dz);
+    const R Dl = (R)Delta;
+    const R lam2 = R(2) * lam;
+
+    if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
+        sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
+        sc.ctl->t += dt;
+        sc.ctl->steps += 1.0;
+    }
+    if (ks >= nz) return;  // warp-uniform; this kernel has no block barrier
+
+    // pipeline registers, primed with the first row so nothing is undefined
+    St<R> Xm2 = load_row(io.in, fs, max(ks - 4, 0), pitch, ic);
+    St<R> Xm1 = Xm2;
+    R ux1, uz1, T1, p1;
+    prims(Xm1, io.zt[max(ks - 4, 0)], C, ux1, uz1, T1, p1);
+    R A2 = R(0), A1 = R(0), dxux1 = R(0), dxuz1 = R(0);
+    St<R> F2 = {R(0), R(0), R(0), R(0)};
+    St<R> XP2 = Xm2;
+    R ppux2 = ux1, ppuz2 = uz1, ppT2 = T1;
+    St<R> FP2 = F2, d1 = F2, Dm = F2;
+    R dd1 = R(0), ss2 = R(0);
+
+    for (int j = ks - 2; j <= ke + 1; ++j) {
+        const int jr = min(max(j, 0), nz - 1);
+        // row j: load, primitives, wave speed |u_z| + c, cross derivatives d/dx
+        const St<R> X0 = load_row(io.in, fs, jr, pitch, ic);
+        R ux0, uz0, T0, p0;
+        prims(X0, io.zt[jr], C, ux0, uz0, T0, p0);
+        const R A0 = fabs(uz0) + rsqrt_(C.cs2 * T0);
+        const R dxux0 = (shdn(ux0) - shup(ux0)) * C.inv_2dx;
+        const R dxuz0 = (shdn(uz0) - shup(uz0)) * C.inv_2dx;
+
+        // predictor flux F^n_{j-1} (forward z-differences inside F)
+        const int m = j - 1;
+        const St<R> F1 = flux_z(Xm1, ux1, uz1, p1, (ux0 - ux1) * C.inv_dz, (uz0 - uz1) * C.inv_dz,
+                                (T0 - T1) * C.inv_dz, dxux1, dxuz1, C);
+        // predictor X^P_{j-1}; plates as half cells with zero wall flux, m = 0, T = T_w
+        St<R> XP1;
+        if (m >= 1 && m <= nz - 2) {
+            XP1.r = Xm1.r - lam * (F1.r - F2.r);
+            XP1.mx = Xm1.mx - lam * (F1.mx - F2.mx);
+            XP1.mz = (Xm1.mz - lam * (F1.mz - F2.mz)) + Dl * (-C.g * Xm1.r);
+            XP1.E = Xm1.E - lam * (F1.E - F2.E);
+        } else if (m <= 0) {
+            XP1.r = Xm1.r - lam2 * F1.r;
+            XP1.mx = R(0); XP1.mz = R(0);
+            XP1.E = XP1.r * C.ebot;
+        } else {
+            XP1.r = Xm1.r + lam2 * F2.r;
+            XP1.mx = R(0); XP1.mz = R(0);
+            XP1.E = XP1.r * C.etop;
+        }
+        R ppux1, ppuz1, ppT1, ppp1;
+        prims(XP1, io.zt[min(max(m, 0), nz - 1)], C, ppux1, ppuz1, ppT1, ppp1);
+        const R dxppux1 = (shdn(ppux1) - shup(ppux1)) * C.inv_2dx;
+        const R dxppuz1 = (shdn(ppuz1) - shup(ppuz1)) * C.inv_2dx;
+        // corrector flux F^P_{j-1} (backward z-differences inside F)
+        const St<R> FP1 = flux_z(XP1, ppux1, ppuz1, ppp1, (ppux1 - ppux2) * C.inv_dz, (ppuz1 - ppuz2) * C.inv_dz,
+                                 (ppT1 - ppT2) * C.inv_dz, dxppux1, dxppuz1, C);
+
+        // corrector X^C_{j-2} and the average (X^P + X^C)/2
+        const int c = j - 2;
+        St<R> Xa;
+        if (c >= 1 && c <= nz - 2) {
+            const R xcr = Xm2.r - lam * (FP1.r - FP2.r);
+            const R xcmx = Xm2.mx - lam * (FP1.mx - FP2.mx);
+            const R xcmz = (Xm2.mz - lam * (FP1.mz - FP2.mz)) + Dl * (-C.g * XP2.r);
+            const R xcE = Xm2.E - lam * (FP1.E - FP2.E);
+            Xa.r = (XP2.r + xcr) * R(0.5);
+            Xa.mx = (XP2.mx + xcmx) * R(0.5);
+            Xa.mz = (XP2.mz + xcmz) * R(0.5);
+            Xa.E = (XP2.E + xcE) * R(0.5);
+        } else if (c <= 0) {
+            Xa.r = (XP2.r + (Xm2.r - lam2 * FP1.r)) * R(0.5);
+            Xa.mx = Xa.mz = Xa.E = R(0);
+        } else {
+            Xa.r = (XP2.r + Xm2.r) * R(0.5);  // F^P on the top plate is m_z = 0
+            Xa.mx = Xa.mz = Xa.E = R(0);
+        }
+
+        // TVD: differences of the input state across interfaces j-1/2
+        const St<R> d0 = {X0.r - Xm1.r, X0.mx - Xm1.mx, X0.mz - Xm1.mz, X0.E - Xm1.E};
+        const R dd0 = dot4(d0, d0);
+        const R ss1 = dot4(d1, d0);
+        St<R> Dn = {R(0), R(0), R(0), R(0)};
+        if (c >= 1 && c <= nz - 3) {  // interface (j-2, j-1); zero next to the plates
+            const R G = tvd_G(ss2, ss1, dd1, lam * fmax(A2, A1), C.tvd_form);
+            Dn = {G * d1.r, G * d1.mx, G * d1.mz, G * d1.E};
+        }
+
+        // output row j-2
+        if (c >= ks && c < ke) {
+            St<R> Xn;
+            if (c >= 1 && c <= nz - 2) {
+                Xn.r = Xa.r + (Dn.r - Dm.r);
+                Xn.mx = Xa.mx + (Dn.mx - Dm.mx);
+                Xn.mz = Xa.mz + (Dn.mz - Dm.mz);
+                Xn.E = Xa.E + (Dn.E - Dm.E);
+            } else {
+                Xn.r = Xa.r;
+                Xn.mx = R(0); Xn.mz = R(0);
+                Xn.E = Xa.r * (c == 0 ? C.ebot : C.etop);
+            }
+            if (own) store_row(io.out, fs, c, pitch, i, Xn);
+        }
+
+        // advance the pipeline
+        Xm2 = Xm1; Xm1 = X0;
+        ux1 = ux0; uz1 = uz0; T1 = T0; p1 = p0;
+        A2 = A1; A1 = A0;
+        dxux1 = dxux0; dxuz1 = dxuz0;
+        F2 = F1; XP2 = XP1;
+        ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1;
+        FP2 = FP1;
+        d1 = d0; dd1 = dd0; ss2 = ss1; Dm = Dn;
+    }
+}
+
+// L_x(Delta) on the interior rows (plate rows pass through).  Row pipeline at
+// step j: F^n_{j-1} and X^P_{j-1} (needs rows j, j-2 for d/dz), then F^P_{j-2}
+// (needs X^P rows j-1, j-3), corrector, average, TVD along x, output row j-2.
+template <class R>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int strip = gw % io.nstrips;
+    const int ks = (gw / io.nstrips) * io.seg_rows;
+    const int nz = C.nz, nx = C.nx, pitch = C.pitch;
+    const long long fs = C.fstride;
+    const int ke = min(ks + io.seg_rows, nz);
+    const int i = strip * kOutW - 2 + lane;
+    int ic = i % nx;
+    if (ic < 0) ic += nx;
+    const bool own = lane >= 2 && lane < 2 + kOutW && i < nx;
+
+    const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
+    const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
+    const R lam = (R)(Delta / C.dx);
+
+    if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
+        sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
+        sc.ctl->t += dt;
+        sc.ctl->steps += 1.0;
+    }
+
+    double vmin = 1e308;
+    int bad = 0;
+    if (ks < nz) {
+        St<R> Xm2 = load_row(io.in, fs, max(ks - 4, 0), pitch, ic);
+        St<R> Xm1 = Xm2;
+        R ux1, uz1, T1, p1;
+        prims(Xm1, io.zt[max(ks - 4, 0)], C, ux1, uz1, T1, p1);
+        R ux2 = ux1, uz2 = uz1, T2 = T1, p2 = p1;
+        St<R> XP2 = Xm2;
+        R ppux2 = ux1, ppuz2 = uz1, ppT2 = T1, ppp2 = p1;
+        R ppux3 = ux1, ppuz3 = uz1;
+
+        for (int j = ks - 2; j <= ke + 1; ++j) {
+            const int jr = min(max(j, 0), nz - 1);
+            const St<R> X0 = load_row(io.in, fs, jr, pitch, ic);
+            R ux0, uz0, T0, p0;
+            prims(X0, io.zt[jr], C, ux0, uz0, T0, p0);
+
+            // row m = j-1: F^n with forward x-differences, central z-differences
+            const int m = j - 1;
+            const St<R> F1 = flux_x(Xm1, ux1, uz1, p1, (shdn(ux1) - ux1) * C.inv_dx, (shdn(uz1) - uz1) * C.inv_dx,
+                                    (shdn(T1) - T1) * C.inv_dx, (ux0 - ux2) * C.inv_2dz, (uz0 - uz2) * C.inv_2dz, C);
+            const St<R> Fl = shup(F1);
+            St<R> XP1 = Xm1;
+            if (m >= 1 && m <= nz - 2) {
+                XP1.r = Xm1.r - lam * (F1.r - Fl.r);
+                XP1.mx = Xm1.mx - lam * (F1.mx - Fl.mx);
+                XP1.mz = Xm1.mz - lam * (F1.mz - Fl.mz);
+                XP1.E = Xm1.E - lam * (F1.E - Fl.E);
+            }
+            R ppux1, ppuz1, ppT1, ppp1;
+            prims(XP1, io.zt[min(max(m, 0), nz - 1)], C, ppux1, ppuz1, ppT1, ppp1);
+
+            // row c = j-2: F^P with backward x-differences, corrector, average
+            const int c = j - 2;
+            const St<R> FP = flux_x(XP2, ppux2, ppuz2, ppp2, (ppux2 - shup(ppux2)) * C.inv_dx,
+                                    (ppuz2 - shup(ppuz2)) * C.inv_dx, (ppT2 - shup(ppT2)) * C.inv_dx,
+                                    (ppux1 - ppux3) * C.inv_2dz, (ppuz1 - ppuz3) * C.inv_2dz, C);
+            const St<R> FPr = shdn(FP);
+            St<R> Xa;
+            Xa.r = (XP2.r + (Xm2.r - lam * (FPr.r - FP.r))) * R(0.5);
+            Xa.mx = (XP2.mx + (Xm2.mx - lam * (FPr.mx - FP.mx))) * R(0.5);
+            Xa.mz = (XP2.mz + (Xm2.mz - lam * (FPr.mz - FP.mz))) * R(0.5);
+            Xa.E = (XP2.E + (Xm2.E - lam * (FPr.E - FP.E))) * R(0.5);
+
+            // TVD along x from the input state of row c
+            const St<R> Xr = shdn(Xm2);
+            const St<R> d0 = {Xr.r - Xm2.r, Xr.mx - Xm2.mx, Xr.mz - Xm2.mz, Xr.E - Xm2.E};
+            const R dd = dot4(d0, d0);
+            const St<R> dl = shup(d0);
+            const R sp = dot4(dl, d0);
+            const R sm = shdn(sp);
+            const R A = fabs(ux2) + rsqrt_(C.cs2 * T2);
+            const R G = tvd_G(sp, sm, dd, lam * fmax(A, shdn(A)), C.tvd_form);
+            const St<R> Dn = {G * d0.r, G * d0.mx, G * d0.mz, G * d0.E};
+            const St<R> Dlf = shup(Dn);
+
+            if (c >= ks && c < ke) {
+                St<R> Xn = Xm2;  // plate rows pass through
+                if (c >= 1 && c <= nz - 2) {
+                    Xn.r = Xa.r + (Dn.r - Dlf.r);
+                    Xn.mx = Xa.mx + (Dn.mx - Dlf.mx);
+                    Xn.mz = Xa.mz + (Dn.mz - Dlf.mz);
+                    Xn.E = Xa.E + (Dn.E - Dlf.E);
+                }
+                if (own) {
+                    store_row(io.out, fs, c, pitch, i, Xn);
+                    if (sc.last) vmin = fmin(vmin, dt_candidate(Xn, io.zt[c], C, bad));
+                }
+            }
+
+            Xm2 = Xm1; Xm1 = X0;
+            ux2 = ux1; uz2 = uz1; T2 = T1; p2 = p1;
+            ux1 = ux0; uz1 = uz0; T1 = T0; p1 = p0;
+            ppux3 = ppux2; ppuz3 = ppuz2;
+            XP2 = XP1;
+            ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
+        }
+    }
+    if (sc.last) block_dt_reduce(vmin, bad, sc.ctl, sc.slot_in ^ 1);
+}
+
+}  // namespace cm

@@ -1,0 +1,188 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (stated per output):
+  FP64 state: relative L2 per field <= 1e-12 after 1000 steps of the 256 x 64,
+    Ra = 1e6 workload; single sweeps <= 1e-13.
+  FP32 state: relative L2 per field <= 1e-5 after 100 steps for rho and E;
+    the momentum fields are measured against the scale rho c (the sound
+    speed times density), since they start at zero.
+  Diagnostics: relative 1e-12 (FP64) on the same state.
+Inputs are seeded and synthetic; the oracle never sees a CUDA result.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from physics import closures, state_from_prims
+
+pytestmark = pytest.mark.gpu
+
+
+def solver_for(cfg: O.Config, precision="fp64", **extra):
+    import paper_2411_10372_gb300 as cm
+    t_top = (1.0 - cfg.eps - cfg.D) if cfg.t_top is None else cfg.t_top
+    return cm.Solver(cfg.nx, cfg.nz, cfg.Ra, cfg.Pr, cfg.gamma, ny=cfg.ny, ndim=cfg.ndim, aspect=cfg.aspect,
+                     precision=precision, eps=cfg.eps, D=cfg.D, cfl=cfg.cfl, dt_fixed=cfg.dt_fixed,
+                     gravity=cfg.gravity, t_bot=cfg.t_bot, t_top=t_top, pert_amp=cfg.pert_amp,
+                     stokes=cfg.stokes, seed=cfg.seed, tvd_form=cfg.tvd_form, **extra)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def stirred_state(cfg, seed, u_amp=0.3, t_amp=0.05):
+    """Seeded synthetic state with every term of the scheme active: the
+    conduction profile with a random temperature field and random velocities
+    (zero on the plates), plates at their wall temperatures."""
+    rng = np.random.default_rng(seed)
+    T_c, p_c, _ = O.profile(cfg)
+    z = np.linspace(0, 1, cfg.nz)
+    Z = np.repeat(z[:, None], cfg.nx, 1)
+    T = T_c[:, None] * (1 + t_amp * rng.uniform(-1, 1, (cfg.nz, cfg.nx)))
+    ux = u_amp * rng.uniform(-1, 1, (cfg.nz, cfg.nx))
+    uz = u_amp * rng.uniform(-1, 1, (cfg.nz, cfg.nx))
+    for f in (ux, uz):
+        f[0] = f[-1] = 0.0
+    t_top = (1.0 - cfg.eps - cfg.D) if cfg.t_top is None else cfg.t_top
+    T[0], T[-1] = cfg.t_bot, t_top
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    rho = p_c[:, None] / (cl["a"] * T) * (1 + 0.02 * rng.uniform(-1, 1, (cfg.nz, cfg.nx)))
+    return state_from_prims(cfg, rho, ux, uz, T, Z)
+
+
+SHAPES = [(4, 5), (8, 5), (29, 7), (57, 9), (64, 33), (100, 17), (256, 64)]
+
+
+@pytest.mark.parametrize("nx,nz", SHAPES)
+@pytest.mark.parametrize("tvd", [O.TVD_SPLIT, O.TVD_SUM, O.TVD_OFF])
+def test_single_sweeps_fp64(nx, nz, tvd):
+    """One L_z and one L_x on a stirred state, every node, FP64."""
+    cfg = O.Config(nx=nx, nz=nz, Ra=1e5, tvd_form=tvd, dt_fixed=1e-3)
+    X = stirred_state(cfg, seed=nx * 1000 + nz)
+    s = solver_for(cfg)
+    for direction in (2, 0):
+        Delta = 0.2 * min(cfg.aspect / nx, 1.0 / (nz - 1)) / 4.0
+        s.set_state(X)
+        s.sweep(direction, Delta)
+        got = s.state()
+        want = O.sweep(cfg, X, direction, Delta)
+        for f in range(4):
+            assert rel_l2(got[f], want[f]) <= 1e-13, (direction, f)
+    s.close()
+
+
+def test_initial_state_and_dt_match_oracle():
+    for precision, tol in (("fp64", 0.0), ("fp32", 6e-8)):
+        cfg = O.Config(nx=100, nz=33, Ra=1e6, pert_amp=1e-3, seed=99)
+        s = solver_for(cfg, precision)
+        got, want = s.state(), O.init(cfg)
+        for f in range(4):
+            assert np.max(np.abs(got[f] - want[f])) <= tol * np.max(np.abs(want[f])) + 1e-300
+        if precision == "fp64":
+            assert abs(s.dt() - O.dt(cfg, want)) <= 1e-15 * O.dt(cfg, want)
+        s.close()
+
+
+def test_config1_fp64_1000_steps():
+    """The 256 x 64, Ra = 1e6, FP64 workload: 1000 steps of both paths from
+    the same seeded initial state."""
+    cfg = O.Config()
+    s = solver_for(cfg)
+    s.step(1000)
+    t_gpu, steps = s.time()
+    got = s.state()
+    want, t_cpu, _ = O.step(cfg, O.init(cfg), 1000)
+    assert steps == 1000
+    assert abs(t_gpu - t_cpu) <= 1e-12 * t_cpu
+    for f in range(4):
+        assert rel_l2(got[f], want[f]) <= 1e-12, f
+    d_gpu = s.sample()
+    d_cpu = O.diag(cfg, want)
+    for k_gpu, k_cpu in (("Nu", "Nu"), ("Nu_bar", "Nu_bar"), ("Re", "Re"), ("KE", "KE"), ("mass", "mass")):
+        assert abs(d_gpu[k_gpu] - d_cpu[k_cpu]) <= 1e-10 * max(abs(d_cpu[k_cpu]), 1e-6), k_gpu
+    s.close()
+
+
+def test_fp32_100_steps():
+    cfg = O.Config()
+    s = solver_for(cfg, "fp32")
+    s.step(100)
+    got = s.state()
+    want, _, _ = O.step(cfg, O.init(cfg), 100)
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    assert rel_l2(got[0], want[0]) <= 1e-5
+    assert rel_l2(got[3], want[3]) <= 1e-5
+    # momentum: against rho c
+    scale = np.linalg.norm(want[0] * math.sqrt(cfg.gamma * cl["a"]))
+    for f in (1, 2):
+        assert np.linalg.norm(got[f] - want[f]) / scale <= 1e-5, f
+    s.close()
+
+
+def test_diagnostics_match_oracle_on_same_state():
+    cfg = O.Config(nx=128, nz=33, Ra=1e7)
+    X = stirred_state(cfg, seed=5, u_amp=0.1)
+    s = solver_for(cfg)
+    s.set_state(X)
+    d = s.sample()
+    want = O.diag(cfg, X)
+    for key in ("Nu", "Nu_conv", "Nu_K", "Nu_bot", "Nu_top", "Nu_bar", "Re", "KE", "mass", "energy"):
+        assert abs(d[key] - want[key]) <= 1e-12 * max(abs(want[key]), 1.0), key
+    assert abs(d["mach_max"] - want["Mach_max"]) <= 1e-12
+    assert abs(s.dt() - O.dt(cfg, X)) <= 1e-15 * O.dt(cfg, X)
+    s.close()
+
+
+def test_mass_conservation_and_diag_ring():
+    cfg = O.Config(nx=200, nz=41, Ra=1e7)
+    s = solver_for(cfg, diag_every=10)
+    s.step(200)
+    ds = s.diagnostics()
+    assert [d["step"] for d in ds] == list(range(10, 201, 10))
+    m = np.array([d["mass"] for d in ds])
+    assert np.max(np.abs(m - m[0])) <= 1e-13 * m[0]
+    assert all(d["status"] == 0 for d in ds)
+    s.close()
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    cfg = O.Config(nx=64, nz=17, Ra=1e6)
+    s = solver_for(cfg)
+    s.step(7)
+    path = str(tmp_path / "c.ckpt")
+    import paper_2411_10372_gb300 as cm
+    cm.cm_save(path)
+    s.step(5)
+    a = s.state()
+    cm.cm_load(path)
+    assert s.time()[1] == 7
+    s.step(5)
+    assert np.array_equal(s.state(), a)
+    with open(path, "r+b") as f:
+        f.seek(0)
+        f.write(b"XXXX")
+    with pytest.raises(cm.CMError) as e:
+        cm.cm_load(path)
+    assert e.value.code == cm.CM_EBADCKPT
+    s.close()
+
+
+def test_full_size_one_step_fp64_and_fp32():
+    """The 4096 x 1024, Ra = 1e10 workload in the bench's launch configuration:
+    one full step on every node against the oracle."""
+    cfg = O.Config(nx=4096, nz=1024, Ra=1e10)
+    X0 = O.init(cfg)
+    want, _, _ = O.step(cfg, X0, 1)
+    for precision, tol in (("fp64", 1e-13), ("fp32", 2e-6)):
+        s = solver_for(cfg, precision)
+        s.step(1)
+        got = s.state()
+        for f in (0, 3):
+            assert rel_l2(got[f], want[f]) <= tol, (precision, f)
+        scale = np.linalg.norm(want[0]) * 3.65
+        for f in (1, 2):
+            assert np.linalg.norm(got[f] - want[f]) / scale <= tol, (precision, f)
+        s.close()
