@@ -118,7 +118,6 @@ def run_gpu(args):
     import paper_2411_10372_gb300 as cm
 
     stream = torch.cuda.Stream()
-    cells = NX * NZ
     hbm, peak_kind = peaks()
 
     def barrier():
@@ -134,8 +133,11 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    NXr, NZr = args.nx, args.nz
+    cells = NXr * NZr
+
     def measure(precision: str, K: int, W: int, clocks: bool):
-        s = cm.Solver(NX, NZ, RA, PR, GAMMA, precision=precision, stream=stream, seed=12345 + rank)
+        s = cm.Solver(NXr, NZr, RA, PR, GAMMA, precision=precision, stream=stream, seed=12345 + rank)
         s.step(W)
         s.sync()
         barrier()
@@ -158,11 +160,17 @@ def run_gpu(args):
         return s, out
 
     # ---- FP32 state: the timed line ----
-    s, r32 = measure("fp32", args.steps, args.warmup, clocks=True)
+    s, r32 = measure("fp32", args.steps, args.warmup, clocks=not args.only_fp32)
+    if args.only_fp32:  # profiling runs: the timed FP32 steps and nothing else
+        s.close()
+        if rank == 0:
+            print(json.dumps({"nx": NXr, "nz": NZr, "steps": args.steps, "sweep_ms": r32["sweep_ms"],
+                              "ms_per_step": r32["total_ms"] / args.steps}), flush=True)
+        return
     # end to end through the public C ABI with host buffers: every step
     # uploads the state from pinned host memory (dense float64), steps once
     # and reads one diagnostics sample back
-    host = torch.empty((4, NZ, NX), dtype=torch.float64, pin_memory=True)
+    host = torch.empty((4, NZr, NXr), dtype=torch.float64, pin_memory=True)
     hostnp = host.numpy()
     cm.cm_get_state(hostnp)
     n_e2e = max(3, min(args.steps, 30))
@@ -197,7 +205,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": r32["total_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD + "_fp32", "nx": NX, "nz": NZ, "Ra": RA, "Pr": PR, "gamma": GAMMA,
+        "config": {"workload": WORKLOAD + "_fp32", "nx": NXr, "nz": NZr, "Ra": RA, "Pr": PR, "gamma": GAMMA,
                    "eps": 0.1, "D": 0.5, "cfl": 0.5, "state": "fp32, fp64 dt and reductions",
                    "l2": "flushed before every timed step (256 MiB memset)", "parallelism": f"replicas x{world}"},
         "roofline": roofline(r32),
@@ -271,6 +279,9 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nx", type=int, default=NX, help="grid override (profiling captures only)")
+    ap.add_argument("--nz", type=int, default=NZ, help="grid override (profiling captures only)")
+    ap.add_argument("--only-fp32", action="store_true", help="time the FP32 steps only (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -66,15 +66,15 @@ __global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int s
         const int j = (int)(jk % C.ny);
         const int k = (int)(jk / C.ny);
         const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
-        const R rho = p[0];
-        const R ri = R(1) / rho;
-        R ux = p[fs] * ri, uy = R(0), uz, E;
-        if (C.ndim == 3) { uy = p[2 * fs] * ri; uz = p[3 * fs] * ri; E = p[4 * fs]; }
-        else { uz = p[2 * fs] * ri; E = p[3 * fs]; }
-        const R T = C.b * (E * ri - R(0.5) * ((ux * ux + uy * uy) + uz * uz) - C.g * zt[k]);
-        const double c = sqrt((double)C.cs2 * (double)T);
-        double v = fmin(C.dx / (fabs((double)ux) + c), C.dz / (fabs((double)uz) + c));
-        if (C.ndim == 3) v = fmin(v, C.dy / (fabs((double)uy) + c));
+        // same operation order as the sweeps' FP64 path (divisions by rho)
+        const double rho = (double)p[0];
+        double ux = (double)p[fs] / rho, uy = 0.0, uz, E;
+        if (C.ndim == 3) { uy = (double)p[2 * fs] / rho; uz = (double)p[3 * fs] / rho; E = (double)p[4 * fs]; }
+        else { uz = (double)p[2 * fs] / rho; E = (double)p[3 * fs]; }
+        const double T = (double)C.b * (E / rho - 0.5 * ((ux * ux + uy * uy) + uz * uz) - (double)C.g * (double)zt[k]);
+        const double c = sqrt((double)C.cs2 * T);
+        double v = fmin(C.dx / (fabs(ux) + c), C.dz / (fabs(uz) + c));
+        if (C.ndim == 3) v = fmin(v, C.dy / (fabs(uy) + c));
         if (!(v > 0.0) || !(v < 1e300)) bad = 1;
         vmin = fmin(vmin, v);
     }

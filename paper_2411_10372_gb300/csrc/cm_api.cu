@@ -90,6 +90,12 @@ void fill_coef(Coef<R>& C, const Ctx& c)
     C.inv_2dx = (R)(1.0 / (2.0 * dx));
     C.inv_2dy = (R)(1.0 / (2.0 * dy));
     C.inv_2dz = (R)(1.0 / (2.0 * dz));
+    C.hx = (R)dx;
+    C.hy = (R)dy;
+    C.hz = (R)dz;
+    C.h2x = (R)(2.0 * dx);
+    C.h2y = (R)(2.0 * dy);
+    C.h2z = (R)(2.0 * dz);
     C.ebot = (R)(P.t_bot / c.b + c.g * 0.0);
     C.etop = (R)(P.t_top / c.b + c.g * 1.0);
     C.dx = dx;

@@ -7,9 +7,18 @@
 //   heat flux -K grad T,  K = 1/(eps D sqrt(Ra Pr))
 // Scheme (Sec. 3.1): flux F_alpha = [m_alpha; m_i u_alpha - tau_{i alpha} + p delta_{i alpha};
 //   u_alpha (E + p) - K dT/dx_alpha - u_b tau_{b alpha}], source -g rho in the z momentum.
+//
+// Rounding: the FP64 instantiation evaluates every formula as a fixed
+// sequence of IEEE operations -- true divisions by the grid spacings and by
+// rho, no FMA contraction (its translation unit is built with --fmad=false),
+// sums in the order the formulas are written -- so the FP64 path is
+// reproducible bit for bit (the flow amplifies a one-ulp change at one node
+// to ~1e-6 in 1000 steps at Ra = 1e6, so nothing looser is testable).  The
+// FP32 instantiation multiplies by precomputed reciprocals instead.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <type_traits>
 
 namespace cm {
 
@@ -20,6 +29,7 @@ struct Coef {
     R a, b, g, mu, kth, cs2, stokes;   // closures; cs2 = gamma a (c^2 = cs2 T)
     R inv_dx, inv_dy, inv_dz;          // 1/h
     R inv_2dx, inv_2dy, inv_2dz;       // 1/(2h)
+    R hx, hy, hz, h2x, h2y, h2z;       // h and 2h (FP64 path divides by these)
     R ebot, etop;                      // E/rho on the plates: T_w/b + g z_w
     double dx, dy, dz, cfl, dt_fixed;
     int nx, ny, nz, pitch;             // nodes; row pitch in elements
@@ -95,15 +105,39 @@ __device__ __forceinline__ double step_dt(const DevCtl* c, int slot, double cfl,
     return cfl * __longlong_as_double((long long)c->dt_slot[slot]);
 }
 
+template <class R> constexpr bool kExact = std::is_same<R, double>::value;
+
+// (a - b) / span: a one-sided (span = h) or central (span = 2h) difference
+template <class R>
+__device__ __forceinline__ R diff(R a, R b, R span, R inv_span)
+{
+    if constexpr (kExact<R>) return (a - b) / span;
+    else return (a - b) * inv_span;
+}
+
 // primitive variables from the conserved state (closures of Sec. 2)
 template <class R>
 __device__ __forceinline__ void prims(const St<R>& q, R z, const Coef<R>& C, R& ux, R& uz, R& T, R& p)
 {
-    R ri = R(1) / q.r;
-    ux = q.mx * ri;
-    uz = q.mz * ri;
-    T = C.b * (q.E * ri - R(0.5) * (ux * ux + uz * uz) - C.g * z);
+    if constexpr (kExact<R>) {
+        ux = q.mx / q.r;
+        uz = q.mz / q.r;
+        T = C.b * (q.E / q.r - R(0.5) * (ux * ux + uz * uz) - C.g * z);
+    } else {
+        R ri = R(1) / q.r;
+        ux = q.mx * ri;
+        uz = q.mz * ri;
+        T = C.b * (q.E * ri - R(0.5) * (ux * ux + uz * uz) - C.g * z);
+    }
     p = C.a * q.r * T;
+}
+
+// local Courant number of an interface: (dt/2) max(|u|+c over its nodes) / h
+template <class R>
+__device__ __forceinline__ R courant(double Delta, R lam, R A0, R A1, R h)
+{
+    if constexpr (kExact<R>) return (R)Delta * fmax(A0, A1) / h;
+    else return lam * fmax(A0, A1);
 }
 
 // F_z at one node; dz_* one-sided along z, dx_* central across
@@ -149,14 +183,24 @@ __device__ __forceinline__ R phi_of(R s, R dd)
 
 // coefficient G of the TVD flux G * dX_{k+1/2}:
 //   Davis form G(r+_k) + G(r-_{k+1}),  printed form G(r+_k + r-_{k+1}),
-//   G(r) = C (1 - phi(r)) / 2,  C = Co (1 - Co) for Co <= 1/2, else 1/4
+//   G(r) = C (1 - phi(r)) / 2,  C = Co (1 - Co) for Co <= 1/2, else 1/4,
+//   r+_k = sp/dd, r-_{k+1} = sm/dd (dd = |dX_{k+1/2}|^2; dd = 0 means dX = 0,
+//   where the flux vanishes whatever G is)
 template <class R>
 __device__ __forceinline__ R tvd_G(R sp, R sm, R dd, R Co, int form)
 {
     R C = (Co <= R(0.5)) ? Co * (R(1) - Co) : R(0.25);
-    if (form == 0) return R(0.5) * C * (R(1) - phi_of(sp, dd)) + R(0.5) * C * (R(1) - phi_of(sm, dd));
-    if (form == 1) return R(0.5) * C * (R(1) - phi_of(sp + sm, dd));
-    return R(0);
+    if (form == 2) return R(0);
+    if constexpr (kExact<R>) {
+        if (dd == R(0)) return R(0);
+        const R rp = sp / dd, rm = sm / dd;
+        auto phi = [](R r) { return fmax(R(0), fmin(R(2) * r, R(1))); };
+        if (form == 0) return R(0.5) * C * (R(1) - phi(rp)) + R(0.5) * C * (R(1) - phi(rm));
+        return R(0.5) * C * (R(1) - phi(rp + rm));
+    } else {
+        if (form == 0) return R(0.5) * C * (R(1) - phi_of(sp, dd)) + R(0.5) * C * (R(1) - phi_of(sm, dd));
+        return R(0.5) * C * (R(1) - phi_of(sp + sm, dd));
+    }
 }
 
 template <class R>

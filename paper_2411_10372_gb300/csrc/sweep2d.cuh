@@ -42,19 +42,33 @@ __device__ __forceinline__ void store_row(R* __restrict__ base, long long fs, in
     d[3 * fs] = q.E;
 }
 
-// dt candidate of one node of the new state: min over x, z of h/(|u|+c)
-template <class R>
-__device__ __forceinline__ double dt_candidate(const St<R>& q, R z, const Coef<R>& C, int& bad)
+// dt candidate of one node of the new state, FP64 path: min over x, z of
+// h/(|u|+c), evaluated as the CFL rule is written
+__device__ __forceinline__ double dt_candidate(const St<double>& q, double z, const Coef<double>& C, int& bad)
 {
-    R ux, uz, T, p;
+    double ux, uz, T, p;
     prims(q, z, C, ux, uz, T, p);
-    double c = sqrt((double)C.cs2 * (double)T);
-    double vx = C.dx / (fabs((double)ux) + c);
-    double vz = C.dz / (fabs((double)uz) + c);
-    double v = fmin(vx, vz);
+    const double c = sqrt(C.cs2 * T);
+    const double v = fmin(C.dx / (fabs(ux) + c), C.dz / (fabs(uz) + c));
     if (!(v > 0.0) || !(v < 1e300)) bad = 1;
     return v;
 }
+
+// FP32 path: the largest rate (|u|+c)/h of a node; the block turns its max
+// into min h/(|u|+c) with one FP64 reciprocal
+__device__ __forceinline__ float dt_rate(const St<float>& q, float z, const Coef<float>& C, int& bad)
+{
+    float ux, uz, T, p;
+    prims(q, z, C, ux, uz, T, p);
+    const float c = sqrtf(C.cs2 * T);
+    const float r = fmaxf((fabsf(ux) + c) * C.inv_dx, (fabsf(uz) + c) * C.inv_dz);
+    if (!(r > 0.f) || !(r < 1e30f)) bad = 1;
+    return r;
+}
+
+__device__ __forceinline__ int clamp_row(int j, int nz) { return min(max(j, 0), nz - 1); }
+
+constexpr int kPrefetch = 3;  // rows loaded ahead of the one being consumed
 
 // L_z(Delta): predictor with backward flux differences, plate fill of X^P,
 // corrector with forward differences of F^P, average, TVD term from the
@@ -102,20 +116,27 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
     St<R> FP2 = F2, d1 = F2, Dm = F2;
     R dd1 = R(0), ss2 = R(0);
 
+    St<R> pf[kPrefetch];
+#pragma unroll
+    for (int q = 0; q < kPrefetch; ++q) pf[q] = load_row(io.in, fs, clamp_row(ks - 2 + q, nz), pitch, ic);
+
     for (int j = ks - 2; j <= ke + 1; ++j) {
-        const int jr = min(max(j, 0), nz - 1);
-        // row j: load, primitives, wave speed |u_z| + c, cross derivatives d/dx
-        const St<R> X0 = load_row(io.in, fs, jr, pitch, ic);
+        const int jr = clamp_row(j, nz);
+        // row j: primitives, wave speed |u_z| + c, cross derivatives d/dx
+        const St<R> X0 = pf[0];
+#pragma unroll
+        for (int q = 0; q < kPrefetch - 1; ++q) pf[q] = pf[q + 1];
+        pf[kPrefetch - 1] = load_row(io.in, fs, clamp_row(j + kPrefetch, nz), pitch, ic);
         R ux0, uz0, T0, p0;
         prims(X0, io.zt[jr], C, ux0, uz0, T0, p0);
         const R A0 = fabs(uz0) + rsqrt_(C.cs2 * T0);
-        const R dxux0 = (shdn(ux0) - shup(ux0)) * C.inv_2dx;
-        const R dxuz0 = (shdn(uz0) - shup(uz0)) * C.inv_2dx;
+        const R dxux0 = diff(shdn(ux0), shup(ux0), C.h2x, C.inv_2dx);
+        const R dxuz0 = diff(shdn(uz0), shup(uz0), C.h2x, C.inv_2dx);
 
         // predictor flux F^n_{j-1} (forward z-differences inside F)
         const int m = j - 1;
-        const St<R> F1 = flux_z(Xm1, ux1, uz1, p1, (ux0 - ux1) * C.inv_dz, (uz0 - uz1) * C.inv_dz,
-                                (T0 - T1) * C.inv_dz, dxux1, dxuz1, C);
+        const St<R> F1 = flux_z(Xm1, ux1, uz1, p1, diff(ux0, ux1, C.hz, C.inv_dz), diff(uz0, uz1, C.hz, C.inv_dz),
+                                diff(T0, T1, C.hz, C.inv_dz), dxux1, dxuz1, C);
         // predictor X^P_{j-1}; plates as half cells with zero wall flux, m = 0, T = T_w
         St<R> XP1;
         if (m >= 1 && m <= nz - 2) {
@@ -134,11 +155,12 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
         }
         R ppux1, ppuz1, ppT1, ppp1;
         prims(XP1, io.zt[min(max(m, 0), nz - 1)], C, ppux1, ppuz1, ppT1, ppp1);
-        const R dxppux1 = (shdn(ppux1) - shup(ppux1)) * C.inv_2dx;
-        const R dxppuz1 = (shdn(ppuz1) - shup(ppuz1)) * C.inv_2dx;
+        const R dxppux1 = diff(shdn(ppux1), shup(ppux1), C.h2x, C.inv_2dx);
+        const R dxppuz1 = diff(shdn(ppuz1), shup(ppuz1), C.h2x, C.inv_2dx);
         // corrector flux F^P_{j-1} (backward z-differences inside F)
-        const St<R> FP1 = flux_z(XP1, ppux1, ppuz1, ppp1, (ppux1 - ppux2) * C.inv_dz, (ppuz1 - ppuz2) * C.inv_dz,
-                                 (ppT1 - ppT2) * C.inv_dz, dxppux1, dxppuz1, C);
+        const St<R> FP1 = flux_z(XP1, ppux1, ppuz1, ppp1, diff(ppux1, ppux2, C.hz, C.inv_dz),
+                                 diff(ppuz1, ppuz2, C.hz, C.inv_dz), diff(ppT1, ppT2, C.hz, C.inv_dz), dxppux1,
+                                 dxppuz1, C);
 
         // corrector X^C_{j-2} and the average (X^P + X^C)/2
         const int c = j - 2;
@@ -166,7 +188,7 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
         const R ss1 = dot4(d1, d0);
         St<R> Dn = {R(0), R(0), R(0), R(0)};
         if (c >= 1 && c <= nz - 3) {  // interface (j-2, j-1); zero next to the plates
-            const R G = tvd_G(ss2, ss1, dd1, lam * fmax(A2, A1), C.tvd_form);
+            const R G = tvd_G(ss2, ss1, dd1, courant(Delta, lam, A2, A1, C.hz), C.tvd_form);
             Dn = {G * d1.r, G * d1.mx, G * d1.mz, G * d1.E};
         }
 
@@ -227,7 +249,8 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
         sc.ctl->steps += 1.0;
     }
 
-    double vmin = 1e308;
+    double vmin = 1e308;  // FP64 path: min h/(|u|+c) over the nodes of this thread
+    R rmax = R(0);        // FP32 path: max (|u|+c)/h
     int bad = 0;
     if (ks < nz) {
         St<R> Xm2 = load_row(io.in, fs, max(ks - 4, 0), pitch, ic);
@@ -239,16 +262,24 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
         R ppux2 = ux1, ppuz2 = uz1, ppT2 = T1, ppp2 = p1;
         R ppux3 = ux1, ppuz3 = uz1;
 
+        St<R> pf[kPrefetch];
+#pragma unroll
+        for (int q = 0; q < kPrefetch; ++q) pf[q] = load_row(io.in, fs, clamp_row(ks - 2 + q, nz), pitch, ic);
+
         for (int j = ks - 2; j <= ke + 1; ++j) {
-            const int jr = min(max(j, 0), nz - 1);
-            const St<R> X0 = load_row(io.in, fs, jr, pitch, ic);
+            const int jr = clamp_row(j, nz);
+            const St<R> X0 = pf[0];
+#pragma unroll
+            for (int q = 0; q < kPrefetch - 1; ++q) pf[q] = pf[q + 1];
+            pf[kPrefetch - 1] = load_row(io.in, fs, clamp_row(j + kPrefetch, nz), pitch, ic);
             R ux0, uz0, T0, p0;
             prims(X0, io.zt[jr], C, ux0, uz0, T0, p0);
 
             // row m = j-1: F^n with forward x-differences, central z-differences
             const int m = j - 1;
-            const St<R> F1 = flux_x(Xm1, ux1, uz1, p1, (shdn(ux1) - ux1) * C.inv_dx, (shdn(uz1) - uz1) * C.inv_dx,
-                                    (shdn(T1) - T1) * C.inv_dx, (ux0 - ux2) * C.inv_2dz, (uz0 - uz2) * C.inv_2dz, C);
+            const St<R> F1 = flux_x(Xm1, ux1, uz1, p1, diff(shdn(ux1), ux1, C.hx, C.inv_dx),
+                                    diff(shdn(uz1), uz1, C.hx, C.inv_dx), diff(shdn(T1), T1, C.hx, C.inv_dx),
+                                    diff(ux0, ux2, C.h2z, C.inv_2dz), diff(uz0, uz2, C.h2z, C.inv_2dz), C);
             const St<R> Fl = shup(F1);
             St<R> XP1 = Xm1;
             if (m >= 1 && m <= nz - 2) {
@@ -262,9 +293,9 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 
             // row c = j-2: F^P with backward x-differences, corrector, average
             const int c = j - 2;
-            const St<R> FP = flux_x(XP2, ppux2, ppuz2, ppp2, (ppux2 - shup(ppux2)) * C.inv_dx,
-                                    (ppuz2 - shup(ppuz2)) * C.inv_dx, (ppT2 - shup(ppT2)) * C.inv_dx,
-                                    (ppux1 - ppux3) * C.inv_2dz, (ppuz1 - ppuz3) * C.inv_2dz, C);
+            const St<R> FP = flux_x(XP2, ppux2, ppuz2, ppp2, diff(ppux2, shup(ppux2), C.hx, C.inv_dx),
+                                    diff(ppuz2, shup(ppuz2), C.hx, C.inv_dx), diff(ppT2, shup(ppT2), C.hx, C.inv_dx),
+                                    diff(ppux1, ppux3, C.h2z, C.inv_2dz), diff(ppuz1, ppuz3, C.h2z, C.inv_2dz), C);
             const St<R> FPr = shdn(FP);
             St<R> Xa;
             Xa.r = (XP2.r + (Xm2.r - lam * (FPr.r - FP.r))) * R(0.5);
@@ -280,7 +311,7 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
             const R sp = dot4(dl, d0);
             const R sm = shdn(sp);
             const R A = fabs(ux2) + rsqrt_(C.cs2 * T2);
-            const R G = tvd_G(sp, sm, dd, lam * fmax(A, shdn(A)), C.tvd_form);
+            const R G = tvd_G(sp, sm, dd, courant(Delta, lam, A, shdn(A), C.hx), C.tvd_form);
             const St<R> Dn = {G * d0.r, G * d0.mx, G * d0.mz, G * d0.E};
             const St<R> Dlf = shup(Dn);
 
@@ -294,7 +325,10 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
                 }
                 if (own) {
                     store_row(io.out, fs, c, pitch, i, Xn);
-                    if (sc.last) vmin = fmin(vmin, dt_candidate(Xn, io.zt[c], C, bad));
+                    if (sc.last) {
+                        if constexpr (kExact<R>) vmin = fmin(vmin, dt_candidate(Xn, io.zt[c], C, bad));
+                        else rmax = fmax(rmax, dt_rate(Xn, io.zt[c], C, bad));
+                    }
                 }
             }
 
@@ -306,7 +340,10 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
             ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
         }
     }
-    if (sc.last) block_dt_reduce(vmin, bad, sc.ctl, sc.slot_in ^ 1);
+    if (sc.last) {
+        if constexpr (!kExact<R>) vmin = rmax > R(0) ? 1.0 / (double)rmax : 1e308;
+        block_dt_reduce(vmin, bad, sc.ctl, sc.slot_in ^ 1);
+    }
 }
 
 }  // namespace cm
