@@ -22,7 +22,8 @@ UNITS = {
     # host arithmetic (the conduction profile) rounds as written: no FMA
     "cm_api.cu": ["-Xcompiler", "-ffp-contract=off"],
     "kernels_f64.cu": ["--fmad=false"],
-    "kernels_f32.cu": ["--fmad=true"],
+    # FP32: FMA contraction, approximate division and square root
+    "kernels_f32.cu": ["--fmad=true", "-prec-div=false", "-prec-sqrt=false"],
 }
 
 

@@ -21,6 +21,10 @@ struct Launch {
     static cudaError_t unpack(const R* X, double* dense, const Coef<R>& C, int nf, cudaStream_t s);
 };
 
+// FP32 sweeps with two columns per lane (nx even); defined in kernels_f32.cu
+cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
+                            const SweepCtl& sc, cudaStream_t s);
+
 cudaError_t launch_diag_final(const double* scratch, const double* zt, const DiagFinal& F, DevCtl* ctl, cm_diag* rec,
                               cudaStream_t s);
 

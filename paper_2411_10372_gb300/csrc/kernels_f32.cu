@@ -1,9 +1,30 @@
 // FP32 instantiation of the kernels (state and stencil arithmetic in FP32,
 // FMA contraction allowed; the dt rule and all reductions stay FP64).
 #include "kernels_impl.cuh"
+#include "sweep2d_x2.cuh"
 
 namespace cm {
 
 template struct Launch<float>;
+
+cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
+                            const SweepCtl& sc, cudaStream_t s)
+{
+    SweepIO2 io;
+    io.in = in;
+    io.out = out;
+    io.zt = zt;
+    io.nstrips = (C.nx + kOutW2 - 1) / kOutW2;
+    static int bz = 0, bx = 0;
+    if (!bz) { bz = blocks_per_sm(sweep_z2d_x2); bx = blocks_per_sm(sweep_x2d_x2); }
+    io.seg_rows = pick_segment(io.nstrips, C.nz, dir == 2 ? bz : bx, sm_count());
+    const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
+    const long long warps = (long long)io.nstrips * nsegs;
+    const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (dir == 2) sweep_z2d_x2<<<blocks, kWarpsPerBlock * 32, 0, s>>>(io, C, sc);
+    else if (dir == 0) sweep_x2d_x2<<<blocks, kWarpsPerBlock * 32, 0, s>>>(io, C, sc);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 }  // namespace cm

@@ -1,5 +1,6 @@
 // kernels_impl.cuh -- launcher definitions; included once per precision.
 #pragma once
+#include <cstdlib>
 #include "kernels.h"
 #include "sweep2d.cuh"
 #include "aux_kernels.cuh"
@@ -42,17 +43,68 @@ static inline int grid_for(long long work, int threads)
     return (int)b;
 }
 
+// rows per warp segment: each segment pays a 4-row pipeline ramp, and the
+// grid should fill the GPU in whole waves; pick the segment length that
+// minimises waves * (rows + ramp) for the kernel's occupancy
+static inline int pick_segment(int nstrips, int nz, int blocks_per_sm, int nsm)
+{
+    // CM_SEG_ROWS=n forces the segment length (tuning experiments)
+    if (const char* e = getenv("CM_SEG_ROWS")) {
+        const int v = atoi(e);
+        if (v >= 4 && v <= 4096) return v;
+    }
+    const long long cap = (long long)blocks_per_sm * kWarpsPerBlock * nsm;
+    int best = 64;
+    double best_cost = 1e300;
+    for (int seg = 256; seg >= 8; seg /= 2) {
+        const long long warps = (long long)nstrips * ((nz + seg - 1) / seg);
+        const long long waves = (warps + cap - 1) / cap;
+        const double cost = (double)waves * (double)(seg + 4);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = seg; }
+    }
+    return best;
+}
+
+static inline int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <class K>
+static inline int blocks_per_sm(K kernel)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kWarpsPerBlock * 32, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
 template <class R>
 cudaError_t Launch<R>::sweep(int dir, const R* in, R* out, const R* zt, const Coef<R>& C, const SweepCtl& sc,
                              int seg_rows, cudaStream_t s)
 {
+    if constexpr (std::is_same<R, float>::value) {
+        if (C.nx % 2 == 0 && (long long)C.fstride * 5 < (1LL << 31)) return launch_sweep_x2(dir, in, out, zt, C, sc, s);
+    }
+    (void)seg_rows;
     SweepIO<R> io;
     io.in = in;
     io.out = out;
     io.zt = zt;
-    io.seg_rows = seg_rows;
     io.nstrips = (C.nx + kOutW - 1) / kOutW;
-    const int nsegs = (C.nz + seg_rows - 1) / seg_rows;
+    static int bz = 0, bx = 0;
+    if (!bz) { bz = blocks_per_sm(sweep_z2d<R>); bx = blocks_per_sm(sweep_x2d<R>); }
+    io.seg_rows = pick_segment(io.nstrips, C.nz, dir == 2 ? bz : bx, sm_count());
+    const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
     const long long warps = (long long)io.nstrips * nsegs;
     const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (dir == 2) sweep_z2d<R><<<blocks, kWarpsPerBlock * 32, 0, s>>>(io, C, sc);

@@ -1,0 +1,392 @@
+// sweep2d_x2.cuh -- FP32 sweeps with two columns per lane (even nx).
+//
+// Same scheme and row pipeline as sweep2d.cuh, but every lane carries the
+// state of two adjacent columns as float2 and does the arithmetic with the
+// packed FP32x2 instructions of sm_100+ (__fadd2_rn, __fmul2_rn,
+// __ffma2_rn): one instruction updates both columns.  A warp covers 64
+// columns; the stencil and the cross derivatives reach two columns, one
+// lane, to each side, so lanes 1..30 produce 60 output columns per strip.
+// Neighbour columns come from one shuffle per exchanged quantity:
+//   value at c+1 = (own.y, lane+1 .x),  value at c-1 = (lane-1 .y, own.x).
+// Loads and stores are 8-byte vectors (the strip origin is even).
+#pragma once
+#include "cm_device.cuh"
+
+namespace cm {
+
+constexpr int kOutW2 = 60;  // output columns per warp strip
+
+typedef float2 f2;
+
+__device__ __forceinline__ f2 bc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+// a - b, rounded once
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// a - s*b
+__device__ __forceinline__ f2 fnma2(f2 s, f2 b, f2 a) { return __ffma2_rn(make_float2(-s.x, -s.y), b, a); }
+
+__device__ __forceinline__ f2 right_of(f2 v) { return make_float2(v.y, __shfl_down_sync(0xffffffffu, v.x, 1)); }
+__device__ __forceinline__ f2 left_of(f2 v) { return make_float2(__shfl_up_sync(0xffffffffu, v.y, 1), v.x); }
+
+struct S2 { f2 r, mx, mz, E; };
+
+__device__ __forceinline__ S2 right_of(const S2& q) { return {right_of(q.r), right_of(q.mx), right_of(q.mz), right_of(q.E)}; }
+__device__ __forceinline__ S2 left_of(const S2& q) { return {left_of(q.r), left_of(q.mx), left_of(q.mz), left_of(q.E)}; }
+
+__device__ __forceinline__ S2 ld2(const float* __restrict__ base, int fs, int off)
+{
+    const float* s = base + off;
+    return {__ldg(reinterpret_cast<const f2*>(s)), __ldg(reinterpret_cast<const f2*>(s + fs)),
+            __ldg(reinterpret_cast<const f2*>(s + 2 * fs)), __ldg(reinterpret_cast<const f2*>(s + 3 * fs))};
+}
+
+__device__ __forceinline__ void st2(float* __restrict__ base, int fs, int off, const S2& q)
+{
+    float* d = base + off;
+    *reinterpret_cast<f2*>(d) = q.r;
+    *reinterpret_cast<f2*>(d + fs) = q.mx;
+    *reinterpret_cast<f2*>(d + 2 * fs) = q.mz;
+    *reinterpret_cast<f2*>(d + 3 * fs) = q.E;
+}
+
+__device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+
+// primitives: u = m/rho, T = b (E/rho - u^2/2 - g z), p = a rho T
+__device__ __forceinline__ void prims2(const S2& q, f2 gz, const Coef<float>& C, f2& ux, f2& uz, f2& T, f2& p)
+{
+    const f2 ri = rcp2(q.r);
+    ux = mul2(q.mx, ri);
+    uz = mul2(q.mz, ri);
+    const f2 ke = fma2(ux, ux, mul2(uz, uz));
+    const f2 e = fma2(q.E, ri, fma2(ke, bc(-0.5f), gz));  // gz = -g z
+    T = mul2(bc(C.b), e);
+    p = mul2(mul2(bc(C.a), q.r), T);
+}
+
+// F_z (one-sided d/dz inside, central d/dx across)
+__device__ __forceinline__ S2 flux_z2(const S2& q, f2 ux, f2 uz, f2 p, f2 dz_ux, f2 dz_uz, f2 dz_T, f2 dx_ux, f2 dx_uz,
+                                      const Coef<float>& C)
+{
+    const f2 div = add2(dx_ux, dz_uz);
+    const f2 tx = mul2(bc(C.mu), add2(dz_ux, dx_uz));
+    const f2 tz = mul2(bc(C.mu), fma2(bc(C.stokes), div, add2(dz_uz, dz_uz)));
+    S2 F;
+    F.r = q.mz;
+    F.mx = fnma2(bc(1.f), tx, mul2(q.mx, uz));
+    F.mz = add2(fnma2(bc(1.f), tz, mul2(q.mz, uz)), p);
+    F.E = sub2(fnma2(bc(C.kth), dz_T, mul2(uz, add2(q.E, p))), fma2(ux, tx, mul2(uz, tz)));
+    return F;
+}
+
+// F_x (one-sided d/dx inside, central d/dz across)
+__device__ __forceinline__ S2 flux_x2(const S2& q, f2 ux, f2 uz, f2 p, f2 dx_ux, f2 dx_uz, f2 dx_T, f2 dz_ux, f2 dz_uz,
+                                      const Coef<float>& C)
+{
+    const f2 div = add2(dx_ux, dz_uz);
+    const f2 tx = mul2(bc(C.mu), fma2(bc(C.stokes), div, add2(dx_ux, dx_ux)));
+    const f2 tz = mul2(bc(C.mu), add2(dx_uz, dz_ux));
+    S2 F;
+    F.r = q.mx;
+    F.mx = add2(fnma2(bc(1.f), tx, mul2(q.mx, ux)), p);
+    F.mz = fnma2(bc(1.f), tz, mul2(q.mz, ux));
+    F.E = sub2(fnma2(bc(C.kth), dx_T, mul2(ux, add2(q.E, p))), fma2(ux, tx, mul2(uz, tz)));
+    return F;
+}
+
+__device__ __forceinline__ f2 dot2(const S2& a, const S2& b)
+{
+    return fma2(a.E, b.E, fma2(a.mz, b.mz, fma2(a.mx, b.mx, mul2(a.r, b.r))));
+}
+
+// TVD coefficient per column: C = min(Co,1/2)(1 - min(Co,1/2)), phi = clamp(2 s/dd, 0, 1)
+// (dd = 0 gives 0/0 = NaN, which the clamp maps to 0; the flux G dX is 0 there anyway)
+__device__ __forceinline__ float tvd_G1(float sp, float sm, float dd, float Co, int form)
+{
+    const float co = fminf(Co, 0.5f);
+    const float Cc = co * (1.f - co);
+    if (form == 0) {
+        const float pp = fminf(fmaxf(__fdividef(sp + sp, dd), 0.f), 1.f);
+        const float pm = fminf(fmaxf(__fdividef(sm + sm, dd), 0.f), 1.f);
+        return 0.5f * Cc * ((1.f - pp) + (1.f - pm));
+    }
+    if (form == 1) {
+        const float s = sp + sm;
+        return 0.5f * Cc * (1.f - fminf(fmaxf(__fdividef(s + s, dd), 0.f), 1.f));
+    }
+    return 0.f;
+}
+
+__device__ __forceinline__ f2 tvd_G2(f2 sp, f2 sm, f2 dd, f2 Co, int form)
+{
+    return make_float2(tvd_G1(sp.x, sm.x, dd.x, Co.x, form), tvd_G1(sp.y, sm.y, dd.y, Co.y, form));
+}
+
+__device__ __forceinline__ f2 abs2(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ f2 sqrt2(f2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ S2 scale2(f2 g, const S2& d) { return {mul2(g, d.r), mul2(g, d.mx), mul2(g, d.mz), mul2(g, d.E)}; }
+__device__ __forceinline__ S2 diff2(const S2& a, const S2& b) { return {sub2(a.r, b.r), sub2(a.mx, b.mx), sub2(a.mz, b.mz), sub2(a.E, b.E)}; }
+
+struct SweepIO2 {
+    const float* in;
+    float* out;
+    const float* zt;
+    int seg_rows;
+    int nstrips;  // ceil(nx / kOutW2)
+};
+
+// L_z(Delta), FP32, two columns per lane
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int strip = gw % io.nstrips;
+    const int ks = (gw / io.nstrips) * io.seg_rows;
+    const int nz = C.nz, nx = C.nx, pitch = C.pitch;
+    const int fs = (int)C.fstride;
+    const int ke = min(ks + io.seg_rows, nz);
+    const int i = strip * kOutW2 - 2 + 2 * lane;  // first of the lane's two columns (even)
+    int ic = i % nx;
+    if (ic < 0) ic += nx;
+    const bool own = lane >= 1 && lane <= 30 && i < nx;
+
+    const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
+    const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
+    const f2 lam = bc((float)(Delta / C.dz));
+    const f2 lam2 = bc(2.f * (float)(Delta / C.dz));
+    const f2 mDg = bc(-(float)Delta * C.g);  // -Delta g: the source term per unit density
+    const f2 half = bc(0.5f);
+
+    if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
+        sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
+        sc.ctl->t += dt;
+        sc.ctl->steps += 1.0;
+    }
+    if (ks >= nz) return;  // warp-uniform; no block barrier in this kernel
+
+    auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
+    auto gz_of = [&](int j) { return bc(-C.g * __ldg(io.zt + min(max(j, 0), nz - 1))); };
+
+    S2 Xm2 = ld2(io.in, fs, row_off(ks - 4));
+    S2 Xm1 = Xm2;
+    f2 ux1, uz1, T1, p1;
+    prims2(Xm1, gz_of(ks - 4), C, ux1, uz1, T1, p1);
+    const f2 z0 = bc(0.f);
+    f2 A2 = z0, A1 = z0, dxux1 = z0, dxuz1 = z0;
+    S2 F2 = {z0, z0, z0, z0};
+    S2 XP2 = Xm2;
+    f2 ppux2 = ux1, ppuz2 = uz1, ppT2 = T1;
+    S2 FP2 = F2, d1 = F2, Dm = F2;
+    f2 dd1 = z0, ss2 = z0;
+
+    S2 pf0 = ld2(io.in, fs, row_off(ks - 2));
+    S2 pf1 = ld2(io.in, fs, row_off(ks - 1));
+
+    for (int j = ks - 2; j <= ke + 1; ++j) {
+        const S2 X0 = pf0;
+        pf0 = pf1;
+        pf1 = ld2(io.in, fs, row_off(j + 2));
+
+        f2 ux0, uz0, T0, p0;
+        prims2(X0, gz_of(j), C, ux0, uz0, T0, p0);
+        const f2 A0 = add2(abs2(uz0), sqrt2(mul2(bc(C.cs2), T0)));
+        const f2 dxux0 = mul2(sub2(right_of(ux0), left_of(ux0)), bc(C.inv_2dx));
+        const f2 dxuz0 = mul2(sub2(right_of(uz0), left_of(uz0)), bc(C.inv_2dx));
+
+        const int m = j - 1;
+        const f2 idz = bc(C.inv_dz);
+        const S2 F1 = flux_z2(Xm1, ux1, uz1, p1, mul2(sub2(ux0, ux1), idz), mul2(sub2(uz0, uz1), idz),
+                              mul2(sub2(T0, T1), idz), dxux1, dxuz1, C);
+        S2 XP1;
+        if (m >= 1 && m <= nz - 2) {
+            XP1.r = fnma2(lam, sub2(F1.r, F2.r), Xm1.r);
+            XP1.mx = fnma2(lam, sub2(F1.mx, F2.mx), Xm1.mx);
+            XP1.mz = fma2(mDg, Xm1.r, fnma2(lam, sub2(F1.mz, F2.mz), Xm1.mz));
+            XP1.E = fnma2(lam, sub2(F1.E, F2.E), Xm1.E);
+        } else if (m <= 0) {
+            XP1.r = fnma2(lam2, F1.r, Xm1.r);
+            XP1.mx = z0; XP1.mz = z0;
+            XP1.E = mul2(XP1.r, bc(C.ebot));
+        } else {
+            XP1.r = fma2(lam2, F2.r, Xm1.r);
+            XP1.mx = z0; XP1.mz = z0;
+            XP1.E = mul2(XP1.r, bc(C.etop));
+        }
+        f2 ppux1, ppuz1, ppT1, ppp1;
+        prims2(XP1, gz_of(m), C, ppux1, ppuz1, ppT1, ppp1);
+        const f2 dxppux1 = mul2(sub2(right_of(ppux1), left_of(ppux1)), bc(C.inv_2dx));
+        const f2 dxppuz1 = mul2(sub2(right_of(ppuz1), left_of(ppuz1)), bc(C.inv_2dx));
+        const S2 FP1 = flux_z2(XP1, ppux1, ppuz1, ppp1, mul2(sub2(ppux1, ppux2), idz), mul2(sub2(ppuz1, ppuz2), idz),
+                               mul2(sub2(ppT1, ppT2), idz), dxppux1, dxppuz1, C);
+
+        const int c = j - 2;
+        S2 Xa;
+        if (c >= 1 && c <= nz - 2) {
+            Xa.r = mul2(half, add2(XP2.r, fnma2(lam, sub2(FP1.r, FP2.r), Xm2.r)));
+            Xa.mx = mul2(half, add2(XP2.mx, fnma2(lam, sub2(FP1.mx, FP2.mx), Xm2.mx)));
+            Xa.mz = mul2(half, add2(XP2.mz, fma2(mDg, XP2.r, fnma2(lam, sub2(FP1.mz, FP2.mz), Xm2.mz))));
+            Xa.E = mul2(half, add2(XP2.E, fnma2(lam, sub2(FP1.E, FP2.E), Xm2.E)));
+        } else if (c <= 0) {
+            Xa.r = mul2(half, add2(XP2.r, fnma2(lam2, FP1.r, Xm2.r)));
+            Xa.mx = Xa.mz = Xa.E = z0;
+        } else {
+            Xa.r = mul2(half, add2(XP2.r, Xm2.r));
+            Xa.mx = Xa.mz = Xa.E = z0;
+        }
+
+        const S2 d0 = diff2(X0, Xm1);
+        const f2 dd0 = dot2(d0, d0);
+        const f2 ss1 = dot2(d1, d0);
+        S2 Dn = {z0, z0, z0, z0};
+        if (c >= 1 && c <= nz - 3) {
+            const f2 G = tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form);
+            Dn = scale2(G, d1);
+        }
+
+        if (c >= ks && c < ke) {
+            S2 Xn;
+            if (c >= 1 && c <= nz - 2) {
+                Xn.r = add2(Xa.r, sub2(Dn.r, Dm.r));
+                Xn.mx = add2(Xa.mx, sub2(Dn.mx, Dm.mx));
+                Xn.mz = add2(Xa.mz, sub2(Dn.mz, Dm.mz));
+                Xn.E = add2(Xa.E, sub2(Dn.E, Dm.E));
+            } else {
+                Xn.r = Xa.r;
+                Xn.mx = z0; Xn.mz = z0;
+                Xn.E = mul2(Xa.r, bc(c == 0 ? C.ebot : C.etop));
+            }
+            if (own) st2(io.out, fs, c * pitch + i, Xn);
+        }
+
+        Xm2 = Xm1; Xm1 = X0;
+        ux1 = ux0; uz1 = uz0; T1 = T0; p1 = p0;
+        A2 = A1; A1 = A0;
+        dxux1 = dxux0; dxuz1 = dxuz0;
+        F2 = F1; XP2 = XP1;
+        ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1;
+        FP2 = FP1;
+        d1 = d0; dd1 = dd0; ss2 = ss1; Dm = Dn;
+    }
+}
+
+// L_x(Delta) on the interior rows, FP32, two columns per lane
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int strip = gw % io.nstrips;
+    const int ks = (gw / io.nstrips) * io.seg_rows;
+    const int nz = C.nz, nx = C.nx, pitch = C.pitch;
+    const int fs = (int)C.fstride;
+    const int ke = min(ks + io.seg_rows, nz);
+    const int i = strip * kOutW2 - 2 + 2 * lane;
+    int ic = i % nx;
+    if (ic < 0) ic += nx;
+    const bool own = lane >= 1 && lane <= 30 && i < nx;
+
+    const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
+    const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
+    const f2 lam = bc((float)(Delta / C.dx));
+    const f2 half = bc(0.5f);
+
+    if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
+        sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
+        sc.ctl->t += dt;
+        sc.ctl->steps += 1.0;
+    }
+
+    float rmax = 0.f;
+    int bad = 0;
+    if (ks < nz) {
+        auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
+        auto gz_of = [&](int j) { return bc(-C.g * __ldg(io.zt + min(max(j, 0), nz - 1))); };
+        const f2 idx_ = bc(C.inv_dx), i2dz = bc(C.inv_2dz);
+
+        S2 Xm2 = ld2(io.in, fs, row_off(ks - 4));
+        S2 Xm1 = Xm2;
+        f2 ux1, uz1, T1, p1;
+        prims2(Xm1, gz_of(ks - 4), C, ux1, uz1, T1, p1);
+        f2 ux2 = ux1, uz2 = uz1, T2 = T1;
+        S2 XP2 = Xm2;
+        f2 ppux2 = ux1, ppuz2 = uz1, ppT2 = T1, ppp2 = p1;
+        f2 ppux3 = ux1, ppuz3 = uz1;
+        S2 pf0 = ld2(io.in, fs, row_off(ks - 2));
+        S2 pf1 = ld2(io.in, fs, row_off(ks - 1));
+
+        for (int j = ks - 2; j <= ke + 1; ++j) {
+            const S2 X0 = pf0;
+            pf0 = pf1;
+            pf1 = ld2(io.in, fs, row_off(j + 2));
+            f2 ux0, uz0, T0, p0;
+            prims2(X0, gz_of(j), C, ux0, uz0, T0, p0);
+
+            // row m = j-1: F^n (forward x), X^P
+            const int m = j - 1;
+            const S2 F1 = flux_x2(Xm1, ux1, uz1, p1, mul2(sub2(right_of(ux1), ux1), idx_),
+                                  mul2(sub2(right_of(uz1), uz1), idx_), mul2(sub2(right_of(T1), T1), idx_),
+                                  mul2(sub2(ux0, ux2), i2dz), mul2(sub2(uz0, uz2), i2dz), C);
+            S2 XP1 = Xm1;
+            if (m >= 1 && m <= nz - 2) {
+                const S2 Fl = left_of(F1);
+                XP1.r = fnma2(lam, sub2(F1.r, Fl.r), Xm1.r);
+                XP1.mx = fnma2(lam, sub2(F1.mx, Fl.mx), Xm1.mx);
+                XP1.mz = fnma2(lam, sub2(F1.mz, Fl.mz), Xm1.mz);
+                XP1.E = fnma2(lam, sub2(F1.E, Fl.E), Xm1.E);
+            }
+            f2 ppux1, ppuz1, ppT1, ppp1;
+            prims2(XP1, gz_of(m), C, ppux1, ppuz1, ppT1, ppp1);
+
+            // row c = j-2: F^P (backward x), corrector, average, TVD along x
+            const int c = j - 2;
+            if (c >= ks && c < ke) {
+                S2 Xn = Xm2;  // plate rows pass through
+                if (c >= 1 && c <= nz - 2) {
+                    const S2 FP = flux_x2(XP2, ppux2, ppuz2, ppp2, mul2(sub2(ppux2, left_of(ppux2)), idx_),
+                                          mul2(sub2(ppuz2, left_of(ppuz2)), idx_), mul2(sub2(ppT2, left_of(ppT2)), idx_),
+                                          mul2(sub2(ppux1, ppux3), i2dz), mul2(sub2(ppuz1, ppuz3), i2dz), C);
+                    const S2 FPr = right_of(FP);
+                    const S2 d0 = diff2(right_of(Xm2), Xm2);
+                    const f2 dd = dot2(d0, d0);
+                    const S2 dl = left_of(d0);
+                    const f2 sp = dot2(dl, d0);
+                    const f2 sm = right_of(sp);
+                    const f2 A = add2(abs2(ux2), sqrt2(mul2(bc(C.cs2), T2)));
+                    const f2 G = tvd_G2(sp, sm, dd, mul2(lam, max2(A, right_of(A))), C.tvd_form);
+                    const S2 Dn = scale2(G, d0);
+                    const S2 Dl = left_of(Dn);
+                    Xn.r = add2(mul2(half, add2(XP2.r, fnma2(lam, sub2(FPr.r, FP.r), Xm2.r))), sub2(Dn.r, Dl.r));
+                    Xn.mx = add2(mul2(half, add2(XP2.mx, fnma2(lam, sub2(FPr.mx, FP.mx), Xm2.mx))), sub2(Dn.mx, Dl.mx));
+                    Xn.mz = add2(mul2(half, add2(XP2.mz, fnma2(lam, sub2(FPr.mz, FP.mz), Xm2.mz))), sub2(Dn.mz, Dl.mz));
+                    Xn.E = add2(mul2(half, add2(XP2.E, fnma2(lam, sub2(FPr.E, FP.E), Xm2.E))), sub2(Dn.E, Dl.E));
+                }
+                if (own) {
+                    st2(io.out, fs, c * pitch + i, Xn);
+                    if (sc.last) {
+                        f2 ux, uz, T, p;
+                        prims2(Xn, gz_of(c), C, ux, uz, T, p);
+                        const f2 cs = sqrt2(mul2(bc(C.cs2), T));
+                        const f2 rx = mul2(add2(abs2(ux), cs), idx_);
+                        const f2 rz = mul2(add2(abs2(uz), cs), bc(C.inv_dz));
+                        const float r = fmaxf(fmaxf(rx.x, rx.y), fmaxf(rz.x, rz.y));
+                        if (!(r > 0.f) || !(r < 1e30f)) bad = 1;
+                        rmax = fmaxf(rmax, r);
+                    }
+                }
+            }
+
+            Xm2 = Xm1; Xm1 = X0;
+            ux2 = ux1; uz2 = uz1; T2 = T1;
+            ux1 = ux0; uz1 = uz0; T1 = T0; p1 = p0;
+            ppux3 = ppux2; ppuz3 = ppuz2;
+            XP2 = XP1;
+            ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
+        }
+    }
+    if (sc.last) block_dt_reduce(rmax > 0.f ? 1.0 / (double)rmax : 1e308, bad, sc.ctl, sc.slot_in ^ 1);
+}
+
+}  // namespace cm

@@ -74,6 +74,28 @@ def test_single_sweeps_fp64(nx, nz, tvd):
     s.close()
 
 
+@pytest.mark.parametrize("nx,nz", [(8, 5), (29, 7), (30, 9), (64, 33), (122, 17), (256, 64), (250, 130)])
+def test_single_sweeps_fp32(nx, nz):
+    """FP32 sweeps (two columns per lane for even nx, one for odd nx) on a
+    stirred FP64 state rounded to FP32: each sweep within FP32 rounding of the
+    oracle applied to the same rounded input."""
+    cfg = O.Config(nx=nx, nz=nz, Ra=1e5, dt_fixed=1e-3)
+    X = stirred_state(cfg, seed=nx * 7 + nz).astype(np.float32).astype(np.float64)
+    s = solver_for(cfg, "fp32")
+    for direction in (2, 0):
+        Delta = 0.2 * min(cfg.aspect / nx, 1.0 / (nz - 1)) / 4.0
+        s.set_state(X)
+        s.sweep(direction, Delta)
+        got = s.state()
+        want = O.sweep(cfg, X, direction, Delta)
+        for f in (0, 3):
+            assert rel_l2(got[f], want[f]) <= 2e-6, (direction, f)
+        scale = np.linalg.norm(want[0]) * 3.65
+        for f in (1, 2):
+            assert np.linalg.norm(got[f] - want[f]) / scale <= 2e-6, (direction, f)
+    s.close()
+
+
 def test_initial_state_and_dt_match_oracle():
     for precision, tol in (("fp64", 0.0), ("fp32", 6e-8)):
         cfg = O.Config(nx=100, nz=33, Ra=1e6, pert_amp=1e-3, seed=99)
