@@ -16,13 +16,18 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     io.zt = zt;
     io.nstrips = (C.nx + kOutW2 - 1) / kOutW2;
     static int bz = 0, bx = 0;
-    if (!bz) { bz = blocks_per_sm(sweep_z2d_x2); bx = blocks_per_sm(sweep_x2d_x2); }
+    if (!bz) {
+        cudaFuncSetAttribute(sweep_z2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        cudaFuncSetAttribute(sweep_x2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        bz = blocks_per_sm(sweep_z2d_x2, kRingBytes);
+        bx = blocks_per_sm(sweep_x2d_x2, kRingBytes);
+    }
     io.seg_rows = pick_segment(io.nstrips, C.nz, dir == 2 ? bz : bx, sm_count());
     const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
     const long long warps = (long long)io.nstrips * nsegs;
     const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (dir == 2) sweep_z2d_x2<<<blocks, kWarpsPerBlock * 32, 0, s>>>(io, C, sc);
-    else if (dir == 0) sweep_x2d_x2<<<blocks, kWarpsPerBlock * 32, 0, s>>>(io, C, sc);
+    if (dir == 2) sweep_z2d_x2<<<blocks, kWarpsPerBlock * 32, kRingBytes, s>>>(io, C, sc);
+    else if (dir == 0) sweep_x2d_x2<<<blocks, kWarpsPerBlock * 32, kRingBytes, s>>>(io, C, sc);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

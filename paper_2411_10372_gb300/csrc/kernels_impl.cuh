@@ -78,10 +78,10 @@ static inline int sm_count()
 }
 
 template <class K>
-static inline int blocks_per_sm(K kernel)
+static inline int blocks_per_sm(K kernel, size_t smem = 0)
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kWarpsPerBlock * 32, 0) != cudaSuccess || b < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kWarpsPerBlock * 32, smem) != cudaSuccess || b < 1) {
         cudaGetLastError();
         b = 1;
     }

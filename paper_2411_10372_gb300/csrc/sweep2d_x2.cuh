@@ -137,10 +137,51 @@ struct SweepIO2 {
     int nstrips;  // ceil(nx / kOutW2)
 };
 
-// L_z(Delta), FP32, two columns per lane
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// ---- asynchronous row loads: each lane copies its own two columns of the
+// four fields into a per-thread ring in shared memory (cp.async), kRing rows
+// deep, so a row is requested kRing-1 rows before it is consumed without
+// holding registers.  A lane only ever reads back what it copied itself, so
+// cp.async.wait_group is the only ordering needed.
+constexpr int kRing = 4;
+
+__device__ __forceinline__ void cp_async8(f2* smem, const float* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_ring() { asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory"); }
+__device__ __forceinline__ void cp_async_drain() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+struct RowRing {
+    f2* base;  // [kRing][4 fields][blockDim.x]
+    int nthreads;
+    __device__ __forceinline__ f2* at(int slot, int f) const { return base + (slot * 4 + f) * nthreads + threadIdx.x; }
+    __device__ __forceinline__ void request(int slot, const float* __restrict__ g, int fs, int off) const
+    {
+        cp_async8(at(slot, 0), g + off);
+        cp_async8(at(slot, 1), g + off + fs);
+        cp_async8(at(slot, 2), g + off + 2 * fs);
+        cp_async8(at(slot, 3), g + off + 3 * fs);
+        cp_async_commit();
+    }
+    __device__ __forceinline__ S2 take(int slot) const
+    {
+        return {*at(slot, 0), *at(slot, 1), *at(slot, 2), *at(slot, 3)};
+    }
+};
+
+// L_z(Delta), FP32, two columns per lane.  Row pipeline at step j (row j
+// just taken from the ring):
+//   F^n_{j-1}, X^P_{j-1}, F^P_{j-1}; TVD flux D across (j-2, j-1);
+//   output X_new_{j-2} = H_{j-2} - (lambda/2) F^P_{j-1} + D;
+//   H_{j-1} = (X^P + X + Delta S^P + lambda F^P)_{j-1} / 2 - D,
+// which is the average (X^P + X^C)/2 plus the TVD term of Sec. 3.1 with the
+// corrector split into its two rows.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 {
+    extern __shared__ f2 ring_mem[];
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int strip = gw % io.nstrips;
@@ -155,10 +196,10 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 
     const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
     const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
-    const f2 lam = bc((float)(Delta / C.dz));
-    const f2 lam2 = bc(2.f * (float)(Delta / C.dz));
-    const f2 mDg = bc(-(float)Delta * C.g);  // -Delta g: the source term per unit density
-    const f2 half = bc(0.5f);
+    const float lamf = (float)(Delta / C.dz);
+    const f2 lam = bc(lamf), hlam = bc(0.5f * lamf), lam2 = bc(2.f * lamf);
+    const f2 mDg = bc(-(float)Delta * C.g);  // Delta * (source per unit density)
+    const f2 half = bc(0.5f), idz = bc(C.inv_dz), i2dx = bc(C.inv_2dx);
 
     if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
         sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
@@ -167,41 +208,48 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
     }
     if (ks >= nz) return;  // warp-uniform; no block barrier in this kernel
 
+    const RowRing ring{ring_mem, (int)blockDim.x};
     auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
-    auto gz_of = [&](int j) { return bc(-C.g * __ldg(io.zt + min(max(j, 0), nz - 1))); };
+    auto gz_of = [&](int j) { return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz)); };
 
-    S2 Xm2 = ld2(io.in, fs, row_off(ks - 4));
-    S2 Xm1 = Xm2;
-    f2 ux1, uz1, T1, p1;
-    prims2(Xm1, gz_of(ks - 4), C, ux1, uz1, T1, p1);
+    const int j0 = ks - 2;
+    for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in, fs, row_off(j0 + q));
+
     const f2 z0 = bc(0.f);
-    f2 A2 = z0, A1 = z0, dxux1 = z0, dxuz1 = z0;
+    S2 Xm1;                 // X_{j-1}
+    f2 ux1, uz1, T1, p1;    // primitives of X_{j-1}
+    f2 A1 = z0, A2 = z0;    // |u_z| + c of rows j-1, j-2
     S2 F2 = {z0, z0, z0, z0};
-    S2 XP2 = Xm2;
-    f2 ppux2 = ux1, ppuz2 = uz1, ppT2 = T1;
-    S2 FP2 = F2, d1 = F2, Dm = F2;
+    f2 ppux2 = z0, ppuz2 = z0, ppT2 = z0;  // primitives of X^P_{j-2}
+    S2 H = {z0, z0, z0, z0};               // H_{j-2}
+    S2 d1 = {z0, z0, z0, z0};
     f2 dd1 = z0, ss2 = z0;
+    {
+        // prime the previous row with the first one so nothing is undefined
+        Xm1 = ld2(io.in, fs, row_off(j0 - 1));
+        prims2(Xm1, gz_of(j0 - 1), C, ux1, uz1, T1, p1);
+        ppux2 = ux1; ppuz2 = uz1; ppT2 = T1;
+    }
 
-    S2 pf0 = ld2(io.in, fs, row_off(ks - 2));
-    S2 pf1 = ld2(io.in, fs, row_off(ks - 1));
-
-    for (int j = ks - 2; j <= ke + 1; ++j) {
-        const S2 X0 = pf0;
-        pf0 = pf1;
-        pf1 = ld2(io.in, fs, row_off(j + 2));
+    for (int j = j0; j <= ke + 1; ++j) {
+        const int t = j - j0;
+        ring.request((t + kRing - 1) % kRing, io.in, fs, row_off(j + kRing - 1));
+        cp_async_wait_ring();
+        const S2 X0 = ring.take(t % kRing);
 
         f2 ux0, uz0, T0, p0;
         prims2(X0, gz_of(j), C, ux0, uz0, T0, p0);
         const f2 A0 = add2(abs2(uz0), sqrt2(mul2(bc(C.cs2), T0)));
-        const f2 dxux0 = mul2(sub2(right_of(ux0), left_of(ux0)), bc(C.inv_2dx));
-        const f2 dxuz0 = mul2(sub2(right_of(uz0), left_of(uz0)), bc(C.inv_2dx));
 
+        // row m = j-1: F^n (forward z, central x), X^P, F^P (backward z)
         const int m = j - 1;
-        const f2 idz = bc(C.inv_dz);
+        const f2 dxux1 = mul2(sub2(right_of(ux1), left_of(ux1)), i2dx);
+        const f2 dxuz1 = mul2(sub2(right_of(uz1), left_of(uz1)), i2dx);
         const S2 F1 = flux_z2(Xm1, ux1, uz1, p1, mul2(sub2(ux0, ux1), idz), mul2(sub2(uz0, uz1), idz),
                               mul2(sub2(T0, T1), idz), dxux1, dxuz1, C);
         S2 XP1;
-        if (m >= 1 && m <= nz - 2) {
+        const bool interior_m = (m >= 1 && m <= nz - 2);
+        if (interior_m) {
             XP1.r = fnma2(lam, sub2(F1.r, F2.r), Xm1.r);
             XP1.mx = fnma2(lam, sub2(F1.mx, F2.mx), Xm1.mx);
             XP1.mz = fma2(mDg, Xm1.r, fnma2(lam, sub2(F1.mz, F2.mz), Xm1.mz));
@@ -217,65 +265,67 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         }
         f2 ppux1, ppuz1, ppT1, ppp1;
         prims2(XP1, gz_of(m), C, ppux1, ppuz1, ppT1, ppp1);
-        const f2 dxppux1 = mul2(sub2(right_of(ppux1), left_of(ppux1)), bc(C.inv_2dx));
-        const f2 dxppuz1 = mul2(sub2(right_of(ppuz1), left_of(ppuz1)), bc(C.inv_2dx));
+        const f2 dxppux1 = mul2(sub2(right_of(ppux1), left_of(ppux1)), i2dx);
+        const f2 dxppuz1 = mul2(sub2(right_of(ppuz1), left_of(ppuz1)), i2dx);
         const S2 FP1 = flux_z2(XP1, ppux1, ppuz1, ppp1, mul2(sub2(ppux1, ppux2), idz), mul2(sub2(ppuz1, ppuz2), idz),
                                mul2(sub2(ppT1, ppT2), idz), dxppux1, dxppuz1, C);
 
-        const int c = j - 2;
-        S2 Xa;
-        if (c >= 1 && c <= nz - 2) {
-            Xa.r = mul2(half, add2(XP2.r, fnma2(lam, sub2(FP1.r, FP2.r), Xm2.r)));
-            Xa.mx = mul2(half, add2(XP2.mx, fnma2(lam, sub2(FP1.mx, FP2.mx), Xm2.mx)));
-            Xa.mz = mul2(half, add2(XP2.mz, fma2(mDg, XP2.r, fnma2(lam, sub2(FP1.mz, FP2.mz), Xm2.mz))));
-            Xa.E = mul2(half, add2(XP2.E, fnma2(lam, sub2(FP1.E, FP2.E), Xm2.E)));
-        } else if (c <= 0) {
-            Xa.r = mul2(half, add2(XP2.r, fnma2(lam2, FP1.r, Xm2.r)));
-            Xa.mx = Xa.mz = Xa.E = z0;
-        } else {
-            Xa.r = mul2(half, add2(XP2.r, Xm2.r));
-            Xa.mx = Xa.mz = Xa.E = z0;
-        }
-
+        // TVD flux across (j-2, j-1) from the input state
         const S2 d0 = diff2(X0, Xm1);
         const f2 dd0 = dot2(d0, d0);
         const f2 ss1 = dot2(d1, d0);
+        const int c = j - 2;
         S2 Dn = {z0, z0, z0, z0};
-        if (c >= 1 && c <= nz - 3) {
-            const f2 G = tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form);
-            Dn = scale2(G, d1);
-        }
+        if (c >= 1 && c <= nz - 3) Dn = scale2(tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form), d1);
 
+        // output row c = j-2
         if (c >= ks && c < ke) {
             S2 Xn;
             if (c >= 1 && c <= nz - 2) {
-                Xn.r = add2(Xa.r, sub2(Dn.r, Dm.r));
-                Xn.mx = add2(Xa.mx, sub2(Dn.mx, Dm.mx));
-                Xn.mz = add2(Xa.mz, sub2(Dn.mz, Dm.mz));
-                Xn.E = add2(Xa.E, sub2(Dn.E, Dm.E));
+                Xn.r = add2(fnma2(hlam, FP1.r, H.r), Dn.r);
+                Xn.mx = add2(fnma2(hlam, FP1.mx, H.mx), Dn.mx);
+                Xn.mz = add2(fnma2(hlam, FP1.mz, H.mz), Dn.mz);
+                Xn.E = add2(fnma2(hlam, FP1.E, H.E), Dn.E);
             } else {
-                Xn.r = Xa.r;
+                // plates: rho = (rho^P + rho^C)/2 with the half-cell corrector
+                Xn.r = (c == 0) ? fnma2(lam, FP1.r, H.r) : H.r;
                 Xn.mx = z0; Xn.mz = z0;
-                Xn.E = mul2(Xa.r, bc(c == 0 ? C.ebot : C.etop));
+                Xn.E = mul2(Xn.r, bc(c == 0 ? C.ebot : C.etop));
             }
             if (own) st2(io.out, fs, c * pitch + i, Xn);
         }
 
-        Xm2 = Xm1; Xm1 = X0;
+        // H of row m for the next step
+        if (interior_m) {
+            H.r = sub2(mul2(half, fma2(lam, FP1.r, add2(XP1.r, Xm1.r))), Dn.r);
+            H.mx = sub2(mul2(half, fma2(lam, FP1.mx, add2(XP1.mx, Xm1.mx))), Dn.mx);
+            H.mz = sub2(mul2(half, fma2(lam, FP1.mz, fma2(mDg, XP1.r, add2(XP1.mz, Xm1.mz)))), Dn.mz);
+            H.E = sub2(mul2(half, fma2(lam, FP1.E, add2(XP1.E, Xm1.E))), Dn.E);
+        } else {
+            H.r = mul2(half, add2(XP1.r, Xm1.r));
+            H.mx = z0; H.mz = z0; H.E = z0;
+        }
+
+        Xm1 = X0;
         ux1 = ux0; uz1 = uz0; T1 = T0; p1 = p0;
         A2 = A1; A1 = A0;
-        dxux1 = dxux0; dxuz1 = dxuz0;
-        F2 = F1; XP2 = XP1;
+        F2 = F1;
         ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1;
-        FP2 = FP1;
-        d1 = d0; dd1 = dd0; ss2 = ss1; Dm = Dn;
+        d1 = d0; dd1 = dd0; ss2 = ss1;
     }
+    cp_async_drain();  // rows requested past the segment end
 }
 
-// L_x(Delta) on the interior rows, FP32, two columns per lane
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// L_x(Delta) on the interior rows (plate rows pass through), FP32, two
+// columns per lane.  Row pipeline at step j: for row m = j-1, F^n (forward
+// x, central z from rows j and j-2), X^P, the TVD term along x and
+// K_m = (X^P + X)_m/2 + D_{i+1/2} - D_{i-1/2}; then for row c = j-2, F^P
+// (backward x, central z from X^P rows j-1 and j-3) and
+// X_new_c = K_c - (lambda/2)(F^P_{i+1} - F^P_i).
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
 sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 {
+    extern __shared__ f2 ring_mem[];
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int strip = gw % io.nstrips;
@@ -290,7 +340,8 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 
     const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
     const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
-    const f2 lam = bc((float)(Delta / C.dx));
+    const float lamf = (float)(Delta / C.dx);
+    const f2 lam = bc(lamf), hlam = bc(0.5f * lamf);
     const f2 half = bc(0.5f);
 
     if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -302,66 +353,72 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
     float rmax = 0.f;
     int bad = 0;
     if (ks < nz) {
+        const RowRing ring{ring_mem, (int)blockDim.x};
         auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
-        auto gz_of = [&](int j) { return bc(-C.g * __ldg(io.zt + min(max(j, 0), nz - 1))); };
+        auto gz_of = [&](int j) { return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz)); };
         const f2 idx_ = bc(C.inv_dx), i2dz = bc(C.inv_2dz);
+        const f2 z0 = bc(0.f);
 
-        S2 Xm2 = ld2(io.in, fs, row_off(ks - 4));
-        S2 Xm1 = Xm2;
+        const int j0 = ks - 2;
+        for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in, fs, row_off(j0 + q));
+
+        S2 Xm1 = ld2(io.in, fs, row_off(j0 - 1));
         f2 ux1, uz1, T1, p1;
-        prims2(Xm1, gz_of(ks - 4), C, ux1, uz1, T1, p1);
-        f2 ux2 = ux1, uz2 = uz1, T2 = T1;
-        S2 XP2 = Xm2;
+        prims2(Xm1, gz_of(j0 - 1), C, ux1, uz1, T1, p1);
+        f2 ux2 = ux1, uz2 = uz1;
+        S2 XP2 = Xm1, K2 = Xm1;
         f2 ppux2 = ux1, ppuz2 = uz1, ppT2 = T1, ppp2 = p1;
         f2 ppux3 = ux1, ppuz3 = uz1;
-        S2 pf0 = ld2(io.in, fs, row_off(ks - 2));
-        S2 pf1 = ld2(io.in, fs, row_off(ks - 1));
 
-        for (int j = ks - 2; j <= ke + 1; ++j) {
-            const S2 X0 = pf0;
-            pf0 = pf1;
-            pf1 = ld2(io.in, fs, row_off(j + 2));
+        for (int j = j0; j <= ke + 1; ++j) {
+            const int t = j - j0;
+            ring.request((t + kRing - 1) % kRing, io.in, fs, row_off(j + kRing - 1));
+            cp_async_wait_ring();
+            const S2 X0 = ring.take(t % kRing);
             f2 ux0, uz0, T0, p0;
             prims2(X0, gz_of(j), C, ux0, uz0, T0, p0);
 
-            // row m = j-1: F^n (forward x), X^P
+            // row m = j-1
             const int m = j - 1;
-            const S2 F1 = flux_x2(Xm1, ux1, uz1, p1, mul2(sub2(right_of(ux1), ux1), idx_),
-                                  mul2(sub2(right_of(uz1), uz1), idx_), mul2(sub2(right_of(T1), T1), idx_),
-                                  mul2(sub2(ux0, ux2), i2dz), mul2(sub2(uz0, uz2), i2dz), C);
-            S2 XP1 = Xm1;
+            S2 XP1 = Xm1, K1 = Xm1;  // plate rows pass through
             if (m >= 1 && m <= nz - 2) {
+                const S2 F1 = flux_x2(Xm1, ux1, uz1, p1, mul2(sub2(right_of(ux1), ux1), idx_),
+                                      mul2(sub2(right_of(uz1), uz1), idx_), mul2(sub2(right_of(T1), T1), idx_),
+                                      mul2(sub2(ux0, ux2), i2dz), mul2(sub2(uz0, uz2), i2dz), C);
                 const S2 Fl = left_of(F1);
                 XP1.r = fnma2(lam, sub2(F1.r, Fl.r), Xm1.r);
                 XP1.mx = fnma2(lam, sub2(F1.mx, Fl.mx), Xm1.mx);
                 XP1.mz = fnma2(lam, sub2(F1.mz, Fl.mz), Xm1.mz);
                 XP1.E = fnma2(lam, sub2(F1.E, Fl.E), Xm1.E);
+                // TVD along x on row m from the input state
+                const S2 d0 = diff2(right_of(Xm1), Xm1);
+                const f2 dd = dot2(d0, d0);
+                const f2 sp = dot2(left_of(d0), d0);
+                const f2 A = add2(abs2(ux1), sqrt2(mul2(bc(C.cs2), T1)));
+                const f2 G = tvd_G2(sp, right_of(sp), dd, mul2(lam, max2(A, right_of(A))), C.tvd_form);
+                const S2 Dn = scale2(G, d0);
+                const S2 Dl = left_of(Dn);
+                K1.r = fma2(half, add2(XP1.r, Xm1.r), sub2(Dn.r, Dl.r));
+                K1.mx = fma2(half, add2(XP1.mx, Xm1.mx), sub2(Dn.mx, Dl.mx));
+                K1.mz = fma2(half, add2(XP1.mz, Xm1.mz), sub2(Dn.mz, Dl.mz));
+                K1.E = fma2(half, add2(XP1.E, Xm1.E), sub2(Dn.E, Dl.E));
             }
             f2 ppux1, ppuz1, ppT1, ppp1;
             prims2(XP1, gz_of(m), C, ppux1, ppuz1, ppT1, ppp1);
 
-            // row c = j-2: F^P (backward x), corrector, average, TVD along x
+            // row c = j-2: F^P (backward x, central z) and the corrector
             const int c = j - 2;
             if (c >= ks && c < ke) {
-                S2 Xn = Xm2;  // plate rows pass through
+                S2 Xn = K2;
                 if (c >= 1 && c <= nz - 2) {
                     const S2 FP = flux_x2(XP2, ppux2, ppuz2, ppp2, mul2(sub2(ppux2, left_of(ppux2)), idx_),
                                           mul2(sub2(ppuz2, left_of(ppuz2)), idx_), mul2(sub2(ppT2, left_of(ppT2)), idx_),
                                           mul2(sub2(ppux1, ppux3), i2dz), mul2(sub2(ppuz1, ppuz3), i2dz), C);
                     const S2 FPr = right_of(FP);
-                    const S2 d0 = diff2(right_of(Xm2), Xm2);
-                    const f2 dd = dot2(d0, d0);
-                    const S2 dl = left_of(d0);
-                    const f2 sp = dot2(dl, d0);
-                    const f2 sm = right_of(sp);
-                    const f2 A = add2(abs2(ux2), sqrt2(mul2(bc(C.cs2), T2)));
-                    const f2 G = tvd_G2(sp, sm, dd, mul2(lam, max2(A, right_of(A))), C.tvd_form);
-                    const S2 Dn = scale2(G, d0);
-                    const S2 Dl = left_of(Dn);
-                    Xn.r = add2(mul2(half, add2(XP2.r, fnma2(lam, sub2(FPr.r, FP.r), Xm2.r))), sub2(Dn.r, Dl.r));
-                    Xn.mx = add2(mul2(half, add2(XP2.mx, fnma2(lam, sub2(FPr.mx, FP.mx), Xm2.mx))), sub2(Dn.mx, Dl.mx));
-                    Xn.mz = add2(mul2(half, add2(XP2.mz, fnma2(lam, sub2(FPr.mz, FP.mz), Xm2.mz))), sub2(Dn.mz, Dl.mz));
-                    Xn.E = add2(mul2(half, add2(XP2.E, fnma2(lam, sub2(FPr.E, FP.E), Xm2.E))), sub2(Dn.E, Dl.E));
+                    Xn.r = fnma2(hlam, sub2(FPr.r, FP.r), K2.r);
+                    Xn.mx = fnma2(hlam, sub2(FPr.mx, FP.mx), K2.mx);
+                    Xn.mz = fnma2(hlam, sub2(FPr.mz, FP.mz), K2.mz);
+                    Xn.E = fnma2(hlam, sub2(FPr.E, FP.E), K2.E);
                 }
                 if (own) {
                     st2(io.out, fs, c * pitch + i, Xn);
@@ -378,15 +435,19 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
                 }
             }
 
-            Xm2 = Xm1; Xm1 = X0;
-            ux2 = ux1; uz2 = uz1; T2 = T1;
+            Xm1 = X0;
+            ux2 = ux1; uz2 = uz1;
             ux1 = ux0; uz1 = uz0; T1 = T0; p1 = p0;
             ppux3 = ppux2; ppuz3 = ppuz2;
-            XP2 = XP1;
+            XP2 = XP1; K2 = K1;
             ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
         }
+        cp_async_drain();  // rows requested past the segment end
     }
     if (sc.last) block_dt_reduce(rmax > 0.f ? 1.0 / (double)rmax : 1e308, bad, sc.ctl, sc.slot_in ^ 1);
 }
+
+// shared memory of the row ring for a block
+constexpr size_t kRingBytes = (size_t)kRing * 4 * kWarpsPerBlock * 32 * sizeof(f2);
 
 }  // namespace cm
