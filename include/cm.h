@@ -191,6 +191,25 @@ int cm_sync(void);
 int cm_save(const char* path);
 int cm_load(const char* path);
 
+/* Diagnostics of a caller's state with no allocation at all (the paper has
+ * no counterpart; this is for callers that must not allocate device memory,
+ * e.g. an in-situ analysis hook called from another application's time loop,
+ * whose memory pool owns the device memory and where a cudaMalloc could fail
+ * or synchronise the device under the host's streams).  Computes the same
+ * record as cm_sample (Sec. 2 definitions, FP64 reductions) without a
+ * context: the scratch lives in a fixed ~1.2 MB __device__ array inside the
+ * library (held on every GPU that loads it until exit), so nz may not exceed
+ * 16384 planes (CM_EINVAL beyond).  The first call on a device looks up that
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race.
+ * state: device pointer to field 0 of a state in the layout of
+ *   cm_state_layout (fields nz*ny*pitch elements apart), precision CM_FP64 or
+ *   CM_FP32; grid, params: host; t, dt, step: copied into the record;
+ * stream: cudaStream_t (NULL = legacy default); out: host.  Blocking. */
+int cm_diag_noalloc(const void* state, int precision, const cm_grid* grid, int pitch, double Ra, double Pr,
+                    double gamma, const cm_params* params, double t, double dt, long long step, void* stream,
+                    cm_diag* out);
+
 /* Free the context and its device memory (not caller-owned state_buf). */
 int cm_finalize(void);
 

@@ -74,6 +74,10 @@ _SIGS = {
     "cm_sync": (ctypes.c_int, []),
     "cm_save": (ctypes.c_int, [ctypes.c_char_p]),
     "cm_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cm_diag_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(cm_grid), ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(cm_params),
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p,
+                                       ctypes.POINTER(cm_diag)]),
     "cm_finalize": (ctypes.c_int, []),
     "cm_last_error": (ctypes.c_char_p, []),
 }
@@ -211,6 +215,17 @@ def cm_save(path: str):
 
 def cm_load(path: str):
     _check(lib().cm_load(path.encode()))
+
+
+def cm_diag_noalloc(state_ptr: int, precision: int, grid: cm_grid, pitch: int, Ra: float, Pr: float,
+                    gamma: float, params: cm_params, t: float = 0.0, dt: float = 0.0, step: int = 0,
+                    stream: int | None = None) -> dict:
+    """Diagnostics of a device state without allocating (see include/cm.h)."""
+    d = cm_diag()
+    _check(lib().cm_diag_noalloc(ctypes.c_void_p(state_ptr), int(precision), ctypes.byref(grid), int(pitch),
+                                 float(Ra), float(Pr), float(gamma), ctypes.byref(params), float(t), float(dt),
+                                 int(step), ctypes.c_void_p(stream) if stream else None, ctypes.byref(d)))
+    return d.as_dict()
 
 
 def cm_finalize():

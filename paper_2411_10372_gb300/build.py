@@ -21,6 +21,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relax
 UNITS = {
     # host arithmetic (the conduction profile) rounds as written: no FMA
     "cm_api.cu": ["-Xcompiler", "-ffp-contract=off"],
+    "diag_noalloc.cu": ["-Xcompiler", "-ffp-contract=off"],
     "kernels_f64.cu": ["--fmad=false"],
     # FP32: FMA contraction, approximate division and square root
     "kernels_f32.cu": ["--fmad=true", "-prec-div=false", "-prec-sqrt=false"],

@@ -730,3 +730,8 @@ int cm_finalize(void)
 const char* cm_last_error(void) { return g_err; }
 
 }  // extern "C"
+
+// error reporting for the other translation units of the library
+namespace cm {
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace cm
