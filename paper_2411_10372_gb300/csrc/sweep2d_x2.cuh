@@ -51,7 +51,22 @@ __device__ __forceinline__ void st2(float* __restrict__ base, int fs, int off, c
     *reinterpret_cast<f2*>(d + 3 * fs) = q.E;
 }
 
-__device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y)); }
+// reciprocal and square root on the special-function unit alone (one MUFU
+// instruction each, ~1 ulp, denormals flushed): the FP32 path's tolerance
+// is far above that
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(rcp_fast(a.x), rcp_fast(a.y)); }
 
 // primitives: u = m/rho, T = b (E/rho - u^2/2 - g z), p = a rho T
 __device__ __forceinline__ void prims2(const S2& q, f2 gz, const Coef<float>& C, f2& ux, f2& uz, f2& T, f2& p)
@@ -100,32 +115,33 @@ __device__ __forceinline__ f2 dot2(const S2& a, const S2& b)
     return fma2(a.E, b.E, fma2(a.mz, b.mz, fma2(a.mx, b.mx, mul2(a.r, b.r))));
 }
 
-// TVD coefficient per column: C = min(Co,1/2)(1 - min(Co,1/2)), phi = clamp(2 s/dd, 0, 1)
-// (dd = 0 gives 0/0 = NaN, which the clamp maps to 0; the flux G dX is 0 there anyway)
-__device__ __forceinline__ float tvd_G1(float sp, float sm, float dd, float Co, int form)
-{
-    const float co = fminf(Co, 0.5f);
-    const float Cc = co * (1.f - co);
-    if (form == 0) {
-        const float pp = fminf(fmaxf(__fdividef(sp + sp, dd), 0.f), 1.f);
-        const float pm = fminf(fmaxf(__fdividef(sm + sm, dd), 0.f), 1.f);
-        return 0.5f * Cc * ((1.f - pp) + (1.f - pm));
-    }
-    if (form == 1) {
-        const float s = sp + sm;
-        return 0.5f * Cc * (1.f - fminf(fmaxf(__fdividef(s + s, dd), 0.f), 1.f));
-    }
-    return 0.f;
-}
+// TVD coefficient G of the flux G dX, both columns at once:
+//   C = c(1 - c), c = min(Co, 1/2);  phi(s) = clamp(2 s / dd, 0, 1)
+//   Davis form: G = C (2 - phi(sp) - phi(sm)) / 2;  printed form: C (1 - phi(sp + sm)) / 2
+// One reciprocal of dd serves both ratios.  dd = 0 (dX = 0) gives 0 * inf =
+// NaN, which the clamp maps to 0; the flux G dX is 0 there anyway.
+__device__ __forceinline__ float clamp01(float x) { return fminf(fmaxf(x, 0.f), 1.f); }
 
 __device__ __forceinline__ f2 tvd_G2(f2 sp, f2 sm, f2 dd, f2 Co, int form)
 {
-    return make_float2(tvd_G1(sp.x, sm.x, dd.x, Co.x, form), tvd_G1(sp.y, sm.y, dd.y, Co.y, form));
+    const f2 c = make_float2(fminf(Co.x, 0.5f), fminf(Co.y, 0.5f));
+    const f2 hC = mul2(make_float2(0.5f, 0.5f), fma2(make_float2(-c.x, -c.y), c, c));  // C/2
+    const f2 r2 = mul2(make_float2(2.f, 2.f), rcp2(dd));
+    if (form == 0) {
+        const f2 a = mul2(sp, r2), b = mul2(sm, r2);
+        const f2 phis = make_float2(clamp01(a.x) + clamp01(b.x), clamp01(a.y) + clamp01(b.y));
+        return mul2(hC, sub2(make_float2(2.f, 2.f), phis));
+    }
+    if (form == 1) {
+        const f2 a = mul2(add2(sp, sm), r2);
+        return mul2(hC, sub2(make_float2(1.f, 1.f), make_float2(clamp01(a.x), clamp01(a.y))));
+    }
+    return make_float2(0.f, 0.f);
 }
 
 __device__ __forceinline__ f2 abs2(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
-__device__ __forceinline__ f2 sqrt2(f2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ f2 sqrt2(f2 a) { return make_float2(sqrt_fast(a.x), sqrt_fast(a.y)); }
 __device__ __forceinline__ S2 scale2(f2 g, const S2& d) { return {mul2(g, d.r), mul2(g, d.mx), mul2(g, d.mz), mul2(g, d.E)}; }
 __device__ __forceinline__ S2 diff2(const S2& a, const S2& b) { return {sub2(a.r, b.r), sub2(a.mx, b.mx), sub2(a.mz, b.mz), sub2(a.E, b.E)}; }
 
@@ -153,23 +169,33 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_ring() { asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory"); }
 __device__ __forceinline__ void cp_async_drain() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+constexpr int kThreads2 = kWarpsPerBlock * 32;  // block size of the packed kernels
+
+// per-thread ring [kRing slots][4 fields][kThreads2] of float2 in shared
+// memory; the field stride is a compile-time constant
 struct RowRing {
-    f2* base;  // [kRing][4 fields][blockDim.x]
-    int nthreads;
-    __device__ __forceinline__ f2* at(int slot, int f) const { return base + (slot * 4 + f) * nthreads + threadIdx.x; }
-    __device__ __forceinline__ void request(int slot, const float* __restrict__ g, int fs, int off) const
+    f2* mine;  // this thread's element of slot 0, field 0
+    __device__ __forceinline__ f2* at(int slot, int f) const { return mine + (slot * 4 + f) * kThreads2; }
+    __device__ __forceinline__ void request(int slot, const float* __restrict__ g, int fs) const
     {
-        cp_async8(at(slot, 0), g + off);
-        cp_async8(at(slot, 1), g + off + fs);
-        cp_async8(at(slot, 2), g + off + 2 * fs);
-        cp_async8(at(slot, 3), g + off + 3 * fs);
+        f2* d = mine + slot * 4 * kThreads2;
+        cp_async8(d, g);
+        cp_async8(d + kThreads2, g + fs);
+        cp_async8(d + 2 * kThreads2, g + 2 * fs);
+        cp_async8(d + 3 * kThreads2, g + 3 * fs);
         cp_async_commit();
     }
     __device__ __forceinline__ S2 take(int slot) const
     {
-        return {*at(slot, 0), *at(slot, 1), *at(slot, 2), *at(slot, 3)};
+        const f2* d = mine + slot * 4 * kThreads2;
+        return {d[0], d[kThreads2], d[2 * kThreads2], d[3 * kThreads2]};
     }
 };
+
+// A segment is "interior" when none of its pipeline rows (ks-5 .. ke+4,
+// prefetch included) touches a plate or leaves the grid: its steps need no
+// plate rules, no row clamping and no range tests.
+__device__ __forceinline__ bool interior_segment(int ks, int ke, int nz) { return ks >= 5 && ke <= nz - 5; }
 
 // L_z(Delta), FP32, two columns per lane.  Row pipeline at step j (row j
 // just taken from the ring):
@@ -178,7 +204,7 @@ struct RowRing {
 //   H_{j-1} = (X^P + X + Delta S^P + lambda F^P)_{j-1} / 2 - D,
 // which is the average (X^P + X^C)/2 plus the TVD term of Sec. 3.1 with the
 // corrector split into its two rows.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+__global__ void __launch_bounds__(kThreads2, 4)
 sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 {
     extern __shared__ f2 ring_mem[];
@@ -208,37 +234,43 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
     }
     if (ks >= nz) return;  // warp-uniform; no block barrier in this kernel
 
-    const RowRing ring{ring_mem, (int)blockDim.x};
+    const RowRing ring{ring_mem + threadIdx.x};
     auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
     auto gz_of = [&](int j) { return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz)); };
-
     const int j0 = ks - 2;
-    for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in, fs, row_off(j0 + q));
+    for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in + row_off(j0 + q), fs);
 
     const f2 z0 = bc(0.f);
-    S2 Xm1;                 // X_{j-1}
-    f2 ux1, uz1, T1, p1;    // primitives of X_{j-1}
-    f2 A1 = z0, A2 = z0;    // |u_z| + c of rows j-1, j-2
+    S2 Xm1 = ld2(io.in, fs, row_off(j0 - 1));  // X_{j-1} (primed with row j0-1)
+    f2 ux1, uz1, T1, p1;                       // primitives of X_{j-1}
+    f2 gz1 = gz_of(j0 - 1);                    // -g z of row j-1
+    prims2(Xm1, gz1, C, ux1, uz1, T1, p1);
+    f2 A1 = z0, A2 = z0;                       // |u_z| + c of rows j-1, j-2
     S2 F2 = {z0, z0, z0, z0};
-    f2 ppux2 = z0, ppuz2 = z0, ppT2 = z0;  // primitives of X^P_{j-2}
-    S2 H = {z0, z0, z0, z0};               // H_{j-2}
+    f2 ppux2 = ux1, ppuz2 = uz1, ppT2 = T1;    // primitives of X^P_{j-2}
+    S2 H = {z0, z0, z0, z0};                   // H_{j-2}
     S2 d1 = {z0, z0, z0, z0};
     f2 dd1 = z0, ss2 = z0;
-    {
-        // prime the previous row with the first one so nothing is undefined
-        Xm1 = ld2(io.in, fs, row_off(j0 - 1));
-        prims2(Xm1, gz_of(j0 - 1), C, ux1, uz1, T1, p1);
-        ppux2 = ux1; ppuz2 = uz1; ppT2 = T1;
-    }
+    const float* gnext = io.in + row_off(j0 + kRing - 1);  // next row to request (interior path)
+    float* gout = io.out + (long long)(j0 - 2) * pitch + i;  // output row of the current step (used only when it exists)
 
-    for (int j = j0; j <= ke + 1; ++j) {
+    // one step of the pipeline; EDGE: plate rules and range tests; STORE: the step has an output row
+    auto row_step = [&](const int j, auto edge_tag, auto store_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        constexpr bool STORE = decltype(store_tag)::value;
         const int t = j - j0;
-        ring.request((t + kRing - 1) % kRing, io.in, fs, row_off(j + kRing - 1));
+        if (EDGE) {
+            ring.request((t + kRing - 1) % kRing, io.in + row_off(j + kRing - 1), fs);
+        } else {
+            ring.request((t + kRing - 1) % kRing, gnext, fs);
+            gnext += pitch;
+        }
         cp_async_wait_ring();
         const S2 X0 = ring.take(t % kRing);
+        const f2 gz0 = EDGE ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
 
         f2 ux0, uz0, T0, p0;
-        prims2(X0, gz_of(j), C, ux0, uz0, T0, p0);
+        prims2(X0, gz0, C, ux0, uz0, T0, p0);
         const f2 A0 = add2(abs2(uz0), sqrt2(mul2(bc(C.cs2), T0)));
 
         // row m = j-1: F^n (forward z, central x), X^P, F^P (backward z)
@@ -248,7 +280,7 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         const S2 F1 = flux_z2(Xm1, ux1, uz1, p1, mul2(sub2(ux0, ux1), idz), mul2(sub2(uz0, uz1), idz),
                               mul2(sub2(T0, T1), idz), dxux1, dxuz1, C);
         S2 XP1;
-        const bool interior_m = (m >= 1 && m <= nz - 2);
+        const bool interior_m = !EDGE || (m >= 1 && m <= nz - 2);
         if (interior_m) {
             XP1.r = fnma2(lam, sub2(F1.r, F2.r), Xm1.r);
             XP1.mx = fnma2(lam, sub2(F1.mx, F2.mx), Xm1.mx);
@@ -264,7 +296,7 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
             XP1.E = mul2(XP1.r, bc(C.etop));
         }
         f2 ppux1, ppuz1, ppT1, ppp1;
-        prims2(XP1, gz_of(m), C, ppux1, ppuz1, ppT1, ppp1);
+        prims2(XP1, gz1, C, ppux1, ppuz1, ppT1, ppp1);
         const f2 dxppux1 = mul2(sub2(right_of(ppux1), left_of(ppux1)), i2dx);
         const f2 dxppuz1 = mul2(sub2(right_of(ppuz1), left_of(ppuz1)), i2dx);
         const S2 FP1 = flux_z2(XP1, ppux1, ppuz1, ppp1, mul2(sub2(ppux1, ppux2), idz), mul2(sub2(ppuz1, ppuz2), idz),
@@ -276,12 +308,13 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         const f2 ss1 = dot2(d1, d0);
         const int c = j - 2;
         S2 Dn = {z0, z0, z0, z0};
-        if (c >= 1 && c <= nz - 3) Dn = scale2(tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form), d1);
+        if (!EDGE || (c >= 1 && c <= nz - 3))
+            Dn = scale2(tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form), d1);
 
         // output row c = j-2
-        if (c >= ks && c < ke) {
+        if (STORE) {
             S2 Xn;
-            if (c >= 1 && c <= nz - 2) {
+            if (!EDGE || (c >= 1 && c <= nz - 2)) {
                 Xn.r = add2(fnma2(hlam, FP1.r, H.r), Dn.r);
                 Xn.mx = add2(fnma2(hlam, FP1.mx, H.mx), Dn.mx);
                 Xn.mz = add2(fnma2(hlam, FP1.mz, H.mz), Dn.mz);
@@ -292,8 +325,9 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
                 Xn.mx = z0; Xn.mz = z0;
                 Xn.E = mul2(Xn.r, bc(c == 0 ? C.ebot : C.etop));
             }
-            if (own) st2(io.out, fs, c * pitch + i, Xn);
+            if (own) st2(gout, fs, 0, Xn);
         }
+        gout += pitch;
 
         // H of row m for the next step
         if (interior_m) {
@@ -308,10 +342,29 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 
         Xm1 = X0;
         ux1 = ux0; uz1 = uz0; T1 = T0; p1 = p0;
+        gz1 = gz0;
         A2 = A1; A1 = A0;
         F2 = F1;
         ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1;
         d1 = d0; dd1 = dd0; ss2 = ss1;
+    };
+
+    const std::true_type yes;
+    const std::false_type no;
+    if (interior_segment(ks, ke, nz)) {
+        for (int j = j0; j < ks + 2; ++j) row_step(j, no, no);  // pipeline ramp: no output yet
+        // two steps per trip, so the pipeline registers swap roles instead of being copied
+        int j = ks + 2;
+        for (; j + 1 <= ke + 1; j += 2) {
+            row_step(j, no, yes);
+            row_step(j + 1, no, yes);
+        }
+        if (j <= ke + 1) row_step(j, no, yes);
+    } else {
+        for (int j = j0; j <= ke + 1; ++j) {
+            if (j - 2 >= ks && j - 2 < ke) row_step(j, yes, yes);
+            else row_step(j, yes, no);
+        }
     }
     cp_async_drain();  // rows requested past the segment end
 }
@@ -322,7 +375,7 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 // K_m = (X^P + X)_m/2 + D_{i+1/2} - D_{i-1/2}; then for row c = j-2, F^P
 // (backward x, central z from X^P rows j-1 and j-3) and
 // X_new_c = K_c - (lambda/2)(F^P_{i+1} - F^P_i).
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+__global__ void __launch_bounds__(kThreads2, 4)
 sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 {
     extern __shared__ f2 ring_mem[];
@@ -353,35 +406,47 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
     float rmax = 0.f;
     int bad = 0;
     if (ks < nz) {
-        const RowRing ring{ring_mem, (int)blockDim.x};
+        const RowRing ring{ring_mem + threadIdx.x};
         auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
         auto gz_of = [&](int j) { return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz)); };
         const f2 idx_ = bc(C.inv_dx), i2dz = bc(C.inv_2dz);
         const f2 z0 = bc(0.f);
 
         const int j0 = ks - 2;
-        for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in, fs, row_off(j0 + q));
+        for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in + row_off(j0 + q), fs);
 
         S2 Xm1 = ld2(io.in, fs, row_off(j0 - 1));
+        f2 gz1 = gz_of(j0 - 1);
         f2 ux1, uz1, T1, p1;
-        prims2(Xm1, gz_of(j0 - 1), C, ux1, uz1, T1, p1);
+        prims2(Xm1, gz1, C, ux1, uz1, T1, p1);
         f2 ux2 = ux1, uz2 = uz1;
         S2 XP2 = Xm1, K2 = Xm1;
         f2 ppux2 = ux1, ppuz2 = uz1, ppT2 = T1, ppp2 = p1;
         f2 ppux3 = ux1, ppuz3 = uz1;
+        f2 gz2 = gz1;  // -g z of row j-2
+        const float* gnext = io.in + row_off(j0 + kRing - 1);
+        float* gout = io.out + (long long)(j0 - 2) * pitch + i;  // used only when the row exists
 
-        for (int j = j0; j <= ke + 1; ++j) {
+        auto row_step = [&](const int j, auto edge_tag, auto store_tag) {
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            constexpr bool STORE = decltype(store_tag)::value;
             const int t = j - j0;
-            ring.request((t + kRing - 1) % kRing, io.in, fs, row_off(j + kRing - 1));
+            if (EDGE) {
+                ring.request((t + kRing - 1) % kRing, io.in + row_off(j + kRing - 1), fs);
+            } else {
+                ring.request((t + kRing - 1) % kRing, gnext, fs);
+                gnext += pitch;
+            }
             cp_async_wait_ring();
             const S2 X0 = ring.take(t % kRing);
+            const f2 gz0 = EDGE ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
             f2 ux0, uz0, T0, p0;
-            prims2(X0, gz_of(j), C, ux0, uz0, T0, p0);
+            prims2(X0, gz0, C, ux0, uz0, T0, p0);
 
             // row m = j-1
             const int m = j - 1;
             S2 XP1 = Xm1, K1 = Xm1;  // plate rows pass through
-            if (m >= 1 && m <= nz - 2) {
+            if (!EDGE || (m >= 1 && m <= nz - 2)) {
                 const S2 F1 = flux_x2(Xm1, ux1, uz1, p1, mul2(sub2(right_of(ux1), ux1), idx_),
                                       mul2(sub2(right_of(uz1), uz1), idx_), mul2(sub2(right_of(T1), T1), idx_),
                                       mul2(sub2(ux0, ux2), i2dz), mul2(sub2(uz0, uz2), i2dz), C);
@@ -404,13 +469,13 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
                 K1.E = fma2(half, add2(XP1.E, Xm1.E), sub2(Dn.E, Dl.E));
             }
             f2 ppux1, ppuz1, ppT1, ppp1;
-            prims2(XP1, gz_of(m), C, ppux1, ppuz1, ppT1, ppp1);
+            prims2(XP1, gz1, C, ppux1, ppuz1, ppT1, ppp1);
 
             // row c = j-2: F^P (backward x, central z) and the corrector
-            const int c = j - 2;
-            if (c >= ks && c < ke) {
+            if (STORE) {
+                const int c = j - 2;
                 S2 Xn = K2;
-                if (c >= 1 && c <= nz - 2) {
+                if (!EDGE || (c >= 1 && c <= nz - 2)) {
                     const S2 FP = flux_x2(XP2, ppux2, ppuz2, ppp2, mul2(sub2(ppux2, left_of(ppux2)), idx_),
                                           mul2(sub2(ppuz2, left_of(ppuz2)), idx_), mul2(sub2(ppT2, left_of(ppT2)), idx_),
                                           mul2(sub2(ppux1, ppux3), i2dz), mul2(sub2(ppuz1, ppuz3), i2dz), C);
@@ -421,10 +486,10 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
                     Xn.E = fnma2(hlam, sub2(FPr.E, FP.E), K2.E);
                 }
                 if (own) {
-                    st2(io.out, fs, c * pitch + i, Xn);
+                    st2(gout, fs, 0, Xn);
                     if (sc.last) {
                         f2 ux, uz, T, p;
-                        prims2(Xn, gz_of(c), C, ux, uz, T, p);
+                        prims2(Xn, gz2, C, ux, uz, T, p);
                         const f2 cs = sqrt2(mul2(bc(C.cs2), T));
                         const f2 rx = mul2(add2(abs2(ux), cs), idx_);
                         const f2 rz = mul2(add2(abs2(uz), cs), bc(C.inv_dz));
@@ -434,13 +499,32 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
                     }
                 }
             }
+            gout += pitch;
 
             Xm1 = X0;
             ux2 = ux1; uz2 = uz1;
             ux1 = ux0; uz1 = uz0; T1 = T0; p1 = p0;
+            gz2 = gz1; gz1 = gz0;
             ppux3 = ppux2; ppuz3 = ppuz2;
             XP2 = XP1; K2 = K1;
             ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
+        };
+
+        const std::true_type yes;
+        const std::false_type no;
+        if (interior_segment(ks, ke, nz)) {
+            for (int j = j0; j < ks + 2; ++j) row_step(j, no, no);
+            int j = ks + 2;
+            for (; j + 1 <= ke + 1; j += 2) {
+                row_step(j, no, yes);
+                row_step(j + 1, no, yes);
+            }
+            if (j <= ke + 1) row_step(j, no, yes);
+        } else {
+            for (int j = j0; j <= ke + 1; ++j) {
+                if (j - 2 >= ks && j - 2 < ke) row_step(j, yes, yes);
+                else row_step(j, yes, no);
+            }
         }
         cp_async_drain();  // rows requested past the segment end
     }
@@ -448,6 +532,6 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 }
 
 // shared memory of the row ring for a block
-constexpr size_t kRingBytes = (size_t)kRing * 4 * kWarpsPerBlock * 32 * sizeof(f2);
+constexpr size_t kRingBytes = (size_t)kRing * 4 * kThreads2 * sizeof(f2);
 
 }  // namespace cm
