@@ -181,6 +181,36 @@ def run_gpu(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     s.close()
 
+    # ---- batched ensemble: 64 independent boxes, N_z = round(32 * 8^u), N_x = 4 N_z,
+    # Ra = 10^(5 + 4 u'), u, u' uniform in [0, 1) from a seeded generator ----
+    batch = None
+    if not args.no_batch:
+        import numpy as np
+        rng = np.random.default_rng(2024 + rank)
+        u, u2 = rng.random(64), rng.random(64)
+        nzs = [int(round(32 * 8 ** x)) for x in u]
+        grids = [cm.cm_grid(2, 4 * nz, 1, nz, 4.0) for nz in nzs]
+        ras = [10 ** (5 + 4 * x) for x in u2]
+        p = cm.cm_default_params()
+        p.precision = cm.CM_FP32
+        p.stream = stream.cuda_stream
+        cm.cm_batch_init(grids, ras, PR, GAMMA, p)
+        cm.cm_batch_step(50)
+        barrier()
+        l0 = cm.cm_batch_launch_count()
+        kb = args.batch_steps
+        ms = max_over_ranks(cm.cm_batch_profile_steps(kb, FLUSH_BYTES))
+        nl = cm.cm_batch_launch_count() - l0
+        cells_b = sum(4 * nz * nz for nz in nzs)
+        seg_z, seg_x = cm.cm_batch_tuning()
+        diags = cm.cm_batch_diagnostics()
+        cm.cm_batch_finalize()
+        batch = {"value": world * cells_b * kb / (ms * 1e-3), "unit": UNIT, "steps": kb, "boxes": 64,
+                 "cells": cells_b, "ms_per_step": ms / kb, "gpu_launches": nl,
+                 "all_finite": all(d["status"] == 0 for d in diags),
+                 "segments_z": sorted(set(seg_z)), "segments_x": sorted(set(seg_x)),
+                 "l2": "flushed once before the timed steps (the steps replay captured 50-step graphs)"}
+
     # ---- FP64 state, same workload ----
     k64 = max(3, min(args.steps, 20))
     s64, r64 = measure("fp64", k64, min(args.warmup, 3), clocks=False)
@@ -214,6 +244,7 @@ def run_gpu(args):
         "clocks": r32["clocks"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * cells * 8,
                 "d2h_bytes_per_step": 128, "steps": n_e2e},
+        "batch": batch,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": r64["total_ms"] / k64, "steps": k64,
                  "sweep_ms": [round(x, 5) for x in r64["sweep_ms"]], "gpu_launches": r64["launches"],
                  "roofline_hbm": roofline(r64)},
@@ -279,6 +310,8 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--nx", type=int, default=NX, help="grid override (profiling captures only)")
     ap.add_argument("--nz", type=int, default=NZ, help="grid override (profiling captures only)")
     ap.add_argument("--only-fp32", action="store_true", help="time the FP32 steps only (profiling captures)")

@@ -191,6 +191,44 @@ int cm_sync(void);
 int cm_save(const char* path);
 int cm_load(const char* path);
 
+/* ---- Batched ensemble: many independent 2D boxes advanced together ----
+ * Each box is the problem of cm_init (Sec. 2 equations, Sec. 3.1 scheme) with
+ * its own grid, Ra, dt (per-box device control block), time and seed
+ * (params->seed + box index).  FP32 state with FP64 dt and reductions.  One
+ * kernel launch per sweep covers every box (warp work items of box, column
+ * strip, row segment); the segment length of each box size class is chosen
+ * at init by timing the batched sweeps (autotuner); runs of 50 steps are
+ * replayed from a captured CUDA graph.  A separate context from cm_init's. */
+
+/* nbox >= 1; grids, Ra: host arrays of nbox (2D grids, even nx); params:
+ * host (precision must be CM_FP32; stream NULL = a stream the batch creates,
+ * otherwise a stream that can be captured).  Blocking. */
+int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, double gamma, const cm_params* params);
+
+/* Queue n steps of every box (asynchronous). */
+int cm_batch_step(int n);
+
+/* One diagnostics sample of every box now (Sec. 2 definitions); out: host,
+ * nbox records.  Blocking.  CM_ENAN if a box met a non-finite value. */
+int cm_batch_diagnostics(cm_diag* out);
+
+/* Dense float64 state of one box (layout of cm_get_state); host out.  Blocking. */
+int cm_batch_get_state(int box, double* host);
+
+/* Segment lengths the autotuner chose per box for the z and x sweeps (host
+ * arrays of nbox; either may be NULL). */
+int cm_batch_tuning(int* seg_z, int* seg_x);
+
+/* Measurement: L2 flush of flush_bytes (0 = none), then n steps bracketed by
+ * CUDA events on the batch stream; *total_ms (host) = their device time. */
+int cm_batch_profile_steps(int n, unsigned long long flush_bytes, double* total_ms);
+
+/* Kernel launches the batch has queued since cm_batch_init. */
+long long cm_batch_launch_count(void);
+
+/* Free the batch context. */
+int cm_batch_finalize(void);
+
 /* Diagnostics of a caller's state with no allocation at all (the paper has
  * no counterpart; this is for callers that must not allocate device memory,
  * e.g. an in-situ analysis hook called from another application's time loop,

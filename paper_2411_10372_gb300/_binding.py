@@ -78,6 +78,15 @@ _SIGS = {
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(cm_params),
                                        ctypes.c_double, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p,
                                        ctypes.POINTER(cm_diag)]),
+    "cm_batch_init": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(cm_grid), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.c_double, ctypes.c_double, ctypes.POINTER(cm_params)]),
+    "cm_batch_step": (ctypes.c_int, [ctypes.c_int]),
+    "cm_batch_diagnostics": (ctypes.c_int, [ctypes.POINTER(cm_diag)]),
+    "cm_batch_get_state": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
+    "cm_batch_tuning": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "cm_batch_profile_steps": (ctypes.c_int, [ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]),
+    "cm_batch_launch_count": (ctypes.c_longlong, []),
+    "cm_batch_finalize": (ctypes.c_int, []),
     "cm_finalize": (ctypes.c_int, []),
     "cm_last_error": (ctypes.c_char_p, []),
 }
@@ -226,6 +235,54 @@ def cm_diag_noalloc(state_ptr: int, precision: int, grid: cm_grid, pitch: int, R
                                  float(Ra), float(Pr), float(gamma), ctypes.byref(params), float(t), float(dt),
                                  int(step), ctypes.c_void_p(stream) if stream else None, ctypes.byref(d)))
     return d.as_dict()
+
+
+_batch_n = 0
+
+
+def cm_batch_init(grids: list, Ra: list, Pr: float, gamma: float, params: cm_params | None = None):
+    global _batch_n
+    n = len(grids)
+    g = (cm_grid * n)(*grids)
+    ra = (ctypes.c_double * n)(*[float(r) for r in Ra])
+    _check(lib().cm_batch_init(n, g, ra, Pr, gamma, ctypes.byref(params) if params is not None else None))
+    _batch_n = n
+
+
+def cm_batch_step(n: int):
+    _check(lib().cm_batch_step(int(n)))
+
+
+def cm_batch_diagnostics() -> list[dict]:
+    out = (cm_diag * max(_batch_n, 1))()
+    _check(lib().cm_batch_diagnostics(out))
+    return [out[i].as_dict() for i in range(_batch_n)]
+
+
+def cm_batch_get_state(box: int, out: np.ndarray) -> np.ndarray:
+    _check(lib().cm_batch_get_state(int(box), _dp(out)))
+    return out
+
+
+def cm_batch_tuning() -> tuple[list[int], list[int]]:
+    z = (ctypes.c_int * max(_batch_n, 1))()
+    x = (ctypes.c_int * max(_batch_n, 1))()
+    _check(lib().cm_batch_tuning(z, x))
+    return list(z)[:_batch_n], list(x)[:_batch_n]
+
+
+def cm_batch_profile_steps(n: int, flush_bytes: int = 0) -> float:
+    ms = ctypes.c_double()
+    _check(lib().cm_batch_profile_steps(int(n), int(flush_bytes), ctypes.byref(ms)))
+    return ms.value
+
+
+def cm_batch_launch_count() -> int:
+    return int(lib().cm_batch_launch_count())
+
+
+def cm_batch_finalize():
+    _check(lib().cm_batch_finalize())
 
 
 def cm_finalize():

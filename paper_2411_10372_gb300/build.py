@@ -22,6 +22,7 @@ UNITS = {
     # host arithmetic (the conduction profile) rounds as written: no FMA
     "cm_api.cu": ["-Xcompiler", "-ffp-contract=off"],
     "diag_noalloc.cu": ["-Xcompiler", "-ffp-contract=off"],
+    "batch.cu": ["-Xcompiler", "-ffp-contract=off"],
     "kernels_f64.cu": ["--fmad=false"],
     # FP32: FMA contraction, approximate division and square root
     "kernels_f32.cu": ["--fmad=true", "-prec-div=false", "-prec-sqrt=false"],

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/cm.h"
+#include "host_setup.h"
 #include "kernels.h"
 
 using namespace cm;
@@ -74,42 +75,8 @@ int fail(int code, const char* fmt, ...)
 template <class R>
 void fill_coef(Coef<R>& C, const Ctx& c)
 {
-    const cm_grid& G = c.grid;
-    const cm_params& P = c.prm;
-    double dx = G.aspect / G.nx, dy = G.aspect / c.ny, dz = 1.0 / (G.nz - 1);
-    C.a = (R)c.a;
-    C.b = (R)c.b;
-    C.g = (R)c.g;
-    C.mu = (R)std::sqrt(c.Pr / c.Ra);
-    C.kth = (R)(1.0 / (P.eps * P.D * std::sqrt(c.Ra * c.Pr)));
-    C.cs2 = (R)c.cs2;
-    C.stokes = (R)P.stokes;
-    C.inv_dx = (R)(1.0 / dx);
-    C.inv_dy = (R)(1.0 / dy);
-    C.inv_dz = (R)(1.0 / dz);
-    C.inv_2dx = (R)(1.0 / (2.0 * dx));
-    C.inv_2dy = (R)(1.0 / (2.0 * dy));
-    C.inv_2dz = (R)(1.0 / (2.0 * dz));
-    C.hx = (R)dx;
-    C.hy = (R)dy;
-    C.hz = (R)dz;
-    C.h2x = (R)(2.0 * dx);
-    C.h2y = (R)(2.0 * dy);
-    C.h2z = (R)(2.0 * dz);
-    C.ebot = (R)(P.t_bot / c.b + c.g * 0.0);
-    C.etop = (R)(P.t_top / c.b + c.g * 1.0);
-    C.dx = dx;
-    C.dy = dy;
-    C.dz = dz;
-    C.cfl = P.cfl;
-    C.dt_fixed = P.dt_fixed;
-    C.nx = G.nx;
-    C.ny = c.ny;
-    C.nz = G.nz;
-    C.pitch = c.pitch;
-    C.fstride = c.fstride;
-    C.tvd_form = P.tvd_form;
-    C.ndim = G.ndim;
+    Closure K(c.gamma, c.prm);
+    cm::fill_coef(C, c.grid, c.ny, c.pitch, c.fstride, c.Ra, c.Pr, K, c.prm);
 }
 
 void free_ctx(Ctx* c)
@@ -139,11 +106,6 @@ int check_grid(const cm_grid* G)
     return CM_OK;
 }
 
-int pitch_of(int nx, int prec)
-{
-    const int align = prec == CM_FP64 ? 32 : 64;  // 256-byte rows
-    return (nx + align - 1) / align * align;
-}
 
 // queue one sweep on the current buffer and swap buffers
 int sweep(Ctx* c, int dir, const SweepCtl& sc)
@@ -411,17 +373,11 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     }
 
     // conduction / hydrostatic profile of constant K, FP64 on the host (nz values)
-    std::vector<double> z(nz), Tc(nz), pc(nz), rhoc(nz);
-    const double Lam = P.t_bot - P.t_top;
-    double rho_min = 1e300;
-    for (int k = 0; k < nz; ++k) {
-        z[k] = (double)k / (double)(nz - 1);
-        Tc[k] = P.t_bot - Lam * z[k];
-        if (Lam != 0.0) pc[k] = c->a * P.t_bot * std::pow(Tc[k] / P.t_bot, c->g / (c->a * Lam));
-        else pc[k] = c->a * P.t_bot * std::exp(-c->g * z[k] / (c->a * P.t_bot));
-        rhoc[k] = pc[k] / (c->a * Tc[k]);
-        rho_min = std::fmin(rho_min, rhoc[k]);
-    }
+    const Profile prof(nz, P, Closure(gamma, P));
+    const std::vector<double>& z = prof.z;
+    const std::vector<double>& Tc = prof.Tc;
+    const std::vector<double>& pc = prof.pc;
+    const double rho_min = prof.rho_min;
     std::vector<float> zf(nz);
     for (int k = 0; k < nz; ++k) zf[k] = (float)z[k];
     cudaStream_t s = c->stream;
@@ -731,7 +687,14 @@ const char* cm_last_error(void) { return g_err; }
 
 }  // extern "C"
 
-// error reporting for the other translation units of the library
+// shared with the other translation units of the library
 namespace cm {
+int pitch_of(int nx, int prec)
+{
+    const int align = prec == CM_FP64 ? 32 : 64;  // 256-byte rows
+    return (nx + align - 1) / align * align;
+}
+
+
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 }  // namespace cm

@@ -25,6 +25,10 @@ struct Launch {
 cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
                             const SweepCtl& sc, cudaStream_t s);
 
+// one batched sweep over every box of a batch (kernels_f32.cu); nblocks from the work list
+struct BatchLaunch;
+cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, cudaStream_t s);
+
 cudaError_t launch_diag_final(const double* scratch, const double* zt, const DiagFinal& F, DevCtl* ctl, cm_diag* rec,
                               cudaStream_t s);
 

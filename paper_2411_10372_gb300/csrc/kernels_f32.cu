@@ -32,4 +32,18 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     return cudaGetLastError();
 }
 
+cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, cudaStream_t s)
+{
+    static bool init = false;
+    if (!init) {
+        cudaFuncSetAttribute(sweep_z2d_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        cudaFuncSetAttribute(sweep_x2d_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        init = true;
+    }
+    if (dir == 2) sweep_z2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+    else if (dir == 0) sweep_x2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 }  // namespace cm

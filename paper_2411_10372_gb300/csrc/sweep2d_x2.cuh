@@ -11,10 +11,10 @@
 // Loads and stores are 8-byte vectors (the strip origin is even).
 #pragma once
 #include "cm_device.cuh"
+#include "sweep2d_x2_types.h"
 
 namespace cm {
 
-constexpr int kOutW2 = 60;  // output columns per warp strip
 
 typedef float2 f2;
 
@@ -204,17 +204,20 @@ __device__ __forceinline__ bool interior_segment(int ks, int ke, int nz) { retur
 //   H_{j-1} = (X^P + X + Delta S^P + lambda F^P)_{j-1} / 2 - D,
 // which is the average (X^P + X^C)/2 plus the TVD term of Sec. 3.1 with the
 // corrector split into its two rows.
-__global__ void __launch_bounds__(kThreads2, 4)
-sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
+// one warp's segment of the z sweep: columns of strip `strip`, output rows
+// [ks, ks + seg_rows); `lead` marks the one thread block that does the
+// per-step bookkeeping of a first sweep
+__device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __restrict__ out, const Coef<float>& C,
+                                        const SweepCtl& sc, int strip, int ks, int seg_rows, bool lead)
 {
     extern __shared__ f2 ring_mem[];
+    SweepIO2 io;
+    io.in = in;
+    io.out = out;
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int strip = gw % io.nstrips;
-    const int ks = (gw / io.nstrips) * io.seg_rows;
     const int nz = C.nz, nx = C.nx, pitch = C.pitch;
     const int fs = (int)C.fstride;
-    const int ke = min(ks + io.seg_rows, nz);
+    const int ke = min(ks + seg_rows, nz);
     const int i = strip * kOutW2 - 2 + 2 * lane;  // first of the lane's two columns (even)
     int ic = i % nx;
     if (ic < 0) ic += nx;
@@ -227,12 +230,12 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
     const f2 mDg = bc(-(float)Delta * C.g);  // Delta * (source per unit density)
     const f2 half = bc(0.5f), idz = bc(C.inv_dz), i2dx = bc(C.inv_2dx);
 
-    if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (sc.first && lead && threadIdx.x == 0) {
         sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
         sc.ctl->t += dt;
         sc.ctl->steps += 1.0;
     }
-    if (ks >= nz) return;  // warp-uniform; no block barrier in this kernel
+    if (ks >= nz) return;  // warp-uniform; no block barrier in this sweep
 
     const RowRing ring{ring_mem + threadIdx.x};
     auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
@@ -254,12 +257,12 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
     const float* gnext = io.in + row_off(j0 + kRing - 1);  // next row to request (interior path)
     float* gout = io.out + (long long)(j0 - 2) * pitch + i;  // output row of the current step (used only when it exists)
 
-    // one step of the pipeline; EDGE: plate rules and range tests; STORE: the step has an output row
+    // one step of the pipeline; edge: plate rules and range tests; STORE: the step has an output row
     auto row_step = [&](const int j, auto edge_tag, auto store_tag) {
-        constexpr bool EDGE = decltype(edge_tag)::value;
-        constexpr bool STORE = decltype(store_tag)::value;
+        constexpr bool edge = decltype(edge_tag)::value;
+        constexpr bool store = decltype(store_tag)::value;
         const int t = j - j0;
-        if (EDGE) {
+        if (edge) {
             ring.request((t + kRing - 1) % kRing, io.in + row_off(j + kRing - 1), fs);
         } else {
             ring.request((t + kRing - 1) % kRing, gnext, fs);
@@ -267,7 +270,7 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         }
         cp_async_wait_ring();
         const S2 X0 = ring.take(t % kRing);
-        const f2 gz0 = EDGE ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
+        const f2 gz0 = edge ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
 
         f2 ux0, uz0, T0, p0;
         prims2(X0, gz0, C, ux0, uz0, T0, p0);
@@ -280,7 +283,7 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         const S2 F1 = flux_z2(Xm1, ux1, uz1, p1, mul2(sub2(ux0, ux1), idz), mul2(sub2(uz0, uz1), idz),
                               mul2(sub2(T0, T1), idz), dxux1, dxuz1, C);
         S2 XP1;
-        const bool interior_m = !EDGE || (m >= 1 && m <= nz - 2);
+        const bool interior_m = !edge || (m >= 1 && m <= nz - 2);
         if (interior_m) {
             XP1.r = fnma2(lam, sub2(F1.r, F2.r), Xm1.r);
             XP1.mx = fnma2(lam, sub2(F1.mx, F2.mx), Xm1.mx);
@@ -308,13 +311,13 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         const f2 ss1 = dot2(d1, d0);
         const int c = j - 2;
         S2 Dn = {z0, z0, z0, z0};
-        if (!EDGE || (c >= 1 && c <= nz - 3))
+        if (!edge || (c >= 1 && c <= nz - 3))
             Dn = scale2(tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form), d1);
 
         // output row c = j-2
-        if (STORE) {
+        if (store) {
             S2 Xn;
-            if (!EDGE || (c >= 1 && c <= nz - 2)) {
+            if (!edge || (c >= 1 && c <= nz - 2)) {
                 Xn.r = add2(fnma2(hlam, FP1.r, H.r), Dn.r);
                 Xn.mx = add2(fnma2(hlam, FP1.mx, H.mx), Dn.mx);
                 Xn.mz = add2(fnma2(hlam, FP1.mz, H.mz), Dn.mz);
@@ -349,11 +352,17 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         d1 = d0; dd1 = dd0; ss2 = ss1;
     };
 
+    // steps j0 .. ke+1: four that only fill the pipeline, then one output row
+    // per step.  Segments clear of the plates and of the grid ends run a
+    // specialised step without plate rules, clamping or range tests, two
+    // steps per trip so the pipeline registers swap roles instead of being
+    // copied.  (The specialisations round alike to within FP32 noise, not bit
+    // for bit, so FP32 results may differ at that level between segment
+    // lengths; for a fixed launch configuration they are reproducible.)
     const std::true_type yes;
     const std::false_type no;
     if (interior_segment(ks, ke, nz)) {
-        for (int j = j0; j < ks + 2; ++j) row_step(j, no, no);  // pipeline ramp: no output yet
-        // two steps per trip, so the pipeline registers swap roles instead of being copied
+        for (int j = j0; j < ks + 2; ++j) row_step(j, no, no);
         int j = ks + 2;
         for (; j + 1 <= ke + 1; j += 2) {
             row_step(j, no, yes);
@@ -362,11 +371,18 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         if (j <= ke + 1) row_step(j, no, yes);
     } else {
         for (int j = j0; j <= ke + 1; ++j) {
-            if (j - 2 >= ks && j - 2 < ke) row_step(j, yes, yes);
+            if (j >= ks + 2) row_step(j, yes, yes);
             else row_step(j, yes, no);
         }
     }
     cp_async_drain();  // rows requested past the segment end
+}
+
+__global__ void __launch_bounds__(kThreads2, 4)
+sweep_z2d_x2(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
+{
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    z2_body(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
 }
 
 // L_x(Delta) on the interior rows (plate rows pass through), FP32, two
@@ -375,17 +391,19 @@ sweep_z2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
 // K_m = (X^P + X)_m/2 + D_{i+1/2} - D_{i-1/2}; then for row c = j-2, F^P
 // (backward x, central z from X^P rows j-1 and j-3) and
 // X_new_c = K_c - (lambda/2)(F^P_{i+1} - F^P_i).
-__global__ void __launch_bounds__(kThreads2, 4)
-sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
+// one warp's segment of the x sweep (see z2_body); every thread of the block
+// must call it when sc.last is set (block reduction of the next dt)
+__device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __restrict__ out, const Coef<float>& C,
+                                        const SweepCtl& sc, int strip, int ks, int seg_rows, bool lead)
 {
     extern __shared__ f2 ring_mem[];
+    SweepIO2 io;
+    io.in = in;
+    io.out = out;
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int strip = gw % io.nstrips;
-    const int ks = (gw / io.nstrips) * io.seg_rows;
     const int nz = C.nz, nx = C.nx, pitch = C.pitch;
     const int fs = (int)C.fstride;
-    const int ke = min(ks + io.seg_rows, nz);
+    const int ke = min(ks + seg_rows, nz);
     const int i = strip * kOutW2 - 2 + 2 * lane;
     int ic = i % nx;
     if (ic < 0) ic += nx;
@@ -397,7 +415,7 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
     const f2 lam = bc(lamf), hlam = bc(0.5f * lamf);
     const f2 half = bc(0.5f);
 
-    if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (sc.first && lead && threadIdx.x == 0) {
         sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
         sc.ctl->t += dt;
         sc.ctl->steps += 1.0;
@@ -428,10 +446,10 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
         float* gout = io.out + (long long)(j0 - 2) * pitch + i;  // used only when the row exists
 
         auto row_step = [&](const int j, auto edge_tag, auto store_tag) {
-            constexpr bool EDGE = decltype(edge_tag)::value;
-            constexpr bool STORE = decltype(store_tag)::value;
+            constexpr bool edge = decltype(edge_tag)::value;
+            constexpr bool store = decltype(store_tag)::value;
             const int t = j - j0;
-            if (EDGE) {
+            if (edge) {
                 ring.request((t + kRing - 1) % kRing, io.in + row_off(j + kRing - 1), fs);
             } else {
                 ring.request((t + kRing - 1) % kRing, gnext, fs);
@@ -439,14 +457,14 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
             }
             cp_async_wait_ring();
             const S2 X0 = ring.take(t % kRing);
-            const f2 gz0 = EDGE ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
+            const f2 gz0 = edge ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
             f2 ux0, uz0, T0, p0;
             prims2(X0, gz0, C, ux0, uz0, T0, p0);
 
             // row m = j-1
             const int m = j - 1;
             S2 XP1 = Xm1, K1 = Xm1;  // plate rows pass through
-            if (!EDGE || (m >= 1 && m <= nz - 2)) {
+            if (!edge || (m >= 1 && m <= nz - 2)) {
                 const S2 F1 = flux_x2(Xm1, ux1, uz1, p1, mul2(sub2(right_of(ux1), ux1), idx_),
                                       mul2(sub2(right_of(uz1), uz1), idx_), mul2(sub2(right_of(T1), T1), idx_),
                                       mul2(sub2(ux0, ux2), i2dz), mul2(sub2(uz0, uz2), i2dz), C);
@@ -472,10 +490,10 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
             prims2(XP1, gz1, C, ppux1, ppuz1, ppT1, ppp1);
 
             // row c = j-2: F^P (backward x, central z) and the corrector
-            if (STORE) {
+            if (store) {
                 const int c = j - 2;
                 S2 Xn = K2;
-                if (!EDGE || (c >= 1 && c <= nz - 2)) {
+                if (!edge || (c >= 1 && c <= nz - 2)) {
                     const S2 FP = flux_x2(XP2, ppux2, ppuz2, ppp2, mul2(sub2(ppux2, left_of(ppux2)), idx_),
                                           mul2(sub2(ppuz2, left_of(ppuz2)), idx_), mul2(sub2(ppT2, left_of(ppT2)), idx_),
                                           mul2(sub2(ppux1, ppux3), i2dz), mul2(sub2(ppuz1, ppuz3), i2dz), C);
@@ -510,6 +528,13 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
             ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
         };
 
+        // steps j0 .. ke+1: four that only fill the pipeline, then one output row
+        // per step.  Segments clear of the plates and of the grid ends run a
+        // specialised step without plate rules, clamping or range tests, two
+        // steps per trip so the pipeline registers swap roles instead of being
+        // copied.  (The specialisations round alike to within FP32 noise, not bit
+        // for bit, so FP32 results may differ at that level between segment
+        // lengths; for a fixed launch configuration they are reproducible.)
         const std::true_type yes;
         const std::false_type no;
         if (interior_segment(ks, ke, nz)) {
@@ -522,13 +547,63 @@ sweep_x2d_x2(SweepIO2 io, Coef<float> C, SweepCtl sc)
             if (j <= ke + 1) row_step(j, no, yes);
         } else {
             for (int j = j0; j <= ke + 1; ++j) {
-                if (j - 2 >= ks && j - 2 < ke) row_step(j, yes, yes);
+                if (j >= ks + 2) row_step(j, yes, yes);
                 else row_step(j, yes, no);
             }
         }
         cp_async_drain();  // rows requested past the segment end
     }
     if (sc.last) block_dt_reduce(rmax > 0.f ? 1.0 / (double)rmax : 1e308, bad, sc.ctl, sc.slot_in ^ 1);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4)
+sweep_x2d_x2(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
+{
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    x2_body(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
+}
+
+// ---- batched ensemble: many independent boxes in one launch per sweep -----
+// Each warp takes one work item (box, strip, first row of its segment); the
+// four warps of a block always belong to the same box, whose coefficients
+// the block stages in shared memory.  Boxes step in lockstep (same sweep,
+// same dt slot parity) but each has its own dt, time and state buffers.
+__device__ __forceinline__ const BatchWork& batch_item(const BatchLaunch& L, Coef<float>& sC, SweepCtl& sc,
+                                                       const float*& in, float*& out)
+{
+    const BatchWork& w = L.work[blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)];
+    const int box = L.work[blockIdx.x * kWarpsPerBlock].box;
+    if (threadIdx.x == 0) sC = L.boxes[box].C;
+    __syncthreads();
+    const BoxDesc& B = L.boxes[box];
+    sc.ctl = B.ctl;
+    sc.slot_in = L.slot;
+    sc.first = L.first;
+    sc.last = L.last;
+    sc.Delta = L.Delta;
+    in = B.buf[L.cur];
+    out = B.buf[L.cur ^ 1];
+    return w;
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch(const __grid_constant__ BatchLaunch L)
+{
+    __shared__ Coef<float> sC;
+    SweepCtl sc;
+    const float* in;
+    float* out;
+    const BatchWork& w = batch_item(L, sC, sc, in, out);
+    z2_body(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_x2d_batch(const __grid_constant__ BatchLaunch L)
+{
+    __shared__ Coef<float> sC;
+    SweepCtl sc;
+    const float* in;
+    float* out;
+    const BatchWork& w = batch_item(L, sC, sc, in, out);
+    x2_body(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
 }
 
 // shared memory of the row ring for a block

@@ -1,0 +1,90 @@
+"""Batched ensemble (many uneven 2D boxes, FP32, one launch per sweep for all
+boxes, graph-replayed steps): every box must agree with its own single-box
+run, and a box must match the FP64 oracle within the FP32 bar of
+tests/test_gpu_parity.py.  Batch and solo runs may split rows into segments
+differently (the autotuner), and the FP32 sweeps are reproducible only for a
+fixed split (at the FP32 noise level otherwise), which this unstable flow
+amplifies to ~2e-6 over 63 steps; 1e-5 is the bar, far below what a wrong
+work item, dt slot or graph replay would produce."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from physics import closures
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(68, 17), (132, 33), (160, 40), (256, 64), (520, 130)]
+RAS = [1e5, 3e6, 1e7, 1e6, 1e8]
+
+
+def _grids(cm):
+    return [cm.cm_grid(2, nx, 1, nz, 4.0) for nx, nz in SIZES]
+
+
+def _params(cm, seed=777):
+    p = cm.cm_default_params()
+    p.precision = cm.CM_FP32
+    p.seed = seed
+    return p
+
+
+def test_batch_boxes_equal_their_solo_runs():
+    import paper_2411_10372_gb300 as cm
+    nsteps = 63  # one 50-step graph replay plus direct launches, odd count
+    cm.cm_batch_init(_grids(cm), RAS, 1.0, 5.0 / 3.0, _params(cm))
+    seg_z, seg_x = cm.cm_batch_tuning()
+    assert all(s in (8, 16, 32, 64, 128) for s in seg_z + seg_x)
+    cm.cm_batch_step(nsteps)
+    diags = cm.cm_batch_diagnostics()
+    batch_states = []
+    for b, (nx, nz) in enumerate(SIZES):
+        out = np.empty((4, nz, nx))
+        batch_states.append(cm.cm_batch_get_state(b, out))
+    cm.cm_batch_finalize()
+    for b, (nx, nz) in enumerate(SIZES):
+        s = cm.Solver(nx, nz, RAS[b], 1.0, 5.0 / 3.0, precision="fp32", seed=777 + b)
+        s.step(nsteps)
+        solo = s.state()
+        d = s.sample()
+        s.close()
+        for f in range(4):
+            err = np.linalg.norm(batch_states[b][f] - solo[f]) / np.linalg.norm(solo[f] if f in (0, 3) else solo[0])
+            assert err <= 1e-5, (b, f, err)
+        assert diags[b]["step"] == nsteps and d["step"] == nsteps
+        for k in ("t", "dt", "mass"):
+            assert abs(diags[b][k] - d[k]) <= 1e-5 * abs(d[k]), (b, k)
+
+
+def test_batch_box_matches_oracle():
+    import paper_2411_10372_gb300 as cm
+    nsteps = 40
+    cm.cm_batch_init(_grids(cm), RAS, 1.0, 5.0 / 3.0, _params(cm, seed=5))
+    cm.cm_batch_step(nsteps)
+    b = 3
+    nx, nz = SIZES[b]
+    got = cm.cm_batch_get_state(b, np.empty((4, nz, nx)))
+    masses = [d["mass"] for d in cm.cm_batch_diagnostics()]
+    cm.cm_batch_finalize()
+    cfg = O.Config(nx=nx, nz=nz, Ra=RAS[b], seed=5 + b)
+    want, _, _ = O.step(cfg, O.init(cfg), nsteps)
+    rel = lambda a, w: float(np.linalg.norm(a - w) / np.linalg.norm(w))
+    assert rel(got[0], want[0]) <= 1e-5 and rel(got[3], want[3]) <= 1e-5
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    scale = np.linalg.norm(want[0]) * math.sqrt(cfg.gamma * cl["a"])
+    for f in (1, 2):
+        assert np.linalg.norm(got[f] - want[f]) / scale <= 1e-5
+    assert abs(masses[b] - O.diag(cfg, want)["mass"]) <= 1e-6
+
+
+def test_batch_rejects_bad_boxes():
+    import paper_2411_10372_gb300 as cm
+    with pytest.raises(cm.CMError) as e:
+        cm.cm_batch_init([cm.cm_grid(2, 65, 1, 17, 4.0)], [1e6], 1.0, 5.0 / 3.0, _params(cm))
+    assert e.value.code == cm.CM_EINVAL
+    p = _params(cm)
+    p.precision = cm.CM_FP64
+    with pytest.raises(cm.CMError):
+        cm.cm_batch_init([cm.cm_grid(2, 64, 1, 17, 4.0)], [1e6], 1.0, 5.0 / 3.0, p)
