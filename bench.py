@@ -211,6 +211,35 @@ def run_gpu(args):
                  "segments_z": sorted(set(seg_z)), "segments_x": sorted(set(seg_x)),
                  "l2": "flushed once before the timed steps (the steps replay captured 50-step graphs)"}
 
+    # ---- 3D box: 512 x 512 x 128 nodes, aspect 4 x 4 x 1, FP32, same Ra ----
+    box3 = None
+    if not args.no_3d:
+        n3 = (512, 512, 128)
+        s3 = cm.Solver(n3[0], n3[2], RA, PR, GAMMA, ny=n3[1], ndim=3, precision="fp32", stream=stream,
+                       seed=777 + rank)
+        s3.step(min(args.warmup, 5))
+        s3.sync()
+        barrier()
+        l3 = cm.cm_launch_count()
+        k3 = args.steps_3d
+        sw3, st3 = cm.cm_profile_steps(k3, FLUSH_BYTES)
+        barrier()
+        nl3 = cm.cm_launch_count() - l3
+        d3 = s3.sample()
+        s3.close()
+        ms3 = max_over_ranks(sum(st3))
+        cells3 = n3[0] * n3[1] * n3[2]
+        kinds3 = {"sweep3d_march_z": sw3[0] + sw3[3], "sweep3d_march_y": sw3[1] + sw3[4],
+                  "sweep3d_x": sw3[2] + sw3[5]}
+        bytes3 = 2 * 5 * 4 * cells3
+        box3 = {"value": world * cells3 * k3 / (ms3 * 1e-3), "unit": UNIT, "steps": k3,
+                "workload": "3d_aspect4x4_512x512x128_Ra1e10_fp32", "ms_per_step": ms3 / k3,
+                "sweep_ms": [round(x, 5) for x in sw3], "gpu_launches": nl3, "finite": d3["status"] == 0,
+                "roofline": {k: {"bound": "hbm", "achieved": round(bytes3 / (v / 2 * 1e-3) / 1e9, 1), "peak": hbm,
+                                 "unit": "GB/s", "frac": round(bytes3 / (v / 2 * 1e-3) / 1e9 / hbm, 4)}
+                             for k, v in kinds3.items()},
+                "l2": "flushed before every timed step (256 MiB memset)"}
+
     # ---- FP64 state, same workload ----
     k64 = max(3, min(args.steps, 20))
     s64, r64 = measure("fp64", k64, min(args.warmup, 3), clocks=False)
@@ -245,6 +274,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * cells * 8,
                 "d2h_bytes_per_step": 128, "steps": n_e2e},
         "batch": batch,
+        "box3d": box3,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": r64["total_ms"] / k64, "steps": k64,
                  "sweep_ms": [round(x, 5) for x in r64["sweep_ms"]], "gpu_launches": r64["launches"],
                  "roofline_hbm": roofline(r64)},
@@ -312,6 +342,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--steps-3d", type=int, default=200)
     ap.add_argument("--nx", type=int, default=NX, help="grid override (profiling captures only)")
     ap.add_argument("--nz", type=int, default=NZ, help="grid override (profiling captures only)")
     ap.add_argument("--only-fp32", action="store_true", help="time the FP32 steps only (profiling captures)")

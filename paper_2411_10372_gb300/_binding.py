@@ -204,10 +204,11 @@ def cm_get_time() -> tuple[float, int]:
 
 def cm_profile_steps(n: int, flush_bytes: int = 0) -> tuple[list[float], list[float]]:
     """(mean ms per sweep position, ms of each step) of n profiled steps."""
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * 6)()
     steps = (ctypes.c_double * n)()
     _check(lib().cm_profile_steps(int(n), int(flush_bytes), ms, steps))
-    return list(ms), list(steps)
+    _, nf, _ = cm_state_layout()
+    return list(ms)[: 6 if nf == 5 else 4], list(steps)
 
 
 def cm_launch_count() -> int:

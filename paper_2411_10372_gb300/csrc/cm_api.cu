@@ -99,9 +99,11 @@ void free_ctx(Ctx* c)
 int check_grid(const cm_grid* G)
 {
     if (!G) return fail(CM_EINVAL, "grid is NULL");
-    if (G->ndim != 2) return fail(CM_EINVAL, "ndim = %d: this build steps 2D grids", G->ndim);
+    if (G->ndim != 2 && G->ndim != 3) return fail(CM_EINVAL, "ndim = %d: must be 2 or 3", G->ndim);
     if (G->nx < 4 || G->nz < 5) return fail(CM_EINVAL, "grid too small: nx >= 4 and nz >= 5 needed (got %d, %d)", G->nx, G->nz);
-    if ((long long)G->nx * G->nz > (1LL << 31)) return fail(CM_EINVAL, "grid too large");
+    if (G->ndim == 3 && G->ny < 4) return fail(CM_EINVAL, "grid too small: ny >= 4 needed in 3D (got %d)", G->ny);
+    const long long ny = G->ndim == 3 ? G->ny : 1;
+    if ((long long)G->nx * ny * G->nz > (1LL << 31)) return fail(CM_EINVAL, "grid too large");
     if (!(G->aspect > 0)) return fail(CM_EINVAL, "aspect must be > 0");
     return CM_OK;
 }
@@ -210,27 +212,35 @@ int download(Ctx* c, double* host)
     return CM_OK;
 }
 
-// queue n steps; with ev != NULL (5 events per step), record ev[5s+q]
-// before sweep q of step s and ev[5s+4] after its last sweep; with flush,
-// overwrite flush_bytes of it before each step, outside the brackets
+// sweeps per step: L_x L_z L_x L_z in 2D, L_x L_y L_z L_x L_y L_z in 3D
+// (applied right to left)
+int sweeps_per_step(const Ctx* c) { return c->grid.ndim == 3 ? 6 : 4; }
+
+// queue n steps; with ev != NULL (S+1 events per step, S sweeps per step),
+// record ev[(S+1)s+q] before sweep q of step s and ev[(S+1)s+S] after its last
+// sweep; with flush, overwrite flush_bytes of it before each step, outside
+// the brackets
 int queue_steps(Ctx* c, int n, cudaEvent_t* ev = nullptr, void* flush = nullptr, size_t flush_bytes = 0)
 {
+    static const int order2[4] = {2, 0, 2, 0};
+    static const int order3[6] = {2, 1, 0, 2, 1, 0};
+    const int S = sweeps_per_step(c);
+    const int* order = S == 6 ? order3 : order2;
     for (int s = 0; s < n; ++s) {
         const int slot = (int)(c->step & 1);
         SweepCtl sc;
         sc.ctl = c->ctl;
         sc.slot_in = slot;
         sc.Delta = 0.0;
-        const int order[4] = {2, 0, 2, 0};  // z, x, z, x: L_x L_z L_x L_z applied right to left
         if (flush) CK(cudaMemsetAsync(flush, s & 0xff, flush_bytes, c->stream));
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < S; ++q) {
             sc.first = (q == 0);
-            sc.last = (q == 3);
-            if (ev) CK(cudaEventRecord(ev[5 * s + q], c->stream));
+            sc.last = (q == S - 1);
+            if (ev) CK(cudaEventRecord(ev[(S + 1) * s + q], c->stream));
             int rc = sweep(c, order[q], sc);
             if (rc) return rc;
         }
-        if (ev) CK(cudaEventRecord(ev[5 * s + 4], c->stream));
+        if (ev) CK(cudaEventRecord(ev[(S + 1) * s + S], c->stream));
         c->step++;
         if (c->prm.diag_every > 0 && c->step % c->prm.diag_every == 0) {
             int rc = sample(c);
@@ -526,7 +536,8 @@ int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* 
 int cm_sweep(int dir, double Delta)
 {
     NEED_CTX();
-    if (dir != 0 && dir != 2) return fail(CM_EINVAL, "dir must be 0 (x) or 2 (z) for a 2D grid");
+    if (g_ctx->grid.ndim == 3 ? (dir < 0 || dir > 2) : (dir != 0 && dir != 2))
+        return fail(CM_EINVAL, "dir must be 0 (x), 1 (y, 3D only) or 2 (z)");
     if (!(Delta > 0)) return fail(CM_EINVAL, "Delta must be > 0");
     SweepCtl sc;
     sc.ctl = g_ctx->ctl;
@@ -573,19 +584,20 @@ int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, doub
             return fail(CM_ENOMEM, "cudaMalloc of the %llu-byte flush buffer failed", flush_bytes);
         }
     }
-    std::vector<cudaEvent_t> ev(5 * (size_t)n, nullptr);
+    const int S = sweeps_per_step(c);
+    std::vector<cudaEvent_t> ev((S + 1) * (size_t)n, nullptr);
     int rc = CM_OK;
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) { rc = fail(CM_ECUDA, "cudaEventCreate failed"); break; }
     if (!rc) rc = queue_steps(c, n, ev.data(), flush, flush_bytes);
     if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess)
         rc = fail(CM_ECUDA, "profiled steps failed: %s", cudaGetErrorString(cudaGetLastError()));
-    double ms[4] = {0, 0, 0, 0};
+    double ms[6] = {0, 0, 0, 0, 0, 0};
     for (int s = 0; !rc && s < n; ++s) {
         double tot = 0;
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < S; ++q) {
             float t = 0.f;
-            if (cudaEventElapsedTime(&t, ev[5 * s + q], ev[5 * s + q + 1]) != cudaSuccess) {
+            if (cudaEventElapsedTime(&t, ev[(S + 1) * s + q], ev[(S + 1) * s + q + 1]) != cudaSuccess) {
                 rc = fail(CM_ECUDA, "cudaEventElapsedTime failed");
                 break;
             }
@@ -598,7 +610,7 @@ int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, doub
         if (e) cudaEventDestroy(e);
     if (flush) cudaFree(flush);
     if (rc) return rc;
-    for (int q = 0; q < 4; ++q) ms_out[q] = ms[q] / n;
+    for (int q = 0; q < S; ++q) ms_out[q] = ms[q] / n;
     return CM_OK;
 }
 

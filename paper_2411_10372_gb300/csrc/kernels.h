@@ -9,7 +9,7 @@ namespace cm {
 
 template <class R>
 struct Launch {
-    // one sweep L_dir (dir 0 = x, 2 = z; 2D)
+    // one sweep L_dir (dir 0 = x, 1 = y (3D only), 2 = z)
     static cudaError_t sweep(int dir, const R* in, R* out, const R* zt, const Coef<R>& C, const SweepCtl& sc,
                              int seg_rows, cudaStream_t s);
     static cudaError_t init(R* X, const Coef<R>& C, const InitArgs& A, cudaStream_t s);

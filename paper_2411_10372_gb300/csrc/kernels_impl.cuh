@@ -3,6 +3,7 @@
 #include <cstdlib>
 #include "kernels.h"
 #include "sweep2d.cuh"
+#include "sweep3d.cuh"
 #include "aux_kernels.cuh"
 
 namespace cm {
@@ -88,10 +89,76 @@ static inline int blocks_per_sm(K kernel, size_t smem = 0)
     return b;
 }
 
+// 3D sweeps: warps per block of the 2.5D kernels (the outer two on each side
+// are halo), and the march segment minimising waves * (rows + ramp)
+constexpr int kNW3 = 16;
+
+static inline int pick_segment3(long long blocks_per_seg, int nmarch, int blocks_per_sm, int nsm)
+{
+    if (const char* e = getenv("CM_SEG_ROWS")) {
+        const int v = atoi(e);
+        if (v >= 4 && v <= 4096) return v;
+    }
+    const long long cap = (long long)blocks_per_sm * nsm;
+    int top = 8;
+    while (top < nmarch && top < 4096) top *= 2;
+    int best = top;
+    double best_cost = 1e300;
+    for (int seg = top; seg >= 8; seg /= 2) {
+        const long long blocks = blocks_per_seg * ((nmarch + seg - 1) / seg);
+        const long long waves = (blocks + cap - 1) / cap;
+        const double cost = (double)waves * (double)(seg + 4);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = seg; }
+    }
+    return best;
+}
+
+template <class K>
+static inline int blocks_per_sm3(K kernel)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kNW3 * 32, 0) != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
+// one 3D sweep: dir 2 = L_z (march z, warps over y), 1 = L_y (march y, warps
+// over z), 0 = L_x (march z, warps over y); grid (x strips, W groups, segments)
+template <class R>
+static cudaError_t sweep3(int dir, const R* in, R* out, const R* zt, const Coef<R>& C, const SweepCtl& sc,
+                          cudaStream_t s)
+{
+    Sweep3IO<R> io;
+    io.in = in;
+    io.out = out;
+    io.zt = zt;
+    io.nstrips = (C.nx + kOutW - 1) / kOutW;
+    io.nmarch = (dir == 1) ? C.ny : C.nz;
+    io.nw = (dir == 1) ? C.nz : C.ny;
+    const int groups = (io.nw + kNW3 - 5) / (kNW3 - 4);
+    static int bps[3] = {0, 0, 0};
+    if (!bps[0]) {
+        bps[0] = blocks_per_sm3(sweep3d_x<R, kNW3>);
+        bps[1] = blocks_per_sm3(sweep3d_march<R, 1, kNW3>);
+        bps[2] = blocks_per_sm3(sweep3d_march<R, 2, kNW3>);
+    }
+    if (dir < 0 || dir > 2) return cudaErrorInvalidValue;
+    io.seg = pick_segment3((long long)io.nstrips * groups, io.nmarch, bps[dir], sm_count());
+    const int nsegs = (io.nmarch + io.seg - 1) / io.seg;
+    const dim3 grid(io.nstrips, groups, nsegs);
+    if (dir == 2) sweep3d_march<R, 2, kNW3><<<grid, kNW3 * 32, 0, s>>>(io, C, sc);
+    else if (dir == 1) sweep3d_march<R, 1, kNW3><<<grid, kNW3 * 32, 0, s>>>(io, C, sc);
+    else sweep3d_x<R, kNW3><<<grid, kNW3 * 32, 0, s>>>(io, C, sc);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t Launch<R>::sweep(int dir, const R* in, R* out, const R* zt, const Coef<R>& C, const SweepCtl& sc,
                              int seg_rows, cudaStream_t s)
 {
+    if (C.ndim == 3) return sweep3(dir, in, out, zt, C, sc, s);
     if constexpr (std::is_same<R, float>::value) {
         if (C.nx % 2 == 0 && (long long)C.fstride * 5 < (1LL << 31)) return launch_sweep_x2(dir, in, out, zt, C, sc, s);
     }

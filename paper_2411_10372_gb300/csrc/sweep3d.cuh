@@ -1,0 +1,419 @@
+// sweep3d.cuh -- fused 3D sweeps L_z, L_y (march kernel) and L_x (lane
+// kernel) of Sec. 3.1, templated on the state precision.
+//
+// Geometry (a 2.5D march).  Lanes span x (a strip of 32 columns, 28 output
+// columns, periodic).  The NW warps of a block span the third direction W
+// (y for the z and x sweeps, z for the y sweep), one row each; the block's
+// outer two warps on each side are halo: their X^P and primitives feed the
+// cross derivatives of the inner NW-4 warps, which alone store.  Every warp
+// marches along the march direction M (z for the z and x sweeps, y for the y
+// sweep) through a segment of rows, keeping rows in flight in registers as
+// the 2D kernels do.  Cross derivatives along x come from lane shuffles,
+// along W from a shared-memory exchange (two block barriers per row), along
+// M from the register pipeline.
+#pragma once
+#include "sweep3d_common.cuh"
+
+namespace cm {
+
+template <class R>
+struct Sweep3IO {
+    const R* in;
+    R* out;
+    const R* zt;   // z of each plane, in R
+    int seg;       // rows per march segment
+    int nstrips;   // x strips of kOutW columns
+    int nmarch;    // rows along the march direction (nz or ny)
+    int nw;        // rows along W (ny or nz)
+};
+
+// state index of (plane k, row jy, column ic)
+__device__ __forceinline__ long long off3(int k, int jy, int ny, int pitch, int ic)
+{
+    return ((long long)k * ny + jy) * pitch + ic;
+}
+
+__device__ __forceinline__ int wrap(int a, int n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// L_z (AL = 2: march z, W = y) or L_y (AL = 1: march y, W = z).
+// Row pipeline at step j (row j of the march just loaded), as in sweep_z2d:
+// F^n_{j-1}, X^P_{j-1}, F^P_{j-1}, average at j-2, TVD flux across
+// (j-2, j-1), output row j-2.  Plates: for L_z at the ends of the march
+// (half-cell density, m = 0, T = T_w); for L_y the plate planes are rows of
+// W and pass through unchanged.
+template <class R, int AL, int NW>
+__global__ void __launch_bounds__(NW * 32)
+sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
+{
+    constexpr int WD = (AL == 2) ? 1 : 2;  // direction of the warps
+    __shared__ R xw[2][NW][32];             // u_AL, u_W of X at the current row, per warp
+    __shared__ R pw[2][NW][32];             // the same for X^P
+
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int strip = blockIdx.x;
+    const int cw = blockIdx.y * (NW - 4) - 2 + w;      // W coordinate of this warp
+    const int ks = blockIdx.z * io.seg;                 // first output row of the segment
+    const int nz = C.nz, ny = C.ny, nx = C.nx, pitch = C.pitch;
+    const long long fs = C.fstride;
+    const int nm = io.nmarch;
+    const int ke = min(ks + io.seg, nm);
+    const int i = strip * kOutW - 2 + lane;
+    const int ic = wrap(i, nx);
+    // W row this warp reads: periodic in y, clamped in z (out-of-range warps compute unused values)
+    const int cwr = (WD == 1) ? wrap(cw, ny) : min(max(cw, 0), nz - 1);
+    const bool w_out = w >= 2 && w < NW - 2 && cw < io.nw && cw >= 0;
+    const bool own = lane >= 2 && lane < 2 + kOutW && i < nx && w_out;
+    // L_y leaves the plate planes unchanged
+    const bool passthru = (AL == 1) && (cwr == 0 || cwr == nz - 1);
+
+    const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
+    const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
+    const R h = (AL == 2) ? C.hz : C.hy;
+    const R lam = (R)(Delta / ((AL == 2) ? C.dz : C.dy));
+    const R Dl = (R)Delta;
+    const R lam2 = R(2) * lam;
+    if (sc.first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+        sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
+        sc.ctl->t += dt;
+        sc.ctl->steps += 1.0;
+    }
+
+    // march row j -> memory row and z of that row
+    auto row_of = [&](int j, long long& off, R& z) {
+        if (AL == 2) {
+            const int k = min(max(j, 0), nz - 1);
+            off = off3(k, cwr, ny, pitch, ic);
+            z = io.zt[k];
+        } else {
+            off = off3(cwr, wrap(j, ny), ny, pitch, ic);
+            z = io.zt[cwr];
+        }
+    };
+    // exchange of two per-lane values with the neighbouring warps (rows W +- 1):
+    // returns their central differences along W; every thread of the block calls it
+    auto exchangeW = [&](R (&buf)[2][NW][32], R a, R b, R& da, R& db) {
+        buf[0][w][lane] = a;
+        buf[1][w][lane] = b;
+        __syncthreads();
+        const int wu = min(w + 1, NW - 1), wd = max(w - 1, 0);
+        da = d3(buf[0][wu][lane], buf[0][wd][lane], C, WD, true);
+        db = d3(buf[1][wu][lane], buf[1][wd][lane], C, WD, true);
+    };
+
+    const int j0 = ks - 2;
+    long long offp;
+    R zp;
+    row_of(j0 - 1, offp, zp);
+    S3<R> Xm1 = s3_load(io.in, fs, offp), Xm2 = Xm1;
+    R u1[3], T1, p1;
+    prims3(Xm1, zp, C, u1, T1, p1);
+    R A1 = R(0), A2 = R(0), dxux1 = R(0), dxua1 = R(0), dwua1 = R(0), dwuw1 = R(0);
+    const S3<R> zero = {R(0), {R(0), R(0), R(0)}, R(0)};
+    S3<R> F2 = zero, XP2 = Xm1, FP2 = zero, d1 = zero, Dm = zero;
+    R ppu2[3] = {u1[0], u1[1], u1[2]}, ppT2 = T1;
+    R dd1 = R(0), ss2 = R(0);
+
+    for (int j = j0; j <= ke + 1; ++j) {
+        long long off0;
+        R z0;
+        row_of(j, off0, z0);
+        const S3<R> X0 = s3_load(io.in, fs, off0);
+        R u0[3], T0, p0;
+        prims3(X0, z0, C, u0, T0, p0);
+        const R A0 = fabs(u0[AL]) + rsqrt_(C.cs2 * T0);
+        const R dxux0 = d3(shdn(u0[0]), shup(u0[0]), C, 0, true);
+        const R dxua0 = d3(shdn(u0[AL]), shup(u0[AL]), C, 0, true);
+        R dwua0, dwuw0;
+        exchangeW(xw, u0[AL], u0[WD], dwua0, dwuw0);
+
+        // row m = j-1: F^n (forward along the march), X^P
+        const int m = j - 1;
+        R du[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) du[c][AL] = d3(u0[c], u1[c], C, AL, false);
+        du[0][0] = dxux1;
+        du[AL][0] = dxua1;
+        du[WD][WD] = dwuw1;
+        du[AL][WD] = dwua1;
+        const S3<R> F1 = flux3<AL>(Xm1, u1, p1, du, d3(T0, T1, C, AL, false), C);
+        S3<R> XP1 = Xm1;
+        R zm;
+        if (AL == 2) {
+            zm = io.zt[min(max(m, 0), nz - 1)];
+            if (m >= 1 && m <= nz - 2) {
+                XP1.r = Xm1.r - lam * (F1.r - F2.r);
+                XP1.m[0] = Xm1.m[0] - lam * (F1.m[0] - F2.m[0]);
+                XP1.m[1] = Xm1.m[1] - lam * (F1.m[1] - F2.m[1]);
+                XP1.m[2] = (Xm1.m[2] - lam * (F1.m[2] - F2.m[2])) + Dl * (-C.g * Xm1.r);
+                XP1.E = Xm1.E - lam * (F1.E - F2.E);
+            } else {
+                XP1.r = (m <= 0) ? Xm1.r - lam2 * F1.r : Xm1.r + lam2 * F2.r;
+                XP1.m[0] = XP1.m[1] = XP1.m[2] = R(0);
+                XP1.E = XP1.r * ((m <= 0) ? C.ebot : C.etop);
+            }
+        } else {
+            zm = z0;
+            if (!passthru) {
+                XP1.r = Xm1.r - lam * (F1.r - F2.r);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) XP1.m[c] = Xm1.m[c] - lam * (F1.m[c] - F2.m[c]);
+                XP1.E = Xm1.E - lam * (F1.E - F2.E);
+            }
+        }
+        R ppu1[3], ppT1, ppp1;
+        prims3(XP1, zm, C, ppu1, ppT1, ppp1);
+        R dwppa1, dwppw1;
+        exchangeW(pw, ppu1[AL], ppu1[WD], dwppa1, dwppw1);
+        R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dq[c][AL] = d3(ppu1[c], ppu2[c], C, AL, false);
+        dq[0][0] = d3(shdn(ppu1[0]), shup(ppu1[0]), C, 0, true);
+        dq[AL][0] = d3(shdn(ppu1[AL]), shup(ppu1[AL]), C, 0, true);
+        dq[WD][WD] = dwppw1;
+        dq[AL][WD] = dwppa1;
+        const S3<R> FP1 = flux3<AL>(XP1, ppu1, ppp1, dq, d3(ppT1, ppT2, C, AL, false), C);
+
+        // row c = j-2: corrector X^C and the average (X^P + X^C)/2
+        const int c = j - 2;
+        S3<R> Xa = Xm2;
+        if (AL == 2) {
+            if (c >= 1 && c <= nz - 2) {
+                Xa.r = (XP2.r + (Xm2.r - lam * (FP1.r - FP2.r))) * R(0.5);
+                Xa.m[0] = (XP2.m[0] + (Xm2.m[0] - lam * (FP1.m[0] - FP2.m[0]))) * R(0.5);
+                Xa.m[1] = (XP2.m[1] + (Xm2.m[1] - lam * (FP1.m[1] - FP2.m[1]))) * R(0.5);
+                Xa.m[2] = (XP2.m[2] + ((Xm2.m[2] - lam * (FP1.m[2] - FP2.m[2])) + Dl * (-C.g * XP2.r))) * R(0.5);
+                Xa.E = (XP2.E + (Xm2.E - lam * (FP1.E - FP2.E))) * R(0.5);
+            } else {
+                Xa.r = (c <= 0) ? (XP2.r + (Xm2.r - lam2 * FP1.r)) * R(0.5) : (XP2.r + Xm2.r) * R(0.5);
+            }
+        } else if (!passthru) {
+            Xa.r = (XP2.r + (Xm2.r - lam * (FP1.r - FP2.r))) * R(0.5);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Xa.m[q] = (XP2.m[q] + (Xm2.m[q] - lam * (FP1.m[q] - FP2.m[q]))) * R(0.5);
+            Xa.E = (XP2.E + (Xm2.E - lam * (FP1.E - FP2.E))) * R(0.5);
+        }
+
+        // TVD flux across (j-2, j-1) from the input state
+        const S3<R> d0 = s3_sub(X0, Xm1);
+        const R dd0 = s3_dot(d0, d0);
+        const R ss1 = s3_dot(d1, d0);
+        S3<R> Dn = zero;
+        const bool tvd_on = (AL == 2) ? (c >= 1 && c <= nz - 3) : !passthru;
+        if (tvd_on) {
+            const R G = tvd_G(ss2, ss1, dd1, courant(Delta, lam, A2, A1, h), C.tvd_form);
+            Dn = {G * d1.r, {G * d1.m[0], G * d1.m[1], G * d1.m[2]}, G * d1.E};
+        }
+
+        if (c >= ks && c < ke && own) {
+            S3<R> Xn = Xa;
+            const bool interior = (AL == 2) ? (c >= 1 && c <= nz - 2) : !passthru;
+            if (interior) {
+                Xn.r = Xa.r + (Dn.r - Dm.r);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (Dn.m[q] - Dm.m[q]);
+                Xn.E = Xa.E + (Dn.E - Dm.E);
+            } else if (AL == 2) {
+                Xn.m[0] = Xn.m[1] = Xn.m[2] = R(0);
+                Xn.E = Xa.r * (c == 0 ? C.ebot : C.etop);
+            }
+            long long offc;
+            R zc;
+            row_of(c, offc, zc);
+            s3_store(io.out, fs, offc, Xn);
+        }
+
+        Xm2 = Xm1;
+        Xm1 = X0;
+        u1[0] = u0[0]; u1[1] = u0[1]; u1[2] = u0[2];
+        T1 = T0;
+        p1 = p0;
+        A2 = A1;
+        A1 = A0;
+        dxux1 = dxux0; dxua1 = dxua0; dwua1 = dwua0; dwuw1 = dwuw0;
+        F2 = F1;
+        XP2 = XP1;
+        ppu2[0] = ppu1[0]; ppu2[1] = ppu1[1]; ppu2[2] = ppu1[2];
+        ppT2 = ppT1;
+        FP2 = FP1;
+        d1 = d0;
+        dd1 = dd0;
+        ss2 = ss1;
+        Dm = Dn;
+    }
+}
+
+// L_x in 3D: march z, warps span y, the x stencil across lanes (as
+// sweep_x2d); plate planes pass through.  Row pipeline at step j: F^n and X^P
+// of row j-1 (d/dz from rows j, j-2; d/dy from the exchange of row j-1),
+// then F^P, corrector, average and TVD along x of row j-2, output row j-2.
+template <class R, int NW>
+__global__ void __launch_bounds__(NW * 32)
+sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
+{
+    __shared__ R xw[2][NW][32];
+    __shared__ R pw[2][NW][32];
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int cw = blockIdx.y * (NW - 4) - 2 + w;  // y row of this warp
+    const int ks = blockIdx.z * io.seg;
+    const int nz = C.nz, ny = C.ny, nx = C.nx, pitch = C.pitch;
+    const long long fs = C.fstride;
+    const int ke = min(ks + io.seg, nz);
+    const int i = blockIdx.x * kOutW - 2 + lane;
+    const int ic = wrap(i, nx);
+    const int cwr = wrap(cw, ny);
+    const bool own = lane >= 2 && lane < 2 + kOutW && i < nx && w >= 2 && w < NW - 2 && cw < ny;
+
+    const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
+    const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
+    const R lam = (R)(Delta / C.dx);
+    if (sc.first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+        sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
+        sc.ctl->t += dt;
+        sc.ctl->steps += 1.0;
+    }
+    auto exchangeW = [&](R (&buf)[2][NW][32], R a, R b, R& da, R& db) {
+        buf[0][w][lane] = a;
+        buf[1][w][lane] = b;
+        __syncthreads();
+        const int wu = min(w + 1, NW - 1), wd = max(w - 1, 0);
+        da = d3(buf[0][wu][lane], buf[0][wd][lane], C, 1, true);
+        db = d3(buf[1][wu][lane], buf[1][wd][lane], C, 1, true);
+    };
+    auto offk = [&](int k) { return off3(min(max(k, 0), nz - 1), cwr, ny, pitch, ic); };
+    auto zk = [&](int k) { return io.zt[min(max(k, 0), nz - 1)]; };
+
+    double vmin = 1e308;
+    R rmax = R(0);
+    int bad = 0;
+    const int j0 = ks - 2;
+    S3<R> Xm1 = s3_load(io.in, fs, offk(j0 - 1)), Xm2 = Xm1;
+    R u1[3], T1, p1;
+    prims3(Xm1, zk(j0 - 1), C, u1, T1, p1);
+    R u2[3] = {u1[0], u1[1], u1[2]}, T2 = T1;
+    R dwx1 = R(0), dwy1 = R(0);          // d/dy of u_x, u_y of row j-1
+    S3<R> XP2 = Xm1;
+    R pp2[3] = {u1[0], u1[1], u1[2]}, ppT2 = T1, ppp2 = p1;
+    R pp3[3] = {u1[0], u1[1], u1[2]};
+    R dwpx2 = R(0), dwpy2 = R(0);        // d/dy of X^P u_x, u_y of row j-2
+
+    for (int j = j0; j <= ke + 1; ++j) {
+        const S3<R> X0 = s3_load(io.in, fs, offk(j));
+        R u0[3], T0, p0;
+        prims3(X0, zk(j), C, u0, T0, p0);
+        R dwx0, dwy0;
+        exchangeW(xw, u0[0], u0[1], dwx0, dwy0);
+
+        // row m = j-1: F^n with forward x-differences, X^P
+        const int m = j - 1;
+        S3<R> XP1 = Xm1;
+        {
+            R du[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) du[c][0] = d3(shdn(u1[c]), u1[c], C, 0, false);
+            du[0][1] = dwx1;
+            du[1][1] = dwy1;
+            du[0][2] = d3(u0[0], u2[0], C, 2, true);
+            du[2][2] = d3(u0[2], u2[2], C, 2, true);
+            const S3<R> F1 = flux3<0>(Xm1, u1, p1, du, d3(shdn(T1), T1, C, 0, false), C);
+            const S3<R> Fl = {shup(F1.r), {shup(F1.m[0]), shup(F1.m[1]), shup(F1.m[2])}, shup(F1.E)};
+            if (m >= 1 && m <= nz - 2) {
+                XP1.r = Xm1.r - lam * (F1.r - Fl.r);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) XP1.m[c] = Xm1.m[c] - lam * (F1.m[c] - Fl.m[c]);
+                XP1.E = Xm1.E - lam * (F1.E - Fl.E);
+            }
+        }
+        R pp1[3], ppT1, ppp1;
+        prims3(XP1, zk(m), C, pp1, ppT1, ppp1);
+        R dwpx1, dwpy1;
+        exchangeW(pw, pp1[0], pp1[1], dwpx1, dwpy1);
+
+        // row c = j-2: F^P with backward x-differences, corrector, average, TVD along x
+        const int c = j - 2;
+        R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) dq[q][0] = d3(pp2[q], shup(pp2[q]), C, 0, false);
+        dq[0][1] = dwpx2;
+        dq[1][1] = dwpy2;
+        dq[0][2] = d3(pp1[0], pp3[0], C, 2, true);
+        dq[2][2] = d3(pp1[2], pp3[2], C, 2, true);
+        const S3<R> FP = flux3<0>(XP2, pp2, ppp2, dq, d3(ppT2, shup(ppT2), C, 0, false), C);
+        const S3<R> FPr = {shdn(FP.r), {shdn(FP.m[0]), shdn(FP.m[1]), shdn(FP.m[2])}, shdn(FP.E)};
+        S3<R> Xa;
+        Xa.r = (XP2.r + (Xm2.r - lam * (FPr.r - FP.r))) * R(0.5);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Xa.m[q] = (XP2.m[q] + (Xm2.m[q] - lam * (FPr.m[q] - FP.m[q]))) * R(0.5);
+        Xa.E = (XP2.E + (Xm2.E - lam * (FPr.E - FP.E))) * R(0.5);
+        const S3<R> Xr = {shdn(Xm2.r), {shdn(Xm2.m[0]), shdn(Xm2.m[1]), shdn(Xm2.m[2])}, shdn(Xm2.E)};
+        const S3<R> d0 = s3_sub(Xr, Xm2);
+        const R dd = s3_dot(d0, d0);
+        const S3<R> dl = {shup(d0.r), {shup(d0.m[0]), shup(d0.m[1]), shup(d0.m[2])}, shup(d0.E)};
+        const R sp = s3_dot(dl, d0);
+        const R sm = shdn(sp);
+        const R A = fabs(u2[0]) + rsqrt_(C.cs2 * T2);
+        const R G = tvd_G(sp, sm, dd, courant(Delta, lam, A, shdn(A), C.hx), C.tvd_form);
+        const S3<R> Dn = {G * d0.r, {G * d0.m[0], G * d0.m[1], G * d0.m[2]}, G * d0.E};
+        const S3<R> Dl = {shup(Dn.r), {shup(Dn.m[0]), shup(Dn.m[1]), shup(Dn.m[2])}, shup(Dn.E)};
+
+        if (c >= ks && c < ke && own) {
+            S3<R> Xn = Xm2;  // plate planes pass through
+            if (c >= 1 && c <= nz - 2) {
+                Xn.r = Xa.r + (Dn.r - Dl.r);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (Dn.m[q] - Dl.m[q]);
+                Xn.E = Xa.E + (Dn.E - Dl.E);
+            }
+            s3_store(io.out, fs, offk(c), Xn);
+            if (sc.last) {
+                R un[3], Tn, pn;
+                prims3(Xn, zk(c), C, un, Tn, pn);
+                if constexpr (kExact<R>) {
+                    const double cs = sqrt(C.cs2 * Tn);
+                    double v = C.dx / (fabs(un[0]) + cs);
+                    v = fmin(v, C.dy / (fabs(un[1]) + cs));
+                    v = fmin(v, C.dz / (fabs(un[2]) + cs));
+                    if (!(v > 0.0) || !(v < 1e300)) bad = 1;
+                    vmin = fmin(vmin, v);
+                } else {
+                    const R cs = rsqrt_(C.cs2 * Tn);
+                    const R r = fmax(fmax((fabs(un[0]) + cs) * C.inv_dx, (fabs(un[1]) + cs) * C.inv_dy),
+                                     (fabs(un[2]) + cs) * C.inv_dz);
+                    if (!(r > R(0)) || !(r < R(1e30))) bad = 1;
+                    rmax = fmax(rmax, r);
+                }
+            }
+        }
+
+        Xm2 = Xm1;
+        Xm1 = X0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            u2[q] = u1[q];
+            u1[q] = u0[q];
+            pp3[q] = pp2[q];
+            pp2[q] = pp1[q];
+        }
+        T2 = T1;
+        T1 = T0;
+        p1 = p0;
+        dwx1 = dwx0;
+        dwy1 = dwy0;
+        XP2 = XP1;
+        ppT2 = ppT1;
+        ppp2 = ppp1;
+        dwpx2 = dwpx1;
+        dwpy2 = dwpy1;
+    }
+    if (sc.last) {
+        if constexpr (!kExact<R>) vmin = rmax > R(0) ? 1.0 / (double)rmax : 1e308;
+        block_dt_reduce(vmin, bad, sc.ctl, sc.slot_in ^ 1);
+    }
+}
+
+}  // namespace cm

@@ -1,0 +1,199 @@
+"""Parity of the 3D CUDA sweeps (through the C ABI) with the FP64 oracle.
+
+Bars (stated per output):
+  FP64: single sweeps L_z, L_y, L_x on a stirred state <= 1e-13 relative L2
+    per field (momentum against rho c); 40 full steps (z, y, x, z, y, x)
+    <= 1e-12.
+  FP32: single sweeps on the same state rounded to FP32 <= 2e-6; 40 steps
+    <= 1e-5 (rho, E) and 1e-5 of rho c (momentum).
+  Full 512 x 512 x 128 FP32 workload: y-independent data stepped in 3D must
+    match the 2D oracle on every y plane (the oracle's 3D operator reduces to
+    its 2D one there, bit for bit), and a shift of the data in x and y must
+    shift the result bit for bit.
+Inputs are seeded and synthetic; the oracle never sees a CUDA result.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from physics import closures, state_from_prims
+from test_gpu_parity import rel_l2, solver_for
+
+pytestmark = pytest.mark.gpu
+
+
+def stirred_state_3d(cfg, seed, u_amp=0.3, t_amp=0.05):
+    """The conduction profile with random temperature, density and velocity
+    fields (velocity zero on the plates), plates at the wall temperatures."""
+    rng = np.random.default_rng(seed)
+    T_c, p_c, _ = O.profile(cfg)
+    shp = (cfg.nz, cfg.ny, cfg.nx)
+    Z = np.broadcast_to(np.linspace(0, 1, cfg.nz)[:, None, None], shp)
+    T = T_c[:, None, None] * (1 + t_amp * rng.uniform(-1, 1, shp))
+    u = [u_amp * rng.uniform(-1, 1, shp) for _ in range(3)]
+    for f in u:
+        f[0] = f[-1] = 0.0
+    t_top = (1.0 - cfg.eps - cfg.D) if cfg.t_top is None else cfg.t_top
+    T[0], T[-1] = cfg.t_bot, t_top
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    rho = p_c[:, None, None] / (cl["a"] * T) * (1 + 0.02 * rng.uniform(-1, 1, shp))
+    return state_from_prims(cfg, rho, u[0], u[2], T, Z, uy=u[1])
+
+
+def check_fields(cfg, got, want, tol):
+    """rho, E relative L2; momenta against the scale rho c."""
+    for f in (0, 4):
+        assert rel_l2(got[f], want[f]) <= tol, (f, rel_l2(got[f], want[f]))
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    scale = np.linalg.norm(want[0]) * math.sqrt(cfg.gamma * cl["a"])
+    for f in (1, 2, 3):
+        err = np.linalg.norm(got[f] - want[f]) / scale
+        assert err <= tol, (f, err)
+
+
+# (nx, ny, nz): ragged x strips (28 columns), ragged y and z warp groups (12
+# rows), several march segments, the smallest legal grid
+SHAPES3 = [(8, 4, 5), (29, 13, 9), (36, 20, 17), (64, 16, 33), (57, 27, 12)]
+
+
+@pytest.mark.parametrize("nx,ny,nz", SHAPES3)
+@pytest.mark.parametrize("tvd", [O.TVD_SPLIT, O.TVD_SUM])
+def test_single_sweeps_3d_fp64(nx, ny, nz, tvd):
+    cfg = O.Config(nx=nx, ny=ny, nz=nz, ndim=3, Ra=1e5, tvd_form=tvd, dt_fixed=1e-3)
+    X = stirred_state_3d(cfg, seed=nx * 10000 + ny * 100 + nz)
+    s = solver_for(cfg)
+    try:
+        for direction in (2, 1, 0):
+            Delta = 0.2 * min(cfg.aspect / nx, cfg.aspect / ny, 1.0 / (nz - 1)) / 4.0
+            s.set_state(X)
+            s.sweep(direction, Delta)
+            got = s.state()
+            want = O.sweep(cfg, X, direction, Delta)
+            check_fields(cfg, got, want, 1e-13)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("nx,ny,nz", SHAPES3[1:])
+def test_single_sweeps_3d_fp32(nx, ny, nz):
+    cfg = O.Config(nx=nx, ny=ny, nz=nz, ndim=3, Ra=1e5, dt_fixed=1e-3)
+    X = stirred_state_3d(cfg, seed=nx + ny + nz).astype(np.float32).astype(np.float64)
+    s = solver_for(cfg, "fp32")
+    try:
+        for direction in (2, 1, 0):
+            Delta = 0.2 * min(cfg.aspect / nx, cfg.aspect / ny, 1.0 / (nz - 1)) / 4.0
+            s.set_state(X)
+            s.sweep(direction, Delta)
+            got = s.state()
+            want = O.sweep(cfg, X, direction, Delta)
+            check_fields(cfg, got, want, 2e-6)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_steps_3d(precision, tol):
+    """40 full steps with the CFL dt from the device reduction, from the
+    seeded initial state of the 3D workload recipe."""
+    cfg = O.Config(nx=40, ny=24, nz=17, ndim=3, Ra=1e6, seed=2024, pert_amp=1e-2)
+    s = solver_for(cfg, precision)
+    try:
+        s.step(40)
+        got = s.state()
+        t_gpu, steps = s.time()
+        dt_gpu = s.dt()
+    finally:
+        s.close()
+    want, t_cpu, _ = O.step(cfg, O.init(cfg), 40)
+    assert steps == 40
+    assert abs(t_gpu - t_cpu) <= (1e-14 if precision == "fp64" else 1e-6) * t_cpu
+    assert abs(dt_gpu - O.dt(cfg, want)) <= (1e-14 if precision == "fp64" else 1e-6) * dt_gpu
+    check_fields(cfg, got, want, tol)
+
+
+def test_y_invariant_gpu_3d_matches_2d_oracle_small():
+    """y-independent data, m_y = 0: every y plane of the FP64 3D GPU result
+    equals the 2D oracle's result."""
+    c2 = O.Config(nx=44, nz=17, Ra=1e6, seed=8, pert_amp=1e-2)
+    c3 = O.Config(nx=44, ny=8, nz=17, ndim=3, Ra=1e6, seed=8, pert_amp=1e-2)
+    X2 = O.init(c2)
+    X3 = np.zeros(c3.shape)
+    for f, g in ((0, 0), (1, 1), (3, 2), (4, 3)):
+        X3[f] = X2[g][:, None, :]
+    s = solver_for(c3)
+    try:
+        s.set_state(X3)
+        s.step(25)
+        got = s.state()
+    finally:
+        s.close()
+    want, _, _ = O.step(c2, X2, 25)
+    assert np.all(got[2] == 0)
+    for f, g in ((0, 0), (1, 1), (3, 2), (4, 3)):
+        for j in range(c3.ny):
+            assert rel_l2(got[f][:, j, :], want[g]) <= 1e-13, (f, j)
+
+
+def _full_y_invariant_state(nx, ny, nz, seed):
+    c2 = O.Config(nx=nx, nz=nz, Ra=1e7, seed=seed, pert_amp=1e-2)
+    X2 = O.init(c2)
+    X3 = np.zeros((5, nz, ny, nx))
+    for f, g in ((0, 0), (1, 1), (3, 2), (4, 3)):
+        X3[f] = X2[g][:, None, :]
+    return c2, X2, X3
+
+
+def test_full_size_fp32_y_invariant_matches_2d_oracle():
+    """The 512 x 512 x 128 FP32 workload in the launch configuration the
+    benchmark times, on y-independent data: 5 steps, every y plane against
+    the 2D oracle (FP32 bar), m_y stays exactly zero, mass conserved."""
+    import paper_2411_10372_gb300 as cm
+    nx, ny, nz = 512, 512, 128
+    c2, X2, X3 = _full_y_invariant_state(nx, ny, nz, seed=31)
+    s = cm.Solver(nx, nz, 1e7, 1.0, 5.0 / 3.0, ny=ny, ndim=3, precision="fp32", pert_amp=1e-2, seed=31)
+    try:
+        X3 = X3.astype(np.float32).astype(np.float64)
+        s.set_state(X3)
+        s.step(5)
+        got = s.state()
+    finally:
+        s.close()
+    X2r = X3[[0, 1, 3, 4]][:, :, 0, :]
+    want, _, _ = O.step(c2, X2r, 5)
+    assert np.all(got[2] == 0)
+    w3 = np.stack([want[0], want[1], np.zeros_like(want[0]), want[2], want[3]])
+    for j in (0, 1, 255, 510, 511):
+        c3 = O.Config(nx=nx, ny=ny, nz=nz, ndim=3, Ra=1e7)
+        check_fields(c3, got[:, :, j:j + 1, :], w3[:, :, None, :], 1e-5)
+    spread = np.max(np.abs(got - got[:, :, :1, :]))
+    assert spread == 0.0
+    wz = np.ones(nz)
+    wz[0] = wz[-1] = 0.5
+    m0 = float(np.einsum("kji,k->", X3[0], wz))
+    m1 = float(np.einsum("kji,k->", got[0], wz))
+    assert abs(m1 - m0) <= 1e-6 * m0
+
+
+def test_full_size_fp32_shift_equivariance():
+    """Periodicity in x and y at the full 512 x 512 x 128 size: shifting the
+    stirred input by (3, 5) columns/rows shifts the 2-step FP32 result bit for
+    bit (every node runs the same arithmetic wherever its strip, warp group
+    or segment falls)."""
+    import paper_2411_10372_gb300 as cm
+    nx, ny, nz = 512, 512, 128
+    cfg = O.Config(nx=nx, ny=ny, nz=nz, ndim=3, Ra=1e7)
+    X = stirred_state_3d(cfg, seed=77, u_amp=0.05).astype(np.float32).astype(np.float64)
+    s = cm.Solver(nx, nz, 1e7, 1.0, 5.0 / 3.0, ny=ny, ndim=3, precision="fp32")
+    try:
+        s.set_state(X)
+        s.step(2)
+        a = s.state()
+        s.set_state(np.roll(X, (5, 3), axis=(2, 3)))
+        s.step(2)
+        b = s.state()
+    finally:
+        s.close()
+    assert np.all(np.isfinite(a))
+    assert np.array_equal(np.roll(a, (5, 3), axis=(2, 3)), b)

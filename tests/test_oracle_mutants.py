@@ -50,6 +50,8 @@ MUTANTS = [
     ("sound_speed_missing_gamma", "double c = sqrt(p->gam * p->a * w->T[n]);", "double c = sqrt(p->a * w->T[n]);"),
     ("perturb_plates", "if (k > 0 && k < p.nz - 1) T = Tc[k]", "T = Tc[k]"),
     ("potential_missing_in_T", "- p->g * zk(p, k));", ");"),
+    ("div_missing_dy", "double div = du[0][0] + du[1][1] + du[2][2];", "double div = du[0][0] + du[2][2];"),
+    ("y_tvd_rminus_row", "int j1 = (al == 1) ? (j + 1) % p->ny : j;", "int j1 = j;"),
 ]
 
 
@@ -64,6 +66,8 @@ def _pin_calls():
             continue
         if name == "test_tvd_reading_davis_split_form_is_tvd":
             calls += [(f"{name}[{c}]", (lambda c=c, fn=fn: fn(c))) for c in (0.1, 0.2, 0.25, 0.4)]
+        elif name == "test_xy_exchange_symmetry_3d":
+            calls += [(f"{name}[{d}]", (lambda d=d, m=m, fn=fn: fn(d, m))) for d, m in ((1, 0), (0, 1), (2, 2))]
         elif name == "test_sound_damping_pins_stokes_reading":
             calls += [(f"{name}[-]", lambda fn=fn: fn(-2.0 / 3.0, True)),
                       (f"{name}[+]", lambda fn=fn: fn(2.0 / 3.0, False))]
