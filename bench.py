@@ -240,6 +240,37 @@ def run_gpu(args):
                              for k, v in kinds3.items()},
                 "l2": "flushed before every timed step (256 MiB memset)"}
 
+    # ---- adjoint: 1024 x 256, Ra = 1e8, FP64, 2000 steps, checkpoints every
+    # 100, J = mean Nu_bar over steps 1501..2000; cost of the reverse pass
+    # (recompute + vector-Jacobian products) over that of the plain forward ----
+    adjoint = None
+    if not args.no_adjoint:
+        na, ka, wa = args.adjoint_steps, max(1, args.adjoint_steps // 20), args.adjoint_steps * 3 // 4 + 1
+        sa = cm.Solver(1024, 256, 1e8, PR, GAMMA, precision="fp64", stream=stream, seed=99 + rank)
+        sa.step(2)
+        sa.sync()
+        t0 = time.perf_counter()
+        sa.step(na)
+        sa.sync()
+        t_fwd = time.perf_counter() - t0
+        sa.close()
+        sa = cm.Solver(1024, 256, 1e8, PR, GAMMA, precision="fp64", stream=stream, seed=99 + rank)
+        sa.step(2)
+        sa.sync()
+        l0 = cm.cm_launch_count()
+        t0 = time.perf_counter()
+        Ja = cm.cm_adj_forward(na, ka, wa)
+        t_afwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        gRa = cm.cm_adj_backward(None, None)
+        t_bwd = time.perf_counter() - t0
+        nla = cm.cm_launch_count() - l0
+        sa.close()
+        adjoint = {"workload": "2d_aspect4_1024x256_Ra1e8_fp64_adjoint", "steps": na, "K": ka, "window": [wa, na],
+                   "J": Ja, "dJ_dRa": gRa, "forward_s": t_fwd, "adj_forward_s": t_afwd, "backward_s": t_bwd,
+                   "ratio_backward_over_forward": t_bwd / t_fwd, "gpu_launches": nla,
+                   "timing": "host wall clock around blocking calls"}
+
     # ---- FP64 state, same workload ----
     k64 = max(3, min(args.steps, 20))
     s64, r64 = measure("fp64", k64, min(args.warmup, 3), clocks=False)
@@ -275,6 +306,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 128, "steps": n_e2e},
         "batch": batch,
         "box3d": box3,
+        "adjoint": adjoint,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": r64["total_ms"] / k64, "steps": k64,
                  "sweep_ms": [round(x, 5) for x in r64["sweep_ms"]], "gpu_launches": r64["launches"],
                  "roofline_hbm": roofline(r64)},
@@ -343,6 +375,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--steps-3d", type=int, default=200)
     ap.add_argument("--nx", type=int, default=NX, help="grid override (profiling captures only)")
     ap.add_argument("--nz", type=int, default=NZ, help="grid override (profiling captures only)")

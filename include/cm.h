@@ -248,6 +248,42 @@ int cm_diag_noalloc(const void* state, int precision, const cm_grid* grid, int p
                     double gamma, const cm_params* params, double t, double dt, long long step, void* stream,
                     cm_diag* out);
 
+/* ---- Adjoint: gradients of a time-averaged plate Nusselt number ----
+ * J = (1/N_w) sum over steps n = win_begin..nsteps of Nu_bar(X^n), Nu_bar =
+ * (Nu_0 + Nu_1)/2 of Eq. mean_Nu (second-order one-sided plate differences
+ * of the plane-averaged temperature, as cm_diag.Nu_bar), X^n the state after
+ * step n of the run started by cm_adj_forward.  Each step's dt is a constant
+ * of J (the CFL dt the forward run took; dt is not differentiated).
+ * Reverse mode of Sec. 3.1's sweeps, hand-written, with non-smooth points
+ * taking fixed one-sided derivatives: phi'(r) = 2 on 0 < 2r < 1 else 0,
+ * d|u|/du = 0 at u = 0, the Co(1 - Co) branch at Co = 1/2, and on a tie in
+ * max(A_k, A_k+1) the first argument.  2D FP64 contexts only (CM_EINVAL
+ * otherwise). */
+
+/* Run nsteps steps from the current state (advancing it, t and the step
+ * count as cm_step does), record each step's dt, keep a device copy of the
+ * state every K steps (ceil(nsteps/K) states), and write J (host) once the
+ * run is done.  1 <= win_begin <= nsteps.  Blocking.  The reverse pass later
+ * holds 4K+1 more states and recomputes each K-step segment: K trades memory
+ * for recomputation.  K = 0 keeps every sweep input of this run instead
+ * (4 nsteps + 1 states, e.g. 67 GB for 2000 steps of 1024 x 256) and the
+ * reverse pass recomputes nothing.  The diagnostics ring is not sampled
+ * during a K = 0 run. */
+int cm_adj_forward(int nsteps, int K, int win_begin, double* J);
+
+/* Reverse pass of the last cm_adj_forward: recompute each K-step segment
+ * from its checkpoint (same kernels, same dt: bit-identical states; nothing
+ * to recompute when K = 0), then apply the vector-Jacobian products of the
+ * sweeps in reverse order.
+ * Outputs (each may be NULL; host or device pointers):
+ *   grad_X0  dJ/dX^0, dense float64 in the cm_get_state layout (4 fields);
+ *   grad_T0  dJ/dT at the interior nodes of X^0 for a temperature change at
+ *            fixed pressure and velocity (the isobaric perturbation of the
+ *            initial condition), dense float64 [nz][nx], 0 on the plates;
+ *   grad_Ra  dJ/dRa through mu = sqrt(Pr/Ra) and K = 1/(eps D sqrt(Ra Pr)).
+ * Blocking; may be called again (it recomputes from the checkpoints). */
+int cm_adj_backward(double* grad_X0, double* grad_T0, double* grad_Ra);
+
 /* Free the context and its device memory (not caller-owned state_buf). */
 int cm_finalize(void);
 

@@ -74,6 +74,8 @@ _SIGS = {
     "cm_sync": (ctypes.c_int, []),
     "cm_save": (ctypes.c_int, [ctypes.c_char_p]),
     "cm_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cm_adj_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "cm_adj_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "cm_diag_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(cm_grid), ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(cm_params),
                                        ctypes.c_double, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p,
@@ -236,6 +238,32 @@ def cm_diag_noalloc(state_ptr: int, precision: int, grid: cm_grid, pitch: int, R
                                  float(Ra), float(Pr), float(gamma), ctypes.byref(params), float(t), float(dt),
                                  int(step), ctypes.c_void_p(stream) if stream else None, ctypes.byref(d)))
     return d.as_dict()
+
+
+def _any_ptr(a):
+    """Host numpy float64 array, a CUDA tensor (its data pointer) or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return _dp(a)
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous() and str(a.dtype) == "torch.float64"
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("expected a float64 numpy array or torch tensor")
+
+
+def cm_adj_forward(nsteps: int, K: int, win_begin: int) -> float:
+    """Forward run for the adjoint; returns J (see include/cm.h)."""
+    J = ctypes.c_double()
+    _check(lib().cm_adj_forward(int(nsteps), int(K), int(win_begin), ctypes.byref(J)))
+    return J.value
+
+
+def cm_adj_backward(grad_X0=None, grad_T0=None) -> float:
+    """Reverse pass; fills grad_X0 / grad_T0 (host arrays or CUDA tensors) and returns dJ/dRa."""
+    g = ctypes.c_double()
+    _check(lib().cm_adj_backward(_any_ptr(grad_X0), _any_ptr(grad_T0), ctypes.byref(g)))
+    return g.value
 
 
 _batch_n = 0

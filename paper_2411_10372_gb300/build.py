@@ -24,6 +24,8 @@ UNITS = {
     "diag_noalloc.cu": ["-Xcompiler", "-ffp-contract=off"],
     "batch.cu": ["-Xcompiler", "-ffp-contract=off"],
     "kernels_f64.cu": ["--fmad=false"],
+    # reverse mode: recomputed intermediates round as the forward kernels do
+    "adjoint.cu": ["--fmad=false", "-Xcompiler", "-ffp-contract=off"],
     # FP32: FMA contraction, approximate division and square root
     "kernels_f32.cu": ["--fmad=true", "-prec-div=false", "-prec-sqrt=false"],
 }

@@ -7,6 +7,7 @@
 // slots) and read by the next step's sweeps, so the host never waits on it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,12 +15,24 @@
 #include <vector>
 
 #include "../../include/cm.h"
+#include "adjoint.h"
 #include "host_setup.h"
 #include "kernels.h"
 
 using namespace cm;
 
 namespace {
+
+// state of the adjoint (cm_adj_forward / cm_adj_backward)
+struct AdjCtx {
+    int nsteps = 0, K = 0, win = 0;
+    std::vector<double> dts;        // dt of each forward step (host)
+    std::vector<double> plane_sums; // sum over x of T on planes 0, 1, 2, K, K-1, K-2 per window step
+    char* ckpt = nullptr;           // device: state at steps 0, K, 2K, ... (K = 0: every sweep input)
+    double* dts_d = nullptr;
+    double* planes_d = nullptr;
+    double J = 0.0;
+};
 
 struct Ctx {
     cm_grid grid;
@@ -48,6 +61,7 @@ struct Ctx {
     Coef<double> cd;
     Coef<float> cf;
     double a, b, g, cs2;
+    AdjCtx* adj;
 };
 
 Ctx* g_ctx = nullptr;
@@ -93,6 +107,12 @@ void free_ctx(Ctx* c)
     cudaFree(c->scratch);
     cudaFree(c->dense);
     cudaFree(c->ring);
+    if (c->adj) {
+        cudaFree(c->adj->ckpt);
+        cudaFree(c->adj->dts_d);
+        cudaFree(c->adj->planes_d);
+        delete c->adj;
+    }
     delete c;
 }
 
@@ -683,6 +703,220 @@ int cm_load(const char* path)
     h.steps = (double)H.step;
     CK(cudaMemcpyAsync(c->ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+// planes of the plate Nusselt differences and the weights of dNu_bar/d(sum_x T)
+// (Eq. mean_Nu: Nu_0 = -(1/eps)(-3 f_0 + 4 f_1 - f_2)/(2 dz), Nu_1 = -(1/eps)(3 g_0 -
+// 4 g_1 + g_2)/(2 dz), f_q, g_q the x-mean of T minus 1 - D z at planes q and K-q)
+static void nu_planes(const Ctx* c, int kq[6], double wq[6])
+{
+    const int K = c->grid.nz - 1;
+    const double dz = 1.0 / K, s = -(1.0 / c->prm.eps) / (2.0 * dz) / (double)c->grid.nx;
+    const int k6[6] = {0, 1, 2, K, K - 1, K - 2};
+    const double c6[6] = {-3.0, 4.0, -1.0, 3.0, -4.0, 1.0};
+    for (int q = 0; q < 6; ++q) {
+        kq[q] = k6[q];
+        wq[q] = 0.5 * s * c6[q];
+    }
+}
+
+static double nu_bar_of(const Ctx* c, const double* S)
+{
+    const int K = c->grid.nz - 1;
+    const double nx = (double)c->grid.nx, D = c->prm.D, eps = c->prm.eps, dz = 1.0 / K;
+    double f[3], g[3];
+    for (int q = 0; q < 3; ++q) {
+        f[q] = S[q] / nx - (1.0 - D * ((double)q / (double)K));
+        g[q] = S[3 + q] / nx - (1.0 - D * ((double)(K - q) / (double)K));
+    }
+    const double nb = -(1.0 / eps) * (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz);
+    const double nt = -(1.0 / eps) * (3.0 * g[0] - 4.0 * g[1] + g[2]) / (2.0 * dz);
+    return (nb + nt) / 2.0;
+}
+
+int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
+{
+    NEED_CTX();
+    Ctx* c = g_ctx;
+    if (c->prec != CM_FP64 || c->grid.ndim != 2) return fail(CM_EINVAL, "the adjoint needs a 2D FP64 context");
+    if (nsteps < 1 || K < 0 || win_begin < 1 || win_begin > nsteps)
+        return fail(CM_EINVAL, "need nsteps >= 1, K >= 0, 1 <= win_begin <= nsteps");
+    if (!c->adj) c->adj = new AdjCtx();
+    AdjCtx* A = c->adj;
+    cudaFree(A->ckpt);
+    cudaFree(A->dts_d);
+    cudaFree(A->planes_d);
+    A->ckpt = nullptr;
+    A->dts_d = A->planes_d = nullptr;
+    A->nsteps = 0;
+    // K = 0: the forward sweeps write into 4 nsteps + 1 stored states, which the
+    // reverse pass reads without recomputing anything
+    const bool keep_all = K == 0;
+    const int nck = keep_all ? 4 * nsteps + 1 : (nsteps + K - 1) / K, nwin = nsteps - win_begin + 1;
+    if (cudaMalloc(&A->ckpt, (size_t)nck * c->buf_bytes) != cudaSuccess ||
+        cudaMalloc(&A->dts_d, (size_t)nsteps * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&A->planes_d, (size_t)nwin * 6 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CM_ENOMEM, "adjoint forward: cudaMalloc of %zu checkpoint bytes failed", (size_t)nck * c->buf_bytes);
+    }
+    int kq[6];
+    double wq[6];
+    nu_planes(c, kq, wq);
+    auto stored = [&](int q) { return (double*)(A->ckpt + (size_t)q * c->buf_bytes); };
+    if (keep_all) CK(cudaMemcpyAsync(stored(0), c->buf[c->cur], c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    const int order[4] = {2, 0, 2, 0};
+    for (int s = 0; s < nsteps; ++s) {
+        if (!keep_all && s % K == 0)
+            CK(cudaMemcpyAsync(stored(s / K), c->buf[c->cur], c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        cudaError_t e = adj_record_dt(c->ctl, (int)(c->step & 1), c->prm.cfl, c->prm.dt_fixed, A->dts_d + s, c->stream);
+        if (e != cudaSuccess) return fail(CM_ECUDA, "adjoint forward: %s", cudaGetErrorString(e));
+        if (keep_all) {  // the step of queue_steps, each sweep into its own stored state
+            SweepCtl sc;
+            std::memset(&sc, 0, sizeof sc);
+            sc.ctl = c->ctl;
+            sc.slot_in = (int)(c->step & 1);
+            for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+                sc.first = q == 0;
+                sc.last = q == 3;
+                e = Launch<double>::sweep(order[q], stored(4 * s + q), stored(4 * s + q + 1),
+                                          (const double*)c->zt_r, c->cd, sc, c->seg_rows, c->stream);
+                c->launches++;
+            }
+            if (e != cudaSuccess) return fail(CM_ECUDA, "adjoint forward: %s", cudaGetErrorString(e));
+            c->step++;
+        } else {
+            int rc = queue_steps(c, 1);
+            if (rc) return rc;
+        }
+        const double* Xn = keep_all ? stored(4 * s + 4) : (const double*)c->buf[c->cur];
+        if (s + 1 >= win_begin) {
+            e = adj_plane_T(Xn, c->zt_d, c->cd, kq, 6, A->planes_d + (size_t)(s + 1 - win_begin) * 6, c->stream);
+            if (e != cudaSuccess) return fail(CM_ECUDA, "adjoint forward: %s", cudaGetErrorString(e));
+        }
+        c->launches += 2;
+    }
+    if (keep_all)
+        CK(cudaMemcpyAsync(c->buf[c->cur], stored(4 * nsteps), c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    A->dts.assign(nsteps, 0.0);
+    A->plane_sums.assign((size_t)nwin * 6, 0.0);
+    CK(cudaMemcpyAsync(A->dts.data(), A->dts_d, nsteps * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(A->plane_sums.data(), A->planes_d, (size_t)nwin * 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double sum = 0.0;
+    for (int q = 0; q < nwin; ++q) sum += nu_bar_of(c, A->plane_sums.data() + (size_t)q * 6);
+    A->J = sum / nwin;
+    A->nsteps = nsteps;
+    A->K = K;
+    A->win = win_begin;
+    if (J) *J = A->J;
+    return CM_OK;
+}
+
+int cm_adj_backward(double* grad_X0, double* grad_T0, double* grad_Ra)
+{
+    NEED_CTX();
+    Ctx* c = g_ctx;
+    AdjCtx* A = c->adj;
+    if (!A || A->nsteps < 1) return fail(CM_EINVAL, "cm_adj_backward needs a cm_adj_forward first");
+    const bool keep_all = A->K == 0;
+    const int K = keep_all ? A->nsteps : A->K, nsteps = A->nsteps, nwin = nsteps - A->win + 1;
+    const int nck = keep_all ? 1 : (nsteps + K - 1) / K;
+    const size_t bb = c->buf_bytes;
+    char* slots = nullptr;   // 4K+1 sweep inputs of one segment
+    char* xbar = nullptr;    // two adjoint states
+    double* acc = nullptr;   // dJ/dmu, dJ/dK
+    double* gT = nullptr;    // dense dJ/dT
+    AdjWork W;
+    std::memset(&W, 0, sizeof W);
+    int rc = CM_OK;
+    auto cleanup = [&]() {
+        cudaFree(slots);
+        cudaFree(xbar);
+        cudaFree(acc);
+        cudaFree(gT);
+        adj_work_free(&W);
+    };
+    if ((!keep_all && cudaMalloc(&slots, (size_t)(4 * K + 1) * bb) != cudaSuccess) ||
+        cudaMalloc(&xbar, 2 * bb) != cudaSuccess ||
+        cudaMalloc(&acc, 2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&gT, (size_t)c->grid.nx * c->grid.nz * sizeof(double)) != cudaSuccess ||
+        adj_work_create(&W, c->cd) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(CM_ENOMEM, "adjoint backward: cudaMalloc of %zu bytes of sweep inputs failed",
+                    (size_t)(4 * K + 1) * bb);
+    }
+    char* base = keep_all ? A->ckpt : slots;
+    auto slot = [&](int q) { return (double*)(base + (size_t)q * bb); };
+    int xc = 0;
+    auto xb = [&](int q) { return (double*)(xbar + (size_t)q * bb); };
+    int kq[6];
+    double wq[6];
+    nu_planes(c, kq, wq);
+    for (int q = 0; q < 6; ++q) wq[q] /= (double)nwin;
+    const int order[4] = {2, 0, 2, 0};
+    cudaError_t e = cudaMemsetAsync(xbar, 0, 2 * bb, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), c->stream);
+    for (int j = nck - 1; j >= 0 && e == cudaSuccess; --j) {
+        const int s0 = j * K, s1 = std::min(nsteps, s0 + K) - 1;
+        // recompute the segment, keeping every sweep input (stored already when K = 0)
+        if (!keep_all) e = cudaMemcpyAsync(slot(0), A->ckpt + (size_t)j * bb, bb, cudaMemcpyDeviceToDevice, c->stream);
+        for (int s = s0; s <= s1 && e == cudaSuccess && !keep_all; ++s) {
+            SweepCtl sc;
+            std::memset(&sc, 0, sizeof sc);
+            sc.ctl = c->ctl;
+            sc.Delta = 0.5 * A->dts[s];
+            for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+                const int at = 4 * (s - s0) + q;
+                e = Launch<double>::sweep(order[q], slot(at), slot(at + 1), (const double*)c->zt_r, c->cd, sc,
+                                          c->seg_rows, c->stream);
+                c->launches++;
+            }
+        }
+        // reverse, step by step
+        for (int s = s1; s >= s0 && e == cudaSuccess; --s) {
+            const double Delta = 0.5 * A->dts[s];
+            if (s + 1 >= A->win) {
+                e = adj_seed_T(xb(xc), slot(4 * (s - s0) + 4), c->zt_d, c->cd, kq, wq, 6, c->stream);
+                c->launches++;
+            }
+            for (int q = 3; q >= 0 && e == cudaSuccess; --q) {
+                e = adj_sweep_vjp(&W, order[q], Delta, slot(4 * (s - s0) + q), xb(xc), xb(xc ^ 1), c->zt_d, c->cd,
+                                  acc, c->stream);
+                c->launches += 11;
+                xc ^= 1;
+            }
+        }
+    }
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(CM_ECUDA, "adjoint backward: %s", cudaGetErrorString(e));
+    }
+    if (grad_X0) {
+        if ((rc = ensure_dense(c))) { cleanup(); return rc; }
+        e = Launch<double>::unpack(xb(xc), c->dense, c->cd, c->nf, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(grad_X0, c->dense, dense_count(c) * sizeof(double), cudaMemcpyDefault, c->stream);
+        c->launches++;
+    }
+    if (grad_T0 && e == cudaSuccess) {
+        e = adj_grad_T((const double*)A->ckpt, xb(xc), c->zt_d, c->cd, gT, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(grad_T0, gT, (size_t)c->grid.nx * c->grid.nz * sizeof(double), cudaMemcpyDefault,
+                                c->stream);
+        c->launches++;
+    }
+    double hacc[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, acc, sizeof hacc, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail(CM_ECUDA, "adjoint backward: %s", cudaGetErrorString(e));
+    if (grad_Ra) {
+        const double mu = std::sqrt(c->Pr / c->Ra), kth = 1.0 / (c->prm.eps * c->prm.D * std::sqrt(c->Ra * c->Pr));
+        *grad_Ra = hacc[0] * (-0.5 * mu / c->Ra) + hacc[1] * (-0.5 * kth / c->Ra);
+    }
     return CM_OK;
 }
 

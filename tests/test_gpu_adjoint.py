@@ -1,0 +1,202 @@
+"""The library's adjoint (cm_adj_forward / cm_adj_backward, FP64 2D) against
+torch.autograd on oracle/torch_ref.py, whose states and gradients are pinned
+to the C oracle (tests/test_torch_ref_pins.py).
+
+Bars: J equal within 1e-12 (the GPU forward is the oracle's arithmetic); the
+gradients dJ/dX^0 (relative L2 per field), dJ/dT0 and dJ/dRa within 1e-9
+(reverse mode in a different association order; the flow's sensitivity
+magnifies rounding by a few orders over the run).  Gradients do not depend
+on the checkpoint interval (bit for bit: the recomputed segments are
+bit-identical; also when every sweep input is kept instead).  At the full
+1024 x 256 size a directional derivative
+matches central finite differences of the GPU forward.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle.torch_ref import Model, isobaric_state
+
+pytestmark = pytest.mark.gpu
+
+
+def _model(cfg):
+    return Model(cfg.nx, cfg.nz, Pr=cfg.Pr, gamma=cfg.gamma, eps=cfg.eps, D=cfg.D, aspect=cfg.aspect,
+                 gravity=cfg.gravity, t_bot=cfg.t_bot, t_top=cfg.t_top, stokes=cfg.stokes, tvd_form=cfg.tvd_form)
+
+
+def _solver(cfg):
+    import paper_2411_10372_gb300 as cm
+    t_top = (1.0 - cfg.eps - cfg.D) if cfg.t_top is None else cfg.t_top
+    return cm.Solver(cfg.nx, cfg.nz, cfg.Ra, cfg.Pr, cfg.gamma, aspect=cfg.aspect, precision="fp64", eps=cfg.eps,
+                     D=cfg.D, cfl=cfg.cfl, dt_fixed=cfg.dt_fixed, gravity=cfg.gravity, t_bot=cfg.t_bot,
+                     t_top=t_top, pert_amp=cfg.pert_amp, stokes=cfg.stokes, seed=cfg.seed, tvd_form=cfg.tvd_form)
+
+
+def _gpu_gradients(cfg, nsteps, K, win, X0=None):
+    import paper_2411_10372_gb300 as cm
+    s = _solver(cfg)
+    try:
+        if X0 is not None:
+            s.set_state(X0)
+        J = cm.cm_adj_forward(nsteps, K, win)
+        gX = np.empty((4, cfg.nz, cfg.nx))
+        gT = np.empty((cfg.nz, cfg.nx))
+        gRa = cm.cm_adj_backward(gX, gT)
+    finally:
+        s.close()
+    return J, gX, gT, gRa
+
+
+def _torch_gradients(cfg, X0, nsteps, win):
+    """J and its gradients by autograd, with the oracle's CFL dts (which the
+    FP64 GPU forward reproduces bit for bit)."""
+    X, dts = X0, []
+    for _ in range(nsteps):
+        X, _, d = O.step(cfg, X, 1)
+        dts.append(float(d[0]))
+    m = _model(cfg)
+    rho = X0[0]
+    ux, uz = X0[1] / rho, X0[2] / rho
+    z = m.z.numpy()
+    T0 = m.b * (X0[3] / rho - 0.5 * (ux * ux + uz * uz) - m.g * z)
+    P0 = m.a * rho * T0
+    X0t = torch.tensor(X0, requires_grad=True)
+    Ra = torch.tensor(cfg.Ra, dtype=torch.float64, requires_grad=True)
+    J = m.objective(X0t, Ra, dts, win)
+    gX, gRa = torch.autograd.grad(J, [X0t, Ra])
+    T0t = torch.tensor(T0, requires_grad=True)
+    Xi = isobaric_state(m, T0t, torch.from_numpy(P0), torch.from_numpy(ux), torch.from_numpy(uz))
+    gT, = torch.autograd.grad(m.objective(Xi, cfg.Ra, dts, win), [T0t])
+    gT = gT.numpy().copy()
+    gT[0] = gT[-1] = 0.0
+    return float(J.detach()), gX.numpy(), gT, float(gRa)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("tvd", [O.TVD_SPLIT, O.TVD_SUM, O.TVD_OFF])
+def test_adjoint_matches_autograd(tvd):
+    cfg = O.Config(nx=32, nz=9, Ra=3e5, seed=21, pert_amp=3e-2, tvd_form=tvd)
+    nsteps, K, win = 30, 7, 21
+    X0 = O.init(cfg)
+    J, gX, gT, gRa = _gpu_gradients(cfg, nsteps, K, win)
+    Jt, gXt, gTt, gRat = _torch_gradients(cfg, X0, nsteps, win)
+    assert abs(J - Jt) <= 1e-12 * abs(Jt)
+    for f in range(4):
+        assert _rel(gX[f], gXt[f]) <= 1e-9, (f, _rel(gX[f], gXt[f]))
+    assert _rel(gT, gTt) <= 1e-9
+    assert np.all(gT[0] == 0) and np.all(gT[-1] == 0)
+    assert abs(gRa - gRat) <= 1e-9 * abs(gRat)
+
+
+def test_adjoint_on_a_stirred_state():
+    """Every branch of the scheme active: random velocities, odd sizes, x-sweep
+    TVD at both signs of the ratios."""
+    from test_gpu_parity import stirred_state
+    cfg = O.Config(nx=29, nz=11, Ra=1e5, seed=4)
+    X0 = stirred_state(cfg, seed=8, u_amp=0.2, t_amp=0.03)
+    nsteps, K, win = 12, 5, 1
+    J, gX, gT, gRa = _gpu_gradients(cfg, nsteps, K, win, X0)
+    Jt, gXt, gTt, gRat = _torch_gradients(cfg, X0, nsteps, win)
+    assert abs(J - Jt) <= 1e-12 * abs(Jt)
+    for f in range(4):
+        assert _rel(gX[f], gXt[f]) <= 1e-9, (f, _rel(gX[f], gXt[f]))
+    assert abs(gRa - gRat) <= 1e-9 * abs(gRat)
+
+
+def test_gradients_do_not_depend_on_checkpoint_interval():
+    cfg = O.Config(nx=40, nz=13, Ra=1e6, seed=2, pert_amp=2e-2)
+    ref = None
+    for K in (1, 6, 25, 0):  # 0: every sweep input kept, nothing recomputed
+        J, gX, gT, gRa = _gpu_gradients(cfg, 25, K, 11)
+        if ref is None:
+            ref = (J, gX, gT, gRa)
+        else:
+            assert J == ref[0] and gRa == ref[3]
+            assert np.array_equal(gX, ref[1]) and np.array_equal(gT, ref[2])
+
+
+def test_backward_can_repeat_and_rejects_misuse():
+    import paper_2411_10372_gb300 as cm
+    cfg = O.Config(nx=32, nz=9, Ra=1e5)
+    s = _solver(cfg)
+    try:
+        with pytest.raises(cm.CMError):
+            cm.cm_adj_backward(None, None)
+        with pytest.raises(cm.CMError):
+            cm.cm_adj_forward(10, 3, 11)
+        with pytest.raises(cm.CMError):
+            cm.cm_adj_forward(10, -1, 5)
+        cm.cm_adj_forward(10, 3, 5)
+        g1, g2 = cm.cm_adj_backward(None, None), cm.cm_adj_backward(None, None)
+        assert g1 == g2 and g1 != 0.0
+    finally:
+        s.close()
+    s = cm.Solver(32, 9, 1e5, precision="fp32")
+    try:
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_adj_forward(4, 2, 1)
+        assert e.value.code == cm.CM_EINVAL
+    finally:
+        s.close()
+
+
+def test_autograd_function_wraps_the_library():
+    import paper_2411_10372_gb300 as cm
+    from paper_2411_10372_gb300.adjoint import NuObjective
+    cfg = O.Config(nx=32, nz=9, Ra=3e5, seed=21, pert_amp=3e-2)
+    X0 = O.init(cfg)
+    J, gX, gT, gRa = _gpu_gradients(cfg, 20, 6, 11)
+    X0t = torch.tensor(X0, requires_grad=True)
+    Ra = torch.tensor(cfg.Ra, dtype=torch.float64, requires_grad=True)
+    Jf = NuObjective.apply(X0t, Ra, dict(nx=32, nz=9, Pr=1.0, gamma=5.0 / 3.0), 20, 6, 11)
+    Jf.backward()
+    assert float(Jf) == J
+    assert np.array_equal(X0t.grad.numpy(), gX)
+    assert float(Ra.grad) == gRa
+    del cm
+
+
+@pytest.mark.parametrize("tvd,tol", [(O.TVD_OFF, 1e-8), (O.TVD_SPLIT, 1e-4)])
+def test_full_size_directional_derivative(tvd, tol):
+    """1024 x 256, Ra = 1e8, FP64 (the adjoint workload's grid): 40 steps at a
+    fixed dt, window 21..40; the adjoint's <dJ/dT0, v> against central
+    differences of J from two more GPU forward runs.  Without the TVD term J
+    is smooth and the difference agrees to 1e-8; with it, a difference of
+    step 1e-5 crosses corners of the limiter (phi at 2r = 0 and 1, C at
+    Co = 1/2) at some of the 2.6e5 nodes, which costs ~1e-5 (measured:
+    1e-5 to 1e-7, not monotone in the step), hence 1e-4."""
+    import paper_2411_10372_gb300 as cm
+    base = O.Config(nx=1024, nz=256, Ra=1e8, seed=12345, tvd_form=tvd)
+    X0 = O.init(base)
+    dt = 0.8 * O.dt(base, X0)
+    cfg = O.Config(nx=1024, nz=256, Ra=1e8, seed=12345, dt_fixed=dt, tvd_form=tvd)
+    nsteps, K, win = 40, 10, 21
+    J, gX, gT, gRa = _gpu_gradients(cfg, nsteps, K, win, X0)
+    rng = np.random.default_rng(99)
+    v = np.zeros((cfg.nz, cfg.nx))
+    v[1:-1] = rng.uniform(-1, 1, (cfg.nz - 2, cfg.nx))
+    m = _model(cfg)
+    rho = X0[0]
+    T0 = m.b * (X0[3] / rho - m.g * m.z.numpy())
+    P0 = m.a * rho * T0
+    h = 1e-5
+    Js = []
+    for sgn in (1.0, -1.0):
+        Xs = isobaric_state(m, torch.from_numpy(T0 + sgn * h * v), torch.from_numpy(P0)).numpy()
+        s = _solver(cfg)
+        try:
+            s.set_state(Xs)
+            Js.append(cm.cm_adj_forward(nsteps, K, win))
+        finally:
+            s.close()
+    fd = (Js[0] - Js[1]) / (2 * h)
+    ad = float(np.sum(gT * v))
+    assert math.isfinite(ad) and abs(ad) > 1.0
+    assert abs(fd - ad) <= tol * abs(ad), (fd, ad)
