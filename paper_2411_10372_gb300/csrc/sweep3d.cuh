@@ -4,13 +4,20 @@
 // Geometry (a 2.5D march).  Lanes span x (a strip of 32 columns, 28 output
 // columns, periodic).  The NW warps of a block span the third direction W
 // (y for the z and x sweeps, z for the y sweep), one row each; the block's
-// outer two warps on each side are halo: their X^P and primitives feed the
-// cross derivatives of the inner NW-4 warps, which alone store.  Every warp
-// marches along the march direction M (z for the z and x sweeps, y for the y
-// sweep) through a segment of rows, keeping rows in flight in registers as
-// the 2D kernels do.  Cross derivatives along x come from lane shuffles,
-// along W from a shared-memory exchange (two block barriers per row), along
-// M from the register pipeline.
+// outer two warps on each side are halo and alone the inner NW-4 store.
+// Every warp marches along the march direction M (z for the z and x sweeps,
+// y for the y sweep) through a segment of rows, keeping rows in flight in
+// registers as the 2D kernels do, with the next row's state loaded one
+// iteration ahead.  Cross derivatives along x come from lane shuffles, along
+// M from the register pipeline, and along W from one shared-memory exchange
+// per row (double-buffered by row parity, so one block barrier per row) of
+// the velocity components the fluxes need, of X at the newest row and of
+// X^P one row behind.
+//
+// Halo roles: the outermost warps (role 0) only supply primitives of X; the
+// next ones (role 1) also compute F^n, X^P and its primitives, which the
+// output warps' F^P cross derivatives read; output warps (role 2) run the
+// whole pipeline.
 #pragma once
 #include "sweep3d_common.cuh"
 
@@ -39,22 +46,29 @@ __device__ __forceinline__ int wrap(int a, int n)
     return a < 0 ? a + n : a;
 }
 
+template <int NW>
+__device__ __forceinline__ int halo_role(int w)
+{
+    return (w == 0 || w == NW - 1) ? 0 : ((w == 1 || w == NW - 2) ? 1 : 2);
+}
+
 // L_z (AL = 2: march z, W = y) or L_y (AL = 1: march y, W = z).
-// Row pipeline at step j (row j of the march just loaded), as in sweep_z2d:
-// F^n_{j-1}, X^P_{j-1}, F^P_{j-1}, average at j-2, TVD flux across
-// (j-2, j-1), output row j-2.  Plates: for L_z at the ends of the march
-// (half-cell density, m = 0, T = T_w); for L_y the plate planes are rows of
-// W and pass through unchanged.
+// Row pipeline at step j (row j of the march just taken from the prefetch),
+// as in sweep_z2d: F^n_{j-1}, X^P_{j-1}, F^P_{j-1}, average at j-2, TVD flux
+// across (j-2, j-1), output row j-2.  Plates: for L_z at the ends of the
+// march (half-cell density, m = 0, T = T_w); for L_y the plate planes are
+// rows of W and pass through unchanged.
 template <class R, int AL, int NW>
 __global__ void __launch_bounds__(NW * 32)
 sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 {
     constexpr int WD = (AL == 2) ? 1 : 2;  // direction of the warps
-    __shared__ R xw[2][NW][32];             // u_AL, u_W of X at the current row, per warp
-    __shared__ R pw[2][NW][32];             // the same for X^P
+    // [row parity][u_AL, u_W of X at row j; u_AL, u_W of X^P at row j-1][warp][lane]
+    __shared__ R xs[2][4][NW][32];
 
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
+    const int role = halo_role<NW>(w);
     const int strip = blockIdx.x;
     const int cw = blockIdx.y * (NW - 4) - 2 + w;      // W coordinate of this warp
     const int ks = blockIdx.z * io.seg;                 // first output row of the segment
@@ -83,35 +97,32 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
         sc.ctl->steps += 1.0;
     }
 
-    // march row j -> memory row and z of that row
-    auto row_of = [&](int j, long long& off, R& z) {
-        if (AL == 2) {
-            const int k = min(max(j, 0), nz - 1);
-            off = off3(k, cwr, ny, pitch, ic);
-            z = io.zt[k];
-        } else {
-            off = off3(cwr, wrap(j, ny), ny, pitch, ic);
-            z = io.zt[cwr];
-        }
+    // memory offset of march row j: plane clamp(j) of row cwr (L_z), row
+    // wrap(j) of plane cwr (L_y); rows are taken in order from j0 - 1 on
+    const long long colbase = (AL == 2) ? (long long)cwr * pitch + ic : (long long)cwr * ny * pitch + ic;
+    const long long rstride = (AL == 2) ? (long long)ny * pitch : (long long)pitch;
+    const int j0 = ks - 2;
+    int jl = j0 - 1;                             // next row to load
+    int jw = (AL == 1) ? wrap(jl, ny) : 0;      // its wrapped index (L_y)
+    const R zc = io.zt[cwr];
+    auto load_next = [&](S3<R>& X, R& z) {
+        const int r = (AL == 2) ? min(max(jl, 0), nz - 1) : jw;
+        X = s3_load(io.in, fs, colbase + r * rstride);
+        z = (AL == 2) ? io.zt[r] : zc;
+        ++jl;
+        if (AL == 1) jw = (jw + 1 == ny) ? 0 : jw + 1;
     };
-    // exchange of two per-lane values with the neighbouring warps (rows W +- 1):
-    // returns their central differences along W; every thread of the block calls it
-    auto exchangeW = [&](R (&buf)[2][NW][32], R a, R b, R& da, R& db) {
-        buf[0][w][lane] = a;
-        buf[1][w][lane] = b;
-        __syncthreads();
-        const int wu = min(w + 1, NW - 1), wd = max(w - 1, 0);
-        da = d3(buf[0][wu][lane], buf[0][wd][lane], C, WD, true);
-        db = d3(buf[1][wu][lane], buf[1][wd][lane], C, WD, true);
+    auto row_off = [&](int j) -> long long {
+        return colbase + (long long)((AL == 2) ? min(max(j, 0), nz - 1) : wrap(j, ny)) * rstride;
     };
 
-    const int j0 = ks - 2;
-    long long offp;
-    R zp;
-    row_of(j0 - 1, offp, zp);
-    S3<R> Xm1 = s3_load(io.in, fs, offp), Xm2 = Xm1;
+    S3<R> Xm1, Xpre;
+    R zm1, zpre;
+    load_next(Xm1, zm1);
+    load_next(Xpre, zpre);
+    S3<R> Xm2 = Xm1;
     R u1[3], T1, p1;
-    prims3(Xm1, zp, C, u1, T1, p1);
+    prims3(Xm1, zm1, C, u1, T1, p1);
     R A1 = R(0), A2 = R(0), dxux1 = R(0), dxua1 = R(0), dwua1 = R(0), dwuw1 = R(0);
     const S3<R> zero = {R(0), {R(0), R(0), R(0)}, R(0)};
     S3<R> F2 = zero, XP2 = Xm1, FP2 = zero, d1 = zero, Dm = zero;
@@ -119,116 +130,125 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
     R dd1 = R(0), ss2 = R(0);
 
     for (int j = j0; j <= ke + 1; ++j) {
-        long long off0;
-        R z0;
-        row_of(j, off0, z0);
-        const S3<R> X0 = s3_load(io.in, fs, off0);
+        const S3<R> X0 = Xpre;
+        const R z0 = zpre;
+        if (j <= ke) load_next(Xpre, zpre);  // row j+1, used next iteration
         R u0[3], T0, p0;
         prims3(X0, z0, C, u0, T0, p0);
-        const R A0 = fabs(u0[AL]) + rsqrt_(C.cs2 * T0);
-        const R dxux0 = d3(shdn(u0[0]), shup(u0[0]), C, 0, true);
-        const R dxua0 = d3(shdn(u0[AL]), shup(u0[AL]), C, 0, true);
-        R dwua0, dwuw0;
-        exchangeW(xw, u0[AL], u0[WD], dwua0, dwuw0);
+        R A0 = R(0), dxux0 = R(0), dxua0 = R(0);
 
-        // row m = j-1: F^n (forward along the march), X^P
+        // row m = j-1: F^n (forward along the march), X^P and its primitives
         const int m = j - 1;
-        R du[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+        S3<R> F1 = zero, XP1 = Xm1;
+        R ppu1[3] = {u1[0], u1[1], u1[2]}, ppT1 = T1, ppp1 = p1;
+        if (role >= 1) {
+            A0 = fabs(u0[AL]) + rsqrt_(C.cs2 * T0);
+            dxux0 = d3(shdn(u0[0]), shup(u0[0]), C, 0, true);
+            dxua0 = d3(shdn(u0[AL]), shup(u0[AL]), C, 0, true);
+            R du[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) du[c][AL] = d3(u0[c], u1[c], C, AL, false);
-        du[0][0] = dxux1;
-        du[AL][0] = dxua1;
-        du[WD][WD] = dwuw1;
-        du[AL][WD] = dwua1;
-        const S3<R> F1 = flux3<AL>(Xm1, u1, p1, du, d3(T0, T1, C, AL, false), C);
-        S3<R> XP1 = Xm1;
-        R zm;
-        if (AL == 2) {
-            zm = io.zt[min(max(m, 0), nz - 1)];
-            if (m >= 1 && m <= nz - 2) {
-                XP1.r = Xm1.r - lam * (F1.r - F2.r);
-                XP1.m[0] = Xm1.m[0] - lam * (F1.m[0] - F2.m[0]);
-                XP1.m[1] = Xm1.m[1] - lam * (F1.m[1] - F2.m[1]);
-                XP1.m[2] = (Xm1.m[2] - lam * (F1.m[2] - F2.m[2])) + Dl * (-C.g * Xm1.r);
-                XP1.E = Xm1.E - lam * (F1.E - F2.E);
-            } else {
-                XP1.r = (m <= 0) ? Xm1.r - lam2 * F1.r : Xm1.r + lam2 * F2.r;
-                XP1.m[0] = XP1.m[1] = XP1.m[2] = R(0);
-                XP1.E = XP1.r * ((m <= 0) ? C.ebot : C.etop);
-            }
-        } else {
-            zm = z0;
-            if (!passthru) {
+            for (int c = 0; c < 3; ++c) du[c][AL] = d3(u0[c], u1[c], C, AL, false);
+            du[0][0] = dxux1;
+            du[AL][0] = dxua1;
+            du[WD][WD] = dwuw1;
+            du[AL][WD] = dwua1;
+            F1 = flux3<AL>(Xm1, u1, p1, du, d3(T0, T1, C, AL, false), C);
+            if (AL == 2) {
+                if (m >= 1 && m <= nz - 2) {
+                    XP1.r = Xm1.r - lam * (F1.r - F2.r);
+                    XP1.m[0] = Xm1.m[0] - lam * (F1.m[0] - F2.m[0]);
+                    XP1.m[1] = Xm1.m[1] - lam * (F1.m[1] - F2.m[1]);
+                    XP1.m[2] = (Xm1.m[2] - lam * (F1.m[2] - F2.m[2])) + Dl * (-C.g * Xm1.r);
+                    XP1.E = Xm1.E - lam * (F1.E - F2.E);
+                } else {
+                    XP1.r = (m <= 0) ? Xm1.r - lam2 * F1.r : Xm1.r + lam2 * F2.r;
+                    XP1.m[0] = XP1.m[1] = XP1.m[2] = R(0);
+                    XP1.E = XP1.r * ((m <= 0) ? C.ebot : C.etop);
+                }
+            } else if (!passthru) {
                 XP1.r = Xm1.r - lam * (F1.r - F2.r);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) XP1.m[c] = Xm1.m[c] - lam * (F1.m[c] - F2.m[c]);
                 XP1.E = Xm1.E - lam * (F1.E - F2.E);
             }
+            prims3(XP1, zm1, C, ppu1, ppT1, ppp1);
         }
-        R ppu1[3], ppT1, ppp1;
-        prims3(XP1, zm, C, ppu1, ppT1, ppp1);
-        R dwppa1, dwppw1;
-        exchangeW(pw, ppu1[AL], ppu1[WD], dwppa1, dwppw1);
-        R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dq[c][AL] = d3(ppu1[c], ppu2[c], C, AL, false);
-        dq[0][0] = d3(shdn(ppu1[0]), shup(ppu1[0]), C, 0, true);
-        dq[AL][0] = d3(shdn(ppu1[AL]), shup(ppu1[AL]), C, 0, true);
-        dq[WD][WD] = dwppw1;
-        dq[AL][WD] = dwppa1;
-        const S3<R> FP1 = flux3<AL>(XP1, ppu1, ppp1, dq, d3(ppT1, ppT2, C, AL, false), C);
 
-        // row c = j-2: corrector X^C and the average (X^P + X^C)/2
-        const int c = j - 2;
-        S3<R> Xa = Xm2;
-        if (AL == 2) {
-            if (c >= 1 && c <= nz - 2) {
+        // exchange across W: u of X at row j and of X^P at row m
+        R(*buf)[NW][32] = xs[j & 1];
+        buf[0][w][lane] = u0[AL];
+        buf[1][w][lane] = u0[WD];
+        buf[2][w][lane] = ppu1[AL];
+        buf[3][w][lane] = ppu1[WD];
+        __syncthreads();
+        const int wu = min(w + 1, NW - 1), wd = max(w - 1, 0);
+        const R dwua0 = d3(buf[0][wu][lane], buf[0][wd][lane], C, WD, true);
+        const R dwuw0 = d3(buf[1][wu][lane], buf[1][wd][lane], C, WD, true);
+
+        S3<R> FP1 = zero, Dn = zero, d0 = zero;
+        R dd0 = R(0), ss1 = R(0);
+        if (role == 2) {
+            const R dwppa1 = d3(buf[2][wu][lane], buf[2][wd][lane], C, WD, true);
+            const R dwppw1 = d3(buf[3][wu][lane], buf[3][wd][lane], C, WD, true);
+            R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dq[c][AL] = d3(ppu1[c], ppu2[c], C, AL, false);
+            dq[0][0] = d3(shdn(ppu1[0]), shup(ppu1[0]), C, 0, true);
+            dq[AL][0] = d3(shdn(ppu1[AL]), shup(ppu1[AL]), C, 0, true);
+            dq[WD][WD] = dwppw1;
+            dq[AL][WD] = dwppa1;
+            FP1 = flux3<AL>(XP1, ppu1, ppp1, dq, d3(ppT1, ppT2, C, AL, false), C);
+
+            // row c = j-2: corrector X^C and the average (X^P + X^C)/2
+            const int c = j - 2;
+            S3<R> Xa = Xm2;
+            if (AL == 2) {
+                if (c >= 1 && c <= nz - 2) {
+                    Xa.r = (XP2.r + (Xm2.r - lam * (FP1.r - FP2.r))) * R(0.5);
+                    Xa.m[0] = (XP2.m[0] + (Xm2.m[0] - lam * (FP1.m[0] - FP2.m[0]))) * R(0.5);
+                    Xa.m[1] = (XP2.m[1] + (Xm2.m[1] - lam * (FP1.m[1] - FP2.m[1]))) * R(0.5);
+                    Xa.m[2] = (XP2.m[2] + ((Xm2.m[2] - lam * (FP1.m[2] - FP2.m[2])) + Dl * (-C.g * XP2.r))) * R(0.5);
+                    Xa.E = (XP2.E + (Xm2.E - lam * (FP1.E - FP2.E))) * R(0.5);
+                } else {
+                    Xa.r = (c <= 0) ? (XP2.r + (Xm2.r - lam2 * FP1.r)) * R(0.5) : (XP2.r + Xm2.r) * R(0.5);
+                }
+            } else if (!passthru) {
                 Xa.r = (XP2.r + (Xm2.r - lam * (FP1.r - FP2.r))) * R(0.5);
-                Xa.m[0] = (XP2.m[0] + (Xm2.m[0] - lam * (FP1.m[0] - FP2.m[0]))) * R(0.5);
-                Xa.m[1] = (XP2.m[1] + (Xm2.m[1] - lam * (FP1.m[1] - FP2.m[1]))) * R(0.5);
-                Xa.m[2] = (XP2.m[2] + ((Xm2.m[2] - lam * (FP1.m[2] - FP2.m[2])) + Dl * (-C.g * XP2.r))) * R(0.5);
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    Xa.m[q] = (XP2.m[q] + (Xm2.m[q] - lam * (FP1.m[q] - FP2.m[q]))) * R(0.5);
                 Xa.E = (XP2.E + (Xm2.E - lam * (FP1.E - FP2.E))) * R(0.5);
-            } else {
-                Xa.r = (c <= 0) ? (XP2.r + (Xm2.r - lam2 * FP1.r)) * R(0.5) : (XP2.r + Xm2.r) * R(0.5);
             }
-        } else if (!passthru) {
-            Xa.r = (XP2.r + (Xm2.r - lam * (FP1.r - FP2.r))) * R(0.5);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) Xa.m[q] = (XP2.m[q] + (Xm2.m[q] - lam * (FP1.m[q] - FP2.m[q]))) * R(0.5);
-            Xa.E = (XP2.E + (Xm2.E - lam * (FP1.E - FP2.E))) * R(0.5);
-        }
 
-        // TVD flux across (j-2, j-1) from the input state
-        const S3<R> d0 = s3_sub(X0, Xm1);
-        const R dd0 = s3_dot(d0, d0);
-        const R ss1 = s3_dot(d1, d0);
-        S3<R> Dn = zero;
-        const bool tvd_on = (AL == 2) ? (c >= 1 && c <= nz - 3) : !passthru;
-        if (tvd_on) {
-            const R G = tvd_G(ss2, ss1, dd1, courant(Delta, lam, A2, A1, h), C.tvd_form);
-            Dn = {G * d1.r, {G * d1.m[0], G * d1.m[1], G * d1.m[2]}, G * d1.E};
-        }
-
-        if (c >= ks && c < ke && own) {
-            S3<R> Xn = Xa;
-            const bool interior = (AL == 2) ? (c >= 1 && c <= nz - 2) : !passthru;
-            if (interior) {
-                Xn.r = Xa.r + (Dn.r - Dm.r);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (Dn.m[q] - Dm.m[q]);
-                Xn.E = Xa.E + (Dn.E - Dm.E);
-            } else if (AL == 2) {
-                Xn.m[0] = Xn.m[1] = Xn.m[2] = R(0);
-                Xn.E = Xa.r * (c == 0 ? C.ebot : C.etop);
+            // TVD flux across (j-2, j-1) from the input state
+            d0 = s3_sub(X0, Xm1);
+            dd0 = s3_dot(d0, d0);
+            ss1 = s3_dot(d1, d0);
+            const bool tvd_on = (AL == 2) ? (c >= 1 && c <= nz - 3) : !passthru;
+            if (tvd_on) {
+                const R G = tvd_G(ss2, ss1, dd1, courant(Delta, lam, A2, A1, h), C.tvd_form);
+                Dn = {G * d1.r, {G * d1.m[0], G * d1.m[1], G * d1.m[2]}, G * d1.E};
             }
-            long long offc;
-            R zc;
-            row_of(c, offc, zc);
-            s3_store(io.out, fs, offc, Xn);
+
+            if (c >= ks && c < ke && own) {
+                S3<R> Xn = Xa;
+                const bool interior = (AL == 2) ? (c >= 1 && c <= nz - 2) : !passthru;
+                if (interior) {
+                    Xn.r = Xa.r + (Dn.r - Dm.r);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (Dn.m[q] - Dm.m[q]);
+                    Xn.E = Xa.E + (Dn.E - Dm.E);
+                } else if (AL == 2) {
+                    Xn.m[0] = Xn.m[1] = Xn.m[2] = R(0);
+                    Xn.E = Xa.r * (c == 0 ? C.ebot : C.etop);
+                }
+                s3_store(io.out, fs, row_off(c), Xn);
+            }
         }
 
         Xm2 = Xm1;
         Xm1 = X0;
+        zm1 = z0;
         u1[0] = u0[0]; u1[1] = u0[1]; u1[2] = u0[2];
         T1 = T0;
         p1 = p0;
@@ -249,16 +269,19 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 
 // L_x in 3D: march z, warps span y, the x stencil across lanes (as
 // sweep_x2d); plate planes pass through.  Row pipeline at step j: F^n and X^P
-// of row j-1 (d/dz from rows j, j-2; d/dy from the exchange of row j-1),
-// then F^P, corrector, average and TVD along x of row j-2, output row j-2.
+// of row j-1 (d/dz from rows j, j-2; d/dy from the exchange of row j-1 one
+// iteration earlier), then F^P (d/dz of X^P from rows j-1, j-3; d/dy from
+// the exchange of row j-2), corrector, average and TVD along x of row j-2,
+// output row j-2.  One exchange per row carries u_x, u_y of X at row j and
+// of X^P at row j-1, both read in the next iteration.
 template <class R, int NW>
 __global__ void __launch_bounds__(NW * 32)
 sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 {
-    __shared__ R xw[2][NW][32];
-    __shared__ R pw[2][NW][32];
+    __shared__ R xs[2][4][NW][32];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
+    const int role = halo_role<NW>(w);
     const int cw = blockIdx.y * (NW - 4) - 2 + w;  // y row of this warp
     const int ks = blockIdx.z * io.seg;
     const int nz = C.nz, ny = C.ny, nx = C.nx, pitch = C.pitch;
@@ -277,15 +300,8 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
         sc.ctl->t += dt;
         sc.ctl->steps += 1.0;
     }
-    auto exchangeW = [&](R (&buf)[2][NW][32], R a, R b, R& da, R& db) {
-        buf[0][w][lane] = a;
-        buf[1][w][lane] = b;
-        __syncthreads();
-        const int wu = min(w + 1, NW - 1), wd = max(w - 1, 0);
-        da = d3(buf[0][wu][lane], buf[0][wd][lane], C, 1, true);
-        db = d3(buf[1][wu][lane], buf[1][wd][lane], C, 1, true);
-    };
-    auto offk = [&](int k) { return off3(min(max(k, 0), nz - 1), cwr, ny, pitch, ic); };
+    const long long colbase = (long long)cwr * pitch + ic, rstride = (long long)ny * pitch;
+    auto offk = [&](int k) { return colbase + (long long)min(max(k, 0), nz - 1) * rstride; };
     auto zk = [&](int k) { return io.zt[min(max(k, 0), nz - 1)]; };
 
     double vmin = 1e308;
@@ -293,8 +309,10 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
     int bad = 0;
     const int j0 = ks - 2;
     S3<R> Xm1 = s3_load(io.in, fs, offk(j0 - 1)), Xm2 = Xm1;
+    S3<R> Xpre = s3_load(io.in, fs, offk(j0));
+    R zm1 = zk(j0 - 1), zpre = zk(j0);
     R u1[3], T1, p1;
-    prims3(Xm1, zk(j0 - 1), C, u1, T1, p1);
+    prims3(Xm1, zm1, C, u1, T1, p1);
     R u2[3] = {u1[0], u1[1], u1[2]}, T2 = T1;
     R dwx1 = R(0), dwy1 = R(0);          // d/dy of u_x, u_y of row j-1
     S3<R> XP2 = Xm1;
@@ -303,16 +321,20 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
     R dwpx2 = R(0), dwpy2 = R(0);        // d/dy of X^P u_x, u_y of row j-2
 
     for (int j = j0; j <= ke + 1; ++j) {
-        const S3<R> X0 = s3_load(io.in, fs, offk(j));
+        const S3<R> X0 = Xpre;
+        const R z0 = zpre;
+        if (j <= ke) {  // row j+1, used next iteration
+            Xpre = s3_load(io.in, fs, offk(j + 1));
+            zpre = zk(j + 1);
+        }
         R u0[3], T0, p0;
-        prims3(X0, zk(j), C, u0, T0, p0);
-        R dwx0, dwy0;
-        exchangeW(xw, u0[0], u0[1], dwx0, dwy0);
+        prims3(X0, z0, C, u0, T0, p0);
 
-        // row m = j-1: F^n with forward x-differences, X^P
+        // row m = j-1: F^n with forward x-differences, X^P and its primitives
         const int m = j - 1;
         S3<R> XP1 = Xm1;
-        {
+        R pp1[3] = {u1[0], u1[1], u1[2]}, ppT1 = T1, ppp1 = p1;
+        if (role >= 1) {
             R du[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
 #pragma unroll
             for (int c = 0; c < 3; ++c) du[c][0] = d3(shdn(u1[c]), u1[c], C, 0, false);
@@ -328,70 +350,83 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
                 for (int c = 0; c < 3; ++c) XP1.m[c] = Xm1.m[c] - lam * (F1.m[c] - Fl.m[c]);
                 XP1.E = Xm1.E - lam * (F1.E - Fl.E);
             }
+            prims3(XP1, zm1, C, pp1, ppT1, ppp1);
         }
-        R pp1[3], ppT1, ppp1;
-        prims3(XP1, zk(m), C, pp1, ppT1, ppp1);
-        R dwpx1, dwpy1;
-        exchangeW(pw, pp1[0], pp1[1], dwpx1, dwpy1);
 
-        // row c = j-2: F^P with backward x-differences, corrector, average, TVD along x
-        const int c = j - 2;
-        R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
-#pragma unroll
-        for (int q = 0; q < 3; ++q) dq[q][0] = d3(pp2[q], shup(pp2[q]), C, 0, false);
-        dq[0][1] = dwpx2;
-        dq[1][1] = dwpy2;
-        dq[0][2] = d3(pp1[0], pp3[0], C, 2, true);
-        dq[2][2] = d3(pp1[2], pp3[2], C, 2, true);
-        const S3<R> FP = flux3<0>(XP2, pp2, ppp2, dq, d3(ppT2, shup(ppT2), C, 0, false), C);
-        const S3<R> FPr = {shdn(FP.r), {shdn(FP.m[0]), shdn(FP.m[1]), shdn(FP.m[2])}, shdn(FP.E)};
-        S3<R> Xa;
-        Xa.r = (XP2.r + (Xm2.r - lam * (FPr.r - FP.r))) * R(0.5);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) Xa.m[q] = (XP2.m[q] + (Xm2.m[q] - lam * (FPr.m[q] - FP.m[q]))) * R(0.5);
-        Xa.E = (XP2.E + (Xm2.E - lam * (FPr.E - FP.E))) * R(0.5);
-        const S3<R> Xr = {shdn(Xm2.r), {shdn(Xm2.m[0]), shdn(Xm2.m[1]), shdn(Xm2.m[2])}, shdn(Xm2.E)};
-        const S3<R> d0 = s3_sub(Xr, Xm2);
-        const R dd = s3_dot(d0, d0);
-        const S3<R> dl = {shup(d0.r), {shup(d0.m[0]), shup(d0.m[1]), shup(d0.m[2])}, shup(d0.E)};
-        const R sp = s3_dot(dl, d0);
-        const R sm = shdn(sp);
-        const R A = fabs(u2[0]) + rsqrt_(C.cs2 * T2);
-        const R G = tvd_G(sp, sm, dd, courant(Delta, lam, A, shdn(A), C.hx), C.tvd_form);
-        const S3<R> Dn = {G * d0.r, {G * d0.m[0], G * d0.m[1], G * d0.m[2]}, G * d0.E};
-        const S3<R> Dl = {shup(Dn.r), {shup(Dn.m[0]), shup(Dn.m[1]), shup(Dn.m[2])}, shup(Dn.E)};
+        // exchange across y: u of X at row j and of X^P at row j-1
+        R(*buf)[NW][32] = xs[j & 1];
+        buf[0][w][lane] = u0[0];
+        buf[1][w][lane] = u0[1];
+        buf[2][w][lane] = pp1[0];
+        buf[3][w][lane] = pp1[1];
+        __syncthreads();
+        const int wu = min(w + 1, NW - 1), wd = max(w - 1, 0);
+        const R dwx0 = d3(buf[0][wu][lane], buf[0][wd][lane], C, 1, true);
+        const R dwy0 = d3(buf[1][wu][lane], buf[1][wd][lane], C, 1, true);
+        const R dwpx1 = d3(buf[2][wu][lane], buf[2][wd][lane], C, 1, true);
+        const R dwpy1 = d3(buf[3][wu][lane], buf[3][wd][lane], C, 1, true);
 
-        if (c >= ks && c < ke && own) {
-            S3<R> Xn = Xm2;  // plate planes pass through
-            if (c >= 1 && c <= nz - 2) {
-                Xn.r = Xa.r + (Dn.r - Dl.r);
+        if (role == 2) {
+            // row c = j-2: F^P with backward x-differences, corrector, average, TVD along x
+            const int c = j - 2;
+            R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
 #pragma unroll
-                for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (Dn.m[q] - Dl.m[q]);
-                Xn.E = Xa.E + (Dn.E - Dl.E);
-            }
-            s3_store(io.out, fs, offk(c), Xn);
-            if (sc.last) {
-                R un[3], Tn, pn;
-                prims3(Xn, zk(c), C, un, Tn, pn);
-                if constexpr (kExact<R>) {
-                    const double cs = sqrt(C.cs2 * Tn);
-                    double v = C.dx / (fabs(un[0]) + cs);
-                    v = fmin(v, C.dy / (fabs(un[1]) + cs));
-                    v = fmin(v, C.dz / (fabs(un[2]) + cs));
-                    if (!(v > 0.0) || !(v < 1e300)) bad = 1;
-                    vmin = fmin(vmin, v);
-                } else {
-                    const R cs = rsqrt_(C.cs2 * Tn);
-                    const R r = fmax(fmax((fabs(un[0]) + cs) * C.inv_dx, (fabs(un[1]) + cs) * C.inv_dy),
-                                     (fabs(un[2]) + cs) * C.inv_dz);
-                    if (!(r > R(0)) || !(r < R(1e30))) bad = 1;
-                    rmax = fmax(rmax, r);
+            for (int q = 0; q < 3; ++q) dq[q][0] = d3(pp2[q], shup(pp2[q]), C, 0, false);
+            dq[0][1] = dwpx2;
+            dq[1][1] = dwpy2;
+            dq[0][2] = d3(pp1[0], pp3[0], C, 2, true);
+            dq[2][2] = d3(pp1[2], pp3[2], C, 2, true);
+            const S3<R> FP = flux3<0>(XP2, pp2, ppp2, dq, d3(ppT2, shup(ppT2), C, 0, false), C);
+            const S3<R> FPr = {shdn(FP.r), {shdn(FP.m[0]), shdn(FP.m[1]), shdn(FP.m[2])}, shdn(FP.E)};
+            S3<R> Xa;
+            Xa.r = (XP2.r + (Xm2.r - lam * (FPr.r - FP.r))) * R(0.5);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Xa.m[q] = (XP2.m[q] + (Xm2.m[q] - lam * (FPr.m[q] - FP.m[q]))) * R(0.5);
+            Xa.E = (XP2.E + (Xm2.E - lam * (FPr.E - FP.E))) * R(0.5);
+            const S3<R> Xr = {shdn(Xm2.r), {shdn(Xm2.m[0]), shdn(Xm2.m[1]), shdn(Xm2.m[2])}, shdn(Xm2.E)};
+            const S3<R> d0 = s3_sub(Xr, Xm2);
+            const R dd = s3_dot(d0, d0);
+            const S3<R> dl = {shup(d0.r), {shup(d0.m[0]), shup(d0.m[1]), shup(d0.m[2])}, shup(d0.E)};
+            const R sp = s3_dot(dl, d0);
+            const R sm = shdn(sp);
+            const R A = fabs(u2[0]) + rsqrt_(C.cs2 * T2);
+            const R G = tvd_G(sp, sm, dd, courant(Delta, lam, A, shdn(A), C.hx), C.tvd_form);
+            const S3<R> Dn = {G * d0.r, {G * d0.m[0], G * d0.m[1], G * d0.m[2]}, G * d0.E};
+            const S3<R> Dl = {shup(Dn.r), {shup(Dn.m[0]), shup(Dn.m[1]), shup(Dn.m[2])}, shup(Dn.E)};
+
+            if (c >= ks && c < ke && own) {
+                S3<R> Xn = Xm2;  // plate planes pass through
+                if (c >= 1 && c <= nz - 2) {
+                    Xn.r = Xa.r + (Dn.r - Dl.r);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (Dn.m[q] - Dl.m[q]);
+                    Xn.E = Xa.E + (Dn.E - Dl.E);
+                }
+                s3_store(io.out, fs, offk(c), Xn);
+                if (sc.last) {
+                    R un[3], Tn, pn;
+                    prims3(Xn, zk(c), C, un, Tn, pn);
+                    if constexpr (kExact<R>) {
+                        const double cs = sqrt(C.cs2 * Tn);
+                        double v = C.dx / (fabs(un[0]) + cs);
+                        v = fmin(v, C.dy / (fabs(un[1]) + cs));
+                        v = fmin(v, C.dz / (fabs(un[2]) + cs));
+                        if (!(v > 0.0) || !(v < 1e300)) bad = 1;
+                        vmin = fmin(vmin, v);
+                    } else {
+                        const R cs = rsqrt_(C.cs2 * Tn);
+                        const R r = fmax(fmax((fabs(un[0]) + cs) * C.inv_dx, (fabs(un[1]) + cs) * C.inv_dy),
+                                         (fabs(un[2]) + cs) * C.inv_dz);
+                        if (!(r > R(0)) || !(r < R(1e30))) bad = 1;
+                        rmax = fmax(rmax, r);
+                    }
                 }
             }
         }
 
         Xm2 = Xm1;
         Xm1 = X0;
+        zm1 = z0;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             u2[q] = u1[q];

@@ -144,6 +144,29 @@ def test_fp32_100_steps():
     s.close()
 
 
+def test_fp32_nu_over_a_window():
+    """FP32 state, FP64 reductions: Nu_bar, Nu and Re of every step of the
+    window 51..100 of the 256 x 64, Ra = 1e6 workload against the FP64 run
+    (which equals the oracle bit for bit).  Stated bars: window means within
+    1e-6 relative, every sample within 1e-5 relative."""
+    cfg = O.Config()
+    out = {}
+    for prec in ("fp64", "fp32"):
+        s = solver_for(cfg, prec, diag_every=1)
+        s.step(100)
+        out[prec] = [d for d in s.diagnostics() if d["step"] > 50]
+        s.close()
+    assert [d["step"] for d in out["fp32"]] == list(range(51, 101))
+    for key in ("Nu_bar", "Nu", "Re"):
+        a = np.array([d[key] for d in out["fp32"]])
+        b = np.array([d[key] for d in out["fp64"]])
+        assert abs(a.mean() - b.mean()) <= 1e-6 * abs(b.mean()), key
+        assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b)), key
+    # the FP64 samples are the oracle's
+    X, _, _ = O.step(cfg, O.init(cfg), 100)
+    assert abs(out["fp64"][-1]["Nu_bar"] - O.diag(cfg, X)["Nu_bar"]) <= 1e-12 * abs(O.diag(cfg, X)["Nu_bar"])
+
+
 def test_diagnostics_match_oracle_on_same_state():
     cfg = O.Config(nx=128, nz=33, Ra=1e7)
     X = stirred_state(cfg, seed=5, u_amp=0.1)
