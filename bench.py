@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NX, NZ, RA, PR, GAMMA = 4096, 1024, 1e10, 1.0, 5.0 / 3.0
+RA3 = 1e9  # the 512 x 512 x 128 box
 WORKLOAD = "2d_aspect4_4096x1024_Ra1e10"
 METRIC = "cell-updates/s per MacCormack-TVD step"
 UNIT = "cell-updates/s"
@@ -215,7 +216,7 @@ def run_gpu(args):
     box3 = None
     if not args.no_3d:
         n3 = (512, 512, 128)
-        s3 = cm.Solver(n3[0], n3[2], RA, PR, GAMMA, ny=n3[1], ndim=3, precision="fp32", stream=stream,
+        s3 = cm.Solver(n3[0], n3[2], RA3, PR, GAMMA, ny=n3[1], ndim=3, precision="fp32", stream=stream,
                        seed=777 + rank)
         s3.step(min(args.warmup, 5))
         s3.sync()
@@ -233,7 +234,7 @@ def run_gpu(args):
                   "sweep3d_x": sw3[2] + sw3[5]}
         bytes3 = 2 * 5 * 4 * cells3
         box3 = {"value": world * cells3 * k3 / (ms3 * 1e-3), "unit": UNIT, "steps": k3,
-                "workload": "3d_aspect4x4_512x512x128_Ra1e10_fp32", "ms_per_step": ms3 / k3,
+                "workload": "3d_aspect4x4_512x512x128_Ra1e9_fp32", "ms_per_step": ms3 / k3,
                 "sweep_ms": [round(x, 5) for x in sw3], "gpu_launches": nl3, "finite": d3["status"] == 0,
                 "roofline": {k: {"bound": "hbm", "achieved": round(bytes3 / (v / 2 * 1e-3) / 1e9, 1), "peak": hbm,
                                  "unit": "GB/s", "frac": round(bytes3 / (v / 2 * 1e-3) / 1e9 / hbm, 4)}
@@ -364,6 +365,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """One kernel family on its own, for profiler captures: a few steps of
+    the chosen case at the given size, then one JSON line (no timing claims)."""
+    import numpy as np
+    import paper_2411_10372_gb300 as cm
+    case, out = args.case, {"case": args.case}
+    if case in ("2d_fp32", "2d_fp64", "3d_fp32", "3d_fp64"):
+        prec = case[3:]
+        if case.startswith("3d"):
+            s = cm.Solver(args.nx, args.nz, RA3, PR, GAMMA, ny=args.ny, ndim=3, precision=prec)
+        else:
+            s = cm.Solver(args.nx, args.nz, RA, PR, GAMMA, precision=prec)
+        s.step(args.warmup)
+        s.step(args.steps)
+        d = s.sample()
+        s.close()
+        out.update(nx=args.nx, ny=args.ny if case.startswith("3d") else 1, nz=args.nz, status=d["status"])
+    elif case == "batch":
+        rng = np.random.default_rng(2024)
+        u, u2 = rng.random(64), rng.random(64)
+        nzs = [int(round(32 * 8 ** x)) for x in u]
+        p = cm.cm_default_params()
+        p.precision = cm.CM_FP32
+        cm.cm_batch_init([cm.cm_grid(2, 4 * nz, 1, nz, 4.0) for nz in nzs], [10 ** (5 + 4 * x) for x in u2], PR,
+                         GAMMA, p)
+        cm.cm_batch_step(args.warmup + args.steps)
+        out.update(boxes=64, status=max(d["status"] for d in cm.cm_batch_diagnostics()))
+        cm.cm_batch_finalize()
+    elif case == "adjoint":
+        s = cm.Solver(args.nx, args.nz, 1e8, PR, GAMMA, precision="fp64")
+        J = cm.cm_adj_forward(args.steps, max(1, args.steps // 4), args.steps // 2 + 1)
+        g = cm.cm_adj_backward(None, None)
+        s.close()
+        out.update(nx=args.nx, nz=args.nz, J=J, dJ_dRa=g)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,8 +418,14 @@ def main():
     ap.add_argument("--steps-3d", type=int, default=200)
     ap.add_argument("--nx", type=int, default=NX, help="grid override (profiling captures only)")
     ap.add_argument("--nz", type=int, default=NZ, help="grid override (profiling captures only)")
+    ap.add_argument("--ny", type=int, default=512, help="3D grid override (--case only)")
     ap.add_argument("--only-fp32", action="store_true", help="time the FP32 steps only (profiling captures)")
+    ap.add_argument("--case", choices=["2d_fp32", "2d_fp64", "3d_fp32", "3d_fp64", "batch", "adjoint"],
+                    help="run one kernel family untimed (profiling captures)")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
