@@ -51,11 +51,14 @@ __global__ void init_state(R* X, Coef<R> C, InitArgs A)
 }
 
 // min over nodes and directions of h/(|u|+c) into a dt slot (used at init and
-// after cm_set_state; during stepping the last sweep does this reduction)
+// after cm_set_state; during stepping the last sweep does this reduction).
+// FP64 states: the sweeps' exact FP64 operation order.  FP32 states: the FP32
+// rates (|u|+c)/h of the FP32 sweeps, one FP64 reciprocal of the block max.
 template <class R>
 __global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int slot)
 {
     double vmin = 1e308;
+    float rmax = 0.f;
     int bad = 0;
     const long long plane = (long long)C.nx * C.ny;
     const long long total = plane * C.nz;
@@ -66,6 +69,20 @@ __global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int s
         const int j = (int)(jk % C.ny);
         const int k = (int)(jk / C.ny);
         const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
+        if constexpr (!kExact<R>) {
+            const float rho = p[0], ri = 1.f / rho;
+            const float ux = p[fs] * ri;
+            float uy = 0.f, uz, E;
+            if (C.ndim == 3) { uy = p[2 * fs] * ri; uz = p[3 * fs] * ri; E = p[4 * fs]; }
+            else { uz = p[2 * fs] * ri; E = p[3 * fs]; }
+            const float T = C.b * (E * ri - 0.5f * ((ux * ux + uy * uy) + uz * uz) - C.g * zt[k]);
+            const float c = sqrtf(C.cs2 * T);
+            float r = fmaxf((fabsf(ux) + c) * C.inv_dx, (fabsf(uz) + c) * C.inv_dz);
+            if (C.ndim == 3) r = fmaxf(r, (fabsf(uy) + c) * C.inv_dy);
+            if (!(r > 0.f) || !(r < 1e30f)) bad = 1;
+            rmax = fmaxf(rmax, r);
+            continue;
+        }
         // same operation order as the sweeps' FP64 path (divisions by rho)
         const double rho = (double)p[0];
         double ux = (double)p[fs] / rho, uy = 0.0, uz, E;
@@ -78,6 +95,7 @@ __global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int s
         if (!(v > 0.0) || !(v < 1e300)) bad = 1;
         vmin = fmin(vmin, v);
     }
+    if constexpr (!kExact<R>) vmin = rmax > 0.f ? 1.0 / (double)rmax : 1e308;
     block_dt_reduce(vmin, bad, ctl, slot);
 }
 
@@ -121,6 +139,29 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
         const int i = (int)(n % C.nx);
         const int j = (int)(n / C.nx);
         const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
+        if constexpr (!kExact<R>) {
+            // FP32 state: the integrands in FP32 (the state's own precision),
+            // their sums in FP64
+            const float rho = p[0], ri = 1.f / rho;
+            const float u = p[fs] * ri;
+            float vy = 0.f, w, E;
+            if (C.ndim == 3) { vy = p[2 * fs] * ri; w = p[3 * fs] * ri; E = p[4 * fs]; }
+            else { w = p[2 * fs] * ri; E = p[3 * fs]; }
+            const float zf = (float)z;
+            const float u2 = (u * u + vy * vy) + w * w;
+            const float T = (float)A.b * (E * ri - 0.5f * u2 - (float)A.g * zf);
+            const float Tsa = T - (1.f - (float)A.D * zf);
+            v[0] += (double)rho;
+            v[1] += (double)E;
+            v[2] += (double)(rho * w * Tsa);
+            v[3] += (double)(rho * w * u2);
+            v[4] += (double)u2;
+            v[5] += (double)(0.5f * rho * u2);
+            v[6] += (double)T;
+            v[7] = fmax(v[7], (double)(sqrtf(u2) / sqrtf((float)A.cs2 * T)));
+            if (!isfinite(E + rho + T + u2)) bad = 1;
+            continue;
+        }
         const double rho = (double)p[0];
         const double u = (double)p[fs] / rho;
         double vy = 0.0, w, E;
