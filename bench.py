@@ -144,18 +144,23 @@ def run_gpu(args):
         barrier()
         launches0 = cm.cm_launch_count()
         clk = Clocks(local)
+        # the value: events only at step boundaries, so the sweeps of a step
+        # overlap their launches exactly as in cm_step
         if clocks:
             with clk:
                 time.sleep(0.5)  # let nvidia-smi start; only samples inside the window count
                 t_start = time.time()
-                sweep_ms, step_ms = cm.cm_profile_steps(K, FLUSH_BYTES)
+                _, step_ms = cm.cm_profile_steps(K, FLUSH_BYTES, per_sweep=False)
                 clk.window = (t_start, time.time())
         else:
-            sweep_ms, step_ms = cm.cm_profile_steps(K, FLUSH_BYTES)
+            _, step_ms = cm.cm_profile_steps(K, FLUSH_BYTES, per_sweep=False)
         barrier()
         launches = cm.cm_launch_count() - launches0
         s.sync()
         total_ms = max_over_ranks(sum(step_ms))
+        # per-kernel durations for the roofline: a second timed pass with an
+        # event pair around every sweep (each duration includes its launch gap)
+        sweep_ms, _ = cm.cm_profile_steps(max(3, min(K, 500)), FLUSH_BYTES, per_sweep=True)
         out = dict(total_ms=total_ms, sweep_ms=sweep_ms, launches=launches, clocks=clk.summary() if clocks else None,
                    w=8 if precision == "fp64" else 4)
         return s, out
@@ -298,7 +303,8 @@ def run_gpu(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD + "_fp32", "nx": NXr, "nz": NZr, "Ra": RA, "Pr": PR, "gamma": GAMMA,
                    "eps": 0.1, "D": 0.5, "cfl": 0.5, "state": "fp32, fp64 dt and reductions",
-                   "l2": "flushed before every timed step (256 MiB memset)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed before every timed step (256 MiB memset)", "parallelism": f"replicas x{world}",
+                   "timing": "events at step boundaries for value; per-sweep events in a second pass for roofline"},
         "roofline": roofline(r32),
         "sweep_ms": [round(x, 5) for x in r32["sweep_ms"]],
         "gpu_launches": r32["launches"],

@@ -174,8 +174,11 @@ int cm_get_time(double* t, long long* steps);
  * overwritten with cudaMemsetAsync to evict the L2 cache (0 = no flush).
  * Waits once at the end.  ms_out (host, 4 entries in 2D: positions z, x, z,
  * x of a step; 6 in 3D: z, y, x, z, y, x) receives the mean device duration
- * in ms of the sweeps at each position; step_ms (host, n entries, may be NULL) the device duration of
- * each step.  n >= 1. */
+ * in ms of the sweeps at each position; step_ms (host, n entries, may be
+ * NULL) the device duration of each step.  ms_out may be NULL (then step_ms
+ * may not): each step is then bracketed by two events and no event sits
+ * between its sweeps, so consecutive sweeps overlap their launches as in
+ * cm_step.  n >= 1. */
 int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, double* step_ms);
 
 /* Number of CUDA kernel launches this context has queued since cm_init. */

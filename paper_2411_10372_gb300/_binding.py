@@ -204,11 +204,14 @@ def cm_get_time() -> tuple[float, int]:
     return t.value, s.value
 
 
-def cm_profile_steps(n: int, flush_bytes: int = 0) -> tuple[list[float], list[float]]:
-    """(mean ms per sweep position, ms of each step) of n profiled steps."""
+def cm_profile_steps(n: int, flush_bytes: int = 0, per_sweep: bool = True) -> tuple[list[float], list[float]]:
+    """(mean ms per sweep position, ms of each step) of n profiled steps; with
+    per_sweep=False only the steps are bracketed (the sweep list is empty)."""
     ms = (ctypes.c_double * 6)()
     steps = (ctypes.c_double * n)()
-    _check(lib().cm_profile_steps(int(n), int(flush_bytes), ms, steps))
+    _check(lib().cm_profile_steps(int(n), int(flush_bytes), ms if per_sweep else None, steps))
+    if not per_sweep:
+        return [], list(steps)
     _, nf, _ = cm_state_layout()
     return list(ms)[: 6 if nf == 5 else 4], list(steps)
 

@@ -236,11 +236,13 @@ int download(Ctx* c, double* host)
 // (applied right to left)
 int sweeps_per_step(const Ctx* c) { return c->grid.ndim == 3 ? 6 : 4; }
 
-// queue n steps; with ev != NULL (S+1 events per step, S sweeps per step),
-// record ev[(S+1)s+q] before sweep q of step s and ev[(S+1)s+S] after its last
-// sweep; with flush, overwrite flush_bytes of it before each step, outside
-// the brackets
-int queue_steps(Ctx* c, int n, cudaEvent_t* ev = nullptr, void* flush = nullptr, size_t flush_bytes = 0)
+// queue n steps; with ev != NULL and per_sweep (S+1 events per step, S sweeps
+// per step), record ev[(S+1)s+q] before sweep q of step s and ev[(S+1)s+S]
+// after its last sweep; with ev != NULL and !per_sweep, ev[2s] before the
+// step and ev[2s+1] after it; with flush, overwrite flush_bytes of it before
+// each step, outside the brackets
+int queue_steps(Ctx* c, int n, cudaEvent_t* ev = nullptr, void* flush = nullptr, size_t flush_bytes = 0,
+                bool per_sweep = true)
 {
     static const int order2[4] = {2, 0, 2, 0};
     static const int order3[6] = {2, 1, 0, 2, 1, 0};
@@ -256,11 +258,11 @@ int queue_steps(Ctx* c, int n, cudaEvent_t* ev = nullptr, void* flush = nullptr,
         for (int q = 0; q < S; ++q) {
             sc.first = (q == 0);
             sc.last = (q == S - 1);
-            if (ev) CK(cudaEventRecord(ev[(S + 1) * s + q], c->stream));
+            if (ev && (per_sweep || q == 0)) CK(cudaEventRecord(ev[per_sweep ? (S + 1) * s + q : 2 * s], c->stream));
             int rc = sweep(c, order[q], sc);
             if (rc) return rc;
         }
-        if (ev) CK(cudaEventRecord(ev[(S + 1) * s + S], c->stream));
+        if (ev) CK(cudaEventRecord(ev[per_sweep ? (S + 1) * s + S : 2 * s + 1], c->stream));
         c->step++;
         if (c->prm.diag_every > 0 && c->step % c->prm.diag_every == 0) {
             int rc = sample(c);
@@ -595,7 +597,7 @@ int cm_get_time(double* t, long long* steps)
 int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, double* step_ms)
 {
     NEED_CTX();
-    if (n < 1 || !ms_out) return fail(CM_EINVAL, "need n >= 1 and ms_out");
+    if (n < 1 || (!ms_out && !step_ms)) return fail(CM_EINVAL, "need n >= 1 and ms_out or step_ms");
     Ctx* c = g_ctx;
     void* flush = nullptr;
     if (flush_bytes) {
@@ -605,15 +607,22 @@ int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, doub
         }
     }
     const int S = sweeps_per_step(c);
-    std::vector<cudaEvent_t> ev((S + 1) * (size_t)n, nullptr);
+    const bool per_sweep = ms_out != nullptr;
+    std::vector<cudaEvent_t> ev((per_sweep ? S + 1 : 2) * (size_t)n, nullptr);
     int rc = CM_OK;
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) { rc = fail(CM_ECUDA, "cudaEventCreate failed"); break; }
-    if (!rc) rc = queue_steps(c, n, ev.data(), flush, flush_bytes);
+    if (!rc) rc = queue_steps(c, n, ev.data(), flush, flush_bytes, per_sweep);
     if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess)
         rc = fail(CM_ECUDA, "profiled steps failed: %s", cudaGetErrorString(cudaGetLastError()));
     double ms[6] = {0, 0, 0, 0, 0, 0};
-    for (int s = 0; !rc && s < n; ++s) {
+    for (int s = 0; !rc && !per_sweep && s < n; ++s) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev[2 * s], ev[2 * s + 1]) != cudaSuccess)
+            rc = fail(CM_ECUDA, "cudaEventElapsedTime failed");
+        step_ms[s] = t;
+    }
+    for (int s = 0; !rc && per_sweep && s < n; ++s) {
         double tot = 0;
         for (int q = 0; q < S; ++q) {
             float t = 0.f;
@@ -630,7 +639,8 @@ int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, doub
         if (e) cudaEventDestroy(e);
     if (flush) cudaFree(flush);
     if (rc) return rc;
-    for (int q = 0; q < S; ++q) ms_out[q] = ms[q] / n;
+    if (per_sweep)
+        for (int q = 0; q < S; ++q) ms_out[q] = ms[q] / n;
     return CM_OK;
 }
 

@@ -98,6 +98,17 @@ template <class R> __device__ __forceinline__ St<R> shdn(const St<R>& q) { retur
 __device__ __forceinline__ float rsqrt_(float v) { return sqrtf(v); }
 __device__ __forceinline__ double rsqrt_(double v) { return sqrt(v); }
 
+// Programmatic dependent launch between the sweeps of a stream: wait until
+// the previous kernel has finished and its writes are visible (before this
+// kernel reads anything it wrote, dt slots included), then allow the next
+// kernel to be scheduled while this one runs.  For a launch without the
+// programmatic-serialization attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // dt as the kernels see it: fixed, or CFL times the slot's minimum
 __device__ __forceinline__ double step_dt(const DevCtl* c, int slot, double cfl, double dt_fixed)
 {

@@ -26,10 +26,9 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
     const long long warps = (long long)io.nstrips * nsegs;
     const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (dir == 2) sweep_z2d_x2<<<blocks, kWarpsPerBlock * 32, kRingBytes, s>>>(io, C, sc);
-    else if (dir == 0) sweep_x2d_x2<<<blocks, kWarpsPerBlock * 32, kRingBytes, s>>>(io, C, sc);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    if (dir == 2) return launch_pdl(true, sweep_z2d_x2, dim3(blocks), dim3(kWarpsPerBlock * 32), kRingBytes, s, io, C, sc);
+    if (dir == 0) return launch_pdl(true, sweep_x2d_x2, dim3(blocks), dim3(kWarpsPerBlock * 32), kRingBytes, s, io, C, sc);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, cudaStream_t s)

@@ -8,6 +8,16 @@ namespace cm {
 
 template struct Launch<double>;
 
+bool pdl_enabled()
+{
+    static int on = -1;
+    if (on < 0) {
+        const char* e = getenv("CM_PDL");
+        on = (e && e[0] == '0') ? 0 : 1;
+    }
+    return on == 1;
+}
+
 cudaError_t launch_diag_final(const double* scratch, const double* zt, const DiagFinal& F, DevCtl* ctl, cm_diag* rec,
                               cudaStream_t s)
 {

@@ -148,10 +148,9 @@ static cudaError_t sweep3(int dir, const R* in, R* out, const R* zt, const Coef<
     io.seg = pick_segment3((long long)io.nstrips * groups, io.nmarch, bps[dir], sm_count());
     const int nsegs = (io.nmarch + io.seg - 1) / io.seg;
     const dim3 grid(io.nstrips, groups, nsegs);
-    if (dir == 2) sweep3d_march<R, 2, kNW3><<<grid, kNW3 * 32, 0, s>>>(io, C, sc);
-    else if (dir == 1) sweep3d_march<R, 1, kNW3><<<grid, kNW3 * 32, 0, s>>>(io, C, sc);
-    else sweep3d_x<R, kNW3><<<grid, kNW3 * 32, 0, s>>>(io, C, sc);
-    return cudaGetLastError();
+    if (dir == 2) return launch_pdl(false, sweep3d_march<R, 2, kNW3>, grid, dim3(kNW3 * 32), 0, s, io, C, sc);
+    if (dir == 1) return launch_pdl(false, sweep3d_march<R, 1, kNW3>, grid, dim3(kNW3 * 32), 0, s, io, C, sc);
+    return launch_pdl(false, sweep3d_x<R, kNW3>, grid, dim3(kNW3 * 32), 0, s, io, C, sc);
 }
 
 template <class R>
@@ -174,10 +173,9 @@ cudaError_t Launch<R>::sweep(int dir, const R* in, R* out, const R* zt, const Co
     const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
     const long long warps = (long long)io.nstrips * nsegs;
     const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (dir == 2) sweep_z2d<R><<<blocks, kWarpsPerBlock * 32, 0, s>>>(io, C, sc);
-    else if (dir == 0) sweep_x2d<R><<<blocks, kWarpsPerBlock * 32, 0, s>>>(io, C, sc);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    if (dir == 2) return launch_pdl(false, sweep_z2d<R>, dim3(blocks), dim3(kWarpsPerBlock * 32), 0, s, io, C, sc);
+    if (dir == 0) return launch_pdl(false, sweep_x2d<R>, dim3(blocks), dim3(kWarpsPerBlock * 32), 0, s, io, C, sc);
+    return cudaErrorInvalidValue;
 }
 
 template <class R>

@@ -79,6 +79,7 @@ template <class R>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int strip = gw % io.nstrips;
@@ -227,6 +228,7 @@ template <class R>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int strip = gw % io.nstrips;

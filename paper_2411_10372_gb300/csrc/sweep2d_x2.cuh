@@ -240,7 +240,9 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
     const RowRing ring{ring_mem + threadIdx.x};
     auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
     auto gz_of = [&](int j) { return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz)); };
-    const int j0 = ks - 2;
+    // the first step is j0 = ks - 1 (primed with row ks - 2): no output row
+    // >= ks uses anything an earlier step would produce
+    const int j0 = ks - 1;
     for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in + row_off(j0 + q), fs);
 
     const f2 z0 = bc(0.f);
@@ -352,7 +354,7 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         d1 = d0; dd1 = dd0; ss2 = ss1;
     };
 
-    // steps j0 .. ke+1: four that only fill the pipeline, then one output row
+    // steps j0 .. ke+1: three that only fill the pipeline, then one output row
     // per step.  Segments clear of the plates and of the grid ends run a
     // specialised step without plate rules, clamping or range tests, two
     // steps per trip so the pipeline registers swap roles instead of being
@@ -381,6 +383,7 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
 __global__ void __launch_bounds__(kThreads2, 4)
 sweep_z2d_x2(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 {
+    pdl_enter();
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     z2_body(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
 }
@@ -430,7 +433,8 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
         const f2 idx_ = bc(C.inv_dx), i2dz = bc(C.inv_2dz);
         const f2 z0 = bc(0.f);
 
-        const int j0 = ks - 2;
+        // the first step is j0 = ks - 1 (primed with row ks - 2), as in z2_body
+        const int j0 = ks - 1;
         for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in + row_off(j0 + q), fs);
 
         S2 Xm1 = ld2(io.in, fs, row_off(j0 - 1));
@@ -528,7 +532,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
             ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
         };
 
-        // steps j0 .. ke+1: four that only fill the pipeline, then one output row
+        // steps j0 .. ke+1: three that only fill the pipeline, then one output row
         // per step.  Segments clear of the plates and of the grid ends run a
         // specialised step without plate rules, clamping or range tests, two
         // steps per trip so the pipeline registers swap roles instead of being
@@ -559,6 +563,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
 __global__ void __launch_bounds__(kThreads2, 4)
 sweep_x2d_x2(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 {
+    pdl_enter();
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     x2_body(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
 }

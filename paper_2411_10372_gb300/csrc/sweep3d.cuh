@@ -62,6 +62,7 @@ template <class R, int AL, int NW>
 __global__ void __launch_bounds__(NW * 32)
 sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 {
+    pdl_enter();
     constexpr int WD = (AL == 2) ? 1 : 2;  // direction of the warps
     // [row parity][u_AL, u_W of X at row j; u_AL, u_W of X^P at row j-1][warp][lane]
     __shared__ R xs[2][4][NW][32];
@@ -278,6 +279,7 @@ template <class R, int NW>
 __global__ void __launch_bounds__(NW * 32)
 sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 {
+    pdl_enter();
     __shared__ R xs[2][4][NW][32];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
