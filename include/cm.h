@@ -157,6 +157,11 @@ int cm_set_state(const double* host);
  * the final state to diag_out (host, may be NULL).  Blocking. */
 int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* diag_out);
 
+/* cm_run_host for an FP32 context with dense float32 host buffers (the
+ * state's own precision: half the bytes over the host link).  CM_EINVAL on
+ * an FP64 context.  Blocking. */
+int cm_run_host_f32(const float* state_in, int nsteps, float* state_out, cm_diag* diag_out);
+
 /* Queue exactly one directional sweep L_dir(Delta) (dir 0 = x, 1 = y, 2 = z)
  * on the current state (Sec. 3.1 predictor, corrector, average and TVD term),
  * without touching dt or time.  For tests of single operators. */

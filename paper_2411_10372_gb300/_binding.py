@@ -74,6 +74,7 @@ _SIGS = {
     "cm_sync": (ctypes.c_int, []),
     "cm_save": (ctypes.c_int, [ctypes.c_char_p]),
     "cm_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cm_run_host_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cm_diag)]),
     "cm_adj_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "cm_adj_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "cm_diag_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(cm_grid), ctypes.c_int,
@@ -253,6 +254,21 @@ def _any_ptr(a):
         assert a.is_contiguous() and str(a.dtype) == "torch.float64"
         return ctypes.c_void_p(a.data_ptr())
     raise TypeError("expected a float64 numpy array or torch tensor")
+
+
+def _fp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def cm_run_host_f32(state_in: np.ndarray | None, nsteps: int, state_out: np.ndarray | None = None,
+                    want_diag: bool = True):
+    """cm_run_host with float32 host arrays (FP32 contexts)."""
+    d = cm_diag()
+    _check(lib().cm_run_host_f32(_fp(state_in), int(nsteps), _fp(state_out), ctypes.byref(d) if want_diag else None))
+    return d.as_dict() if want_diag else None
 
 
 def cm_adj_forward(nsteps: int, K: int, win_begin: int) -> float:

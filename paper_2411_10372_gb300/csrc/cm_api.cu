@@ -555,6 +555,42 @@ int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* 
     return CM_OK;
 }
 
+int cm_run_host_f32(const float* state_in, int nsteps, float* state_out, cm_diag* diag_out)
+{
+    NEED_CTX();
+    Ctx* c = g_ctx;
+    if (c->prec != CM_FP32) return fail(CM_EINVAL, "cm_run_host_f32 needs an FP32 context");
+    if (nsteps < 0) return fail(CM_EINVAL, "nsteps must be >= 0");
+    int rc;
+    float* dense32 = nullptr;
+    if ((state_in || state_out) && (rc = ensure_dense(c))) return rc;
+    dense32 = (float*)c->dense;  // the FP64 staging area holds twice as many floats
+    const size_t bytes = dense_count(c) * sizeof(float);
+    if (state_in) {
+        CK(cudaMemcpyAsync(dense32, state_in, bytes, cudaMemcpyHostToDevice, c->stream));
+        cudaError_t e = Launch<float>::pack32(dense32, (float*)c->buf[c->cur], c->cf, c->nf, c->stream);
+        if (e != cudaSuccess) return fail(CM_ECUDA, "pack launch: %s", cudaGetErrorString(e));
+        c->launches++;
+        if ((rc = recompute_dt(c, (int)(c->step & 1)))) return rc;
+    }
+    if ((rc = queue_steps(c, nsteps))) return rc;
+    if (state_out) {
+        cudaError_t e = Launch<float>::unpack32((const float*)c->buf[c->cur], dense32, c->cf, c->nf, c->stream);
+        if (e != cudaSuccess) return fail(CM_ECUDA, "unpack launch: %s", cudaGetErrorString(e));
+        c->launches++;
+        CK(cudaMemcpyAsync(state_out, dense32, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (diag_out) {
+        if ((rc = sample(c))) return rc;
+        c->ring_count--;
+        const int slot = (c->ring_head + c->ring_count) % c->ring_cap;
+        CK(cudaMemcpyAsync(diag_out, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    if (diag_out && diag_out->status != CM_OK) return fail(CM_ENAN, "non-finite value in the final state");
+    return CM_OK;
+}
+
 int cm_sweep(int dir, double Delta)
 {
     NEED_CTX();

@@ -42,6 +42,9 @@ struct Launch {
     // dense float64 [nf][nz][ny][nx] <-> pitched state in R
     static cudaError_t pack(const double* dense, R* X, const Coef<R>& C, int nf, cudaStream_t s);
     static cudaError_t unpack(const R* X, double* dense, const Coef<R>& C, int nf, cudaStream_t s);
+    // the same with a dense float32 array
+    static cudaError_t pack32(const float* dense, R* X, const Coef<R>& C, int nf, cudaStream_t s);
+    static cudaError_t unpack32(const R* X, float* dense, const Coef<R>& C, int nf, cudaStream_t s);
 };
 
 // FP32 sweeps with two columns per lane (nx even); defined in kernels_f32.cu

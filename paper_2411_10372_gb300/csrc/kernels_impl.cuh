@@ -8,8 +8,8 @@
 
 namespace cm {
 
-template <class R>
-__global__ void pack_state(const double* __restrict__ dense, R* __restrict__ X, Coef<R> C, int nf)
+template <class R, class S>
+__global__ void pack_state(const S* __restrict__ dense, R* __restrict__ X, Coef<R> C, int nf)
 {
     const long long plane = (long long)C.nx * C.ny * C.nz;
     const long long total = plane * nf;
@@ -22,8 +22,8 @@ __global__ void pack_state(const double* __restrict__ dense, R* __restrict__ X, 
     }
 }
 
-template <class R>
-__global__ void unpack_state(const R* __restrict__ X, double* __restrict__ dense, Coef<R> C, int nf)
+template <class R, class S>
+__global__ void unpack_state(const R* __restrict__ X, S* __restrict__ dense, Coef<R> C, int nf)
 {
     const long long plane = (long long)C.nx * C.ny * C.nz;
     const long long total = plane * nf;
@@ -32,7 +32,7 @@ __global__ void unpack_state(const R* __restrict__ X, double* __restrict__ dense
         const long long r = n % plane;
         const int i = (int)(r % C.nx);
         const long long row = r / C.nx;
-        dense[n] = (double)X[f * C.fstride + row * C.pitch + i];
+        dense[n] = (S)X[f * C.fstride + row * C.pitch + i];
     }
 }
 
@@ -204,14 +204,28 @@ cudaError_t Launch<R>::diag_planes(const R* X, const Coef<R>& C, const DiagArgs&
 template <class R>
 cudaError_t Launch<R>::pack(const double* dense, R* X, const Coef<R>& C, int nf, cudaStream_t s)
 {
-    pack_state<R><<<grid_for((long long)C.nx * C.ny * C.nz * nf, 256), 256, 0, s>>>(dense, X, C, nf);
+    pack_state<R, double><<<grid_for((long long)C.nx * C.ny * C.nz * nf, 256), 256, 0, s>>>(dense, X, C, nf);
     return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t Launch<R>::unpack(const R* X, double* dense, const Coef<R>& C, int nf, cudaStream_t s)
 {
-    unpack_state<R><<<grid_for((long long)C.nx * C.ny * C.nz * nf, 256), 256, 0, s>>>(X, dense, C, nf);
+    unpack_state<R, double><<<grid_for((long long)C.nx * C.ny * C.nz * nf, 256), 256, 0, s>>>(X, dense, C, nf);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t Launch<R>::pack32(const float* dense, R* X, const Coef<R>& C, int nf, cudaStream_t s)
+{
+    pack_state<R, float><<<grid_for((long long)C.nx * C.ny * C.nz * nf, 256), 256, 0, s>>>(dense, X, C, nf);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t Launch<R>::unpack32(const R* X, float* dense, const Coef<R>& C, int nf, cudaStream_t s)
+{
+    unpack_state<R, float><<<grid_for((long long)C.nx * C.ny * C.nz * nf, 256), 256, 0, s>>>(X, dense, C, nf);
     return cudaGetLastError();
 }
 

@@ -202,6 +202,32 @@ def test_mass_conservation_and_diag_ring():
     s.close()
 
 
+def test_run_host_f32_matches_run_host():
+    """The float32 host-buffer entry point moves the FP32 state without
+    rounding: same final state and diagnostics as the float64 one."""
+    import paper_2411_10372_gb300 as cm
+    s = cm.Solver(256, 64, 1e6, precision="fp32")
+    try:
+        s.step(5)
+        X = s.state()
+        out64 = np.empty_like(X)
+        d64 = cm.cm_run_host(X, 3, out64)
+        out32 = np.empty(X.shape, dtype=np.float32)
+        d32 = cm.cm_run_host_f32(X.astype(np.float32), 3, out32)
+        assert np.array_equal(out32.astype(np.float64), out64)
+        for k in ("Nu", "Nu_bar", "Re", "mass", "energy", "dt"):
+            assert d32[k] == d64[k], k
+    finally:
+        s.close()
+    s = cm.Solver(64, 17, 1e6, precision="fp64")
+    try:
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_run_host_f32(None, 1)
+        assert e.value.code == cm.CM_EINVAL
+    finally:
+        s.close()
+
+
 def test_checkpoint_roundtrip(tmp_path):
     cfg = O.Config(nx=64, nz=17, Ra=1e6)
     s = solver_for(cfg)
