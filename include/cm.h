@@ -100,11 +100,15 @@ typedef struct cm_diag {
     int pad_;
 } cm_diag;
 
-/* Fill *p with the defaults listed in cm_params.  Never fails for p != NULL. */
+/* Fill *p with the defaults listed in cm_params (eps, D, plate temperatures
+ * and the Stokes coefficient of Sec. 2; CFL and TVD form are the readings of
+ * Sec. 3.1 stated in cm_params).  Never fails for p != NULL. */
 int cm_default_params(cm_params* p);
 
-/* Bytes of device memory the two state buffers need (for cm_params.state_buf).
- * grid: host; precision: CM_FP64 or CM_FP32; bytes: host out. */
+/* Bytes of device memory the two state buffers need (for cm_params.state_buf);
+ * the state is the conserved vector (rho, m, E) of Sec. 3.1 in the layout of
+ * cm_state_layout.  grid: host; precision: CM_FP64 or CM_FP32; bytes: host out.
+ * CM_EINVAL for a bad grid or precision. */
 int cm_state_bytes(const cm_grid* grid, int precision, unsigned long long* bytes);
 
 /* Create the context and write the initial state: the
@@ -131,11 +135,15 @@ int cm_sample(void);
 
 /* Wait for the stream, then copy up to max queued samples (oldest first) to
  * out (host, max entries) and drop them; *n_out (host) receives the count.
+ * Each record holds Nu (Eq. volume_Nu), Nu_0, Nu_1 and Nu_bar (Eq. mean_Nu),
+ * Re (Eq. Re, instantaneous) and the budgets of Sec. 2, reduced in FP64.
  * Returns CM_ENAN if any copied sample saw a non-finite value. */
 int cm_diagnostics(cm_diag* out, int max, int* n_out);
 
-/* Device pointer to field f (0 <= f < nfields) of the current state, or NULL
- * if there is no context or f is out of range.  Layout: see cm_state_layout. */
+/* Device pointer to field f (0 <= f < nfields) of the current state vector
+ * (Sec. 3.1: rho, m_x, (m_y,) m_z, E), or NULL if there is no context or f is
+ * out of range.  Layout: see cm_state_layout.  The library owns the memory
+ * unless cm_params.state_buf was given. */
 void* cm_state_ptr(int field);
 
 /* Layout of the current state on the device: element (k, j, i) of field f is
@@ -143,8 +151,8 @@ void* cm_state_ptr(int field);
  * All arguments are host out-pointers; any may be NULL. */
 int cm_state_layout(int* pitch, int* nfields, int* elem_bytes);
 
-/* Wait for the stream and copy the current state into host (dense float64,
- * nfields*nz*ny*nx values, layout in the header comment). */
+/* Wait for the stream and copy the current state vector (Sec. 3.1) into host
+ * (dense float64, nfields*nz*ny*nx values, layout in the header comment). */
 int cm_get_state(double* host);
 
 /* Replace the current state by host (dense float64, same layout; converted
@@ -152,7 +160,8 @@ int cm_get_state(double* host);
 int cm_set_state(const double* host);
 
 /* End-to-end call with host buffers: upload state_in (host, dense float64,
- * may be NULL to keep the device state), run nsteps steps, then write the
+ * may be NULL to keep the device state), run nsteps steps of Eq. time_step
+ * (as cm_step), then write the
  * final state to state_out (host, may be NULL) and one diagnostics sample of
  * the final state to diag_out (host, may be NULL).  Blocking. */
 int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* diag_out);
@@ -167,10 +176,14 @@ int cm_run_host_f32(const float* state_in, int nsteps, float* state_out, cm_diag
  * without touching dt or time.  For tests of single operators. */
 int cm_sweep(int dir, double Delta);
 
-/* Wait for the stream; *dt (host) = the dt the next step will use. */
+/* Wait for the stream; *dt (host) = the dt the next step will use: CFL times
+ * the minimum over nodes and directions of h/(|u_alpha| + c), c^2 = gamma p/rho
+ * (the paper leaves dt to the Courant condition of Sec. 3.1; this is the
+ * stated reading), or dt_fixed. */
 int cm_get_dt(double* dt);
 
-/* Wait for the stream; simulated time and completed steps (host out). */
+/* Wait for the stream; simulated time (the sum of the steps' dt, Eq.
+ * time_step) and completed steps (host out). */
 int cm_get_time(double* t, long long* steps);
 
 /* Measurement: queue n steps exactly as cm_step does, with CUDA events
@@ -186,10 +199,11 @@ int cm_get_time(double* t, long long* steps);
  * cm_step.  n >= 1. */
 int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, double* step_ms);
 
-/* Number of CUDA kernel launches this context has queued since cm_init. */
+/* Number of CUDA kernel launches this context has queued since cm_init
+ * (measurement; no paper passage). */
 long long cm_launch_count(void);
 
-/* Wait for all queued work of the context. */
+/* Wait for all queued work of the context (no paper passage). */
 int cm_sync(void);
 
 /* Write / read a checkpoint: a header {magic, version, grid, precision,
@@ -210,10 +224,13 @@ int cm_load(const char* path);
 
 /* nbox >= 1; grids, Ra: host arrays of nbox (2D grids, even nx); params:
  * host (precision must be CM_FP32; stream NULL = a stream the batch creates,
- * otherwise a stream that can be captured).  Blocking. */
+ * otherwise a stream that can be captured).  Each box gets the initial state
+ * of cm_init (seed + box index) and is advanced by Eq. time_step (Sec. 3.1)
+ * with its own dt.  CM_EINVAL for an odd nx, an FP64 precision or a bad grid.
+ * Blocking. */
 int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, double gamma, const cm_params* params);
 
-/* Queue n steps of every box (asynchronous). */
+/* Queue n steps (Eq. time_step) of every box (asynchronous). */
 int cm_batch_step(int n);
 
 /* One diagnostics sample of every box now (Sec. 2 definitions); out: host,
