@@ -19,6 +19,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   dt ............... closed form on the conduction state
   diag ............. Nu = 1 on the conduction state, analytic fields
   advect1d ......... total-variation test of the TVD reading
+  torch_ref.py ..... PyTorch restatement of the 2D step for autograd (the
+                     adjoint's reference): equal to this oracle state by
+                     state and in Nu_bar; its gradient equals central
+                     differences of this oracle (tests/test_torch_ref_pins.py)
 """
 from __future__ import annotations
 

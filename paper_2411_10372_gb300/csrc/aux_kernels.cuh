@@ -81,19 +81,19 @@ __global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int s
             if (C.ndim == 3) r = fmaxf(r, (fabsf(uy) + c) * C.inv_dy);
             if (!(r > 0.f) || !(r < 1e30f)) bad = 1;
             rmax = fmaxf(rmax, r);
-            continue;
+        } else {
+            // same operation order as the sweeps' FP64 path (divisions by rho)
+            const double rho = (double)p[0];
+            double ux = (double)p[fs] / rho, uy = 0.0, uz, E;
+            if (C.ndim == 3) { uy = (double)p[2 * fs] / rho; uz = (double)p[3 * fs] / rho; E = (double)p[4 * fs]; }
+            else { uz = (double)p[2 * fs] / rho; E = (double)p[3 * fs]; }
+            const double T = (double)C.b * (E / rho - 0.5 * ((ux * ux + uy * uy) + uz * uz) - (double)C.g * (double)zt[k]);
+            const double c = sqrt((double)C.cs2 * T);
+            double v = fmin(C.dx / (fabs(ux) + c), C.dz / (fabs(uz) + c));
+            if (C.ndim == 3) v = fmin(v, C.dy / (fabs(uy) + c));
+            if (!(v > 0.0) || !(v < 1e300)) bad = 1;
+            vmin = fmin(vmin, v);
         }
-        // same operation order as the sweeps' FP64 path (divisions by rho)
-        const double rho = (double)p[0];
-        double ux = (double)p[fs] / rho, uy = 0.0, uz, E;
-        if (C.ndim == 3) { uy = (double)p[2 * fs] / rho; uz = (double)p[3 * fs] / rho; E = (double)p[4 * fs]; }
-        else { uz = (double)p[2 * fs] / rho; E = (double)p[3 * fs]; }
-        const double T = (double)C.b * (E / rho - 0.5 * ((ux * ux + uy * uy) + uz * uz) - (double)C.g * (double)zt[k]);
-        const double c = sqrt((double)C.cs2 * T);
-        double v = fmin(C.dx / (fabs(ux) + c), C.dz / (fabs(uz) + c));
-        if (C.ndim == 3) v = fmin(v, C.dy / (fabs(uy) + c));
-        if (!(v > 0.0) || !(v < 1e300)) bad = 1;
-        vmin = fmin(vmin, v);
     }
     if constexpr (!kExact<R>) vmin = rmax > 0.f ? 1.0 / (double)rmax : 1e308;
     block_dt_reduce(vmin, bad, ctl, slot);
@@ -160,26 +160,26 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
             v[6] += (double)T;
             v[7] = fmax(v[7], (double)(sqrtf(u2) / sqrtf((float)A.cs2 * T)));
             if (!isfinite(E + rho + T + u2)) bad = 1;
-            continue;
+        } else {
+            const double rho = (double)p[0];
+            const double u = (double)p[fs] / rho;
+            double vy = 0.0, w, E;
+            if (C.ndim == 3) { vy = (double)p[2 * fs] / rho; w = (double)p[3 * fs] / rho; E = (double)p[4 * fs]; }
+            else { w = (double)p[2 * fs] / rho; E = (double)p[3 * fs]; }
+            const double u2 = u * u + vy * vy + w * w;
+            const double T = A.b * (E / rho - 0.5 * u2 - A.g * z);
+            const double Tsa = T - (1.0 - A.D * z);
+            v[0] += rho;
+            v[1] += E;
+            v[2] += rho * w * Tsa;
+            v[3] += rho * w * u2;
+            v[4] += u2;
+            v[5] += 0.5 * rho * u2;
+            v[6] += T;
+            const double M = sqrt(u2) / sqrt(A.cs2 * T);
+            v[7] = fmax(v[7], M);
+            if (!isfinite(E + rho + T + u2)) bad = 1;
         }
-        const double rho = (double)p[0];
-        const double u = (double)p[fs] / rho;
-        double vy = 0.0, w, E;
-        if (C.ndim == 3) { vy = (double)p[2 * fs] / rho; w = (double)p[3 * fs] / rho; E = (double)p[4 * fs]; }
-        else { w = (double)p[2 * fs] / rho; E = (double)p[3 * fs]; }
-        const double u2 = u * u + vy * vy + w * w;
-        const double T = A.b * (E / rho - 0.5 * u2 - A.g * z);
-        const double Tsa = T - (1.0 - A.D * z);
-        v[0] += rho;
-        v[1] += E;
-        v[2] += rho * w * Tsa;
-        v[3] += rho * w * u2;
-        v[4] += u2;
-        v[5] += 0.5 * rho * u2;
-        v[6] += T;
-        const double M = sqrt(u2) / sqrt(A.cs2 * T);
-        v[7] = fmax(v[7], M);
-        if (!isfinite(E + rho + T + u2)) bad = 1;
     }
     block_sum_q(v, scratch + (size_t)k * kDiagQ);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, 1);
