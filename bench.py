@@ -170,11 +170,12 @@ def run_gpu(args):
         launches = cm.cm_launch_count() - launches0
         s.sync()
         total_ms = max_ms(sum(step_ms))
+        seg = cm.cm_tuning()
         # per-kernel durations for the roofline: a second timed pass with an
         # event pair around every sweep (each duration includes its launch gap)
         sweep_ms, _ = cm.cm_profile_steps(max(3, min(K, 500)), FLUSH_BYTES, per_sweep=True)
         out = dict(total_ms=total_ms, sweep_ms=sweep_ms, launches=launches, clocks=clk.summary() if clocks else None,
-                   w=8 if precision == "fp64" else 4)
+                   w=8 if precision == "fp64" else 4, segments={"z": seg[0], "x": seg[1]})
         return s, out
 
     # ---- FP32 state: the timed line ----
@@ -309,14 +310,16 @@ def run_gpu(args):
     s64, r64 = measure("fp64", k64, min(args.warmup, 3), clocks=False)
     s64.close()
 
-    def measured_traffic(kernel: str):
+    def measured_traffic(kernel: str, segments: dict):
         """DRAM bytes per launch of `kernel` from the committed ncu capture, if
-        its kernel sources are unchanged since (else None)."""
+        its kernel sources and segment lengths are unchanged since (else None)."""
         import hashlib
         path = os.path.join(ROOT, "profiles", "sweep2d_fp32_x2_4096x1024_traffic.json")
         if (NXr, NZr) != (NX, NZ) or not os.path.exists(path):
             return None
         rec = json.load(open(path))
+        if rec.get("segment_rows") != segments:
+            return None
         for name, digest in rec["source_sha256"].items():
             src = os.path.join(ROOT, "paper_2411_10372_gb300", "csrc", name)
             if hashlib.sha256(open(src, "rb").read()).hexdigest() != digest:
@@ -335,7 +338,7 @@ def run_gpu(args):
         achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
         return {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
-                "traffic": measured_traffic(dom) if w == 4 else None,
+                "traffic": measured_traffic(dom, r["segments"]) if w == 4 else None,
                 "bytes_per_launch": bytes_per_launch, "ms_per_launch": round(per_launch_ms, 5)}
 
     K = args.steps
@@ -353,6 +356,7 @@ def run_gpu(args):
                    "timing": "events at step boundaries for value; per-sweep events in a second pass for roofline"},
         "roofline": roofline(r32),
         "sweep_ms": [round(x, 5) for x in r32["sweep_ms"]],
+        "segment_rows": r32["segments"],
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * cells * 4,

@@ -74,6 +74,7 @@ _SIGS = {
     "cm_sync": (ctypes.c_int, []),
     "cm_save": (ctypes.c_int, [ctypes.c_char_p]),
     "cm_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cm_tuning": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cm_run_host_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cm_diag)]),
     "cm_adj_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "cm_adj_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
@@ -215,6 +216,13 @@ def cm_profile_steps(n: int, flush_bytes: int = 0, per_sweep: bool = True) -> tu
         return [], list(steps)
     _, nf, _ = cm_state_layout()
     return list(ms)[: 6 if nf == 5 else 4], list(steps)
+
+
+def cm_tuning() -> tuple[int, int]:
+    """(rows per segment of the z sweep, of the x sweep) chosen at cm_init (0 = model)."""
+    z, x = ctypes.c_int(), ctypes.c_int()
+    _check(lib().cm_tuning(ctypes.byref(z), ctypes.byref(x)))
+    return z.value, x.value
 
 
 def cm_launch_count() -> int:

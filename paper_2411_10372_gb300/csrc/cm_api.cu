@@ -57,7 +57,7 @@ struct Ctx {
     cudaStream_t stream;
     long long step;
     long long launches;
-    int seg_rows;
+    int seg_z, seg_x;           // rows per warp segment of the packed FP32 2D sweeps (0 = model)
     Coef<double> cd;
     Coef<float> cf;
     double a, b, g, cs2;
@@ -135,10 +135,10 @@ int sweep(Ctx* c, int dir, const SweepCtl& sc)
     cudaError_t e;
     if (c->prec == CM_FP64)
         e = Launch<double>::sweep(dir, (const double*)c->buf[c->cur], (double*)c->buf[c->cur ^ 1],
-                                  (const double*)c->zt_r, c->cd, sc, c->seg_rows, c->stream);
+                                  (const double*)c->zt_r, c->cd, sc, 0, c->stream);
     else
         e = Launch<float>::sweep(dir, (const float*)c->buf[c->cur], (float*)c->buf[c->cur ^ 1],
-                                 (const float*)c->zt_r, c->cf, sc, c->seg_rows, c->stream);
+                                 (const float*)c->zt_r, c->cf, sc, dir == 2 ? c->seg_z : c->seg_x, c->stream);
     if (e != cudaSuccess) return fail(CM_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
     c->launches++;
     c->cur ^= 1;
@@ -334,6 +334,60 @@ int cm_state_bytes(const cm_grid* grid, int precision, unsigned long long* bytes
     return CM_OK;
 }
 
+// Segment length of the packed FP32 2D sweeps (rows per warp).  Their time
+// at a grid size depends on it in ways no simple occupancy model captures
+// (measured at 4096 x 1024: 29 rows 0.140 ms per step, 32 rows 0.160, 28 rows
+// 0.161, 24 rows 0.150), so each direction is timed at a fixed list of
+// lengths and the fastest kept.  The sweeps read the current state and write
+// the spare buffer, so the state, dt and time are untouched; the choice only
+// changes how the work is split (the result only at FP32 rounding level).
+int tune_segments(Ctx* c)
+{
+    if (c->prec != CM_FP32 || c->grid.ndim != 2 || (c->grid.nx & 1) || getenv("CM_SEG_ROWS")) return CM_OK;
+    static const int cand[] = {12, 16, 18, 20, 21, 22, 24, 26, 28, 29, 30, 31, 32, 36, 40, 48, 64, 96, 128};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    SweepCtl sc;
+    std::memset(&sc, 0, sizeof sc);
+    sc.ctl = c->ctl;
+    sc.slot_in = (int)(c->step & 1);
+    sc.Delta = 1e-9;
+    const float* in = (const float*)c->buf[c->cur];
+    float* spare = (float*)c->buf[c->cur ^ 1];
+    int best_seg[3] = {0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int dir = 0; dir <= 2 && e == cudaSuccess; dir += 2) {
+        float best = 1e30f;
+        for (int seg : cand) {
+            if (seg > c->grid.nz) break;
+            float t_min = 1e30f;
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                e = Launch<float>::sweep(dir, in, spare, (const float*)c->zt_r, c->cf, sc, seg, c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+                for (int q = 0; q < 4 && e == cudaSuccess; ++q)
+                    e = Launch<float>::sweep(dir, in, spare, (const float*)c->zt_r, c->cf, sc, seg, c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                t_min = std::min(t_min, t);
+                c->launches += 5;
+            }
+            if (t_min < best) {
+                best = t_min;
+                best_seg[dir] = seg;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "segment tuning: %s", cudaGetErrorString(e));
+    c->seg_x = best_seg[0];
+    c->seg_z = best_seg[2];
+    return CM_OK;
+}
+
 int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_params* params)
 {
     int rc = check_grid(grid);
@@ -371,14 +425,7 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     c->b = gamma * P.eps * P.D;
     c->g = P.gravity / P.eps;
     c->cs2 = gamma * c->a;
-    // rows per warp segment: long segments amortise the 4-row pipeline
-    // ramp; shorter ones when the grid has too few strips to fill the GPU
-    {
-        const long long strips = (grid->nx + kOutW - 1) / kOutW;
-        int seg = 64;
-        while (seg > 16 && strips * ((grid->nz + seg - 1) / seg) < 152LL * 16) seg /= 2;
-        c->seg_rows = seg;
-    }
+    c->seg_z = c->seg_x = 0;  // occupancy model until tune_segments
     fill_coef(c->cd, *c);
     fill_coef(c->cf, *c);
 
@@ -461,7 +508,16 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     const double dnum = nu * 0.5 * dt0 / (hh * hh);
     if (dnum > 0.5)
         return bail(fail(CM_EUNSTABLE, "explicit diffusion number %.3g > 0.5 at dt = %.3g: refine dt (dt_fixed) or raise Ra", dnum, dt0));
+    if ((rc = tune_segments(c))) return bail(rc);
     g_ctx = c;
+    return CM_OK;
+}
+
+int cm_tuning(int* seg_z, int* seg_x)
+{
+    NEED_CTX();
+    if (seg_z) *seg_z = g_ctx->seg_z;
+    if (seg_x) *seg_x = g_ctx->seg_x;
     return CM_OK;
 }
 
@@ -826,7 +882,7 @@ int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
                 sc.first = q == 0;
                 sc.last = q == 3;
                 e = Launch<double>::sweep(order[q], stored(4 * s + q), stored(4 * s + q + 1),
-                                          (const double*)c->zt_r, c->cd, sc, c->seg_rows, c->stream);
+                                          (const double*)c->zt_r, c->cd, sc, 0, c->stream);
                 c->launches++;
             }
             if (e != cudaSuccess) return fail(CM_ECUDA, "adjoint forward: %s", cudaGetErrorString(e));
@@ -916,8 +972,8 @@ int cm_adj_backward(double* grad_X0, double* grad_T0, double* grad_Ra)
             sc.Delta = 0.5 * A->dts[s];
             for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
                 const int at = 4 * (s - s0) + q;
-                e = Launch<double>::sweep(order[q], slot(at), slot(at + 1), (const double*)c->zt_r, c->cd, sc,
-                                          c->seg_rows, c->stream);
+                e = Launch<double>::sweep(order[q], slot(at), slot(at + 1), (const double*)c->zt_r, c->cd, sc, 0,
+                                          c->stream);
                 c->launches++;
             }
         }

@@ -32,7 +32,8 @@ cudaError_t launch_pdl(bool pdl, K kernel, dim3 grid, dim3 block, size_t smem, c
 
 template <class R>
 struct Launch {
-    // one sweep L_dir (dir 0 = x, 1 = y (3D only), 2 = z)
+    // one sweep L_dir (dir 0 = x, 1 = y (3D only), 2 = z); seg_rows: rows per
+    // warp segment of the packed FP32 2D sweeps (0 = occupancy model)
     static cudaError_t sweep(int dir, const R* in, R* out, const R* zt, const Coef<R>& C, const SweepCtl& sc,
                              int seg_rows, cudaStream_t s);
     static cudaError_t init(R* X, const Coef<R>& C, const InitArgs& A, cudaStream_t s);
@@ -47,9 +48,11 @@ struct Launch {
     static cudaError_t unpack32(const R* X, float* dense, const Coef<R>& C, int nf, cudaStream_t s);
 };
 
-// FP32 sweeps with two columns per lane (nx even); defined in kernels_f32.cu
+// FP32 sweeps with two columns per lane (nx even); defined in kernels_f32.cu.
+// seg_rows > 0 sets the rows per warp segment, 0 leaves it to the occupancy
+// model (CM_SEG_ROWS in the environment overrides both)
 cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
-                            const SweepCtl& sc, cudaStream_t s);
+                            const SweepCtl& sc, int seg_rows, cudaStream_t s);
 
 // one batched sweep over every box of a batch (kernels_f32.cu); nblocks from the work list
 struct BatchLaunch;

@@ -8,7 +8,7 @@ namespace cm {
 template struct Launch<float>;
 
 cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
-                            const SweepCtl& sc, cudaStream_t s)
+                            const SweepCtl& sc, int seg_rows, cudaStream_t s)
 {
     SweepIO2 io;
     io.in = in;
@@ -22,7 +22,8 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
         bz = blocks_per_sm(sweep_z2d_x2, kRingBytes);
         bx = blocks_per_sm(sweep_x2d_x2, kRingBytes);
     }
-    io.seg_rows = pick_segment(io.nstrips, C.nz, dir == 2 ? bz : bx, sm_count());
+    io.seg_rows = (seg_rows > 0 && !getenv("CM_SEG_ROWS")) ? seg_rows
+                                                           : pick_segment(io.nstrips, C.nz, dir == 2 ? bz : bx, sm_count());
     const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
     const long long warps = (long long)io.nstrips * nsegs;
     const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);

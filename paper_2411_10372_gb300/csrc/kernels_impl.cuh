@@ -159,7 +159,8 @@ cudaError_t Launch<R>::sweep(int dir, const R* in, R* out, const R* zt, const Co
 {
     if (C.ndim == 3) return sweep3(dir, in, out, zt, C, sc, s);
     if constexpr (std::is_same<R, float>::value) {
-        if (C.nx % 2 == 0 && (long long)C.fstride * 5 < (1LL << 31)) return launch_sweep_x2(dir, in, out, zt, C, sc, s);
+        if (C.nx % 2 == 0 && (long long)C.fstride * 5 < (1LL << 31))
+            return launch_sweep_x2(dir, in, out, zt, C, sc, seg_rows, s);
     }
     (void)seg_rows;
     SweepIO<R> io;
