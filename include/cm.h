@@ -199,10 +199,10 @@ int cm_get_time(double* t, long long* steps);
  * cm_step.  n >= 1. */
 int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, double* step_ms);
 
-/* Rows per warp segment that cm_init chose for the FP32 2D sweeps along z and
- * x by timing a fixed list of lengths (0 = the occupancy model: FP64, 3D,
- * odd nx, or CM_SEG_ROWS set).  The work split only; no paper passage.
- * Host out-pointers, may be NULL. */
+/* Rows per warp segment that cm_init chose for the FP32 sweeps along z and x
+ * by timing a fixed list of lengths (0 = the occupancy model: FP64, odd nx in
+ * 2D, or CM_SEG_ROWS set).  The work split only; no paper passage.  Host
+ * out-pointers, may be NULL. */
 int cm_tuning(int* seg_z, int* seg_x);
 
 /* Number of CUDA kernel launches this context has queued since cm_init

@@ -57,7 +57,7 @@ struct Ctx {
     cudaStream_t stream;
     long long step;
     long long launches;
-    int seg_z, seg_x;           // rows per warp segment of the packed FP32 2D sweeps (0 = model)
+    int seg[3];                 // rows per segment of the FP32 sweeps by direction x, y, z (0 = model)
     Coef<double> cd;
     Coef<float> cf;
     double a, b, g, cs2;
@@ -138,7 +138,7 @@ int sweep(Ctx* c, int dir, const SweepCtl& sc)
                                   (const double*)c->zt_r, c->cd, sc, 0, c->stream);
     else
         e = Launch<float>::sweep(dir, (const float*)c->buf[c->cur], (float*)c->buf[c->cur ^ 1],
-                                 (const float*)c->zt_r, c->cf, sc, dir == 2 ? c->seg_z : c->seg_x, c->stream);
+                                 (const float*)c->zt_r, c->cf, sc, c->seg[dir], c->stream);
     if (e != cudaSuccess) return fail(CM_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
     c->launches++;
     c->cur ^= 1;
@@ -334,17 +334,23 @@ int cm_state_bytes(const cm_grid* grid, int precision, unsigned long long* bytes
     return CM_OK;
 }
 
-// Segment length of the packed FP32 2D sweeps (rows per warp).  Their time
-// at a grid size depends on it in ways no simple occupancy model captures
-// (measured at 4096 x 1024: 29 rows 0.140 ms per step, 32 rows 0.160, 28 rows
-// 0.161, 24 rows 0.150), so each direction is timed at a fixed list of
-// lengths and the fastest kept.  The sweeps read the current state and write
-// the spare buffer, so the state, dt and time are untouched; the choice only
-// changes how the work is split (the result only at FP32 rounding level).
+// Segment length of the FP32 sweeps (rows per warp segment of the march).
+// Their time at a grid size depends on it in ways no simple occupancy model
+// captures (measured at 4096 x 1024: 29 rows 0.140 ms per step, 32 rows 0.160,
+// 28 rows 0.161, 24 rows 0.150; at 512 x 512 x 128: 64 rows 4.97 ms, the model's
+// 128 rows 5.16 ms), so each direction is timed at a fixed list of lengths and
+// the fastest kept.  The sweeps read the current state and write the spare
+// buffer, so the state, dt and time are untouched; the choice only changes
+// how the work is split (the result only at FP32 rounding level).
 int tune_segments(Ctx* c)
 {
-    if (c->prec != CM_FP32 || c->grid.ndim != 2 || (c->grid.nx & 1) || getenv("CM_SEG_ROWS")) return CM_OK;
-    static const int cand[] = {12, 16, 18, 20, 21, 22, 24, 26, 28, 29, 30, 31, 32, 36, 40, 48, 64, 96, 128};
+    const bool d2 = c->grid.ndim == 2;
+    if (c->prec != CM_FP32 || (d2 && (c->grid.nx & 1)) || getenv("CM_SEG_ROWS")) return CM_OK;
+    static const int cand2[] = {12, 16, 18, 20, 21, 22, 24, 26, 28, 29, 30, 31, 32, 36, 40, 48, 64, 96, 128};
+    static const int cand3[] = {32, 48, 64, 96, 128, 192, 256};
+    const int* cand = d2 ? cand2 : cand3;
+    const int ncand = d2 ? (int)(sizeof cand2 / sizeof cand2[0]) : (int)(sizeof cand3 / sizeof cand3[0]);
+    const int reps = d2 ? 3 : 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -357,15 +363,18 @@ int tune_segments(Ctx* c)
     float* spare = (float*)c->buf[c->cur ^ 1];
     int best_seg[3] = {0, 0, 0};
     cudaError_t e = cudaSuccess;
-    for (int dir = 0; dir <= 2 && e == cudaSuccess; dir += 2) {
+    for (int dir = 0; dir <= 2 && e == cudaSuccess; ++dir) {
+        if (d2 && dir == 1) continue;
+        const int nmarch = dir == 1 ? c->ny : c->grid.nz;
         float best = 1e30f;
-        for (int seg : cand) {
-            if (seg > c->grid.nz) break;
+        for (int q = 0; q < ncand && e == cudaSuccess; ++q) {
+            const int seg = cand[q];
+            if (seg > nmarch) break;
             float t_min = 1e30f;
-            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+            for (int rep = 0; rep < reps && e == cudaSuccess; ++rep) {
                 e = Launch<float>::sweep(dir, in, spare, (const float*)c->zt_r, c->cf, sc, seg, c->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-                for (int q = 0; q < 4 && e == cudaSuccess; ++q)
+                for (int k = 0; k < 4 && e == cudaSuccess; ++k)
                     e = Launch<float>::sweep(dir, in, spare, (const float*)c->zt_r, c->cf, sc, seg, c->stream);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -383,8 +392,7 @@ int tune_segments(Ctx* c)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return fail(CM_ECUDA, "segment tuning: %s", cudaGetErrorString(e));
-    c->seg_x = best_seg[0];
-    c->seg_z = best_seg[2];
+    for (int d = 0; d < 3; ++d) c->seg[d] = best_seg[d];
     return CM_OK;
 }
 
@@ -425,7 +433,7 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     c->b = gamma * P.eps * P.D;
     c->g = P.gravity / P.eps;
     c->cs2 = gamma * c->a;
-    c->seg_z = c->seg_x = 0;  // occupancy model until tune_segments
+    c->seg[0] = c->seg[1] = c->seg[2] = 0;  // occupancy model until tune_segments
     fill_coef(c->cd, *c);
     fill_coef(c->cf, *c);
 
@@ -516,8 +524,8 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
 int cm_tuning(int* seg_z, int* seg_x)
 {
     NEED_CTX();
-    if (seg_z) *seg_z = g_ctx->seg_z;
-    if (seg_x) *seg_x = g_ctx->seg_x;
+    if (seg_z) *seg_z = g_ctx->seg[2];
+    if (seg_x) *seg_x = g_ctx->seg[0];
     return CM_OK;
 }
 

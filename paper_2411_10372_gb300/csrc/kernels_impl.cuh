@@ -128,7 +128,7 @@ static inline int blocks_per_sm3(K kernel)
 // over z), 0 = L_x (march z, warps over y); grid (x strips, W groups, segments)
 template <class R>
 static cudaError_t sweep3(int dir, const R* in, R* out, const R* zt, const Coef<R>& C, const SweepCtl& sc,
-                          cudaStream_t s)
+                          int seg_rows, cudaStream_t s)
 {
     Sweep3IO<R> io;
     io.in = in;
@@ -145,7 +145,9 @@ static cudaError_t sweep3(int dir, const R* in, R* out, const R* zt, const Coef<
         bps[2] = blocks_per_sm3(sweep3d_march<R, 2, kNW3>);
     }
     if (dir < 0 || dir > 2) return cudaErrorInvalidValue;
-    io.seg = pick_segment3((long long)io.nstrips * groups, io.nmarch, bps[dir], sm_count());
+    io.seg = (seg_rows > 0 && !getenv("CM_SEG_ROWS"))
+                 ? seg_rows
+                 : pick_segment3((long long)io.nstrips * groups, io.nmarch, bps[dir], sm_count());
     const int nsegs = (io.nmarch + io.seg - 1) / io.seg;
     const dim3 grid(io.nstrips, groups, nsegs);
     if (dir == 2) return launch_pdl(false, sweep3d_march<R, 2, kNW3>, grid, dim3(kNW3 * 32), 0, s, io, C, sc);
@@ -157,7 +159,7 @@ template <class R>
 cudaError_t Launch<R>::sweep(int dir, const R* in, R* out, const R* zt, const Coef<R>& C, const SweepCtl& sc,
                              int seg_rows, cudaStream_t s)
 {
-    if (C.ndim == 3) return sweep3(dir, in, out, zt, C, sc, s);
+    if (C.ndim == 3) return sweep3(dir, in, out, zt, C, sc, seg_rows, s);
     if constexpr (std::is_same<R, float>::value) {
         if (C.nx % 2 == 0 && (long long)C.fstride * 5 < (1LL << 31))
             return launch_sweep_x2(dir, in, out, zt, C, sc, seg_rows, s);
