@@ -266,3 +266,31 @@ def test_full_size_one_step_fp64_and_fp32():
         for f in (1, 2):
             assert np.linalg.norm(got[f] - want[f]) / scale <= tol, (precision, f)
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_non_finite_state_is_reported(precision):
+    """A NaN planted in a host-built state is caught by the dt reduction and
+    the diagnostics: the host call returns CM_ENAN (no device fault; NaN
+    arithmetic is ordinary)."""
+    import paper_2411_10372_gb300 as cm
+    s = cm.Solver(64, 17, 1e6, precision=precision)
+    try:
+        X = s.state()
+        X[0, 8, 10] = np.nan
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_run_host(X, 1, None, True)
+        assert e.value.code == cm.CM_ENAN
+    finally:
+        s.close()
+
+
+def test_diffusion_limit_is_refused_at_init():
+    """At Ra = 10 on a 256 x 64 grid the explicit diffusion number at the CFL
+    dt exceeds 1/2: cm_init refuses with CM_EUNSTABLE before any step runs."""
+    import paper_2411_10372_gb300 as cm
+    with pytest.raises(cm.CMError) as e:
+        cm.Solver(256, 64, 10.0, precision="fp64")
+    assert e.value.code == cm.CM_EUNSTABLE
+    s = cm.Solver(256, 64, 10.0, precision="fp64", dt_fixed=1e-5)  # a small fixed dt is accepted
+    s.close()
