@@ -133,6 +133,14 @@ int cm_step(int n);
 /* Queue one diagnostics sample of the current state now (Sec. 2 definitions). */
 int cm_sample(void);
 
+/* Horizontal (x, y) means of the current state on every z plane, the
+ * profiles of Sec. 4-5: out (host, nz x 8 doubles, plane k at out[8k..8k+7])
+ * receives <rho>_A, <E>_A, <rho u_z T_sa>_A (convective heat flux),
+ * <rho u_z |u|^2>_A, <|u|^2>_A, <rho |u|^2 / 2>_A, <T>_A and the plane's
+ * maximum Mach number, T_sa = T - (1 - D z); sums in FP64 (FP32 states: the
+ * per-node quantities in FP32).  Blocking. */
+int cm_profiles(double* out);
+
 /* Wait for the stream, then copy up to max queued samples (oldest first) to
  * out (host, max entries) and drop them; *n_out (host) receives the count.
  * Each record holds Nu (Eq. volume_Nu), Nu_0, Nu_1 and Nu_bar (Eq. mean_Nu),

@@ -16,7 +16,7 @@ from ._binding import (cm_adj_backward, cm_adj_forward, cm_batch_diagnostics, cm
                        CM_FP32, CM_FP64, CM_OK, CM_TVD_DAVIS, CM_TVD_OFF, CM_TVD_SUM, CMError, cm_default_params,
                        cm_diag, cm_diag_noalloc, cm_diagnostics, cm_finalize, cm_get_dt, cm_get_state, cm_get_time, cm_grid,
                        cm_init, cm_last_error, cm_launch_count, cm_load, cm_profile_steps, cm_params, cm_run_host,
-                       cm_run_host_f32, cm_sample, cm_tuning,
+                       cm_profiles, cm_run_host_f32, cm_sample, cm_tuning,
                        cm_save, cm_set_state, cm_state_bytes, cm_state_layout, cm_state_ptr, cm_step, cm_sweep,
                        cm_sync, lib)
 

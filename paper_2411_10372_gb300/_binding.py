@@ -74,6 +74,7 @@ _SIGS = {
     "cm_sync": (ctypes.c_int, []),
     "cm_save": (ctypes.c_int, [ctypes.c_char_p]),
     "cm_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cm_profiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "cm_tuning": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cm_run_host_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cm_diag)]),
     "cm_adj_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -216,6 +217,16 @@ def cm_profile_steps(n: int, flush_bytes: int = 0, per_sweep: bool = True) -> tu
         return [], list(steps)
     _, nf, _ = cm_state_layout()
     return list(ms)[: 6 if nf == 5 else 4], list(steps)
+
+
+PROFILE_KEYS = ("rho", "E", "conv_flux", "kin_flux", "u2", "KE", "T", "mach_max")
+
+
+def cm_profiles(nz: int) -> dict:
+    """Plane means of the current state (include/cm.h): name -> array of nz values."""
+    out = np.empty((nz, 8), dtype=np.float64)
+    _check(lib().cm_profiles(out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return {k: out[:, q].copy() for q, k in enumerate(PROFILE_KEYS)}
 
 
 def cm_tuning() -> tuple[int, int]:

@@ -542,6 +542,34 @@ int cm_sample(void)
     return sample(g_ctx);
 }
 
+int cm_profiles(double* out)
+{
+    NEED_CTX();
+    Ctx* c = g_ctx;
+    if (!out) return fail(CM_EINVAL, "out is NULL");
+    DiagArgs A;
+    A.zt = c->zt_d;
+    A.a = c->a;
+    A.b = c->b;
+    A.g = c->g;
+    A.D = c->prm.D;
+    A.cs2 = c->cs2;
+    cudaError_t e = c->prec == CM_FP64
+        ? Launch<double>::diag_planes((const double*)c->buf[c->cur], c->cd, A, c->scratch, c->ctl, c->stream)
+        : Launch<float>::diag_planes((const float*)c->buf[c->cur], c->cf, A, c->scratch, c->ctl, c->stream);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "profiles launch: %s", cudaGetErrorString(e));
+    c->launches++;
+    const int nz = c->grid.nz;
+    std::vector<double> sums((size_t)nz * kDiagQ);
+    CK(cudaMemcpyAsync(sums.data(), c->scratch, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double cells = (double)c->grid.nx * c->ny;
+    for (int k = 0; k < nz; ++k)
+        for (int q = 0; q < kDiagQ; ++q)
+            out[(size_t)k * kDiagQ + q] = q == kDiagQ - 1 ? sums[(size_t)k * kDiagQ + q] : sums[(size_t)k * kDiagQ + q] / cells;
+    return CM_OK;
+}
+
 int cm_diagnostics(cm_diag* out, int max, int* n_out)
 {
     NEED_CTX();

@@ -294,3 +294,28 @@ def test_diffusion_limit_is_refused_at_init():
     assert e.value.code == cm.CM_EUNSTABLE
     s = cm.Solver(256, 64, 10.0, precision="fp64", dt_fixed=1e-5)  # a small fixed dt is accepted
     s.close()
+
+
+def test_profiles_match_plane_means_of_the_oracle_state():
+    """cm_profiles on an FP64 state equals the plane means computed here from
+    the same state with numpy (Sec. 2 closures: T from E, rho, u and g z)."""
+    import paper_2411_10372_gb300 as cm
+    cfg = O.Config(nx=96, nz=25, Ra=1e6)
+    X = stirred_state(cfg, seed=12, u_amp=0.2)
+    s = solver_for(cfg)
+    try:
+        s.set_state(X)
+        got = cm.cm_profiles(cfg.nz)
+    finally:
+        s.close()
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    z = np.linspace(0, 1, cfg.nz)[:, None]
+    rho, ux, uz, E = X[0], X[1] / X[0], X[2] / X[0], X[3]
+    u2 = ux * ux + uz * uz
+    T = cl["b"] * (E / rho - 0.5 * u2 - (cfg.gravity / cfg.eps) * z)
+    Tsa = T - (1 - cfg.D * z)
+    want = {"rho": rho.mean(1), "E": E.mean(1), "conv_flux": (rho * uz * Tsa).mean(1),
+            "kin_flux": (rho * uz * u2).mean(1), "u2": u2.mean(1), "KE": (0.5 * rho * u2).mean(1), "T": T.mean(1),
+            "mach_max": (np.sqrt(u2) / np.sqrt(cfg.gamma * cl["a"] * T)).max(1)}
+    for k, w in want.items():
+        assert np.max(np.abs(got[k] - w)) <= 1e-12 * max(np.max(np.abs(w)), 1e-3), k
