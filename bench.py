@@ -150,7 +150,9 @@ def run_gpu(args):
     cells = NXr * NZr
 
     def measure(precision: str, K: int, W: int, clocks: bool):
-        s = cm.Solver(NXr, NZr, RA, PR, GAMMA, precision=precision, stream=stream, seed=12345 + rank)
+        # the workload samples the diagnostics every 100 steps (FP64 sums of Nu, Re, KE, budgets)
+        s = cm.Solver(NXr, NZr, RA, PR, GAMMA, precision=precision, stream=stream, seed=12345 + rank,
+                      diag_every=100, diag_capacity=4096)
         s.step(W)
         s.sync()
         barrier()
@@ -174,8 +176,11 @@ def run_gpu(args):
         # per-kernel durations for the roofline: a second timed pass with an
         # event pair around every sweep (each duration includes its launch gap)
         sweep_ms, _ = cm.cm_profile_steps(max(3, min(K, 500)), FLUSH_BYTES, per_sweep=True)
+        ds = s.diagnostics()
+        diag = {"samples": len(ds), "all_finite": all(d["status"] == 0 for d in ds),
+                "last_Nu_bar": ds[-1]["Nu_bar"] if ds else None}
         out = dict(total_ms=total_ms, sweep_ms=sweep_ms, launches=launches, clocks=clk.summary() if clocks else None,
-                   w=8 if precision == "fp64" else 4, segments={"z": seg[0], "x": seg[1]})
+                   w=8 if precision == "fp64" else 4, segments={"z": seg[0], "x": seg[1]}, diag=diag)
         return s, out
 
     # ---- FP32 state: the timed line ----
@@ -352,11 +357,13 @@ def run_gpu(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD + "_fp32", "nx": NXr, "nz": NZr, "Ra": RA, "Pr": PR, "gamma": GAMMA,
                    "eps": 0.1, "D": 0.5, "cfl": 0.5, "state": "fp32, fp64 dt and reductions",
+                   "diagnostics": "sampled every 100 steps inside the timed region",
                    "l2": "flushed before every timed step (256 MiB memset)", "parallelism": f"replicas x{world}",
                    "timing": "events at step boundaries for value; per-sweep events in a second pass for roofline"},
         "roofline": roofline(r32),
         "sweep_ms": [round(x, 5) for x in r32["sweep_ms"]],
         "segment_rows": r32["segments"],
+        "diagnostics": r32["diag"],
         "gpu_launches": r32["launches"],
         "clocks": r32["clocks"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * cells * 4,
