@@ -3,8 +3,11 @@
 //
 // One sweep Y = L_al(Delta) X is differentiated in stages, each a kernel with
 // one thread per node.  First the sweep's intermediates are recomputed from X
-// (primitives, F^n, X^P and its primitives, F^P; same operation order as the
-// forward kernels, this unit is built with --fmad=false).  Then the adjoint
+// (primitives, F^n, X^P and its primitives).  The quantities that decide the
+// limiter's and C(Co)'s branches (primitives, wave speeds, the differences of
+// X and their dot products, the ratios and Co) are rounded exactly as in the
+// forward kernels (explicit intrinsics); everything else may use multiply-add
+// contraction.  Then the adjoint
 // runs the stages backwards: TVD term, corrector and average, F^P, X^P,
 // predictor, F^n, primitives.  Every stage whose forward reads neighbours is
 // written as a gather: a node collects the contributions it made to its
@@ -68,14 +71,18 @@ __device__ __forceinline__ void st4(double* X, long long fs, long long n, const 
     X[3 * fs + n] = q.v[3];
 }
 
-// primitives in the forward kernels' operation order (Sec. 2 closures)
+// primitives in the forward kernels' operation order (Sec. 2 closures), each
+// operation rounded on its own (explicit intrinsics: this unit contracts
+// multiply-adds elsewhere), so that T and the wave speed that decide the
+// limiter's branches equal the forward run's bit for bit
 __device__ __forceinline__ void prims_of(const Q4& q, double z, const Coef<double>& C, double& ux, double& uz,
                                          double& T, double& p)
 {
     ux = q.v[1] / q.v[0];
     uz = q.v[2] / q.v[0];
-    T = C.b * (q.v[3] / q.v[0] - 0.5 * (ux * ux + uz * uz) - C.g * z);
-    p = C.a * q.v[0] * T;
+    const double ke = __dmul_rn(0.5, __dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uz, uz)));
+    T = __dmul_rn(C.b, __dsub_rn(__dsub_rn(q.v[3] / q.v[0], ke), __dmul_rn(C.g, z)));
+    p = __dmul_rn(__dmul_rn(C.a, q.v[0]), T);
 }
 
 // grid-stride loop over the nodes; each iteration defines i, k and the index n = k * pitch + i
@@ -100,7 +107,7 @@ __global__ void k_prims(const double* __restrict__ X, const double* __restrict__
         w.U1[n] = uz;
         w.T[n] = T;
         w.P[n] = p;
-        w.A[n] = fabs(AL == 2 ? uz : ux) + sqrt(C.cs2 * T);
+        w.A[n] = __dadd_rn(fabs(AL == 2 ? uz : ux), __dsqrt_rn(__dmul_rn(C.cs2, T)));
     }
 }
 
@@ -192,9 +199,12 @@ __global__ void k_pred(const double* __restrict__ X, const double* __restrict__ 
 
 // ---- reverse stages -------------------------------------------------------
 
+// dot product in the forward kernels' order, every operation rounded on its own
 __device__ __forceinline__ double dot4q(const Q4& a, const Q4& b)
 {
-    return ((a.v[0] * b.v[0] + a.v[1] * b.v[1]) + a.v[2] * b.v[2]) + a.v[3] * b.v[3];
+    return __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(a.v[0], b.v[0]), __dmul_rn(a.v[1], b.v[1])),
+                               __dmul_rn(a.v[2], b.v[2])),
+                     __dmul_rn(a.v[3], b.v[3]));
 }
 
 __device__ __forceinline__ double phi_r(double r) { return fmax(0.0, fmin(2.0 * r, 1.0)); }
@@ -225,7 +235,7 @@ __device__ TvdAdj tvd_iface_adj(const Q4 (&x)[4], double A0, double A1, const Q4
     const double sp = dot4q(dm, d0), sm = dot4q(d0, dp), dd = dot4q(d0, d0);
     if (form == 2 || dd == 0.0) return r;
     const double rp = sp / dd, rm = sm / dd;
-    const double Co = Delta * fmax(A0, A1) / h;
+    const double Co = __dmul_rn(Delta, fmax(A0, A1)) / h;
     const double Cc = Co <= 0.5 ? Co * (1.0 - Co) : 0.25;
     const double dC = Co <= 0.5 ? 1.0 - 2.0 * Co : 0.0;
     const double Gb = dot4q(Db, d0);
