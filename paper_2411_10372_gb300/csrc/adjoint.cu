@@ -703,11 +703,19 @@ __global__ void k_grad_T(const double* __restrict__ X, const double* __restrict_
 
 // ---- host side ---------------------------------------------------------------
 
+// grid-stride launches of the reverse stages: at most 8 blocks per SM
 static int adj_blocks(const Coef<double>& C)
 {
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+    }
     const long long nodes = (long long)C.nx * C.nz;
     long long b = (nodes + kAdjThreads - 1) / kAdjThreads;
-    if (b > 152LL * 8) b = 152LL * 8;
+    if (b > 8LL * nsm) b = 8LL * nsm;
     return (int)(b < 1 ? 1 : b);
 }
 

@@ -139,26 +139,32 @@ int queue_steps(Batch& B, int n)
 }
 
 // time one batched sweep (fixed tiny Delta, written to the scratch buffer,
-// no bookkeeping): median of 3 after a warm-up, in ms
-float time_sweep(Batch& B, int dir)
+// no bookkeeping): *ms = median of 3 after a warm-up
+int time_sweep(Batch& B, int dir, float* ms_out)
 {
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CKB(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(CM_ECUDA, "autotune: cudaEventCreate failed");
+    }
     std::vector<float> t;
-    for (int r = 0; r < 4; ++r) {
-        cudaEventRecord(e0, B.stream);
-        launch(B, dir, 0, 0, 1e-9);
-        cudaEventRecord(e1, B.stream);
-        cudaEventSynchronize(e1);
+    int rc = CM_OK;
+    for (int r = 0; r < 4 && !rc; ++r) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (r) t.push_back(ms);
+        rc = ck(cudaEventRecord(e0, B.stream), "autotune: cudaEventRecord");
+        if (!rc) rc = launch(B, dir, 0, 0, 1e-9);
+        if (!rc) rc = ck(cudaEventRecord(e1, B.stream), "autotune: cudaEventRecord");
+        if (!rc) rc = ck(cudaEventSynchronize(e1), "autotune: cudaEventSynchronize");
+        if (!rc) rc = ck(cudaEventElapsedTime(&ms, e0, e1), "autotune: cudaEventElapsedTime");
+        if (!rc && r) t.push_back(ms);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc) return rc;
     std::sort(t.begin(), t.end());
-    return t[t.size() / 2];
+    *ms_out = t[t.size() / 2];
+    return CM_OK;
 }
 
 // Autotuner: coordinate descent over the segment length of each box size
@@ -178,7 +184,8 @@ int autotune(Batch& B)
         };
         int rc = apply();
         if (rc) return rc;
-        float best = time_sweep(B, dir);
+        float best = 0.f;
+        if ((rc = time_sweep(B, dir, &best))) return rc;
         for (int c = 0; c < 4; ++c) {
             if (!present[c]) continue;
             for (int v : cand) {
@@ -186,7 +193,8 @@ int autotune(Batch& B)
                 const int keep = seg[c];
                 seg[c] = v;
                 if ((rc = apply())) return rc;
-                const float t = time_sweep(B, dir);
+                float t = 0.f;
+                if ((rc = time_sweep(B, dir, &t))) return rc;
                 if (t < 0.99f * best) best = t;
                 else seg[c] = keep;
             }

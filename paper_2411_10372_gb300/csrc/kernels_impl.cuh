@@ -36,10 +36,23 @@ __global__ void unpack_state(const R* __restrict__ X, S* __restrict__ dense, Coe
     }
 }
 
+static inline int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// grid-stride launches: at most 16 blocks per SM
 static inline int grid_for(long long work, int threads)
 {
     long long b = (work + threads - 1) / threads;
-    if (b > 152LL * 16) b = 152LL * 16;
+    if (b > 16LL * sm_count()) b = 16LL * sm_count();
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -64,18 +77,6 @@ static inline int pick_segment(int nstrips, int nz, int blocks_per_sm, int nsm)
         if (cost < best_cost - 1e-9) { best_cost = cost; best = seg; }
     }
     return best;
-}
-
-static inline int sm_count()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
 }
 
 template <class K>
