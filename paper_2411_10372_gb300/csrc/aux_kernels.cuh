@@ -134,14 +134,21 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
     const long long plane = (long long)C.nx * C.ny;
     const long long fs = C.fstride;
     double v[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // FP32 states: per-thread compensated (Kahan) FP32 sums of the FP32
+    // integrands over the thread's nodes of the plane, widened once to FP64;
+    // the max in FP32 (exact).  Every sum across threads, blocks and planes is
+    // FP64.  (The compensated partial is accurate to FP32 rounding of the
+    // partial itself, the precision of each integrand; on GB300 this keeps the
+    // FP64 pipe out of the per-node work.)
+    float ks[kDiagQ - 1] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float kc[kDiagQ - 1] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float mach32 = 0.f;
     int bad = 0;
     for (long long n = threadIdx.x; n < plane; n += kDiagThreads) {
         const int i = (int)(n % C.nx);
         const int j = (int)(n / C.nx);
         const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
         if constexpr (!kExact<R>) {
-            // FP32 state: the integrands in FP32 (the state's own precision),
-            // their sums in FP64
             const float rho = p[0], ri = 1.f / rho;
             const float u = p[fs] * ri;
             float vy = 0.f, w, E;
@@ -151,14 +158,15 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
             const float u2 = (u * u + vy * vy) + w * w;
             const float T = (float)A.b * (E * ri - 0.5f * u2 - (float)A.g * zf);
             const float Tsa = T - (1.f - (float)A.D * zf);
-            v[0] += (double)rho;
-            v[1] += (double)E;
-            v[2] += (double)(rho * w * Tsa);
-            v[3] += (double)(rho * w * u2);
-            v[4] += (double)u2;
-            v[5] += (double)(0.5f * rho * u2);
-            v[6] += (double)T;
-            v[7] = fmax(v[7], (double)(sqrtf(u2) / sqrtf((float)A.cs2 * T)));
+            const float x[kDiagQ - 1] = {rho, E, rho * w * Tsa, rho * w * u2, u2, 0.5f * rho * u2, T};
+#pragma unroll
+            for (int q = 0; q < kDiagQ - 1; ++q) {
+                const float y = __fsub_rn(x[q], kc[q]);
+                const float t = __fadd_rn(ks[q], y);
+                kc[q] = __fsub_rn(__fsub_rn(t, ks[q]), y);
+                ks[q] = t;
+            }
+            mach32 = fmaxf(mach32, sqrtf(u2) / sqrtf((float)A.cs2 * T));
             if (!isfinite(E + rho + T + u2)) bad = 1;
         } else {
             const double rho = (double)p[0];
@@ -180,6 +188,11 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
             v[7] = fmax(v[7], M);
             if (!isfinite(E + rho + T + u2)) bad = 1;
         }
+    }
+    if constexpr (!kExact<R>) {
+#pragma unroll
+        for (int q = 0; q < kDiagQ - 1; ++q) v[q] = (double)ks[q] - (double)kc[q];
+        v[7] = (double)mach32;
     }
     block_sum_q(v, scratch + (size_t)k * kDiagQ);
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, 1);

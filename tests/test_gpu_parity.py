@@ -144,11 +144,14 @@ def test_fp32_100_steps():
     s.close()
 
 
-# stated bars (relative: window mean, worst sample), about 3x the measured 2.7e-5 / 6.2e-5 (Nu_bar),
-# 1.5e-5 / 1.9e-5 (Nu), 9.8e-4 / 1.7e-3 (Re).  Nu_bar is a one-sided plate difference of the
-# plane-mean T, so the FP32 rounding of the state (~6e-8 in T) enters it amplified by 1/(eps 2 dz)
-# ~ 300; Re measures the velocity, itself still small at step 100, whose FP32 error is ~1e-5 of rho c.
-BARS_NU_WINDOW = {"Nu_bar": (1e-4, 2e-4), "Nu": (5e-5, 1e-4), "Re": (3e-3, 5e-3)}
+# stated bars (relative: window mean, worst sample).  Measured: Nu_bar 2.7e-5 / 6.2e-5 and 7.6e-5 /
+# 1.0e-4, Nu 1.5e-5 / 1.9e-5 and 8.7e-6 / 1.0e-5, Re 9.8e-4 / 1.7e-3 and 8.3e-4 / 1.6e-3 for two
+# segment lengths of the FP32 sweeps (the tuner at init picks the length, and the FP32 rounding, hence
+# its amplification by this unstable flow, depends on it).  Nu_bar is a one-sided plate difference
+# of the plane-mean T, so the FP32 rounding of the state (~6e-8 in T) enters it amplified by
+# 8/(eps 2 dz) ~ 2500; Re measures the velocity, itself still small at step 100, whose FP32 error is
+# ~1e-5 of rho c.
+BARS_NU_WINDOW = {"Nu_bar": (2e-4, 4e-4), "Nu": (5e-5, 1e-4), "Re": (3e-3, 5e-3)}
 
 
 def test_fp32_nu_over_a_window():
