@@ -259,10 +259,14 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
     const float* gnext = io.in + row_off(j0 + kRing - 1);  // next row to request (interior path)
     float* gout = io.out + (long long)(j0 - 2) * pitch + i;  // output row of the current step (used only when it exists)
 
-    // one step of the pipeline; edge: plate rules and range tests; STORE: the step has an output row
-    auto row_step = [&](const int j, auto edge_tag, auto store_tag) {
+    // one step of the pipeline; edge: plate rules and range tests; store: the
+    // step has an output row; ramp 1 / 2: the first / second step of an
+    // interior segment, which skip what no stored row uses (1: X^P, F^P, the
+    // TVD coefficient and H; 2: F^P, the TVD coefficient and H)
+    auto row_step = [&](const int j, auto edge_tag, auto store_tag, auto ramp_tag) {
         constexpr bool edge = decltype(edge_tag)::value;
         constexpr bool store = decltype(store_tag)::value;
+        constexpr int ramp = decltype(ramp_tag)::value;
         const int t = j - j0;
         if (edge) {
             ring.request((t + kRing - 1) % kRing, io.in + row_off(j + kRing - 1), fs);
@@ -284,9 +288,10 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         const f2 dxuz1 = mul2(sub2(right_of(uz1), left_of(uz1)), i2dx);
         const S2 F1 = flux_z2(Xm1, ux1, uz1, p1, mul2(sub2(ux0, ux1), idz), mul2(sub2(uz0, uz1), idz),
                               mul2(sub2(T0, T1), idz), dxux1, dxuz1, C);
-        S2 XP1;
+        S2 XP1 = Xm1;
         const bool interior_m = !edge || (m >= 1 && m <= nz - 2);
-        if (interior_m) {
+        if (ramp == 1) {
+        } else if (interior_m) {
             XP1.r = fnma2(lam, sub2(F1.r, F2.r), Xm1.r);
             XP1.mx = fnma2(lam, sub2(F1.mx, F2.mx), Xm1.mx);
             XP1.mz = fma2(mDg, Xm1.r, fnma2(lam, sub2(F1.mz, F2.mz), Xm1.mz));
@@ -300,20 +305,23 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
             XP1.mx = z0; XP1.mz = z0;
             XP1.E = mul2(XP1.r, bc(C.etop));
         }
-        f2 ppux1, ppuz1, ppT1, ppp1;
-        prims2(XP1, gz1, C, ppux1, ppuz1, ppT1, ppp1);
-        const f2 dxppux1 = mul2(sub2(right_of(ppux1), left_of(ppux1)), i2dx);
-        const f2 dxppuz1 = mul2(sub2(right_of(ppuz1), left_of(ppuz1)), i2dx);
-        const S2 FP1 = flux_z2(XP1, ppux1, ppuz1, ppp1, mul2(sub2(ppux1, ppux2), idz), mul2(sub2(ppuz1, ppuz2), idz),
-                               mul2(sub2(ppT1, ppT2), idz), dxppux1, dxppuz1, C);
+        f2 ppux1 = z0, ppuz1 = z0, ppT1 = z0, ppp1 = z0;
+        if (ramp != 1) prims2(XP1, gz1, C, ppux1, ppuz1, ppT1, ppp1);
+        S2 FP1 = {z0, z0, z0, z0};
+        if (ramp == 0) {
+            const f2 dxppux1 = mul2(sub2(right_of(ppux1), left_of(ppux1)), i2dx);
+            const f2 dxppuz1 = mul2(sub2(right_of(ppuz1), left_of(ppuz1)), i2dx);
+            FP1 = flux_z2(XP1, ppux1, ppuz1, ppp1, mul2(sub2(ppux1, ppux2), idz), mul2(sub2(ppuz1, ppuz2), idz),
+                          mul2(sub2(ppT1, ppT2), idz), dxppux1, dxppuz1, C);
+        }
 
         // TVD flux across (j-2, j-1) from the input state
         const S2 d0 = diff2(X0, Xm1);
         const f2 dd0 = dot2(d0, d0);
-        const f2 ss1 = dot2(d1, d0);
+        const f2 ss1 = ramp == 1 ? z0 : dot2(d1, d0);
         const int c = j - 2;
         S2 Dn = {z0, z0, z0, z0};
-        if (!edge || (c >= 1 && c <= nz - 3))
+        if (ramp == 0 && (!edge || (c >= 1 && c <= nz - 3)))
             Dn = scale2(tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form), d1);
 
         // output row c = j-2
@@ -335,7 +343,8 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         gout += pitch;
 
         // H of row m for the next step
-        if (interior_m) {
+        if (ramp != 0) {
+        } else if (interior_m) {
             H.r = sub2(mul2(half, fma2(lam, FP1.r, add2(XP1.r, Xm1.r))), Dn.r);
             H.mx = sub2(mul2(half, fma2(lam, FP1.mx, add2(XP1.mx, Xm1.mx))), Dn.mx);
             H.mz = sub2(mul2(half, fma2(lam, FP1.mz, fma2(mDg, XP1.r, add2(XP1.mz, Xm1.mz)))), Dn.mz);
@@ -363,18 +372,23 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
     // lengths; for a fixed launch configuration they are reproducible.)
     const std::true_type yes;
     const std::false_type no;
+    const std::integral_constant<int, 0> full;
+    const std::integral_constant<int, 1> ramp1;
+    const std::integral_constant<int, 2> ramp2;
     if (interior_segment(ks, ke, nz)) {
-        for (int j = j0; j < ks + 2; ++j) row_step(j, no, no);
+        row_step(j0, no, no, ramp1);      // j0 = ks - 1
+        row_step(j0 + 1, no, no, ramp2);  // ks
+        row_step(j0 + 2, no, no, full);   // ks + 1
         int j = ks + 2;
         for (; j + 1 <= ke + 1; j += 2) {
-            row_step(j, no, yes);
-            row_step(j + 1, no, yes);
+            row_step(j, no, yes, full);
+            row_step(j + 1, no, yes, full);
         }
-        if (j <= ke + 1) row_step(j, no, yes);
+        if (j <= ke + 1) row_step(j, no, yes, full);
     } else {
         for (int j = j0; j <= ke + 1; ++j) {
-            if (j >= ks + 2) row_step(j, yes, yes);
-            else row_step(j, yes, no);
+            if (j >= ks + 2) row_step(j, yes, yes, full);
+            else row_step(j, yes, no, full);
         }
     }
     cp_async_drain();  // rows requested past the segment end
@@ -449,9 +463,12 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
         const float* gnext = io.in + row_off(j0 + kRing - 1);
         float* gout = io.out + (long long)(j0 - 2) * pitch + i;  // used only when the row exists
 
-        auto row_step = [&](const int j, auto edge_tag, auto store_tag) {
+        // ramp 1: the first step of an interior segment, which skips what no
+        // stored row uses (F^n, X^P, the TVD term and K of row ks - 2)
+        auto row_step = [&](const int j, auto edge_tag, auto store_tag, auto ramp_tag) {
             constexpr bool edge = decltype(edge_tag)::value;
             constexpr bool store = decltype(store_tag)::value;
+            constexpr int ramp = decltype(ramp_tag)::value;
             const int t = j - j0;
             if (edge) {
                 ring.request((t + kRing - 1) % kRing, io.in + row_off(j + kRing - 1), fs);
@@ -468,7 +485,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
             // row m = j-1
             const int m = j - 1;
             S2 XP1 = Xm1, K1 = Xm1;  // plate rows pass through
-            if (!edge || (m >= 1 && m <= nz - 2)) {
+            if (ramp != 1 && (!edge || (m >= 1 && m <= nz - 2))) {
                 const S2 F1 = flux_x2(Xm1, ux1, uz1, p1, mul2(sub2(right_of(ux1), ux1), idx_),
                                       mul2(sub2(right_of(uz1), uz1), idx_), mul2(sub2(right_of(T1), T1), idx_),
                                       mul2(sub2(ux0, ux2), i2dz), mul2(sub2(uz0, uz2), i2dz), C);
@@ -477,6 +494,8 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
                 XP1.mx = fnma2(lam, sub2(F1.mx, Fl.mx), Xm1.mx);
                 XP1.mz = fnma2(lam, sub2(F1.mz, Fl.mz), Xm1.mz);
                 XP1.E = fnma2(lam, sub2(F1.E, Fl.E), Xm1.E);
+            }
+            if (ramp == 0 && (!edge || (m >= 1 && m <= nz - 2))) {
                 // TVD along x on row m from the input state
                 const S2 d0 = diff2(right_of(Xm1), Xm1);
                 const f2 dd = dot2(d0, d0);
@@ -490,8 +509,8 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
                 K1.mz = fma2(half, add2(XP1.mz, Xm1.mz), sub2(Dn.mz, Dl.mz));
                 K1.E = fma2(half, add2(XP1.E, Xm1.E), sub2(Dn.E, Dl.E));
             }
-            f2 ppux1, ppuz1, ppT1, ppp1;
-            prims2(XP1, gz1, C, ppux1, ppuz1, ppT1, ppp1);
+            f2 ppux1 = z0, ppuz1 = z0, ppT1 = z0, ppp1 = z0;
+            if (ramp != 1) prims2(XP1, gz1, C, ppux1, ppuz1, ppT1, ppp1);
 
             // row c = j-2: F^P (backward x, central z) and the corrector
             if (store) {
@@ -541,18 +560,22 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
         // lengths; for a fixed launch configuration they are reproducible.)
         const std::true_type yes;
         const std::false_type no;
+        const std::integral_constant<int, 0> full;
+        const std::integral_constant<int, 1> ramp1;
         if (interior_segment(ks, ke, nz)) {
-            for (int j = j0; j < ks + 2; ++j) row_step(j, no, no);
+            row_step(j0, no, no, ramp1);      // j0 = ks - 1
+            row_step(j0 + 1, no, no, full);   // ks
+            row_step(j0 + 2, no, no, full);   // ks + 1
             int j = ks + 2;
             for (; j + 1 <= ke + 1; j += 2) {
-                row_step(j, no, yes);
-                row_step(j + 1, no, yes);
+                row_step(j, no, yes, full);
+                row_step(j + 1, no, yes, full);
             }
-            if (j <= ke + 1) row_step(j, no, yes);
+            if (j <= ke + 1) row_step(j, no, yes, full);
         } else {
             for (int j = j0; j <= ke + 1; ++j) {
-                if (j >= ks + 2) row_step(j, yes, yes);
-                else row_step(j, yes, no);
+                if (j >= ks + 2) row_step(j, yes, yes, full);
+                else row_step(j, yes, no, full);
             }
         }
         cp_async_drain();  // rows requested past the segment end
