@@ -18,6 +18,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                      shear / thermal / sound decay rates, Sod shock tube
   dt ............... closed form on the conduction state
   diag ............. Nu = 1 on the conduction state, analytic fields
+  stretched z-grid . exact mass conservation, steady linear conduction without
+                     gravity, exact trapezoid / plate-derivative rules, second-
+                     order self-convergence on nested tanh grids
   advect1d ......... total-variation test of the TVD reading
   torch_ref.py ..... PyTorch restatement of the 2D step for autograd (the
                      adjoint's reference): equal to this oracle state by
@@ -61,6 +64,7 @@ class _Cfg(ctypes.Structure):
         ("cfl", ctypes.c_double), ("dt_fixed", ctypes.c_double), ("gravity", ctypes.c_double),
         ("t_bot", ctypes.c_double), ("t_top", ctypes.c_double), ("pert_amp", ctypes.c_double),
         ("stokes", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("zstretch", ctypes.c_double), ("znodes", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -90,6 +94,8 @@ class Config:
     seed: int = 12345
     tvd_form: int = TVD_SPLIT
     stokes: float = -2.0 / 3.0
+    zstretch: float = 0.0             # beta of the tanh z-grid (Sec. 3); 0 = uniform
+    znodes: "np.ndarray | None" = None  # explicit plane heights, overriding zstretch
 
     @property
     def nf(self) -> int:
@@ -103,10 +109,17 @@ class Config:
 
     def c(self) -> _Cfg:
         t_top = (1.0 - self.eps - self.D) if self.t_top is None else self.t_top
-        return _Cfg(self.ndim, self.nx, self.ny if self.ndim == 3 else 1, self.nz,
-                    self.tvd_form, 0, self.aspect, self.Ra, self.Pr, self.gamma, self.eps,
-                    self.D, self.cfl, self.dt_fixed, self.gravity, self.t_bot, t_top,
-                    self.pert_amp, self.stokes, self.seed & 0xFFFFFFFFFFFFFFFF)
+        zn = None
+        if self.znodes is not None:
+            zn = np.ascontiguousarray(self.znodes, dtype=np.float64)
+            assert zn.shape == (self.nz,)
+        c = _Cfg(self.ndim, self.nx, self.ny if self.ndim == 3 else 1, self.nz,
+                 self.tvd_form, 0, self.aspect, self.Ra, self.Pr, self.gamma, self.eps,
+                 self.D, self.cfl, self.dt_fixed, self.gravity, self.t_bot, t_top,
+                 self.pert_amp, self.stokes, self.seed & 0xFFFFFFFFFFFFFFFF, self.zstretch,
+                 zn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if zn is not None else None)
+        c._keep = zn  # the C side reads znodes through the pointer
+        return c
 
 
 _lib = None
@@ -140,6 +153,7 @@ def lib(path: str | None = None):
         cp = ctypes.POINTER(_Cfg)
         L.orc_init.argtypes = [cp, dp]
         L.orc_profile.argtypes = [cp, dp, dp, dp]
+        L.orc_znodes.argtypes = [cp, dp]
         L.orc_sweep.argtypes = [cp, ctypes.c_int, ctypes.c_double, dp]
         L.orc_dt.argtypes = [cp, dp]
         L.orc_dt.restype = ctypes.c_double
@@ -172,6 +186,14 @@ def profile(cfg: Config):
     c = cfg.c()
     lib().orc_profile(ctypes.byref(c), _ptr(T), _ptr(p), _ptr(r))
     return T, p, r
+
+
+def znodes(cfg: Config) -> np.ndarray:
+    """The nz plane heights of cfg's z-grid (uniform, tanh of cfg.zstretch, or cfg.znodes)."""
+    z = np.zeros(cfg.nz)
+    c = cfg.c()
+    lib().orc_znodes(ctypes.byref(c), _ptr(z))
+    return z
 
 
 def sweep(cfg: Config, X: np.ndarray, direction: int, Delta: float) -> np.ndarray:

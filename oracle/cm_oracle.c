@@ -43,7 +43,14 @@
  *     the state at the start of the step; local Courant number of interface
  *     k+1/2 uses the larger |u|+c of its two nodes and the sweep's dt/2;
  *   - initial state: exact conduction/hydrostatic profile for constant K,
- *     isobaric temperature perturbation at interior nodes.
+ *     isobaric temperature perturbation at interior nodes;
+ *   - the tanh z-grid (Sec. 3 names it, without its formula or stretching):
+ *     z_k = (1 + tanh(beta (2k/K - 1))/tanh(beta))/2, or any given planes;
+ *     the z flux differences are conservative over cells of width w_k, the
+ *     derivatives inside F divide by the distance of the planes they use,
+ *     the TVD flux of an interface is weighted by its spacing over w_k, the
+ *     CFL step uses the smaller spacing next to a plane, and the plate
+ *     derivative is that of the quadratic through three planes.
  */
 #include <math.h>
 #include <stdint.h>
@@ -65,6 +72,8 @@ typedef struct {
     double pert_amp;     /* amplitude of the temperature perturbation */
     double stokes;       /* coefficient of (div u) delta_ij inside tau/mu */
     uint64_t seed;
+    double zstretch;     /* beta of the tanh z-grid; 0 = uniform planes */
+    const double* znodes; /* optional: the nz plane heights (0 .. 1), overriding zstretch */
 } orc_cfg;
 
 /* derived constants */
@@ -81,7 +90,24 @@ typedef struct {
     double t_bot, t_top;
     double cfl, dt_fixed;
     double Ra, Pr, eps, D, aspect;
+    /* z-grid (Sec. 3: tanh planes in z, uniform in x and y).  z[k]: height of
+     * plane k; hp[k] = z[k+1] - z[k], the spacing above plane k; w[k]: the
+     * width of plane k's cell, (hp[k-1] + hp[k])/2 inside and hp/2 on the
+     * plates (so that sum_k w[k] = 1 and the trapezoid rule in z is
+     * sum_k w[k] f_k).  On the uniform grid hp = dz and w = dz, dz/2 exactly. */
+    int stretched;
+    double *z, *hp, *w;
 } P;
+
+/* plane k of the tanh grid with nz - 1 = K intervals:
+ * z_k = (1 + tanh(beta (2k/K - 1)) / tanh(beta)) / 2, plates exactly 0 and 1 */
+static double tanh_plane(double beta, int k, int K)
+{
+    if (k == 0) return 0.0;
+    if (k == K) return 1.0;
+    double s = 2.0 * k / K - 1.0;
+    return 0.5 * (1.0 + tanh(beta * s) / tanh(beta));
+}
 
 static void derive(const orc_cfg* c, P* p)
 {
@@ -107,10 +133,47 @@ static void derive(const orc_cfg* c, P* p)
     p->dt_fixed = c->dt_fixed;
     p->Ra = c->Ra; p->Pr = c->Pr; p->eps = c->eps; p->D = c->D;
     p->aspect = c->aspect;
+
+    int nz = c->nz, K = nz - 1;
+    p->stretched = c->znodes != NULL || c->zstretch != 0.0;
+    p->z = malloc(nz * sizeof(double));
+    p->hp = malloc(nz * sizeof(double));
+    p->w = malloc(nz * sizeof(double));
+    for (int k = 0; k < nz; k++) {
+        if (c->znodes) p->z[k] = c->znodes[k];
+        else if (c->zstretch != 0.0) p->z[k] = tanh_plane(c->zstretch, k, K);
+        else p->z[k] = (double)k / (double)K;
+    }
+    if (!p->stretched) {
+        for (int k = 0; k < nz; k++) {
+            p->hp[k] = p->h[2];
+            p->w[k] = (k == 0 || k == K) ? p->h[2] / 2.0 : p->h[2];
+        }
+    } else {
+        for (int k = 0; k < K; k++) p->hp[k] = p->z[k + 1] - p->z[k];
+        p->hp[K] = p->hp[K - 1]; /* never used */
+        p->w[0] = p->hp[0] / 2.0;
+        p->w[K] = p->hp[K - 1] / 2.0;
+        for (int k = 1; k < K; k++) p->w[k] = (p->hp[k - 1] + p->hp[k]) / 2.0;
+    }
+}
+
+static void release(P* p)
+{
+    free(p->z); free(p->hp); free(p->w);
 }
 
 /* z of plane k: nodes on both plates, z_0 = 0 and z_{nz-1} = 1 */
-static double zk(const P* p, int k) { return (double)k / (double)(p->nz - 1); }
+static double zk(const P* p, int k) { return p->z[k]; }
+
+/* smallest spacing next to plane k, the z step of the CFL rule there */
+static double hmin_z(const P* p, int k)
+{
+    int K = p->nz - 1;
+    if (k == 0) return p->hp[0];
+    if (k == K) return p->hp[K - 1];
+    return fmin(p->hp[k - 1], p->hp[k]);
+}
 
 static size_t idx(const P* p, int i, int j, int k)
 {
@@ -153,7 +216,9 @@ static void prims(const P* p, const double* X, double* U, double* T, double* Pr)
 
 /* Velocity and temperature gradients at node (i,j,k) for a sweep along al:
  * along al a one-sided difference (forward if fwd, else backward), across
- * al central differences.  du[c][d] = d u_c / d x_d. */
+ * al central differences.  du[c][d] = d u_c / d x_d.  In z every difference
+ * is divided by the distance between the two planes it uses (exact for a
+ * linear profile on any grid). */
 static void grad(const P* p, const double* U, const double* T, int i, int j, int k,
                  int al, int fwd, double du[3][3], double dT[3])
 {
@@ -165,11 +230,11 @@ static void grad(const P* p, const double* U, const double* T, int i, int j, int
         if (d == al) {
             np = fwd ? nbr(p, i, j, k, d, +1) : self;
             nm = fwd ? self : nbr(p, i, j, k, d, -1);
-            span = p->h[d];
+            span = (d == 2) ? (fwd ? p->hp[k] : p->hp[k - 1]) : p->h[d];
         } else {
             np = nbr(p, i, j, k, d, +1);
             nm = nbr(p, i, j, k, d, -1);
-            span = 2.0 * p->h[d];
+            span = (d == 2) ? p->hp[k - 1] + p->hp[k] : 2.0 * p->h[d];
         }
         for (int c = 0; c < 3; c++)
             du[c][d] = (U[c * N + np] - U[c * N + nm]) / span;
@@ -218,8 +283,8 @@ static double Gfun(double r, double C) { return 0.5 * C * (1.0 - phi_minmod(r));
  *   D =  G(r+_{n0} + r-_{n1})     dX_{n0+1/2}   (tvd_form 1)
  * r+_{n0} = (dX_{n0-1/2}, dX_{n0+1/2}) / (dX_{n0+1/2}, dX_{n0+1/2})
  * r-_{n1} = (dX_{n0+1/2}, dX_{n0+3/2}) / (dX_{n0+1/2}, dX_{n0+1/2})
- * Co = (dt/2) max(|u_al|+c over n0, n1) / h_al. */
-static void tvd_flux(const P* p, const double* X, const double* A, double Delta, int al,
+ * Co = (dt/2) max(|u_al|+c over n0, n1) / h, h the spacing of the interface. */
+static void tvd_flux(const P* p, const double* X, const double* A, double Delta, double h,
                      size_t nm, size_t n0, size_t n1, size_t n2, double D[5])
 {
     size_t N = p->n;
@@ -238,7 +303,7 @@ static void tvd_flux(const P* p, const double* X, const double* A, double Delta,
     for (int c = 0; c < 5; c++) D[c] = 0.0;
     if (p->tvd_form == 2 || dd == 0.0) return;
     double rp = s_plus / dd, rm = s_minus / dd;
-    double Co = Delta * fmax(A[n0], A[n1]) / p->h[al];
+    double Co = Delta * fmax(A[n0], A[n1]) / h;
     double C = coefC(Co);
     double G = (p->tvd_form == 0) ? Gfun(rp, C) + Gfun(rm, C) : Gfun(rp + rm, C);
     for (int c = 0; c < 5; c++) D[c] = G * d0[c];
@@ -291,12 +356,16 @@ static void set_plate(const P* p, double* X, size_t n, int top)
     X[4 * N + n] = X[n] * (Tw / p->b + p->g * zw);
 }
 
-/* L_z(Delta): one predictor-corrector-TVD sweep along z (Sec. 3.1) */
+/* L_z(Delta): one predictor-corrector-TVD sweep along z (Sec. 3.1), in the
+ * conservative form of a non-uniform grid: plane k is a cell of width w[k],
+ * so the flux differences of the predictor and corrector are divided by
+ * w[k] and the TVD flux through interface k+1/2, a difference over hp[k], is
+ * scaled by hp[k]/w[k].  On the uniform grid every ratio is exactly 1 and
+ * Delta/w[k] is Delta/dz (2 Delta/dz on the plates). */
 static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* w)
 {
     size_t N = p->n;
     int nz = p->nz, K = nz - 1;
-    double lam = Delta / p->h[2];
 
     prims(p, X, w->U, w->T, w->Pr);
     wave_speed(p, 2, w->U, w->T, w->A);
@@ -310,11 +379,12 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
                 size_t n = idx(p, i, j, k);
                 for (int c = 0; c < 5; c++) w->F[c * N + n] = F[c];
             }
-    /* predictor at interior nodes: X^P = X - (Delta/dz)(F_k - F_{k-1}) + Delta S,
+    /* predictor at interior nodes: X^P = X - (Delta/w_k)(F_k - F_{k-1}) + Delta S,
      * S = (0, 0, 0, -g rho, 0) */
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
+                double lam = Delta / p->w[k];
                 size_t n = idx(p, i, j, k), nm = idx(p, i, j, k - 1);
                 for (int c = 0; c < 5; c++) {
                     double S = (c == 3) ? -p->g * X[n] : 0.0;
@@ -325,8 +395,8 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
     for (int j = 0; j < p->ny; j++)
         for (int i = 0; i < p->nx; i++) {
             size_t n0 = idx(p, i, j, 0), nK = idx(p, i, j, K), nK1 = idx(p, i, j, K - 1);
-            w->XP[n0] = X[n0] - 2.0 * lam * w->F[n0];
-            w->XP[nK] = X[nK] + 2.0 * lam * w->F[nK1];
+            w->XP[n0] = X[n0] - (Delta / p->w[0]) * w->F[n0];
+            w->XP[nK] = X[nK] + (Delta / p->w[K]) * w->F[nK1];
             set_plate(p, w->XP, n0, 0);
             set_plate(p, w->XP, nK, 1);
         }
@@ -342,11 +412,12 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
                 size_t n = idx(p, i, j, k);
                 for (int c = 0; c < 5; c++) w->FP[c * N + n] = F[c];
             }
-    /* corrector at interior nodes: X^C = X - (Delta/dz)(F^P_{k+1} - F^P_k) + Delta S^P;
+    /* corrector at interior nodes: X^C = X - (Delta/w_k)(F^P_{k+1} - F^P_k) + Delta S^P;
      * then the average (X^P + X^C)/2 */
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
+                double lam = Delta / p->w[k];
                 size_t n = idx(p, i, j, k), np = idx(p, i, j, k + 1);
                 for (int c = 0; c < 5; c++) {
                     double S = (c == 3) ? -p->g * w->XP[n] : 0.0;
@@ -358,7 +429,7 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
     for (int j = 0; j < p->ny; j++)
         for (int i = 0; i < p->nx; i++) {
             size_t n0 = idx(p, i, j, 0), n1 = idx(p, i, j, 1), nK = idx(p, i, j, K);
-            double rc0 = X[n0] - 2.0 * lam * w->FP[n1];
+            double rc0 = X[n0] - (Delta / p->w[0]) * w->FP[n1];
             double rcK = X[nK]; /* F^P at the top plate is m_z = 0 */
             Y[n0] = (w->XP[n0] + rc0) / 2.0;
             Y[nK] = (w->XP[nK] + rcK) / 2.0;
@@ -370,19 +441,21 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
                 double D[5];
-                tvd_flux(p, X, w->A, Delta, 2, idx(p, i, j, k - 1), idx(p, i, j, k),
+                tvd_flux(p, X, w->A, Delta, p->hp[k], idx(p, i, j, k - 1), idx(p, i, j, k),
                          idx(p, i, j, k + 1), idx(p, i, j, k + 2), D);
                 size_t n = idx(p, i, j, k);
                 for (int c = 0; c < 5; c++) w->D[c * N + n] = D[c];
             }
-    /* X^{new} = (X^P + X^C)/2 + (D_{k+1/2} - D_{k-1/2}) */
-    for (int k = 1; k < K; k++)
+    /* X^{new} = (X^P + X^C)/2 + ((hp_k/w_k) D_{k+1/2} - (hp_{k-1}/w_k) D_{k-1/2}) */
+    for (int k = 1; k < K; k++) {
+        double rp = p->hp[k] / p->w[k], rm = p->hp[k - 1] / p->w[k];
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
                 size_t n = idx(p, i, j, k), nm = idx(p, i, j, k - 1);
                 for (int c = 0; c < 5; c++)
-                    Y[c * N + n] = Y[c * N + n] + (w->D[c * N + n] - w->D[c * N + nm]);
+                    Y[c * N + n] = Y[c * N + n] + (rp * w->D[c * N + n] - rm * w->D[c * N + nm]);
             }
+    }
     for (int j = 0; j < p->ny; j++)
         for (int i = 0; i < p->nx; i++) {
             set_plate(p, Y, idx(p, i, j, 0), 0);
@@ -450,7 +523,7 @@ static void sweep_h(const P* p, int al, double Delta, const double* X, double* Y
                 int j1 = (al == 1) ? (j + 1) % p->ny : j;
                 size_t n2 = nbr(p, i1, j1, k, al, +1);
                 double D[5];
-                tvd_flux(p, X, w->A, Delta, al, nm, n0, n1, n2, D);
+                tvd_flux(p, X, w->A, Delta, p->h[al], nm, n0, n1, n2, D);
                 for (int c = 0; c < 5; c++) w->D[c * N + n0] = D[c];
             }
     for (int k = 1; k < K; k++)
@@ -491,9 +564,11 @@ static double dt_of(const P* p, const double* X, Work* w)
     double best = INFINITY;
     for (size_t n = 0; n < N; n++) {
         double c = sqrt(p->gam * p->a * w->T[n]);
+        int k = (int)(n / ((size_t)p->nx * p->ny));
         for (int d = 0; d < 3; d++) {
             if (d == 1 && p->ndim == 2) continue;
-            double v = p->h[d] / (fabs(w->U[d * N + n]) + c);
+            double h = (d == 2) ? hmin_z(p, k) : p->h[d];
+            double v = h / (fabs(w->U[d * N + n]) + c);
             if (v < best) best = v;
         }
     }
@@ -525,6 +600,16 @@ void orc_profile(const orc_cfg* c, double* Tc, double* pc, double* rhoc)
         if (pc) pc[k] = pr;
         if (rhoc) rhoc[k] = pr / (p.a * T);
     }
+    release(&p);
+}
+
+/* the nz plane heights the oracle uses for c (uniform, tanh or given) */
+void orc_znodes(const orc_cfg* c, double* z)
+{
+    P p;
+    derive(c, &p);
+    for (int k = 0; k < p.nz; k++) z[k] = p.z[k];
+    release(&p);
 }
 
 /* SplitMix64 (Steele, Lea & Flood 2014): output number idx+1 of the
@@ -567,6 +652,7 @@ void orc_init(const orc_cfg* c, double* ext)
             }
     to_external(&p, X, ext);
     free(X); free(Tc); free(pc);
+    release(&p);
 }
 
 /* one directional sweep L_dir(Delta) applied to ext (in place); dir 0=x 1=y 2=z */
@@ -585,6 +671,7 @@ void orc_sweep(const orc_cfg* c, int dir, double Delta, double* ext)
     to_external(&p, Y, ext);
     work_free(&w);
     free(X); free(Y);
+    release(&p);
 }
 
 double orc_dt(const orc_cfg* c, const double* ext)
@@ -598,6 +685,7 @@ double orc_dt(const orc_cfg* c, const double* ext)
     double dt = dt_of(&p, X, &w);
     work_free(&w);
     free(X);
+    release(&p);
     return dt;
 }
 
@@ -634,15 +722,19 @@ void orc_step(const orc_cfg* c, double* ext, int nsteps, double* t, double* dts)
     to_external(&p, X, ext);
     work_free(&w);
     free(X); free(Y);
+    release(&p);
 }
 
 /* Diagnostics (Sec. 2).  Volume averages use the trapezoid rule in z (half
- * weight on the plate planes) and the plain mean in x, y.
+ * weight on the plate planes; on a stretched grid the weight of plane k is
+ * its cell width w[k]) and the plain mean in x, y.
  * out[0]  Nu      = 1 + Nu_conv + Nu_K                       (Eq. volume_Nu)
  * out[1]  Nu_conv = sqrt(Ra Pr)/eps <rho u_z T_sa>_V
  * out[2]  Nu_K    = D sqrt(Ra Pr)/2 <rho u_z u^2>_V
  * out[3]  Nu_bot  = -(1/eps) d<T_sa>_A/dz at z=0, second-order forward difference
  * out[4]  Nu_top  = same at z=1, second-order backward difference   (Eq. mean_Nu)
+ *         (on a stretched grid: the derivative of the quadratic through
+ *         the three planes next to the plate)
  * out[5]  Nu_bar  = (Nu_bot + Nu_top)/2
  * out[6]  Re      = sqrt(Ra/Pr) sqrt(<u^2>_V)  (instantaneous; Eq. Re before the time mean)
  * out[7]  KE      = <rho u^2 / 2>_V
@@ -660,7 +752,7 @@ void orc_diag(const orc_cfg* c, const double* ext, double* out)
     double s_conv = 0, s_k = 0, s_u2 = 0, s_ke = 0, s_m = 0, s_e = 0, mach = 0;
     double* TA = calloc(p.nz, sizeof(double));
     for (int k = 0; k < p.nz; k++) {
-        double wgt = (k == 0 || k == p.nz - 1) ? 0.5 : 1.0;
+        double wgt = p.stretched ? p.w[k] : ((k == 0 || k == p.nz - 1) ? 0.5 : 1.0);
         double z = zk(&p, k);
         for (int j = 0; j < p.ny; j++)
             for (int i = 0; i < p.nx; i++) {
@@ -681,7 +773,7 @@ void orc_diag(const orc_cfg* c, const double* ext, double* out)
                 if (M > mach) mach = M;
             }
     }
-    double vol = (double)p.nx * p.ny * (p.nz - 1);
+    double vol = p.stretched ? (double)p.nx * p.ny : (double)p.nx * p.ny * (p.nz - 1);
     double sRP = sqrt(p.Ra * p.Pr);
     out[1] = sRP / p.eps * (s_conv / vol);
     out[2] = p.D * sRP / 2.0 * (s_k / vol);
@@ -692,9 +784,23 @@ void orc_diag(const orc_cfg* c, const double* ext, double* out)
         f[q] = TA[q] / ((double)p.nx * p.ny) - (1.0 - p.D * zk(&p, q));
         g[q] = TA[K - q] / ((double)p.nx * p.ny) - (1.0 - p.D * zk(&p, K - q));
     }
-    double dz = p.h[2];
-    out[3] = -(1.0 / p.eps) * (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz);
-    out[4] = -(1.0 / p.eps) * (3.0 * g[0] - 4.0 * g[1] + g[2]) / (2.0 * dz);
+    if (!p.stretched) {
+        double dz = p.h[2];
+        out[3] = -(1.0 / p.eps) * (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz);
+        out[4] = -(1.0 / p.eps) * (3.0 * g[0] - 4.0 * g[1] + g[2]) / (2.0 * dz);
+    } else {
+        /* derivative at the plate of the quadratic through the three planes:
+         * spacings h1 (plate to the next plane) and h2 (the one after) */
+        double h1 = p.z[1] - p.z[0], h2 = p.z[2] - p.z[1];
+        double db = -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * f[0] + (h1 + h2) / (h1 * h2) * f[1]
+                    - h1 / (h2 * (h1 + h2)) * f[2];
+        h1 = p.z[K] - p.z[K - 1];
+        h2 = p.z[K - 1] - p.z[K - 2];
+        double dt_ = (2.0 * h1 + h2) / (h1 * (h1 + h2)) * g[0] - (h1 + h2) / (h1 * h2) * g[1]
+                     + h1 / (h2 * (h1 + h2)) * g[2];
+        out[3] = -(1.0 / p.eps) * db;
+        out[4] = -(1.0 / p.eps) * dt_;
+    }
     out[5] = (out[3] + out[4]) / 2.0;
     out[6] = sqrt(p.Ra / p.Pr) * sqrt(s_u2 / vol);
     out[7] = s_ke / vol;
@@ -703,6 +809,7 @@ void orc_diag(const orc_cfg* c, const double* ext, double* out)
     out[10] = mach;
     free(TA);
     free(X);
+    release(&p);
 }
 
 /* 1D scalar periodic linear advection u_t + a u_x = 0 (a > 0) with the same

@@ -30,15 +30,15 @@ MUTANTS = [
      "X[c * N + n] - lam * (w->F[c * N + np] - w->FP[c * N + n]) + Delta * S;"),
     ("no_average", "Y[c * N + n] = (w->XP[c * N + n] + w->XC[c * N + n]) / 2.0;\n                }\n            }\n    /* TVD flux D at",
      "Y[c * N + n] = w->XC[c * N + n];\n                }\n            }\n    /* TVD flux D at"),
-    ("wall_half_cell_factor", "X[nK] + 2.0 * lam * w->F[nK1]", "X[nK] + lam * w->F[nK1]"),
+    ("wall_half_cell_factor", "X[nK] + (Delta / p->w[K]) * w->F[nK1]", "X[nK] + (Delta / (2.0 * p->w[K])) * w->F[nK1]"),
     ("plate_temperatures_swapped", "double Tw = top ? p->t_top : p->t_bot;", "double Tw = top ? p->t_bot : p->t_top;"),
     ("tvd_sum_form", "(p->tvd_form == 0) ? Gfun(rp, C) + Gfun(rm, C) : Gfun(rp + rm, C)",
      "(p->tvd_form == 1) ? Gfun(rp, C) + Gfun(rm, C) : Gfun(rp + rm, C)"),
     ("tvd_sign", "Y[c * N + n] + (w->D[c * N + n] - w->D[c * N + nm]);\n            }\n}",
      "Y[c * N + n] - (w->D[c * N + n] - w->D[c * N + nm]);\n            }\n}"),
     ("tvd_rminus_index", "dp[c] = X[c * N + n2] - X[c * N + n1];", "dp[c] = X[c * N + n0] - X[c * N + nm];"),
-    ("courant_full_dt", "double Co = Delta * fmax(A[n0], A[n1]) / p->h[al];",
-     "double Co = 2.0 * Delta * fmax(A[n0], A[n1]) / p->h[al];"),
+    ("courant_full_dt", "double Co = Delta * fmax(A[n0], A[n1]) / h;",
+     "double Co = 2.0 * Delta * fmax(A[n0], A[n1]) / h;"),
     ("split_order_x_first", "sweep_z(&p, Delta, X, Y, &w);              /* X -> Y */",
      "sweep_h(&p, 0, Delta, X, Y, &w);"),
     ("limiter_phi_no_factor2", "fmin(2.0 * r, 1.0)", "fmin(r, 1.0)"),
@@ -52,6 +52,32 @@ MUTANTS = [
     ("potential_missing_in_T", "- p->g * zk(p, k));", ");"),
     ("div_missing_dy", "double div = du[0][0] + du[1][1] + du[2][2];", "double div = du[0][0] + du[2][2];"),
     ("y_tvd_rminus_row", "int j1 = (al == 1) ? (j + 1) % p->ny : j;", "int j1 = j;"),
+    # stretched z-grid
+    ("tanh_missing_normalisation", "return 0.5 * (1.0 + tanh(beta * s) / tanh(beta));",
+     "return 0.5 * (1.0 + tanh(beta * s));"),
+    ("stretched_inner_derivative_uses_width", "span = (d == 2) ? (fwd ? p->hp[k] : p->hp[k - 1]) : p->h[d];",
+     "span = (d == 2) ? p->w[k] : p->h[d];"),
+    ("stretched_backward_derivative_index", "span = (d == 2) ? (fwd ? p->hp[k] : p->hp[k - 1]) : p->h[d];",
+     "span = (d == 2) ? (fwd ? p->hp[k] : p->hp[k]) : p->h[d];"),
+    ("stretched_cross_span", "span = (d == 2) ? p->hp[k - 1] + p->hp[k] : 2.0 * p->h[d];",
+     "span = (d == 2) ? 2.0 * p->hp[k] : 2.0 * p->h[d];"),
+    ("stretched_predictor_over_spacing",
+     "double lam = Delta / p->w[k];\n                size_t n = idx(p, i, j, k), nm",
+     "double lam = Delta / p->hp[k];\n                size_t n = idx(p, i, j, k), nm"),
+    ("stretched_corrector_over_spacing",
+     "double lam = Delta / p->w[k];\n                size_t n = idx(p, i, j, k), np",
+     "double lam = Delta / p->hp[k - 1];\n                size_t n = idx(p, i, j, k), np"),
+    ("stretched_plate_half_cell", "(Delta / p->w[0]) * w->FP[n1]", "(Delta / p->hp[0]) * w->FP[n1]"),
+    ("stretched_tvd_weights_swapped", "double rp = p->hp[k] / p->w[k], rm = p->hp[k - 1] / p->w[k];",
+     "double rp = p->hp[k - 1] / p->w[k], rm = p->hp[k] / p->w[k];"),
+    ("stretched_tvd_unweighted", "(rp * w->D[c * N + n] - rm * w->D[c * N + nm])",
+     "(w->D[c * N + n] - w->D[c * N + nm])"),
+    ("stretched_width_one_sided", "p->w[k] = (p->hp[k - 1] + p->hp[k]) / 2.0;", "p->w[k] = p->hp[k];"),
+    ("stretched_cfl_largest_spacing", "return fmin(p->hp[k - 1], p->hp[k]);", "return fmax(p->hp[k - 1], p->hp[k]);"),
+    ("stretched_diag_uniform_weights", "double wgt = p.stretched ? p.w[k] : ((k == 0 || k == p.nz - 1) ? 0.5 : 1.0);",
+     "double wgt = (k == 0 || k == p.nz - 1) ? 0.5 : 1.0;"),
+    ("stretched_plate_nu_coefficient", "-(2.0 * h1 + h2) / (h1 * (h1 + h2)) * f[0]", "-(2.0 * h1 + h2) / (h1 * (h1 + h1)) * f[0]"),
+    ("stretched_plate_nu_top_spacing", "h2 = p.z[K - 1] - p.z[K - 2];", "h2 = p.z[K] - p.z[K - 1];"),
 ]
 
 

@@ -674,3 +674,214 @@ def test_xy_exchange_symmetry_3d(direction, mirror):
     Y = O.sweep(cfg, X, direction, Delta)
     for f in range(5):
         assert np.max(np.abs(Y[f] - X[f])) > 1e-8 * max(scale[f], scale[0]), f
+
+
+# ------------------------------------------------------ stretched z-grid ----
+# Sec. 3 runs on a tanh grid in z.  The pins below fix the conservative
+# metric form of the z sweep, the plane-distance rule of the derivatives
+# inside F, the CFL spacing and the trapezoid / plate-derivative rules of the
+# diagnostics on such grids, from invariants and closed forms.
+
+def random_planes(nz, seed, spread=0.6):
+    """Seeded strictly increasing plane heights from 0 to 1 with uneven spacing."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 + spread * rng.uniform(-1, 1, nz - 1)
+    z = np.concatenate([[0.0], np.cumsum(h)])
+    z /= z[-1]
+    z[-1] = 1.0
+    return z
+
+
+def stirred_on(cfg, z, seed, u_amp=0.3, t_amp=0.05):
+    """Conduction profile on the planes z with random temperature, density and
+    velocity perturbations (zero velocity on the plates, plates at T_w)."""
+    rng = np.random.default_rng(seed)
+    T_c, p_c, _ = O.profile(cfg)
+    T = T_c[:, None] * (1 + t_amp * rng.uniform(-1, 1, (cfg.nz, cfg.nx)))
+    ux = u_amp * rng.uniform(-1, 1, (cfg.nz, cfg.nx))
+    uz = u_amp * rng.uniform(-1, 1, (cfg.nz, cfg.nx))
+    for f in (ux, uz):
+        f[0] = f[-1] = 0.0
+    t_top = (1.0 - cfg.eps - cfg.D) if cfg.t_top is None else cfg.t_top
+    T[0], T[-1] = cfg.t_bot, t_top
+    c = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    rho = p_c[:, None] / (c["a"] * T) * (1 + 0.02 * rng.uniform(-1, 1, (cfg.nz, cfg.nx)))
+    return state_from_prims(cfg, rho, ux, uz, T, cols(cfg, z))
+
+
+def test_tanh_planes_are_symmetric_nested_and_reduce_to_uniform():
+    """The tanh grid: plates at exactly 0 and 1, strictly increasing, mirror
+    symmetric about z = 1/2, finest at the plates, nested (every other plane of
+    the 2K grid is a plane of the K grid), and uniform as beta -> 0."""
+    for nz, beta in ((9, 2.0), (33, 1.5), (65, 3.0)):
+        z = O.znodes(O.Config(nx=4, nz=nz, zstretch=beta))
+        h = np.diff(z)
+        assert z[0] == 0.0 and z[-1] == 1.0 and np.all(h > 0)
+        assert np.max(np.abs(z + z[::-1] - 1.0)) < 1e-15
+        assert h[0] <= h.min() * (1 + 1e-12) and h[len(h) // 2 - 1] >= h.max() * (1 - 1e-12)
+        z2 = O.znodes(O.Config(nx=4, nz=2 * nz - 1, zstretch=beta))
+        assert np.max(np.abs(z2[::2] - z)) < 1e-15
+    z = O.znodes(O.Config(nx=4, nz=17, zstretch=1e-7))
+    assert np.max(np.abs(z - np.linspace(0, 1, 17))) < 1e-13
+
+
+def test_stretched_mass_is_conserved_exactly():
+    """Conservative form of the z sweep on uneven planes (cells of width w_k,
+    half cells on the plates, TVD fluxes weighted by spacing over width): the
+    trapezoid mass (numpy's trapezoid rule on the planes) keeps to round-off
+    through predictor, corrector, plate rules and TVD term, for a tanh grid
+    and for a random grid."""
+    for z_kind, tvd in (("tanh", O.TVD_SPLIT), ("random", O.TVD_SPLIT), ("random", O.TVD_SUM)):
+        nz = 17
+        if z_kind == "tanh":
+            cfg = O.Config(nx=16, nz=nz, Ra=1e5, zstretch=2.0, tvd_form=tvd)
+        else:
+            cfg = O.Config(nx=16, nz=nz, Ra=1e5, znodes=random_planes(nz, 3), tvd_form=tvd)
+        z = O.znodes(cfg)
+        X = stirred_on(cfg, z, seed=11)
+        m0 = np.trapezoid(X[0].mean(axis=1), z)
+        Y, _, _ = O.step(cfg, X, 40)
+        assert np.all(np.isfinite(Y))
+        m1 = np.trapezoid(Y[0].mean(axis=1), z)
+        assert abs(m1 - m0) / m0 < 1e-13, (z_kind, tvd)
+        # and the oracle's own mass diagnostic is that trapezoid rule
+        assert abs(O.diag(cfg, Y)["mass"] / m1 - 1) < 1e-14
+
+
+def test_stretched_linear_conduction_without_gravity_is_steady():
+    """No gravity, fluid at rest, uniform pressure, T linear between the plate
+    temperatures: the heat flux K dT/dz is the same through every interval only
+    if each derivative inside F divides by the distance of the two planes it
+    uses, so the state must stay steady to round-off on uneven planes (TVD on:
+    the limiter sees ratios near the spacing ratio and stays off)."""
+    for znodes, tvd in ((None, O.TVD_OFF), (None, O.TVD_SPLIT), (random_planes(17, 5, 0.3), O.TVD_OFF)):
+        cfg = O.Config(nx=8, nz=17, Ra=1e4, gravity=0.0, pert_amp=0.0, tvd_form=tvd,
+                       zstretch=2.0 if znodes is None else 0.0, znodes=znodes)
+        z = O.znodes(cfg)
+        c = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+        t_top = 1.0 - cfg.eps - cfg.D
+        T = cfg.t_bot + (t_top - cfg.t_bot) * z
+        rho = 0.8 / (c["a"] * T)
+        X = state_from_prims(cfg, cols(cfg, rho), cols(cfg, 0 * z), cols(cfg, 0 * z), cols(cfg, T), cols(cfg, z))
+        Y, _, _ = O.step(cfg, X, 5)
+        for f in range(4):
+            scale = np.max(np.abs(X[f])) if f in (0, 3) else np.max(np.abs(X[3]))
+            assert np.max(np.abs(Y[f] - X[f])) / scale < 1e-13, (tvd, f)
+
+
+def test_stretched_diagnostics_trapezoid_and_plate_quadratic():
+    """On uneven planes the volume average is the trapezoid rule (exact for a
+    density linear in z) and the plate Nusselt numbers are the derivatives of
+    the quadratic through three planes (exact for a quadratic <T_sa>_A:
+    T_sa = -eps z + q z (1 - z) gives Nu_bot = 1 - q/eps, Nu_top = 1 + q/eps)."""
+    for kw in (dict(zstretch=2.5), dict(znodes=random_planes(21, 9))):
+        cfg = O.Config(nx=16, nz=21, **kw)
+        z = O.znodes(cfg)
+        q = 0.03
+        T = (1 - cfg.D * z) + 0.01 - cfg.eps * z + q * z * (1 - z)  # offset: no coefficient multiplies 0
+        rho = 1.0 + 0.3 * z
+        X = state_from_prims(cfg, cols(cfg, rho), cols(cfg, 0 * z), cols(cfg, 0 * z), cols(cfg, T), cols(cfg, z))
+        d = O.diag(cfg, X)
+        assert abs(d["mass"] - 1.15) < 1e-14
+        assert abs(d["Nu_bot"] - (1 - q / cfg.eps)) < 1e-10
+        assert abs(d["Nu_top"] - (1 + q / cfg.eps)) < 1e-10
+
+
+def test_stretched_dt_uses_smallest_plane_spacing():
+    """A7 on uneven planes: dt = CFL min h/(|u|+c), the z step of a plane
+    being the smaller of its two spacings; at rest with T = 1 that is the
+    first spacing at a plate, z_1 - z_0."""
+    for nx, nz, beta in ((64, 33, 2.0), (16, 17, 1.0)):
+        cfg = iso_cfg(nx=nx, nz=nz, zstretch=beta)
+        z = O.znodes(cfg)
+        X = state_from_prims(cfg, cols(cfg, 1 + 0 * z), cols(cfg, 0 * z), cols(cfg, 0 * z), cols(cfg, 1 + 0 * z))
+        h = min(cfg.aspect / nx, z[1] - z[0])
+        assert abs(O.dt(cfg, X) - cfg.cfl * h / sound_speed(cfg)) < 1e-15
+        # a fast upward stream on plane 1 only: there the step is the smaller
+        # of its spacings, z_1 - z_0, against |u_z| + c = 3c
+        c = sound_speed(cfg)
+        uz = 0 * z
+        uz[1] = 2 * c
+        X = state_from_prims(cfg, cols(cfg, 1 + 0 * z), cols(cfg, 0 * z), cols(cfg, uz), cols(cfg, 1 + 0 * z))
+        want = cfg.cfl * min(cfg.aspect / nx / c, (z[1] - z[0]) / (3 * c))
+        assert abs(O.dt(cfg, X) - want) < 1e-15
+
+
+def test_stretched_shear_wave_decay_converges_at_second_order():
+    """Transverse shear wave between no-slip plates, gravity off, rest state
+    rho = T = 1: u_x = A sin(pi z) exp(-mu pi^2 t) exactly (linear; A = 1e-6
+    keeps the quadratic terms below 1e-12).  On tanh grids the viscous flux
+    differences are the conservative three-point form over cells w_k, second
+    order on a smooth stretching: the error at t = 0.3 falls ~4x per
+    refinement (a metric mixing w_k and spacings would leave first order)."""
+    errs = []
+    for nz in (17, 33, 65):
+        cfg = iso_cfg(nx=4, nz=nz, Ra=1e4, zstretch=1.5)
+        z = O.znodes(cfg)
+        A = 1e-6
+        ux = A * np.sin(np.pi * z)
+        X = state_from_prims(cfg, cols(cfg, 1 + 0 * z), cols(cfg, ux), cols(cfg, 0 * z), cols(cfg, 1 + 0 * z))
+        mu = math.sqrt(cfg.Pr / cfg.Ra)
+        dt = 0.4 * (z[1] - z[0]) / sound_speed(cfg)
+        t_end = 0.3
+        n = int(math.ceil(t_end / dt))
+        cfg.dt_fixed = t_end / n
+        Y, t, _ = O.step(cfg, X, n)
+        exact = A * np.sin(np.pi * z) * math.exp(-mu * np.pi ** 2 * t)
+        errs.append(np.max(np.abs(Y[1, :, 0] / Y[0, :, 0] - exact)) / A)
+    assert errs[0] / errs[1] > 3.2 and errs[1] / errs[2] > 3.5, errs
+
+
+def test_explicit_uniform_planes_match_uniform_grid():
+    """The stretched code path on planes given as k/K equals the uniform grid
+    (same arithmetic up to the rounding of the spacings)."""
+    cfg_u = O.Config(nx=16, nz=13, Ra=1e5)
+    cfg_s = O.Config(nx=16, nz=13, Ra=1e5, znodes=np.arange(13) / 12.0)
+    X = stirred_on(cfg_u, np.linspace(0, 1, 13), seed=2)
+    Yu, _, du = O.step(cfg_u, X, 3)
+    Ys, _, ds = O.step(cfg_s, X, 3)
+    assert np.max(np.abs(du - ds) / du) < 1e-14
+    for f in range(4):
+        assert np.max(np.abs(Yu[f] - Ys[f])) / np.max(np.abs(Yu[f])) < 1e-13, f
+    for key, v in O.diag(cfg_u, Yu).items():
+        assert abs(O.diag(cfg_s, Ys)[key] - v) <= 1e-12 * max(abs(v), 1e-3), key
+
+
+def planes_through_half(nz, seed):
+    """Seeded uneven planes with plane (nz-1)/2 at exactly z = 1/2 and
+    different spacings on its two sides."""
+    K = nz - 1
+    rng = np.random.default_rng(seed)
+    lo = np.cumsum(1.0 + 0.6 * rng.uniform(-1, 1, K // 2))
+    hi = np.cumsum(1.0 + 0.6 * rng.uniform(-1, 1, K // 2))
+    z = np.concatenate([[0.0], 0.5 * lo / lo[-1], 0.5 + 0.5 * hi / hi[-1]])
+    z[K // 2] = 0.5
+    z[-1] = 1.0
+    return z
+
+
+def test_stretched_cross_derivative_exact_for_linear_fields():
+    """Cross derivatives along z inside F_x are central differences over the
+    distance of the two planes they use, exact for velocities linear in z on
+    any planes.  So an x-sweep of the plane at z = 1/2 on two different uneven
+    grids (and on the uniform one) gives the same result for a field whose
+    velocities are linear in z, whatever the spacings on either side (to
+    rounding of the differences over spans of ~0.03; a span other than the
+    distance of the two planes errs by ~1e-3)."""
+    nz = 17
+    kx = 2 * np.pi / 4.0
+    results = []
+    for znodes in (None, planes_through_half(nz, 4), planes_through_half(nz, 8)):
+        cfg = iso_cfg(nx=16, nz=nz, Ra=1e3, znodes=znodes)
+        z = O.znodes(cfg)
+        assert z[nz // 2] == 0.5
+        x = np.arange(cfg.nx) * cfg.aspect / cfg.nx
+        Z, Xx = np.meshgrid(z, x, indexing="ij")
+        ux = 0.05 * np.sin(kx * Xx) * Z + 0.02
+        uz = 0.04 * np.cos(kx * Xx) * (Z - 0.5) + 0.03 * Z
+        T = 1.0 + 0.05 * np.sin(kx * Xx)
+        X = state_from_prims(cfg, 1.0 + 0 * Z, ux, uz, T, Z)
+        Y = O.sweep(cfg, X, 0, 2e-3)
+        results.append(Y[:, nz // 2, :])
+    for r in results[1:]:
+        assert np.max(np.abs(r - results[0])) / np.max(np.abs(results[0])) < 1e-10
