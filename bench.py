@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 NX, NZ, RA, PR, GAMMA = 4096, 1024, 1e10, 1.0, 5.0 / 3.0
 RA3 = 1e9  # the 512 x 512 x 128 box
+ZSTRETCH = 2.0  # tanh z-grid of the stretched leg (first spacing 0.25 of the uniform one)
 WORKLOAD = "2d_aspect4_4096x1024_Ra1e10"
 METRIC = "cell-updates/s per MacCormack-TVD step"
 UNIT = "cell-updates/s"
@@ -149,10 +150,10 @@ def run_gpu(args):
     NXr, NZr = args.nx, args.nz
     cells = NXr * NZr
 
-    def measure(precision: str, K: int, W: int, clocks: bool):
+    def measure(precision: str, K: int, W: int, clocks: bool, zstretch: float = 0.0):
         # the workload samples the diagnostics every 100 steps (FP64 sums of Nu, Re, KE, budgets)
         s = cm.Solver(NXr, NZr, RA, PR, GAMMA, precision=precision, stream=stream, seed=12345 + rank,
-                      diag_every=100, diag_capacity=4096)
+                      diag_every=100, diag_capacity=4096, zstretch=zstretch)
         s.step(W)
         s.sync()
         barrier()
@@ -315,6 +316,20 @@ def run_gpu(args):
     s64, r64 = measure("fp64", k64, min(args.warmup, 3), clocks=False)
     s64.close()
 
+    # ---- the same FP32 workload on the tanh z-grid of Sec. 3 (stretched kernels) ----
+    stretched = None
+    if not args.no_stretched:
+        kst = max(3, min(args.steps, 1000))
+        sst, rst = measure("fp32", kst, args.warmup, clocks=False, zstretch=ZSTRETCH)
+        zs = sst.z
+        sst.close()
+        stretched = {"value": job_rate(cells, kst, rst["total_ms"], world), "unit": UNIT, "steps": kst,
+                     "workload": WORKLOAD + f"_tanh{ZSTRETCH:g}_fp32", "zstretch": ZSTRETCH,
+                     "dz_min_over_uniform": float(min(zs[1:] - zs[:-1]) * (NZr - 1)),
+                     "ms_per_step": rst["total_ms"] / kst, "gpu_launches": rst["launches"],
+                     "segment_rows": rst["segments"], "diagnostics": rst["diag"],
+                     "sweep_ms": [round(x, 5) for x in rst["sweep_ms"]]}
+
     def measured_traffic(kernel: str, segments: dict):
         """DRAM bytes per launch of `kernel` from the committed ncu capture, if
         its kernel sources and segment lengths are unchanged since (else None)."""
@@ -332,9 +347,9 @@ def run_gpu(args):
         got = rec["per_launch_bytes"].get(kernel)
         return got["total"] if got else None
 
-    def roofline(r):
+    def roofline(r, suffix=None):
         nf, w = 4, r["w"]
-        suffix = "_x2" if w == 4 else "<double>"
+        suffix = suffix or ("_x2" if w == 4 else "<double>")
         kinds = {"sweep_z2d" + suffix: r["sweep_ms"][0] + r["sweep_ms"][2],
                  "sweep_x2d" + suffix: r["sweep_ms"][1] + r["sweep_ms"][3]}
         dom = max(kinds, key=kinds.get)
@@ -343,7 +358,7 @@ def run_gpu(args):
         achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
         return {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
-                "traffic": measured_traffic(dom, r["segments"]) if w == 4 else None,
+                "traffic": measured_traffic(dom, r["segments"]) if w == 4 and suffix == "_x2" else None,
                 "bytes_per_launch": bytes_per_launch, "ms_per_launch": round(per_launch_ms, 5)}
 
     K = args.steps
@@ -375,7 +390,10 @@ def run_gpu(args):
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": r64["total_ms"] / k64, "steps": k64,
                  "sweep_ms": [round(x, 5) for x in r64["sweep_ms"]], "gpu_launches": r64["launches"],
                  "roofline_hbm": roofline(r64)},
+        "stretched": stretched,
     }
+    if stretched is not None:
+        stretched["roofline"] = roofline(rst, "_x2s")
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(steps=args.cpu_steps)
     if rank == 0:
@@ -440,7 +458,7 @@ def run_case(args):
         if case.startswith("3d"):
             s = cm.Solver(args.nx, args.nz, RA3, PR, GAMMA, ny=args.ny, ndim=3, precision=prec)
         else:
-            s = cm.Solver(args.nx, args.nz, RA, PR, GAMMA, precision=prec)
+            s = cm.Solver(args.nx, args.nz, RA, PR, GAMMA, precision=prec, zstretch=args.zstretch)
         s.step(args.warmup)
         s.step(args.steps)
         d = s.sample()
@@ -478,12 +496,14 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-stretched", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--steps-3d", type=int, default=200)
     ap.add_argument("--nx", type=int, default=NX, help="grid override (profiling captures only)")
     ap.add_argument("--nz", type=int, default=NZ, help="grid override (profiling captures only)")
     ap.add_argument("--ny", type=int, default=512, help="3D grid override (--case only)")
     ap.add_argument("--only-fp32", action="store_true", help="time the FP32 steps only (profiling captures)")
+    ap.add_argument("--zstretch", type=float, default=0.0, help="tanh z-grid for --case 2d_* (profiling captures)")
     ap.add_argument("--case", choices=["2d_fp32", "2d_fp64", "3d_fp32", "3d_fp64", "batch", "adjoint"],
                     help="run one kernel family untimed (profiling captures)")
     args = ap.parse_args()

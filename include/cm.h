@@ -56,6 +56,21 @@ typedef struct cm_grid {
     int ndim;       /* 2 or 3 */
     int nx, ny, nz; /* nodes; x (and y) periodic; nz counts both plates (ny ignored in 2D) */
     double aspect;  /* Gamma = L/d: the box is Gamma (x Gamma) x 1 */
+    /* z-grid (Sec. 3: uniform in x, y; a tangent-hyperbolic grid in z that
+     * refines the plate boundary layers).  zstretch = beta > 0 puts plane k at
+     *   z_k = (1 + tanh(beta (2k/K - 1)) / tanh(beta)) / 2,  K = nz - 1
+     * (the paper does not print beta); 0 = uniform planes k/K.  znodes, if not
+     * NULL, gives the nz plane heights instead (host, read during cm_init only;
+     * z_0 = 0 < z_1 < ... < z_K = 1 exactly).  On such a grid the z sweep is
+     * written in conservative form over cells of width w_k = (z_{k+1} -
+     * z_{k-1})/2 (half cells on the plates), derivatives divide by the
+     * distance of the planes they use, volume averages use the trapezoid
+     * rule on the planes and the plate Nusselt numbers the derivative of the
+     * quadratic through three planes.  Stretched grids: 2D single contexts
+     * only (cm_init returns CM_EINVAL for 3D, cm_batch_init and cm_adj_* for
+     * any stretched grid). */
+    double zstretch;
+    const double* znodes;
 } cm_grid;
 
 typedef struct cm_params {
@@ -212,6 +227,11 @@ int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, doub
  * 2D, or CM_SEG_ROWS set).  The work split only; no paper passage.  Host
  * out-pointers, may be NULL. */
 int cm_tuning(int* seg_z, int* seg_x);
+
+/* Copy the nz plane heights z_k of the context's z-grid (uniform, tanh or
+ * given; see cm_grid) to z (host, nz doubles).  CM_ENOTINIT without a context,
+ * CM_EINVAL for z = NULL. */
+int cm_znodes(double* z);
 
 /* Number of CUDA kernel launches this context has queued since cm_init
  * (measurement; no paper passage). */

@@ -8,6 +8,8 @@ no arithmetic of the method.
 """
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 
 from ._binding import (cm_adj_backward, cm_adj_forward, cm_batch_diagnostics, cm_batch_finalize, cm_batch_get_state, cm_batch_init,
@@ -18,7 +20,7 @@ from ._binding import (cm_adj_backward, cm_adj_forward, cm_batch_diagnostics, cm
                        cm_init, cm_last_error, cm_launch_count, cm_load, cm_profile_steps, cm_params, cm_run_host,
                        cm_profiles, cm_run_host_f32, cm_sample, cm_tuning,
                        cm_save, cm_set_state, cm_state_bytes, cm_state_layout, cm_state_ptr, cm_step, cm_sweep,
-                       cm_sync, lib)
+                       cm_sync, cm_znodes, lib)
 
 __all__ = [n for n in dir() if n.startswith("cm_") or n.startswith("CM")] + ["Solver", "lib"]
 
@@ -27,11 +29,20 @@ class Solver:
     """One solver context (the library keeps a single context per process).
 
     Parameters follow cm_params; `precision` is "fp64" or "fp32".  `stream`
-    may be a torch.cuda.Stream (its handle is passed to the library)."""
+    may be a torch.cuda.Stream (its handle is passed to the library).
+    `zstretch` (beta of the tanh z-grid) or `znodes` (the nz plane heights)
+    select a stretched z-grid (cm_grid)."""
 
     def __init__(self, nx: int, nz: int, Ra: float, Pr: float = 1.0, gamma: float = 5.0 / 3.0, *,
-                 ny: int = 1, ndim: int = 2, aspect: float = 4.0, precision: str = "fp64", stream=None, **params):
-        self.grid = cm_grid(ndim, nx, ny if ndim == 3 else 1, nz, aspect)
+                 ny: int = 1, ndim: int = 2, aspect: float = 4.0, precision: str = "fp64", stream=None,
+                 zstretch: float = 0.0, znodes=None, **params):
+        zn = None
+        if znodes is not None:
+            zn = np.ascontiguousarray(znodes, dtype=np.float64)
+            if zn.shape != (nz,):
+                raise ValueError(f"znodes must hold nz = {nz} plane heights")
+        self.grid = cm_grid(ndim, nx, ny if ndim == 3 else 1, nz, aspect, zstretch,
+                            zn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if zn is not None else None)
         p = cm_default_params()
         t_top_given = "t_top" in params
         for k, v in params.items():
@@ -47,6 +58,12 @@ class Solver:
         self.Ra, self.Pr, self.gamma = Ra, Pr, gamma
         self.nf = 5 if ndim == 3 else 4
         cm_init(self.grid, Ra, Pr, gamma, p)
+        self.grid.znodes = None  # read during cm_init only
+
+    @property
+    def z(self) -> np.ndarray:
+        """Plane heights of the z-grid."""
+        return cm_znodes(self.grid.nz)
 
     @property
     def shape(self) -> tuple:

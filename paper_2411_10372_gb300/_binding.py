@@ -22,7 +22,8 @@ CM_TVD_DAVIS, CM_TVD_SUM, CM_TVD_OFF = 0, 1, 2
 
 class cm_grid(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-                ("aspect", ctypes.c_double)]
+                ("aspect", ctypes.c_double), ("zstretch", ctypes.c_double),
+                ("znodes", ctypes.POINTER(ctypes.c_double))]
 
 
 class cm_params(ctypes.Structure):
@@ -76,6 +77,7 @@ _SIGS = {
     "cm_load": (ctypes.c_int, [ctypes.c_char_p]),
     "cm_profiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "cm_tuning": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "cm_znodes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "cm_run_host_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cm_diag)]),
     "cm_adj_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "cm_adj_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
@@ -227,6 +229,13 @@ def cm_profiles(nz: int) -> dict:
     out = np.empty((nz, 8), dtype=np.float64)
     _check(lib().cm_profiles(out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return {k: out[:, q].copy() for q, k in enumerate(PROFILE_KEYS)}
+
+
+def cm_znodes(nz: int) -> np.ndarray:
+    """The nz plane heights of the context's z-grid (include/cm.h)."""
+    z = np.empty(nz, dtype=np.float64)
+    _check(lib().cm_znodes(z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return z
 
 
 def cm_tuning() -> tuple[int, int]:

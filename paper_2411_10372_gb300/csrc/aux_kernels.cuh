@@ -77,7 +77,7 @@ __global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int s
             else { uz = p[2 * fs] * ri; E = p[3 * fs]; }
             const float T = C.b * (E * ri - 0.5f * ((ux * ux + uy * uy) + uz * uz) - C.g * zt[k]);
             const float c = sqrtf(C.cs2 * T);
-            float r = fmaxf((fabsf(ux) + c) * C.inv_dx, (fabsf(uz) + c) * C.inv_dz);
+            float r = fmaxf((fabsf(ux) + c) * C.inv_dx, (fabsf(uz) + c) * (C.zp ? C.zp[k].ihmin : C.inv_dz));
             if (C.ndim == 3) r = fmaxf(r, (fabsf(uy) + c) * C.inv_dy);
             if (!(r > 0.f) || !(r < 1e30f)) bad = 1;
             rmax = fmaxf(rmax, r);
@@ -89,7 +89,7 @@ __global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int s
             else { uz = (double)p[2 * fs] / rho; E = (double)p[3 * fs]; }
             const double T = (double)C.b * (E / rho - 0.5 * ((ux * ux + uy * uy) + uz * uz) - (double)C.g * (double)zt[k]);
             const double c = sqrt((double)C.cs2 * T);
-            double v = fmin(C.dx / (fabs(ux) + c), C.dz / (fabs(uz) + c));
+            double v = fmin(C.dx / (fabs(ux) + c), (C.zp ? (double)C.zp[k].hmin : C.dz) / (fabs(uz) + c));
             if (C.ndim == 3) v = fmin(v, C.dy / (fabs(uy) + c));
             if (!(v > 0.0) || !(v < 1e300)) bad = 1;
             vmin = fmin(vmin, v);
@@ -202,19 +202,21 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
 #ifdef CM_DEFINE_DIAG_FINAL  // one definition, in kernels_f64.cu
 // combine the plane sums (trapezoid weights, fixed order) into one cm_diag
 // record: Eq. volume_Nu, Eq. mean_Nu (second-order one-sided differences of
-// <T_sa>_A at the plates), Eq. Re (instantaneous), KE, mass, energy
+// <T_sa>_A at the plates), Eq. Re (instantaneous), KE, mass, energy.  On a
+// stretched z-grid (F.zp) the weight of plane k is its cell width w_k and the
+// plate derivative that of the quadratic through three planes.
 __global__ void __launch_bounds__(kDiagThreads) diag_final(const double* scratch, const double* zt, DiagFinal F, DevCtl* ctl, cm_diag* rec)
 {
     double v[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = threadIdx.x; k < F.nz; k += kDiagThreads) {
-        const double w = (k == 0 || k == F.nz - 1) ? 0.5 : 1.0;
+        const double w = F.zp ? F.zp[k].w : ((k == 0 || k == F.nz - 1) ? 0.5 : 1.0);
         for (int q = 0; q < 6; ++q) v[q] += w * scratch[(size_t)k * kDiagQ + q];
         v[7] = fmax(v[7], scratch[(size_t)k * kDiagQ + 7]);
     }
     __shared__ double tot[kDiagQ];
     block_sum_q(v, tot);
     if (threadIdx.x == 0) {
-        const double vol = F.cells * (double)(F.nz - 1);
+        const double vol = F.zp ? F.cells : F.cells * (double)(F.nz - 1);
         const double sRP = sqrt(F.Ra * F.Pr);
         cm_diag d;
         d.Nu_conv = sRP / F.eps * (tot[2] / vol);
@@ -227,8 +229,21 @@ __global__ void __launch_bounds__(kDiagThreads) diag_final(const double* scratch
             f[q] = scratch[(size_t)q * kDiagQ + 6] / F.cells - (1.0 - F.D * zt[q]);
             g[q] = scratch[(size_t)(K - q) * kDiagQ + 6] / F.cells - (1.0 - F.D * zt[K - q]);
         }
-        d.Nu_bot = -(1.0 / F.eps) * (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz);
-        d.Nu_top = -(1.0 / F.eps) * (3.0 * g[0] - 4.0 * g[1] + g[2]) / (2.0 * dz);
+        if (!F.zp) {
+            d.Nu_bot = -(1.0 / F.eps) * (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz);
+            d.Nu_top = -(1.0 / F.eps) * (3.0 * g[0] - 4.0 * g[1] + g[2]) / (2.0 * dz);
+        } else {
+            // spacings h1 (plate to the next plane) and h2 (the one after)
+            double h1 = zt[1] - zt[0], h2 = zt[2] - zt[1];
+            const double db = -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * f[0] + (h1 + h2) / (h1 * h2) * f[1]
+                              - h1 / (h2 * (h1 + h2)) * f[2];
+            h1 = zt[K] - zt[K - 1];
+            h2 = zt[K - 1] - zt[K - 2];
+            const double dtp = (2.0 * h1 + h2) / (h1 * (h1 + h2)) * g[0] - (h1 + h2) / (h1 * h2) * g[1]
+                               + h1 / (h2 * (h1 + h2)) * g[2];
+            d.Nu_bot = -(1.0 / F.eps) * db;
+            d.Nu_top = -(1.0 / F.eps) * dtp;
+        }
         d.Nu_bar = (d.Nu_bot + d.Nu_top) / 2.0;
         d.Re = sqrt(F.Ra / F.Pr) * sqrt(tot[4] / vol);
         d.KE = tot[5] / vol;

@@ -237,6 +237,8 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
             return set_error(CM_EINVAL, "cm_batch_init: every box must be 2D with even nx >= 4, nz >= 5, Ra > 0");
         if ((long long)G.nz * pitch_of(G.nx, CM_FP32) * 5 >= (1LL << 31))
             return set_error(CM_EINVAL, "cm_batch_init: box too large");
+        if (G.znodes || G.zstretch != 0.0)
+            return set_error(CM_EINVAL, "cm_batch_init: the batch steps uniform z-grids only");
     }
     if (g_batch) { free_batch(g_batch); g_batch = nullptr; }
     Batch* B = new Batch();
@@ -401,7 +403,7 @@ int cm_batch_diagnostics(cm_diag* out)
         A.D = B.prm.D;
         A.cs2 = K.cs2;
         CKB(Launch<float>::diag_planes(x.buf[B.cur], x.C, A, x.scratch, x.ctl, B.stream));
-        DiagFinal F;
+        DiagFinal F{};
         F.Ra = x.Ra;
         F.Pr = B.Pr;
         F.eps = B.prm.eps;

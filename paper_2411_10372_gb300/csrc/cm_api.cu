@@ -47,6 +47,10 @@ struct Ctx {
     int cur;                    // buffer holding the current state
     void* zt_r;                 // z table in the state precision
     double* zt_d;               // z table, FP64
+    void* zp_r;                 // stretched z-grid: per-plane metric in the state precision (else NULL)
+    Plane<double>* zp_d;        // the same in FP64 (diagnostics), else NULL
+    double* zplanes;            // host copy of the nz plane heights
+    unsigned long long zhash;   // FNV-1a of the plane heights of a stretched grid, 0 if uniform
     double* Tc_d;
     double* pc_d;
     DevCtl* ctl;
@@ -101,6 +105,9 @@ void free_ctx(Ctx* c)
     if (c->own_buf && c->buf[0]) cudaFree(c->buf[0]);
     cudaFree(c->zt_r);
     cudaFree(c->zt_d);
+    if (c->zp_r != (void*)c->zp_d) cudaFree(c->zp_r);
+    cudaFree(c->zp_d);
+    std::free(c->zplanes);
     cudaFree(c->Tc_d);
     cudaFree(c->pc_d);
     cudaFree(c->ctl);
@@ -176,7 +183,7 @@ int sample(Ctx* c)
         ? Launch<double>::diag_planes((const double*)c->buf[c->cur], c->cd, A, c->scratch, c->ctl, c->stream)
         : Launch<float>::diag_planes((const float*)c->buf[c->cur], c->cf, A, c->scratch, c->ctl, c->stream);
     if (e != cudaSuccess) return fail(CM_ECUDA, "diagnostics launch: %s", cudaGetErrorString(e));
-    DiagFinal F;
+    DiagFinal F{};
     F.Ra = c->Ra;
     F.Pr = c->Pr;
     F.eps = c->prm.eps;
@@ -186,6 +193,7 @@ int sample(Ctx* c)
     F.cells = (double)c->grid.nx * c->ny;
     F.nz = c->grid.nz;
     F.slot = (int)(c->step & 1);
+    F.zp = c->zp_d;
     e = launch_diag_final(c->scratch, c->zt_d, F, c->ctl, c->ring + slot, c->stream);
     if (e != cudaSuccess) return fail(CM_ECUDA, "diagnostics launch: %s", cudaGetErrorString(e));
     c->launches += 2;
@@ -283,7 +291,10 @@ unsigned long long param_hash(const Ctx* c)
 {
     double v[12] = {c->Ra, c->Pr, c->gamma, c->prm.eps, c->prm.D, c->prm.cfl, c->prm.dt_fixed,
                     c->prm.gravity, c->prm.t_bot, c->prm.t_top, c->prm.stokes, (double)c->prm.tvd_form};
-    return fnv1a(v, sizeof v);
+    const unsigned long long h = fnv1a(v, sizeof v);
+    if (!c->zhash) return h;  // uniform planes: the hash of earlier checkpoints
+    const unsigned long long both[2] = {h, c->zhash};
+    return fnv1a(both, sizeof both);
 }
 
 struct CkptHeader {
@@ -411,11 +422,17 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     if (P.tvd_form < 0 || P.tvd_form > 2) return fail(CM_EINVAL, "tvd_form must be 0, 1 or 2");
     if (P.diag_capacity < 1) P.diag_capacity = 1024;
     if (P.state_buf && ((uintptr_t)P.state_buf & 255)) return fail(CM_EINVAL, "state_buf must be 256-byte aligned");
+    std::vector<double> planes;
+    const char* why = "";
+    if (!make_planes(*grid, planes, &why)) return fail(CM_EINVAL, "%s", why);
+    const bool st = stretched(*grid);
+    if (st && grid->ndim == 3) return fail(CM_EINVAL, "stretched z-grids are implemented for 2D contexts only");
 
     if (g_ctx) { free_ctx(g_ctx); g_ctx = nullptr; }
     Ctx* c = new Ctx();
     std::memset((void*)c, 0, sizeof *c);
     c->grid = *grid;
+    c->grid.znodes = nullptr;  // caller memory: the planes are copied below
     c->prm = P;
     c->Ra = Ra;
     c->Pr = Pr;
@@ -459,8 +476,39 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
         return bail(fail(CM_ENOMEM, "cudaMalloc of the work arrays failed"));
     }
 
+    c->zplanes = (double*)std::malloc(nz * sizeof(double));
+    if (!c->zplanes) return bail(fail(CM_ENOMEM, "host allocation of the plane table failed"));
+    std::memcpy(c->zplanes, planes.data(), nz * sizeof(double));
+    if (st) {
+        // per-plane metric tables of the stretched grid (FP64 for the
+        // diagnostics, the state precision for the sweeps)
+        c->zhash = fnv1a(planes.data(), nz * sizeof(double)) | 1ULL;
+        std::vector<Plane<double>> td;
+        plane_table(planes, td);
+        std::vector<Plane<float>> tf;
+        plane_table(planes, tf);
+        if (cudaMalloc(&c->zp_d, nz * sizeof(Plane<double>)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(CM_ENOMEM, "cudaMalloc of the plane table failed"));
+        }
+        if (c->prec == CM_FP64) c->zp_r = c->zp_d;
+        else if (cudaMalloc(&c->zp_r, nz * sizeof(Plane<float>)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(CM_ENOMEM, "cudaMalloc of the plane table failed"));
+        }
+        if (cudaMemcpyAsync(c->zp_d, td.data(), nz * sizeof(Plane<double>), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            (c->prec == CM_FP32 &&
+             cudaMemcpyAsync(c->zp_r, tf.data(), nz * sizeof(Plane<float>), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(CM_ECUDA, "upload of the plane table failed"));
+        }
+        c->cd.zp = c->zp_d;
+        c->cf.zp = (const Plane<float>*)c->zp_r;
+    }
+
     // conduction / hydrostatic profile of constant K, FP64 on the host (nz values)
-    const Profile prof(nz, P, Closure(gamma, P));
+    const Profile prof(planes, P, Closure(gamma, P));
     const std::vector<double>& z = prof.z;
     const std::vector<double>& Tc = prof.Tc;
     const std::vector<double>& pc = prof.pc;
@@ -512,12 +560,22 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     if (!(dt0 > 0) || !std::isfinite(dt0) || (h.status & 1)) return bail(fail(CM_ENAN, "non-finite initial state"));
     const double mu = std::sqrt(Pr / Ra), K = 1.0 / (P.eps * P.D * std::sqrt(Ra * Pr));
     const double nu = std::fmax(4.0 / 3.0 * mu, K * c->b) / rho_min;
-    const double hh = std::fmin(grid->aspect / grid->nx, 1.0 / (nz - 1));
+    double hz = 1.0 / (nz - 1);
+    for (int k = 0; k + 1 < nz; ++k) hz = std::fmin(hz, planes[k + 1] - planes[k]);
+    const double hh = std::fmin(grid->aspect / grid->nx, hz);
     const double dnum = nu * 0.5 * dt0 / (hh * hh);
     if (dnum > 0.5)
         return bail(fail(CM_EUNSTABLE, "explicit diffusion number %.3g > 0.5 at dt = %.3g: refine dt (dt_fixed) or raise Ra", dnum, dt0));
     if ((rc = tune_segments(c))) return bail(rc);
     g_ctx = c;
+    return CM_OK;
+}
+
+int cm_znodes(double* z)
+{
+    NEED_CTX();
+    if (!z) return fail(CM_EINVAL, "z is NULL");
+    std::memcpy(z, g_ctx->zplanes, g_ctx->grid.nz * sizeof(double));
     return CM_OK;
 }
 
@@ -878,6 +936,7 @@ int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
     NEED_CTX();
     Ctx* c = g_ctx;
     if (c->prec != CM_FP64 || c->grid.ndim != 2) return fail(CM_EINVAL, "the adjoint needs a 2D FP64 context");
+    if (c->zp_d) return fail(CM_EINVAL, "the adjoint is implemented for uniform z-grids only");
     if (nsteps < 1 || K < 0 || win_begin < 1 || win_begin > nsteps)
         return fail(CM_EINVAL, "need nsteps >= 1, K >= 0, 1 <= win_begin <= nsteps");
     if (!c->adj) c->adj = new AdjCtx();

@@ -24,6 +24,21 @@ namespace cm {
 
 // Coefficients of one solver instance in the state precision R (the dt rule
 // stays in FP64).
+// Metric of one z plane of a non-uniform grid (the tanh grid of Sec. 3, or
+// any given planes), in the state precision.  hp: spacing to the plane
+// above, z_{k+1} - z_k; w: width of the plane's cell, (hp_{k-1} + hp_k)/2
+// (hp/2 on the plates); rp, rm: hp_k / w_k and hp_{k-1} / w_k, the weights of
+// the TVD fluxes above and below; sc: hp_{k-1} + hp_k, the span of a central
+// difference; hmin: the smaller spacing next to the plane (CFL); i*: the
+// reciprocals; z: the height.  Plate rows hold harmless values where a
+// quantity does not exist.
+template <class R>
+struct alignas(16) Plane {
+    R hp, ihp, w, iw;
+    R rp, rm, sc, isc;
+    R hmin, ihmin, z, pad;
+};
+
 template <class R>
 struct Coef {
     R a, b, g, mu, kth, cs2, stokes;   // closures; cs2 = gamma a (c^2 = cs2 T)
@@ -35,6 +50,7 @@ struct Coef {
     int nx, ny, nz, pitch;             // nodes; row pitch in elements
     long long fstride;                 // elements between two fields
     int tvd_form, ndim;
+    const Plane<R>* zp;                // per-plane metric of a stretched z-grid; nullptr = uniform planes
 };
 
 // Device control block: dt slots (raw min of h/(|u|+c) as IEEE bits, so that
@@ -82,6 +98,7 @@ struct DiagFinal {
     double cells;       // nx * ny
     int nz;
     int slot;           // dt slot of the next step
+    const Plane<double>* zp;  // stretched z-grid (trapezoid weights, plate derivatives); nullptr = uniform
 };
 
 template <class R> struct St { R r, mx, mz, E; };       // 2D conserved state

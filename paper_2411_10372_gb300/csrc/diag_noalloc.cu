@@ -102,6 +102,8 @@ extern "C" int cm_diag_noalloc(const void* state, int precision, const cm_grid* 
     if (grid->ndim != 2 && grid->ndim != 3) return set_error(CM_EINVAL, "cm_diag_noalloc: ndim must be 2 or 3");
     const int ny = grid->ndim == 3 ? grid->ny : 1;
     if (grid->nx < 1 || ny < 1 || grid->nz < 5) return set_error(CM_EINVAL, "cm_diag_noalloc: bad grid");
+    if (grid->znodes || grid->zstretch != 0.0)
+        return set_error(CM_EINVAL, "cm_diag_noalloc: uniform z-grids only (use cm_diagnostics for stretched grids)");
     if (grid->nz > kNoAllocMaxNz) {
         char msg[160];
         snprintf(msg, sizeof msg, "cm_diag_noalloc: nz = %d exceeds the no-alloc maximum of %d planes", grid->nz,
@@ -146,7 +148,7 @@ extern "C" int cm_diag_noalloc(const void* state, int precision, const cm_grid* 
         e = precision == CM_FP64
                 ? Launch<double>::diag_planes((const double*)state, layout_coef<double>(*grid, pitch, ny), A, planes, ctl, s)
                 : Launch<float>::diag_planes((const float*)state, layout_coef<float>(*grid, pitch, ny), A, planes, ctl, s);
-    DiagFinal F;
+    DiagFinal F{};
     F.Ra = Ra;
     F.Pr = Pr;
     F.eps = params->eps;

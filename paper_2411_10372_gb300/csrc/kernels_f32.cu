@@ -19,6 +19,8 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     if (!bz) {
         cudaFuncSetAttribute(sweep_z2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         cudaFuncSetAttribute(sweep_x2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        cudaFuncSetAttribute(sweep_z2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        cudaFuncSetAttribute(sweep_x2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         bz = blocks_per_sm(sweep_z2d_x2, kRingBytes);
         bx = blocks_per_sm(sweep_x2d_x2, kRingBytes);
     }
@@ -27,8 +29,13 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
     const long long warps = (long long)io.nstrips * nsegs;
     const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (dir == 2) return launch_pdl(true, sweep_z2d_x2, dim3(blocks), dim3(kWarpsPerBlock * 32), kRingBytes, s, io, C, sc);
-    if (dir == 0) return launch_pdl(true, sweep_x2d_x2, dim3(blocks), dim3(kWarpsPerBlock * 32), kRingBytes, s, io, C, sc);
+    const dim3 g(blocks), b(kWarpsPerBlock * 32);
+    if (dir == 2)
+        return C.zp ? launch_pdl(true, sweep_z2d_x2s, g, b, kRingBytes, s, io, C, sc)
+                    : launch_pdl(true, sweep_z2d_x2, g, b, kRingBytes, s, io, C, sc);
+    if (dir == 0)
+        return C.zp ? launch_pdl(true, sweep_x2d_x2s, g, b, kRingBytes, s, io, C, sc)
+                    : launch_pdl(true, sweep_x2d_x2, g, b, kRingBytes, s, io, C, sc);
     return cudaErrorInvalidValue;
 }
 

@@ -172,13 +172,18 @@ cudaError_t Launch<R>::sweep(int dir, const R* in, R* out, const R* zt, const Co
     io.zt = zt;
     io.nstrips = (C.nx + kOutW - 1) / kOutW;
     static int bz = 0, bx = 0;
-    if (!bz) { bz = blocks_per_sm(sweep_z2d<R>); bx = blocks_per_sm(sweep_x2d<R>); }
+    if (!bz) { bz = blocks_per_sm(sweep_z2d<R, false>); bx = blocks_per_sm(sweep_x2d<R, false>); }
     io.seg_rows = pick_segment(io.nstrips, C.nz, dir == 2 ? bz : bx, sm_count());
     const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
     const long long warps = (long long)io.nstrips * nsegs;
     const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (dir == 2) return launch_pdl(false, sweep_z2d<R>, dim3(blocks), dim3(kWarpsPerBlock * 32), 0, s, io, C, sc);
-    if (dir == 0) return launch_pdl(false, sweep_x2d<R>, dim3(blocks), dim3(kWarpsPerBlock * 32), 0, s, io, C, sc);
+    const dim3 g(blocks), b(kWarpsPerBlock * 32);
+    if (dir == 2)
+        return C.zp ? launch_pdl(false, sweep_z2d<R, true>, g, b, 0, s, io, C, sc)
+                    : launch_pdl(false, sweep_z2d<R, false>, g, b, 0, s, io, C, sc);
+    if (dir == 0)
+        return C.zp ? launch_pdl(false, sweep_x2d<R, true>, g, b, 0, s, io, C, sc)
+                    : launch_pdl(false, sweep_x2d<R, false>, g, b, 0, s, io, C, sc);
     return cudaErrorInvalidValue;
 }
 

@@ -43,30 +43,39 @@ __device__ __forceinline__ void store_row(R* __restrict__ base, long long fs, in
 }
 
 // dt candidate of one node of the new state, FP64 path: min over x, z of
-// h/(|u|+c), evaluated as the CFL rule is written
-__device__ __forceinline__ double dt_candidate(const St<double>& q, double z, const Coef<double>& C, int& bad)
+// h/(|u|+c), evaluated as the CFL rule is written; hz: the node's z step
+__device__ __forceinline__ double dt_candidate(const St<double>& q, double z, double hz, const Coef<double>& C, int& bad)
 {
     double ux, uz, T, p;
     prims(q, z, C, ux, uz, T, p);
     const double c = sqrt(C.cs2 * T);
-    const double v = fmin(C.dx / (fabs(ux) + c), C.dz / (fabs(uz) + c));
+    const double v = fmin(C.dx / (fabs(ux) + c), hz / (fabs(uz) + c));
     if (!(v > 0.0) || !(v < 1e300)) bad = 1;
     return v;
 }
 
 // FP32 path: the largest rate (|u|+c)/h of a node; the block turns its max
-// into min h/(|u|+c) with one FP64 reciprocal
-__device__ __forceinline__ float dt_rate(const St<float>& q, float z, const Coef<float>& C, int& bad)
+// into min h/(|u|+c) with one FP64 reciprocal; ihz: 1 / the node's z step
+__device__ __forceinline__ float dt_rate(const St<float>& q, float z, float ihz, const Coef<float>& C, int& bad)
 {
     float ux, uz, T, p;
     prims(q, z, C, ux, uz, T, p);
     const float c = sqrtf(C.cs2 * T);
-    const float r = fmaxf((fabsf(ux) + c) * C.inv_dx, (fabsf(uz) + c) * C.inv_dz);
+    const float r = fmaxf((fabsf(ux) + c) * C.inv_dx, (fabsf(uz) + c) * ihz);
     if (!(r > 0.f) || !(r < 1e30f)) bad = 1;
     return r;
 }
 
 __device__ __forceinline__ int clamp_row(int j, int nz) { return min(max(j, 0), nz - 1); }
+
+// Delta / w_k of a stretched plane: the flux-difference factor of its cell
+// (FP64: the division as written; FP32: times the stored reciprocal)
+template <class R>
+__device__ __forceinline__ R lam_cell(double Delta, const Plane<R>& P)
+{
+    if constexpr (kExact<R>) return Delta / P.w;
+    else return (R)Delta * P.iw;
+}
 
 constexpr int kPrefetch = 3;  // rows loaded ahead of the one being consumed
 
@@ -75,7 +84,11 @@ constexpr int kPrefetch = 3;  // rows loaded ahead of the one being consumed
 // input state, plate values.  Row pipeline at step j (row j just loaded):
 //   F^n_{j-1}, X^P_{j-1}, F^P_{j-1}, average at j-2, TVD flux at (j-2,j-1),
 //   output row j-2.
-template <class R>
+// ST: stretched z-grid (C.zp): the flux differences of plane k are divided by
+// its cell width w_k, the one-sided derivatives by the spacing they span, the
+// TVD fluxes weighted by spacing over width (conservative form on uneven
+// planes; on uniform planes every factor reduces to the constant one).
+template <class R, bool ST>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 {
@@ -96,7 +109,11 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
     const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
     const R lam = (R)(Delta / C.dz);
     const R Dl = (R)Delta;
-    const R lam2 = R(2) * lam;
+    R lam_bot = R(2) * lam, lam_top = R(2) * lam;  // half cells on the plates: Delta / w
+    if constexpr (ST) {
+        lam_bot = lam_cell(Delta, C.zp[0]);
+        lam_top = lam_cell(Delta, C.zp[nz - 1]);
+    }
 
     if (sc.first && blockIdx.x == 0 && threadIdx.x == 0) {
         sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
@@ -136,21 +153,29 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 
         // predictor flux F^n_{j-1} (forward z-differences inside F)
         const int m = j - 1;
-        const St<R> F1 = flux_z(Xm1, ux1, uz1, p1, diff(ux0, ux1, C.hz, C.inv_dz), diff(uz0, uz1, C.hz, C.inv_dz),
-                                diff(T0, T1, C.hz, C.inv_dz), dxux1, dxuz1, C);
+        R hf = C.hz, ihf = C.inv_dz, hb = C.hz, ihb = C.inv_dz, lam_m = lam;
+        if constexpr (ST) {
+            const Plane<R>& Pm = C.zp[clamp_row(m, nz)];
+            const Plane<R>& Pb = C.zp[clamp_row(m - 1, nz)];
+            hf = Pm.hp; ihf = Pm.ihp;  // spacing above plane m
+            hb = Pb.hp; ihb = Pb.ihp;  // spacing below plane m
+            lam_m = lam_cell(Delta, Pm);
+        }
+        const St<R> F1 = flux_z(Xm1, ux1, uz1, p1, diff(ux0, ux1, hf, ihf), diff(uz0, uz1, hf, ihf),
+                                diff(T0, T1, hf, ihf), dxux1, dxuz1, C);
         // predictor X^P_{j-1}; plates as half cells with zero wall flux, m = 0, T = T_w
         St<R> XP1;
         if (m >= 1 && m <= nz - 2) {
-            XP1.r = Xm1.r - lam * (F1.r - F2.r);
-            XP1.mx = Xm1.mx - lam * (F1.mx - F2.mx);
-            XP1.mz = (Xm1.mz - lam * (F1.mz - F2.mz)) + Dl * (-C.g * Xm1.r);
-            XP1.E = Xm1.E - lam * (F1.E - F2.E);
+            XP1.r = Xm1.r - lam_m * (F1.r - F2.r);
+            XP1.mx = Xm1.mx - lam_m * (F1.mx - F2.mx);
+            XP1.mz = (Xm1.mz - lam_m * (F1.mz - F2.mz)) + Dl * (-C.g * Xm1.r);
+            XP1.E = Xm1.E - lam_m * (F1.E - F2.E);
         } else if (m <= 0) {
-            XP1.r = Xm1.r - lam2 * F1.r;
+            XP1.r = Xm1.r - lam_bot * F1.r;
             XP1.mx = R(0); XP1.mz = R(0);
             XP1.E = XP1.r * C.ebot;
         } else {
-            XP1.r = Xm1.r + lam2 * F2.r;
+            XP1.r = Xm1.r + lam_top * F2.r;
             XP1.mx = R(0); XP1.mz = R(0);
             XP1.E = XP1.r * C.etop;
         }
@@ -159,24 +184,33 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
         const R dxppux1 = diff(shdn(ppux1), shup(ppux1), C.h2x, C.inv_2dx);
         const R dxppuz1 = diff(shdn(ppuz1), shup(ppuz1), C.h2x, C.inv_2dx);
         // corrector flux F^P_{j-1} (backward z-differences inside F)
-        const St<R> FP1 = flux_z(XP1, ppux1, ppuz1, ppp1, diff(ppux1, ppux2, C.hz, C.inv_dz),
-                                 diff(ppuz1, ppuz2, C.hz, C.inv_dz), diff(ppT1, ppT2, C.hz, C.inv_dz), dxppux1,
+        const St<R> FP1 = flux_z(XP1, ppux1, ppuz1, ppp1, diff(ppux1, ppux2, hb, ihb),
+                                 diff(ppuz1, ppuz2, hb, ihb), diff(ppT1, ppT2, hb, ihb), dxppux1,
                                  dxppuz1, C);
 
         // corrector X^C_{j-2} and the average (X^P + X^C)/2
         const int c = j - 2;
+        R lam_c = lam, hc = C.hz, lamh_c = lam, rp_c = R(1), rm_c = R(1);
+        if constexpr (ST) {
+            const Plane<R>& Pc = C.zp[clamp_row(c, nz)];
+            lam_c = lam_cell(Delta, Pc);
+            hc = Pc.hp;                  // spacing of interface (c, c+1)
+            lamh_c = (R)Delta * Pc.ihp;  // FP32 Courant factor of that interface
+            rp_c = Pc.rp;
+            rm_c = Pc.rm;
+        }
         St<R> Xa;
         if (c >= 1 && c <= nz - 2) {
-            const R xcr = Xm2.r - lam * (FP1.r - FP2.r);
-            const R xcmx = Xm2.mx - lam * (FP1.mx - FP2.mx);
-            const R xcmz = (Xm2.mz - lam * (FP1.mz - FP2.mz)) + Dl * (-C.g * XP2.r);
-            const R xcE = Xm2.E - lam * (FP1.E - FP2.E);
+            const R xcr = Xm2.r - lam_c * (FP1.r - FP2.r);
+            const R xcmx = Xm2.mx - lam_c * (FP1.mx - FP2.mx);
+            const R xcmz = (Xm2.mz - lam_c * (FP1.mz - FP2.mz)) + Dl * (-C.g * XP2.r);
+            const R xcE = Xm2.E - lam_c * (FP1.E - FP2.E);
             Xa.r = (XP2.r + xcr) * R(0.5);
             Xa.mx = (XP2.mx + xcmx) * R(0.5);
             Xa.mz = (XP2.mz + xcmz) * R(0.5);
             Xa.E = (XP2.E + xcE) * R(0.5);
         } else if (c <= 0) {
-            Xa.r = (XP2.r + (Xm2.r - lam2 * FP1.r)) * R(0.5);
+            Xa.r = (XP2.r + (Xm2.r - lam_bot * FP1.r)) * R(0.5);
             Xa.mx = Xa.mz = Xa.E = R(0);
         } else {
             Xa.r = (XP2.r + Xm2.r) * R(0.5);  // F^P on the top plate is m_z = 0
@@ -189,7 +223,7 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
         const R ss1 = dot4(d1, d0);
         St<R> Dn = {R(0), R(0), R(0), R(0)};
         if (c >= 1 && c <= nz - 3) {  // interface (j-2, j-1); zero next to the plates
-            const R G = tvd_G(ss2, ss1, dd1, courant(Delta, lam, A2, A1, C.hz), C.tvd_form);
+            const R G = tvd_G(ss2, ss1, dd1, courant(Delta, lamh_c, A2, A1, hc), C.tvd_form);
             Dn = {G * d1.r, G * d1.mx, G * d1.mz, G * d1.E};
         }
 
@@ -197,10 +231,17 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
         if (c >= ks && c < ke) {
             St<R> Xn;
             if (c >= 1 && c <= nz - 2) {
-                Xn.r = Xa.r + (Dn.r - Dm.r);
-                Xn.mx = Xa.mx + (Dn.mx - Dm.mx);
-                Xn.mz = Xa.mz + (Dn.mz - Dm.mz);
-                Xn.E = Xa.E + (Dn.E - Dm.E);
+                if constexpr (ST) {
+                    Xn.r = Xa.r + (rp_c * Dn.r - rm_c * Dm.r);
+                    Xn.mx = Xa.mx + (rp_c * Dn.mx - rm_c * Dm.mx);
+                    Xn.mz = Xa.mz + (rp_c * Dn.mz - rm_c * Dm.mz);
+                    Xn.E = Xa.E + (rp_c * Dn.E - rm_c * Dm.E);
+                } else {
+                    Xn.r = Xa.r + (Dn.r - Dm.r);
+                    Xn.mx = Xa.mx + (Dn.mx - Dm.mx);
+                    Xn.mz = Xa.mz + (Dn.mz - Dm.mz);
+                    Xn.E = Xa.E + (Dn.E - Dm.E);
+                }
             } else {
                 Xn.r = Xa.r;
                 Xn.mx = R(0); Xn.mz = R(0);
@@ -224,7 +265,9 @@ sweep_z2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 // L_x(Delta) on the interior rows (plate rows pass through).  Row pipeline at
 // step j: F^n_{j-1} and X^P_{j-1} (needs rows j, j-2 for d/dz), then F^P_{j-2}
 // (needs X^P rows j-1, j-3), corrector, average, TVD along x, output row j-2.
-template <class R>
+// ST: stretched z-grid: the central z-differences divide by the distance of
+// the two planes they use, and the CFL z step is the plane's smaller spacing.
+template <class R, bool ST>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 {
@@ -279,9 +322,14 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 
             // row m = j-1: F^n with forward x-differences, central z-differences
             const int m = j - 1;
+            R scm = C.h2z, iscm = C.inv_2dz;
+            if constexpr (ST) {
+                const Plane<R>& Pm = C.zp[clamp_row(m, nz)];
+                scm = Pm.sc; iscm = Pm.isc;
+            }
             const St<R> F1 = flux_x(Xm1, ux1, uz1, p1, diff(shdn(ux1), ux1, C.hx, C.inv_dx),
                                     diff(shdn(uz1), uz1, C.hx, C.inv_dx), diff(shdn(T1), T1, C.hx, C.inv_dx),
-                                    diff(ux0, ux2, C.h2z, C.inv_2dz), diff(uz0, uz2, C.h2z, C.inv_2dz), C);
+                                    diff(ux0, ux2, scm, iscm), diff(uz0, uz2, scm, iscm), C);
             const St<R> Fl = shup(F1);
             St<R> XP1 = Xm1;
             if (m >= 1 && m <= nz - 2) {
@@ -295,9 +343,17 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
 
             // row c = j-2: F^P with backward x-differences, corrector, average
             const int c = j - 2;
+            R scc = C.h2z, iscc = C.inv_2dz;
+            double hzc = C.dz;
+            R ihzc = C.inv_dz;
+            if constexpr (ST) {
+                const Plane<R>& Pc = C.zp[clamp_row(c, nz)];
+                scc = Pc.sc; iscc = Pc.isc;
+                hzc = (double)Pc.hmin; ihzc = Pc.ihmin;
+            }
             const St<R> FP = flux_x(XP2, ppux2, ppuz2, ppp2, diff(ppux2, shup(ppux2), C.hx, C.inv_dx),
                                     diff(ppuz2, shup(ppuz2), C.hx, C.inv_dx), diff(ppT2, shup(ppT2), C.hx, C.inv_dx),
-                                    diff(ppux1, ppux3, C.h2z, C.inv_2dz), diff(ppuz1, ppuz3, C.h2z, C.inv_2dz), C);
+                                    diff(ppux1, ppux3, scc, iscc), diff(ppuz1, ppuz3, scc, iscc), C);
             const St<R> FPr = shdn(FP);
             St<R> Xa;
             Xa.r = (XP2.r + (Xm2.r - lam * (FPr.r - FP.r))) * R(0.5);
@@ -328,8 +384,8 @@ sweep_x2d(SweepIO<R> io, Coef<R> C, SweepCtl sc)
                 if (own) {
                     store_row(io.out, fs, c, pitch, i, Xn);
                     if (sc.last) {
-                        if constexpr (kExact<R>) vmin = fmin(vmin, dt_candidate(Xn, io.zt[c], C, bad));
-                        else rmax = fmax(rmax, dt_rate(Xn, io.zt[c], C, bad));
+                        if constexpr (kExact<R>) vmin = fmin(vmin, dt_candidate(Xn, io.zt[c], hzc, C, bad));
+                        else rmax = fmax(rmax, dt_rate(Xn, io.zt[c], ihzc, C, bad));
                     }
                 }
             }

@@ -206,7 +206,11 @@ __device__ __forceinline__ bool interior_segment(int ks, int ke, int nz) { retur
 // corrector split into its two rows.
 // one warp's segment of the z sweep: columns of strip `strip`, output rows
 // [ks, ks + seg_rows); `lead` marks the one thread block that does the
-// per-step bookkeeping of a first sweep
+// per-step bookkeeping of a first sweep.  ST: stretched z-grid (C.zp):
+// flux differences of plane k over its cell width w_k,
+// one-sided derivatives over the spacing they span, TVD fluxes weighted by
+// spacing over width, Courant numbers over the interface spacing.
+template <bool ST = false>
 __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __restrict__ out, const Coef<float>& C,
                                         const SweepCtl& sc, int strip, int ks, int seg_rows, bool lead)
 {
@@ -229,6 +233,14 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
     const f2 lam = bc(lamf), hlam = bc(0.5f * lamf), lam2 = bc(2.f * lamf);
     const f2 mDg = bc(-(float)Delta * C.g);  // Delta * (source per unit density)
     const f2 half = bc(0.5f), idz = bc(C.inv_dz), i2dx = bc(C.inv_2dx);
+    const float Df = (float)Delta;
+    // plate half cells: Delta / w (predictor) and Delta / (2 w) (corrector average)
+    f2 lam_bot = lam2, lam_top = lam2, hlam_bot = lam;
+    if constexpr (ST) {
+        lam_bot = bc(Df * C.zp[0].iw);
+        lam_top = bc(Df * C.zp[nz - 1].iw);
+        hlam_bot = bc(0.5f * Df * C.zp[0].iw);
+    }
 
     if (sc.first && lead && threadIdx.x == 0) {
         sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
@@ -239,10 +251,14 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
 
     const RowRing ring{ring_mem + threadIdx.x};
     auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
-    auto gz_of = [&](int j) { return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz)); };
+    auto gz_of = [&](int j) {
+        if constexpr (ST) return bc(-C.g * __ldg(&C.zp[min(max(j, 0), nz - 1)].z));
+        else return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz));
+    };
     // the first step is j0 = ks - 1 (primed with row ks - 2): no output row
     // >= ks uses anything an earlier step would produce
     const int j0 = ks - 1;
+
     for (int q = 0; q < kRing - 1; ++q) ring.request(q, io.in + row_off(j0 + q), fs);
 
     const f2 z0 = bc(0.f);
@@ -276,7 +292,9 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         }
         cp_async_wait_ring();
         const S2 X0 = ring.take(t % kRing);
-        const f2 gz0 = edge ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
+        f2 gz0;
+        if constexpr (ST) gz0 = edge ? gz_of(j) : bc(-C.g * __ldg(&C.zp[j].z));
+        else gz0 = edge ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
 
         f2 ux0, uz0, T0, p0;
         prims2(X0, gz0, C, ux0, uz0, T0, p0);
@@ -284,24 +302,33 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
 
         // row m = j-1: F^n (forward z, central x), X^P, F^P (backward z)
         const int m = j - 1;
+        // stretched: planes m and c = m - 1 (clamped on the edge path)
+        const int mc = ST ? (edge ? min(max(m, 0), nz - 1) : m) : 0;
+        const int cc = ST ? (edge ? min(max(m - 1, 0), nz - 1) : m - 1) : 0;
+        f2 lam_m = lam, idz_f = idz, idz_b = idz;  // Delta/w_m, 1/(spacing above m), 1/(spacing below m)
+        if constexpr (ST) {
+            lam_m = bc(Df * __ldg(&C.zp[mc].iw));
+            idz_f = bc(__ldg(&C.zp[mc].ihp));
+            idz_b = bc(__ldg(&C.zp[cc].ihp));
+        }
         const f2 dxux1 = mul2(sub2(right_of(ux1), left_of(ux1)), i2dx);
         const f2 dxuz1 = mul2(sub2(right_of(uz1), left_of(uz1)), i2dx);
-        const S2 F1 = flux_z2(Xm1, ux1, uz1, p1, mul2(sub2(ux0, ux1), idz), mul2(sub2(uz0, uz1), idz),
-                              mul2(sub2(T0, T1), idz), dxux1, dxuz1, C);
+        const S2 F1 = flux_z2(Xm1, ux1, uz1, p1, mul2(sub2(ux0, ux1), idz_f), mul2(sub2(uz0, uz1), idz_f),
+                              mul2(sub2(T0, T1), idz_f), dxux1, dxuz1, C);
         S2 XP1 = Xm1;
         const bool interior_m = !edge || (m >= 1 && m <= nz - 2);
         if (ramp == 1) {
         } else if (interior_m) {
-            XP1.r = fnma2(lam, sub2(F1.r, F2.r), Xm1.r);
-            XP1.mx = fnma2(lam, sub2(F1.mx, F2.mx), Xm1.mx);
-            XP1.mz = fma2(mDg, Xm1.r, fnma2(lam, sub2(F1.mz, F2.mz), Xm1.mz));
-            XP1.E = fnma2(lam, sub2(F1.E, F2.E), Xm1.E);
+            XP1.r = fnma2(lam_m, sub2(F1.r, F2.r), Xm1.r);
+            XP1.mx = fnma2(lam_m, sub2(F1.mx, F2.mx), Xm1.mx);
+            XP1.mz = fma2(mDg, Xm1.r, fnma2(lam_m, sub2(F1.mz, F2.mz), Xm1.mz));
+            XP1.E = fnma2(lam_m, sub2(F1.E, F2.E), Xm1.E);
         } else if (m <= 0) {
-            XP1.r = fnma2(lam2, F1.r, Xm1.r);
+            XP1.r = fnma2(lam_bot, F1.r, Xm1.r);
             XP1.mx = z0; XP1.mz = z0;
             XP1.E = mul2(XP1.r, bc(C.ebot));
         } else {
-            XP1.r = fma2(lam2, F2.r, Xm1.r);
+            XP1.r = fma2(lam_top, F2.r, Xm1.r);
             XP1.mx = z0; XP1.mz = z0;
             XP1.E = mul2(XP1.r, bc(C.etop));
         }
@@ -311,8 +338,8 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         if (ramp == 0) {
             const f2 dxppux1 = mul2(sub2(right_of(ppux1), left_of(ppux1)), i2dx);
             const f2 dxppuz1 = mul2(sub2(right_of(ppuz1), left_of(ppuz1)), i2dx);
-            FP1 = flux_z2(XP1, ppux1, ppuz1, ppp1, mul2(sub2(ppux1, ppux2), idz), mul2(sub2(ppuz1, ppuz2), idz),
-                          mul2(sub2(ppT1, ppT2), idz), dxppux1, dxppuz1, C);
+            FP1 = flux_z2(XP1, ppux1, ppuz1, ppp1, mul2(sub2(ppux1, ppux2), idz_b), mul2(sub2(ppuz1, ppuz2), idz_b),
+                          mul2(sub2(ppT1, ppT2), idz_b), dxppux1, dxppuz1, C);
         }
 
         // TVD flux across (j-2, j-1) from the input state
@@ -321,20 +348,30 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         const f2 ss1 = ramp == 1 ? z0 : dot2(d1, d0);
         const int c = j - 2;
         S2 Dn = {z0, z0, z0, z0};
-        if (ramp == 0 && (!edge || (c >= 1 && c <= nz - 3)))
-            Dn = scale2(tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form), d1);
+        if (ramp == 0 && (!edge || (c >= 1 && c <= nz - 3))) {
+            const f2 lamh_c = ST ? bc(Df * __ldg(&C.zp[cc].ihp)) : lam;  // Delta / (spacing of interface c, c+1)
+            Dn = scale2(tvd_G2(ss2, ss1, dd1, mul2(lamh_c, max2(A2, A1)), C.tvd_form), d1);
+        }
 
         // output row c = j-2
         if (store) {
             S2 Xn;
             if (!edge || (c >= 1 && c <= nz - 2)) {
-                Xn.r = add2(fnma2(hlam, FP1.r, H.r), Dn.r);
-                Xn.mx = add2(fnma2(hlam, FP1.mx, H.mx), Dn.mx);
-                Xn.mz = add2(fnma2(hlam, FP1.mz, H.mz), Dn.mz);
-                Xn.E = add2(fnma2(hlam, FP1.E, H.E), Dn.E);
+                if constexpr (ST) {
+                    const f2 hl = bc(0.5f * Df * __ldg(&C.zp[cc].iw)), rp = bc(__ldg(&C.zp[cc].rp));
+                    Xn.r = fma2(rp, Dn.r, fnma2(hl, FP1.r, H.r));
+                    Xn.mx = fma2(rp, Dn.mx, fnma2(hl, FP1.mx, H.mx));
+                    Xn.mz = fma2(rp, Dn.mz, fnma2(hl, FP1.mz, H.mz));
+                    Xn.E = fma2(rp, Dn.E, fnma2(hl, FP1.E, H.E));
+                } else {
+                    Xn.r = add2(fnma2(hlam, FP1.r, H.r), Dn.r);
+                    Xn.mx = add2(fnma2(hlam, FP1.mx, H.mx), Dn.mx);
+                    Xn.mz = add2(fnma2(hlam, FP1.mz, H.mz), Dn.mz);
+                    Xn.E = add2(fnma2(hlam, FP1.E, H.E), Dn.E);
+                }
             } else {
                 // plates: rho = (rho^P + rho^C)/2 with the half-cell corrector
-                Xn.r = (c == 0) ? fnma2(lam, FP1.r, H.r) : H.r;
+                Xn.r = (c == 0) ? fnma2(hlam_bot, FP1.r, H.r) : H.r;
                 Xn.mx = z0; Xn.mz = z0;
                 Xn.E = mul2(Xn.r, bc(c == 0 ? C.ebot : C.etop));
             }
@@ -345,10 +382,18 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         // H of row m for the next step
         if (ramp != 0) {
         } else if (interior_m) {
-            H.r = sub2(mul2(half, fma2(lam, FP1.r, add2(XP1.r, Xm1.r))), Dn.r);
-            H.mx = sub2(mul2(half, fma2(lam, FP1.mx, add2(XP1.mx, Xm1.mx))), Dn.mx);
-            H.mz = sub2(mul2(half, fma2(lam, FP1.mz, fma2(mDg, XP1.r, add2(XP1.mz, Xm1.mz)))), Dn.mz);
-            H.E = sub2(mul2(half, fma2(lam, FP1.E, add2(XP1.E, Xm1.E))), Dn.E);
+            if constexpr (ST) {
+                const f2 rm = bc(__ldg(&C.zp[mc].rm));
+                H.r = fnma2(rm, Dn.r, mul2(half, fma2(lam_m, FP1.r, add2(XP1.r, Xm1.r))));
+                H.mx = fnma2(rm, Dn.mx, mul2(half, fma2(lam_m, FP1.mx, add2(XP1.mx, Xm1.mx))));
+                H.mz = fnma2(rm, Dn.mz, mul2(half, fma2(lam_m, FP1.mz, fma2(mDg, XP1.r, add2(XP1.mz, Xm1.mz)))));
+                H.E = fnma2(rm, Dn.E, mul2(half, fma2(lam_m, FP1.E, add2(XP1.E, Xm1.E))));
+            } else {
+                H.r = sub2(mul2(half, fma2(lam, FP1.r, add2(XP1.r, Xm1.r))), Dn.r);
+                H.mx = sub2(mul2(half, fma2(lam, FP1.mx, add2(XP1.mx, Xm1.mx))), Dn.mx);
+                H.mz = sub2(mul2(half, fma2(lam, FP1.mz, fma2(mDg, XP1.r, add2(XP1.mz, Xm1.mz)))), Dn.mz);
+                H.E = sub2(mul2(half, fma2(lam, FP1.E, add2(XP1.E, Xm1.E))), Dn.E);
+            }
         } else {
             H.r = mul2(half, add2(XP1.r, Xm1.r));
             H.mx = z0; H.mz = z0; H.E = z0;
@@ -409,7 +454,10 @@ sweep_z2d_x2(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 // (backward x, central z from X^P rows j-1 and j-3) and
 // X_new_c = K_c - (lambda/2)(F^P_{i+1} - F^P_i).
 // one warp's segment of the x sweep (see z2_body); every thread of the block
-// must call it when sc.last is set (block reduction of the next dt)
+// must call it when sc.last is set (block reduction of the next dt).  ST:
+// stretched z-grid: central z-differences over the distance of the two planes
+// they use, CFL z step of a plane its smaller spacing.
+template <bool ST = false>
 __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __restrict__ out, const Coef<float>& C,
                                         const SweepCtl& sc, int strip, int ks, int seg_rows, bool lead)
 {
@@ -443,7 +491,10 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
     if (ks < nz) {
         const RowRing ring{ring_mem + threadIdx.x};
         auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
-        auto gz_of = [&](int j) { return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz)); };
+        auto gz_of = [&](int j) {
+            if constexpr (ST) return bc(-C.g * __ldg(&C.zp[min(max(j, 0), nz - 1)].z));
+            else return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz));
+        };
         const f2 idx_ = bc(C.inv_dx), i2dz = bc(C.inv_2dz);
         const f2 z0 = bc(0.f);
 
@@ -462,6 +513,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
         f2 gz2 = gz1;  // -g z of row j-2
         const float* gnext = io.in + row_off(j0 + kRing - 1);
         float* gout = io.out + (long long)(j0 - 2) * pitch + i;  // used only when the row exists
+        float isc_prev = C.inv_2dz;  // stretched: 1/sc of plane m - 1 = c, carried
 
         // ramp 1: the first step of an interior segment, which skips what no
         // stored row uses (F^n, X^P, the TVD term and K of row ks - 2)
@@ -478,17 +530,26 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
             }
             cp_async_wait_ring();
             const S2 X0 = ring.take(t % kRing);
-            const f2 gz0 = edge ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
+            f2 gz0;
+            if constexpr (ST) gz0 = edge ? gz_of(j) : bc(-C.g * __ldg(&C.zp[j].z));
+            else gz0 = edge ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
             f2 ux0, uz0, T0, p0;
             prims2(X0, gz0, C, ux0, uz0, T0, p0);
 
             // row m = j-1
             const int m = j - 1;
+            f2 i2dz_m = i2dz, i2dz_c = i2dz;  // 1/(central z span) of planes m and c = m - 1
+            float isc_m = 0.f;
+            if constexpr (ST) {
+                isc_m = __ldg(&C.zp[edge ? min(max(m, 0), nz - 1) : m].isc);
+                i2dz_m = bc(isc_m);
+                i2dz_c = bc(isc_prev);
+            }
             S2 XP1 = Xm1, K1 = Xm1;  // plate rows pass through
             if (ramp != 1 && (!edge || (m >= 1 && m <= nz - 2))) {
                 const S2 F1 = flux_x2(Xm1, ux1, uz1, p1, mul2(sub2(right_of(ux1), ux1), idx_),
                                       mul2(sub2(right_of(uz1), uz1), idx_), mul2(sub2(right_of(T1), T1), idx_),
-                                      mul2(sub2(ux0, ux2), i2dz), mul2(sub2(uz0, uz2), i2dz), C);
+                                      mul2(sub2(ux0, ux2), i2dz_m), mul2(sub2(uz0, uz2), i2dz_m), C);
                 const S2 Fl = left_of(F1);
                 XP1.r = fnma2(lam, sub2(F1.r, Fl.r), Xm1.r);
                 XP1.mx = fnma2(lam, sub2(F1.mx, Fl.mx), Xm1.mx);
@@ -519,7 +580,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
                 if (!edge || (c >= 1 && c <= nz - 2)) {
                     const S2 FP = flux_x2(XP2, ppux2, ppuz2, ppp2, mul2(sub2(ppux2, left_of(ppux2)), idx_),
                                           mul2(sub2(ppuz2, left_of(ppuz2)), idx_), mul2(sub2(ppT2, left_of(ppT2)), idx_),
-                                          mul2(sub2(ppux1, ppux3), i2dz), mul2(sub2(ppuz1, ppuz3), i2dz), C);
+                                          mul2(sub2(ppux1, ppux3), i2dz_c), mul2(sub2(ppuz1, ppuz3), i2dz_c), C);
                     const S2 FPr = right_of(FP);
                     Xn.r = fnma2(hlam, sub2(FPr.r, FP.r), K2.r);
                     Xn.mx = fnma2(hlam, sub2(FPr.mx, FP.mx), K2.mx);
@@ -533,7 +594,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
                         prims2(Xn, gz2, C, ux, uz, T, p);
                         const f2 cs = sqrt2(mul2(bc(C.cs2), T));
                         const f2 rx = mul2(add2(abs2(ux), cs), idx_);
-                        const f2 rz = mul2(add2(abs2(uz), cs), bc(C.inv_dz));
+                        const f2 rz = mul2(add2(abs2(uz), cs), bc(ST ? __ldg(&C.zp[c].ihmin) : C.inv_dz));
                         const float r = fmaxf(fmaxf(rx.x, rx.y), fmaxf(rz.x, rz.y));
                         if (!(r > 0.f) || !(r < 1e30f)) bad = 1;
                         rmax = fmaxf(rmax, r);
@@ -549,6 +610,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
             ppux3 = ppux2; ppuz3 = ppuz2;
             XP2 = XP1; K2 = K1;
             ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
+            if constexpr (ST) isc_prev = isc_m;
         };
 
         // steps j0 .. ke+1: three that only fill the pipeline, then one output row
@@ -589,6 +651,23 @@ sweep_x2d_x2(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
     pdl_enter();
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     x2_body(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
+}
+
+// the same two sweeps on a stretched z-grid (C.zp set)
+__global__ void __launch_bounds__(kThreads2, 4)
+sweep_z2d_x2s(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
+{
+    pdl_enter();
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    z2_body<true>(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4)
+sweep_x2d_x2s(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
+{
+    pdl_enter();
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    x2_body<true>(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
 }
 
 // ---- batched ensemble: many independent boxes in one launch per sweep -----

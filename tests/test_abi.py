@@ -41,7 +41,7 @@ def test_struct_layout_matches_c(tmp_path):
 int main(void) {
   printf("cm_grid %zu\\ncm_params %zu\\ncm_diag %zu\\n", sizeof(cm_grid), sizeof(cm_params), sizeof(cm_diag));
   O(cm_params, seed); O(cm_params, precision); O(cm_params, stream); O(cm_params, state_buf);
-  O(cm_diag, status); O(cm_diag, mach_max); O(cm_grid, aspect);
+  O(cm_diag, status); O(cm_diag, mach_max); O(cm_grid, aspect); O(cm_grid, zstretch); O(cm_grid, znodes);
   return 0; }
 ''')
     exe = tmp_path / "probe"
@@ -86,3 +86,28 @@ def test_argument_errors_need_no_gpu():
     assert e.value.code == cm.CM_ENOTINIT
     assert cm.cm_state_ptr(0) == 0
     assert "cm_init" in cm.cm_last_error() or "no context" in cm.cm_last_error()
+
+
+def test_stretched_grid_argument_errors_need_no_gpu():
+    """The z-grid is validated before any device work: planes must run from
+    exactly 0 to exactly 1 and increase; beta must be in [0, 20]; stretched
+    grids are 2D single contexts only (3D, batch and the no-alloc
+    diagnostics reject them)."""
+    import numpy as np
+    bad = [np.linspace(0, 1, 16) * 0.99, np.r_[0.0, 0.5, 0.3, np.linspace(0.6, 1, 13)],
+           np.r_[1e-9, np.linspace(0.1, 1, 15)], np.r_[0.0, np.nan, np.linspace(0.2, 1, 14)]]
+    for z in bad:
+        g = cm.cm_grid(2, 64, 1, 16, 4.0, 0.0, z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_init(g, 1e6, 1.0, 5 / 3)
+        assert e.value.code == cm.CM_EINVAL, z
+    for beta in (-1.0, 25.0, float("nan")):
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_init(cm.cm_grid(2, 64, 1, 16, 4.0, beta), 1e6, 1.0, 5 / 3)
+        assert e.value.code == cm.CM_EINVAL, beta
+    with pytest.raises(cm.CMError) as e:
+        cm.cm_init(cm.cm_grid(3, 16, 16, 16, 4.0, 2.0), 1e6, 1.0, 5 / 3)
+    assert e.value.code == cm.CM_EINVAL and "2D" in cm.cm_last_error()
+    with pytest.raises(cm.CMError) as e:
+        cm.cm_batch_init([cm.cm_grid(2, 64, 1, 16, 4.0, 1.5)], [1e6], 1.0, 5 / 3)
+    assert e.value.code == cm.CM_EINVAL

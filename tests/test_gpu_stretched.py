@@ -1,0 +1,184 @@
+"""Parity of the CUDA path with the FP64 oracle on stretched z-grids (the tanh
+grid of Sec. 3 and seeded uneven planes), through the C ABI.
+
+Bars: FP64 single sweeps <= 1e-13 relative L2 per field, FP64 steps <= 1e-12
+after 200 steps, diagnostics <= 1e-12; FP32 as on the uniform grid (single
+sweeps 2e-6, 100 steps 1e-5, momentum against rho c).  Inputs are seeded and
+synthetic; the plane heights are inputs given to both sides (or beta, from
+which each side computes its own tanh planes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from physics import closures
+from test_gpu_parity import rel_l2
+from test_oracle_pins import random_planes, stirred_on
+
+pytestmark = pytest.mark.gpu
+
+
+def solver_for(cfg: O.Config, precision="fp64", **extra):
+    import paper_2411_10372_gb300 as cm
+    t_top = (1.0 - cfg.eps - cfg.D) if cfg.t_top is None else cfg.t_top
+    return cm.Solver(cfg.nx, cfg.nz, cfg.Ra, cfg.Pr, cfg.gamma, aspect=cfg.aspect, precision=precision,
+                     eps=cfg.eps, D=cfg.D, cfl=cfg.cfl, dt_fixed=cfg.dt_fixed, gravity=cfg.gravity,
+                     t_bot=cfg.t_bot, t_top=t_top, pert_amp=cfg.pert_amp, stokes=cfg.stokes, seed=cfg.seed,
+                     tvd_form=cfg.tvd_form, zstretch=cfg.zstretch, znodes=cfg.znodes, **extra)
+
+
+GRIDS = [("tanh2", dict(zstretch=2.0)), ("tanh1", dict(zstretch=1.0)), ("random", "random")]
+SHAPES = [(8, 9), (29, 17), (64, 33), (100, 41), (256, 65)]
+
+
+def cfg_for(nx, nz, grid, **kw):
+    if grid == "random":
+        return O.Config(nx=nx, nz=nz, znodes=random_planes(nz, seed=nx + nz), **kw)
+    return O.Config(nx=nx, nz=nz, **grid, **kw)
+
+
+@pytest.mark.parametrize("nx,nz", SHAPES)
+@pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
+def test_planes_match_oracle(nx, nz, name, grid):
+    cfg = cfg_for(nx, nz, grid)
+    s = solver_for(cfg)
+    z = s.z
+    want = O.znodes(cfg)
+    if cfg.znodes is not None:
+        assert np.array_equal(z, want)
+    else:
+        assert np.max(np.abs(z - want)) <= 2e-16
+    s.close()
+
+
+@pytest.mark.parametrize("nx,nz", SHAPES)
+@pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
+@pytest.mark.parametrize("tvd", [O.TVD_SPLIT, O.TVD_SUM, O.TVD_OFF])
+def test_single_sweeps_fp64(nx, nz, name, grid, tvd):
+    """One L_z and one L_x on a stirred state, every node, FP64."""
+    cfg = cfg_for(nx, nz, grid, Ra=1e5, tvd_form=tvd, dt_fixed=1e-5)
+    z = O.znodes(cfg)
+    X = stirred_on(cfg, z, seed=nx * 31 + nz)
+    s = solver_for(cfg)
+    for direction in (2, 0):
+        Delta = 0.2 * min(cfg.aspect / nx, float(np.min(np.diff(z)))) / 4.0
+        s.set_state(X)
+        s.sweep(direction, Delta)
+        got = s.state()
+        want = O.sweep(cfg, X, direction, Delta)
+        for f in range(4):
+            assert rel_l2(got[f], want[f]) <= 1e-13, (direction, f, rel_l2(got[f], want[f]))
+    s.close()
+
+
+@pytest.mark.parametrize("nx,nz", [(30, 17), (64, 33), (250, 65), (122, 41)])
+@pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
+def test_single_sweeps_fp32(nx, nz, name, grid):
+    """FP32 sweeps (packed two-column kernels for even nx) on a stirred state
+    rounded to FP32, against the oracle on the same rounded input."""
+    cfg = cfg_for(nx, nz, grid, Ra=1e5, dt_fixed=1e-5)
+    z = O.znodes(cfg)
+    X = stirred_on(cfg, z, seed=nx * 7 + nz).astype(np.float32).astype(np.float64)
+    s = solver_for(cfg, "fp32")
+    for direction in (2, 0):
+        Delta = 0.2 * min(cfg.aspect / nx, float(np.min(np.diff(z)))) / 4.0
+        s.set_state(X)
+        s.sweep(direction, Delta)
+        got = s.state()
+        want = O.sweep(cfg, X, direction, Delta)
+        for f in (0, 3):
+            assert rel_l2(got[f], want[f]) <= 2e-6, (direction, f, rel_l2(got[f], want[f]))
+        scale = np.linalg.norm(want[0]) * 3.65
+        for f in (1, 2):
+            assert np.linalg.norm(got[f] - want[f]) / scale <= 2e-6, (direction, f)
+    s.close()
+
+
+@pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
+def test_fp64_steps_match_oracle(name, grid):
+    """200 FP64 steps of the 256 x 65, Ra = 1e6 configuration on a stretched
+    grid from the seeded initial state: state, time and dt sequence."""
+    cfg = cfg_for(256, 65, grid, Ra=1e6)
+    s = solver_for(cfg, diag_every=50)
+    assert np.array_equal(s.state(), O.init(cfg))
+    X0 = O.init(cfg)
+    assert abs(s.dt() - O.dt(cfg, X0)) <= 1e-15 * O.dt(cfg, X0)
+    s.step(200)
+    t_gpu, steps = s.time()
+    got = s.state()
+    want, t_cpu, _ = O.step(cfg, X0, 200)
+    assert steps == 200 and abs(t_gpu - t_cpu) <= 1e-13 * t_cpu
+    for f in range(4):
+        assert rel_l2(got[f], want[f]) <= 1e-12, (f, rel_l2(got[f], want[f]))
+    d_gpu = s.diagnostics()[-1]
+    d_cpu = O.diag(cfg, want)
+    for key in ("Nu", "Nu_conv", "Nu_K", "Nu_bot", "Nu_top", "Nu_bar", "Re", "KE", "mass", "energy"):
+        assert abs(d_gpu[key] - d_cpu[key]) <= 1e-10 * max(abs(d_cpu[key]), 1e-6), key
+    # trapezoid mass on the planes is conserved
+    z = O.znodes(cfg)
+    m0 = np.trapezoid(X0[0].mean(axis=1), z)
+    assert abs(np.trapezoid(got[0].mean(axis=1), z) - m0) <= 1e-13 * m0
+    s.close()
+
+
+@pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
+def test_fp32_steps(name, grid):
+    cfg = cfg_for(256, 65, grid, Ra=1e6)
+    s = solver_for(cfg, "fp32")
+    s.step(100)
+    got = s.state()
+    want, _, _ = O.step(cfg, O.init(cfg), 100)
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    assert rel_l2(got[0], want[0]) <= 1e-5
+    assert rel_l2(got[3], want[3]) <= 1e-5
+    scale = np.linalg.norm(want[0] * math.sqrt(cfg.gamma * cl["a"]))
+    for f in (1, 2):
+        assert np.linalg.norm(got[f] - want[f]) / scale <= 1e-5, f
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_diagnostics_and_dt_on_same_state(precision):
+    """Trapezoid weights w_k and the plate quadratic on uneven planes; dt from
+    the smaller spacing next to each plane."""
+    cfg = cfg_for(128, 33, dict(zstretch=2.5), Ra=1e7)
+    z = O.znodes(cfg)
+    X = stirred_on(cfg, z, seed=5, u_amp=0.1)
+    if precision == "fp32":
+        X = X.astype(np.float32).astype(np.float64)
+    s = solver_for(cfg, precision)
+    s.set_state(X)
+    d = s.sample()
+    want = O.diag(cfg, X)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    for key in ("Nu", "Nu_conv", "Nu_K", "Re", "KE", "mass", "energy"):
+        assert abs(d[key] - want[key]) <= tol * max(abs(want[key]), 1.0), key
+    # plate Nusselt numbers: the rounding of a plane mean of T (unit u: 2e-14
+    # in FP64 sums of FP64 T, 2e-7 for FP32 T) enters amplified by the sum of
+    # the three-plane derivative coefficients over eps (~16000 here: the
+    # first spacing is 0.0025)
+    u = 2e-14 if precision == "fp64" else 2e-7
+    for key, (a, b, c) in (("Nu_bot", (z[0], z[1], z[2])), ("Nu_top", (z[-1], z[-2], z[-3]))):
+        h1, h2 = abs(b - a), abs(c - b)
+        amp = ((2 * h1 + h2) / (h1 * (h1 + h2)) + (h1 + h2) / (h1 * h2) + h1 / (h2 * (h1 + h2))) / cfg.eps
+        assert abs(d[key] - want[key]) <= u * amp, (key, d[key] - want[key], u * amp)
+    dt_tol = 1e-15 if precision == "fp64" else 1e-6
+    assert abs(s.dt() - O.dt(cfg, X)) <= dt_tol * O.dt(cfg, X)
+    s.close()
+
+
+def test_uniform_grid_path_unchanged_by_explicit_uniform_planes():
+    """Planes given as k/K run the stretched kernels; they agree with the
+    uniform kernels to rounding of the spacings."""
+    cfg_u = O.Config(nx=128, nz=33, Ra=1e6)
+    cfg_s = O.Config(nx=128, nz=33, Ra=1e6, znodes=np.arange(33) / 32.0)
+    out = []
+    for cfg in (cfg_u, cfg_s):
+        s = solver_for(cfg)
+        s.step(50)
+        out.append(s.state())
+        s.close()
+    for f in range(4):
+        assert rel_l2(out[1][f], out[0][f]) <= 1e-12, f
