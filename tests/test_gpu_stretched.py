@@ -182,3 +182,26 @@ def test_uniform_grid_path_unchanged_by_explicit_uniform_planes():
         s.close()
     for f in range(4):
         assert rel_l2(out[1][f], out[0][f]) <= 1e-12, f
+
+
+def test_full_size_one_step_fp64_and_fp32():
+    """The 4096 x 1024, Ra = 1e10 workload on the tanh grid (beta = 2) in the
+    bench's launch configuration: one full step on every node against the
+    oracle, and the trapezoid mass on the planes."""
+    cfg = O.Config(nx=4096, nz=1024, Ra=1e10, zstretch=2.0)
+    X0 = O.init(cfg)
+    want, _, _ = O.step(cfg, X0, 1)
+    z = O.znodes(cfg)
+    m0 = np.trapezoid(X0[0].mean(axis=1), z)
+    for precision, tol in (("fp64", 1e-13), ("fp32", 2e-6)):
+        s = solver_for(cfg, precision)
+        s.step(1)
+        got = s.state()
+        for f in (0, 3):
+            assert rel_l2(got[f], want[f]) <= tol, (precision, f)
+        scale = np.linalg.norm(want[0]) * 3.65
+        for f in (1, 2):
+            assert np.linalg.norm(got[f] - want[f]) / scale <= tol, (precision, f)
+        mass_tol = 1e-14 if precision == "fp64" else 1e-6
+        assert abs(np.trapezoid(got[0].mean(axis=1), z) - m0) <= mass_tol * m0, precision
+        s.close()
