@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 NX, NZ, RA, PR, GAMMA = 4096, 1024, 1e10, 1.0, 5.0 / 3.0
 RA3 = 1e9  # the 512 x 512 x 128 box
-ZSTRETCH = 2.0  # tanh z-grid of the stretched leg (first spacing 0.25 of the uniform one)
+ZSTRETCH = 2.0  # tanh z-grid of the stretched leg (first spacing 0.147 of the uniform one)
 WORKLOAD = "2d_aspect4_4096x1024_Ra1e10"
 METRIC = "cell-updates/s per MacCormack-TVD step"
 UNIT = "cell-updates/s"
