@@ -279,6 +279,24 @@ def run_gpu(args):
                                  "unit": "GB/s", "frac": round(bytes3 / (v / 2 * 1e-3) / 1e9 / hbm, 4)}
                              for k, v in kinds3.items()},
                 "l2": "flushed before every timed step (256 MiB memset)"}
+        if not args.no_stretched:
+            # the same box on the tanh z-grid (stretched kernels)
+            s3 = cm.Solver(n3[0], n3[2], RA3, PR, GAMMA, ny=n3[1], ndim=3, precision="fp32", stream=stream,
+                           seed=777 + rank, zstretch=ZSTRETCH)
+            s3.step(min(args.warmup, 5))
+            s3.sync()
+            barrier()
+            l3 = cm.cm_launch_count()
+            k3s = max(3, args.steps_3d // 2)
+            sw3s, st3s = cm.cm_profile_steps(k3s, FLUSH_BYTES)
+            barrier()
+            nl3s = cm.cm_launch_count() - l3
+            d3s = s3.sample()
+            s3.close()
+            ms3s = max_ms(sum(st3s))
+            box3["stretched"] = {"value": job_rate(cells3, k3s, ms3s, world), "unit": UNIT, "steps": k3s,
+                                 "zstretch": ZSTRETCH, "ms_per_step": ms3s / k3s, "gpu_launches": nl3s,
+                                 "finite": d3s["status"] == 0, "sweep_ms": [round(x, 5) for x in sw3s]}
 
     # ---- adjoint: 1024 x 256, Ra = 1e8, FP64, 2000 steps, checkpoints every
     # 100, J = mean Nu_bar over steps 1501..2000; cost of the reverse pass

@@ -66,9 +66,9 @@ typedef struct cm_grid {
      * z_{k-1})/2 (half cells on the plates), derivatives divide by the
      * distance of the planes they use, volume averages use the trapezoid
      * rule on the planes and the plate Nusselt numbers the derivative of the
-     * quadratic through three planes.  Stretched grids: 2D single contexts
-     * only (cm_init returns CM_EINVAL for 3D, cm_batch_init and cm_adj_* for
-     * any stretched grid). */
+     * quadratic through three planes.  Stretched grids: single contexts, 2D
+     * and 3D (cm_batch_init, cm_adj_* and cm_diag_noalloc return CM_EINVAL
+     * for a stretched grid). */
     double zstretch;
     const double* znodes;
 } cm_grid;

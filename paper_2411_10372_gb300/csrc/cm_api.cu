@@ -426,7 +426,6 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     const char* why = "";
     if (!make_planes(*grid, planes, &why)) return fail(CM_EINVAL, "%s", why);
     const bool st = stretched(*grid);
-    if (st && grid->ndim == 3) return fail(CM_EINVAL, "stretched z-grids are implemented for 2D contexts only");
 
     if (g_ctx) { free_ctx(g_ctx); g_ctx = nullptr; }
     Ctx* c = new Ctx();

@@ -150,10 +150,15 @@ static cudaError_t sweep3(int dir, const R* in, R* out, const R* zt, const Coef<
                  ? seg_rows
                  : pick_segment3((long long)io.nstrips * groups, io.nmarch, bps[dir], sm_count());
     const int nsegs = (io.nmarch + io.seg - 1) / io.seg;
-    const dim3 grid(io.nstrips, groups, nsegs);
-    if (dir == 2) return launch_pdl(false, sweep3d_march<R, 2, kNW3>, grid, dim3(kNW3 * 32), 0, s, io, C, sc);
-    if (dir == 1) return launch_pdl(false, sweep3d_march<R, 1, kNW3>, grid, dim3(kNW3 * 32), 0, s, io, C, sc);
-    return launch_pdl(false, sweep3d_x<R, kNW3>, grid, dim3(kNW3 * 32), 0, s, io, C, sc);
+    const dim3 grid(io.nstrips, groups, nsegs), b(kNW3 * 32);
+    if (C.zp) {  // stretched z-grid
+        if (dir == 2) return launch_pdl(false, sweep3d_march<R, 2, kNW3, true>, grid, b, 0, s, io, C, sc);
+        if (dir == 1) return launch_pdl(false, sweep3d_march<R, 1, kNW3, true>, grid, b, 0, s, io, C, sc);
+        return launch_pdl(false, sweep3d_x<R, kNW3, true>, grid, b, 0, s, io, C, sc);
+    }
+    if (dir == 2) return launch_pdl(false, sweep3d_march<R, 2, kNW3>, grid, b, 0, s, io, C, sc);
+    if (dir == 1) return launch_pdl(false, sweep3d_march<R, 1, kNW3>, grid, b, 0, s, io, C, sc);
+    return launch_pdl(false, sweep3d_x<R, kNW3>, grid, b, 0, s, io, C, sc);
 }
 
 template <class R>

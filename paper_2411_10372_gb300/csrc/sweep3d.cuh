@@ -52,13 +52,18 @@ __device__ __forceinline__ int halo_role(int w)
     return (w == 0 || w == NW - 1) ? 0 : ((w == 1 || w == NW - 2) ? 1 : 2);
 }
 
-// L_z (AL = 2: march z, W = y) or L_y (AL = 1: march y, W = z).
+// L_z (AL = 2: march z, W = y) or L_y (AL = 1: march y, W = z).  ST: a
+// stretched z-grid (C.zp): for L_z the flux differences of plane k divide by
+// its cell width, the one-sided derivatives by the spacing they span and the
+// TVD fluxes are weighted by spacing over width (as in the 2D z sweep); for
+// L_y the central z-differences across W divide by the distance of the two
+// planes next to the warp's plane.
 // Row pipeline at step j (row j of the march just taken from the prefetch),
 // as in sweep_z2d: F^n_{j-1}, X^P_{j-1}, F^P_{j-1}, average at j-2, TVD flux
 // across (j-2, j-1), output row j-2.  Plates: for L_z at the ends of the
 // march (half-cell density, m = 0, T = T_w); for L_y the plate planes are
 // rows of W and pass through unchanged.
-template <class R, int AL, int NW>
+template <class R, int AL, int NW, bool ST = false>
 __global__ void __launch_bounds__(NW * 32)
 sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 {
@@ -92,6 +97,18 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
     const R lam = (R)(Delta / ((AL == 2) ? C.dz : C.dy));
     const R Dl = (R)Delta;
     const R lam2 = R(2) * lam;
+    // stretched grid: plate half cells (L_z) and the warp plane's central z span (L_y)
+    R lam_bot = lam2, lam_top = lam2, wsc = C.h2z, iwsc = C.inv_2dz;
+    if constexpr (ST) {
+        if (AL == 2) {
+            lam_bot = lam_cell(Delta, C.zp[0]);
+            lam_top = lam_cell(Delta, C.zp[nz - 1]);
+        } else {
+            const Plane<R>& Pw = C.zp[cwr];
+            wsc = Pw.sc;
+            iwsc = Pw.isc;
+        }
+    }
     if (sc.first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
         sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
         sc.ctl->t += dt;
@@ -140,6 +157,15 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 
         // row m = j-1: F^n (forward along the march), X^P and its primitives
         const int m = j - 1;
+        // spacings along the march (stretched L_z: per plane) and the cell factor of row m
+        R hf = h, ihf = (AL == 2) ? C.inv_dz : C.inv_dy, hb = hf, ihb = ihf, lam_m = lam;
+        if constexpr (ST && AL == 2) {
+            const Plane<R>& Pm = C.zp[min(max(m, 0), nz - 1)];
+            const Plane<R>& Pb = C.zp[min(max(m - 1, 0), nz - 1)];
+            hf = Pm.hp; ihf = Pm.ihp;
+            hb = Pb.hp; ihb = Pb.ihp;
+            lam_m = lam_cell(Delta, Pm);
+        }
         S3<R> F1 = zero, XP1 = Xm1;
         R ppu1[3] = {u1[0], u1[1], u1[2]}, ppT1 = T1, ppp1 = p1;
         if (role >= 1) {
@@ -148,21 +174,21 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
             dxua0 = d3(shdn(u0[AL]), shup(u0[AL]), C, 0, true);
             R du[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) du[c][AL] = d3(u0[c], u1[c], C, AL, false);
+            for (int c = 0; c < 3; ++c) du[c][AL] = diff(u0[c], u1[c], hf, ihf);
             du[0][0] = dxux1;
             du[AL][0] = dxua1;
             du[WD][WD] = dwuw1;
             du[AL][WD] = dwua1;
-            F1 = flux3<AL>(Xm1, u1, p1, du, d3(T0, T1, C, AL, false), C);
+            F1 = flux3<AL>(Xm1, u1, p1, du, diff(T0, T1, hf, ihf), C);
             if (AL == 2) {
                 if (m >= 1 && m <= nz - 2) {
-                    XP1.r = Xm1.r - lam * (F1.r - F2.r);
-                    XP1.m[0] = Xm1.m[0] - lam * (F1.m[0] - F2.m[0]);
-                    XP1.m[1] = Xm1.m[1] - lam * (F1.m[1] - F2.m[1]);
-                    XP1.m[2] = (Xm1.m[2] - lam * (F1.m[2] - F2.m[2])) + Dl * (-C.g * Xm1.r);
-                    XP1.E = Xm1.E - lam * (F1.E - F2.E);
+                    XP1.r = Xm1.r - lam_m * (F1.r - F2.r);
+                    XP1.m[0] = Xm1.m[0] - lam_m * (F1.m[0] - F2.m[0]);
+                    XP1.m[1] = Xm1.m[1] - lam_m * (F1.m[1] - F2.m[1]);
+                    XP1.m[2] = (Xm1.m[2] - lam_m * (F1.m[2] - F2.m[2])) + Dl * (-C.g * Xm1.r);
+                    XP1.E = Xm1.E - lam_m * (F1.E - F2.E);
                 } else {
-                    XP1.r = (m <= 0) ? Xm1.r - lam2 * F1.r : Xm1.r + lam2 * F2.r;
+                    XP1.r = (m <= 0) ? Xm1.r - lam_bot * F1.r : Xm1.r + lam_top * F2.r;
                     XP1.m[0] = XP1.m[1] = XP1.m[2] = R(0);
                     XP1.E = XP1.r * ((m <= 0) ? C.ebot : C.etop);
                 }
@@ -183,35 +209,46 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
         buf[3][w][lane] = ppu1[WD];
         __syncthreads();
         const int wu = min(w + 1, NW - 1), wd = max(w - 1, 0);
-        const R dwua0 = d3(buf[0][wu][lane], buf[0][wd][lane], C, WD, true);
-        const R dwuw0 = d3(buf[1][wu][lane], buf[1][wd][lane], C, WD, true);
+        // central differences across W (W = z for L_y: the warp plane's span)
+        auto dw = [&](R a, R b) { return (WD == 2) ? diff(a, b, wsc, iwsc) : d3(a, b, C, WD, true); };
+        const R dwua0 = dw(buf[0][wu][lane], buf[0][wd][lane]);
+        const R dwuw0 = dw(buf[1][wu][lane], buf[1][wd][lane]);
 
         S3<R> FP1 = zero, Dn = zero, d0 = zero;
         R dd0 = R(0), ss1 = R(0);
         if (role == 2) {
-            const R dwppa1 = d3(buf[2][wu][lane], buf[2][wd][lane], C, WD, true);
-            const R dwppw1 = d3(buf[3][wu][lane], buf[3][wd][lane], C, WD, true);
+            const R dwppa1 = dw(buf[2][wu][lane], buf[2][wd][lane]);
+            const R dwppw1 = dw(buf[3][wu][lane], buf[3][wd][lane]);
             R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dq[c][AL] = d3(ppu1[c], ppu2[c], C, AL, false);
+            for (int c = 0; c < 3; ++c) dq[c][AL] = diff(ppu1[c], ppu2[c], hb, ihb);
             dq[0][0] = d3(shdn(ppu1[0]), shup(ppu1[0]), C, 0, true);
             dq[AL][0] = d3(shdn(ppu1[AL]), shup(ppu1[AL]), C, 0, true);
             dq[WD][WD] = dwppw1;
             dq[AL][WD] = dwppa1;
-            FP1 = flux3<AL>(XP1, ppu1, ppp1, dq, d3(ppT1, ppT2, C, AL, false), C);
+            FP1 = flux3<AL>(XP1, ppu1, ppp1, dq, diff(ppT1, ppT2, hb, ihb), C);
 
             // row c = j-2: corrector X^C and the average (X^P + X^C)/2
             const int c = j - 2;
+            R lam_c = lam, hc = h, lamh_c = lam, rp_c = R(1), rm_c = R(1);
+            if constexpr (ST && AL == 2) {
+                const Plane<R>& Pc = C.zp[min(max(c, 0), nz - 1)];
+                lam_c = lam_cell(Delta, Pc);
+                hc = Pc.hp;
+                lamh_c = (R)Delta * Pc.ihp;
+                rp_c = Pc.rp;
+                rm_c = Pc.rm;
+            }
             S3<R> Xa = Xm2;
             if (AL == 2) {
                 if (c >= 1 && c <= nz - 2) {
-                    Xa.r = (XP2.r + (Xm2.r - lam * (FP1.r - FP2.r))) * R(0.5);
-                    Xa.m[0] = (XP2.m[0] + (Xm2.m[0] - lam * (FP1.m[0] - FP2.m[0]))) * R(0.5);
-                    Xa.m[1] = (XP2.m[1] + (Xm2.m[1] - lam * (FP1.m[1] - FP2.m[1]))) * R(0.5);
-                    Xa.m[2] = (XP2.m[2] + ((Xm2.m[2] - lam * (FP1.m[2] - FP2.m[2])) + Dl * (-C.g * XP2.r))) * R(0.5);
-                    Xa.E = (XP2.E + (Xm2.E - lam * (FP1.E - FP2.E))) * R(0.5);
+                    Xa.r = (XP2.r + (Xm2.r - lam_c * (FP1.r - FP2.r))) * R(0.5);
+                    Xa.m[0] = (XP2.m[0] + (Xm2.m[0] - lam_c * (FP1.m[0] - FP2.m[0]))) * R(0.5);
+                    Xa.m[1] = (XP2.m[1] + (Xm2.m[1] - lam_c * (FP1.m[1] - FP2.m[1]))) * R(0.5);
+                    Xa.m[2] = (XP2.m[2] + ((Xm2.m[2] - lam_c * (FP1.m[2] - FP2.m[2])) + Dl * (-C.g * XP2.r))) * R(0.5);
+                    Xa.E = (XP2.E + (Xm2.E - lam_c * (FP1.E - FP2.E))) * R(0.5);
                 } else {
-                    Xa.r = (c <= 0) ? (XP2.r + (Xm2.r - lam2 * FP1.r)) * R(0.5) : (XP2.r + Xm2.r) * R(0.5);
+                    Xa.r = (c <= 0) ? (XP2.r + (Xm2.r - lam_bot * FP1.r)) * R(0.5) : (XP2.r + Xm2.r) * R(0.5);
                 }
             } else if (!passthru) {
                 Xa.r = (XP2.r + (Xm2.r - lam * (FP1.r - FP2.r))) * R(0.5);
@@ -227,7 +264,7 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
             ss1 = s3_dot(d1, d0);
             const bool tvd_on = (AL == 2) ? (c >= 1 && c <= nz - 3) : !passthru;
             if (tvd_on) {
-                const R G = tvd_G(ss2, ss1, dd1, courant(Delta, lam, A2, A1, h), C.tvd_form);
+                const R G = tvd_G(ss2, ss1, dd1, courant(Delta, lamh_c, A2, A1, hc), C.tvd_form);
                 Dn = {G * d1.r, {G * d1.m[0], G * d1.m[1], G * d1.m[2]}, G * d1.E};
             }
 
@@ -235,10 +272,17 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
                 S3<R> Xn = Xa;
                 const bool interior = (AL == 2) ? (c >= 1 && c <= nz - 2) : !passthru;
                 if (interior) {
-                    Xn.r = Xa.r + (Dn.r - Dm.r);
+                    if constexpr (ST && AL == 2) {
+                        Xn.r = Xa.r + (rp_c * Dn.r - rm_c * Dm.r);
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (Dn.m[q] - Dm.m[q]);
-                    Xn.E = Xa.E + (Dn.E - Dm.E);
+                        for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (rp_c * Dn.m[q] - rm_c * Dm.m[q]);
+                        Xn.E = Xa.E + (rp_c * Dn.E - rm_c * Dm.E);
+                    } else {
+                        Xn.r = Xa.r + (Dn.r - Dm.r);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) Xn.m[q] = Xa.m[q] + (Dn.m[q] - Dm.m[q]);
+                        Xn.E = Xa.E + (Dn.E - Dm.E);
+                    }
                 } else if (AL == 2) {
                     Xn.m[0] = Xn.m[1] = Xn.m[2] = R(0);
                     Xn.E = Xa.r * (c == 0 ? C.ebot : C.etop);
@@ -274,8 +318,10 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 // iteration earlier), then F^P (d/dz of X^P from rows j-1, j-3; d/dy from
 // the exchange of row j-2), corrector, average and TVD along x of row j-2,
 // output row j-2.  One exchange per row carries u_x, u_y of X at row j and
-// of X^P at row j-1, both read in the next iteration.
-template <class R, int NW>
+// of X^P at row j-1, both read in the next iteration.  ST: stretched z-grid:
+// central z-differences over the distance of the two planes next to the
+// row, CFL z step the row plane's smaller spacing.
+template <class R, int NW, bool ST = false>
 __global__ void __launch_bounds__(NW * 32)
 sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 {
@@ -334,6 +380,11 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 
         // row m = j-1: F^n with forward x-differences, X^P and its primitives
         const int m = j - 1;
+        R scm = C.h2z, iscm = C.inv_2dz;  // central z span at row m
+        if constexpr (ST) {
+            const Plane<R>& Pm = C.zp[min(max(m, 0), nz - 1)];
+            scm = Pm.sc; iscm = Pm.isc;
+        }
         S3<R> XP1 = Xm1;
         R pp1[3] = {u1[0], u1[1], u1[2]}, ppT1 = T1, ppp1 = p1;
         if (role >= 1) {
@@ -342,8 +393,8 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
             for (int c = 0; c < 3; ++c) du[c][0] = d3(shdn(u1[c]), u1[c], C, 0, false);
             du[0][1] = dwx1;
             du[1][1] = dwy1;
-            du[0][2] = d3(u0[0], u2[0], C, 2, true);
-            du[2][2] = d3(u0[2], u2[2], C, 2, true);
+            du[0][2] = diff(u0[0], u2[0], scm, iscm);
+            du[2][2] = diff(u0[2], u2[2], scm, iscm);
             const S3<R> F1 = flux3<0>(Xm1, u1, p1, du, d3(shdn(T1), T1, C, 0, false), C);
             const S3<R> Fl = {shup(F1.r), {shup(F1.m[0]), shup(F1.m[1]), shup(F1.m[2])}, shup(F1.E)};
             if (m >= 1 && m <= nz - 2) {
@@ -371,13 +422,19 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
         if (role == 2) {
             // row c = j-2: F^P with backward x-differences, corrector, average, TVD along x
             const int c = j - 2;
+            R scc = C.h2z, iscc = C.inv_2dz, hzc = C.hz, ihzc = C.inv_dz;
+            if constexpr (ST) {
+                const Plane<R>& Pc = C.zp[min(max(c, 0), nz - 1)];
+                scc = Pc.sc; iscc = Pc.isc;
+                hzc = Pc.hmin; ihzc = Pc.ihmin;
+            }
             R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
 #pragma unroll
             for (int q = 0; q < 3; ++q) dq[q][0] = d3(pp2[q], shup(pp2[q]), C, 0, false);
             dq[0][1] = dwpx2;
             dq[1][1] = dwpy2;
-            dq[0][2] = d3(pp1[0], pp3[0], C, 2, true);
-            dq[2][2] = d3(pp1[2], pp3[2], C, 2, true);
+            dq[0][2] = diff(pp1[0], pp3[0], scc, iscc);
+            dq[2][2] = diff(pp1[2], pp3[2], scc, iscc);
             const S3<R> FP = flux3<0>(XP2, pp2, ppp2, dq, d3(ppT2, shup(ppT2), C, 0, false), C);
             const S3<R> FPr = {shdn(FP.r), {shdn(FP.m[0]), shdn(FP.m[1]), shdn(FP.m[2])}, shdn(FP.E)};
             S3<R> Xa;
@@ -412,13 +469,13 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
                         const double cs = sqrt(C.cs2 * Tn);
                         double v = C.dx / (fabs(un[0]) + cs);
                         v = fmin(v, C.dy / (fabs(un[1]) + cs));
-                        v = fmin(v, C.dz / (fabs(un[2]) + cs));
+                        v = fmin(v, (ST ? (double)hzc : C.dz) / (fabs(un[2]) + cs));
                         if (!(v > 0.0) || !(v < 1e300)) bad = 1;
                         vmin = fmin(vmin, v);
                     } else {
                         const R cs = rsqrt_(C.cs2 * Tn);
                         const R r = fmax(fmax((fabs(un[0]) + cs) * C.inv_dx, (fabs(un[1]) + cs) * C.inv_dy),
-                                         (fabs(un[2]) + cs) * C.inv_dz);
+                                         (fabs(un[2]) + cs) * ihzc);
                         if (!(r > R(0)) || !(r < R(1e30))) bad = 1;
                         rmax = fmax(rmax, r);
                     }

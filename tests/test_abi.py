@@ -91,8 +91,7 @@ def test_argument_errors_need_no_gpu():
 def test_stretched_grid_argument_errors_need_no_gpu():
     """The z-grid is validated before any device work: planes must run from
     exactly 0 to exactly 1 and increase; beta must be in [0, 20]; stretched
-    grids are 2D single contexts only (3D, batch and the no-alloc
-    diagnostics reject them)."""
+    grids are single contexts only (the batch rejects them)."""
     import numpy as np
     bad = [np.linspace(0, 1, 16) * 0.99, np.r_[0.0, 0.5, 0.3, np.linspace(0.6, 1, 13)],
            np.r_[1e-9, np.linspace(0.1, 1, 15)], np.r_[0.0, np.nan, np.linspace(0.2, 1, 14)]]
@@ -105,9 +104,6 @@ def test_stretched_grid_argument_errors_need_no_gpu():
         with pytest.raises(cm.CMError) as e:
             cm.cm_init(cm.cm_grid(2, 64, 1, 16, 4.0, beta), 1e6, 1.0, 5 / 3)
         assert e.value.code == cm.CM_EINVAL, beta
-    with pytest.raises(cm.CMError) as e:
-        cm.cm_init(cm.cm_grid(3, 16, 16, 16, 4.0, 2.0), 1e6, 1.0, 5 / 3)
-    assert e.value.code == cm.CM_EINVAL and "2D" in cm.cm_last_error()
     with pytest.raises(cm.CMError) as e:
         cm.cm_batch_init([cm.cm_grid(2, 64, 1, 16, 4.0, 1.5)], [1e6], 1.0, 5 / 3)
     assert e.value.code == cm.CM_EINVAL

@@ -205,3 +205,128 @@ def test_full_size_one_step_fp64_and_fp32():
         mass_tol = 1e-14 if precision == "fp64" else 1e-6
         assert abs(np.trapezoid(got[0].mean(axis=1), z) - m0) <= mass_tol * m0, precision
         s.close()
+
+
+# ---- 3D on stretched planes ----
+
+def stirred_3d_on(cfg, z, seed, u_amp=0.3, t_amp=0.05):
+    """3D conduction profile on the planes z with random temperature, density
+    and velocity fields (velocity zero on the plates)."""
+    from physics import state_from_prims
+    rng = np.random.default_rng(seed)
+    T_c, p_c, _ = O.profile(cfg)
+    shp = (cfg.nz, cfg.ny, cfg.nx)
+    Z = np.broadcast_to(np.asarray(z)[:, None, None], shp)
+    T = T_c[:, None, None] * (1 + t_amp * rng.uniform(-1, 1, shp))
+    u = [u_amp * rng.uniform(-1, 1, shp) for _ in range(3)]
+    for f in u:
+        f[0] = f[-1] = 0.0
+    T[0], T[-1] = cfg.t_bot, 1.0 - cfg.eps - cfg.D
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    rho = p_c[:, None, None] / (cl["a"] * T) * (1 + 0.02 * rng.uniform(-1, 1, shp))
+    return state_from_prims(cfg, rho, u[0], u[2], T, Z, uy=u[1])
+
+
+def solver3_for(cfg, precision="fp64", **extra):
+    import paper_2411_10372_gb300 as cm
+    return cm.Solver(cfg.nx, cfg.nz, cfg.Ra, cfg.Pr, cfg.gamma, ny=cfg.ny, ndim=3, aspect=cfg.aspect,
+                     precision=precision, eps=cfg.eps, D=cfg.D, cfl=cfg.cfl, dt_fixed=cfg.dt_fixed,
+                     t_top=1.0 - cfg.eps - cfg.D, pert_amp=cfg.pert_amp, seed=cfg.seed, tvd_form=cfg.tvd_form,
+                     zstretch=cfg.zstretch, znodes=cfg.znodes, **extra)
+
+
+def check3(cfg, got, want, tol):
+    for f in (0, 4):
+        assert rel_l2(got[f], want[f]) <= tol, (f, rel_l2(got[f], want[f]))
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    scale = np.linalg.norm(want[0]) * math.sqrt(cfg.gamma * cl["a"])
+    for f in (1, 2, 3):
+        assert np.linalg.norm(got[f] - want[f]) / scale <= tol, f
+
+
+SHAPES3 = [(8, 4, 9), (29, 13, 17), (36, 20, 13)]
+
+
+def cfg3_for(nx, ny, nz, grid, **kw):
+    if grid == "random":
+        return O.Config(nx=nx, ny=ny, nz=nz, ndim=3, znodes=random_planes(nz, seed=nx + ny + nz), **kw)
+    return O.Config(nx=nx, ny=ny, nz=nz, ndim=3, **grid, **kw)
+
+
+@pytest.mark.parametrize("nx,ny,nz", SHAPES3)
+@pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
+def test_single_sweeps_3d(nx, ny, nz, name, grid):
+    """L_z, L_y, L_x on a stirred 3D state on stretched planes: FP64 <= 1e-13,
+    FP32 (same state rounded) <= 2e-6."""
+    cfg = cfg3_for(nx, ny, nz, grid, Ra=1e5, dt_fixed=1e-5)
+    z = O.znodes(cfg)
+    X = stirred_3d_on(cfg, z, seed=nx * 100 + ny + nz)
+    for precision, tol in (("fp64", 1e-13), ("fp32", 2e-6)):
+        Xp = X if precision == "fp64" else X.astype(np.float32).astype(np.float64)
+        s = solver3_for(cfg, precision)
+        try:
+            for direction in (2, 1, 0):
+                Delta = 0.2 * min(cfg.aspect / nx, cfg.aspect / ny, float(np.min(np.diff(z)))) / 4.0
+                s.set_state(Xp)
+                s.sweep(direction, Delta)
+                check3(cfg, s.state(), O.sweep(cfg, Xp, direction, Delta), tol)
+        finally:
+            s.close()
+
+
+@pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
+def test_steps_3d(name, grid):
+    """30 full 3D steps from the seeded initial state on stretched planes:
+    FP64 <= 1e-12 with time and mass; FP32 <= 1e-5."""
+    cfg = cfg3_for(36, 20, 17, grid, Ra=1e6, pert_amp=0.02)
+    X0 = O.init(cfg)
+    want, t_cpu, _ = O.step(cfg, X0, 30)
+    z = O.znodes(cfg)
+    for precision, tol in (("fp64", 1e-12), ("fp32", 1e-5)):
+        s = solver3_for(cfg, precision)
+        try:
+            s.step(30)
+            t_gpu, steps = s.time()
+            got = s.state()
+            assert steps == 30 and abs(t_gpu - t_cpu) <= (1e-13 if precision == "fp64" else 1e-6) * t_cpu
+            check3(cfg, got, want, tol)
+            if precision == "fp64":
+                m0 = np.trapezoid(X0[0].mean(axis=(1, 2)), z)
+                assert abs(np.trapezoid(got[0].mean(axis=(1, 2)), z) - m0) <= 1e-13 * m0
+                d = s.sample()
+                dw = O.diag(cfg, got)
+                for key in ("Nu", "Nu_bar", "Re", "KE", "mass", "energy"):
+                    assert abs(d[key] - dw[key]) <= 1e-10 * max(abs(dw[key]), 1e-6), key
+        finally:
+            s.close()
+
+
+def test_full_size_3d_fp32_y_invariant_matches_2d_oracle():
+    """The 512 x 512 x 128 FP32 box on the tanh grid (beta = 2) in the launch
+    configuration the benchmark times, on y-independent data: 3 steps, y
+    planes against the 2D stretched oracle (FP32 bar), every y plane equal,
+    m_y exactly zero, trapezoid mass on the planes kept."""
+    import paper_2411_10372_gb300 as cm
+    nx, ny, nz = 512, 512, 128
+    c2 = O.Config(nx=nx, nz=nz, Ra=1e7, seed=31, pert_amp=1e-2, zstretch=2.0)
+    X2 = O.init(c2).astype(np.float32).astype(np.float64)
+    X3 = np.zeros((5, nz, ny, nx))
+    for f, g in ((0, 0), (1, 1), (3, 2), (4, 3)):
+        X3[f] = X2[g][:, None, :]
+    s = cm.Solver(nx, nz, 1e7, 1.0, 5.0 / 3.0, ny=ny, ndim=3, precision="fp32", pert_amp=1e-2, seed=31,
+                  zstretch=2.0)
+    try:
+        s.set_state(X3)
+        s.step(3)
+        got = s.state()
+    finally:
+        s.close()
+    want, _, _ = O.step(c2, X2, 3)
+    assert np.all(got[2] == 0)
+    assert np.max(np.abs(got - got[:, :, :1, :])) == 0.0
+    c3 = O.Config(nx=nx, ny=1, nz=nz, ndim=3, Ra=1e7)
+    w3 = np.stack([want[0], want[1], np.zeros_like(want[0]), want[2], want[3]])[:, :, None, :]
+    check3(c3, got[:, :, :1, :], w3, 1e-5)
+    z = O.znodes(c2)
+    m0 = np.trapezoid(X3[0].mean(axis=(1, 2)), z)
+    assert abs(np.trapezoid(got[0].mean(axis=(1, 2)), z) - m0) <= 1e-6 * m0
