@@ -22,6 +22,11 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                      gravity, exact trapezoid / plate-derivative rules, second-
                      order self-convergence on nested tanh grids
   advect1d ......... total-variation test of the TVD reading
+  ext_profiles /
+  extended ......... closed forms of the force terms on polynomial and
+                     trigonometric fields (uniform and stretched planes), C of
+                     trigonometric fields, boundary layers of a built profile,
+                     exact histogram counts
   torch_ref.py ..... PyTorch restatement of the 2D step for autograd (the
                      adjoint's reference): equal to this oracle state by
                      state and in Nu_bar; its gradient equals central
@@ -154,6 +159,9 @@ def lib(path: str | None = None):
         L.orc_init.argtypes = [cp, dp]
         L.orc_profile.argtypes = [cp, dp, dp, dp]
         L.orc_znodes.argtypes = [cp, dp]
+        L.orc_ext_profiles.argtypes = [cp, dp, dp]
+        L.orc_extended.argtypes = [cp, dp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_double,
+                                   ctypes.c_double]
         L.orc_sweep.argtypes = [cp, ctypes.c_int, ctypes.c_double, dp]
         L.orc_dt.argtypes = [cp, dp]
         L.orc_dt.restype = ctypes.c_double
@@ -230,6 +238,31 @@ def diag(cfg: Config, X: np.ndarray) -> dict:
     c = cfg.c()
     lib().orc_diag(ctypes.byref(c), _ptr(Xc), _ptr(out))
     return dict(zip(DIAG_KEYS, out.tolist()))
+
+
+EXT_PROFILE_KEYS = ("F_n", "F_p", "F_b", "F_v", "rho_uz_sq", "Tsa_sq")
+EXT_KEYS = ("C", "rho_uz_sq", "Tsa_sq", "lambda_b", "lambda_t", "F_n", "F_p", "F_b", "F_v", "r_max")
+
+
+def ext_profiles(cfg: Config, X: np.ndarray) -> dict:
+    """Plane means of the z-momentum terms and of (rho u_z)^2, T_sa^2 (name -> nz values)."""
+    Xc = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros((cfg.nz, 6))
+    c = cfg.c()
+    lib().orc_ext_profiles(ctypes.byref(c), _ptr(Xc), _ptr(out))
+    return {k: out[:, q].copy() for q, k in enumerate(EXT_PROFILE_KEYS)}
+
+
+def extended(cfg: Config, X: np.ndarray, nbins: int = 64, lo: float = -16.0, hi: float = 0.0):
+    """(dict of C, boundary-layer thicknesses, volume-averaged forces, r_max;
+    histogram of log10 K_e/I_e)."""
+    Xc = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros(len(EXT_KEYS))
+    hist = np.zeros(nbins, dtype=np.int64)
+    c = cfg.c()
+    lib().orc_extended(ctypes.byref(c), _ptr(Xc), _ptr(out), hist.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                       int(nbins), float(lo), float(hi))
+    return dict(zip(EXT_KEYS, out.tolist())), hist
 
 
 def advect1d(u0: np.ndarray, a: float, dt: float, h: float, nsteps: int, tvd_form: int) -> np.ndarray:

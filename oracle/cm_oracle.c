@@ -847,3 +847,165 @@ void orc_advect1d(int n, double a, double dt, double h, int nsteps, int tvd_form
     }
     free(F); free(uP); free(FP); free(y); free(D);
 }
+
+/* ---- extended diagnostics (the analyses of Sec. 4-6) ----
+ *
+ * z derivatives at an interior plane k use the three planes k-1, k, k+1
+ * (spacings hm below, hp above): the derivative and second derivative of
+ * the quadratic through them (exact for quadratics on any planes; the
+ * central differences on uniform planes).  x and y derivatives are central
+ * (periodic). */
+static double dz3(const P* p, int k, double fm, double f0, double fp)
+{
+    double hm = p->z[k] - p->z[k - 1], hp = p->z[k + 1] - p->z[k];
+    return (hm * hm * fp - hp * hp * fm + (hp * hp - hm * hm) * f0) / (hm * hp * (hm + hp));
+}
+
+static double dzz3(const P* p, int k, double fm, double f0, double fp)
+{
+    double hm = p->z[k] - p->z[k - 1], hp = p->z[k + 1] - p->z[k];
+    return 2.0 * ((fp - f0) / hp - (f0 - fm) / hm) / (hm + hp);
+}
+
+/* Plane means of the terms of the z-momentum equation and of the two
+ * squares in the correlation C(Ra):
+ *   out[k*6+0] <F_n>_A = <rho (u . grad) u_z>_A        (nonlinear term)
+ *   out[k*6+1] <F_p>_A = <-dp/dz>_A                   (pressure gradient)
+ *   out[k*6+2] <F_b>_A = <rho g>_A                    (buoyancy, g = gravity/eps)
+ *   out[k*6+3] <F_v>_A = <d_i tau_iz>_A               (viscous force)
+ *   out[k*6+4] <(rho u_z)^2>_A,  out[k*6+5] <T_sa^2>_A, T_sa = T - (1 - D z)
+ * The force terms need neighbouring planes: on the plates they are 0.
+ * d_i tau_iz = mu (d_xx u_z + d_yy u_z + (2 + s) d_zz u_z + (1 + s)(d_x d_z u_x + d_y d_z u_y)),
+ * s the Stokes coefficient (tau_ij = mu (d_j u_i + d_i u_j + s (div u) delta_ij)). */
+void orc_ext_profiles(const orc_cfg* c, const double* ext, double* out)
+{
+    P p;
+    derive(c, &p);
+    size_t N = p.n;
+    double* X = malloc(5 * N * sizeof(double));
+    double *U = malloc(3 * N * sizeof(double)), *T = malloc(N * sizeof(double)), *Pr = malloc(N * sizeof(double));
+    to_internal(&p, ext, X);
+    prims(&p, X, U, T, Pr);
+    double cells = (double)p.nx * p.ny;
+    int K = p.nz - 1;
+    for (int k = 0; k < p.nz; k++) {
+        double s[6] = {0, 0, 0, 0, 0, 0};
+        double z = zk(&p, k);
+        for (int j = 0; j < p.ny; j++)
+            for (int i = 0; i < p.nx; i++) {
+                size_t n = idx(&p, i, j, k);
+                double rho = X[n];
+                double ux = U[n], uy = U[N + n], uz = U[2 * N + n];
+                double Tsa = T[n] - (1.0 - p.D * z);
+                s[4] += (rho * uz) * (rho * uz);
+                s[5] += Tsa * Tsa;
+                if (k == 0 || k == K) continue;
+                size_t xp = nbr(&p, i, j, k, 0, +1), xm = nbr(&p, i, j, k, 0, -1);
+                size_t yp = nbr(&p, i, j, k, 1, +1), ym = nbr(&p, i, j, k, 1, -1);
+                size_t zp = idx(&p, i, j, k + 1), zm = idx(&p, i, j, k - 1);
+                double dx = p.h[0], dy = p.h[1];
+                double dxuz = (U[2 * N + xp] - U[2 * N + xm]) / (2.0 * dx);
+                double dyuz = (U[2 * N + yp] - U[2 * N + ym]) / (2.0 * dy);
+                double dzuz = dz3(&p, k, U[2 * N + zm], uz, U[2 * N + zp]);
+                s[0] += rho * ((ux * dxuz + uy * dyuz) + uz * dzuz);
+                s[1] += -dz3(&p, k, Pr[zm], Pr[n], Pr[zp]);
+                s[2] += rho * p.g;
+                double dxx = (U[2 * N + xp] - 2.0 * uz + U[2 * N + xm]) / (dx * dx);
+                double dyy = (U[2 * N + yp] - 2.0 * uz + U[2 * N + ym]) / (dy * dy);
+                double dzz = dzz3(&p, k, U[2 * N + zm], uz, U[2 * N + zp]);
+                /* d_x d_z u_x: x-central of the z-derivative on the planes */
+                size_t xpzp = idx(&p, (i + 1) % p.nx, j, k + 1), xmzp = idx(&p, (i - 1 + p.nx) % p.nx, j, k + 1);
+                size_t xpzm = idx(&p, (i + 1) % p.nx, j, k - 1), xmzm = idx(&p, (i - 1 + p.nx) % p.nx, j, k - 1);
+                double dxdzux = (dz3(&p, k, U[xpzm], U[xp], U[xpzp]) - dz3(&p, k, U[xmzm], U[xm], U[xmzp])) / (2.0 * dx);
+                double dydzuy = 0.0;
+                if (p.ndim == 3) {
+                    size_t ypzp = idx(&p, i, (j + 1) % p.ny, k + 1), ymzp = idx(&p, i, (j - 1 + p.ny) % p.ny, k + 1);
+                    size_t ypzm = idx(&p, i, (j + 1) % p.ny, k - 1), ymzm = idx(&p, i, (j - 1 + p.ny) % p.ny, k - 1);
+                    dydzuy = (dz3(&p, k, U[N + ypzm], U[N + yp], U[N + ypzp]) -
+                              dz3(&p, k, U[N + ymzm], U[N + ym], U[N + ymzp])) / (2.0 * dy);
+                }
+                s[3] += p.mu * ((dxx + dyy) + (2.0 + p.stokes) * dzz + (1.0 + p.stokes) * (dxdzux + dydzuy));
+            }
+        for (int q = 0; q < 6; q++) out[(size_t)k * 6 + q] = s[q] / cells;
+    }
+    free(X); free(U); free(T); free(Pr);
+    release(&p);
+}
+
+/* Quantities derived from the plane means:
+ *   out[0] C = <rho u_z T_sa>_V / sqrt(<(rho u_z)^2>_V <T_sa^2>_V)   (Eq. Corr_Ra)
+ *   out[1] <(rho u_z)^2>_V, out[2] <T_sa^2>_V
+ *   out[3] lambda_b, out[4] lambda_t: thermal boundary-layer thicknesses.
+ *          Reading of "where the slope of <T>_A approximates the adiabatic
+ *          gradient -D": from the bottom plate up, lambda_b is the height z_k
+ *          of the first plane whose slope to the plane above,
+ *          (<T>_{k+1} - <T>_k)/(z_{k+1} - z_k), is no steeper than -D; from the
+ *          top plate down, lambda_t = 1 - z_k of the first plane whose slope
+ *          from the plane below is no steeper than -D; 1 if there is none.
+ *   out[5..8] <F_n>, <F_p>, <F_b>, <F_v> over the interior planes (weights
+ *          w_k of the interior planes, normalised by their sum)
+ *   out[9] max over nodes of r = K_e / I_e = (rho u^2/2) / (rho C_v T) = b u^2 / (2 T)
+ * hist[q] (q < nbins): nodes with log10 r in [lo + q w, lo + (q+1) w),
+ *          w = (hi - lo)/nbins; below lo (or r = 0) in bin 0, at or above hi
+ *          in bin nbins - 1. */
+void orc_extended(const orc_cfg* c, const double* ext, double* out, long long* hist, int nbins, double lo, double hi)
+{
+    P p;
+    derive(c, &p);
+    size_t N = p.n;
+    int K = p.nz - 1;
+    double* prof = malloc((size_t)p.nz * 6 * sizeof(double));
+    orc_ext_profiles(c, ext, prof);
+    double* X = malloc(5 * N * sizeof(double));
+    double *U = malloc(3 * N * sizeof(double)), *T = malloc(N * sizeof(double)), *Pr = malloc(N * sizeof(double));
+    to_internal(&p, ext, X);
+    prims(&p, X, U, T, Pr);
+    double cells = (double)p.nx * p.ny;
+    double s_conv = 0, s_m2 = 0, s_t2 = 0, wsum = 0, f[4] = {0, 0, 0, 0};
+    double* TA = calloc(p.nz, sizeof(double));
+    for (int k = 0; k < p.nz; k++) {
+        double wgt = p.stretched ? p.w[k] : ((k == 0 || k == K) ? 0.5 : 1.0);
+        double z = zk(&p, k), conv = 0.0;
+        for (int j = 0; j < p.ny; j++)
+            for (int i = 0; i < p.nx; i++) {
+                size_t n = idx(&p, i, j, k);
+                conv += X[n] * U[2 * N + n] * (T[n] - (1.0 - p.D * z));
+                TA[k] += T[n];
+            }
+        s_conv += wgt * conv / cells;
+        s_m2 += wgt * prof[(size_t)k * 6 + 4];
+        s_t2 += wgt * prof[(size_t)k * 6 + 5];
+        TA[k] /= cells;
+        if (k > 0 && k < K) {
+            wsum += wgt;
+            for (int q = 0; q < 4; q++) f[q] += wgt * prof[(size_t)k * 6 + q];
+        }
+    }
+    double vol = p.stretched ? 1.0 : (double)(p.nz - 1);
+    out[1] = s_m2 / vol;
+    out[2] = s_t2 / vol;
+    out[0] = (s_conv / vol) / sqrt(out[1] * out[2]);
+    out[3] = 1.0;
+    for (int k = 0; k < K; k++)
+        if ((TA[k + 1] - TA[k]) / (p.z[k + 1] - p.z[k]) >= -p.D) { out[3] = p.z[k]; break; }
+    out[4] = 1.0;
+    for (int k = K; k > 0; k--)
+        if ((TA[k] - TA[k - 1]) / (p.z[k] - p.z[k - 1]) >= -p.D) { out[4] = 1.0 - p.z[k]; break; }
+    for (int q = 0; q < 4; q++) out[5 + q] = f[q] / wsum;
+    double rmax = 0.0, bw = (hi - lo) / nbins;
+    for (int q = 0; q < nbins; q++) hist[q] = 0;
+    for (size_t n = 0; n < N; n++) {
+        double u2 = U[n] * U[n] + U[N + n] * U[N + n] + U[2 * N + n] * U[2 * N + n];
+        double r = p.b * u2 / (2.0 * T[n]);
+        if (r > rmax) rmax = r;
+        int q = 0;
+        if (r > 0.0) {
+            double t = (log10(r) - lo) / bw;
+            q = t < 0.0 ? 0 : (t >= nbins ? nbins - 1 : (int)t);
+        }
+        hist[q]++;
+    }
+    out[9] = rmax;
+    free(prof); free(X); free(U); free(T); free(Pr); free(TA);
+    release(&p);
+}

@@ -78,6 +78,23 @@ MUTANTS = [
      "double wgt = (k == 0 || k == p.nz - 1) ? 0.5 : 1.0;"),
     ("stretched_plate_nu_coefficient", "-(2.0 * h1 + h2) / (h1 * (h1 + h2)) * f[0]", "-(2.0 * h1 + h2) / (h1 * (h1 + h1)) * f[0]"),
     ("stretched_plate_nu_top_spacing", "h2 = p.z[K - 1] - p.z[K - 2];", "h2 = p.z[K] - p.z[K - 1];"),
+    # extended diagnostics
+    ("ext_dz3_weights_swapped", "return (hm * hm * fp - hp * hp * fm + (hp * hp - hm * hm) * f0)",
+     "return (hp * hp * fp - hm * hm * fm + (hm * hm - hp * hp) * f0)"),
+    ("ext_dzz3_missing_factor", "return 2.0 * ((fp - f0) / hp - (f0 - fm) / hm) / (hm + hp);",
+     "return ((fp - f0) / hp - (f0 - fm) / hm) / (hm + hp);"),
+    ("ext_fn_missing_x_advection", "s[0] += rho * ((ux * dxuz + uy * dyuz) + uz * dzuz);",
+     "s[0] += rho * (uy * dyuz + uz * dzuz);"),
+    ("ext_fn_missing_y_advection", "s[0] += rho * ((ux * dxuz + uy * dyuz) + uz * dzuz);",
+     "s[0] += rho * (ux * dxuz + uz * dzuz);"),
+    ("ext_fp_sign", "s[1] += -dz3(&p, k, Pr[zm], Pr[n], Pr[zp]);", "s[1] += dz3(&p, k, Pr[zm], Pr[n], Pr[zp]);"),
+    ("ext_fv_stokes_factor", "(2.0 + p.stokes) * dzz", "(1.0 + p.stokes) * dzz"),
+    ("ext_correlation_no_sqrt", "out[0] = (s_conv / vol) / sqrt(out[1] * out[2]);",
+     "out[0] = (s_conv / vol) / (out[1] * out[2]);"),
+    ("ext_bl_threshold_sign", "if ((TA[k + 1] - TA[k]) / (p.z[k + 1] - p.z[k]) >= -p.D)",
+     "if ((TA[k + 1] - TA[k]) / (p.z[k + 1] - p.z[k]) >= p.D)"),
+    ("ext_bl_top_index", "out[4] = 1.0 - p.z[k]; break;", "out[4] = 1.0 - p.z[k - 1]; break;"),
+    ("ext_r_missing_half", "double r = p.b * u2 / (2.0 * T[n]);", "double r = p.b * u2 / T[n];"),
 ]
 
 

@@ -912,3 +912,117 @@ def test_stretched_3d_y_invariant_equals_2d_and_conserves_mass():
     Y, _, _ = O.step(c3, X, 8)
     assert np.all(np.isfinite(Y))
     assert abs(np.trapezoid(Y[0].mean(axis=(1, 2)), z) - m0) < 1e-13 * m0
+
+
+# ------------------------------------------------- extended diagnostics ----
+# Plane means of the z-momentum terms, C(Ra), boundary layers and the K_e/I_e
+# histogram (the analyses of Sec. 4-6), against closed forms.
+
+def _ext_fields(cfg, z, c0=0.3, U0=0.05, V0=0.04, q=0.02, rho0=0.9):
+    """G = z(1-z); u_z = G (c0 + cos kx [+ cos ky]); u_x = U0 G sin kx;
+    u_y = V0 G sin ky (3D); rho = rho0; T = 1 - D z + q G."""
+    k = 2 * np.pi / cfg.aspect
+    if cfg.ndim == 3:
+        Zg, Yg, Xg = np.meshgrid(z, np.arange(cfg.ny) * cfg.aspect / cfg.ny, np.arange(cfg.nx) * cfg.aspect / cfg.nx,
+                                 indexing="ij")
+    else:
+        Zg, Xg = np.meshgrid(z, np.arange(cfg.nx) * cfg.aspect / cfg.nx, indexing="ij")
+        Yg = None
+    G = Zg * (1 - Zg)
+    uz = G * (c0 + np.cos(k * Xg) + (np.cos(k * Yg) if Yg is not None else 0))
+    ux = U0 * G * np.sin(k * Xg)
+    uy = V0 * G * np.sin(k * Yg) if Yg is not None else None
+    T = 1 - cfg.D * Zg + q * G
+    return state_from_prims(cfg, rho0 + 0 * Zg, ux, uz, T, Zg, uy=uy)
+
+
+def test_ext_force_profiles_closed_forms():
+    """Eq. momentum along z, term by term: on quadratic-in-z fields the
+    three-plane z derivatives are exact on any planes and the central x (y)
+    differences of sin / cos are exact with the factor sigma = sin(k h)/h, so
+    the plane means at interior planes are, with G = z(1-z):
+      F_n = rho0 [G G' (c0^2 + m/2) - U0 G^2 sigma_x/2 - V0 G^2 sigma_y/2]  (m = 1 in 2D, 2 in 3D)
+      F_p = -a rho0 (-D + q G'),  F_b = rho0 g,  F_v = mu (2 + s) c0 G''
+      (rho u_z)^2 = rho0^2 G^2 (c0^2 + m/2),  T_sa^2 = q^2 G^2."""
+    c0, U0, V0, q, rho0 = 0.3, 0.05, 0.04, 0.02, 0.9
+    cases = [O.Config(nx=16, nz=13, Ra=1e4), O.Config(nx=16, nz=13, Ra=1e4, zstretch=2.0),
+             O.Config(nx=16, nz=13, Ra=1e4, znodes=random_planes(13, 77)),
+             O.Config(nx=12, ny=10, nz=9, ndim=3, Ra=1e4, zstretch=1.5)]
+    for cfg in cases:
+        z = O.znodes(cfg)
+        X = _ext_fields(cfg, z, c0, U0, V0, q, rho0)
+        prof = O.ext_profiles(cfg, X)
+        cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+        k = 2 * np.pi / cfg.aspect
+        sx = np.sin(k * cfg.aspect / cfg.nx) / (cfg.aspect / cfg.nx)
+        sy = np.sin(k * cfg.aspect / cfg.ny) / (cfg.aspect / cfg.ny) if cfg.ndim == 3 else 0.0
+        m = 2 if cfg.ndim == 3 else 1
+        G, Gp = z * (1 - z), 1 - 2 * z
+        want = dict(F_n=rho0 * (G * Gp * (c0 ** 2 + m / 2) - U0 * G ** 2 * sx / 2 - (V0 * G ** 2 * sy / 2 if m == 2 else 0)),
+                    F_p=-cl["a"] * rho0 * (-cfg.D + q * Gp), F_b=rho0 * cfg.gravity / cfg.eps + 0 * z,
+                    F_v=cl["mu"] * (2 + cfg.stokes) * c0 * (-2.0) + 0 * z,
+                    rho_uz_sq=rho0 ** 2 * G ** 2 * (c0 ** 2 + m / 2), Tsa_sq=q ** 2 * G ** 2)
+        for key, v in want.items():
+            got = prof[key]
+            sl = slice(1, -1) if key.startswith("F_") else slice(None)
+            assert np.max(np.abs(got[sl] - v[sl])) <= 1e-12 * max(np.max(np.abs(v)), 1e-3), (key, cfg.ndim, got[sl], v[sl])
+            if key.startswith("F_"):
+                assert got[0] == 0.0 and got[-1] == 0.0
+
+
+def test_ext_correlation_closed_form():
+    """Eq. Corr_Ra on rho u_z = W s2 (1 + cos kx), T_sa = s s2 cos kx,
+    s2 = sin^2(pi z): <rho u_z T_sa> = 3 W s / 16, <(rho u_z)^2> = 9 W^2 / 16,
+    <T_sa^2> = 3 s^2 / 16 (trapezoid-exact trigonometric integrands), so
+    C = 1/sqrt(3)."""
+    cfg = O.Config(nx=64, nz=33, Ra=1e6)
+    z = np.linspace(0, 1, cfg.nz)
+    Zg, Xg = np.meshgrid(z, np.arange(cfg.nx) * cfg.aspect / cfg.nx, indexing="ij")
+    k = 2 * np.pi / cfg.aspect
+    W, s = 0.02, 0.01
+    s2 = np.sin(np.pi * Zg) ** 2
+    X = state_from_prims(cfg, 1.0 + 0 * Zg, 0 * Zg, W * s2 * (1 + np.cos(k * Xg)),
+                         (1 - cfg.D * Zg) + s * s2 * np.cos(k * Xg), Zg)
+    e, _ = O.extended(cfg, X)
+    assert abs(e["rho_uz_sq"] / (9 * W * W / 16) - 1) < 1e-12
+    assert abs(e["Tsa_sq"] / (3 * s * s / 16) - 1) < 1e-12
+    assert abs(e["C"] - 1 / math.sqrt(3)) < 1e-12
+
+
+def test_ext_boundary_layers_of_built_profile():
+    """Reading of the boundary-layer edge (first plane from a plate where the
+    slope of <T>_A is no steeper than the adiabatic -D): a profile with bulk
+    slope -D + 1e-3 and parabolic layers ending at planes 4 (bottom) and
+    K - 8 (top) gives lambda_b = z_4, lambda_t = 1 - z_{K-8}, on uniform and
+    tanh planes; the conduction state (slope -(eps + D)) has no bulk: 1."""
+    for kw in ({}, {"zstretch": 1.5}):
+        cfg = O.Config(nx=8, nz=33, **kw)
+        z = O.znodes(cfg)
+        K = cfg.nz - 1
+        zb, zt = z[4], z[K - 8]
+        T = 1.0 - (cfg.D - 1e-3) * z + np.where(z < zb, (zb - z) ** 2, 0.0) - np.where(z > zt, (z - zt) ** 2, 0.0)
+        X = state_from_prims(cfg, cols(cfg, 1 + 0 * z), cols(cfg, 0 * z), cols(cfg, 0 * z), cols(cfg, T), cols(cfg, z))
+        e, _ = O.extended(cfg, X)
+        assert e["lambda_b"] == zb and e["lambda_t"] == 1.0 - zt, (kw, e["lambda_b"], zb, e["lambda_t"], 1 - zt)
+    cfg = O.Config(nx=8, nz=17, pert_amp=0.0)
+    e, _ = O.extended(cfg, O.init(cfg))
+    assert e["lambda_b"] == 1.0 and e["lambda_t"] == 1.0
+
+
+def test_ext_histogram_counts_are_exact():
+    """r = K_e/I_e = b u^2/(2T) placed at bin centres of log10 r: the counts
+    are the planted ones (nodes at rest, r = 0, in bin 0), r_max the largest."""
+    cfg = O.Config(nx=16, nz=9, gravity=0.0, t_top=1.0)
+    nb, lo, hi = 32, -12.0, 0.0
+    rng = np.random.default_rng(8)
+    qs = rng.integers(0, nb, (cfg.nz, cfg.nx))
+    qs[0] = qs[-1] = -1                      # plates at rest
+    b = cfg.gamma * cfg.eps * cfg.D
+    r = np.where(qs >= 0, 10.0 ** (lo + (qs + 0.5) * (hi - lo) / nb), 0.0)
+    ux = np.sqrt(2 * r / b)                  # T = 1
+    z = np.linspace(0, 1, cfg.nz)
+    X = state_from_prims(cfg, cols(cfg, 1 + 0 * z), ux, 0 * ux, 1 + 0 * ux, cols(cfg, z))
+    e, hist = O.extended(cfg, X, nb, lo, hi)
+    want = np.bincount(np.where(qs >= 0, qs, 0).ravel(), minlength=nb)
+    assert np.array_equal(hist, want)
+    assert abs(e["r_max"] / r.max() - 1) < 1e-12
