@@ -214,6 +214,19 @@ def run_gpu(args):
     for _ in range(n_e2e):
         cm.cm_run_host(hostnp, 1, None, True)
     e2e64_s = max_ms(time.perf_counter() - t0)
+    # extended diagnostics of the stepped state (force terms, C(Ra), boundary
+    # layers, K_e/I_e histogram): one blocking call, host wall clock
+    s.extended(96, -14.0, 0.0)
+    t0 = time.perf_counter()
+    n_ext = 5
+    for _ in range(n_ext):
+        ext_vals, ext_hist = s.extended(96, -14.0, 0.0)
+    ext_ms = (time.perf_counter() - t0) * 1e3 / n_ext
+    ext_bytes = 4 * 4 * cells  # one read of the FP32 state (neighbours from L1/L2)
+    extended = {"ms_per_call": round(ext_ms, 4), "state_bytes": ext_bytes,
+                "GB_per_s_of_state": round(ext_bytes / (ext_ms * 1e-3) / 1e9, 1),
+                "values": {k: ext_vals[k] for k in ("C", "lambda_b", "lambda_top", "F_n", "F_p", "F_b", "F_v", "r_max")},
+                "hist_nodes": int(ext_hist.sum()), "timing": "host wall clock around cm_extended (launch, copies, host sums)"}
     s.close()
 
     # ---- batched ensemble: 64 independent boxes, N_z = round(32 * 8^u), N_x = 4 N_z,
@@ -409,6 +422,7 @@ def run_gpu(args):
                  "sweep_ms": [round(x, 5) for x in r64["sweep_ms"]], "gpu_launches": r64["launches"],
                  "roofline_hbm": roofline(r64)},
         "stretched": stretched,
+        "extended": extended,
     }
     if stretched is not None:
         stretched["roofline"] = roofline(rst, "_x2s")

@@ -228,6 +228,35 @@ int cm_profile_steps(int n, unsigned long long flush_bytes, double* ms_out, doub
  * out-pointers, may be NULL. */
 int cm_tuning(int* seg_z, int* seg_x);
 
+/* Extended diagnostics of the current state (the analyses of Secs. 4-6).
+ * z derivatives: of the quadratic through three planes (central on uniform
+ * planes); x, y: central.  Volume averages as in cm_diag. */
+typedef struct cm_ext {
+    double C;          /* <rho u_z T_sa>_V / sqrt(<(rho u_z)^2>_V <T_sa^2>_V) (Eq. Corr_Ra); NaN at rest */
+    double rho_uz_sq;  /* <(rho u_z)^2>_V */
+    double Tsa_sq;     /* <T_sa^2>_V, T_sa = T - (1 - D z) */
+    double lambda_b;   /* bottom thermal boundary layer: height of the first plane above the plate whose
+                          slope of <T>_A to the next plane up is no steeper than the adiabatic -D (1 if none) */
+    double lambda_top; /* the same from the top plate down (distance from the top plate) */
+    double F_n, F_p, F_b, F_v; /* averages over the interior planes (weights of the trapezoid rule) of
+                          rho (u.grad) u_z, -dp/dz, rho g and d_i tau_iz (Sec. 6, z momentum) */
+    double r_max;      /* max over nodes of K_e/I_e = (rho u^2/2)/(rho C_v T) */
+} cm_ext;
+
+/* Plane means of F_n, F_p, F_b, F_v (0 on the plates), (rho u_z)^2 and
+ * T_sa^2: out (host) receives nz x 6 doubles, plane-major.  FP64 arithmetic
+ * on the state (FP32 states widened).  Blocking.  CM_ENOTINIT / CM_EINVAL
+ * (out NULL) / CM_ECUDA. */
+int cm_ext_profiles(double* out);
+
+/* The quantities of cm_ext for the current state, and, if hist != NULL, the
+ * histogram of log10 (K_e/I_e) over all nodes: hist (host, nbins counts,
+ * 1 <= nbins <= 1024) counts values in [lo + q w, lo + (q+1) w), w =
+ * (hi - lo)/nbins, values below lo (and nodes at rest) in bin 0, values at
+ * or above hi in the last bin.  Blocking.  CM_EINVAL for out NULL, a bad
+ * nbins or hi <= lo. */
+int cm_extended(cm_ext* out, long long* hist, int nbins, double log10_lo, double log10_hi);
+
 /* Copy the nz plane heights z_k of the context's z-grid (uniform, tanh or
  * given; see cm_grid) to z (host, nz doubles).  CM_ENOTINIT without a context,
  * CM_EINVAL for z = NULL. */

@@ -20,7 +20,7 @@ from ._binding import (cm_adj_backward, cm_adj_forward, cm_batch_diagnostics, cm
                        cm_init, cm_last_error, cm_launch_count, cm_load, cm_profile_steps, cm_params, cm_run_host,
                        cm_profiles, cm_run_host_f32, cm_sample, cm_tuning,
                        cm_save, cm_set_state, cm_state_bytes, cm_state_layout, cm_state_ptr, cm_step, cm_sweep,
-                       cm_sync, cm_znodes, lib)
+                       cm_sync, cm_znodes, cm_ext, cm_ext_profiles, cm_extended, lib)
 
 __all__ = [n for n in dir() if n.startswith("cm_") or n.startswith("CM")] + ["Solver", "lib"]
 
@@ -64,6 +64,14 @@ class Solver:
     def z(self) -> np.ndarray:
         """Plane heights of the z-grid."""
         return cm_znodes(self.grid.nz)
+
+    def ext_profiles(self) -> dict:
+        """Plane means of F_n, F_p, F_b, F_v, (rho u_z)^2, T_sa^2 of the current state."""
+        return cm_ext_profiles(self.grid.nz)
+
+    def extended(self, nbins: int = 64, log10_lo: float = -16.0, log10_hi: float = 0.0):
+        """C(Ra), boundary layers, averaged z-momentum terms, max K_e/I_e and its histogram."""
+        return cm_extended(nbins, log10_lo, log10_hi)
 
     @property
     def shape(self) -> tuple:

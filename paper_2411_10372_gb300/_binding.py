@@ -47,6 +47,14 @@ class cm_diag(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad_"}
 
 
+class cm_ext(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in ("C", "rho_uz_sq", "Tsa_sq", "lambda_b", "lambda_top", "F_n", "F_p",
+                                               "F_b", "F_v", "r_max")]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class CMError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{msg} (status {code})")
@@ -78,6 +86,9 @@ _SIGS = {
     "cm_profiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "cm_tuning": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cm_znodes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "cm_ext_profiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "cm_extended": (ctypes.c_int, [ctypes.POINTER(cm_ext), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_double]),
     "cm_run_host_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cm_diag)]),
     "cm_adj_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "cm_adj_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
@@ -229,6 +240,25 @@ def cm_profiles(nz: int) -> dict:
     out = np.empty((nz, 8), dtype=np.float64)
     _check(lib().cm_profiles(out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return {k: out[:, q].copy() for q, k in enumerate(PROFILE_KEYS)}
+
+
+EXT_PROFILE_KEYS = ("F_n", "F_p", "F_b", "F_v", "rho_uz_sq", "Tsa_sq")
+
+
+def cm_ext_profiles(nz: int) -> dict:
+    """Plane means of the z-momentum terms and of (rho u_z)^2, T_sa^2 (include/cm.h): name -> nz values."""
+    out = np.empty((nz, 6), dtype=np.float64)
+    _check(lib().cm_ext_profiles(out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return {k: out[:, q].copy() for q, k in enumerate(EXT_PROFILE_KEYS)}
+
+
+def cm_extended(nbins: int = 64, log10_lo: float = -16.0, log10_hi: float = 0.0):
+    """(cm_ext as a dict, histogram of log10 K_e/I_e as int64 array; None if nbins == 0)."""
+    e = cm_ext()
+    hist = np.zeros(max(nbins, 1), dtype=np.int64)
+    hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if nbins > 0 else None
+    _check(lib().cm_extended(ctypes.byref(e), hp, int(nbins), float(log10_lo), float(log10_hi)))
+    return e.as_dict(), (hist if nbins > 0 else None)
 
 
 def cm_znodes(nz: int) -> np.ndarray:

@@ -199,6 +199,133 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
 }
 
 
+// ---- extended diagnostics -------------------------------------------------
+
+// FP64 primitives of the node at `off` (the oracle's order of operations)
+template <class R>
+__device__ __forceinline__ void ext_prims(const R* X, long long fs, int ndim, long long off, double z, const ExtArgs& A,
+                                          double& rho, double& ux, double& uy, double& uz, double& T)
+{
+    rho = (double)X[off];
+    ux = (double)X[off + fs] / rho;
+    double E;
+    if (ndim == 3) {
+        uy = (double)X[off + 2 * fs] / rho;
+        uz = (double)X[off + 3 * fs] / rho;
+        E = (double)X[off + 4 * fs];
+    } else {
+        uy = 0.0;
+        uz = (double)X[off + 2 * fs] / rho;
+        E = (double)X[off + 3 * fs];
+    }
+    T = A.b * (E / rho - 0.5 * ((ux * ux + uy * uy) + uz * uz) - A.g * z);
+}
+
+// derivative and second derivative at plane k of the quadratic through
+// planes k-1, k, k+1 (central differences on uniform planes)
+__device__ __forceinline__ double ext_dz(const double* zt, int k, double fm, double f0, double fp)
+{
+    const double hm = zt[k] - zt[k - 1], hp = zt[k + 1] - zt[k];
+    return (hm * hm * fp - hp * hp * fm + (hp * hp - hm * hm) * f0) / (hm * hp * (hm + hp));
+}
+__device__ __forceinline__ double ext_dzz(const double* zt, int k, double fm, double f0, double fp)
+{
+    const double hm = zt[k] - zt[k - 1], hp = zt[k + 1] - zt[k];
+    return 2.0 * ((fp - f0) / hp - (f0 - fm) / hm) / (hm + hp);
+}
+
+// One block per plane k: FP64 sums over the plane of the z-momentum terms
+//   F_n = rho (u . grad) u_z, F_p = -dp/dz, F_b = rho g,
+//   F_v = mu (d_xx u_z + d_yy u_z + (2 + s) d_zz u_z + (1 + s)(d_x d_z u_x + d_y d_z u_y))
+// (interior planes; 0 on the plates), of (rho u_z)^2, T_sa^2, rho u_z T_sa
+// and T, the max of r = K_e/I_e = b u^2/(2T), and the histogram of log10 r.
+// scratch[k*16 + q]: q = 0..5 F_n, F_p, F_b, F_v, (rho u_z)^2, T_sa^2; 6
+// rho u_z T_sa; 7 max r; 8 T.
+template <class R>
+__global__ void __launch_bounds__(kDiagThreads) ext_planes(const R* X, Coef<R> C, ExtArgs A, double* scratch)
+{
+    __shared__ unsigned int bins[kExtMaxBins];
+    const int k = blockIdx.x, K = C.nz - 1, nx = C.nx, ny = C.ny;
+    for (int q = threadIdx.x; q < A.nbins; q += kDiagThreads) bins[q] = 0u;
+    __syncthreads();
+    const long long fs = C.fstride;
+    const double z = A.zt[k];
+    const bool inner = k > 0 && k < K;
+    double v[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double tsum[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    auto off = [&](int kk, int j, int i) { return ((long long)kk * ny + j) * C.pitch + i; };
+    auto uzat = [&](int kk, int j, int i) {
+        double r, a, b, c, t;
+        ext_prims(X, fs, C.ndim, off(kk, j, i), A.zt[kk], A, r, a, b, c, t);
+        return c;
+    };
+    for (long long n = threadIdx.x; n < (long long)nx * ny; n += kDiagThreads) {
+        const int i = (int)(n % nx), j = (int)(n / nx);
+        double rho, ux, uy, uz, T;
+        ext_prims(X, fs, C.ndim, off(k, j, i), z, A, rho, ux, uy, uz, T);
+        const double Tsa = T - (1.0 - A.D * z);
+        v[4] += (rho * uz) * (rho * uz);
+        v[5] += Tsa * Tsa;
+        v[6] += rho * uz * Tsa;
+        tsum[0] += T;
+        const double u2 = (ux * ux + uy * uy) + uz * uz;
+        const double r = A.b * u2 / (2.0 * T);
+        v[7] = fmax(v[7], r);
+        int q = 0;
+        if (r > 0.0) {
+            const double t = (log10(r) - A.lo) / A.bw;
+            q = t < 0.0 ? 0 : (t >= A.nbins ? A.nbins - 1 : (int)t);
+        }
+        atomicAdd(&bins[q], 1u);
+        if (!inner) continue;
+        const int ip = (i + 1) % nx, im = (i - 1 + nx) % nx;
+        double rz[2], uxz[2], uyz[2], uzz[2], Tz[2];
+        for (int s = 0; s < 2; ++s)
+            ext_prims(X, fs, C.ndim, off(k + (s ? 1 : -1), j, i), A.zt[k + (s ? 1 : -1)], A, rz[s], uxz[s], uyz[s], uzz[s], Tz[s]);
+        const double uzp = uzat(k, j, ip), uzm = uzat(k, j, im);
+        const double dxuz = (uzp - uzm) / (2.0 * A.dx);
+        const double dxx = (uzp - 2.0 * uz + uzm) / (A.dx * A.dx);
+        const double dzuz = ext_dz(A.zt, k, uzz[0], uz, uzz[1]);
+        const double dzz = ext_dzz(A.zt, k, uzz[0], uz, uzz[1]);
+        double dyuz = 0.0, dyy = 0.0, dydzuy = 0.0;
+        // d_x d_z u_x: x-central of the z derivatives at columns i +- 1
+        double uxp[3], uxm[3];
+        for (int s = 0; s < 3; ++s) {
+            double r_, a_, b_, c_, t_;
+            ext_prims(X, fs, C.ndim, off(k + s - 1, j, ip), A.zt[k + s - 1], A, r_, a_, b_, c_, t_);
+            uxp[s] = a_;
+            ext_prims(X, fs, C.ndim, off(k + s - 1, j, im), A.zt[k + s - 1], A, r_, a_, b_, c_, t_);
+            uxm[s] = a_;
+        }
+        const double dxdzux = (ext_dz(A.zt, k, uxp[0], uxp[1], uxp[2]) - ext_dz(A.zt, k, uxm[0], uxm[1], uxm[2])) / (2.0 * A.dx);
+        if (C.ndim == 3) {
+            const int jp = (j + 1) % ny, jm = (j - 1 + ny) % ny;
+            const double uyp_ = uzat(k, jp, i), uym_ = uzat(k, jm, i);
+            dyuz = (uyp_ - uym_) / (2.0 * A.dy);
+            dyy = (uyp_ - 2.0 * uz + uym_) / (A.dy * A.dy);
+            double uyp[3], uym[3];
+            for (int s = 0; s < 3; ++s) {
+                double r_, a_, b_, c_, t_;
+                ext_prims(X, fs, C.ndim, off(k + s - 1, jp, i), A.zt[k + s - 1], A, r_, a_, b_, c_, t_);
+                uyp[s] = b_;
+                ext_prims(X, fs, C.ndim, off(k + s - 1, jm, i), A.zt[k + s - 1], A, r_, a_, b_, c_, t_);
+                uym[s] = b_;
+            }
+            dydzuy = (ext_dz(A.zt, k, uyp[0], uyp[1], uyp[2]) - ext_dz(A.zt, k, uym[0], uym[1], uym[2])) / (2.0 * A.dy);
+        }
+        v[0] += rho * ((ux * dxuz + uy * dyuz) + uz * dzuz);
+        v[1] += -ext_dz(A.zt, k, A.a * rz[0] * Tz[0], A.a * rho * T, A.a * rz[1] * Tz[1]);
+        v[2] += rho * A.g;
+        v[3] += A.mu * ((dxx + dyy) + (2.0 + A.stokes) * dzz + (1.0 + A.stokes) * (dxdzux + dydzuy));
+    }
+    block_sum_q(v, scratch + (size_t)k * 16);
+    __syncthreads();  // block_sum_q's shared staging is reused
+    block_sum_q(tsum, scratch + (size_t)k * 16 + 8);
+    __syncthreads();
+    for (int q = threadIdx.x; q < A.nbins; q += kDiagThreads)
+        if (bins[q]) atomicAdd(A.hist + q, (unsigned long long)bins[q]);
+}
+
 #ifdef CM_DEFINE_DIAG_FINAL  // one definition, in kernels_f64.cu
 // combine the plane sums (trapezoid weights, fixed order) into one cm_diag
 // record: Eq. volume_Nu, Eq. mean_Nu (second-order one-sided differences of

@@ -55,6 +55,8 @@ struct Ctx {
     double* pc_d;
     DevCtl* ctl;
     double* scratch;            // per-plane diagnostics sums (nz * kDiagQ)
+    double* ext_scratch;        // extended diagnostics: per-plane sums (nz * 16), allocated on first use
+    unsigned long long* ext_hist; // histogram counts (kExtMaxBins), allocated on first use
     double* dense;              // dense FP64 staging for host transfers (lazy)
     cm_diag* ring;
     int ring_cap, ring_head, ring_count;
@@ -112,6 +114,8 @@ void free_ctx(Ctx* c)
     cudaFree(c->pc_d);
     cudaFree(c->ctl);
     cudaFree(c->scratch);
+    cudaFree(c->ext_scratch);
+    cudaFree(c->ext_hist);
     cudaFree(c->dense);
     cudaFree(c->ring);
     if (c->adj) {
@@ -624,6 +628,121 @@ int cm_profiles(double* out)
     for (int k = 0; k < nz; ++k)
         for (int q = 0; q < kDiagQ; ++q)
             out[(size_t)k * kDiagQ + q] = q == kDiagQ - 1 ? sums[(size_t)k * kDiagQ + q] : sums[(size_t)k * kDiagQ + q] / cells;
+    return CM_OK;
+}
+
+// extended diagnostics of the current state: per-plane sums (nz x 16, see
+// ext_planes) and, with nbins > 0, the histogram of log10 K_e/I_e
+int run_ext(Ctx* c, int nbins, double lo, double hi, std::vector<double>& sums, std::vector<unsigned long long>& hist)
+{
+    const int nz = c->grid.nz;
+    if (!c->ext_scratch) {
+        if (cudaMalloc(&c->ext_scratch, (size_t)nz * 16 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&c->ext_hist, kExtMaxBins * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CM_ENOMEM, "cudaMalloc of the extended-diagnostics scratch failed");
+        }
+    }
+    ExtArgs A;
+    A.zt = c->zt_d;
+    A.a = c->a;
+    A.b = c->b;
+    A.g = c->g;
+    A.D = c->prm.D;
+    A.mu = std::sqrt(c->Pr / c->Ra);
+    A.stokes = c->prm.stokes;
+    A.dx = c->grid.aspect / c->grid.nx;
+    A.dy = c->grid.aspect / c->ny;
+    A.nbins = nbins > 0 ? nbins : 1;
+    A.lo = nbins > 0 ? lo : -16.0;
+    A.bw = nbins > 0 ? (hi - lo) / nbins : 16.0;
+    A.hist = c->ext_hist;
+    CK(cudaMemsetAsync(c->ext_hist, 0, kExtMaxBins * sizeof(unsigned long long), c->stream));
+    cudaError_t e = c->prec == CM_FP64
+        ? Launch<double>::ext_planes((const double*)c->buf[c->cur], c->cd, A, c->ext_scratch, c->stream)
+        : Launch<float>::ext_planes((const float*)c->buf[c->cur], c->cf, A, c->ext_scratch, c->stream);
+    if (e != cudaSuccess) return fail(CM_ECUDA, "extended diagnostics launch: %s", cudaGetErrorString(e));
+    c->launches++;
+    sums.assign((size_t)nz * 16, 0.0);
+    hist.assign(A.nbins, 0ULL);
+    CK(cudaMemcpyAsync(sums.data(), c->ext_scratch, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hist.data(), c->ext_hist, hist.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CM_OK;
+}
+
+int cm_ext_profiles(double* out)
+{
+    NEED_CTX();
+    if (!out) return fail(CM_EINVAL, "out is NULL");
+    Ctx* c = g_ctx;
+    std::vector<double> sums;
+    std::vector<unsigned long long> hist;
+    int rc = run_ext(c, 0, 0.0, 0.0, sums, hist);
+    if (rc) return rc;
+    const double cells = (double)c->grid.nx * c->ny;
+    for (int k = 0; k < c->grid.nz; ++k)
+        for (int q = 0; q < 6; ++q) out[(size_t)k * 6 + q] = sums[(size_t)k * 16 + q] / cells;
+    return CM_OK;
+}
+
+int cm_extended(cm_ext* out, long long* hist_out, int nbins, double log10_lo, double log10_hi)
+{
+    NEED_CTX();
+    if (!out) return fail(CM_EINVAL, "out is NULL");
+    if (hist_out && (nbins < 1 || nbins > kExtMaxBins || !(log10_hi > log10_lo)))
+        return fail(CM_EINVAL, "need 1 <= nbins <= %d and log10_hi > log10_lo", kExtMaxBins);
+    Ctx* c = g_ctx;
+    std::vector<double> sums;
+    std::vector<unsigned long long> hist;
+    int rc = run_ext(c, hist_out ? nbins : 0, log10_lo, log10_hi, sums, hist);
+    if (rc) return rc;
+    const int nz = c->grid.nz, K = nz - 1;
+    const double* z = c->zplanes;
+    const bool st = c->zp_d != nullptr;
+    const double cells = (double)c->grid.nx * c->ny;
+    // trapezoid weights of the planes (cell widths on a stretched grid)
+    auto wgt = [&](int k) {
+        if (!st) return (k == 0 || k == K) ? 0.5 : 1.0;
+        if (k == 0) return (z[1] - z[0]) / 2.0;
+        if (k == K) return (z[K] - z[K - 1]) / 2.0;
+        return ((z[k] - z[k - 1]) + (z[k + 1] - z[k])) / 2.0;
+    };
+    double s_conv = 0, s_m2 = 0, s_t2 = 0, wsum = 0, f[4] = {0, 0, 0, 0}, rmax = 0;
+    std::vector<double> TA(nz);
+    for (int k = 0; k < nz; ++k) {
+        const double* sk = &sums[(size_t)k * 16];
+        const double w = wgt(k);
+        s_conv += w * sk[6] / cells;
+        s_m2 += w * (sk[4] / cells);
+        s_t2 += w * (sk[5] / cells);
+        TA[k] = sk[8] / cells;
+        rmax = std::fmax(rmax, sk[7]);
+        if (k > 0 && k < K) {
+            wsum += w;
+            for (int q = 0; q < 4; ++q) f[q] += w * (sk[q] / cells);
+        }
+    }
+    const double vol = st ? 1.0 : (double)(nz - 1);
+    cm_ext r;
+    r.rho_uz_sq = s_m2 / vol;
+    r.Tsa_sq = s_t2 / vol;
+    r.C = (s_conv / vol) / std::sqrt(r.rho_uz_sq * r.Tsa_sq);
+    r.lambda_b = 1.0;
+    for (int k = 0; k < K; ++k)
+        if ((TA[k + 1] - TA[k]) / (z[k + 1] - z[k]) >= -c->prm.D) { r.lambda_b = z[k]; break; }
+    r.lambda_top = 1.0;
+    for (int k = K; k > 0; --k)
+        if ((TA[k] - TA[k - 1]) / (z[k] - z[k - 1]) >= -c->prm.D) { r.lambda_top = 1.0 - z[k]; break; }
+    r.F_n = f[0] / wsum;
+    r.F_p = f[1] / wsum;
+    r.F_b = f[2] / wsum;
+    r.F_v = f[3] / wsum;
+    r.r_max = rmax;
+    *out = r;
+    if (hist_out)
+        for (int q = 0; q < nbins; ++q) hist_out[q] = (long long)hist[q];
     return CM_OK;
 }
 

@@ -101,6 +101,18 @@ struct DiagFinal {
     const Plane<double>* zp;  // stretched z-grid (trapezoid weights, plate derivatives); nullptr = uniform
 };
 
+// extended diagnostics (force terms of the z momentum equation, C(Ra),
+// K_e/I_e histogram), FP64
+constexpr int kExtMaxBins = 1024;
+struct ExtArgs {
+    const double* zt;                // plane heights
+    double a, b, g, D, mu, stokes;   // closures and the Stokes coefficient
+    double dx, dy;
+    double lo, bw;                   // histogram of log10 r: lower edge and bin width
+    int nbins;
+    unsigned long long* hist;        // nbins counts (device; the caller zeroes it)
+};
+
 template <class R> struct St { R r, mx, mz, E; };       // 2D conserved state
 template <class R> struct St3 { R r, mx, my, mz, E; };  // 3D conserved state
 

@@ -208,6 +208,13 @@ cudaError_t Launch<R>::dt(const R* X, const R* zt, const Coef<R>& C, DevCtl* ctl
 }
 
 template <class R>
+cudaError_t Launch<R>::ext_planes(const R* X, const Coef<R>& C, const ExtArgs& A, double* scratch, cudaStream_t s)
+{
+    cm::ext_planes<R><<<C.nz, kDiagThreads, 0, s>>>(X, C, A, scratch);
+    return cudaGetLastError();
+}
+
+template <class R>
 cudaError_t Launch<R>::diag_planes(const R* X, const Coef<R>& C, const DiagArgs& A, double* scratch, DevCtl* ctl,
                                    cudaStream_t s)
 {

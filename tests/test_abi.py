@@ -41,7 +41,7 @@ def test_struct_layout_matches_c(tmp_path):
 int main(void) {
   printf("cm_grid %zu\\ncm_params %zu\\ncm_diag %zu\\n", sizeof(cm_grid), sizeof(cm_params), sizeof(cm_diag));
   O(cm_params, seed); O(cm_params, precision); O(cm_params, stream); O(cm_params, state_buf);
-  O(cm_diag, status); O(cm_diag, mach_max); O(cm_grid, aspect); O(cm_grid, zstretch); O(cm_grid, znodes);
+  O(cm_diag, status); O(cm_diag, mach_max); O(cm_grid, aspect); O(cm_grid, zstretch); O(cm_grid, znodes); O(cm_ext, r_max);
   return 0; }
 ''')
     exe = tmp_path / "probe"
