@@ -245,8 +245,9 @@ typedef struct cm_ext {
 
 /* Plane means of F_n, F_p, F_b, F_v (0 on the plates), (rho u_z)^2 and
  * T_sa^2: out (host) receives nz x 6 doubles, plane-major.  FP64 arithmetic
- * on the state (FP32 states widened).  Blocking.  CM_ENOTINIT / CM_EINVAL
- * (out NULL) / CM_ECUDA. */
+ * on the state (FP32 states widened).  The first call allocates device work
+ * space of 40 bytes per node (FP64 primitives), kept until cm_finalize.
+ * Blocking.  CM_ENOTINIT / CM_EINVAL (out NULL) / CM_ENOMEM / CM_ECUDA. */
 int cm_ext_profiles(double* out);
 
 /* The quantities of cm_ext for the current state, and, if hist != NULL, the

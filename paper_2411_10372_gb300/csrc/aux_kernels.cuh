@@ -234,35 +234,51 @@ __device__ __forceinline__ double ext_dzz(const double* zt, int k, double fm, do
     return 2.0 * ((fp - f0) / hp - (f0 - fm) / hm) / (hm + hp);
 }
 
+// FP64 primitives of every node, once: P[q * n + node], q = 0..4 rho, u_x,
+// u_y, u_z, T; node = (k ny + j) nx + i (dense)
+template <class R>
+__global__ void ext_prims_all(const R* X, Coef<R> C, ExtArgs A, double* P)
+{
+    const long long n = (long long)C.nx * C.ny * C.nz;
+    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < n; d += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(d % C.nx);
+        const long long jk = d / C.nx;
+        const int j = (int)(jk % C.ny), k = (int)(jk / C.ny);
+        double rho, ux, uy, uz, T;
+        ext_prims(X, C.fstride, C.ndim, ((long long)k * C.ny + j) * C.pitch + i, A.zt[k], A, rho, ux, uy, uz, T);
+        P[d] = rho;
+        P[n + d] = ux;
+        P[2 * n + d] = uy;
+        P[3 * n + d] = uz;
+        P[4 * n + d] = T;
+    }
+}
+
 // One block per plane k: FP64 sums over the plane of the z-momentum terms
 //   F_n = rho (u . grad) u_z, F_p = -dp/dz, F_b = rho g,
 //   F_v = mu (d_xx u_z + d_yy u_z + (2 + s) d_zz u_z + (1 + s)(d_x d_z u_x + d_y d_z u_y))
 // (interior planes; 0 on the plates), of (rho u_z)^2, T_sa^2, rho u_z T_sa
-// and T, the max of r = K_e/I_e = b u^2/(2T), and the histogram of log10 r.
-// scratch[k*16 + q]: q = 0..5 F_n, F_p, F_b, F_v, (rho u_z)^2, T_sa^2; 6
-// rho u_z T_sa; 7 max r; 8 T.
-template <class R>
-__global__ void __launch_bounds__(kDiagThreads) ext_planes(const R* X, Coef<R> C, ExtArgs A, double* scratch)
+// and T, the max of r = K_e/I_e = b u^2/(2T), and the histogram of log10 r,
+// from the primitives P of ext_prims_all.  scratch[k*16 + q]: q = 0..5 F_n,
+// F_p, F_b, F_v, (rho u_z)^2, T_sa^2; 6 rho u_z T_sa; 7 max r; 8 T.
+static __global__ void __launch_bounds__(kDiagThreads) ext_planes(int nx, int ny, int nz, int ndim, ExtArgs A, const double* P,
+                                                           double* scratch)
 {
     __shared__ unsigned int bins[kExtMaxBins];
-    const int k = blockIdx.x, K = C.nz - 1, nx = C.nx, ny = C.ny;
+    const int k = blockIdx.x, K = nz - 1;
     for (int q = threadIdx.x; q < A.nbins; q += kDiagThreads) bins[q] = 0u;
     __syncthreads();
-    const long long fs = C.fstride;
+    const long long N = (long long)nx * ny * nz;
+    const double *Pr = P, *Pux = P + N, *Puy = P + 2 * N, *Puz = P + 3 * N, *PT = P + 4 * N;
     const double z = A.zt[k];
     const bool inner = k > 0 && k < K;
     double v[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
     double tsum[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
-    auto off = [&](int kk, int j, int i) { return ((long long)kk * ny + j) * C.pitch + i; };
-    auto uzat = [&](int kk, int j, int i) {
-        double r, a, b, c, t;
-        ext_prims(X, fs, C.ndim, off(kk, j, i), A.zt[kk], A, r, a, b, c, t);
-        return c;
-    };
+    auto at = [&](int kk, int j, int i) { return ((long long)kk * ny + j) * nx + i; };
     for (long long n = threadIdx.x; n < (long long)nx * ny; n += kDiagThreads) {
         const int i = (int)(n % nx), j = (int)(n / nx);
-        double rho, ux, uy, uz, T;
-        ext_prims(X, fs, C.ndim, off(k, j, i), z, A, rho, ux, uy, uz, T);
+        const long long c0 = at(k, j, i);
+        const double rho = Pr[c0], ux = Pux[c0], uy = Puy[c0], uz = Puz[c0], T = PT[c0];
         const double Tsa = T - (1.0 - A.D * z);
         v[4] += (rho * uz) * (rho * uz);
         v[5] += Tsa * Tsa;
@@ -279,42 +295,28 @@ __global__ void __launch_bounds__(kDiagThreads) ext_planes(const R* X, Coef<R> C
         atomicAdd(&bins[q], 1u);
         if (!inner) continue;
         const int ip = (i + 1) % nx, im = (i - 1 + nx) % nx;
-        double rz[2], uxz[2], uyz[2], uzz[2], Tz[2];
-        for (int s = 0; s < 2; ++s)
-            ext_prims(X, fs, C.ndim, off(k + (s ? 1 : -1), j, i), A.zt[k + (s ? 1 : -1)], A, rz[s], uxz[s], uyz[s], uzz[s], Tz[s]);
-        const double uzp = uzat(k, j, ip), uzm = uzat(k, j, im);
+        const long long zm = at(k - 1, j, i), zp = at(k + 1, j, i);
+        const double uzp = Puz[at(k, j, ip)], uzm = Puz[at(k, j, im)];
         const double dxuz = (uzp - uzm) / (2.0 * A.dx);
         const double dxx = (uzp - 2.0 * uz + uzm) / (A.dx * A.dx);
-        const double dzuz = ext_dz(A.zt, k, uzz[0], uz, uzz[1]);
-        const double dzz = ext_dzz(A.zt, k, uzz[0], uz, uzz[1]);
-        double dyuz = 0.0, dyy = 0.0, dydzuy = 0.0;
+        const double dzuz = ext_dz(A.zt, k, Puz[zm], uz, Puz[zp]);
+        const double dzz = ext_dzz(A.zt, k, Puz[zm], uz, Puz[zp]);
         // d_x d_z u_x: x-central of the z derivatives at columns i +- 1
-        double uxp[3], uxm[3];
-        for (int s = 0; s < 3; ++s) {
-            double r_, a_, b_, c_, t_;
-            ext_prims(X, fs, C.ndim, off(k + s - 1, j, ip), A.zt[k + s - 1], A, r_, a_, b_, c_, t_);
-            uxp[s] = a_;
-            ext_prims(X, fs, C.ndim, off(k + s - 1, j, im), A.zt[k + s - 1], A, r_, a_, b_, c_, t_);
-            uxm[s] = a_;
-        }
-        const double dxdzux = (ext_dz(A.zt, k, uxp[0], uxp[1], uxp[2]) - ext_dz(A.zt, k, uxm[0], uxm[1], uxm[2])) / (2.0 * A.dx);
-        if (C.ndim == 3) {
+        const double dxdzux = (ext_dz(A.zt, k, Pux[at(k - 1, j, ip)], Pux[at(k, j, ip)], Pux[at(k + 1, j, ip)]) -
+                               ext_dz(A.zt, k, Pux[at(k - 1, j, im)], Pux[at(k, j, im)], Pux[at(k + 1, j, im)])) /
+                              (2.0 * A.dx);
+        double dyuz = 0.0, dyy = 0.0, dydzuy = 0.0;
+        if (ndim == 3) {
             const int jp = (j + 1) % ny, jm = (j - 1 + ny) % ny;
-            const double uyp_ = uzat(k, jp, i), uym_ = uzat(k, jm, i);
+            const double uyp_ = Puz[at(k, jp, i)], uym_ = Puz[at(k, jm, i)];
             dyuz = (uyp_ - uym_) / (2.0 * A.dy);
             dyy = (uyp_ - 2.0 * uz + uym_) / (A.dy * A.dy);
-            double uyp[3], uym[3];
-            for (int s = 0; s < 3; ++s) {
-                double r_, a_, b_, c_, t_;
-                ext_prims(X, fs, C.ndim, off(k + s - 1, jp, i), A.zt[k + s - 1], A, r_, a_, b_, c_, t_);
-                uyp[s] = b_;
-                ext_prims(X, fs, C.ndim, off(k + s - 1, jm, i), A.zt[k + s - 1], A, r_, a_, b_, c_, t_);
-                uym[s] = b_;
-            }
-            dydzuy = (ext_dz(A.zt, k, uyp[0], uyp[1], uyp[2]) - ext_dz(A.zt, k, uym[0], uym[1], uym[2])) / (2.0 * A.dy);
+            dydzuy = (ext_dz(A.zt, k, Puy[at(k - 1, jp, i)], Puy[at(k, jp, i)], Puy[at(k + 1, jp, i)]) -
+                      ext_dz(A.zt, k, Puy[at(k - 1, jm, i)], Puy[at(k, jm, i)], Puy[at(k + 1, jm, i)])) /
+                     (2.0 * A.dy);
         }
         v[0] += rho * ((ux * dxuz + uy * dyuz) + uz * dzuz);
-        v[1] += -ext_dz(A.zt, k, A.a * rz[0] * Tz[0], A.a * rho * T, A.a * rz[1] * Tz[1]);
+        v[1] += -ext_dz(A.zt, k, A.a * Pr[zm] * PT[zm], A.a * rho * T, A.a * Pr[zp] * PT[zp]);
         v[2] += rho * A.g;
         v[3] += A.mu * ((dxx + dyy) + (2.0 + A.stokes) * dzz + (1.0 + A.stokes) * (dxdzux + dydzuy));
     }

@@ -56,6 +56,7 @@ struct Ctx {
     DevCtl* ctl;
     double* scratch;            // per-plane diagnostics sums (nz * kDiagQ)
     double* ext_scratch;        // extended diagnostics: per-plane sums (nz * 16), allocated on first use
+    double* ext_prims;          // extended diagnostics: FP64 rho, u, T of every node (5 x nodes), first use
     unsigned long long* ext_hist; // histogram counts (kExtMaxBins), allocated on first use
     double* dense;              // dense FP64 staging for host transfers (lazy)
     cm_diag* ring;
@@ -115,6 +116,7 @@ void free_ctx(Ctx* c)
     cudaFree(c->ctl);
     cudaFree(c->scratch);
     cudaFree(c->ext_scratch);
+    cudaFree(c->ext_prims);
     cudaFree(c->ext_hist);
     cudaFree(c->dense);
     cudaFree(c->ring);
@@ -637,7 +639,9 @@ int run_ext(Ctx* c, int nbins, double lo, double hi, std::vector<double>& sums, 
 {
     const int nz = c->grid.nz;
     if (!c->ext_scratch) {
+        const size_t nodes = (size_t)c->grid.nx * c->ny * nz;
         if (cudaMalloc(&c->ext_scratch, (size_t)nz * 16 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&c->ext_prims, 5 * nodes * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&c->ext_hist, kExtMaxBins * sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
             return fail(CM_ENOMEM, "cudaMalloc of the extended-diagnostics scratch failed");
@@ -659,8 +663,8 @@ int run_ext(Ctx* c, int nbins, double lo, double hi, std::vector<double>& sums, 
     A.hist = c->ext_hist;
     CK(cudaMemsetAsync(c->ext_hist, 0, kExtMaxBins * sizeof(unsigned long long), c->stream));
     cudaError_t e = c->prec == CM_FP64
-        ? Launch<double>::ext_planes((const double*)c->buf[c->cur], c->cd, A, c->ext_scratch, c->stream)
-        : Launch<float>::ext_planes((const float*)c->buf[c->cur], c->cf, A, c->ext_scratch, c->stream);
+        ? Launch<double>::ext_planes((const double*)c->buf[c->cur], c->cd, A, c->ext_prims, c->ext_scratch, c->stream)
+        : Launch<float>::ext_planes((const float*)c->buf[c->cur], c->cf, A, c->ext_prims, c->ext_scratch, c->stream);
     if (e != cudaSuccess) return fail(CM_ECUDA, "extended diagnostics launch: %s", cudaGetErrorString(e));
     c->launches++;
     sums.assign((size_t)nz * 16, 0.0);

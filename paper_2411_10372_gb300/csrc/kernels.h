@@ -40,8 +40,10 @@ struct Launch {
     static cudaError_t dt(const R* X, const R* zt, const Coef<R>& C, DevCtl* ctl, int slot, cudaStream_t s);
     static cudaError_t diag_planes(const R* X, const Coef<R>& C, const DiagArgs& A, double* scratch, DevCtl* ctl,
                                    cudaStream_t s);
-    // extended diagnostics: per-plane sums into scratch[k*16 + q] (see ext_planes)
-    static cudaError_t ext_planes(const R* X, const Coef<R>& C, const ExtArgs& A, double* scratch, cudaStream_t s);
+    // extended diagnostics: FP64 primitives of every node into prims (5 x nodes),
+    // then per-plane sums into scratch[k*16 + q] (see ext_planes)
+    static cudaError_t ext_planes(const R* X, const Coef<R>& C, const ExtArgs& A, double* prims, double* scratch,
+                                  cudaStream_t s);
     // dense float64 [nf][nz][ny][nx] <-> pitched state in R
     static cudaError_t pack(const double* dense, R* X, const Coef<R>& C, int nf, cudaStream_t s);
     static cudaError_t unpack(const R* X, double* dense, const Coef<R>& C, int nf, cudaStream_t s);

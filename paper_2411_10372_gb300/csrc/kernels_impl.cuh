@@ -208,9 +208,11 @@ cudaError_t Launch<R>::dt(const R* X, const R* zt, const Coef<R>& C, DevCtl* ctl
 }
 
 template <class R>
-cudaError_t Launch<R>::ext_planes(const R* X, const Coef<R>& C, const ExtArgs& A, double* scratch, cudaStream_t s)
+cudaError_t Launch<R>::ext_planes(const R* X, const Coef<R>& C, const ExtArgs& A, double* prims, double* scratch,
+                                  cudaStream_t s)
 {
-    cm::ext_planes<R><<<C.nz, kDiagThreads, 0, s>>>(X, C, A, scratch);
+    ext_prims_all<R><<<grid_for((long long)C.nx * C.ny * C.nz, 256), 256, 0, s>>>(X, C, A, prims);
+    cm::ext_planes<<<C.nz, kDiagThreads, 0, s>>>(C.nx, C.ny, C.nz, C.ndim, A, prims, scratch);
     return cudaGetLastError();
 }
 
