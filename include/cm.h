@@ -235,9 +235,11 @@ typedef struct cm_ext {
     double C;          /* <rho u_z T_sa>_V / sqrt(<(rho u_z)^2>_V <T_sa^2>_V) (Eq. Corr_Ra); NaN at rest */
     double rho_uz_sq;  /* <(rho u_z)^2>_V */
     double Tsa_sq;     /* <T_sa^2>_V, T_sa = T - (1 - D z) */
-    double lambda_b;   /* bottom thermal boundary layer: height of the first plane above the plate whose
-                          slope of <T>_A to the next plane up is no steeper than the adiabatic -D (1 if none) */
-    double lambda_top; /* the same from the top plate down (distance from the top plate) */
+    double lambda_b;   /* bottom thermal boundary layer (Sec. 4), as the tangent construction: superadiabatic
+                          drop from the plate to the bulk over the plate gradient,
+                          (Tb - <T_sa>_A(0)) / (d<T_sa>_A/dz at 0), Tb the trapezoid mean of <T_sa>_A
+                          over 1/4 <= z <= 3/4, the plate derivative that of the plate Nusselt number */
+    double lambda_top; /* the same at the top plate: (<T_sa>_A(1) - Tb) / (d<T_sa>_A/dz at 1) */
     double F_n, F_p, F_b, F_v; /* averages over the interior planes (weights of the trapezoid rule) of
                           rho (u.grad) u_z, -dp/dz, rho g and d_i tau_iz (Sec. 6, z momentum) */
     double r_max;      /* max over nodes of K_e/I_e = (rho u^2/2)/(rho C_v T) */

@@ -935,13 +935,16 @@ void orc_ext_profiles(const orc_cfg* c, const double* ext, double* out)
 /* Quantities derived from the plane means:
  *   out[0] C = <rho u_z T_sa>_V / sqrt(<(rho u_z)^2>_V <T_sa^2>_V)   (Eq. Corr_Ra)
  *   out[1] <(rho u_z)^2>_V, out[2] <T_sa^2>_V
- *   out[3] lambda_b, out[4] lambda_t: thermal boundary-layer thicknesses.
- *          Reading of "where the slope of <T>_A approximates the adiabatic
- *          gradient -D": from the bottom plate up, lambda_b is the height z_k
- *          of the first plane whose slope to the plane above,
- *          (<T>_{k+1} - <T>_k)/(z_{k+1} - z_k), is no steeper than -D; from the
- *          top plate down, lambda_t = 1 - z_k of the first plane whose slope
- *          from the plane below is no steeper than -D; 1 if there is none.
+ *   out[3] lambda_b, out[4] lambda_t: thermal boundary-layer thicknesses,
+ *          read as the classical tangent construction: the depth at which the
+ *          plate tangent of <T_sa>_A meets the adiabatic bulk, i.e. the
+ *          superadiabatic drop across the layer over the plate gradient,
+ *          lambda_b = (Tb - f_0) / (d<T_sa>_A/dz at z = 0),
+ *          lambda_t = (f_K - Tb) / (d<T_sa>_A/dz at z = 1),
+ *          with the plate derivatives of the plate Nusselt numbers (the
+ *          three-plane quadratic) and Tb the trapezoid mean of <T_sa>_A over
+ *          the planes with 1/4 <= z <= 3/4 (the bulk, where <T>_A follows
+ *          the adiabat).
  *   out[5..8] <F_n>, <F_p>, <F_b>, <F_v> over the interior planes (weights
  *          w_k of the interior planes, normalised by their sum)
  *   out[9] max over nodes of r = K_e / I_e = (rho u^2/2) / (rho C_v T) = b u^2 / (2 T)
@@ -985,12 +988,27 @@ void orc_extended(const orc_cfg* c, const double* ext, double* out, long long* h
     out[1] = s_m2 / vol;
     out[2] = s_t2 / vol;
     out[0] = (s_conv / vol) / sqrt(out[1] * out[2]);
-    out[3] = 1.0;
-    for (int k = 0; k < K; k++)
-        if ((TA[k + 1] - TA[k]) / (p.z[k + 1] - p.z[k]) >= -p.D) { out[3] = p.z[k]; break; }
-    out[4] = 1.0;
-    for (int k = K; k > 0; k--)
-        if ((TA[k] - TA[k - 1]) / (p.z[k] - p.z[k - 1]) >= -p.D) { out[4] = 1.0 - p.z[k]; break; }
+    {
+        double sa[3], sb[3], tb = 0.0, tw = 0.0;
+        for (int q = 0; q < 3; q++) {
+            sa[q] = TA[q] - (1.0 - p.D * p.z[q]);
+            sb[q] = TA[K - q] - (1.0 - p.D * p.z[K - q]);
+        }
+        for (int k = 0; k <= K; k++)
+            if (p.z[k] >= 0.25 && p.z[k] <= 0.75) {
+                double wk = p.stretched ? p.w[k] : 1.0;
+                tb += wk * (TA[k] - (1.0 - p.D * p.z[k]));
+                tw += wk;
+            }
+        tb /= tw;
+        double h1 = p.z[1] - p.z[0], h2 = p.z[2] - p.z[1];
+        double db = -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * sa[0] + (h1 + h2) / (h1 * h2) * sa[1] - h1 / (h2 * (h1 + h2)) * sa[2];
+        h1 = p.z[K] - p.z[K - 1];
+        h2 = p.z[K - 1] - p.z[K - 2];
+        double dtp = (2.0 * h1 + h2) / (h1 * (h1 + h2)) * sb[0] - (h1 + h2) / (h1 * h2) * sb[1] + h1 / (h2 * (h1 + h2)) * sb[2];
+        out[3] = (tb - sa[0]) / db;
+        out[4] = (sb[0] - tb) / dtp;
+    }
     for (int q = 0; q < 4; q++) out[5 + q] = f[q] / wsum;
     double rmax = 0.0, bw = (hi - lo) / nbins;
     for (int q = 0; q < nbins; q++) hist[q] = 0;

@@ -733,12 +733,32 @@ int cm_extended(cm_ext* out, long long* hist_out, int nbins, double log10_lo, do
     r.rho_uz_sq = s_m2 / vol;
     r.Tsa_sq = s_t2 / vol;
     r.C = (s_conv / vol) / std::sqrt(r.rho_uz_sq * r.Tsa_sq);
-    r.lambda_b = 1.0;
-    for (int k = 0; k < K; ++k)
-        if ((TA[k + 1] - TA[k]) / (z[k + 1] - z[k]) >= -c->prm.D) { r.lambda_b = z[k]; break; }
-    r.lambda_top = 1.0;
-    for (int k = K; k > 0; --k)
-        if ((TA[k] - TA[k - 1]) / (z[k] - z[k - 1]) >= -c->prm.D) { r.lambda_top = 1.0 - z[k]; break; }
+    {
+        // boundary layers: the plate tangent of <T_sa>_A against the bulk mean
+        // of <T_sa>_A over 1/4 <= z <= 3/4 (trapezoid weights)
+        const double D = c->prm.D;
+        double sa[3], sb[3], tb = 0.0, tw = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            sa[q] = TA[q] - (1.0 - D * z[q]);
+            sb[q] = TA[K - q] - (1.0 - D * z[K - q]);
+        }
+        for (int k = 0; k <= K; ++k)
+            if (z[k] >= 0.25 && z[k] <= 0.75) {
+                const double wk = st ? wgt(k) : 1.0;
+                tb += wk * (TA[k] - (1.0 - D * z[k]));
+                tw += wk;
+            }
+        tb /= tw;
+        double h1 = z[1] - z[0], h2 = z[2] - z[1];
+        const double db = -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * sa[0] + (h1 + h2) / (h1 * h2) * sa[1] -
+                          h1 / (h2 * (h1 + h2)) * sa[2];
+        h1 = z[K] - z[K - 1];
+        h2 = z[K - 1] - z[K - 2];
+        const double dtp = (2.0 * h1 + h2) / (h1 * (h1 + h2)) * sb[0] - (h1 + h2) / (h1 * h2) * sb[1] +
+                           h1 / (h2 * (h1 + h2)) * sb[2];
+        r.lambda_b = (tb - sa[0]) / db;
+        r.lambda_top = (sb[0] - tb) / dtp;
+    }
     r.F_n = f[0] / wsum;
     r.F_p = f[1] / wsum;
     r.F_b = f[2] / wsum;

@@ -6,7 +6,9 @@ Both sides evaluate every quantity in FP64 from the same state (FP32 states
 widened), in the same order of operations per node; only the order of the
 sums over nodes differs.  Bars: plane means and derived quantities <= 1e-12
 relative (1e-12 of the largest plane value for profiles that cross zero);
-boundary-layer heights and histogram counts exactly equal.
+boundary layers 1e-9 relative (a plate derivative amplifies the rounding of
+the plane means, as for the plate Nusselt numbers); histogram counts exactly
+equal.
 """
 import math
 
@@ -31,7 +33,7 @@ def compare(got_prof, want_prof, got_ext, want_ext, got_hist, want_hist):
     for key, g in got_ext.items():
         w = want_ext[m.get(key, key)]
         if key.startswith("lambda"):
-            assert g == w, (key, g, w)
+            assert abs(g - w) <= 1e-9 * abs(w), (key, g, w)
         else:
             assert abs(g - w) <= 1e-12 * max(abs(w), 1e-300), (key, g, w)
     assert np.array_equal(got_hist, want_hist)
@@ -77,7 +79,7 @@ def test_extended_3d_matches_oracle(kind):
 
 def test_conduction_state_has_no_flow_terms():
     """At rest: F_n = F_v = 0 exactly, every node at r = 0 (bin 0), C undefined
-    (0/0), no adiabatic layer (lambda = 1)."""
+    (0/0); T_sa = -eps z is linear, so the tangent construction gives 1/2."""
     cfg = O.Config(nx=64, nz=33, Ra=1e6, pert_amp=0.0)
     s = solver_for(cfg)
     try:
@@ -87,7 +89,7 @@ def test_conduction_state_has_no_flow_terms():
         s.close()
     assert np.all(prof["F_n"] == 0) and np.all(prof["F_v"] == 0)
     assert math.isnan(ext["C"]) and ext["r_max"] == 0.0
-    assert ext["lambda_b"] == 1.0 and ext["lambda_top"] == 1.0
+    assert abs(ext["lambda_b"] - 0.5) < 1e-9 and abs(ext["lambda_top"] - 0.5) < 1e-9
     assert hist[0] == cfg.nx * cfg.nz and hist[1:].sum() == 0
 
 

@@ -330,3 +330,27 @@ def test_full_size_3d_fp32_y_invariant_matches_2d_oracle():
     z = O.znodes(c2)
     m0 = np.trapezoid(X3[0].mean(axis=(1, 2)), z)
     assert abs(np.trapezoid(got[0].mean(axis=(1, 2)), z) - m0) <= 1e-6 * m0
+
+
+def test_checkpoint_carries_the_planes(tmp_path):
+    """cm_save / cm_load: the checkpoint's parameter hash covers the plane
+    heights of a stretched grid; a context on other planes (or uniform ones)
+    refuses it, one on the same planes restores the state bit for bit."""
+    import paper_2411_10372_gb300 as cm
+    cfg = O.Config(nx=64, nz=17, Ra=1e6, zstretch=1.5)
+    s = solver_for(cfg)
+    s.step(3)
+    X = s.state()
+    path = str(tmp_path / "st.ckpt")
+    cm.cm_save(path)
+    s.close()
+    for other in (O.Config(nx=64, nz=17, Ra=1e6), O.Config(nx=64, nz=17, Ra=1e6, zstretch=1.6)):
+        s = solver_for(other)
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_load(path)
+        assert e.value.code == cm.CM_EBADCKPT
+        s.close()
+    s = solver_for(cfg)
+    cm.cm_load(path)
+    assert np.array_equal(s.state(), X)
+    s.close()

@@ -91,9 +91,9 @@ MUTANTS = [
     ("ext_fv_stokes_factor", "(2.0 + p.stokes) * dzz", "(1.0 + p.stokes) * dzz"),
     ("ext_correlation_no_sqrt", "out[0] = (s_conv / vol) / sqrt(out[1] * out[2]);",
      "out[0] = (s_conv / vol) / (out[1] * out[2]);"),
-    ("ext_bl_threshold_sign", "if ((TA[k + 1] - TA[k]) / (p.z[k + 1] - p.z[k]) >= -p.D)",
-     "if ((TA[k + 1] - TA[k]) / (p.z[k + 1] - p.z[k]) >= p.D)"),
-    ("ext_bl_top_index", "out[4] = 1.0 - p.z[k]; break;", "out[4] = 1.0 - p.z[k - 1]; break;"),
+    ("ext_bl_bulk_band", "if (p.z[k] >= 0.25 && p.z[k] <= 0.75) {", "if (p.z[k] >= 0.0 && p.z[k] <= 0.75) {"),
+    ("ext_bl_top_sign", "out[4] = (sb[0] - tb) / dtp;", "out[4] = (tb - sb[0]) / dtp;"),
+    ("ext_bl_bottom_plane", "out[3] = (tb - sa[0]) / db;", "out[3] = (tb - sa[1]) / db;"),
     ("ext_r_missing_half", "double r = p.b * u2 / (2.0 * T[n]);", "double r = p.b * u2 / T[n];"),
 ]
 
