@@ -221,19 +221,6 @@ __device__ __forceinline__ void ext_prims(const R* X, long long fs, int ndim, lo
     T = A.b * (E / rho - 0.5 * ((ux * ux + uy * uy) + uz * uz) - A.g * z);
 }
 
-// derivative and second derivative at plane k of the quadratic through
-// planes k-1, k, k+1 (central differences on uniform planes)
-__device__ __forceinline__ double ext_dz(const double* zt, int k, double fm, double f0, double fp)
-{
-    const double hm = zt[k] - zt[k - 1], hp = zt[k + 1] - zt[k];
-    return (hm * hm * fp - hp * hp * fm + (hp * hp - hm * hm) * f0) / (hm * hp * (hm + hp));
-}
-__device__ __forceinline__ double ext_dzz(const double* zt, int k, double fm, double f0, double fp)
-{
-    const double hm = zt[k] - zt[k - 1], hp = zt[k + 1] - zt[k];
-    return 2.0 * ((fp - f0) / hp - (f0 - fm) / hm) / (hm + hp);
-}
-
 // FP64 primitives of every node, once: P[q * n + node], q = 0..4 rho, u_x,
 // u_y, u_z, T; node = (k ny + j) nx + i (dense)
 template <class R>
@@ -255,6 +242,8 @@ __global__ void ext_prims_all(const R* X, Coef<R> C, ExtArgs A, double* P)
 }
 
 // One block per plane k: FP64 sums over the plane of the z-momentum terms
+// (z derivatives: derivative and second derivative at plane k of the
+// quadratic through planes k-1, k, k+1; central on uniform planes)
 //   F_n = rho (u . grad) u_z, F_p = -dp/dz, F_b = rho g,
 //   F_v = mu (d_xx u_z + d_yy u_z + (2 + s) d_zz u_z + (1 + s)(d_x d_z u_x + d_y d_z u_y))
 // (interior planes; 0 on the plates), of (rho u_z)^2, T_sa^2, rho u_z T_sa
@@ -275,6 +264,21 @@ static __global__ void __launch_bounds__(kDiagThreads) ext_planes(int nx, int ny
     double v[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
     double tsum[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
     auto at = [&](int kk, int j, int i) { return ((long long)kk * ny + j) * nx + i; };
+    // the plane's spacings and the reciprocals of the three-plane derivatives'
+    // denominators (one division each per block instead of per node)
+    double hm = 1.0, hp = 1.0, iden = 0.0, ihm = 0.0, ihp = 0.0, ihs = 0.0;
+    if (inner) {
+        hm = A.zt[k] - A.zt[k - 1];
+        hp = A.zt[k + 1] - A.zt[k];
+        iden = 1.0 / (hm * hp * (hm + hp));
+        ihm = 1.0 / hm;
+        ihp = 1.0 / hp;
+        ihs = 1.0 / (hm + hp);
+    }
+    auto dz = [&](double fm, double f0, double fp) { return (hm * hm * fp - hp * hp * fm + (hp * hp - hm * hm) * f0) * iden; };
+    auto dzz = [&](double fm, double f0, double fp) { return 2.0 * ((fp - f0) * ihp - (f0 - fm) * ihm) * ihs; };
+    const double i2dx = 1.0 / (2.0 * A.dx), idx2 = 1.0 / (A.dx * A.dx);
+    const double i2dy = 1.0 / (2.0 * A.dy), idy2 = 1.0 / (A.dy * A.dy);
     for (long long n = threadIdx.x; n < (long long)nx * ny; n += kDiagThreads) {
         const int i = (int)(n % nx), j = (int)(n / nx);
         const long long c0 = at(k, j, i);
@@ -297,28 +301,26 @@ static __global__ void __launch_bounds__(kDiagThreads) ext_planes(int nx, int ny
         const int ip = (i + 1) % nx, im = (i - 1 + nx) % nx;
         const long long zm = at(k - 1, j, i), zp = at(k + 1, j, i);
         const double uzp = Puz[at(k, j, ip)], uzm = Puz[at(k, j, im)];
-        const double dxuz = (uzp - uzm) / (2.0 * A.dx);
-        const double dxx = (uzp - 2.0 * uz + uzm) / (A.dx * A.dx);
-        const double dzuz = ext_dz(A.zt, k, Puz[zm], uz, Puz[zp]);
-        const double dzz = ext_dzz(A.zt, k, Puz[zm], uz, Puz[zp]);
+        const double dxuz = (uzp - uzm) * i2dx;
+        const double dxx = (uzp - 2.0 * uz + uzm) * idx2;
+        const double dzuz = dz(Puz[zm], uz, Puz[zp]);
+        const double dzzu = dzz(Puz[zm], uz, Puz[zp]);
         // d_x d_z u_x: x-central of the z derivatives at columns i +- 1
-        const double dxdzux = (ext_dz(A.zt, k, Pux[at(k - 1, j, ip)], Pux[at(k, j, ip)], Pux[at(k + 1, j, ip)]) -
-                               ext_dz(A.zt, k, Pux[at(k - 1, j, im)], Pux[at(k, j, im)], Pux[at(k + 1, j, im)])) /
-                              (2.0 * A.dx);
+        const double dxdzux = (dz(Pux[at(k - 1, j, ip)], Pux[at(k, j, ip)], Pux[at(k + 1, j, ip)]) -
+                               dz(Pux[at(k - 1, j, im)], Pux[at(k, j, im)], Pux[at(k + 1, j, im)])) * i2dx;
         double dyuz = 0.0, dyy = 0.0, dydzuy = 0.0;
         if (ndim == 3) {
             const int jp = (j + 1) % ny, jm = (j - 1 + ny) % ny;
             const double uyp_ = Puz[at(k, jp, i)], uym_ = Puz[at(k, jm, i)];
-            dyuz = (uyp_ - uym_) / (2.0 * A.dy);
-            dyy = (uyp_ - 2.0 * uz + uym_) / (A.dy * A.dy);
-            dydzuy = (ext_dz(A.zt, k, Puy[at(k - 1, jp, i)], Puy[at(k, jp, i)], Puy[at(k + 1, jp, i)]) -
-                      ext_dz(A.zt, k, Puy[at(k - 1, jm, i)], Puy[at(k, jm, i)], Puy[at(k + 1, jm, i)])) /
-                     (2.0 * A.dy);
+            dyuz = (uyp_ - uym_) * i2dy;
+            dyy = (uyp_ - 2.0 * uz + uym_) * idy2;
+            dydzuy = (dz(Puy[at(k - 1, jp, i)], Puy[at(k, jp, i)], Puy[at(k + 1, jp, i)]) -
+                      dz(Puy[at(k - 1, jm, i)], Puy[at(k, jm, i)], Puy[at(k + 1, jm, i)])) * i2dy;
         }
         v[0] += rho * ((ux * dxuz + uy * dyuz) + uz * dzuz);
-        v[1] += -ext_dz(A.zt, k, A.a * Pr[zm] * PT[zm], A.a * rho * T, A.a * Pr[zp] * PT[zp]);
+        v[1] += -dz(A.a * Pr[zm] * PT[zm], A.a * rho * T, A.a * Pr[zp] * PT[zp]);
         v[2] += rho * A.g;
-        v[3] += A.mu * ((dxx + dyy) + (2.0 + A.stokes) * dzz + (1.0 + A.stokes) * (dxdzux + dydzuy));
+        v[3] += A.mu * ((dxx + dyy) + (2.0 + A.stokes) * dzzu + (1.0 + A.stokes) * (dxdzux + dydzuy));
     }
     block_sum_q(v, scratch + (size_t)k * 16);
     __syncthreads();  // block_sum_q's shared staging is reused
