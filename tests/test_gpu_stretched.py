@@ -73,11 +73,12 @@ def test_single_sweeps_fp64(nx, nz, name, grid, tvd):
     s.close()
 
 
-@pytest.mark.parametrize("nx,nz", [(30, 17), (64, 33), (250, 65), (122, 41)])
+@pytest.mark.parametrize("nx,nz", [(30, 17), (64, 33), (250, 65), (122, 41), (29, 17), (57, 33)])
 @pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
 def test_single_sweeps_fp32(nx, nz, name, grid):
-    """FP32 sweeps (packed two-column kernels for even nx) on a stirred state
-    rounded to FP32, against the oracle on the same rounded input."""
+    """FP32 sweeps on a stirred state rounded to FP32, against the oracle on
+    the same rounded input: packed two-column kernels for even nx, the
+    one-column kernels for odd nx."""
     cfg = cfg_for(nx, nz, grid, Ra=1e5, dt_fixed=1e-5)
     z = O.znodes(cfg)
     X = stirred_on(cfg, z, seed=nx * 7 + nz).astype(np.float32).astype(np.float64)
