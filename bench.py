@@ -488,7 +488,7 @@ def run_case(args):
     if case in ("2d_fp32", "2d_fp64", "3d_fp32", "3d_fp64"):
         prec = case[3:]
         if case.startswith("3d"):
-            s = cm.Solver(args.nx, args.nz, RA3, PR, GAMMA, ny=args.ny, ndim=3, precision=prec)
+            s = cm.Solver(args.nx, args.nz, RA3, PR, GAMMA, ny=args.ny, ndim=3, precision=prec, zstretch=args.zstretch)
         else:
             s = cm.Solver(args.nx, args.nz, RA, PR, GAMMA, precision=prec, zstretch=args.zstretch)
         s.step(args.warmup)
@@ -496,6 +496,13 @@ def run_case(args):
         d = s.sample()
         s.close()
         out.update(nx=args.nx, ny=args.ny if case.startswith("3d") else 1, nz=args.nz, status=d["status"])
+    elif case == "extended":
+        s = cm.Solver(args.nx, args.nz, RA, PR, GAMMA, precision="fp32", zstretch=args.zstretch)
+        s.step(args.warmup)
+        for _ in range(max(1, args.steps)):
+            e, hist = s.extended(96, -14.0, 0.0)
+        s.close()
+        out.update(nx=args.nx, nz=args.nz, C=e["C"], hist_nodes=int(hist.sum()))
     elif case == "batch":
         rng = np.random.default_rng(2024)
         u, u2 = rng.random(64), rng.random(64)
@@ -535,8 +542,8 @@ def main():
     ap.add_argument("--nz", type=int, default=NZ, help="grid override (profiling captures only)")
     ap.add_argument("--ny", type=int, default=512, help="3D grid override (--case only)")
     ap.add_argument("--only-fp32", action="store_true", help="time the FP32 steps only (profiling captures)")
-    ap.add_argument("--zstretch", type=float, default=0.0, help="tanh z-grid for --case 2d_* (profiling captures)")
-    ap.add_argument("--case", choices=["2d_fp32", "2d_fp64", "3d_fp32", "3d_fp64", "batch", "adjoint"],
+    ap.add_argument("--zstretch", type=float, default=0.0, help="tanh z-grid for --case 2d_*, 3d_*, extended (profiling captures)")
+    ap.add_argument("--case", choices=["2d_fp32", "2d_fp64", "3d_fp32", "3d_fp64", "batch", "adjoint", "extended"],
                     help="run one kernel family untimed (profiling captures)")
     args = ap.parse_args()
     if args.case:
