@@ -19,8 +19,9 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     if (!bz) {
         cudaFuncSetAttribute(sweep_z2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         cudaFuncSetAttribute(sweep_x2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        cudaFuncSetAttribute(sweep_z2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        cudaFuncSetAttribute(sweep_x2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        // stretched kernels: the ring plus the warps' plane caches
+        cudaFuncSetAttribute(sweep_z2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes + 96 * 1024);
+        cudaFuncSetAttribute(sweep_x2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes + 96 * 1024);
         bz = blocks_per_sm(sweep_z2d_x2, kRingBytes);
         bx = blocks_per_sm(sweep_x2d_x2, kRingBytes);
     }
@@ -30,11 +31,12 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     const long long warps = (long long)io.nstrips * nsegs;
     const int blocks = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
     const dim3 g(blocks), b(kWarpsPerBlock * 32);
+    const size_t cache = (size_t)kWarpsPerBlock * plane_cap2(io.seg_rows) * sizeof(float);
     if (dir == 2)
-        return C.zp ? launch_pdl(true, sweep_z2d_x2s, g, b, kRingBytes, s, io, C, sc)
+        return C.zp ? launch_pdl(true, sweep_z2d_x2s, g, b, kRingBytes + 5 * cache, s, io, C, sc)
                     : launch_pdl(true, sweep_z2d_x2, g, b, kRingBytes, s, io, C, sc);
     if (dir == 0)
-        return C.zp ? launch_pdl(true, sweep_x2d_x2s, g, b, kRingBytes, s, io, C, sc)
+        return C.zp ? launch_pdl(true, sweep_x2d_x2s, g, b, kRingBytes + 2 * cache, s, io, C, sc)
                     : launch_pdl(true, sweep_x2d_x2, g, b, kRingBytes, s, io, C, sc);
     return cudaErrorInvalidValue;
 }

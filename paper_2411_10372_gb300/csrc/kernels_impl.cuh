@@ -151,10 +151,18 @@ static cudaError_t sweep3(int dir, const R* in, R* out, const R* zt, const Coef<
                  : pick_segment3((long long)io.nstrips * groups, io.nmarch, bps[dir], sm_count());
     const int nsegs = (io.nmarch + io.seg - 1) / io.seg;
     const dim3 grid(io.nstrips, groups, nsegs), b(kNW3 * 32);
-    if (C.zp) {  // stretched z-grid
-        if (dir == 2) return launch_pdl(false, sweep3d_march<R, 2, kNW3, true>, grid, b, 0, s, io, C, sc);
+    if (C.zp) {  // stretched z-grid: the z and x kernels cache the segment's plane metric in shared memory
+        static bool attr = false;
+        if (!attr) {
+            const int lim = 96 * 1024;
+            cudaFuncSetAttribute(sweep3d_march<R, 2, kNW3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+            cudaFuncSetAttribute(sweep3d_x<R, kNW3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+            attr = true;
+        }
+        if (dir == 2)
+            return launch_pdl(false, sweep3d_march<R, 2, kNW3, true>, grid, b, plane_cache_bytes<R>(io.seg, 4), s, io, C, sc);
         if (dir == 1) return launch_pdl(false, sweep3d_march<R, 1, kNW3, true>, grid, b, 0, s, io, C, sc);
-        return launch_pdl(false, sweep3d_x<R, kNW3, true>, grid, b, 0, s, io, C, sc);
+        return launch_pdl(false, sweep3d_x<R, kNW3, true>, grid, b, plane_cache_bytes<R>(io.seg, 2), s, io, C, sc);
     }
     if (dir == 2) return launch_pdl(false, sweep3d_march<R, 2, kNW3>, grid, b, 0, s, io, C, sc);
     if (dir == 1) return launch_pdl(false, sweep3d_march<R, 1, kNW3>, grid, b, 0, s, io, C, sc);

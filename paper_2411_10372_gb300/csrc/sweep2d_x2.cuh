@@ -192,6 +192,18 @@ struct RowRing {
     }
 };
 
+// Stretched z-grid: each warp copies the metric of the planes its segment
+// touches (ks - 3 .. ke + 1, clamped) into its own slice of shared memory,
+// after the row ring, so that every row reads it by broadcast.  NV values
+// per plane; entry e holds plane clamp(ks - 3 + e).
+constexpr int kPlaneBack2 = 3;
+__host__ __device__ constexpr int plane_cap2(int seg_rows) { return seg_rows + kPlaneBack2 + 2; }
+template <int NV>
+__device__ __forceinline__ float* plane_cache2(f2* ring_mem, int seg_rows)
+{
+    return reinterpret_cast<float*>(ring_mem + kRing * 4 * kThreads2) + (threadIdx.x >> 5) * plane_cap2(seg_rows) * NV;
+}
+
 // A segment is "interior" when none of its pipeline rows (ks-5 .. ke+4,
 // prefetch included) touches a plate or leaves the grid: its steps need no
 // plate rules, no row clamping and no range tests.
@@ -251,8 +263,22 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
 
     const RowRing ring{ring_mem + threadIdx.x};
     auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
+    // stretched: this warp's plane cache {1/hp, 1/w, rp, rm, z}
+    float* pc = ST ? plane_cache2<5>(ring_mem, seg_rows) : nullptr;
+    if constexpr (ST) {
+        for (int e = lane; e < ke - ks + kPlaneBack2 + 2; e += 32) {
+            const Plane<float>& P = C.zp[min(max(ks - kPlaneBack2 + e, 0), nz - 1)];
+            pc[e * 5 + 0] = P.ihp;
+            pc[e * 5 + 1] = P.iw;
+            pc[e * 5 + 2] = P.rp;
+            pc[e * 5 + 3] = P.rm;
+            pc[e * 5 + 4] = P.z;
+        }
+        __syncwarp();
+    }
+    auto pv = [&](int k, int q) { return pc[(k - (ks - kPlaneBack2)) * 5 + q]; };
     auto gz_of = [&](int j) {
-        if constexpr (ST) return bc(-C.g * __ldg(&C.zp[min(max(j, 0), nz - 1)].z));
+        if constexpr (ST) return bc(-C.g * pv(j, 4));
         else return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz));
     };
     // the first step is j0 = ks - 1 (primed with row ks - 2): no output row
@@ -293,7 +319,7 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         cp_async_wait_ring();
         const S2 X0 = ring.take(t % kRing);
         f2 gz0;
-        if constexpr (ST) gz0 = edge ? gz_of(j) : bc(-C.g * __ldg(&C.zp[j].z));
+        if constexpr (ST) gz0 = gz_of(j);
         else gz0 = edge ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
 
         f2 ux0, uz0, T0, p0;
@@ -302,14 +328,12 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
 
         // row m = j-1: F^n (forward z, central x), X^P, F^P (backward z)
         const int m = j - 1;
-        // stretched: planes m and c = m - 1 (clamped on the edge path)
-        const int mc = ST ? (edge ? min(max(m, 0), nz - 1) : m) : 0;
-        const int cc = ST ? (edge ? min(max(m - 1, 0), nz - 1) : m - 1) : 0;
+        // stretched: planes m and c = m - 1 from the warp's cache
         f2 lam_m = lam, idz_f = idz, idz_b = idz;  // Delta/w_m, 1/(spacing above m), 1/(spacing below m)
         if constexpr (ST) {
-            lam_m = bc(Df * __ldg(&C.zp[mc].iw));
-            idz_f = bc(__ldg(&C.zp[mc].ihp));
-            idz_b = bc(__ldg(&C.zp[cc].ihp));
+            lam_m = bc(Df * pv(m, 1));
+            idz_f = bc(pv(m, 0));
+            idz_b = bc(pv(m - 1, 0));
         }
         const f2 dxux1 = mul2(sub2(right_of(ux1), left_of(ux1)), i2dx);
         const f2 dxuz1 = mul2(sub2(right_of(uz1), left_of(uz1)), i2dx);
@@ -349,7 +373,7 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         const int c = j - 2;
         S2 Dn = {z0, z0, z0, z0};
         if (ramp == 0 && (!edge || (c >= 1 && c <= nz - 3))) {
-            const f2 lamh_c = ST ? bc(Df * __ldg(&C.zp[cc].ihp)) : lam;  // Delta / (spacing of interface c, c+1)
+            const f2 lamh_c = ST ? bc(Df * pv(c, 0)) : lam;  // Delta / (spacing of interface c, c+1)
             Dn = scale2(tvd_G2(ss2, ss1, dd1, mul2(lamh_c, max2(A2, A1)), C.tvd_form), d1);
         }
 
@@ -358,7 +382,7 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
             S2 Xn;
             if (!edge || (c >= 1 && c <= nz - 2)) {
                 if constexpr (ST) {
-                    const f2 hl = bc(0.5f * Df * __ldg(&C.zp[cc].iw)), rp = bc(__ldg(&C.zp[cc].rp));
+                    const f2 hl = bc(0.5f * Df * pv(c, 1)), rp = bc(pv(c, 2));
                     Xn.r = fma2(rp, Dn.r, fnma2(hl, FP1.r, H.r));
                     Xn.mx = fma2(rp, Dn.mx, fnma2(hl, FP1.mx, H.mx));
                     Xn.mz = fma2(rp, Dn.mz, fnma2(hl, FP1.mz, H.mz));
@@ -383,7 +407,7 @@ __device__ __forceinline__ void z2_body(const float* __restrict__ in, float* __r
         if (ramp != 0) {
         } else if (interior_m) {
             if constexpr (ST) {
-                const f2 rm = bc(__ldg(&C.zp[mc].rm));
+                const f2 rm = bc(pv(m, 3));
                 H.r = fnma2(rm, Dn.r, mul2(half, fma2(lam_m, FP1.r, add2(XP1.r, Xm1.r))));
                 H.mx = fnma2(rm, Dn.mx, mul2(half, fma2(lam_m, FP1.mx, add2(XP1.mx, Xm1.mx))));
                 H.mz = fnma2(rm, Dn.mz, mul2(half, fma2(lam_m, FP1.mz, fma2(mDg, XP1.r, add2(XP1.mz, Xm1.mz)))));
@@ -491,8 +515,19 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
     if (ks < nz) {
         const RowRing ring{ring_mem + threadIdx.x};
         auto row_off = [&](int j) { return min(max(j, 0), nz - 1) * pitch + ic; };
+        // stretched: this warp's plane cache {1/sc, z}
+        float* pc = ST ? plane_cache2<2>(ring_mem, seg_rows) : nullptr;
+        if constexpr (ST) {
+            for (int e = lane; e < ke - ks + kPlaneBack2 + 2; e += 32) {
+                const Plane<float>& P = C.zp[min(max(ks - kPlaneBack2 + e, 0), nz - 1)];
+                pc[e * 2 + 0] = P.isc;
+                pc[e * 2 + 1] = P.z;
+            }
+            __syncwarp();
+        }
+        auto pv = [&](int k, int q) { return pc[(k - (ks - kPlaneBack2)) * 2 + q]; };
         auto gz_of = [&](int j) {
-            if constexpr (ST) return bc(-C.g * __ldg(&C.zp[min(max(j, 0), nz - 1)].z));
+            if constexpr (ST) return bc(-C.g * pv(j, 1));
             else return bc(-C.g * ((float)min(max(j, 0), nz - 1) * C.hz));
         };
         const f2 idx_ = bc(C.inv_dx), i2dz = bc(C.inv_2dz);
@@ -531,7 +566,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
             cp_async_wait_ring();
             const S2 X0 = ring.take(t % kRing);
             f2 gz0;
-            if constexpr (ST) gz0 = edge ? gz_of(j) : bc(-C.g * __ldg(&C.zp[j].z));
+            if constexpr (ST) gz0 = gz_of(j);
             else gz0 = edge ? gz_of(j) : bc(-C.g * ((float)j * C.hz));
             f2 ux0, uz0, T0, p0;
             prims2(X0, gz0, C, ux0, uz0, T0, p0);
@@ -541,7 +576,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
             f2 i2dz_m = i2dz, i2dz_c = i2dz;  // 1/(central z span) of planes m and c = m - 1
             float isc_m = 0.f;
             if constexpr (ST) {
-                isc_m = __ldg(&C.zp[edge ? min(max(m, 0), nz - 1) : m].isc);
+                isc_m = pv(m, 0);
                 i2dz_m = bc(isc_m);
                 i2dz_c = bc(isc_prev);
             }

@@ -46,6 +46,33 @@ __device__ __forceinline__ int wrap(int a, int n)
     return a < 0 ? a + n : a;
 }
 
+// Stretched z-grid: the per-plane metric of the planes a block's segment
+// touches (ks - 4 .. ke, clamped), copied once into shared memory so that
+// every row reads it by broadcast (all warps of a block march the same
+// rows).  NV values per plane; entry e holds plane clamp(ks - 4 + e).
+constexpr int kPlaneBack = 4;
+template <class R, int NV>
+__device__ __forceinline__ void fill_planes(R* pz, const Coef<R>& C, int ks, int ke, bool march_z)
+{
+    const int n = ke - ks + kPlaneBack + 1;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const Plane<R>& P = C.zp[min(max(ks - kPlaneBack + e, 0), C.nz - 1)];
+        if (march_z) {
+            // FP64: the spacings (the exact path divides); FP32: reciprocals
+            pz[e * NV + 0] = kExact<R> ? P.hp : P.ihp;
+            pz[e * NV + 1] = kExact<R> ? P.w : P.iw;
+            pz[e * NV + 2] = P.rp;
+            pz[e * NV + 3] = P.rm;
+        } else {
+            pz[e * NV + 0] = kExact<R> ? P.sc : P.isc;
+            pz[e * NV + 1] = kExact<R> ? P.hmin : P.ihmin;
+        }
+    }
+    __syncthreads();
+}
+template <class R>
+inline size_t plane_cache_bytes(int seg, int nv) { return (size_t)(seg + kPlaneBack + 1) * nv * sizeof(R); }
+
 template <int NW>
 __device__ __forceinline__ int halo_role(int w)
 {
@@ -68,6 +95,8 @@ __global__ void __launch_bounds__(NW * 32)
 sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 {
     pdl_enter();
+    extern __shared__ unsigned char pz_raw[];
+    R* pz = reinterpret_cast<R*>(pz_raw);  // stretched L_z: plane cache (fill_planes)
     constexpr int WD = (AL == 2) ? 1 : 2;  // direction of the warps
     // [row parity][u_AL, u_W of X at row j; u_AL, u_W of X^P at row j-1][warp][lane]
     __shared__ R xs[2][4][NW][32];
@@ -115,6 +144,9 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
         sc.ctl->steps += 1.0;
     }
 
+    if constexpr (ST && AL == 2) fill_planes<R, 4>(pz, C, ks, ke, true);
+    auto pl = [&](int k, int q) -> R { return pz[(k - (ks - kPlaneBack)) * 4 + q]; };
+
     // memory offset of march row j: plane clamp(j) of row cwr (L_z), row
     // wrap(j) of plane cwr (L_y); rows are taken in order from j0 - 1 on
     const long long colbase = (AL == 2) ? (long long)cwr * pitch + ic : (long long)cwr * ny * pitch + ic;
@@ -160,11 +192,16 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
         // spacings along the march (stretched L_z: per plane) and the cell factor of row m
         R hf = h, ihf = (AL == 2) ? C.inv_dz : C.inv_dy, hb = hf, ihb = ihf, lam_m = lam;
         if constexpr (ST && AL == 2) {
-            const Plane<R>& Pm = C.zp[min(max(m, 0), nz - 1)];
-            const Plane<R>& Pb = C.zp[min(max(m - 1, 0), nz - 1)];
-            hf = Pm.hp; ihf = Pm.ihp;
-            hb = Pb.hp; ihb = Pb.ihp;
-            lam_m = lam_cell(Delta, Pm);
+            // spacing above m and below m, and Delta / w_m (FP64: spacings; FP32: reciprocals)
+            if constexpr (kExact<R>) {
+                hf = pl(m, 0);
+                hb = pl(m - 1, 0);
+                lam_m = Delta / pl(m, 1);
+            } else {
+                ihf = pl(m, 0);
+                ihb = pl(m - 1, 0);
+                lam_m = (R)Delta * pl(m, 1);
+            }
         }
         S3<R> F1 = zero, XP1 = Xm1;
         R ppu1[3] = {u1[0], u1[1], u1[2]}, ppT1 = T1, ppp1 = p1;
@@ -232,12 +269,15 @@ sweep3d_march(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
             const int c = j - 2;
             R lam_c = lam, hc = h, lamh_c = lam, rp_c = R(1), rm_c = R(1);
             if constexpr (ST && AL == 2) {
-                const Plane<R>& Pc = C.zp[min(max(c, 0), nz - 1)];
-                lam_c = lam_cell(Delta, Pc);
-                hc = Pc.hp;
-                lamh_c = (R)Delta * Pc.ihp;
-                rp_c = Pc.rp;
-                rm_c = Pc.rm;
+                if constexpr (kExact<R>) {
+                    hc = pl(c, 0);
+                    lam_c = Delta / pl(c, 1);
+                } else {
+                    lamh_c = (R)Delta * pl(c, 0);
+                    lam_c = (R)Delta * pl(c, 1);
+                }
+                rp_c = pl(c, 2);
+                rm_c = pl(c, 3);
             }
             S3<R> Xa = Xm2;
             if (AL == 2) {
@@ -327,6 +367,8 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
 {
     pdl_enter();
     __shared__ R xs[2][4][NW][32];
+    extern __shared__ unsigned char pz_raw[];
+    R* pz = reinterpret_cast<R*>(pz_raw);  // stretched grid: plane cache (fill_planes)
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int role = halo_role<NW>(w);
@@ -348,6 +390,8 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
         sc.ctl->t += dt;
         sc.ctl->steps += 1.0;
     }
+    if constexpr (ST) fill_planes<R, 2>(pz, C, ks, ke, false);
+    auto pl = [&](int k, int q) -> R { return pz[(k - (ks - kPlaneBack)) * 2 + q]; };
     const long long colbase = (long long)cwr * pitch + ic, rstride = (long long)ny * pitch;
     auto offk = [&](int k) { return colbase + (long long)min(max(k, 0), nz - 1) * rstride; };
     auto zk = [&](int k) { return io.zt[min(max(k, 0), nz - 1)]; };
@@ -382,8 +426,8 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
         const int m = j - 1;
         R scm = C.h2z, iscm = C.inv_2dz;  // central z span at row m
         if constexpr (ST) {
-            const Plane<R>& Pm = C.zp[min(max(m, 0), nz - 1)];
-            scm = Pm.sc; iscm = Pm.isc;
+            if constexpr (kExact<R>) scm = pl(m, 0);
+            else iscm = pl(m, 0);
         }
         S3<R> XP1 = Xm1;
         R pp1[3] = {u1[0], u1[1], u1[2]}, ppT1 = T1, ppp1 = p1;
@@ -424,9 +468,13 @@ sweep3d_x(Sweep3IO<R> io, Coef<R> C, SweepCtl sc)
             const int c = j - 2;
             R scc = C.h2z, iscc = C.inv_2dz, hzc = C.hz, ihzc = C.inv_dz;
             if constexpr (ST) {
-                const Plane<R>& Pc = C.zp[min(max(c, 0), nz - 1)];
-                scc = Pc.sc; iscc = Pc.isc;
-                hzc = Pc.hmin; ihzc = Pc.ihmin;
+                if constexpr (kExact<R>) {
+                    scc = pl(c, 0);
+                    hzc = pl(c, 1);
+                } else {
+                    iscc = pl(c, 0);
+                    ihzc = pl(c, 1);
+                }
             }
             R dq[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
 #pragma unroll
