@@ -548,7 +548,6 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
         f2 gz2 = gz1;  // -g z of row j-2
         const float* gnext = io.in + row_off(j0 + kRing - 1);
         float* gout = io.out + (long long)(j0 - 2) * pitch + i;  // used only when the row exists
-        float isc_prev = C.inv_2dz;  // stretched: 1/sc of plane m - 1 = c, carried
 
         // ramp 1: the first step of an interior segment, which skips what no
         // stored row uses (F^n, X^P, the TVD term and K of row ks - 2)
@@ -574,11 +573,9 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
             // row m = j-1
             const int m = j - 1;
             f2 i2dz_m = i2dz, i2dz_c = i2dz;  // 1/(central z span) of planes m and c = m - 1
-            float isc_m = 0.f;
             if constexpr (ST) {
-                isc_m = pv(m, 0);
-                i2dz_m = bc(isc_m);
-                i2dz_c = bc(isc_prev);
+                i2dz_m = bc(pv(m, 0));
+                i2dz_c = bc(pv(m - 1, 0));
             }
             S2 XP1 = Xm1, K1 = Xm1;  // plate rows pass through
             if (ramp != 1 && (!edge || (m >= 1 && m <= nz - 2))) {
@@ -645,7 +642,6 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
             ppux3 = ppux2; ppuz3 = ppuz2;
             XP2 = XP1; K2 = K1;
             ppux2 = ppux1; ppuz2 = ppuz1; ppT2 = ppT1; ppp2 = ppp1;
-            if constexpr (ST) isc_prev = isc_m;
         };
 
         // steps j0 .. ke+1: three that only fill the pipeline, then one output row
