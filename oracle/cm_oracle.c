@@ -25,8 +25,8 @@
  *   Sec. 3.1, "second-order forward and backward differences at the
  *     plates" ................................................ orc_diag() (plate Nu)
  *
- * Readings where the paper is silent, ambiguous or garbled (each listed in
- * the design doc with its justification):
+ * Readings where the paper is silent, ambiguous or garbled (each pinned by
+ * the tests named in oracle/__init__.py):
  *   - stress tensor: the divergence term enters with coefficient cfg->stokes
  *     (default -2/3, Stokes' hypothesis; the paper prints +2/3);
  *   - corrector uses F^P at both k+1 and k (the printed F^(n)_{k+1} is

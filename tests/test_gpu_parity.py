@@ -5,7 +5,8 @@ Bars (stated per output):
     Ra = 1e6 workload; single sweeps <= 1e-13.
   FP32 state: relative L2 per field <= 1e-5 after 100 steps for rho and E;
     the momentum fields are measured against the scale rho c (the sound
-    speed times density), since they start at zero.
+    speed times density), since they start at zero and a relative error of
+    a field near zero says nothing about the arithmetic.
   Diagnostics: relative 1e-12 (FP64) on the same state.
 Inputs are seeded and synthetic; the oracle never sees a CUDA result.
 """
