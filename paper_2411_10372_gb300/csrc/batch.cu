@@ -63,6 +63,7 @@ struct Batch {
     cudaGraphExec_t graph;
     int graph_steps;
     int cur;
+    bool const_coefs;   // coefficients in constant memory (at most kConstBoxes boxes)
 };
 
 Batch* g_batch = nullptr;
@@ -119,7 +120,7 @@ int launch(Batch& B, int dir, int first, int last, double Delta)
     L.first = first;
     L.last = last;
     L.Delta = Delta;
-    CKB(launch_sweep_batch(dir, L, dir == 2 ? B.nblk_z : B.nblk_x, B.stream));
+    CKB(launch_sweep_batch(dir, L, dir == 2 ? B.nblk_z : B.nblk_x, B.const_coefs, B.stream));
     B.launches++;
     return CM_OK;
 }
@@ -342,6 +343,13 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
         B->launches += 2;
     }
     if (!rc) rc = ck(cudaMemcpyAsync(B->d_boxes, desc.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice, B->stream), "upload");
+    B->const_coefs = nbox <= kConstBoxes;
+    if (!rc && B->const_coefs) {
+        std::vector<Coef<float>> coefs(nbox);
+        for (int b = 0; b < nbox; ++b) coefs[b] = desc[b].C;
+        rc = ck(set_batch_coefs(coefs.data(), nbox, B->stream), "coefficient upload");
+        if (!rc) rc = ck(cudaStreamSynchronize(B->stream), "coefficient upload");  // coefs is freed on return
+    }
     if (!rc) rc = upload_work(*B);
     if (!rc) rc = autotune(*B);
     if (!rc) rc = ck(cudaStreamSynchronize(B->stream), "batch init");

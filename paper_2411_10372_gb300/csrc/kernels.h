@@ -58,9 +58,14 @@ struct Launch {
 cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
                             const SweepCtl& sc, int seg_rows, cudaStream_t s);
 
-// one batched sweep over every box of a batch (kernels_f32.cu); nblocks from the work list
+// one batched sweep over every box of a batch (kernels_f32.cu); nblocks from
+// the work list; const_coefs: the boxes' coefficients were uploaded with
+// set_batch_coefs (batches of at most kConstBoxes boxes)
 struct BatchLaunch;
-cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, cudaStream_t s);
+constexpr int kConstBoxes = 256;
+cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool const_coefs, cudaStream_t s);
+// copy the coefficients of n <= kConstBoxes boxes to constant memory (kernels_f32.cu)
+cudaError_t set_batch_coefs(const Coef<float>* C, int n, cudaStream_t s);
 
 cudaError_t launch_diag_final(const double* scratch, const double* zt, const DiagFinal& F, DevCtl* ctl, cm_diag* rec,
                               cudaStream_t s);

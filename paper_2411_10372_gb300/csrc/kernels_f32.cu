@@ -41,18 +41,32 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, cudaStream_t s)
+cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool const_coefs, cudaStream_t s)
 {
     static bool init = false;
     if (!init) {
         cudaFuncSetAttribute(sweep_z2d_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         cudaFuncSetAttribute(sweep_x2d_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        cudaFuncSetAttribute(sweep_z2d_batch_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        cudaFuncSetAttribute(sweep_x2d_batch_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         init = true;
     }
-    if (dir == 2) sweep_z2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
-    else if (dir == 0) sweep_x2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
-    else return cudaErrorInvalidValue;
+    if (dir == 2) {
+        if (const_coefs) sweep_z2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+        else sweep_z2d_batch_smem<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+    } else if (dir == 0) {
+        if (const_coefs) sweep_x2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+        else sweep_x2d_batch_smem<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
+}
+
+cudaError_t set_batch_coefs(const Coef<float>* C, int n, cudaStream_t s)
+{
+    if (n < 1 || n > kConstBoxes) return cudaErrorInvalidValue;
+    return cudaMemcpyToSymbolAsync(c_box, C, n * sizeof(Coef<float>), 0, cudaMemcpyHostToDevice, s);
 }
 
 }  // namespace cm

@@ -703,16 +703,18 @@ sweep_x2d_x2s(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 
 // ---- batched ensemble: many independent boxes in one launch per sweep -----
 // Each warp takes one work item (box, strip, first row of its segment); the
-// four warps of a block always belong to the same box, whose coefficients
-// the block stages in shared memory.  Boxes step in lockstep (same sweep,
-// same dt slot parity) but each has its own dt, time and state buffers.
-__device__ __forceinline__ const BatchWork& batch_item(const BatchLaunch& L, Coef<float>& sC, SweepCtl& sc,
-                                                       const float*& in, float*& out)
+// four warps of a block always belong to the same box.  Boxes step in
+// lockstep (same sweep, same dt slot parity) but each has its own dt, time
+// and state buffers.  Batches of up to kConstBoxes boxes read each box's
+// coefficients from constant memory with a block-uniform index (no per-thread
+// registers for them); larger batches stage them in shared memory.
+__constant__ Coef<float> c_box[kConstBoxes];
+
+__device__ __forceinline__ const BatchWork& batch_item(const BatchLaunch& L, SweepCtl& sc, const float*& in,
+                                                       float*& out, int& box)
 {
     const BatchWork& w = L.work[blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)];
-    const int box = L.work[blockIdx.x * kWarpsPerBlock].box;
-    if (threadIdx.x == 0) sC = L.boxes[box].C;
-    __syncthreads();
+    box = L.work[blockIdx.x * kWarpsPerBlock].box;
     const BoxDesc& B = L.boxes[box];
     sc.ctl = B.ctl;
     sc.slot_in = L.slot;
@@ -726,21 +728,51 @@ __device__ __forceinline__ const BatchWork& batch_item(const BatchLaunch& L, Coe
 
 __global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch(const __grid_constant__ BatchLaunch L)
 {
-    __shared__ Coef<float> sC;
     SweepCtl sc;
     const float* in;
     float* out;
-    const BatchWork& w = batch_item(L, sC, sc, in, out);
-    z2_body(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+    int box;
+    const BatchWork& w = batch_item(L, sc, in, out, box);
+    box = __shfl_sync(0xffffffffu, box, 0);  // warp-uniform index into the constant bank
+    z2_body(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
 }
 
 __global__ void __launch_bounds__(kThreads2, 4) sweep_x2d_batch(const __grid_constant__ BatchLaunch L)
+{
+    SweepCtl sc;
+    const float* in;
+    float* out;
+    int box;
+    const BatchWork& w = batch_item(L, sc, in, out, box);
+    box = __shfl_sync(0xffffffffu, box, 0);
+    x2_body(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+}
+
+// the same for batches of more than kConstBoxes boxes: the block stages its
+// box's coefficients in shared memory
+__global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch_smem(const __grid_constant__ BatchLaunch L)
 {
     __shared__ Coef<float> sC;
     SweepCtl sc;
     const float* in;
     float* out;
-    const BatchWork& w = batch_item(L, sC, sc, in, out);
+    int box;
+    const BatchWork& w = batch_item(L, sc, in, out, box);
+    if (threadIdx.x == 0) sC = L.boxes[box].C;
+    __syncthreads();
+    z2_body(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_x2d_batch_smem(const __grid_constant__ BatchLaunch L)
+{
+    __shared__ Coef<float> sC;
+    SweepCtl sc;
+    const float* in;
+    float* out;
+    int box;
+    const BatchWork& w = batch_item(L, sc, in, out, box);
+    if (threadIdx.x == 0) sC = L.boxes[box].C;
+    __syncthreads();
     x2_body(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
 }
 

@@ -88,3 +88,32 @@ def test_batch_rejects_bad_boxes():
     p.precision = cm.CM_FP64
     with pytest.raises(cm.CMError):
         cm.cm_batch_init([cm.cm_grid(2, 64, 1, 17, 4.0)], [1e6], 1.0, 5.0 / 3.0, p)
+
+
+def test_large_batch_stages_coefficients_in_shared_memory():
+    """More boxes than the constant-memory table holds (300 > 256): the
+    kernels that stage each box's coefficients in shared memory run, and a
+    box of an uneven mix (different Ra, hence different mu and K) still
+    equals its solo run."""
+    import paper_2411_10372_gb300 as cm
+    n = 300
+    sizes = [(16 + 2 * (b % 5), 6 + b % 4) for b in range(n)]
+    ras = [1e5 * (1 + b % 7) for b in range(n)]
+    grids = [cm.cm_grid(2, nx, 1, nz, 4.0) for nx, nz in sizes]
+    cm.cm_batch_init(grids, ras, 1.0, 5.0 / 3.0, _params(cm, seed=31))
+    nsteps = 7
+    cm.cm_batch_step(nsteps)
+    diags = cm.cm_batch_diagnostics()
+    picks = (0, 137, 299)
+    states = {b: cm.cm_batch_get_state(b, np.empty((4, sizes[b][1], sizes[b][0]))) for b in picks}
+    cm.cm_batch_finalize()
+    assert all(d["status"] == 0 and d["step"] == nsteps for d in diags)
+    for b in picks:
+        nx, nz = sizes[b]
+        s = cm.Solver(nx, nz, ras[b], 1.0, 5.0 / 3.0, precision="fp32", seed=31 + b)
+        s.step(nsteps)
+        solo = s.state()
+        s.close()
+        for f in range(4):
+            err = np.linalg.norm(states[b][f] - solo[f]) / np.linalg.norm(solo[f] if f in (0, 3) else solo[0])
+            assert err <= 1e-5, (b, f, err)
