@@ -246,7 +246,10 @@ typedef struct cm_ext {
 } cm_ext;
 
 /* Plane means of F_n, F_p, F_b, F_v (0 on the plates), (rho u_z)^2 and
- * T_sa^2: out (host) receives nz x 6 doubles, plane-major.  FP64 arithmetic
+ * T_sa^2, and the vertical profiles of Sec. 4: <T_sa>_A = <T>_A - T_A(z),
+ * <rho>_A - rho_A(z) with the adiabatic profiles T_A = 1 - D z and
+ * rho_A = (1 - D z)^(1/(gamma-1)), and the rms velocity U(z) = sqrt(<u^2>_A):
+ * out (host) receives nz x 9 doubles, plane-major.  FP64 arithmetic
  * on the state (FP32 states widened).  The first call allocates device work
  * space of 40 bytes per node (FP64 primitives), kept until cm_finalize.
  * Blocking.  CM_ENOTINIT / CM_EINVAL (out NULL) / CM_ENOMEM / CM_ECUDA. */

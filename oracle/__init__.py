@@ -240,14 +240,15 @@ def diag(cfg: Config, X: np.ndarray) -> dict:
     return dict(zip(DIAG_KEYS, out.tolist()))
 
 
-EXT_PROFILE_KEYS = ("F_n", "F_p", "F_b", "F_v", "rho_uz_sq", "Tsa_sq")
+EXT_PROFILE_KEYS = ("F_n", "F_p", "F_b", "F_v", "rho_uz_sq", "Tsa_sq", "Tsa", "rho_minus_rhoA", "U")
 EXT_KEYS = ("C", "rho_uz_sq", "Tsa_sq", "lambda_b", "lambda_t", "F_n", "F_p", "F_b", "F_v", "r_max")
 
 
 def ext_profiles(cfg: Config, X: np.ndarray) -> dict:
-    """Plane means of the z-momentum terms and of (rho u_z)^2, T_sa^2 (name -> nz values)."""
+    """Plane means of the z-momentum terms, of (rho u_z)^2, T_sa^2, T_sa, rho - rho_A and
+    the rms velocity U (name -> nz values)."""
     Xc = np.ascontiguousarray(X, dtype=np.float64)
-    out = np.zeros((cfg.nz, 6))
+    out = np.zeros((cfg.nz, 9))
     c = cfg.c()
     lib().orc_ext_profiles(ctypes.byref(c), _ptr(Xc), _ptr(out))
     return {k: out[:, q].copy() for q, k in enumerate(EXT_PROFILE_KEYS)}

@@ -867,13 +867,16 @@ static double dzz3(const P* p, int k, double fm, double f0, double fp)
     return 2.0 * ((fp - f0) / hp - (f0 - fm) / hm) / (hm + hp);
 }
 
-/* Plane means of the terms of the z-momentum equation and of the two
- * squares in the correlation C(Ra):
- *   out[k*6+0] <F_n>_A = <rho (u . grad) u_z>_A        (nonlinear term)
- *   out[k*6+1] <F_p>_A = <-dp/dz>_A                   (pressure gradient)
- *   out[k*6+2] <F_b>_A = <rho g>_A                    (buoyancy, g = gravity/eps)
- *   out[k*6+3] <F_v>_A = <d_i tau_iz>_A               (viscous force)
- *   out[k*6+4] <(rho u_z)^2>_A,  out[k*6+5] <T_sa^2>_A, T_sa = T - (1 - D z)
+/* Plane means of the terms of the z-momentum equation, of the two squares
+ * in the correlation C(Ra) and the vertical profiles of Sec. 4:
+ *   out[k*9+0] <F_n>_A = <rho (u . grad) u_z>_A        (nonlinear term)
+ *   out[k*9+1] <F_p>_A = <-dp/dz>_A                   (pressure gradient)
+ *   out[k*9+2] <F_b>_A = <rho g>_A                    (buoyancy, g = gravity/eps)
+ *   out[k*9+3] <F_v>_A = <d_i tau_iz>_A               (viscous force)
+ *   out[k*9+4] <(rho u_z)^2>_A,  out[k*9+5] <T_sa^2>_A, T_sa = T - (1 - D z)
+ *   out[k*9+6] <T_sa>_A = <T>_A - T_A(z), T_A = 1 - D z
+ *   out[k*9+7] <rho>_A - rho_A(z), rho_A = (1 - D z)^(1/(gamma-1))
+ *   out[k*9+8] U(z) = sqrt(<u^2>_A), the plane's rms velocity
  * The force terms need neighbouring planes: on the plates they are 0.
  * d_i tau_iz = mu (d_xx u_z + d_yy u_z + (2 + s) d_zz u_z + (1 + s)(d_x d_z u_x + d_y d_z u_y)),
  * s the Stokes coefficient (tau_ij = mu (d_j u_i + d_i u_j + s (div u) delta_ij)). */
@@ -889,7 +892,7 @@ void orc_ext_profiles(const orc_cfg* c, const double* ext, double* out)
     double cells = (double)p.nx * p.ny;
     int K = p.nz - 1;
     for (int k = 0; k < p.nz; k++) {
-        double s[6] = {0, 0, 0, 0, 0, 0};
+        double s[6] = {0, 0, 0, 0, 0, 0}, tsum = 0.0, rsum = 0.0, usum = 0.0;
         double z = zk(&p, k);
         for (int j = 0; j < p.ny; j++)
             for (int i = 0; i < p.nx; i++) {
@@ -899,6 +902,9 @@ void orc_ext_profiles(const orc_cfg* c, const double* ext, double* out)
                 double Tsa = T[n] - (1.0 - p.D * z);
                 s[4] += (rho * uz) * (rho * uz);
                 s[5] += Tsa * Tsa;
+                tsum += T[n];
+                rsum += rho;
+                usum += (ux * ux + uy * uy) + uz * uz;
                 if (k == 0 || k == K) continue;
                 size_t xp = nbr(&p, i, j, k, 0, +1), xm = nbr(&p, i, j, k, 0, -1);
                 size_t yp = nbr(&p, i, j, k, 1, +1), ym = nbr(&p, i, j, k, 1, -1);
@@ -926,7 +932,10 @@ void orc_ext_profiles(const orc_cfg* c, const double* ext, double* out)
                 }
                 s[3] += p.mu * ((dxx + dyy) + (2.0 + p.stokes) * dzz + (1.0 + p.stokes) * (dxdzux + dydzuy));
             }
-        for (int q = 0; q < 6; q++) out[(size_t)k * 6 + q] = s[q] / cells;
+        for (int q = 0; q < 6; q++) out[(size_t)k * 9 + q] = s[q] / cells;
+        out[(size_t)k * 9 + 6] = tsum / cells - (1.0 - p.D * z);
+        out[(size_t)k * 9 + 7] = rsum / cells - pow(1.0 - p.D * z, 1.0 / (p.gam - 1.0));
+        out[(size_t)k * 9 + 8] = sqrt(usum / cells);
     }
     free(X); free(U); free(T); free(Pr);
     release(&p);
@@ -957,7 +966,7 @@ void orc_extended(const orc_cfg* c, const double* ext, double* out, long long* h
     derive(c, &p);
     size_t N = p.n;
     int K = p.nz - 1;
-    double* prof = malloc((size_t)p.nz * 6 * sizeof(double));
+    double* prof = malloc((size_t)p.nz * 9 * sizeof(double));
     orc_ext_profiles(c, ext, prof);
     double* X = malloc(5 * N * sizeof(double));
     double *U = malloc(3 * N * sizeof(double)), *T = malloc(N * sizeof(double)), *Pr = malloc(N * sizeof(double));
@@ -976,12 +985,12 @@ void orc_extended(const orc_cfg* c, const double* ext, double* out, long long* h
                 TA[k] += T[n];
             }
         s_conv += wgt * conv / cells;
-        s_m2 += wgt * prof[(size_t)k * 6 + 4];
-        s_t2 += wgt * prof[(size_t)k * 6 + 5];
+        s_m2 += wgt * prof[(size_t)k * 9 + 4];
+        s_t2 += wgt * prof[(size_t)k * 9 + 5];
         TA[k] /= cells;
         if (k > 0 && k < K) {
             wsum += wgt;
-            for (int q = 0; q < 4; q++) f[q] += wgt * prof[(size_t)k * 6 + q];
+            for (int q = 0; q < 4; q++) f[q] += wgt * prof[(size_t)k * 9 + q];
         }
     }
     double vol = p.stretched ? 1.0 : (double)(p.nz - 1);

@@ -66,7 +66,7 @@ class Solver:
         return cm_znodes(self.grid.nz)
 
     def ext_profiles(self) -> dict:
-        """Plane means of F_n, F_p, F_b, F_v, (rho u_z)^2, T_sa^2 of the current state."""
+        """Plane means of F_n, F_p, F_b, F_v, (rho u_z)^2, T_sa^2, and the profiles T_sa, rho - rho_A, U."""
         return cm_ext_profiles(self.grid.nz)
 
     def extended(self, nbins: int = 64, log10_lo: float = -16.0, log10_hi: float = 0.0):

@@ -242,12 +242,13 @@ def cm_profiles(nz: int) -> dict:
     return {k: out[:, q].copy() for q, k in enumerate(PROFILE_KEYS)}
 
 
-EXT_PROFILE_KEYS = ("F_n", "F_p", "F_b", "F_v", "rho_uz_sq", "Tsa_sq")
+EXT_PROFILE_KEYS = ("F_n", "F_p", "F_b", "F_v", "rho_uz_sq", "Tsa_sq", "Tsa", "rho_minus_rhoA", "U")
 
 
 def cm_ext_profiles(nz: int) -> dict:
-    """Plane means of the z-momentum terms and of (rho u_z)^2, T_sa^2 (include/cm.h): name -> nz values."""
-    out = np.empty((nz, 6), dtype=np.float64)
+    """Plane means of the z-momentum terms, (rho u_z)^2, T_sa^2, and the profiles T_sa,
+    rho - rho_A, U (include/cm.h): name -> nz values."""
+    out = np.empty((nz, 9), dtype=np.float64)
     _check(lib().cm_ext_profiles(out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return {k: out[:, q].copy() for q, k in enumerate(EXT_PROFILE_KEYS)}
 

@@ -249,7 +249,8 @@ __global__ void ext_prims_all(const R* X, Coef<R> C, ExtArgs A, double* P)
 // (interior planes; 0 on the plates), of (rho u_z)^2, T_sa^2, rho u_z T_sa
 // and T, the max of r = K_e/I_e = b u^2/(2T), and the histogram of log10 r,
 // from the primitives P of ext_prims_all.  scratch[k*16 + q]: q = 0..5 F_n,
-// F_p, F_b, F_v, (rho u_z)^2, T_sa^2; 6 rho u_z T_sa; 7 max r; 8 T.
+// F_p, F_b, F_v, (rho u_z)^2, T_sa^2; 6 rho u_z T_sa; 7 max r; 8 T; 9 rho;
+// 10 u^2.
 static __global__ void __launch_bounds__(kDiagThreads) ext_planes(int nx, int ny, int nz, int ndim, ExtArgs A, const double* P,
                                                            double* scratch)
 {
@@ -289,6 +290,8 @@ static __global__ void __launch_bounds__(kDiagThreads) ext_planes(int nx, int ny
         v[6] += rho * uz * Tsa;
         tsum[0] += T;
         const double u2 = (ux * ux + uy * uy) + uz * uz;
+        tsum[1] += rho;
+        tsum[2] += u2;
         const double r = A.b * u2 / (2.0 * T);
         v[7] = fmax(v[7], r);
         int q = 0;

@@ -685,9 +685,15 @@ int cm_ext_profiles(double* out)
     std::vector<unsigned long long> hist;
     int rc = run_ext(c, 0, 0.0, 0.0, sums, hist);
     if (rc) return rc;
-    const double cells = (double)c->grid.nx * c->ny;
-    for (int k = 0; k < c->grid.nz; ++k)
-        for (int q = 0; q < 6; ++q) out[(size_t)k * 6 + q] = sums[(size_t)k * 16 + q] / cells;
+    const double cells = (double)c->grid.nx * c->ny, D = c->prm.D;
+    for (int k = 0; k < c->grid.nz; ++k) {
+        const double* sk = &sums[(size_t)k * 16];
+        const double z = c->zplanes[k];
+        for (int q = 0; q < 6; ++q) out[(size_t)k * 9 + q] = sk[q] / cells;
+        out[(size_t)k * 9 + 6] = sk[8] / cells - (1.0 - D * z);
+        out[(size_t)k * 9 + 7] = sk[9] / cells - std::pow(1.0 - D * z, 1.0 / (c->gamma - 1.0));
+        out[(size_t)k * 9 + 8] = std::sqrt(sk[10] / cells);
+    }
     return CM_OK;
 }
 

@@ -95,6 +95,8 @@ MUTANTS = [
     ("ext_bl_top_sign", "out[4] = (sb[0] - tb) / dtp;", "out[4] = (tb - sb[0]) / dtp;"),
     ("ext_bl_bottom_plane", "out[3] = (tb - sa[0]) / db;", "out[3] = (tb - sa[1]) / db;"),
     ("ext_r_missing_half", "double r = p.b * u2 / (2.0 * T[n]);", "double r = p.b * u2 / T[n];"),
+    ("ext_rhoA_exponent", "pow(1.0 - p.D * z, 1.0 / (p.gam - 1.0))", "pow(1.0 - p.D * z, p.gam / (p.gam - 1.0))"),
+    ("ext_rms_without_root", "out[(size_t)k * 9 + 8] = sqrt(usum / cells);", "out[(size_t)k * 9 + 8] = usum / cells;"),
 ]
 
 

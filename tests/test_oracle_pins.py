@@ -943,7 +943,10 @@ def test_ext_force_profiles_closed_forms():
     the plane means at interior planes are, with G = z(1-z):
       F_n = rho0 [G G' (c0^2 + m/2) - U0 G^2 sigma_x/2 - V0 G^2 sigma_y/2]  (m = 1 in 2D, 2 in 3D)
       F_p = -a rho0 (-D + q G'),  F_b = rho0 g,  F_v = mu (2 + s) c0 G''
-      (rho u_z)^2 = rho0^2 G^2 (c0^2 + m/2),  T_sa^2 = q^2 G^2."""
+      (rho u_z)^2 = rho0^2 G^2 (c0^2 + m/2),  T_sa^2 = q^2 G^2,
+    and the vertical profiles of Sec. 4: T_sa = q G, rho - rho_A =
+    rho0 - (1 - D z)^(1/(gamma-1)) and U = sqrt(<u^2>_A) =
+    G sqrt(c0^2 + m/2 + U0^2/2 + V0^2/2)."""
     c0, U0, V0, q, rho0 = 0.3, 0.05, 0.04, 0.02, 0.9
     cases = [O.Config(nx=16, nz=13, Ra=1e4), O.Config(nx=16, nz=13, Ra=1e4, zstretch=2.0),
              O.Config(nx=16, nz=13, Ra=1e4, znodes=random_planes(13, 77)),
@@ -961,7 +964,9 @@ def test_ext_force_profiles_closed_forms():
         want = dict(F_n=rho0 * (G * Gp * (c0 ** 2 + m / 2) - U0 * G ** 2 * sx / 2 - (V0 * G ** 2 * sy / 2 if m == 2 else 0)),
                     F_p=-cl["a"] * rho0 * (-cfg.D + q * Gp), F_b=rho0 * cfg.gravity / cfg.eps + 0 * z,
                     F_v=cl["mu"] * (2 + cfg.stokes) * c0 * (-2.0) + 0 * z,
-                    rho_uz_sq=rho0 ** 2 * G ** 2 * (c0 ** 2 + m / 2), Tsa_sq=q ** 2 * G ** 2)
+                    rho_uz_sq=rho0 ** 2 * G ** 2 * (c0 ** 2 + m / 2), Tsa_sq=q ** 2 * G ** 2, Tsa=q * G,
+                    rho_minus_rhoA=rho0 - (1 - cfg.D * z) ** (1 / (cfg.gamma - 1)),
+                    U=G * np.sqrt(c0 ** 2 + m / 2 + U0 ** 2 / 2 + (V0 ** 2 / 2 if m == 2 else 0)))
         for key, v in want.items():
             got = prof[key]
             sl = slice(1, -1) if key.startswith("F_") else slice(None)
