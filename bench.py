@@ -34,6 +34,9 @@ sys.path.insert(0, ROOT)
 NX, NZ, RA, PR, GAMMA = 4096, 1024, 1e10, 1.0, 5.0 / 3.0
 RA3 = 1e9  # the 512 x 512 x 128 box
 ZSTRETCH = 2.0  # tanh z-grid of the stretched leg (first spacing 0.147 of the uniform one)
+# tanh z-grid of the stretched batch: beta = 2 would put the nz = 254, Ra = 1.5e5 box at an explicit
+# diffusion number of 1.36 (cm_batch_init rejects it); beta = 1 (the paper's plate refinement) gives 0.37
+BATCH_ZSTRETCH = 1.0
 WORKLOAD = "2d_aspect4_4096x1024_Ra1e10"
 METRIC = "cell-updates/s per MacCormack-TVD step"
 UNIT = "cell-updates/s"
@@ -237,22 +240,26 @@ def run_gpu(args):
         rng = np.random.default_rng(2024 + rank)
         u, u2 = rng.random(64), rng.random(64)
         nzs = [int(round(32 * 8 ** x)) for x in u]
-        grids = [cm.cm_grid(2, 4 * nz, 1, nz, 4.0) for nz in nzs]
         ras = [10 ** (5 + 4 * x) for x in u2]
         p = cm.cm_default_params()
         p.precision = cm.CM_FP32
         p.stream = stream.cuda_stream
-        cm.cm_batch_init(grids, ras, PR, GAMMA, p)
-        cm.cm_batch_step(50)
-        barrier()
-        l0 = cm.cm_batch_launch_count()
         kb = args.batch_steps
-        ms = max_ms(cm.cm_batch_profile_steps(kb, FLUSH_BYTES))
-        nl = cm.cm_batch_launch_count() - l0
+
+        def run_batch(beta):
+            cm.cm_batch_init([cm.cm_grid(2, 4 * nz, 1, nz, 4.0, beta) for nz in nzs], ras, PR, GAMMA, p)
+            cm.cm_batch_step(50)
+            barrier()
+            l0 = cm.cm_batch_launch_count()
+            ms = max_ms(cm.cm_batch_profile_steps(kb, FLUSH_BYTES))
+            nl = cm.cm_batch_launch_count() - l0
+            tuning = cm.cm_batch_tuning()
+            diags = cm.cm_batch_diagnostics()
+            cm.cm_batch_finalize()
+            return ms, nl, tuning, diags
+
+        ms, nl, (seg_z, seg_x), diags = run_batch(0.0)
         cells_b = sum(4 * nz * nz for nz in nzs)
-        seg_z, seg_x = cm.cm_batch_tuning()
-        diags = cm.cm_batch_diagnostics()
-        cm.cm_batch_finalize()
         per_sweep_ms = ms / kb / 4.0
         ach_b = 2 * 4 * 4 * cells_b / (per_sweep_ms * 1e-3) / 1e9
         batch = {"value": job_rate(cells_b, kb, ms, world), "unit": UNIT, "steps": kb, "boxes": 64,
@@ -263,6 +270,12 @@ def run_gpu(args):
                  "all_finite": all(d["status"] == 0 for d in diags),
                  "segments_z": sorted(set(seg_z)), "segments_x": sorted(set(seg_x)),
                  "l2": "flushed once before the timed steps (the steps replay captured 50-step graphs)"}
+        if not args.no_stretched:
+            # the same ensemble with every box on the tanh z-grid of beta = BATCH_ZSTRETCH
+            ms_s, nl_s, _, diags_s = run_batch(BATCH_ZSTRETCH)
+            batch["stretched"] = {"zstretch": BATCH_ZSTRETCH, "value": job_rate(cells_b, kb, ms_s, world),
+                                  "ms_per_step": ms_s / kb, "gpu_launches": nl_s, "vs_uniform": round(ms / ms_s, 4),
+                                  "all_finite": all(d["status"] == 0 for d in diags_s)}
 
     # ---- 3D box: 512 x 512 x 128 nodes, aspect 4 x 4 x 1, FP32, same Ra ----
     box3 = None
@@ -509,7 +522,7 @@ def run_case(args):
         nzs = [int(round(32 * 8 ** x)) for x in u]
         p = cm.cm_default_params()
         p.precision = cm.CM_FP32
-        cm.cm_batch_init([cm.cm_grid(2, 4 * nz, 1, nz, 4.0) for nz in nzs], [10 ** (5 + 4 * x) for x in u2], PR,
+        cm.cm_batch_init([cm.cm_grid(2, 4 * nz, 1, nz, 4.0, args.zstretch) for nz in nzs], [10 ** (5 + 4 * x) for x in u2], PR,
                          GAMMA, p)
         cm.cm_batch_step(args.warmup + args.steps)
         out.update(boxes=64, status=max(d["status"] for d in cm.cm_batch_diagnostics()))
@@ -542,7 +555,7 @@ def main():
     ap.add_argument("--nz", type=int, default=NZ, help="grid override (profiling captures only)")
     ap.add_argument("--ny", type=int, default=512, help="3D grid override (--case only)")
     ap.add_argument("--only-fp32", action="store_true", help="time the FP32 steps only (profiling captures)")
-    ap.add_argument("--zstretch", type=float, default=0.0, help="tanh z-grid for --case 2d_*, 3d_*, extended (profiling captures)")
+    ap.add_argument("--zstretch", type=float, default=0.0, help="tanh z-grid for --case 2d_*, 3d_*, batch, extended (profiling captures)")
     ap.add_argument("--case", choices=["2d_fp32", "2d_fp64", "3d_fp32", "3d_fp64", "batch", "adjoint", "extended"],
                     help="run one kernel family untimed (profiling captures)")
     args = ap.parse_args()

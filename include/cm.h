@@ -66,9 +66,9 @@ typedef struct cm_grid {
      * z_{k-1})/2 (half cells on the plates), derivatives divide by the
      * distance of the planes they use, volume averages use the trapezoid
      * rule on the planes and the plate Nusselt numbers the derivative of the
-     * quadratic through three planes.  Stretched grids: single contexts, 2D
-     * and 3D (cm_batch_init, cm_adj_* and cm_diag_noalloc return CM_EINVAL
-     * for a stretched grid). */
+     * quadratic through three planes.  Stretched grids: single contexts (2D
+     * and 3D), the boxes of a batch and cm_diag_noalloc (cm_adj_* return
+     * CM_EINVAL for a stretched grid). */
     double zstretch;
     const double* znodes;
 } cm_grid;
@@ -295,8 +295,13 @@ int cm_load(const char* path);
  * host (precision must be CM_FP32; stream NULL = a stream the batch creates,
  * otherwise a stream that can be captured).  Each box gets the initial state
  * of cm_init (seed + box index) and is advanced by Eq. time_step (Sec. 3.1)
- * with its own dt.  CM_EINVAL for an odd nx, an FP64 precision or a bad grid.
- * Blocking. */
+ * with its own dt.  A box may have a stretched z-grid (zstretch or znodes,
+ * read during this call only, as in cm_init); then every box of the batch is
+ * stepped by the stretched-grid sweeps, a uniform box with the plane table
+ * of its planes k/K (the result of cm_init with znodes = k/K).  CM_EINVAL for
+ * an odd nx, an FP64 precision or a bad grid (before any device work);
+ * CM_EUNSTABLE if a box's explicit diffusion number at its first dt is above
+ * 1/2 (the bound of cm_init; the message names the box).  Blocking. */
 int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, double gamma, const cm_params* params);
 
 /* Queue n steps (Eq. time_step) of every box (asynchronous). */
@@ -329,10 +334,13 @@ int cm_batch_finalize(void);
  * whose memory pool owns the device memory and where a cudaMalloc could fail
  * or synchronise the device under the host's streams).  Computes the same
  * record as cm_sample (Sec. 2 definitions, FP64 reductions) without a
- * context: the scratch lives in a fixed ~1.2 MB __device__ array inside the
+ * context: the scratch lives in a fixed ~2.8 MB __device__ array inside the
  * library (held on every GPU that loads it until exit), so nz may not exceed
- * 16384 planes (CM_EINVAL beyond).  The first call on a device looks up that
- * array's device address; make that first call before any stream capture.
+ * 16384 planes (CM_EINVAL beyond).  A stretched grid (zstretch or znodes,
+ * as for cm_init) gets its plane table built on the host and copied into
+ * that array (the stretched-grid weights of cm_sample).  The first call on
+ * a device looks up that array's device address; make that first call
+ * before any stream capture.
  * All calls share the array: calls that overlap on the GPU race.
  * state: device pointer to field 0 of a state in the layout of
  *   cm_state_layout (fields nz*ny*pitch elements apart), precision CM_FP64 or

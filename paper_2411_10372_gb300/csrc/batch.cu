@@ -40,6 +40,8 @@ struct Box {
     double* pc;
     double* scratch;    // per-plane diagnostics sums
     DevCtl* ctl;
+    Plane<float>* zp_f;     // stretched batches: per-plane metric (sweeps), else NULL
+    Plane<double>* zp_d;    // the same in FP64 (diagnostics), else NULL
     Coef<float> C;
     int cls;            // size class for the autotuner
     int seg_z, seg_x;   // chosen segment lengths
@@ -64,6 +66,7 @@ struct Batch {
     int graph_steps;
     int cur;
     bool const_coefs;   // coefficients in constant memory (at most kConstBoxes boxes)
+    bool stretched;     // some box has a stretched z-grid: every box runs the plane-table sweeps
 };
 
 Batch* g_batch = nullptr;
@@ -120,7 +123,7 @@ int launch(Batch& B, int dir, int first, int last, double Delta)
     L.first = first;
     L.last = last;
     L.Delta = Delta;
-    CKB(launch_sweep_batch(dir, L, dir == 2 ? B.nblk_z : B.nblk_x, B.const_coefs, B.stream));
+    CKB(launch_sweep_batch(dir, L, dir == 2 ? B.nblk_z : B.nblk_x, B.const_coefs, B.stretched, B.stream));
     B.launches++;
     return CM_OK;
 }
@@ -175,6 +178,7 @@ int autotune(Batch& B)
 {
     // not only powers of two: the single-box sweeps ran fastest at 29 rows
     const int cand[] = {8, 12, 16, 20, 24, 29, 32, 40, 48, 64, 96, 128};
+    static_assert(kBatchSegMax >= 128, "the stretched batch kernels size their plane caches for kBatchSegMax rows");
     bool present[4] = {false, false, false, false};
     for (const Box& x : B.boxes) present[x.cls] = true;
     for (int dir : {2, 0}) {
@@ -238,8 +242,18 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
             return set_error(CM_EINVAL, "cm_batch_init: every box must be 2D with even nx >= 4, nz >= 5, Ra > 0");
         if ((long long)G.nz * pitch_of(G.nx, CM_FP32) * 5 >= (1LL << 31))
             return set_error(CM_EINVAL, "cm_batch_init: box too large");
-        if (G.znodes || G.zstretch != 0.0)
-            return set_error(CM_EINVAL, "cm_batch_init: the batch steps uniform z-grids only");
+    }
+    // z-planes of every box (uniform, tanh or given), validated before any device work
+    std::vector<std::vector<double>> planes(nbox);
+    bool any_st = false;
+    for (int b = 0; b < nbox; ++b) {
+        const char* why = "";
+        if (!make_planes(grids[b], planes[b], &why)) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "cm_batch_init: box %d: %s", b, why);
+            return set_error(CM_EINVAL, msg);
+        }
+        any_st = any_st || stretched(grids[b]);
     }
     if (g_batch) { free_batch(g_batch); g_batch = nullptr; }
     Batch* B = new Batch();
@@ -255,6 +269,7 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
     B->step = 0;
     B->launches = 0;
     B->cur = 0;
+    B->stretched = any_st;
     auto bail = [&](int code) { free_batch(B); return code; };
     if (P.stream) {
         B->stream = (cudaStream_t)P.stream;
@@ -269,10 +284,12 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
     B->boxes.resize(nbox);
     size_t bytes = 0, items = 0;
     auto take = [&](size_t n) { size_t o = bytes; bytes += (n + 255) / 256 * 256; return o; };
-    std::vector<size_t> off(8 * nbox);
+    constexpr int kPieces = 9;
+    std::vector<size_t> off(kPieces * nbox);
     for (int b = 0; b < nbox; ++b) {
         Box& x = B->boxes[b];
         x.grid = grids[b];
+        x.grid.znodes = nullptr;  // caller memory: the planes were copied above
         x.Ra = Ra[b];
         x.pitch = pitch_of(x.grid.nx, CM_FP32);
         x.fstride = (long long)x.grid.nz * x.pitch;
@@ -280,13 +297,15 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
         const int nz = x.grid.nz;
         x.cls = nz < 64 ? 0 : nz < 128 ? 1 : nz < 256 ? 2 : 3;
         x.seg_z = x.seg_x = 8;  // smallest candidate: sizes the work buffers
-        off[8 * b + 0] = take(2 * x.buf_elems * sizeof(float));
-        off[8 * b + 1] = take(nz * sizeof(float));
-        off[8 * b + 2] = take(nz * sizeof(double));
-        off[8 * b + 3] = take(nz * sizeof(double));
-        off[8 * b + 4] = take(nz * sizeof(double));
-        off[8 * b + 5] = take((size_t)nz * kDiagQ * sizeof(double));
-        off[8 * b + 6] = take(sizeof(DevCtl));
+        off[kPieces * b + 0] = take(2 * x.buf_elems * sizeof(float));
+        off[kPieces * b + 1] = take(nz * sizeof(float));
+        off[kPieces * b + 2] = take(nz * sizeof(double));
+        off[kPieces * b + 3] = take(nz * sizeof(double));
+        off[kPieces * b + 4] = take(nz * sizeof(double));
+        off[kPieces * b + 5] = take((size_t)nz * kDiagQ * sizeof(double));
+        off[kPieces * b + 6] = take(sizeof(DevCtl));
+        off[kPieces * b + 7] = take(any_st ? nz * sizeof(Plane<float>) : 0);
+        off[kPieces * b + 8] = take(any_st ? nz * sizeof(Plane<double>) : 0);
         items += ((size_t)((x.grid.nx + kOutW2 - 1) / kOutW2) * ((nz + 7) / 8) + kWarpsPerBlock);
     }
     B->work_cap = items;
@@ -303,16 +322,26 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
     for (int b = 0; b < nbox && !rc; ++b) {
         Box& x = B->boxes[b];
         const int nz = x.grid.nz;
-        x.buf[0] = (float*)(base + off[8 * b + 0]);
+        x.buf[0] = (float*)(base + off[kPieces * b + 0]);
         x.buf[1] = x.buf[0] + x.buf_elems;
-        x.zt_f = (float*)(base + off[8 * b + 1]);
-        x.zt_d = (double*)(base + off[8 * b + 2]);
-        x.Tc = (double*)(base + off[8 * b + 3]);
-        x.pc = (double*)(base + off[8 * b + 4]);
-        x.scratch = (double*)(base + off[8 * b + 5]);
-        x.ctl = (DevCtl*)(base + off[8 * b + 6]);
+        x.zt_f = (float*)(base + off[kPieces * b + 1]);
+        x.zt_d = (double*)(base + off[kPieces * b + 2]);
+        x.Tc = (double*)(base + off[kPieces * b + 3]);
+        x.pc = (double*)(base + off[kPieces * b + 4]);
+        x.scratch = (double*)(base + off[kPieces * b + 5]);
+        x.ctl = (DevCtl*)(base + off[kPieces * b + 6]);
+        x.zp_f = any_st ? (Plane<float>*)(base + off[kPieces * b + 7]) : nullptr;
+        x.zp_d = any_st ? (Plane<double>*)(base + off[kPieces * b + 8]) : nullptr;
         fill_coef(x.C, x.grid, 1, x.pitch, x.fstride, x.Ra, Pr, K, P);
-        const Profile prof(nz, P, K);
+        const Profile prof(planes[b], P, K);
+        std::vector<Plane<float>> tf;
+        std::vector<Plane<double>> td;
+        if (any_st) {
+            // uniform boxes of a stretched batch get the table of the planes k/K
+            plane_table(planes[b], tf);
+            plane_table(planes[b], td);
+            x.C.zp = x.zp_f;
+        }
         std::vector<float> zf(nz);
         for (int k = 0; k < nz; ++k) zf[k] = (float)prof.z[k];
         DevCtl h;
@@ -324,6 +353,10 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
         if (!rc) rc = ck(cudaMemcpyAsync(x.Tc, prof.Tc.data(), nz * sizeof(double), cudaMemcpyHostToDevice, B->stream), "upload");
         if (!rc) rc = ck(cudaMemcpyAsync(x.pc, prof.pc.data(), nz * sizeof(double), cudaMemcpyHostToDevice, B->stream), "upload");
         if (!rc) rc = ck(cudaMemcpyAsync(x.ctl, &h, sizeof h, cudaMemcpyHostToDevice, B->stream), "upload");
+        if (!rc && any_st)
+            rc = ck(cudaMemcpyAsync(x.zp_f, tf.data(), nz * sizeof(Plane<float>), cudaMemcpyHostToDevice, B->stream), "upload");
+        if (!rc && any_st)
+            rc = ck(cudaMemcpyAsync(x.zp_d, td.data(), nz * sizeof(Plane<double>), cudaMemcpyHostToDevice, B->stream), "upload");
         InitArgs A;
         A.Tc = x.Tc;
         A.pc = x.pc;
@@ -336,6 +369,26 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
         if (!rc) rc = ck(Launch<float>::init(x.buf[0], x.C, A, B->stream), "init launch");
         if (!rc) rc = ck(Launch<float>::dt(x.buf[0], x.zt_f, x.C, x.ctl, 0, B->stream), "dt launch");
         if (!rc) rc = ck(cudaStreamSynchronize(B->stream), "init");  // host tables above are freed on return
+        if (!rc) {
+            // the first dt, and the explicit-diffusion bound cm_init applies
+            DevCtl hc;
+            rc = ck(cudaMemcpy(&hc, x.ctl, sizeof hc, cudaMemcpyDeviceToHost), "control block read");
+            double hmin = 0.0;
+            std::memcpy(&hmin, &hc.dt_slot[0], sizeof hmin);
+            const double dt0 = P.dt_fixed > 0 ? P.dt_fixed : P.cfl * hmin;
+            char msg[200];
+            if (!rc && (!(dt0 > 0) || !std::isfinite(dt0) || (hc.status & 1))) {
+                snprintf(msg, sizeof msg, "cm_batch_init: box %d: non-finite initial state", b);
+                rc = set_error(CM_ENAN, msg);
+            }
+            const double dnum = rc ? 0.0 : diffusion_number(x.grid, planes[b], x.Ra, Pr, P, K, prof.rho_min, dt0);
+            if (dnum > 0.5) {
+                snprintf(msg, sizeof msg,
+                         "cm_batch_init: box %d: explicit diffusion number %.3g > 0.5 at dt = %.3g: refine dt "
+                         "(dt_fixed) or raise Ra", b, dnum, dt0);
+                rc = set_error(CM_EUNSTABLE, msg);
+            }
+        }
         desc[b].C = x.C;
         desc[b].buf[0] = x.buf[0];
         desc[b].buf[1] = x.buf[1];
@@ -421,6 +474,7 @@ int cm_batch_diagnostics(cm_diag* out)
         F.cells = (double)x.grid.nx;
         F.nz = x.grid.nz;
         F.slot = (int)(B.step & 1);
+        F.zp = x.zp_d;
         CKB(launch_diag_final(x.scratch, x.zt_d, F, x.ctl, B.d_recs + b, B.stream));
         B.launches += 2;
     }

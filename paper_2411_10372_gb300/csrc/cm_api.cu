@@ -563,12 +563,7 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     std::memcpy(&hmin, &h.dt_slot[0], sizeof hmin);
     const double dt0 = P.dt_fixed > 0 ? P.dt_fixed : P.cfl * hmin;
     if (!(dt0 > 0) || !std::isfinite(dt0) || (h.status & 1)) return bail(fail(CM_ENAN, "non-finite initial state"));
-    const double mu = std::sqrt(Pr / Ra), K = 1.0 / (P.eps * P.D * std::sqrt(Ra * Pr));
-    const double nu = std::fmax(4.0 / 3.0 * mu, K * c->b) / rho_min;
-    double hz = 1.0 / (nz - 1);
-    for (int k = 0; k + 1 < nz; ++k) hz = std::fmin(hz, planes[k + 1] - planes[k]);
-    const double hh = std::fmin(grid->aspect / grid->nx, hz);
-    const double dnum = nu * 0.5 * dt0 / (hh * hh);
+    const double dnum = diffusion_number(*grid, planes, Ra, Pr, P, Closure(gamma, P), rho_min, dt0);
     if (dnum > 0.5)
         return bail(fail(CM_EUNSTABLE, "explicit diffusion number %.3g > 0.5 at dt = %.3g: refine dt (dt_fixed) or raise Ra", dnum, dt0));
     if ((rc = tune_segments(c))) return bail(rc);

@@ -10,10 +10,10 @@
 // fixed-size scratch region that lives in the library image itself.
 //
 // The scratch region is a file-scope __device__ array (kNoAllocWords
-// doubles, ~1.2 MB): every GPU that loads libcm.so holds it until the
+// doubles, ~2.8 MB): every GPU that loads libcm.so holds it until the
 // process exits.  It contains the control block the reduction reports into,
-// the z coordinate of each plane, the per-plane partial sums and the output
-// record.  Host code cannot use the array's name as a device address, so the
+// the z coordinate of each plane, the per-plane partial sums, the output
+// record and, for a stretched z-grid, the FP64 per-plane metric table.  Host code cannot use the array's name as a device address, so the
 // address is looked up once per device with cudaGetSymbolAddress, with that
 // device current, on the first call on that device.
 #include <cuda_runtime.h>
@@ -21,7 +21,10 @@
 #include <cstdio>
 #include <cstring>
 
+#include <vector>
+
 #include "../../include/cm.h"
+#include "host_setup.h"
 #include "kernels.h"
 
 namespace cm {
@@ -35,7 +38,11 @@ constexpr int kCtlWords = 8;          // DevCtl (40 bytes) rounded up
 constexpr int kRecWords = 16;         // cm_diag (128 bytes)
 constexpr int kZOff = kCtlWords + kRecWords;
 constexpr int kPlanesOff = kZOff + kNoAllocMaxNz;
-constexpr int kNoAllocWords = kPlanesOff + kNoAllocMaxNz * kDiagQ;
+constexpr int kTableOff = kPlanesOff + kNoAllocMaxNz * kDiagQ;
+constexpr int kTableWords = kNoAllocMaxNz * (int)(sizeof(Plane<double>) / sizeof(double));
+constexpr int kNoAllocWords = kTableOff + kTableWords;
+static_assert(sizeof(Plane<double>) % sizeof(double) == 0, "plane table entries must be whole words");
+static_assert((kTableOff * sizeof(double)) % alignof(Plane<double>) == 0, "plane table misaligned");
 static_assert(sizeof(DevCtl) <= kCtlWords * sizeof(double), "control block does not fit");
 static_assert(sizeof(cm_diag) <= kRecWords * sizeof(double), "record does not fit");
 
@@ -102,8 +109,6 @@ extern "C" int cm_diag_noalloc(const void* state, int precision, const cm_grid* 
     if (grid->ndim != 2 && grid->ndim != 3) return set_error(CM_EINVAL, "cm_diag_noalloc: ndim must be 2 or 3");
     const int ny = grid->ndim == 3 ? grid->ny : 1;
     if (grid->nx < 1 || ny < 1 || grid->nz < 5) return set_error(CM_EINVAL, "cm_diag_noalloc: bad grid");
-    if (grid->znodes || grid->zstretch != 0.0)
-        return set_error(CM_EINVAL, "cm_diag_noalloc: uniform z-grids only (use cm_diagnostics for stretched grids)");
     if (grid->nz > kNoAllocMaxNz) {
         char msg[160];
         snprintf(msg, sizeof msg, "cm_diag_noalloc: nz = %d exceeds the no-alloc maximum of %d planes", grid->nz,
@@ -115,6 +120,20 @@ extern "C" int cm_diag_noalloc(const void* state, int precision, const cm_grid* 
         return set_error(CM_EINVAL, "cm_diag_noalloc: precision must be CM_FP64 or CM_FP32");
     if (!(Ra > 0) || !(Pr > 0) || !(gamma > 1) || !(params->eps > 0) || !(params->D > 0))
         return set_error(CM_EINVAL, "cm_diag_noalloc: need Ra, Pr, eps, D > 0 and gamma > 1");
+    // stretched z-grid: the planes and their FP64 metric, built on the host
+    // (host memory only) and copied into the scratch array below
+    const bool st = stretched(*grid);
+    std::vector<double> zplanes;
+    std::vector<Plane<double>> table;
+    if (st) {
+        const char* why = "";
+        if (!make_planes(*grid, zplanes, &why)) {
+            char msg[160];
+            snprintf(msg, sizeof msg, "cm_diag_noalloc: %s", why);
+            return set_error(CM_EINVAL, msg);
+        }
+        plane_table(zplanes, table);
+    }
 
     double* base = nullptr;
     int rc = scratch_on_current_device(&base);
@@ -123,6 +142,7 @@ extern "C" int cm_diag_noalloc(const void* state, int precision, const cm_grid* 
     cm_diag* rec = reinterpret_cast<cm_diag*>(base + kCtlWords);
     double* zt = base + kZOff;
     double* planes = base + kPlanesOff;
+    Plane<double>* ztab = reinterpret_cast<Plane<double>*>(base + kTableOff);
     cudaStream_t s = (cudaStream_t)stream;
 
     // control block of this call: status cleared, time, steps, dt in slot 0
@@ -132,7 +152,11 @@ extern "C" int cm_diag_noalloc(const void* state, int precision, const cm_grid* 
     h.steps = (double)step;
     std::memcpy(&h.dt_slot[0], &dt, sizeof dt);
     cudaError_t e = cudaMemcpyAsync(ctl, &h, sizeof h, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && st) {
+        e = cudaMemcpyAsync(zt, zplanes.data(), grid->nz * sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ztab, table.data(), grid->nz * sizeof(Plane<double>), cudaMemcpyHostToDevice, s);
+    } else if (e == cudaSuccess) {
         fill_plane_z<<<(grid->nz + 255) / 256, 256, 0, s>>>(zt, grid->nz);
         e = cudaGetLastError();
     }
@@ -158,6 +182,7 @@ extern "C" int cm_diag_noalloc(const void* state, int precision, const cm_grid* 
     F.cells = (double)grid->nx * ny;
     F.nz = grid->nz;
     F.slot = 0;
+    F.zp = st ? ztab : nullptr;
     if (e == cudaSuccess) e = launch_diag_final(planes, zt, F, ctl, rec, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, rec, sizeof(cm_diag), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -153,6 +153,21 @@ struct Profile {
     }
 };
 
+// Diffusion number of the explicit viscous / conduction terms at step dt:
+// nu = max(4/3 mu, K b) / min rho over the smallest spacing h (x or z),
+// nu (dt/2) / h^2 (each sweep advances by dt/2).  Above 0.5 the explicit
+// sweeps are unstable.
+inline double diffusion_number(const cm_grid& G, const std::vector<double>& planes, double Ra, double Pr,
+                               const cm_params& P, const Closure& K, double rho_min, double dt)
+{
+    const double mu = std::sqrt(Pr / Ra), kth = 1.0 / (P.eps * P.D * std::sqrt(Ra * Pr));
+    const double nu = std::fmax(4.0 / 3.0 * mu, kth * K.b) / rho_min;
+    double hz = 1.0 / (double)(planes.size() - 1);
+    for (size_t k = 0; k + 1 < planes.size(); ++k) hz = std::fmin(hz, planes[k + 1] - planes[k]);
+    const double hh = std::fmin(G.aspect / G.nx, hz);
+    return nu * 0.5 * dt / (hh * hh);
+}
+
 int pitch_of(int nx, int prec);
 
 }  // namespace cm

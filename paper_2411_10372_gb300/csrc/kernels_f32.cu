@@ -41,22 +41,40 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool const_coefs, cudaStream_t s)
+cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool const_coefs, bool stretched,
+                               cudaStream_t s)
 {
+    // stretched: per-warp plane caches of 5 (z) or 2 (x) values per plane after the ring
+    constexpr size_t kCacheZ = kRingBytes + (size_t)kWarpsPerBlock * plane_cap2(kBatchSegMax) * 5 * sizeof(float);
+    constexpr size_t kCacheX = kRingBytes + (size_t)kWarpsPerBlock * plane_cap2(kBatchSegMax) * 2 * sizeof(float);
     static bool init = false;
     if (!init) {
         cudaFuncSetAttribute(sweep_z2d_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         cudaFuncSetAttribute(sweep_x2d_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         cudaFuncSetAttribute(sweep_z2d_batch_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         cudaFuncSetAttribute(sweep_x2d_batch_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        cudaFuncSetAttribute(sweep_z2d_batch_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheZ);
+        cudaFuncSetAttribute(sweep_x2d_batch_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheX);
+        cudaFuncSetAttribute(sweep_z2d_batch_smem_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheZ);
+        cudaFuncSetAttribute(sweep_x2d_batch_smem_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheX);
         init = true;
     }
     if (dir == 2) {
-        if (const_coefs) sweep_z2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
-        else sweep_z2d_batch_smem<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+        if (stretched) {
+            if (const_coefs) sweep_z2d_batch_s<<<nblocks, kThreads2, kCacheZ, s>>>(L);
+            else sweep_z2d_batch_smem_s<<<nblocks, kThreads2, kCacheZ, s>>>(L);
+        } else {
+            if (const_coefs) sweep_z2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+            else sweep_z2d_batch_smem<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+        }
     } else if (dir == 0) {
-        if (const_coefs) sweep_x2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
-        else sweep_x2d_batch_smem<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+        if (stretched) {
+            if (const_coefs) sweep_x2d_batch_s<<<nblocks, kThreads2, kCacheX, s>>>(L);
+            else sweep_x2d_batch_smem_s<<<nblocks, kThreads2, kCacheX, s>>>(L);
+        } else {
+            if (const_coefs) sweep_x2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+            else sweep_x2d_batch_smem<<<nblocks, kThreads2, kRingBytes, s>>>(L);
+        }
     } else {
         return cudaErrorInvalidValue;
     }

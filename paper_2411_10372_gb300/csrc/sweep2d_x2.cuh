@@ -726,7 +726,10 @@ __device__ __forceinline__ const BatchWork& batch_item(const BatchLaunch& L, Swe
     return w;
 }
 
-__global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch(const __grid_constant__ BatchLaunch L)
+// one batched sweep (Z: the z sweep, else x) with each box's coefficients in
+// constant memory; ST: stretched z-grids (every box's C.zp set)
+template <bool Z, bool ST>
+__device__ __forceinline__ void batch_sweep_const(const BatchLaunch& L)
 {
     SweepCtl sc;
     const float* in;
@@ -734,25 +737,15 @@ __global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch(const __grid_con
     int box;
     const BatchWork& w = batch_item(L, sc, in, out, box);
     box = __shfl_sync(0xffffffffu, box, 0);  // warp-uniform index into the constant bank
-    z2_body(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
-}
-
-__global__ void __launch_bounds__(kThreads2, 4) sweep_x2d_batch(const __grid_constant__ BatchLaunch L)
-{
-    SweepCtl sc;
-    const float* in;
-    float* out;
-    int box;
-    const BatchWork& w = batch_item(L, sc, in, out, box);
-    box = __shfl_sync(0xffffffffu, box, 0);
-    x2_body(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+    if constexpr (Z) z2_body<ST>(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+    else x2_body<ST>(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
 }
 
 // the same for batches of more than kConstBoxes boxes: the block stages its
-// box's coefficients in shared memory
-__global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch_smem(const __grid_constant__ BatchLaunch L)
+// box's coefficients in shared memory (sC)
+template <bool Z, bool ST>
+__device__ __forceinline__ void batch_sweep_smem(const BatchLaunch& L, Coef<float>& sC)
 {
-    __shared__ Coef<float> sC;
     SweepCtl sc;
     const float* in;
     float* out;
@@ -760,20 +753,54 @@ __global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch_smem(const __gri
     const BatchWork& w = batch_item(L, sc, in, out, box);
     if (threadIdx.x == 0) sC = L.boxes[box].C;
     __syncthreads();
-    z2_body(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+    if constexpr (Z) z2_body<ST>(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+    else x2_body<ST>(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch(const __grid_constant__ BatchLaunch L)
+{
+    batch_sweep_const<true, false>(L);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_x2d_batch(const __grid_constant__ BatchLaunch L)
+{
+    batch_sweep_const<false, false>(L);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch_smem(const __grid_constant__ BatchLaunch L)
+{
+    __shared__ Coef<float> sC;
+    batch_sweep_smem<true, false>(L, sC);
 }
 
 __global__ void __launch_bounds__(kThreads2, 4) sweep_x2d_batch_smem(const __grid_constant__ BatchLaunch L)
 {
     __shared__ Coef<float> sC;
-    SweepCtl sc;
-    const float* in;
-    float* out;
-    int box;
-    const BatchWork& w = batch_item(L, sc, in, out, box);
-    if (threadIdx.x == 0) sC = L.boxes[box].C;
-    __syncthreads();
-    x2_body(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+    batch_sweep_smem<false, false>(L, sC);
+}
+
+// batches with stretched z-grids: each warp's plane cache follows the row
+// ring in dynamic shared memory, sized for segments of up to kBatchSegMax rows
+__global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch_s(const __grid_constant__ BatchLaunch L)
+{
+    batch_sweep_const<true, true>(L);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_x2d_batch_s(const __grid_constant__ BatchLaunch L)
+{
+    batch_sweep_const<false, true>(L);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch_smem_s(const __grid_constant__ BatchLaunch L)
+{
+    __shared__ Coef<float> sC;
+    batch_sweep_smem<true, true>(L, sC);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4) sweep_x2d_batch_smem_s(const __grid_constant__ BatchLaunch L)
+{
+    __shared__ Coef<float> sC;
+    batch_sweep_smem<false, true>(L, sC);
 }
 
 // shared memory of the row ring for a block

@@ -90,8 +90,8 @@ def test_argument_errors_need_no_gpu():
 
 def test_stretched_grid_argument_errors_need_no_gpu():
     """The z-grid is validated before any device work: planes must run from
-    exactly 0 to exactly 1 and increase; beta must be in [0, 20]; stretched
-    grids are single contexts only (the batch rejects them)."""
+    exactly 0 to exactly 1 and increase; beta must be in [0, 20]; the batch
+    checks each box's grid the same way, and cm_diag_noalloc its grid."""
     import numpy as np
     bad = [np.linspace(0, 1, 16) * 0.99, np.r_[0.0, 0.5, 0.3, np.linspace(0.6, 1, 13)],
            np.r_[1e-9, np.linspace(0.1, 1, 15)], np.r_[0.0, np.nan, np.linspace(0.2, 1, 14)]]
@@ -104,6 +104,13 @@ def test_stretched_grid_argument_errors_need_no_gpu():
         with pytest.raises(cm.CMError) as e:
             cm.cm_init(cm.cm_grid(2, 64, 1, 16, 4.0, beta), 1e6, 1.0, 5 / 3)
         assert e.value.code == cm.CM_EINVAL, beta
-    with pytest.raises(cm.CMError) as e:
-        cm.cm_batch_init([cm.cm_grid(2, 64, 1, 16, 4.0, 1.5)], [1e6], 1.0, 5 / 3)
-    assert e.value.code == cm.CM_EINVAL
+    p = cm.cm_default_params()
+    p.precision = cm.CM_FP32
+    for beta in (-1.0, 25.0):
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_batch_init([cm.cm_grid(2, 64, 1, 16, 4.0), cm.cm_grid(2, 64, 1, 16, 4.0, beta)], [1e6, 1e6], 1.0,
+                             5 / 3, p)
+        assert e.value.code == cm.CM_EINVAL and "box 1" in cm.cm_last_error(), beta
+        with pytest.raises(cm.CMError) as e:  # rejected before the scratch array is touched
+            cm.cm_diag_noalloc(1 << 20, cm.CM_FP32, cm.cm_grid(2, 64, 1, 16, 4.0, beta), 64, 1e6, 1.0, 5 / 3, p)
+        assert e.value.code == cm.CM_EINVAL and "zstretch" in cm.cm_last_error(), beta

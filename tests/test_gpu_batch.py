@@ -6,6 +6,7 @@ differently (the autotuner), and the FP32 sweeps are reproducible only for a
 fixed split (at the FP32 noise level otherwise), which this unstable flow
 amplifies to ~2e-6 over 63 steps; 1e-5 is the bar, far below what a wrong
 work item, dt slot or graph replay would produce."""
+import ctypes
 import math
 
 import numpy as np
@@ -90,7 +91,71 @@ def test_batch_rejects_bad_boxes():
         cm.cm_batch_init([cm.cm_grid(2, 64, 1, 17, 4.0)], [1e6], 1.0, 5.0 / 3.0, p)
 
 
-def test_large_batch_stages_coefficients_in_shared_memory():
+def test_stretched_batch_boxes_equal_their_solo_runs():
+    """Boxes on tanh z-grids (beta 1 and 2), one on given planes and one
+    uniform box share a batch: the plane-table sweeps step every box, and each
+    box equals its solo run on the same planes (the uniform box: znodes =
+    k/K).  The plate Nusselt numbers and the mass use the stretched-grid
+    weights, which differ from the uniform ones by far more than the bars
+    (eps = 0.1 is the default of _params)."""
+    import paper_2411_10372_gb300 as cm
+    sizes = [(68, 17), (132, 33), (160, 40), (256, 64)]
+    ras = [1e5, 3e6, 1e7, 1e6]
+    s0 = np.linspace(0.0, 1.0, sizes[2][1])
+    given = s0 - 0.6 * np.sin(2 * np.pi * s0) / (2 * np.pi)  # plates refined, strictly increasing
+    given[0], given[-1] = 0.0, 1.0
+    uniform = np.arange(sizes[3][1]) / (sizes[3][1] - 1)
+    solo_kw = [dict(zstretch=1.0), dict(zstretch=2.0), dict(znodes=given), dict(znodes=uniform)]
+    given_ptr = given.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    grids = [cm.cm_grid(2, sizes[0][0], 1, sizes[0][1], 4.0, 1.0), cm.cm_grid(2, sizes[1][0], 1, sizes[1][1], 4.0, 2.0),
+             cm.cm_grid(2, sizes[2][0], 1, sizes[2][1], 4.0, 0.0, given_ptr), cm.cm_grid(2, sizes[3][0], 1, sizes[3][1], 4.0)]
+    nsteps = 63
+    cm.cm_batch_init(grids, ras, 1.0, 5.0 / 3.0, _params(cm, seed=91))
+    cm.cm_batch_step(nsteps)
+    diags = cm.cm_batch_diagnostics()
+    states = [cm.cm_batch_get_state(b, np.empty((4, nz, nx))) for b, (nx, nz) in enumerate(sizes)]
+    cm.cm_batch_finalize()
+    for b, (nx, nz) in enumerate(sizes):
+        s = cm.Solver(nx, nz, ras[b], 1.0, 5.0 / 3.0, precision="fp32", seed=91 + b, **solo_kw[b])
+        s.step(nsteps)
+        solo = s.state()
+        d = s.sample()
+        z = s.z
+        s.close()
+        for f in range(4):
+            err = np.linalg.norm(states[b][f] - solo[f]) / np.linalg.norm(solo[f] if f in (0, 3) else solo[0])
+            assert err <= 1e-5, (b, f, err)
+        assert diags[b]["status"] == 0 and diags[b]["step"] == nsteps
+        for k in ("t", "dt", "mass"):
+            assert abs(diags[b][k] - d[k]) <= 1e-5 * abs(d[k]), (b, k)
+        # plate Nu: a difference of the plane means of T (1e-6 allowed, the
+        # FP32 split noise) enters amplified by the three-plane derivative
+        # coefficients over eps; uniform-grid weights on these planes would be
+        # off by O(1)
+        for k, (a, m, c) in (("Nu_bot", z[:3]), ("Nu_top", z[::-1][:3])):
+            h1, h2 = abs(m - a), abs(c - m)
+            amp = ((2 * h1 + h2) / (h1 * (h1 + h2)) + (h1 + h2) / (h1 * h2) + h1 / (h2 * (h1 + h2))) / 0.1
+            assert abs(diags[b][k] - d[k]) <= 1e-6 * amp, (b, k, diags[b][k], d[k], 1e-6 * amp)
+
+
+def test_batch_rejects_a_box_beyond_the_explicit_diffusion_bound():
+    """cm_init's bound on the explicit diffusion number holds per box: on
+    the tanh grid of beta = 2 the 1016 x 254 box at Ra = 1.5e5 has a first
+    spacing of 5.8e-4 and a diffusion number of 1.36 at its first dt."""
+    import paper_2411_10372_gb300 as cm
+    grids = [cm.cm_grid(2, 128, 1, 32, 4.0, 2.0), cm.cm_grid(2, 1016, 1, 254, 4.0, 2.0)]
+    with pytest.raises(cm.CMError) as e:
+        cm.cm_batch_init(grids, [1e7, 1.48e5], 1.0, 5.0 / 3.0, _params(cm))
+    assert e.value.code == cm.CM_EUNSTABLE and "box 1" in str(e.value), str(e.value)
+    with pytest.raises(cm.CMError) as e:
+        cm.Solver(1016, 254, 1.48e5, 1.0, 5.0 / 3.0, precision="fp32", zstretch=2.0)
+    assert e.value.code == cm.CM_EUNSTABLE
+    cm.cm_batch_init([cm.cm_grid(2, 1016, 1, 254, 4.0, 1.0)], [1.48e5], 1.0, 5.0 / 3.0, _params(cm))
+    cm.cm_batch_finalize()
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.5])
+def test_large_batch_stages_coefficients_in_shared_memory(beta):
     """More boxes than the constant-memory table holds (300 > 256): the
     kernels that stage each box's coefficients in shared memory run, and a
     box of an uneven mix (different Ra, hence different mu and K) still
@@ -99,7 +164,7 @@ def test_large_batch_stages_coefficients_in_shared_memory():
     n = 300
     sizes = [(16 + 2 * (b % 5), 6 + b % 4) for b in range(n)]
     ras = [1e5 * (1 + b % 7) for b in range(n)]
-    grids = [cm.cm_grid(2, nx, 1, nz, 4.0) for nx, nz in sizes]
+    grids = [cm.cm_grid(2, nx, 1, nz, 4.0, beta) for nx, nz in sizes]
     cm.cm_batch_init(grids, ras, 1.0, 5.0 / 3.0, _params(cm, seed=31))
     nsteps = 7
     cm.cm_batch_step(nsteps)
@@ -110,7 +175,7 @@ def test_large_batch_stages_coefficients_in_shared_memory():
     assert all(d["status"] == 0 and d["step"] == nsteps for d in diags)
     for b in picks:
         nx, nz = sizes[b]
-        s = cm.Solver(nx, nz, ras[b], 1.0, 5.0 / 3.0, precision="fp32", seed=31 + b)
+        s = cm.Solver(nx, nz, ras[b], 1.0, 5.0 / 3.0, precision="fp32", seed=31 + b, zstretch=beta)
         s.step(nsteps)
         solo = s.state()
         s.close()

@@ -7,8 +7,11 @@ uses only a fixed scratch array inside libcm.so.  Here it is called through
 the C ABI on the solver's own state and must reproduce the record of the
 context entry point (cm_sample + cm_diagnostics) within the diagnostics
 tolerance of the parity tests (1e-12 relative), on two calls in a row, for
-FP64 and FP32 states.  This file is collected last on purpose.
+FP64 and FP32 states on uniform and stretched z-grids.  This file is
+collected last on purpose.
 """
+import ctypes
+
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -21,11 +24,23 @@ def _close(a, b, tol=1e-12):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_noalloc_diagnostics_match_context_entry_point(precision):
+@pytest.mark.parametrize("zgrid", ["uniform", "tanh", "given"])
+def test_noalloc_diagnostics_match_context_entry_point(precision, zgrid):
+    """Uniform planes, the tanh grid (beta = 2) and given planes: on the
+    stretched grids the plate Nusselt numbers and the volume averages use the
+    plane table copied into the scratch array."""
+    import numpy as np
     import paper_2411_10372_gb300 as cm
     code = cm.CM_FP64 if precision == "fp64" else cm.CM_FP32
     Ra, Pr, gamma = 1e6, 1.0, 5.0 / 3.0
-    s = cm.Solver(256, 64, Ra, Pr, gamma, precision=precision)
+    z = np.linspace(0.0, 1.0, 64)
+    z = z - 0.5 * np.sin(2 * np.pi * z) / (2 * np.pi)
+    z[0], z[-1] = 0.0, 1.0
+    kw = {"uniform": {}, "tanh": {"zstretch": 2.0}, "given": {"znodes": z}}[zgrid]
+    s = cm.Solver(256, 64, Ra, Pr, gamma, precision=precision, **kw)
+    grid = s.grid
+    if zgrid == "given":  # the solver's grid drops znodes after cm_init
+        grid = cm.cm_grid(2, 256, 1, 64, s.grid.aspect, 0.0, z.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     try:
         for n_more in (40, 7):  # two states: the second call sees the first call's scratch
             s.step(n_more)
@@ -34,7 +49,7 @@ def test_noalloc_diagnostics_match_context_entry_point(precision):
             dt = cm.cm_get_dt()
             ref = s.sample()
             for _ in range(2):  # two calls in a row on the same state
-                got = cm.cm_diag_noalloc(cm.cm_state_ptr(0), code, s.grid, pitch, Ra, Pr, gamma, s.params,
+                got = cm.cm_diag_noalloc(cm.cm_state_ptr(0), code, grid, pitch, Ra, Pr, gamma, s.params,
                                          t, dt, steps)
                 assert got["status"] == 0 and got["step"] == ref["step"] == steps
                 for k in KEYS:
