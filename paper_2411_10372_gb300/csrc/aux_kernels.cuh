@@ -54,27 +54,24 @@ __global__ void init_state(R* X, Coef<R> C, InitArgs A)
 // after cm_set_state; during stepping the last sweep does this reduction).
 // FP64 states: the sweeps' exact FP64 operation order.  FP32 states: the FP32
 // rates (|u|+c)/h of the FP32 sweeps, one FP64 reciprocal of the block max.
+// CFL bound of the nodes one thread visits (Sec. 3.1): FP32 keeps the largest
+// rate max((|u_x| + c)/h_x, (|u_z| + c)/h_z), FP64 the smallest
+// min(h/(|u| + c)) with the divisions of the sweeps' FP64 path; h_z of plane
+// k is its smaller adjacent spacing on a stretched grid.
 template <class R>
-__global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int slot)
-{
+struct DtAcc {
     double vmin = 1e308;
     float rmax = 0.f;
     int bad = 0;
-    const long long plane = (long long)C.nx * C.ny;
-    const long long total = plane * C.nz;
-    const long long fs = C.fstride;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total; n += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(n % C.nx);
-        const long long jk = n / C.nx;
-        const int j = (int)(jk % C.ny);
-        const int k = (int)(jk / C.ny);
-        const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
+    // node values rho, m_x, (m_y,) m_z, E of plane k (3D: five values)
+    __device__ __forceinline__ void add(const R* v, int k, const R* zt, const Coef<R>& C)
+    {
         if constexpr (!kExact<R>) {
-            const float rho = p[0], ri = 1.f / rho;
-            const float ux = p[fs] * ri;
+            const float rho = v[0], ri = 1.f / rho;
+            const float ux = v[1] * ri;
             float uy = 0.f, uz, E;
-            if (C.ndim == 3) { uy = p[2 * fs] * ri; uz = p[3 * fs] * ri; E = p[4 * fs]; }
-            else { uz = p[2 * fs] * ri; E = p[3 * fs]; }
+            if (C.ndim == 3) { uy = v[2] * ri; uz = v[3] * ri; E = v[4]; }
+            else { uz = v[2] * ri; E = v[3]; }
             const float T = C.b * (E * ri - 0.5f * ((ux * ux + uy * uy) + uz * uz) - C.g * zt[k]);
             const float c = sqrtf(C.cs2 * T);
             float r = fmaxf((fabsf(ux) + c) * C.inv_dx, (fabsf(uz) + c) * (C.zp ? C.zp[k].ihmin : C.inv_dz));
@@ -83,20 +80,72 @@ __global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int s
             rmax = fmaxf(rmax, r);
         } else {
             // same operation order as the sweeps' FP64 path (divisions by rho)
-            const double rho = (double)p[0];
-            double ux = (double)p[fs] / rho, uy = 0.0, uz, E;
-            if (C.ndim == 3) { uy = (double)p[2 * fs] / rho; uz = (double)p[3 * fs] / rho; E = (double)p[4 * fs]; }
-            else { uz = (double)p[2 * fs] / rho; E = (double)p[3 * fs]; }
+            const double rho = (double)v[0];
+            double ux = (double)v[1] / rho, uy = 0.0, uz, E;
+            if (C.ndim == 3) { uy = (double)v[2] / rho; uz = (double)v[3] / rho; E = (double)v[4]; }
+            else { uz = (double)v[2] / rho; E = (double)v[3]; }
             const double T = (double)C.b * (E / rho - 0.5 * ((ux * ux + uy * uy) + uz * uz) - (double)C.g * (double)zt[k]);
             const double c = sqrt((double)C.cs2 * T);
-            double v = fmin(C.dx / (fabs(ux) + c), (C.zp ? (double)C.zp[k].hmin : C.dz) / (fabs(uz) + c));
-            if (C.ndim == 3) v = fmin(v, C.dy / (fabs(uy) + c));
-            if (!(v > 0.0) || !(v < 1e300)) bad = 1;
-            vmin = fmin(vmin, v);
+            double h = fmin(C.dx / (fabs(ux) + c), (C.zp ? (double)C.zp[k].hmin : C.dz) / (fabs(uz) + c));
+            if (C.ndim == 3) h = fmin(h, C.dy / (fabs(uy) + c));
+            if (!(h > 0.0) || !(h < 1e300)) bad = 1;
+            vmin = fmin(vmin, h);
         }
     }
-    if constexpr (!kExact<R>) vmin = rmax > 0.f ? 1.0 / (double)rmax : 1e308;
-    block_dt_reduce(vmin, bad, ctl, slot);
+    // the block's contribution to the dt slot (smallest h/(|u| + c))
+    __device__ __forceinline__ double result() const
+    {
+        if constexpr (!kExact<R>) return rmax > 0.f ? 1.0 / (double)rmax : 1e308;
+        else return vmin;
+    }
+};
+
+template <class R>
+__global__ void dt_reduce(const R* X, const R* zt, Coef<R> C, DevCtl* ctl, int slot)
+{
+    DtAcc<R> acc;
+    const long long plane = (long long)C.nx * C.ny;
+    const long long total = plane * C.nz;
+    const long long fs = C.fstride;
+    const int nf = C.ndim == 3 ? 5 : 4;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total; n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % C.nx);
+        const long long jk = n / C.nx;
+        const int j = (int)(jk % C.ny);
+        const int k = (int)(jk / C.ny);
+        const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
+        R v[5];
+        for (int f = 0; f < nf; ++f) v[f] = p[f * fs];
+        acc.add(v, k, zt, C);
+    }
+    block_dt_reduce(acc.result(), acc.bad, ctl, slot);
+}
+
+// Packs planes [k0, k1) of a dense state (field-major, then k, j, i; any
+// element type S, converted to R) into the pitched layout X and reduces the
+// CFL bound of those nodes into dt slot `slot`, the operations of dt_reduce
+// on the packed values.  One launch per plane chunk of an upload.
+template <class R, class S>
+__global__ void pack_dt(const S* __restrict__ dense, R* __restrict__ X, const R* __restrict__ zt, Coef<R> C,
+                        DevCtl* ctl, int slot, int k0, int k1)
+{
+    DtAcc<R> acc;
+    const long long plane = (long long)C.nx * C.ny;
+    const long long field = plane * C.nz;
+    const int nf = C.ndim == 3 ? 5 : 4;
+    for (long long n = plane * k0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; n < plane * k1;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % C.nx);
+        const long long row = n / C.nx;  // k*ny + j
+        const int k = (int)(row / C.ny);
+        R v[5];
+        for (int f = 0; f < nf; ++f) {
+            v[f] = (R)dense[f * field + n];
+            X[f * C.fstride + row * C.pitch + i] = v[f];
+        }
+        acc.add(v, k, zt, C);
+    }
+    block_dt_reduce(acc.result(), acc.bad, ctl, slot);
 }
 
 // ---- diagnostics ---------------------------------------------------------

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/cm.h"
@@ -22,6 +23,8 @@
 using namespace cm;
 
 namespace {
+
+constexpr int kUpChunks = 4;  // most plane chunks of a copied host upload
 
 // state of the adjoint (cm_adj_forward / cm_adj_backward)
 struct AdjCtx {
@@ -59,6 +62,8 @@ struct Ctx {
     double* ext_prims;          // extended diagnostics: FP64 rho, u, T of every node (5 x nodes), first use
     unsigned long long* ext_hist; // histogram counts (kExtMaxBins), allocated on first use
     double* dense;              // dense FP64 staging for host transfers (lazy)
+    cudaStream_t copy_stream;   // host uploads: chunk copies (lazy, with dense)
+    cudaEvent_t up_ev[kUpChunks + 1];  // chunk q arrived (q < kUpChunks); compute stream ready (last)
     cm_diag* ring;
     int ring_cap, ring_head, ring_count;
     cudaStream_t stream;
@@ -119,6 +124,9 @@ void free_ctx(Ctx* c)
     cudaFree(c->ext_prims);
     cudaFree(c->ext_hist);
     cudaFree(c->dense);
+    for (cudaEvent_t& e : c->up_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     cudaFree(c->ring);
     if (c->adj) {
         cudaFree(c->adj->ckpt);
@@ -215,23 +223,95 @@ int ensure_dense(Ctx* c)
         cudaGetLastError();
         return fail(CM_ENOMEM, "cudaMalloc of %zu bytes (host transfer staging) failed", n * sizeof(double));
     }
+    bool ok = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t& e : c->up_ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return fail(CM_ECUDA, "creation of the upload stream and events failed");
+    }
     return CM_OK;
 }
 
 size_t dense_count(const Ctx* c) { return (size_t)c->nf * c->grid.nz * c->ny * c->grid.nx; }
 
-int upload(Ctx* c, const double* host)
+// Device address of a pinned host array of `count` elements that the GPU can
+// read in place (one mapped range: both ends pinned, their device addresses
+// as far apart as their host addresses), else NULL.
+template <class S>
+const S* mapped_view(const S* host, size_t count)
 {
-    int rc = ensure_dense(c);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(c->dense, host, dense_count(c) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    cudaError_t e = c->prec == CM_FP64
-        ? Launch<double>::pack(c->dense, (double*)c->buf[c->cur], c->cd, c->nf, c->stream)
-        : Launch<float>::pack(c->dense, (float*)c->buf[c->cur], c->cf, c->nf, c->stream);
+    cudaPointerAttributes a0, a1;
+    if (cudaPointerGetAttributes(&a0, host) != cudaSuccess ||
+        cudaPointerGetAttributes(&a1, host + (count - 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+        return nullptr;
+    if ((const char*)a1.devicePointer - (const char*)a0.devicePointer != (ptrdiff_t)((count - 1) * sizeof(S)))
+        return nullptr;
+    return (const S*)a0.devicePointer;
+}
+
+// packs planes [k0, k1) of the dense array src (device-readable) into the
+// current buffer, their CFL bound reduced into dt slot `slot`
+template <class S>
+int pack_planes(Ctx* c, const S* src, int slot, int k0, int k1)
+{
+    cudaError_t e;
+    if constexpr (std::is_same<S, double>::value)
+        e = c->prec == CM_FP64
+            ? Launch<double>::pack_dt(src, (double*)c->buf[c->cur], (const double*)c->zt_r, c->cd, c->ctl, slot, k0, k1, c->stream)
+            : Launch<float>::pack_dt(src, (float*)c->buf[c->cur], (const float*)c->zt_r, c->cf, c->ctl, slot, k0, k1, c->stream);
+    else
+        e = Launch<float>::pack_dt32(src, (float*)c->buf[c->cur], (const float*)c->zt_r, c->cf, c->ctl, slot, k0, k1, c->stream);
     if (e != cudaSuccess) return fail(CM_ECUDA, "pack launch: %s", cudaGetErrorString(e));
     c->launches++;
-    return recompute_dt(c, (int)(c->step & 1));
+    return CM_OK;
 }
+
+// Upload of a dense host state (S = double or float) into the current
+// buffer, with the step's dt recomputed by the same kernel (pack_dt).  A
+// pinned host array is read in place over the host link by that one kernel.
+// Other host memory is copied in up to kUpChunks plane chunks (one 2D copy
+// of all fields per chunk) on the copy stream into the staging array, and
+// each chunk is packed on the compute stream as soon as it has arrived, so
+// the packing of one chunk runs under the copy of the next.
+template <class S>
+int upload_host(Ctx* c, const S* host)
+{
+    const int slot = (int)(c->step & 1), nz = c->grid.nz;
+    const size_t plane = (size_t)c->ny * c->grid.nx, field = plane * nz;
+    const unsigned long long inf = 0x7FF0000000000000ULL;
+    CK(cudaMemcpyAsync(&c->ctl->dt_slot[slot], &inf, sizeof inf, cudaMemcpyHostToDevice, c->stream));
+    if (const S* view = mapped_view(host, field * c->nf)) return pack_planes(c, view, slot, 0, nz);
+    int rc = ensure_dense(c);
+    if (rc) return rc;
+    S* staging = (S*)c->dense;  // sized for float64, so it holds either type
+    const size_t bytes = field * c->nf * sizeof(S), fbytes = field * sizeof(S);
+    const int nch = (int)std::min<size_t>({(size_t)kUpChunks, (size_t)nz, std::max<size_t>(1, bytes >> 23)});
+    // the staging array may still be read by earlier work on the compute stream
+    CK(cudaEventRecord(c->up_ev[kUpChunks], c->stream));
+    CK(cudaStreamWaitEvent(c->copy_stream, c->up_ev[kUpChunks], 0));
+    for (int q = 0; q < nch; ++q) {
+        const int k0 = (int)((long long)nz * q / nch), k1 = (int)((long long)nz * (q + 1) / nch);
+        const size_t off = k0 * plane, w = (k1 - k0) * plane * sizeof(S);
+        if (fbytes <= ((size_t)1 << 30)) {
+            CK(cudaMemcpy2DAsync(staging + off, fbytes, host + off, fbytes, w, c->nf, cudaMemcpyHostToDevice,
+                                 c->copy_stream));
+        } else {
+            for (int f = 0; f < c->nf; ++f)
+                CK(cudaMemcpyAsync(staging + f * field + off, host + f * field + off, w, cudaMemcpyHostToDevice,
+                                   c->copy_stream));
+        }
+        CK(cudaEventRecord(c->up_ev[q], c->copy_stream));
+        CK(cudaStreamWaitEvent(c->stream, c->up_ev[q], 0));
+        if ((rc = pack_planes(c, (const S*)staging, slot, k0, k1))) return rc;
+    }
+    return CM_OK;
+}
+
+int upload(Ctx* c, const double* host) { return upload_host(c, host); }
 
 int download(Ctx* c, double* host)
 {
@@ -859,13 +939,7 @@ int cm_run_host_f32(const float* state_in, int nsteps, float* state_out, cm_diag
     if ((state_in || state_out) && (rc = ensure_dense(c))) return rc;
     dense32 = (float*)c->dense;  // the FP64 staging area holds twice as many floats
     const size_t bytes = dense_count(c) * sizeof(float);
-    if (state_in) {
-        CK(cudaMemcpyAsync(dense32, state_in, bytes, cudaMemcpyHostToDevice, c->stream));
-        cudaError_t e = Launch<float>::pack32(dense32, (float*)c->buf[c->cur], c->cf, c->nf, c->stream);
-        if (e != cudaSuccess) return fail(CM_ECUDA, "pack launch: %s", cudaGetErrorString(e));
-        c->launches++;
-        if ((rc = recompute_dt(c, (int)(c->step & 1)))) return rc;
-    }
+    if (state_in && (rc = upload_host(c, state_in))) return rc;
     if ((rc = queue_steps(c, nsteps))) return rc;
     if (state_out) {
         cudaError_t e = Launch<float>::unpack32((const float*)c->buf[c->cur], dense32, c->cf, c->nf, c->stream);

@@ -50,6 +50,12 @@ struct Launch {
     // the same with a dense float32 array
     static cudaError_t pack32(const float* dense, R* X, const Coef<R>& C, int nf, cudaStream_t s);
     static cudaError_t unpack32(const R* X, float* dense, const Coef<R>& C, int nf, cudaStream_t s);
+    // planes [k0, k1) of a dense float64 / float32 [nf][nz][ny][nx] array into
+    // the pitched state, their CFL bound reduced into dt slot `slot` (as dt)
+    static cudaError_t pack_dt(const double* dense, R* X, const R* zt, const Coef<R>& C, DevCtl* ctl, int slot,
+                               int k0, int k1, cudaStream_t s);
+    static cudaError_t pack_dt32(const float* dense, R* X, const R* zt, const Coef<R>& C, DevCtl* ctl, int slot,
+                                 int k0, int k1, cudaStream_t s);
 };
 
 // FP32 sweeps with two columns per lane (nx even); defined in kernels_f32.cu.

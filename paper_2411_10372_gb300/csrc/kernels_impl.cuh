@@ -260,4 +260,22 @@ cudaError_t Launch<R>::unpack32(const R* X, float* dense, const Coef<R>& C, int 
     return cudaGetLastError();
 }
 
+template <class R>
+cudaError_t Launch<R>::pack_dt(const double* dense, R* X, const R* zt, const Coef<R>& C, DevCtl* ctl, int slot,
+                               int k0, int k1, cudaStream_t s)
+{
+    cm::pack_dt<R, double><<<grid_for((long long)C.nx * C.ny * (k1 - k0), 256), 256, 0, s>>>(dense, X, zt, C, ctl,
+                                                                                             slot, k0, k1);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t Launch<R>::pack_dt32(const float* dense, R* X, const R* zt, const Coef<R>& C, DevCtl* ctl, int slot,
+                                 int k0, int k1, cudaStream_t s)
+{
+    cm::pack_dt<R, float><<<grid_for((long long)C.nx * C.ny * (k1 - k0), 256), 256, 0, s>>>(dense, X, zt, C, ctl,
+                                                                                            slot, k0, k1);
+    return cudaGetLastError();
+}
+
 }  // namespace cm

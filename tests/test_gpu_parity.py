@@ -232,6 +232,57 @@ def test_run_host_f32_matches_run_host():
         s.close()
 
 
+@pytest.mark.parametrize("precision,ndim,beta", [("fp32", 2, 0.0), ("fp64", 2, 0.0), ("fp32", 2, 2.0), ("fp32", 3, 0.0)])
+def test_chunked_upload_reproduces_the_device_path(precision, ndim, beta):
+    """Pageable host states are uploaded in plane chunks (4 here), each
+    packed, its CFL bound reduced into the dt slot, as soon as it arrives.
+    The initial state read back and uploaded again must give the dt that the
+    init kernel computed, bit for bit, and then the same steps."""
+    import paper_2411_10372_gb300 as cm
+    if ndim == 2:
+        s = cm.Solver(2048, 512, 1e8, precision=precision, zstretch=beta)
+    else:
+        s = cm.Solver(128, 64, 1e7, ny=128, ndim=3, precision=precision)
+    try:
+        dt0 = s.dt()
+        X0 = s.state()
+        s.step(5)
+        A = s.state()
+        s.set_state(X0)
+        assert s.dt() == dt0
+        s.step(5)
+        assert np.array_equal(s.state(), A)
+    finally:
+        s.close()
+
+
+def test_pinned_upload_reads_in_place_and_equals_the_copied_upload():
+    """A pinned host state is read in place by the upload kernel; pageable
+    memory goes through chunked copies.  Both give the same run, bit for
+    bit, for float64 and float32 host arrays."""
+    torch = pytest.importorskip("torch")
+    import paper_2411_10372_gb300 as cm
+    s = cm.Solver(2048, 512, 1e8, precision="fp32")
+    try:
+        s.step(3)
+        X = s.state()
+        for dtype, run in ((np.float64, cm.cm_run_host), (np.float32, cm.cm_run_host_f32)):
+            Xh = X.astype(dtype)
+            pinned = torch.empty(X.shape, dtype=torch.float64 if dtype == np.float64 else torch.float32,
+                                 pin_memory=True)
+            pinned.numpy()[...] = Xh
+            outs, diags = [], []
+            for src in (Xh, pinned.numpy()):
+                out = np.empty(X.shape, dtype=dtype)
+                diags.append(run(src, 2, out))
+                outs.append(out)
+            assert np.array_equal(outs[0], outs[1]), dtype
+            for k in ("Nu", "Nu_bar", "Re", "mass", "energy", "dt"):  # t and step run on
+                assert diags[0][k] == diags[1][k], (dtype, k)
+    finally:
+        s.close()
+
+
 def test_checkpoint_roundtrip(tmp_path):
     cfg = O.Config(nx=64, nz=17, Ra=1e6)
     s = solver_for(cfg)
