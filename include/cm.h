@@ -67,8 +67,8 @@ typedef struct cm_grid {
      * distance of the planes they use, volume averages use the trapezoid
      * rule on the planes and the plate Nusselt numbers the derivative of the
      * quadratic through three planes.  Stretched grids: single contexts (2D
-     * and 3D), the boxes of a batch and cm_diag_noalloc (cm_adj_* return
-     * CM_EINVAL for a stretched grid). */
+     * and 3D, the adjoint included), the boxes of a batch and
+     * cm_diag_noalloc. */
     double zstretch;
     const double* znodes;
 } cm_grid;
@@ -353,14 +353,15 @@ int cm_diag_noalloc(const void* state, int precision, const cm_grid* grid, int p
 /* ---- Adjoint: gradients of a time-averaged plate Nusselt number ----
  * J = (1/N_w) sum over steps n = win_begin..nsteps of Nu_bar(X^n), Nu_bar =
  * (Nu_0 + Nu_1)/2 of Eq. mean_Nu (second-order one-sided plate differences
- * of the plane-averaged temperature, as cm_diag.Nu_bar), X^n the state after
+ * of the plane-averaged temperature, as cm_diag.Nu_bar; on a stretched grid
+ * the derivative of the quadratic through three planes), X^n the state after
  * step n of the run started by cm_adj_forward.  Each step's dt is a constant
  * of J (the CFL dt the forward run took; dt is not differentiated).
  * Reverse mode of Sec. 3.1's sweeps, hand-written, with non-smooth points
  * taking fixed one-sided derivatives: phi'(r) = 2 on 0 < 2r < 1 else 0,
  * d|u|/du = 0 at u = 0, the Co(1 - Co) branch at Co = 1/2, and on a tie in
  * max(A_k, A_k+1) the first argument.  2D FP64 contexts only (CM_EINVAL
- * otherwise). */
+ * otherwise), uniform or stretched z-grid. */
 
 /* Run nsteps steps from the current state (advancing it, t and the step
  * count as cm_step does), record each step's dt, keep a device copy of the

@@ -14,6 +14,14 @@ points are written with torch.where so that autograd takes the same one-sided
 derivatives as the library: phi'(r) = 2 only on 0 < 2r < 1, d|u|/du = 0 at 0,
 the Co(1 - Co) branch at Co = 1/2, and the first argument on a tie of
 max(A_k, A_k+1).
+
+On a stretched z-grid (znodes: the nz plane heights, Sec. 3) the z sweep is
+written in conservative form as in the C oracle: the flux differences of
+plane k over its cell width w_k (half cells on the plates), one-sided
+derivatives over the spacing they span, TVD fluxes weighted by spacing over
+width with the Courant number over the interface spacing; the x sweep's
+central z-differences over the distance of the two planes they use; the plate
+Nusselt numbers from the derivative of the quadratic through three planes.
 """
 from __future__ import annotations
 
@@ -27,7 +35,7 @@ class Model:
     planes including both plates (plate temperatures t_bot and t_top)."""
 
     def __init__(self, nx, nz, Pr=1.0, gamma=5.0 / 3.0, eps=0.1, D=0.5, aspect=4.0, gravity=1.0, t_bot=1.0,
-                 t_top=None, stokes=-2.0 / 3.0, tvd_form=TVD_SPLIT):
+                 t_top=None, stokes=-2.0 / 3.0, tvd_form=TVD_SPLIT, znodes=None):
         self.nx, self.nz, self.K = nx, nz, nz - 1
         self.Pr, self.gamma, self.eps, self.D = Pr, gamma, eps, D
         self.a = (gamma - 1.0) / (gamma * eps * D)
@@ -42,6 +50,18 @@ class Model:
         self.e_bot = t_bot / self.b + self.g * 0.0
         self.e_top = t_top / self.b + self.g * 1.0
         self.z = (torch.arange(nz, dtype=torch.float64) / (nz - 1))[:, None]
+        self.stretched = znodes is not None
+        if self.stretched:
+            z = torch.as_tensor(znodes, dtype=torch.float64).reshape(nz)
+            K = nz - 1
+            hp = z[1:] - z[:-1]                              # spacing of interval k (planes k, k+1)
+            w = torch.cat([hp[:1] / 2.0, (hp[:-1] + hp[1:]) / 2.0, hp[-1:] / 2.0])  # cell widths
+            self.z = z[:, None]
+            self.hp = hp[:, None]
+            self.w = w[:, None]
+            self.sc = (hp[:-1] + hp[1:])[:, None]            # central span of planes 1..K-1
+            self.rp = (hp[1:K] / w[1:K])[:, None]            # TVD weights of planes 1..K-1
+            self.rm = (hp[0:K - 1] / w[1:K])[:, None]
 
     # mu = sqrt(Pr/Ra), K = 1/(eps D sqrt(Ra Pr)) (Sec. 2)
     def coefs(self, Ra):
@@ -98,7 +118,11 @@ class Model:
 
     def sweep_z(self, X, Delta, mu, kth):
         K, hz, hx = self.K, self.hz, self.hx
-        lam = Delta / hz
+        st = self.stretched
+        # Delta / w on the interior planes and on the two plate half cells
+        lam = Delta / self.w[1:K] if st else Delta / hz
+        lam_b = Delta / self.w[0, 0] if st else 2.0 * (Delta / hz)
+        lam_t = Delta / self.w[K, 0] if st else 2.0 * (Delta / hz)
         ux, uz, T, p = self.prims(X, self.z)
         A = torch.abs(uz) + torch.sqrt(self.cs2 * T)
 
@@ -106,15 +130,15 @@ class Model:
             return (torch.roll(f, -1, -1) - torch.roll(f, 1, -1)) / (2.0 * hx)
 
         def dzf(f):  # forward along z on planes 0..K-1 (= backward on 1..K)
-            return (f[1:] - f[:-1]) / hz
+            return (f[1:] - f[:-1]) / (self.hp if st else hz)
         # F^n on planes 0..K-1
         F = self._flux(X[:, :K], uz[:K], ux[:K], p[:K], dzf(uz), dzf(ux), dzf(T), dxc(uz)[:K], dxc(ux)[:K], True,
                        mu, kth)
         S = torch.zeros_like(X[:, 1:K])
         S = torch.stack([S[0], S[1], -self.g * X[0, 1:K], S[3]])
         XPi = X[:, 1:K] - lam * (F[:, 1:K] - F[:, 0:K - 1]) + Delta * S
-        r0 = X[0, 0] - 2.0 * lam * F[0, 0]
-        rK = X[0, K] + 2.0 * lam * F[0, K - 1]
+        r0 = X[0, 0] - lam_b * F[0, 0]
+        rK = X[0, K] + lam_t * F[0, K - 1]
         zr = torch.zeros_like(r0)
         P0 = torch.stack([r0, zr, zr, r0 * self.e_bot])[:, None]
         PK = torch.stack([rK, zr, zr, rK * self.e_top])[:, None]
@@ -126,16 +150,19 @@ class Model:
         SP = torch.stack([S[0], S[1], -self.g * XP[0, 1:K], S[3]])
         XC = X[:, 1:K] - lam * (FP[:, 1:K] - FP[:, 0:K - 1]) + Delta * SP
         Y1 = (XPi + XC) / 2.0
-        y0 = (XP[0, 0] + (X[0, 0] - 2.0 * lam * FP[0, 0])) / 2.0
+        y0 = (XP[0, 0] + (X[0, 0] - lam_b * FP[0, 0])) / 2.0
         yK = (XP[0, K] + X[0, K]) / 2.0
         # TVD fluxes at interfaces k + 1/2, k = 1..K-2 (zero at the plate-adjacent ones)
         dm = X[:, 1:K - 1] - X[:, 0:K - 2]
         d0 = X[:, 2:K] - X[:, 1:K - 1]
         dp = X[:, 3:K + 1] - X[:, 2:K]
-        Dk = self._tvd(dm, d0, dp, A[1:K - 1], A[2:K], Delta, hz)
+        Dk = self._tvd(dm, d0, dp, A[1:K - 1], A[2:K], Delta, self.hp[1:K - 1] if st else hz)
         zrow = torch.zeros_like(X[:, :1])
         Dall = torch.cat([zrow, Dk, zrow], dim=1)  # interfaces 0..K-1
-        Yi = Y1 + (Dall[:, 1:K] - Dall[:, 0:K - 1])
+        if st:
+            Yi = Y1 + (self.rp * Dall[:, 1:K] - self.rm * Dall[:, 0:K - 1])
+        else:
+            Yi = Y1 + (Dall[:, 1:K] - Dall[:, 0:K - 1])
         B0 = torch.stack([y0, zr, zr, y0 * self.e_bot])[:, None]
         BK = torch.stack([yK, zr, zr, yK * self.e_top])[:, None]
         return torch.cat([B0, Yi, BK], dim=1)
@@ -148,7 +175,7 @@ class Model:
         Xi = X[:, 1:K]
 
         def dzc(f):  # central along z on rows 1..K-1
-            return (f[2:] - f[:-2]) / (2.0 * hz)
+            return (f[2:] - f[:-2]) / (self.sc if self.stretched else 2.0 * hz)
 
         def dxf(f):
             return (torch.roll(f, -1, -1) - f) / hx
@@ -184,6 +211,17 @@ class Model:
         differences of the x-mean temperature minus 1 - D z."""
         _, _, T, _ = self.prims(X, self.z)
         K, dz = self.K, self.hz
+        if self.stretched:
+            z = self.z[:, 0]
+            f = [T[q].sum() / self.nx - (1.0 - self.D * z[q]) for q in range(3)]
+            g = [T[K - q].sum() / self.nx - (1.0 - self.D * z[K - q]) for q in range(3)]
+
+            def d3(v, h1, h2):  # derivative at the first of three planes h1, h1 + h2 apart
+                return (-(2.0 * h1 + h2) / (h1 * (h1 + h2)) * v[0] + (h1 + h2) / (h1 * h2) * v[1]
+                        - h1 / (h2 * (h1 + h2)) * v[2])
+            nb = -(1.0 / self.eps) * d3(f, z[1] - z[0], z[2] - z[1])
+            nt = (1.0 / self.eps) * d3(g, z[K] - z[K - 1], z[K - 1] - z[K - 2])
+            return (nb + nt) / 2.0
         f = [T[q].sum() / self.nx - (1.0 - self.D * (q / K)) for q in range(3)]
         g = [T[K - q].sum() / self.nx - (1.0 - self.D * ((K - q) / K)) for q in range(3)]
         nb = -(1.0 / self.eps) * (-3.0 * f[0] + 4.0 * f[1] - f[2]) / (2.0 * dz)

@@ -16,6 +16,14 @@
 // phi'(r) = 2 on 0 < 2r < 1 and 0 elsewhere, d|u|/du = 0 at u = 0, the
 // Co(1 - Co) branch for Co <= 1/2, and on a tie of max(A_k, A_k+1) the first
 // argument.  dt of each step is a constant (the recorded one).
+//
+// Stretched z-grid (C.zp set): the spans and factors follow the forward
+// sweeps' conservative form.  Along z, the flux differences of plane k scale
+// with Delta / w_k (the plate half cells with Delta / w_0, Delta / w_K), the
+// one-sided derivatives of a flux at plane j divide by h_j (F^n) or h_{j-1}
+// (F^P), the TVD flux of interface (s, s+1) enters Y_s with weight rp_s and
+// Y_{s+1} with rm_{s+1} and its Courant number divides by h_s; the x sweep's
+// central z-differences at plane k divide by sc_k = h_{k-1} + h_k.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -123,7 +131,11 @@ __device__ __forceinline__ void flux_derivs(const Coef<double>& C, const double*
     const double ha = AL == 2 ? C.hz : C.hx, h2c = AL == 2 ? C.h2x : C.h2z;
     const long long np = FWD ? nb_al<AL>(C, i, k, 1) : n, nm = FWD ? n : nb_al<AL>(C, i, k, -1);
     // no branch of the reverse pass depends on these, so reciprocal spans suffice
-    const double ia = 1.0 / ha, ic = 1.0 / h2c;
+    double ia = 1.0 / ha, ic = 1.0 / h2c;
+    if (C.zp) {
+        if (AL == 2) ia = C.zp[FWD ? k : k - 1].ihp;  // spacing spanned by the one-sided difference
+        else ic = C.zp[k].isc;                        // distance of planes k-1 and k+1
+    }
     d[0] = (Ua[np] - Ua[nm]) * ia;
     d[1] = (Uc[np] - Uc[nm]) * ia;
     d[2] = (Tt[np] - Tt[nm]) * ia;
@@ -179,11 +191,13 @@ __global__ void k_pred(const double* __restrict__ X, const double* __restrict__ 
         const Q4 x = ld4(X, w.fs, n);
         Q4 xp = x;
         if (interior_row(C, k)) {
+            const double lk = (AL == 2 && C.zp) ? Delta / C.zp[k].w : lam;
             const Q4 f0 = ld4(w.F, w.fs, n), f1 = ld4(w.F, w.fs, nb_al<AL>(C, i, k, -1));
-            for (int c = 0; c < 4; ++c) xp.v[c] = x.v[c] - lam * (f0.v[c] - f1.v[c]);
+            for (int c = 0; c < 4; ++c) xp.v[c] = x.v[c] - lk * (f0.v[c] - f1.v[c]);
             if (AL == 2) xp.v[2] = xp.v[2] + Delta * (-C.g * x.v[0]);
         } else if (AL == 2) {
-            xp.v[0] = (k == 0) ? x.v[0] - (2.0 * lam) * w.F[n] : x.v[0] + (2.0 * lam) * w.F[nb_al<AL>(C, i, k, -1)];
+            const double lpl = C.zp ? Delta / C.zp[k].w : 2.0 * lam;  // plate half cell
+            xp.v[0] = (k == 0) ? x.v[0] - lpl * w.F[n] : x.v[0] + lpl * w.F[nb_al<AL>(C, i, k, -1)];
             xp.v[1] = xp.v[2] = 0.0;
             xp.v[3] = xp.v[0] * (k == 0 ? C.ebot : C.etop);
         }
@@ -298,8 +312,14 @@ __global__ void __launch_bounds__(kAdjThreads) r_tvd_iface(const double* __restr
             const long long s1 = nb_al<AL>(C, i, k, 1);
             const Q4 y0 = ld4(Ybar, w.fs, n), y1 = ld4(Ybar, w.fs, s1);
             Q4 Db;
-            for (int c = 0; c < 4; ++c) Db.v[c] = y0.v[c] - y1.v[c];
-            t = tvd_iface_adj(xs, w.A[n], w.A[s1], Db, Delta, h, C.tvd_form);
+            if (AL == 2 && C.zp) {
+                const double wp = C.zp[k].rp, wm = C.zp[k + 1].rm;
+                for (int c = 0; c < 4; ++c) Db.v[c] = wp * y0.v[c] - wm * y1.v[c];
+                t = tvd_iface_adj(xs, w.A[n], w.A[s1], Db, Delta, C.zp[k].hp, C.tvd_form);
+            } else {
+                for (int c = 0; c < 4; ++c) Db.v[c] = y0.v[c] - y1.v[c];
+                t = tvd_iface_adj(xs, w.A[n], w.A[s1], Db, Delta, h, C.tvd_form);
+            }
         }
         // cx[0] = -dm_b, cx[3] = dp_b, cx[1] = dm_b - d0_b  ->  d0_b = -cx[0] - cx[1]
         Q4 tm, t0, tp;
@@ -393,16 +413,23 @@ __global__ void r_corr(const double* __restrict__ Ybar, double* __restrict__ Xba
         st4(Xbar, w.fs, n, xb);
         st4(w.XPB, w.fs, n, xpb);
         if (has_flux<AL, false>(C, k)) {
+            const int km = AL == 2 ? k - 1 : k;
+            // Delta / w of planes k and k-1, half of the bottom plate's (stretched L_z)
+            double lk = lam, lkm = lam, lhb = lam;
+            if (AL == 2 && C.zp) {
+                lk = Delta / C.zp[k].w;
+                lkm = Delta / C.zp[km].w;
+                lhb = 0.5 * (Delta / C.zp[0].w);
+            }
             Q4 fpb = {{0.0, 0.0, 0.0, 0.0}};
             if (interior_row(C, k))
-                for (int c = 0; c < 4; ++c) fpb.v[c] += lam * (0.5 * y1.v[c]);
-            const int km = AL == 2 ? k - 1 : k;
+                for (int c = 0; c < 4; ++c) fpb.v[c] += lk * (0.5 * y1.v[c]);
             const long long nm = nb_al<AL>(C, i, k, -1);
             if (interior_row(C, km)) {
                 const Q4 y1m = y1bar_of<AL>(C, Ybar, w.fs, km, nm);
-                for (int c = 0; c < 4; ++c) fpb.v[c] -= lam * (0.5 * y1m.v[c]);
+                for (int c = 0; c < 4; ++c) fpb.v[c] -= lkm * (0.5 * y1m.v[c]);
             }
-            if (AL == 2 && k == 1) fpb.v[0] += -lam * y1bar_of<AL>(C, Ybar, w.fs, 0, nm).v[0];
+            if (AL == 2 && k == 1) fpb.v[0] += -lhb * y1bar_of<AL>(C, Ybar, w.fs, 0, nm).v[0];
             st4(w.FPB, w.fs, n, fpb);
         }
     }
@@ -515,29 +542,37 @@ __global__ void __launch_bounds__(kAdjThreads) r_gather(const double* __restrict
         double Tb = w.UB[2 * fs + n];
         // along: the flux at j uses (f[j+1] - f[j]) / h (FWD) or (f[j] - f[j-1]) / h (BWD)
         const double sgn = FWD ? -1.0 : 1.0;
+        // 1 / span of the along-sweep difference of the flux at plane j (stretched L_z:
+        // h_j for F^n, h_{j-1} for F^P); of the across difference (stretched L_x: sc_j)
+        auto ia_of = [&](int j) { return (AL == 2 && C.zp) ? C.zp[FWD ? j : j - 1].ihp : ia; };
+        auto ic_of = [&](int j) { return (AL == 0 && C.zp) ? C.zp[j].isc : ic; };
         if (has_flux<AL, FWD>(C, k)) {
-            uab += sgn * w.DA[n] * ia;
-            ucb += sgn * w.DA[fs + n] * ia;
-            Tb += sgn * w.DA[2 * fs + n] * ia;
+            const double a = ia_of(k);
+            uab += sgn * w.DA[n] * a;
+            ucb += sgn * w.DA[fs + n] * a;
+            Tb += sgn * w.DA[2 * fs + n] * a;
         }
         const int kj = AL == 2 ? (FWD ? k - 1 : k + 1) : k;
         if (kj >= 0 && kj <= K && has_flux<AL, FWD>(C, kj)) {
             const long long nj = nb_al<AL>(C, i, k, FWD ? -1 : 1);
-            uab -= sgn * w.DA[nj] * ia;
-            ucb -= sgn * w.DA[fs + nj] * ia;
-            Tb -= sgn * w.DA[2 * fs + nj] * ia;
+            const double a = ia_of(kj);
+            uab -= sgn * w.DA[nj] * a;
+            ucb -= sgn * w.DA[fs + nj] * a;
+            Tb -= sgn * w.DA[2 * fs + nj] * a;
         }
-        // across: the flux at j uses (f[j+c] - f[j-c]) / 2h
+        // across: the flux at j uses (f[j+c] - f[j-c]) / 2h (stretched L_x: / sc_j)
         const int kl = AL == 2 ? k : k - 1, ku = AL == 2 ? k : k + 1;
         if (kl >= 0 && has_flux<AL, FWD>(C, kl)) {
             const long long nj = nb_ac<AL>(C, i, k, -1);
-            uab += w.DC[nj] * ic;
-            ucb += w.DC[fs + nj] * ic;
+            const double a = ic_of(kl);
+            uab += w.DC[nj] * a;
+            ucb += w.DC[fs + nj] * a;
         }
         if (ku <= K && has_flux<AL, FWD>(C, ku)) {
             const long long nj = nb_ac<AL>(C, i, k, 1);
-            uab -= w.DC[nj] * ic;
-            ucb -= w.DC[fs + nj] * ic;
+            const double a = ic_of(ku);
+            uab -= w.DC[nj] * a;
+            ucb -= w.DC[fs + nj] * a;
         }
         const double ux = Ux[n], uz = Uz[n];
         if (with_A) {
@@ -583,17 +618,25 @@ __global__ void r_pred(double* __restrict__ Xbar, Coef<double> C, AdjWork w, dou
         if (AL == 2 && interior_row(C, k)) xb.v[0] += Delta * (-C.g) * xpb.v[2];
         st4(Xbar, fs, n, xb);
         if (has_flux<AL, true>(C, k)) {
+            const int kp = AL == 2 ? k + 1 : k;
+            // Delta / w of planes k and k+1 and of the plate half cells (stretched L_z)
+            double lk = lam, lkp = lam, lbot = 2.0 * lam, ltop = 2.0 * lam;
+            if (AL == 2 && C.zp) {
+                lk = Delta / C.zp[k].w;
+                lkp = Delta / C.zp[kp].w;
+                lbot = Delta / C.zp[0].w;
+                ltop = Delta / C.zp[K].w;
+            }
             Q4 fb = {{0.0, 0.0, 0.0, 0.0}};
             if (interior_row(C, k))
-                for (int c = 0; c < 4; ++c) fb.v[c] -= lam * xpb.v[c];
-            const int kp = AL == 2 ? k + 1 : k;
+                for (int c = 0; c < 4; ++c) fb.v[c] -= lk * xpb.v[c];
             const long long np = nb_al<AL>(C, i, k, 1);
             if (interior_row(C, kp)) {
                 const Q4 xpbp = ld4(w.XPB, fs, np);
-                for (int c = 0; c < 4; ++c) fb.v[c] += lam * xpbp.v[c];
+                for (int c = 0; c < 4; ++c) fb.v[c] += lkp * xpbp.v[c];
             }
-            if (AL == 2 && k == 0) fb.v[0] += -(2.0 * lam) * xpb.v[0];
-            if (AL == 2 && k == K - 1) fb.v[0] += (2.0 * lam) * w.XPB[np];
+            if (AL == 2 && k == 0) fb.v[0] += -lbot * xpb.v[0];
+            if (AL == 2 && k == K - 1) fb.v[0] += ltop * w.XPB[np];
             st4(w.FB, fs, n, fb);
         }
     }

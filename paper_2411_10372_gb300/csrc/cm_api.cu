@@ -1119,19 +1119,40 @@ int cm_load(const char* path)
     return CM_OK;
 }
 
+// Coefficients of the plate derivative of the quadratic through three planes
+// h1 and h1 + h2 away from the plate: f'(plate) = c0 f_0 + c1 f_1 + c2 f_2
+// (second-order one-sided difference; on uniform planes (-3, 4, -1) / (2 dz)).
+static void plate_coefs(double h1, double h2, double c[3])
+{
+    c[0] = -(2.0 * h1 + h2) / (h1 * (h1 + h2));
+    c[1] = (h1 + h2) / (h1 * h2);
+    c[2] = -h1 / (h2 * (h1 + h2));
+}
+
 // planes of the plate Nusselt differences and the weights of dNu_bar/d(sum_x T)
 // (Eq. mean_Nu: Nu_0 = -(1/eps)(-3 f_0 + 4 f_1 - f_2)/(2 dz), Nu_1 = -(1/eps)(3 g_0 -
-// 4 g_1 + g_2)/(2 dz), f_q, g_q the x-mean of T minus 1 - D z at planes q and K-q)
+// 4 g_1 + g_2)/(2 dz), f_q, g_q the x-mean of T minus 1 - D z at planes q and K-q;
+// on a stretched grid the three-plane quadratic's derivative at each plate)
 static void nu_planes(const Ctx* c, int kq[6], double wq[6])
 {
     const int K = c->grid.nz - 1;
-    const double dz = 1.0 / K, s = -(1.0 / c->prm.eps) / (2.0 * dz) / (double)c->grid.nx;
     const int k6[6] = {0, 1, 2, K, K - 1, K - 2};
-    const double c6[6] = {-3.0, 4.0, -1.0, 3.0, -4.0, 1.0};
-    for (int q = 0; q < 6; ++q) {
-        kq[q] = k6[q];
-        wq[q] = 0.5 * s * c6[q];
+    for (int q = 0; q < 6; ++q) kq[q] = k6[q];
+    if (c->zp_d) {
+        const double* z = c->zplanes;
+        const double s = -(1.0 / c->prm.eps) / (double)c->grid.nx;
+        double cb[3], ct[3];
+        plate_coefs(z[1] - z[0], z[2] - z[1], cb);
+        plate_coefs(z[K] - z[K - 1], z[K - 1] - z[K - 2], ct);
+        for (int q = 0; q < 3; ++q) {
+            wq[q] = 0.5 * s * cb[q];
+            wq[3 + q] = -0.5 * s * ct[q];  // the top derivative points into the fluid: -d/dz
+        }
+        return;
     }
+    const double dz = 1.0 / K, s = -(1.0 / c->prm.eps) / (2.0 * dz) / (double)c->grid.nx;
+    const double c6[6] = {-3.0, 4.0, -1.0, 3.0, -4.0, 1.0};
+    for (int q = 0; q < 6; ++q) wq[q] = 0.5 * s * c6[q];
 }
 
 static double nu_bar_of(const Ctx* c, const double* S)
@@ -1139,6 +1160,22 @@ static double nu_bar_of(const Ctx* c, const double* S)
     const int K = c->grid.nz - 1;
     const double nx = (double)c->grid.nx, D = c->prm.D, eps = c->prm.eps, dz = 1.0 / K;
     double f[3], g[3];
+    if (c->zp_d) {
+        // as the diagnostics on a stretched grid: quadratic through three planes
+        const double* z = c->zplanes;
+        for (int q = 0; q < 3; ++q) {
+            f[q] = S[q] / nx - (1.0 - D * z[q]);
+            g[q] = S[3 + q] / nx - (1.0 - D * z[K - q]);
+        }
+        double h1 = z[1] - z[0], h2 = z[2] - z[1];
+        const double db = -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * f[0] + (h1 + h2) / (h1 * h2) * f[1]
+                          - h1 / (h2 * (h1 + h2)) * f[2];
+        h1 = z[K] - z[K - 1];
+        h2 = z[K - 1] - z[K - 2];
+        const double dtp = (2.0 * h1 + h2) / (h1 * (h1 + h2)) * g[0] - (h1 + h2) / (h1 * h2) * g[1]
+                           + h1 / (h2 * (h1 + h2)) * g[2];
+        return (-(1.0 / eps) * db + -(1.0 / eps) * dtp) / 2.0;
+    }
     for (int q = 0; q < 3; ++q) {
         f[q] = S[q] / nx - (1.0 - D * ((double)q / (double)K));
         g[q] = S[3 + q] / nx - (1.0 - D * ((double)(K - q) / (double)K));
@@ -1153,7 +1190,6 @@ int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
     NEED_CTX();
     Ctx* c = g_ctx;
     if (c->prec != CM_FP64 || c->grid.ndim != 2) return fail(CM_EINVAL, "the adjoint needs a 2D FP64 context");
-    if (c->zp_d) return fail(CM_EINVAL, "the adjoint is implemented for uniform z-grids only");
     if (nsteps < 1 || K < 0 || win_begin < 1 || win_begin > nsteps)
         return fail(CM_EINVAL, "need nsteps >= 1, K >= 0, 1 <= win_begin <= nsteps");
     if (!c->adj) c->adj = new AdjCtx();

@@ -9,7 +9,9 @@ magnifies rounding by a few orders over the run).  Gradients do not depend
 on the checkpoint interval (bit for bit: the recomputed segments are
 bit-identical; also when every sweep input is kept instead).  At the full
 1024 x 256 size a directional derivative
-matches central finite differences of the GPU forward.
+matches central finite differences of the GPU forward.  The same holds on
+stretched z-grids (the tanh grid and given planes), where the reverse stages
+use the conservative form's per-plane spans and weights.
 """
 import math
 
@@ -23,9 +25,21 @@ from oracle.torch_ref import Model, isobaric_state
 pytestmark = pytest.mark.gpu
 
 
+def _stretched(cfg):
+    return cfg.zstretch != 0.0 or cfg.znodes is not None
+
+
 def _model(cfg):
     return Model(cfg.nx, cfg.nz, Pr=cfg.Pr, gamma=cfg.gamma, eps=cfg.eps, D=cfg.D, aspect=cfg.aspect,
-                 gravity=cfg.gravity, t_bot=cfg.t_bot, t_top=cfg.t_top, stokes=cfg.stokes, tvd_form=cfg.tvd_form)
+                 gravity=cfg.gravity, t_bot=cfg.t_bot, t_top=cfg.t_top, stokes=cfg.stokes, tvd_form=cfg.tvd_form,
+                 znodes=O.znodes(cfg) if _stretched(cfg) else None)
+
+
+def _given_planes(nz):
+    s = np.linspace(0.0, 1.0, nz)
+    z = s - 0.6 * np.sin(2 * np.pi * s) / (2 * np.pi)
+    z[0], z[-1] = 0.0, 1.0
+    return z
 
 
 def _solver(cfg):
@@ -33,7 +47,8 @@ def _solver(cfg):
     t_top = (1.0 - cfg.eps - cfg.D) if cfg.t_top is None else cfg.t_top
     return cm.Solver(cfg.nx, cfg.nz, cfg.Ra, cfg.Pr, cfg.gamma, aspect=cfg.aspect, precision="fp64", eps=cfg.eps,
                      D=cfg.D, cfl=cfg.cfl, dt_fixed=cfg.dt_fixed, gravity=cfg.gravity, t_bot=cfg.t_bot,
-                     t_top=t_top, pert_amp=cfg.pert_amp, stokes=cfg.stokes, seed=cfg.seed, tvd_form=cfg.tvd_form)
+                     t_top=t_top, pert_amp=cfg.pert_amp, stokes=cfg.stokes, seed=cfg.seed, tvd_form=cfg.tvd_form,
+                     zstretch=cfg.zstretch, znodes=cfg.znodes)
 
 
 def _gpu_gradients(cfg, nsteps, K, win, X0=None):
@@ -80,9 +95,11 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("tvd", [O.TVD_SPLIT, O.TVD_SUM, O.TVD_OFF])
-def test_adjoint_matches_autograd(tvd):
-    cfg = O.Config(nx=32, nz=9, Ra=3e5, seed=21, pert_amp=3e-2, tvd_form=tvd)
+@pytest.mark.parametrize("tvd,zgrid", [(O.TVD_SPLIT, "uniform"), (O.TVD_SUM, "uniform"), (O.TVD_OFF, "uniform"),
+                                       (O.TVD_SPLIT, "tanh"), (O.TVD_SUM, "given"), (O.TVD_OFF, "tanh")])
+def test_adjoint_matches_autograd(tvd, zgrid):
+    kw = {"uniform": {}, "tanh": {"zstretch": 1.5}, "given": {"znodes": _given_planes(9)}}[zgrid]
+    cfg = O.Config(nx=32, nz=9, Ra=3e5, seed=21, pert_amp=3e-2, tvd_form=tvd, **kw)
     nsteps, K, win = 30, 7, 21
     X0 = O.init(cfg)
     J, gX, gT, gRa = _gpu_gradients(cfg, nsteps, K, win)
@@ -95,11 +112,12 @@ def test_adjoint_matches_autograd(tvd):
     assert abs(gRa - gRat) <= 1e-9 * abs(gRat)
 
 
-def test_adjoint_on_a_stirred_state():
+@pytest.mark.parametrize("beta", [0.0, 1.5])
+def test_adjoint_on_a_stirred_state(beta):
     """Every branch of the scheme active: random velocities, odd sizes, x-sweep
-    TVD at both signs of the ratios."""
+    TVD at both signs of the ratios; uniform and tanh z-grids."""
     from test_gpu_parity import stirred_state
-    cfg = O.Config(nx=29, nz=11, Ra=1e5, seed=4)
+    cfg = O.Config(nx=29, nz=11, Ra=1e5, seed=4, zstretch=beta)
     X0 = stirred_state(cfg, seed=8, u_amp=0.2, t_amp=0.03)
     nsteps, K, win = 12, 5, 1
     J, gX, gT, gRa = _gpu_gradients(cfg, nsteps, K, win, X0)
@@ -110,8 +128,9 @@ def test_adjoint_on_a_stirred_state():
     assert abs(gRa - gRat) <= 1e-9 * abs(gRat)
 
 
-def test_gradients_do_not_depend_on_checkpoint_interval():
-    cfg = O.Config(nx=40, nz=13, Ra=1e6, seed=2, pert_amp=2e-2)
+@pytest.mark.parametrize("beta", [0.0, 1.5])
+def test_gradients_do_not_depend_on_checkpoint_interval(beta):
+    cfg = O.Config(nx=40, nz=13, Ra=1e6, seed=2, pert_amp=2e-2, zstretch=beta)
     ref = None
     for K in (1, 6, 25, 0):  # 0: every sweep input kept, nothing recomputed
         J, gX, gT, gRa = _gpu_gradients(cfg, 25, K, 11)
