@@ -19,9 +19,11 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     if (!bz) {
         cudaFuncSetAttribute(sweep_z2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         cudaFuncSetAttribute(sweep_x2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
+        cudaFuncSetAttribute(sweep_x2d_x2_dt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
         // stretched kernels: the ring plus the warps' plane caches
         cudaFuncSetAttribute(sweep_z2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes + 96 * 1024);
         cudaFuncSetAttribute(sweep_x2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes + 96 * 1024);
+        cudaFuncSetAttribute(sweep_x2d_x2s_dt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes + 96 * 1024);
         bz = blocks_per_sm(sweep_z2d_x2, kRingBytes);
         bx = blocks_per_sm(sweep_x2d_x2, kRingBytes);
     }
@@ -35,9 +37,15 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     if (dir == 2)
         return C.zp ? launch_pdl(true, sweep_z2d_x2s, g, b, kRingBytes + 5 * cache, s, io, C, sc)
                     : launch_pdl(true, sweep_z2d_x2, g, b, kRingBytes, s, io, C, sc);
-    if (dir == 0)
-        return C.zp ? launch_pdl(true, sweep_x2d_x2s, g, b, kRingBytes + 2 * cache, s, io, C, sc)
-                    : launch_pdl(true, sweep_x2d_x2, g, b, kRingBytes, s, io, C, sc);
+    if (dir == 0) {
+        // the last sweep of a step also reduces the next dt (separate kernels, so
+        // that the other x sweeps carry none of that code)
+        if (C.zp)
+            return sc.last ? launch_pdl(true, sweep_x2d_x2s_dt, g, b, kRingBytes + 2 * cache, s, io, C, sc)
+                           : launch_pdl(true, sweep_x2d_x2s, g, b, kRingBytes + 2 * cache, s, io, C, sc);
+        return sc.last ? launch_pdl(true, sweep_x2d_x2_dt, g, b, kRingBytes, s, io, C, sc)
+                       : launch_pdl(true, sweep_x2d_x2, g, b, kRingBytes, s, io, C, sc);
+    }
     return cudaErrorInvalidValue;
 }
 

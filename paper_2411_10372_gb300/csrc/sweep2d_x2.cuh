@@ -478,13 +478,15 @@ sweep_z2d_x2(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 // (backward x, central z from X^P rows j-1 and j-3) and
 // X_new_c = K_c - (lambda/2)(F^P_{i+1} - F^P_i).
 // one warp's segment of the x sweep (see z2_body); every thread of the block
-// must call it when sc.last is set (block reduction of the next dt).  ST:
+// must call it when it reduces the next dt: DT = 1 always, 0 never, -1 when
+// sc.last is set (the reduction needs a block barrier).  ST:
 // stretched z-grid: central z-differences over the distance of the two planes
 // they use, CFL z step of a plane its smaller spacing.
-template <bool ST = false>
+template <bool ST = false, int DT = -1>
 __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __restrict__ out, const Coef<float>& C,
                                         const SweepCtl& sc, int strip, int ks, int seg_rows, bool lead)
 {
+    const bool want_dt = DT < 0 ? sc.last != 0 : DT == 1;
     extern __shared__ f2 ring_mem[];
     SweepIO2 io;
     io.in = in;
@@ -621,7 +623,7 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
                 }
                 if (own) {
                     st2(gout, fs, 0, Xn);
-                    if (sc.last) {
+                    if (want_dt) {
                         f2 ux, uz, T, p;
                         prims2(Xn, gz2, C, ux, uz, T, p);
                         const f2 cs = sqrt2(mul2(bc(C.cs2), T));
@@ -673,15 +675,26 @@ __device__ __forceinline__ void x2_body(const float* __restrict__ in, float* __r
         }
         cp_async_drain();  // rows requested past the segment end
     }
-    if (sc.last) block_dt_reduce(rmax > 0.f ? 1.0 / (double)rmax : 1e308, bad, sc.ctl, sc.slot_in ^ 1);
+    if (want_dt) block_dt_reduce(rmax > 0.f ? 1.0 / (double)rmax : 1e308, bad, sc.ctl, sc.slot_in ^ 1);
 }
 
+// the x sweep without (sc.last unset) and with (_dt) the next step's dt reduction
 __global__ void __launch_bounds__(kThreads2, 4)
 sweep_x2d_x2(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 {
     pdl_enter();
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    x2_body(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
+    x2_body<false, 0>(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows,
+                      blockIdx.x == 0);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4)
+sweep_x2d_x2_dt(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
+{
+    pdl_enter();
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    x2_body<false, 1>(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows,
+                      blockIdx.x == 0);
 }
 
 // the same two sweeps on a stretched z-grid (C.zp set)
@@ -698,7 +711,17 @@ sweep_x2d_x2s(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 {
     pdl_enter();
     const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    x2_body<true>(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows, blockIdx.x == 0);
+    x2_body<true, 0>(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows,
+                     blockIdx.x == 0);
+}
+
+__global__ void __launch_bounds__(kThreads2, 4)
+sweep_x2d_x2s_dt(SweepIO2 io, const __grid_constant__ Coef<float> C, SweepCtl sc)
+{
+    pdl_enter();
+    const int gw = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    x2_body<true, 1>(io.in, io.out, C, sc, gw % io.nstrips, (gw / io.nstrips) * io.seg_rows, io.seg_rows,
+                     blockIdx.x == 0);
 }
 
 // ---- batched ensemble: many independent boxes in one launch per sweep -----
@@ -738,7 +761,7 @@ __device__ __forceinline__ void batch_sweep_const(const BatchLaunch& L)
     const BatchWork& w = batch_item(L, sc, in, out, box);
     box = __shfl_sync(0xffffffffu, box, 0);  // warp-uniform index into the constant bank
     if constexpr (Z) z2_body<ST>(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
-    else x2_body<ST>(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+    else x2_body<ST, -1>(in, out, c_box[box], sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
 }
 
 // the same for batches of more than kConstBoxes boxes: the block stages its
@@ -754,7 +777,7 @@ __device__ __forceinline__ void batch_sweep_smem(const BatchLaunch& L, Coef<floa
     if (threadIdx.x == 0) sC = L.boxes[box].C;
     __syncthreads();
     if constexpr (Z) z2_body<ST>(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
-    else x2_body<ST>(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
+    else x2_body<ST, -1>(in, out, sC, sc, w.strip, w.ks, w.seg_rows, w.lead != 0);
 }
 
 __global__ void __launch_bounds__(kThreads2, 4) sweep_z2d_batch(const __grid_constant__ BatchLaunch L)
