@@ -215,16 +215,29 @@ int sample(Ctx* c)
     return CM_OK;
 }
 
+// the staging array of host transfers and the copy stream and events of
+// chunked uploads, each created on first use (a failed call leaves the
+// others in place and the next call retries the missing ones)
 int ensure_dense(Ctx* c)
 {
-    if (c->dense) return CM_OK;
-    size_t n = (size_t)c->nf * c->grid.nz * c->ny * c->grid.nx;
-    if (cudaMalloc(&c->dense, n * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CM_ENOMEM, "cudaMalloc of %zu bytes (host transfer staging) failed", n * sizeof(double));
+    if (!c->dense) {
+        size_t n = (size_t)c->nf * c->grid.nz * c->ny * c->grid.nx;
+        if (cudaMalloc(&c->dense, n * sizeof(double)) != cudaSuccess) {
+            c->dense = nullptr;
+            cudaGetLastError();
+            return fail(CM_ENOMEM, "cudaMalloc of %zu bytes (host transfer staging) failed", n * sizeof(double));
+        }
     }
-    bool ok = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
-    for (cudaEvent_t& e : c->up_ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    bool ok = true;
+    if (!c->copy_stream && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->copy_stream = nullptr;
+        ok = false;
+    }
+    for (cudaEvent_t& e : c->up_ev)
+        if (ok && !e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            e = nullptr;
+            ok = false;
+        }
     if (!ok) {
         cudaGetLastError();
         return fail(CM_ECUDA, "creation of the upload stream and events failed");
