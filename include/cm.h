@@ -179,11 +179,15 @@ int cm_state_layout(int* pitch, int* nfields, int* elem_bytes);
 int cm_get_state(double* host);
 
 /* Replace the current state by host (dense float64, same layout; converted
- * to the context's precision) and recompute dt from it.  Blocking. */
+ * to the context's precision) and recompute dt from it, in one pass.  A
+ * pinned host array (cudaHostAlloc / cudaHostRegister, one mapped range) is
+ * read in place over the host link by that pass; other host memory is copied
+ * in plane chunks, each packed while the next is copied.  Blocking. */
 int cm_set_state(const double* host);
 
 /* End-to-end call with host buffers: upload state_in (host, dense float64,
- * may be NULL to keep the device state), run nsteps steps of Eq. time_step
+ * may be NULL to keep the device state; as cm_set_state, so pinned memory is
+ * the fast path), run nsteps steps of Eq. time_step
  * (as cm_step), then write the
  * final state to state_out (host, may be NULL) and one diagnostics sample of
  * the final state to diag_out (host, may be NULL).  Blocking. */
