@@ -4,9 +4,10 @@
 //
 // Each box is the single-box problem of include/cm.h (Sec. 2 equations,
 // Sec. 3.1 scheme) with its own dt (per-box device control block), seed and
-// Ra.  Work is split into warp items (box, column strip, row segment); the
-// segment length of each box size class is chosen at init by an autotuner
-// that times the batched sweeps themselves.
+// Ra, on uniform planes or on a stretched z-grid (Sec. 3; then every box of
+// the batch carries a plane table).  Work is split into warp items (box,
+// column strip, row segment); the segment length of each box size class is
+// chosen at init by an autotuner that times the batched sweeps themselves.
 #include <cuda_runtime.h>
 
 #include <algorithm>
