@@ -13,9 +13,10 @@
 // doubles, ~2.8 MB): every GPU that loads libcm.so holds it until the
 // process exits.  It contains the control block the reduction reports into,
 // the z coordinate of each plane, the per-plane partial sums, the output
-// record and, for a stretched z-grid, the FP64 per-plane metric table.  Host code cannot use the array's name as a device address, so the
-// address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, on the first call on that device.
+// record and, for a stretched z-grid, the FP64 per-plane metric table.
+// Host code cannot use the array's name as a device address, so the address
+// is looked up once per device with cudaGetSymbolAddress, with that device
+// current, on the first call on that device.
 #include <cuda_runtime.h>
 
 #include <cstdio>
