@@ -326,6 +326,19 @@ int upload_host(Ctx* c, const S* host)
 
 int upload(Ctx* c, const double* host) { return upload_host(c, host); }
 
+// An entry point that failed after queuing work on the caller's host memory
+// (an in-place read of a pinned state, copies into or out of it) waits for
+// that work before it returns, so that no kernel or copy still touches the
+// caller's buffers afterwards.  Returns rc.
+int drain_on_error(Ctx* c, int rc)
+{
+    if (rc != CM_OK) {
+        cudaStreamSynchronize(c->stream);
+        if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    }
+    return rc;
+}
+
 int download(Ctx* c, double* host)
 {
     int rc = ensure_dense(c);
@@ -915,7 +928,7 @@ int cm_set_state(const double* host)
     NEED_CTX();
     if (!host) return fail(CM_EINVAL, "host is NULL");
     int rc = upload(g_ctx, host);
-    if (rc) return rc;
+    if (rc) return drain_on_error(g_ctx, rc);
     CK(cudaStreamSynchronize(g_ctx->stream));
     return CM_OK;
 }
@@ -925,20 +938,22 @@ int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* 
     NEED_CTX();
     if (nsteps < 0) return fail(CM_EINVAL, "nsteps must be >= 0");
     Ctx* c = g_ctx;
-    int rc;
-    if (state_in && (rc = upload(c, state_in))) return rc;
-    if ((rc = queue_steps(c, nsteps))) return rc;
-    if (state_out && (rc = download(c, state_out))) return rc;
-    if (diag_out) {
-        // a sample of the final state, outside the ring
-        if ((rc = sample(c))) return rc;
-        c->ring_count--;
-        const int slot = (c->ring_head + c->ring_count) % c->ring_cap;
-        CK(cudaMemcpyAsync(diag_out, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
-    }
-    CK(cudaStreamSynchronize(c->stream));
-    if (diag_out && diag_out->status != CM_OK) return fail(CM_ENAN, "non-finite value in the final state");
-    return CM_OK;
+    return drain_on_error(c, [&]() -> int {
+        int rc;
+        if (state_in && (rc = upload(c, state_in))) return rc;
+        if ((rc = queue_steps(c, nsteps))) return rc;
+        if (state_out && (rc = download(c, state_out))) return rc;
+        if (diag_out) {
+            // a sample of the final state, outside the ring
+            if ((rc = sample(c))) return rc;
+            c->ring_count--;
+            const int slot = (c->ring_head + c->ring_count) % c->ring_cap;
+            CK(cudaMemcpyAsync(diag_out, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        if (diag_out && diag_out->status != CM_OK) return fail(CM_ENAN, "non-finite value in the final state");
+        return CM_OK;
+    }());
 }
 
 int cm_run_host_f32(const float* state_in, int nsteps, float* state_out, cm_diag* diag_out)
@@ -947,28 +962,30 @@ int cm_run_host_f32(const float* state_in, int nsteps, float* state_out, cm_diag
     Ctx* c = g_ctx;
     if (c->prec != CM_FP32) return fail(CM_EINVAL, "cm_run_host_f32 needs an FP32 context");
     if (nsteps < 0) return fail(CM_EINVAL, "nsteps must be >= 0");
-    int rc;
-    float* dense32 = nullptr;
-    if ((state_in || state_out) && (rc = ensure_dense(c))) return rc;
-    dense32 = (float*)c->dense;  // the FP64 staging area holds twice as many floats
-    const size_t bytes = dense_count(c) * sizeof(float);
-    if (state_in && (rc = upload_host(c, state_in))) return rc;
-    if ((rc = queue_steps(c, nsteps))) return rc;
-    if (state_out) {
-        cudaError_t e = Launch<float>::unpack32((const float*)c->buf[c->cur], dense32, c->cf, c->nf, c->stream);
-        if (e != cudaSuccess) return fail(CM_ECUDA, "unpack launch: %s", cudaGetErrorString(e));
-        c->launches++;
-        CK(cudaMemcpyAsync(state_out, dense32, bytes, cudaMemcpyDeviceToHost, c->stream));
-    }
-    if (diag_out) {
-        if ((rc = sample(c))) return rc;
-        c->ring_count--;
-        const int slot = (c->ring_head + c->ring_count) % c->ring_cap;
-        CK(cudaMemcpyAsync(diag_out, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
-    }
-    CK(cudaStreamSynchronize(c->stream));
-    if (diag_out && diag_out->status != CM_OK) return fail(CM_ENAN, "non-finite value in the final state");
-    return CM_OK;
+    return drain_on_error(c, [&]() -> int {
+        int rc;
+        float* dense32 = nullptr;
+        if ((state_in || state_out) && (rc = ensure_dense(c))) return rc;
+        dense32 = (float*)c->dense;  // the FP64 staging area holds twice as many floats
+        const size_t bytes = dense_count(c) * sizeof(float);
+        if (state_in && (rc = upload_host(c, state_in))) return rc;
+        if ((rc = queue_steps(c, nsteps))) return rc;
+        if (state_out) {
+            cudaError_t e = Launch<float>::unpack32((const float*)c->buf[c->cur], dense32, c->cf, c->nf, c->stream);
+            if (e != cudaSuccess) return fail(CM_ECUDA, "unpack launch: %s", cudaGetErrorString(e));
+            c->launches++;
+            CK(cudaMemcpyAsync(state_out, dense32, bytes, cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (diag_out) {
+            if ((rc = sample(c))) return rc;
+            c->ring_count--;
+            const int slot = (c->ring_head + c->ring_count) % c->ring_cap;
+            CK(cudaMemcpyAsync(diag_out, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        if (diag_out && diag_out->status != CM_OK) return fail(CM_ENAN, "non-finite value in the final state");
+        return CM_OK;
+    }());
 }
 
 int cm_sweep(int dir, double Delta)
@@ -1121,7 +1138,7 @@ int cm_load(const char* path)
         if (!std::isfinite(v)) return fail(CM_EBADCKPT, "%s holds non-finite values", path);
     c->step = H.step;
     int rc = upload(c, host.data());
-    if (rc) return rc;
+    if (rc) return drain_on_error(c, rc);
     DevCtl h;
     CK(cudaMemcpyAsync(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
