@@ -114,3 +114,13 @@ def test_stretched_grid_argument_errors_need_no_gpu():
         with pytest.raises(cm.CMError) as e:  # rejected before the scratch array is touched
             cm.cm_diag_noalloc(1 << 20, cm.CM_FP32, cm.cm_grid(2, 64, 1, 16, 4.0, beta), 64, 1e6, 1.0, 5 / 3, p)
         assert e.value.code == cm.CM_EINVAL and "zstretch" in cm.cm_last_error(), beta
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libcm.so the binding raises instead of
+    computing anything."""
+    from paper_2411_10372_gb300 import _binding as B
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "absent" / "libcm.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        B.lib(build_if_missing=False)
