@@ -52,6 +52,12 @@ extern "C" {
 #define CM_TVD_SUM 1        /* G(r+_k + r-_{k+1}) dX_{k+1/2}: as printed     */
 #define CM_TVD_OFF 2        /* no TVD term (plain MacCormack; tests only)    */
 
+/* derivative of the TVD limiter phi(r) of Sec. 3.1 in the reverse pass */
+#define CM_ADJ_PHI_EXACT 0  /* phi'(r) = 2 on 0 < 2r < 1, else 0: the derivative of the
+                               discrete step wherever it exists (default) */
+#define CM_ADJ_PHI_FROZEN 1 /* phi' = 0: no derivative through the ratios r (the limiter's
+                               values held fixed; C(Co) still differentiated) */
+
 typedef struct cm_grid {
     int ndim;       /* 2 or 3 */
     int nx, ny, nz; /* nodes; x (and y) periodic; nz counts both plates (ny ignored in 2D) */
@@ -91,6 +97,8 @@ typedef struct cm_params {
     void* state_buf;     /* optional caller-owned device memory for the two state
                             buffers (>= cm_state_bytes bytes, 256-byte aligned);
                             NULL = the library allocates.  Must outlive cm_finalize. */
+    int adj_limiter;     /* CM_ADJ_PHI_*: derivative of the TVD limiter in cm_adj_backward */
+    int pad_;
 } cm_params;
 
 /* One diagnostics sample (Sec. 2, Eqs. volume_Nu, mean_Nu, Re), FP64.
@@ -175,7 +183,11 @@ void* cm_state_ptr(int field);
 int cm_state_layout(int* pitch, int* nfields, int* elem_bytes);
 
 /* Wait for the stream and copy the current state vector (Sec. 3.1) into host
- * (dense float64, nfields*nz*ny*nx values, layout in the header comment). */
+ * (dense float64, nfields*nz*ny*nx values, layout in the header comment).
+ * State-sized host arrays, here and in every entry point below, are either
+ * pageable memory or inside one pinned allocation; an array that spans
+ * several pinned allocations (or pinned and pageable pages), which CUDA's
+ * copies reject, is refused with CM_EINVAL before any transfer. */
 int cm_get_state(double* host);
 
 /* Replace the current state by host (dense float64, same layout; converted
@@ -184,6 +196,15 @@ int cm_get_state(double* host);
  * read in place over the host link by that pass; other host memory is copied
  * in plane chunks, each packed while the next is copied.  Blocking. */
 int cm_set_state(const double* host);
+
+/* Replace the current state by the initial condition of cm_init built on a
+ * given temperature field: T (host, dense float64 [nz][ny][nx], read during
+ * the call) at the interior planes, the plate temperatures on the plates, the
+ * conduction pressure p_c(z) of each plane (rho = p_c / (a T)) and u = 0;
+ * then dt is recomputed from it.  cm_init is this with T = T_c(z) + A xi.
+ * Time and step count are kept.  CM_EINVAL if T is NULL or an interior value
+ * is not a positive finite number.  Blocking. */
+int cm_set_temperature(const double* T);
 
 /* End-to-end call with host buffers: upload state_in (host, dense float64,
  * may be NULL to keep the device state; as cm_set_state, so pinned memory is
@@ -332,19 +353,24 @@ long long cm_batch_launch_count(void);
 /* Free the batch context. */
 int cm_batch_finalize(void);
 
-/* Diagnostics of a caller's state with no allocation at all (the paper has
- * no counterpart; this is for callers that must not allocate device memory,
- * e.g. an in-situ analysis hook called from another application's time loop,
- * whose memory pool owns the device memory and where a cudaMalloc could fail
- * or synchronise the device under the host's streams).  Computes the same
- * record as cm_sample (Sec. 2 definitions, FP64 reductions) without a
- * context: the scratch lives in a fixed ~2.8 MB __device__ array inside the
- * library (held on every GPU that loads it until exit), so nz may not exceed
- * 16384 planes (CM_EINVAL beyond).  A stretched grid (zstretch or znodes,
- * as for cm_init) gets its plane table built on the host and copied into
- * that array (the stretched-grid weights of cm_sample).  The first call on
- * a device looks up that array's device address; make that first call
- * before any stream capture.
+/* Diagnostics of a caller's state with no allocation at all.  The paper has
+ * no counterpart: this entry point exists for callers that must not allocate
+ * device memory, e.g. an in-situ analysis hook called from another
+ * application's time loop, whose memory pool owns the device memory and where
+ * a cudaMalloc could fail or synchronise the device under the host's streams.
+ * Computes the same record as cm_sample without a context: the scratch lives
+ * in a fixed ~2.8 MB __device__ array inside the library, so nz may not
+ * exceed 16384 planes (CM_EINVAL beyond).  The array is device memory of
+ * the library's module: it is placed on a device when the module is loaded
+ * there, which under CUDA's default lazy loading is the first call of this
+ * entry point on that device (CUDA_MODULE_LOADING=EAGER: when the library's
+ * first CUDA call creates the context); it stays until the process exits.
+ * A host whose pool claims most of HBM should therefore make one call (or
+ * load the library eagerly) during its setup, before the pool grows.  That
+ * first call on a device also looks up the array's device address; make it
+ * before any stream capture.  A stretched grid (zstretch or znodes, as for
+ * cm_init) gets its plane table built in host memory and copied into that
+ * array (the stretched-grid weights of cm_sample).
  * All calls share the array: calls that overlap on the GPU race.
  * state: device pointer to field 0 of a state in the layout of
  *   cm_state_layout (fields nz*ny*pitch elements apart), precision CM_FP64 or
@@ -365,7 +391,26 @@ int cm_diag_noalloc(const void* state, int precision, const cm_grid* grid, int p
  * taking fixed one-sided derivatives: phi'(r) = 2 on 0 < 2r < 1 else 0,
  * d|u|/du = 0 at u = 0, the Co(1 - Co) branch at Co = 1/2, and on a tie in
  * max(A_k, A_k+1) the first argument.  2D FP64 contexts only (CM_EINVAL
- * otherwise), uniform or stretched z-grid. */
+ * otherwise), uniform or stretched z-grid.
+ * The limiter's ratio r = <dX_-, dX_+>/<dX_+, dX_+> over the conserved
+ * components is not Lipschitz in X (where dX_+ -> 0 and dX_- is not parallel
+ * to it), so the exact derivative (cm_params.adj_limiter = CM_ADJ_PHI_EXACT)
+ * of a long run can grow far beyond the response of J to any finite change;
+ * CM_ADJ_PHI_FROZEN (phi' = 0) drops the derivative through r and stays
+ * bounded.  The reading is taken from the context's cm_params at
+ * cm_adj_backward. */
+
+/* Replay: the next cm_adj_forward runs of exactly n steps take step s's dt
+ * from dts[s] (host, n values > 0, copied) instead of the CFL rule or
+ * dt_fixed, so that a run from a perturbed state or at another Ra (a finite
+ * difference of J) uses the dts of the run it is compared with.  n = 0 (dts
+ * may be NULL) clears it.  CM_EINVAL for n < 0 or a dt that is not a positive
+ * finite number. */
+int cm_adj_set_dts(const double* dts, int n);
+
+/* The dt of each step of the last cm_adj_forward (host out, n values; n must
+ * equal its nsteps).  CM_EINVAL otherwise. */
+int cm_adj_get_dts(double* dts, int n);
 
 /* Run nsteps steps from the current state (advancing it, t and the step
  * count as cm_step does), record each step's dt, keep a device copy of the

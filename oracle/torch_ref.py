@@ -13,7 +13,8 @@ step's dt is an input (the adjoint treats dt as a constant).  Non-smooth
 points are written with torch.where so that autograd takes the same one-sided
 derivatives as the library: phi'(r) = 2 only on 0 < 2r < 1, d|u|/du = 0 at 0,
 the Co(1 - Co) branch at Co = 1/2, and the first argument on a tie of
-max(A_k, A_k+1).
+max(A_k, A_k+1).  With frozen_phi the ratios r enter as constants (phi' = 0),
+the library's second reading of the limiter's derivative.
 
 On a stretched z-grid (znodes: the nz plane heights, Sec. 3) the z sweep is
 written in conservative form as in the C oracle: the flux differences of
@@ -35,7 +36,7 @@ class Model:
     planes including both plates (plate temperatures t_bot and t_top)."""
 
     def __init__(self, nx, nz, Pr=1.0, gamma=5.0 / 3.0, eps=0.1, D=0.5, aspect=4.0, gravity=1.0, t_bot=1.0,
-                 t_top=None, stokes=-2.0 / 3.0, tvd_form=TVD_SPLIT, znodes=None):
+                 t_top=None, stokes=-2.0 / 3.0, tvd_form=TVD_SPLIT, znodes=None, frozen_phi=False):
         self.nx, self.nz, self.K = nx, nz, nz - 1
         self.Pr, self.gamma, self.eps, self.D = Pr, gamma, eps, D
         self.a = (gamma - 1.0) / (gamma * eps * D)
@@ -46,6 +47,9 @@ class Model:
         self.hz = 1.0 / (nz - 1)
         self.stokes = stokes
         self.tvd_form = tvd_form
+        # frozen_phi: autograd takes no derivative through the limiter's ratios
+        # (the reverse-mode reading phi' = 0); the step's values are unchanged
+        self.frozen_phi = frozen_phi
         t_top = (1.0 - eps - D) if t_top is None else t_top
         self.e_bot = t_bot / self.b + self.g * 0.0
         self.e_top = t_top / self.b + self.g * 1.0
@@ -99,6 +103,8 @@ class Model:
         if self.tvd_form == TVD_OFF:
             return torch.zeros_like(d0)
         sp, sm, dd = dot(dm, d0), dot(d0, dp), dot(d0, d0)
+        if self.frozen_phi:
+            sp, sm, dd = sp.detach(), sm.detach(), dd.detach()
         zero = dd == 0.0
         safe = torch.where(zero, torch.ones_like(dd), dd)
         rp, rm = sp / safe, sm / safe

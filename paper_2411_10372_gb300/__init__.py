@@ -12,14 +12,15 @@ import ctypes
 
 import numpy as np
 
-from ._binding import (cm_adj_backward, cm_adj_forward, cm_batch_diagnostics, cm_batch_finalize, cm_batch_get_state, cm_batch_init,
+from ._binding import (cm_adj_backward, cm_adj_forward, cm_adj_get_dts, cm_adj_set_dts, CM_ADJ_PHI_EXACT,
+                       CM_ADJ_PHI_FROZEN, cm_batch_diagnostics, cm_batch_finalize, cm_batch_get_state, cm_batch_init,
                        cm_batch_launch_count, cm_batch_profile_steps, cm_batch_step, cm_batch_tuning,
                        CM_EBADCKPT, CM_ECUDA, CM_EINVAL, CM_ENAN, CM_ENOMEM, CM_ENOTINIT, CM_EUNSTABLE,
                        CM_FP32, CM_FP64, CM_OK, CM_TVD_DAVIS, CM_TVD_OFF, CM_TVD_SUM, CMError, cm_default_params,
                        cm_diag, cm_diag_noalloc, cm_diagnostics, cm_finalize, cm_get_dt, cm_get_state, cm_get_time, cm_grid,
                        cm_init, cm_last_error, cm_launch_count, cm_load, cm_profile_steps, cm_params, cm_run_host,
                        cm_profiles, cm_run_host_f32, cm_sample, cm_tuning,
-                       cm_save, cm_set_state, cm_state_bytes, cm_state_layout, cm_state_ptr, cm_step, cm_sweep,
+                       cm_save, cm_set_state, cm_set_temperature, cm_state_bytes, cm_state_layout, cm_state_ptr, cm_step, cm_sweep,
                        cm_sync, cm_znodes, cm_ext, cm_ext_profiles, cm_extended, lib)
 
 __all__ = [n for n in dir() if n.startswith("cm_") or n.startswith("CM")] + ["Solver", "lib"]

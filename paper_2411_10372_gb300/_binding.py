@@ -18,6 +18,7 @@ CM_OK, CM_EINVAL, CM_ECUDA, CM_ENOTINIT, CM_ENAN = 0, -1, -2, -3, -4
 CM_EUNSTABLE, CM_ENOMEM, CM_EBADCKPT = -7, -8, -9
 CM_FP64, CM_FP32 = 0, 1
 CM_TVD_DAVIS, CM_TVD_SUM, CM_TVD_OFF = 0, 1, 2
+CM_ADJ_PHI_EXACT, CM_ADJ_PHI_FROZEN = 0, 1
 
 
 class cm_grid(ctypes.Structure):
@@ -32,7 +33,7 @@ class cm_params(ctypes.Structure):
                 ("t_top", ctypes.c_double), ("pert_amp", ctypes.c_double), ("stokes", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int), ("tvd_form", ctypes.c_int),
                 ("diag_every", ctypes.c_int), ("diag_capacity", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("state_buf", ctypes.c_void_p)]
+                ("state_buf", ctypes.c_void_p), ("adj_limiter", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class cm_diag(ctypes.Structure):
@@ -73,6 +74,7 @@ _SIGS = {
     "cm_state_layout": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)] * 3),
     "cm_get_state": (ctypes.c_int, [ctypes.c_void_p]),
     "cm_set_state": (ctypes.c_int, [ctypes.c_void_p]),
+    "cm_set_temperature": (ctypes.c_int, [ctypes.c_void_p]),
     "cm_run_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cm_diag)]),
     "cm_sweep": (ctypes.c_int, [ctypes.c_int, ctypes.c_double]),
     "cm_get_dt": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
@@ -92,6 +94,8 @@ _SIGS = {
     "cm_run_host_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(cm_diag)]),
     "cm_adj_forward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "cm_adj_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "cm_adj_set_dts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "cm_adj_get_dts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "cm_diag_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(cm_grid), ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(cm_params),
                                        ctypes.c_double, ctypes.c_double, ctypes.c_longlong, ctypes.c_void_p,
@@ -195,6 +199,11 @@ def cm_get_state(out: np.ndarray) -> np.ndarray:
 
 def cm_set_state(state: np.ndarray):
     _check(lib().cm_set_state(_dp(np.ascontiguousarray(state, dtype=np.float64))))
+
+
+def cm_set_temperature(T: np.ndarray):
+    """The initial condition of cm_init built on the temperature field T (nz x nx, or nz x ny x nx)."""
+    _check(lib().cm_set_temperature(_dp(np.ascontiguousarray(T, dtype=np.float64))))
 
 
 def cm_run_host(state_in: np.ndarray | None, nsteps: int, state_out: np.ndarray | None = None,
@@ -342,6 +351,19 @@ def cm_adj_backward(grad_X0=None, grad_T0=None) -> float:
     g = ctypes.c_double()
     _check(lib().cm_adj_backward(_any_ptr(grad_X0), _any_ptr(grad_T0), ctypes.byref(g)))
     return g.value
+
+
+def cm_adj_set_dts(dts) -> None:
+    """Replay these per-step dts in the next cm_adj_forward of len(dts) steps (None or [] clears)."""
+    a = np.ascontiguousarray([] if dts is None else dts, dtype=np.float64)
+    _check(lib().cm_adj_set_dts(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a.size else None, int(a.size)))
+
+
+def cm_adj_get_dts(nsteps: int) -> np.ndarray:
+    """The dt of each step of the last cm_adj_forward (nsteps of them)."""
+    out = np.empty(int(nsteps), dtype=np.float64)
+    _check(lib().cm_adj_get_dts(out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nsteps)))
+    return out
 
 
 _batch_n = 0

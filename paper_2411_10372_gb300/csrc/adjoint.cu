@@ -17,6 +17,14 @@
 // Co(1 - Co) branch for Co <= 1/2, and on a tie of max(A_k, A_k+1) the first
 // argument.  dt of each step is a constant (the recorded one).
 //
+// The limiter's ratio r = <dX_-, dX_+> / <dX_+, dX_+> of the vector TVD term
+// is not Lipschitz in X: where dX_+ -> 0 with dX_- not parallel to it, the
+// exact derivative of phi(r) dX_+ grows like |dX_-| / |dX_+|.  The tangent map
+// of a long run then grows without bound although the run itself stays
+// bounded.  AdjWork::frozen_phi = 1 drops the derivative through r (phi' = 0
+// everywhere: the limiter's switch values held fixed, C(Co) still
+// differentiated), which keeps the reverse pass bounded.
+//
 // Stretched z-grid (C.zp set): the spans and factors follow the forward
 // sweeps' conservative form.  Along z, the flux differences of plane k scale
 // with Delta / w_k (the plate half cells with Delta / w_0, Delta / w_K), the
@@ -234,7 +242,7 @@ struct TvdAdj {
 };
 
 __device__ TvdAdj tvd_iface_adj(const Q4 (&x)[4], double A0, double A1, const Q4& Db, double Delta, double h,
-                                int form)
+                                int form, int frozen_phi)
 {
     TvdAdj r;
     for (int q = 0; q < 4; ++q)
@@ -266,6 +274,7 @@ __device__ TvdAdj tvd_iface_adj(const Q4 (&x)[4], double A0, double A1, const Q4
         Cb = Gb * 0.5 * (1.0 - phi_r(rs));
         rpb = rmb = -Gb * 0.5 * Cc * dphi_r(rs);
     }
+    if (frozen_phi) rpb = rmb = 0.0;
     const double spb = rpb / dd, smb = rmb / dd, ddb = -(rpb * rp + rmb * rm) / dd;
     for (int c = 0; c < 4; ++c) {
         const double dmb = spb * d0.v[c];
@@ -315,10 +324,10 @@ __global__ void __launch_bounds__(kAdjThreads) r_tvd_iface(const double* __restr
             if (AL == 2 && C.zp) {
                 const double wp = C.zp[k].rp, wm = C.zp[k + 1].rm;
                 for (int c = 0; c < 4; ++c) Db.v[c] = wp * y0.v[c] - wm * y1.v[c];
-                t = tvd_iface_adj(xs, w.A[n], w.A[s1], Db, Delta, C.zp[k].hp, C.tvd_form);
+                t = tvd_iface_adj(xs, w.A[n], w.A[s1], Db, Delta, C.zp[k].hp, C.tvd_form, w.frozen_phi);
             } else {
                 for (int c = 0; c < 4; ++c) Db.v[c] = y0.v[c] - y1.v[c];
-                t = tvd_iface_adj(xs, w.A[n], w.A[s1], Db, Delta, h, C.tvd_form);
+                t = tvd_iface_adj(xs, w.A[n], w.A[s1], Db, Delta, h, C.tvd_form, w.frozen_phi);
             }
         }
         // cx[0] = -dm_b, cx[3] = dp_b, cx[1] = dm_b - d0_b  ->  d0_b = -cx[0] - cx[1]

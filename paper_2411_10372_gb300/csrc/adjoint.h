@@ -23,6 +23,7 @@ struct AdjWork {
     double *AB;                    // adjoint of |u_al| + c
     double *DVm, *DV0, *DVp, *DVA; // per TVD interface: adjoints of its three differences and two wave speeds
     double *part;                  // per-block partial sums of dJ/dmu and dJ/dK, 2 x nblocks x 2
+    int frozen_phi;                // 1: no derivative through the limiter's ratios (phi' = 0)
 };
 
 // allocate / free the work arrays for grid C (nz planes of pitch C.pitch)

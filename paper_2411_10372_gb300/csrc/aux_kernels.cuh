@@ -31,8 +31,12 @@ __global__ void init_state(R* X, Coef<R> C, InitArgs A)
         const unsigned long long dense = ((unsigned long long)k * C.ny + j) * C.nx + i;
         double T = A.Tc[k];
         if (k > 0 && k < C.nz - 1) {
-            const double u = (double)(splitmix64(A.seed, dense) >> 11) * 0x1.0p-53;
-            T = A.Tc[k] + A.amp * (2.0 * u - 1.0);
+            if (A.Tfield) {
+                T = A.Tfield[dense];
+            } else {
+                const double u = (double)(splitmix64(A.seed, dense) >> 11) * 0x1.0p-53;
+                T = A.Tc[k] + A.amp * (2.0 * u - 1.0);
+            }
         }
         const double rho = A.pc[k] / (A.a * T);
         const double E = rho * (T / A.b + A.g * A.zt[k]);

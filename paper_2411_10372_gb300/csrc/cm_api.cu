@@ -5,6 +5,7 @@
 // The dt of a step is produced on the device by the previous step's last
 // sweep (an FP64 atomic min of h/(|u|+c) over the new state into one of two
 // slots) and read by the next step's sweeps, so the host never waits on it.
+#include <cuda.h>  // driver API types only: the one driver call is fetched through the runtime
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +31,7 @@ constexpr int kUpChunks = 4;  // most plane chunks of a copied host upload
 struct AdjCtx {
     int nsteps = 0, K = 0, win = 0;
     std::vector<double> dts;        // dt of each forward step (host)
+    std::vector<double> replay;     // dts the next forward of replay.size() steps takes (cm_adj_set_dts)
     std::vector<double> plane_sums; // sum over x of T on planes 0, 1, 2, K, K-1, K-2 per window step
     char* ckpt = nullptr;           // device: state at steps 0, K, 2K, ... (K = 0: every sweep input)
     double* dts_d = nullptr;
@@ -178,14 +180,9 @@ int recompute_dt(Ctx* c, int slot)
     return CM_OK;
 }
 
-int sample(Ctx* c)
+// queue one diagnostics record of the current state into dst (device)
+int sample_into(Ctx* c, cm_diag* dst)
 {
-    int slot;
-    if (c->ring_count == c->ring_cap) {  // full: drop the oldest
-        c->ring_head = (c->ring_head + 1) % c->ring_cap;
-        c->ring_count--;
-    }
-    slot = (c->ring_head + c->ring_count) % c->ring_cap;
     DiagArgs A;
     A.zt = c->zt_d;
     A.a = c->a;
@@ -208,10 +205,32 @@ int sample(Ctx* c)
     F.nz = c->grid.nz;
     F.slot = (int)(c->step & 1);
     F.zp = c->zp_d;
-    e = launch_diag_final(c->scratch, c->zt_d, F, c->ctl, c->ring + slot, c->stream);
+    e = launch_diag_final(c->scratch, c->zt_d, F, c->ctl, dst, c->stream);
     if (e != cudaSuccess) return fail(CM_ECUDA, "diagnostics launch: %s", cudaGetErrorString(e));
     c->launches += 2;
-    c->ring_count++;
+    return CM_OK;
+}
+
+// queue a sample into the ring (a full ring drops its oldest sample)
+int sample(Ctx* c)
+{
+    if (c->ring_count == c->ring_cap) {
+        c->ring_head = (c->ring_head + 1) % c->ring_cap;
+        c->ring_count--;
+    }
+    const int rc = sample_into(c, c->ring + (c->ring_head + c->ring_count) % c->ring_cap);
+    if (!rc) c->ring_count++;
+    return rc;
+}
+
+// the record of the final state of cm_run_host / cm_run_host_f32: its own
+// device slot after the ring, so queued samples stay untouched
+int sample_final(Ctx* c, cm_diag* host_out)
+{
+    cm_diag* dst = c->ring + c->ring_cap;
+    int rc = sample_into(c, dst);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(host_out, dst, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
     return CM_OK;
 }
 
@@ -248,22 +267,69 @@ int ensure_dense(Ctx* c)
 size_t dense_count(const Ctx* c) { return (size_t)c->nf * c->grid.nz * c->ny * c->grid.nx; }
 
 // Device address of a pinned host array of `count` elements that the GPU can
-// read in place (one mapped range: both ends pinned, their device addresses
-// as far apart as their host addresses), else NULL.
+// read in place: both ends pinned and inside ONE pinned allocation (the same
+// CUDA buffer ID, so every page between them is pinned and mapped), their
+// device addresses as far apart as their host addresses; else NULL, and the
+// caller copies.  Two separately pinned ranges (adjacent or with pageable
+// pages between them) have different buffer IDs and take the copy.
+using PtrAttrFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+
+PtrAttrFn ptr_attr_fn()
+{
+    static PtrAttrFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PtrAttrFn)f;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool one_pinned_buffer(const void* a, const void* b)
+{
+    PtrAttrFn fn = ptr_attr_fn();
+    unsigned long long ia = 0, ib = 0;
+    if (!fn || fn(&ia, CU_POINTER_ATTRIBUTE_BUFFER_ID, (CUdeviceptr)a) != CUDA_SUCCESS ||
+        fn(&ib, CU_POINTER_ATTRIBUTE_BUFFER_ID, (CUdeviceptr)b) != CUDA_SUCCESS)
+        return false;
+    return ia != 0 && ia == ib;
+}
+
+// Kind of a host array of count elements: 1 = inside one pinned allocation
+// (*view = its device-mapped address), 0 = pageable at both ends (copied
+// through the staging array), -1 = pinned at an end but not one allocation
+// (several registrations, or pinned and pageable pages): CUDA's copies
+// reject such a range, so the entry points refuse it up front.
 template <class S>
-const S* mapped_view(const S* host, size_t count)
+int host_kind(const S* host, size_t count, const S** view)
 {
     cudaPointerAttributes a0, a1;
     if (cudaPointerGetAttributes(&a0, host) != cudaSuccess ||
         cudaPointerGetAttributes(&a1, host + (count - 1)) != cudaSuccess) {
         cudaGetLastError();
-        return nullptr;
+        return 0;
     }
-    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
-        return nullptr;
+    const bool p0 = a0.type == cudaMemoryTypeHost, p1 = a1.type == cudaMemoryTypeHost;
+    if (!p0 && !p1) return 0;
+    if (!p0 || !p1 || !a0.devicePointer || !a1.devicePointer) return -1;
     if ((const char*)a1.devicePointer - (const char*)a0.devicePointer != (ptrdiff_t)((count - 1) * sizeof(S)))
-        return nullptr;
-    return (const S*)a0.devicePointer;
+        return -1;
+    if (!one_pinned_buffer(host, host + (count - 1))) return -1;
+    if (view) *view = (const S*)a0.devicePointer;
+    return 1;
+}
+
+int refuse_split_pinned(const char* what)
+{
+    return fail(CM_EINVAL, "%s spans several pinned allocations (or pinned and pageable memory): pass one pinned "
+                "allocation or pageable memory", what);
 }
 
 // packs planes [k0, k1) of the dense array src (device-readable) into the
@@ -295,9 +361,12 @@ int upload_host(Ctx* c, const S* host)
 {
     const int slot = (int)(c->step & 1), nz = c->grid.nz;
     const size_t plane = (size_t)c->ny * c->grid.nx, field = plane * nz;
+    const S* view = nullptr;
+    const int kind = host_kind(host, field * c->nf, &view);
+    if (kind < 0) return refuse_split_pinned("the host state");
     const unsigned long long inf = 0x7FF0000000000000ULL;
     CK(cudaMemcpyAsync(&c->ctl->dt_slot[slot], &inf, sizeof inf, cudaMemcpyHostToDevice, c->stream));
-    if (const S* view = mapped_view(host, field * c->nf)) return pack_planes(c, view, slot, 0, nz);
+    if (kind > 0) return pack_planes(c, view, slot, 0, nz);
     int rc = ensure_dense(c);
     if (rc) return rc;
     S* staging = (S*)c->dense;  // sized for float64, so it holds either type
@@ -341,6 +410,7 @@ int drain_on_error(Ctx* c, int rc)
 
 int download(Ctx* c, double* host)
 {
+    if (host_kind<double>(host, dense_count(c), nullptr) < 0) return refuse_split_pinned("the host output");
     int rc = ensure_dense(c);
     if (rc) return rc;
     cudaError_t e = c->prec == CM_FP64
@@ -441,6 +511,7 @@ int cm_default_params(cm_params* p)
     p->diag_capacity = 1024;
     p->stream = nullptr;
     p->state_buf = nullptr;
+    p->adj_limiter = CM_ADJ_PHI_EXACT;
     return CM_OK;
 }
 
@@ -532,6 +603,8 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     if (!(P.t_bot > 0) || !(P.t_top > 0)) return fail(CM_EINVAL, "plate temperatures must be > 0");
     if (P.precision != CM_FP64 && P.precision != CM_FP32) return fail(CM_EINVAL, "precision must be CM_FP64 or CM_FP32");
     if (P.tvd_form < 0 || P.tvd_form > 2) return fail(CM_EINVAL, "tvd_form must be 0, 1 or 2");
+    if (P.adj_limiter != CM_ADJ_PHI_EXACT && P.adj_limiter != CM_ADJ_PHI_FROZEN)
+        return fail(CM_EINVAL, "adj_limiter must be CM_ADJ_PHI_EXACT or CM_ADJ_PHI_FROZEN");
     if (P.diag_capacity < 1) P.diag_capacity = 1024;
     if (P.state_buf && ((uintptr_t)P.state_buf & 255)) return fail(CM_EINVAL, "state_buf must be 256-byte aligned");
     std::vector<double> planes;
@@ -582,7 +655,7 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
         cudaMalloc(&c->Tc_d, nz * sizeof(double)) != cudaSuccess || cudaMalloc(&c->pc_d, nz * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->ctl, sizeof(DevCtl)) != cudaSuccess ||
         cudaMalloc(&c->scratch, (size_t)nz * kDiagQ * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->ring, (size_t)c->ring_cap * sizeof(cm_diag)) != cudaSuccess) {
+        cudaMalloc(&c->ring, (size_t)(c->ring_cap + 1) * sizeof(cm_diag)) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(CM_ENOMEM, "cudaMalloc of the work arrays failed"));
     }
@@ -933,6 +1006,40 @@ int cm_set_state(const double* host)
     return CM_OK;
 }
 
+int cm_set_temperature(const double* T)
+{
+    NEED_CTX();
+    Ctx* c = g_ctx;
+    if (!T) return fail(CM_EINVAL, "T is NULL");
+    const int nz = c->grid.nz;
+    const size_t plane = (size_t)c->ny * c->grid.nx;
+    for (size_t n = plane; n < (size_t)(nz - 1) * plane; ++n)
+        if (!(T[n] > 0.0) || !std::isfinite(T[n]))
+            return fail(CM_EINVAL, "interior temperature %g at dense index %zu is not a positive finite number", T[n], n);
+    return drain_on_error(c, [&]() -> int {
+        int rc = ensure_dense(c);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(c->dense, T, (size_t)nz * plane * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        InitArgs A;
+        A.Tc = c->Tc_d;
+        A.pc = c->pc_d;
+        A.zt = c->zt_d;
+        A.a = c->a;
+        A.b = c->b;
+        A.g = c->g;
+        A.amp = 0.0;
+        A.seed = 0;
+        A.Tfield = c->dense;
+        cudaError_t e = c->prec == CM_FP64 ? Launch<double>::init((double*)c->buf[c->cur], c->cd, A, c->stream)
+                                            : Launch<float>::init((float*)c->buf[c->cur], c->cf, A, c->stream);
+        if (e != cudaSuccess) return fail(CM_ECUDA, "init launch: %s", cudaGetErrorString(e));
+        c->launches++;
+        if ((rc = recompute_dt(c, (int)(c->step & 1)))) return rc;
+        CK(cudaStreamSynchronize(c->stream));
+        return CM_OK;
+    }());
+}
+
 int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* diag_out)
 {
     NEED_CTX();
@@ -943,13 +1050,7 @@ int cm_run_host(const double* state_in, int nsteps, double* state_out, cm_diag* 
         if (state_in && (rc = upload(c, state_in))) return rc;
         if ((rc = queue_steps(c, nsteps))) return rc;
         if (state_out && (rc = download(c, state_out))) return rc;
-        if (diag_out) {
-            // a sample of the final state, outside the ring
-            if ((rc = sample(c))) return rc;
-            c->ring_count--;
-            const int slot = (c->ring_head + c->ring_count) % c->ring_cap;
-            CK(cudaMemcpyAsync(diag_out, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
-        }
+        if (diag_out && (rc = sample_final(c, diag_out))) return rc;
         CK(cudaStreamSynchronize(c->stream));
         if (diag_out && diag_out->status != CM_OK) return fail(CM_ENAN, "non-finite value in the final state");
         return CM_OK;
@@ -965,6 +1066,8 @@ int cm_run_host_f32(const float* state_in, int nsteps, float* state_out, cm_diag
     return drain_on_error(c, [&]() -> int {
         int rc;
         float* dense32 = nullptr;
+        if (state_out && host_kind<float>(state_out, dense_count(c), nullptr) < 0)
+            return refuse_split_pinned("the host output");
         if ((state_in || state_out) && (rc = ensure_dense(c))) return rc;
         dense32 = (float*)c->dense;  // the FP64 staging area holds twice as many floats
         const size_t bytes = dense_count(c) * sizeof(float);
@@ -976,12 +1079,7 @@ int cm_run_host_f32(const float* state_in, int nsteps, float* state_out, cm_diag
             c->launches++;
             CK(cudaMemcpyAsync(state_out, dense32, bytes, cudaMemcpyDeviceToHost, c->stream));
         }
-        if (diag_out) {
-            if ((rc = sample(c))) return rc;
-            c->ring_count--;
-            const int slot = (c->ring_head + c->ring_count) % c->ring_cap;
-            CK(cudaMemcpyAsync(diag_out, c->ring + slot, sizeof(cm_diag), cudaMemcpyDeviceToHost, c->stream));
-        }
+        if (diag_out && (rc = sample_final(c, diag_out))) return rc;
         CK(cudaStreamSynchronize(c->stream));
         if (diag_out && diag_out->status != CM_OK) return fail(CM_ENAN, "non-finite value in the final state");
         return CM_OK;
@@ -1215,6 +1313,29 @@ static double nu_bar_of(const Ctx* c, const double* S)
     return (nb + nt) / 2.0;
 }
 
+int cm_adj_set_dts(const double* dts, int n)
+{
+    NEED_CTX();
+    Ctx* c = g_ctx;
+    if (n < 0 || (n > 0 && !dts)) return fail(CM_EINVAL, "cm_adj_set_dts: need n >= 0 and dts for n > 0");
+    for (int s = 0; s < n; ++s)
+        if (!(dts[s] > 0.0) || !std::isfinite(dts[s]))
+            return fail(CM_EINVAL, "cm_adj_set_dts: dt of step %d is %g, not a positive finite number", s, dts[s]);
+    if (!c->adj) c->adj = new AdjCtx();
+    c->adj->replay.assign(dts, dts + n);
+    return CM_OK;
+}
+
+int cm_adj_get_dts(double* dts, int n)
+{
+    NEED_CTX();
+    const AdjCtx* A = g_ctx->adj;
+    if (!A || A->nsteps < 1 || n != A->nsteps || !dts)
+        return fail(CM_EINVAL, "cm_adj_get_dts: need the step count of the last cm_adj_forward and a buffer");
+    std::memcpy(dts, A->dts.data(), sizeof(double) * (size_t)n);
+    return CM_OK;
+}
+
 int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
 {
     NEED_CTX();
@@ -1224,6 +1345,9 @@ int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
         return fail(CM_EINVAL, "need nsteps >= 1, K >= 0, 1 <= win_begin <= nsteps");
     if (!c->adj) c->adj = new AdjCtx();
     AdjCtx* A = c->adj;
+    // replayed dts: each step runs with dt_fixed = its dt (restored below)
+    const bool replay = (int)A->replay.size() == nsteps;
+    const double dt_fixed0 = c->cd.dt_fixed;
     cudaFree(A->ckpt);
     cudaFree(A->dts_d);
     cudaFree(A->planes_d);
@@ -1249,8 +1373,12 @@ int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
     for (int s = 0; s < nsteps; ++s) {
         if (!keep_all && s % K == 0)
             CK(cudaMemcpyAsync(stored(s / K), c->buf[c->cur], c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream));
-        cudaError_t e = adj_record_dt(c->ctl, (int)(c->step & 1), c->prm.cfl, c->prm.dt_fixed, A->dts_d + s, c->stream);
-        if (e != cudaSuccess) return fail(CM_ECUDA, "adjoint forward: %s", cudaGetErrorString(e));
+        if (replay) c->cd.dt_fixed = A->replay[s];
+        cudaError_t e = adj_record_dt(c->ctl, (int)(c->step & 1), c->prm.cfl, c->cd.dt_fixed, A->dts_d + s, c->stream);
+        if (e != cudaSuccess) {
+            c->cd.dt_fixed = dt_fixed0;
+            return fail(CM_ECUDA, "adjoint forward: %s", cudaGetErrorString(e));
+        }
         if (keep_all) {  // the step of queue_steps, each sweep into its own stored state
             SweepCtl sc;
             std::memset(&sc, 0, sizeof sc);
@@ -1263,10 +1391,12 @@ int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
                                           (const double*)c->zt_r, c->cd, sc, 0, c->stream);
                 c->launches++;
             }
+            c->cd.dt_fixed = dt_fixed0;
             if (e != cudaSuccess) return fail(CM_ECUDA, "adjoint forward: %s", cudaGetErrorString(e));
             c->step++;
         } else {
             int rc = queue_steps(c, 1);
+            c->cd.dt_fixed = dt_fixed0;
             if (rc) return rc;
         }
         const double* Xn = keep_all ? stored(4 * s + 4) : (const double*)c->buf[c->cur];
@@ -1328,6 +1458,7 @@ int cm_adj_backward(double* grad_X0, double* grad_T0, double* grad_Ra)
         return fail(CM_ENOMEM, "adjoint backward: cudaMalloc of %zu bytes of sweep inputs failed",
                     (size_t)(4 * K + 1) * bb);
     }
+    W.frozen_phi = c->prm.adj_limiter == CM_ADJ_PHI_FROZEN ? 1 : 0;
     char* base = keep_all ? A->ckpt : slots;
     auto slot = [&](int q) { return (double*)(base + (size_t)q * bb); };
     int xc = 0;

@@ -86,6 +86,7 @@ struct InitArgs {
     const double* zt;   // z of each plane
     double a, b, g, amp;
     unsigned long long seed;
+    const double* Tfield = nullptr;  // dense [nz][ny][nx] interior temperatures replacing Tc + amp xi (or NULL)
 };
 
 struct DiagArgs {

@@ -206,6 +206,23 @@ def test_mass_conservation_and_diag_ring():
     s.close()
 
 
+def test_host_run_record_leaves_the_ring_alone():
+    """The final-state record of cm_run_host / cm_run_host_f32 has its own
+    device slot: with the ring full, the queued samples all survive."""
+    import paper_2411_10372_gb300 as cm
+    for precision, run in (("fp64", cm.cm_run_host), ("fp32", cm.cm_run_host_f32)):
+        s = cm.Solver(64, 17, 1e6, precision=precision, diag_every=1, diag_capacity=8)
+        try:
+            s.step(12)  # 12 samples into a ring of 8: the last 8 are kept
+            d = run(None, 0, None, True)
+            assert d["step"] == 12 and d["status"] == 0
+            ds = s.diagnostics()
+            assert [x["step"] for x in ds] == list(range(5, 13))
+            assert ds[-1]["Nu_bar"] == d["Nu_bar"] and ds[-1]["mass"] == d["mass"]
+        finally:
+            s.close()
+
+
 def test_run_host_f32_matches_run_host():
     """The float32 host-buffer entry point moves the FP32 state without
     rounding: same final state and diagnostics as the float64 one."""
@@ -279,6 +296,56 @@ def test_pinned_upload_reads_in_place_and_equals_the_copied_upload():
             assert np.array_equal(outs[0], outs[1]), dtype
             for k in ("Nu", "Nu_bar", "Re", "mass", "energy", "dt"):  # t and step run on
                 assert diags[0][k] == diags[1][k], (dtype, k)
+    finally:
+        s.close()
+
+
+def test_in_place_read_needs_one_pinned_allocation():
+    """The upload reads a host state in place only when the whole array lies
+    in one pinned allocation (one CUDA buffer ID): one pack launch.  Pageable
+    memory takes the chunked copy (4 chunks of this 32 MB state: 4 pack
+    launches) and gives the same state.  An array pinned as two separate
+    (here adjacent) registrations, which CUDA's copies reject, is refused with
+    CM_EINVAL before any transfer, as input and as output, and the context
+    stays usable."""
+    torch = pytest.importorskip("torch")
+    import paper_2411_10372_gb300 as cm
+    cudart = torch.cuda.cudart()
+    s = cm.Solver(2048, 512, 1e8, precision="fp32")
+    try:
+        s.step(2)
+        X = s.state()
+        nbytes = X.nbytes
+        page = 1 << 16  # covers 4 KB and 64 KB pages
+        raw = np.empty(nbytes + 2 * page, dtype=np.uint8)
+        off = (-raw.ctypes.data) % page
+        two = raw[off:off + nbytes].view(np.float64).reshape(X.shape)
+        half = (nbytes // 2) // page * page
+        base = two.ctypes.data
+        assert int(cudart.cudaHostRegister(base, half, 0)) == 0
+        try:
+            assert int(cudart.cudaHostRegister(base + half, nbytes - half, 0)) == 0
+            try:
+                pinned = torch.empty(X.shape, dtype=torch.float64, pin_memory=True)
+                results = {}
+                for name, src in (("pageable", X.copy()), ("pinned", pinned.numpy())):
+                    src[...] = X
+                    n0 = cm.cm_launch_count()
+                    s.set_state(src)
+                    results[name] = (cm.cm_launch_count() - n0, s.state())
+                assert results["pinned"][0] == 1 and results["pageable"][0] == 4
+                assert np.array_equal(results["pinned"][1], results["pageable"][1])
+                two[...] = X
+                dt = s.dt()
+                for call in (lambda: s.set_state(two), lambda: cm.cm_get_state(two)):
+                    with pytest.raises(cm.CMError) as e:
+                        call()
+                    assert e.value.code == cm.CM_EINVAL and "pinned" in str(e.value)
+                assert s.dt() == dt and np.array_equal(s.state(), results["pageable"][1])
+            finally:
+                cudart.cudaHostUnregister(base + half)
+        finally:
+            cudart.cudaHostUnregister(base)
     finally:
         s.close()
 

@@ -58,6 +58,54 @@ def test_noalloc_diagnostics_match_context_entry_point(precision, zgrid):
         s.close()
 
 
+@pytest.mark.parametrize("zgrid", ["uniform", "tanh"])
+def test_noalloc_on_a_3d_state(zgrid):
+    """A 3D state (5 fields, ny rows per plane) gives the record of cm_sample."""
+    import paper_2411_10372_gb300 as cm
+    Ra, Pr, gamma = 1e6, 1.0, 5.0 / 3.0
+    s = cm.Solver(40, 17, Ra, Pr, gamma, ny=24, ndim=3, precision="fp32", pert_amp=1e-2,
+                  zstretch=2.0 if zgrid == "tanh" else 0.0)
+    try:
+        s.step(6)
+        pitch, nf, elem = cm.cm_state_layout()
+        assert nf == 5
+        t, steps = cm.cm_get_time()
+        dt = cm.cm_get_dt()
+        ref = s.sample()
+        for _ in range(2):
+            got = cm.cm_diag_noalloc(cm.cm_state_ptr(0), cm.CM_FP32, s.grid, pitch, Ra, Pr, gamma, s.params, t, dt,
+                                     steps)
+            for k in KEYS:
+                assert _close(got[k], ref[k]), (k, got[k], ref[k])
+    finally:
+        s.close()
+
+
+def test_noalloc_takes_no_device_memory():
+    """After a first call (which loads the module holding the scratch array),
+    further calls leave the device's free memory exactly as it was."""
+    torch = pytest.importorskip("torch")
+    import paper_2411_10372_gb300 as cm
+    Ra, Pr, gamma = 1e6, 1.0, 5.0 / 3.0
+    s = cm.Solver(256, 64, Ra, Pr, gamma, precision="fp64", zstretch=2.0)
+    try:
+        s.step(5)
+        pitch, _, _ = cm.cm_state_layout()
+        t, steps = cm.cm_get_time()
+        dt = cm.cm_get_dt()
+        args = (cm.cm_state_ptr(0), cm.CM_FP64, s.grid, pitch, Ra, Pr, gamma, s.params, t, dt, steps)
+        first = cm.cm_diag_noalloc(*args)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(5):
+            got = cm.cm_diag_noalloc(*args)
+            assert got["Nu_bar"] == first["Nu_bar"]
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    finally:
+        s.close()
+
+
 def test_noalloc_rejects_grid_beyond_scratch():
     import paper_2411_10372_gb300 as cm
     g = cm.cm_grid(2, 64, 1, 16385, 4.0)
