@@ -19,6 +19,7 @@ stream.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import math
 import os
@@ -41,6 +42,16 @@ WORKLOAD = "2d_aspect4_4096x1024_Ra1e10"
 METRIC = "cell-updates/s per MacCormack-TVD step"
 UNIT = "cell-updates/s"
 FLUSH_BYTES = 256 << 20
+# FP64 flops of one 2D sweep per interior node: add, sub, mul, div and sqrt as
+# the formulas of Secs. 2 and 3.1 evaluate them (23 divisions and one square
+# root each), counted on the restatement of the step by tests/test_flop_count.py;
+# FP64_FLOPS drops the 8 subtractions of the two TVD differences per interface
+# that repeat a neighbouring interface's
+FP64_FLOPS_FORMULA = {"z": 185, "x": 179}
+FP64_FLOPS = {"z": 177, "x": 171}
+# FP64 peak of GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.07 GHz
+# (the nominal 1.25 TFLOP/s; derived from unit counts and the maximum clock, not measured)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def peaks():
@@ -325,33 +336,77 @@ def run_gpu(args):
                                  "finite": d3s["status"] == 0, "sweep_ms": [round(x, 5) for x in sw3s]}
 
     # ---- adjoint: 1024 x 256, Ra = 1e8, FP64, 2000 steps, checkpoints every
-    # 100, J = mean Nu_bar over steps 1501..2000; cost of the reverse pass
-    # (recompute + vector-Jacobian products) over that of the plain forward ----
+    # 100, J = mean Nu_bar over steps 1501..2000, from the conduction profile
+    # plus a seeded uniform temperature perturbation of amplitude 1e-3 (the
+    # initial condition of cm_init on a numpy-seeded field, cm_set_temperature).
+    # Cost of the reverse pass (recompute + vector-Jacobian products) over that
+    # of the plain forward; the gradient of the frozen-limiter reading checked
+    # against central differences of J on the same dts; the exact reading's
+    # gradient norm beside it ----
     adjoint = None
     if not args.no_adjoint:
+        import numpy as np
         na, ka, wa = args.adjoint_steps, max(1, args.adjoint_steps // 20), args.adjoint_steps * 3 // 4 + 1
-        sa = cm.Solver(1024, 256, 1e8, PR, GAMMA, precision="fp64", stream=stream, seed=99 + rank)
-        sa.step(2)
+        NXa, NZa, RAa = 1024, 256, 1e8
+        rng = np.random.default_rng(99 + rank)
+        za = np.linspace(0.0, 1.0, NZa)[:, None]
+        T0 = np.repeat(1.0 - 0.6 * za, NXa, axis=1)  # T_c(z) between the plate temperatures 1 and 1 - eps - D
+        T0[1:-1] += 1e-3 * rng.uniform(-1.0, 1.0, (NZa - 2, NXa))
+        v = np.zeros((NZa, NXa))
+        v[1:-1] = rng.uniform(-1.0, 1.0, (NZa - 2, NXa))
+
+        def adj_solver(limiter=cm.CM_ADJ_PHI_FROZEN):
+            s_ = cm.Solver(NXa, NZa, RAa, PR, GAMMA, precision="fp64", stream=stream, adj_limiter=limiter)
+            cm.cm_set_temperature(T0)
+            return s_
+
+        sa = adj_solver()
+        sa.step(1)  # warm-up of the kernels
+        cm.cm_set_temperature(T0)
         sa.sync()
         t0 = time.perf_counter()
         sa.step(na)
         sa.sync()
         t_fwd = time.perf_counter() - t0
         sa.close()
-        sa = cm.Solver(1024, 256, 1e8, PR, GAMMA, precision="fp64", stream=stream, seed=99 + rank)
-        sa.step(2)
-        sa.sync()
+        sa = adj_solver()
         l0 = cm.cm_launch_count()
         t0 = time.perf_counter()
         Ja = cm.cm_adj_forward(na, ka, wa)
         t_afwd = time.perf_counter() - t0
+        gT = np.empty((NZa, NXa))
         t0 = time.perf_counter()
-        gRa = cm.cm_adj_backward(None, None)
+        gRa = cm.cm_adj_backward(None, gT)
         t_bwd = time.perf_counter() - t0
         nla = cm.cm_launch_count() - l0
+        dts = cm.cm_adj_get_dts(na)
+        sa.close()
+        ad = float(np.sum(gT * v))
+        # central differences of J along v on the replayed dts (untimed)
+        h = 1e-4
+        Js = []
+        for sg in (1.0, -1.0):
+            sa = cm.Solver(NXa, NZa, RAa, PR, GAMMA, precision="fp64", stream=stream)
+            cm.cm_set_temperature(T0 + sg * h * v)
+            cm.cm_adj_set_dts(dts)
+            Js.append(cm.cm_adj_forward(na, na, wa))
+            sa.close()
+        fd = (Js[0] - Js[1]) / (2 * h)
+        sa = adj_solver(cm.CM_ADJ_PHI_EXACT)
+        cm.cm_adj_forward(na, ka, wa)
+        gTe = np.empty((NZa, NXa))
+        gRa_e = cm.cm_adj_backward(None, gTe)
         sa.close()
         adjoint = {"workload": "2d_aspect4_1024x256_Ra1e8_fp64_adjoint", "steps": na, "K": ka, "window": [wa, na],
-                   "J": Ja, "dJ_dRa": gRa, "forward_s": t_fwd, "adj_forward_s": t_afwd, "backward_s": t_bwd,
+                   "J": Ja, "reading": "frozen limiter (phi' = 0)", "dJ_dRa": gRa,
+                   "grad_T0_norm": float(np.linalg.norm(gT)),
+                   "fd_check": {"direction": "uniform random interior temperature field (seed 99)", "step": h,
+                                "adjoint": ad, "central_difference": fd, "rel_diff": abs(fd - ad) / abs(ad),
+                                "window_checked": [wa, na]},
+                   "exact_reading": {"grad_T0_norm": float(np.linalg.norm(gTe)), "dJ_dRa": gRa_e,
+                                     "note": "phi' = 2 on 0 < 2r < 1: agrees with finite differences to 200 steps, "
+                                             "grows without bound beyond (non-Lipschitz vector limiter)"},
+                   "forward_s": t_fwd, "adj_forward_s": t_afwd, "backward_s": t_bwd,
                    "ratio_backward_over_forward": t_bwd / t_fwd, "gpu_launches": nla,
                    "timing": "host wall clock around blocking calls"}
 
@@ -405,6 +460,20 @@ def run_gpu(args):
                 "traffic": measured_traffic(dom, r["segments"]) if w == 4 and suffix == "_x2" else None,
                 "bytes_per_launch": bytes_per_launch, "ms_per_launch": round(per_launch_ms, 5)}
 
+    def roofline_fp64_alu(r):
+        """FP64 leg against the FP64 ALU peak: the method's flops (FP64_FLOPS per
+        interior node of each sweep) over the dominant sweep kind's launch time."""
+        interior = NXr * (NZr - 2)
+        kinds = {"z": (r["sweep_ms"][0] + r["sweep_ms"][2]) / 2.0, "x": (r["sweep_ms"][1] + r["sweep_ms"][3]) / 2.0}
+        dom = max(kinds, key=kinds.get)
+        tflops = {d: FP64_FLOPS[d] * interior / (ms * 1e-3) / 1e12 for d, ms in kinds.items()}
+        step_tflops = sum(2 * FP64_FLOPS[d] for d in kinds) * interior / (sum(r["sweep_ms"]) * 1e-3) / 1e12
+        return {"kernel": "sweep_" + dom + "2d<double>", "bound": "alu", "achieved": round(tflops[dom], 4),
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops[dom] / FP64_PEAK_TFLOPS, 4),
+                "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s), not measured",
+                "flops_per_node": dict(FP64_FLOPS), "per_kind_tflops": {d: round(v, 4) for d, v in tflops.items()},
+                "step_frac": round(step_tflops / FP64_PEAK_TFLOPS, 4), "traffic": None}
+
     K = args.steps
     value = job_rate(cells, K, r32["total_ms"], world)
     value64 = job_rate(cells, k64, r64["total_ms"], world)
@@ -433,7 +502,7 @@ def run_gpu(args):
         "adjoint": adjoint,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": r64["total_ms"] / k64, "steps": k64,
                  "sweep_ms": [round(x, 5) for x in r64["sweep_ms"]], "gpu_launches": r64["launches"],
-                 "roofline_hbm": roofline(r64)},
+                 "roofline": roofline_fp64_alu(r64), "roofline_hbm": roofline(r64)},
         "stretched": stretched,
         "extended": extended,
     }
@@ -447,17 +516,52 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def host_cpu() -> dict:
+    """Model name and online core count of the host CPU."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(steps: int, nx: int = NX):
-    """The FP64 oracle as it stands, one thread, on a bounded sample of the
-    workload: `steps` full steps of the nx x 1024 grid from the seeded state."""
+    """The FP64 oracle as it stands on a bounded sample of the workload:
+    `steps` full steps of the nx x 1024 grid from the seeded state, first on
+    one thread, then the same source built with OpenMP on all host cores
+    (bit-identical states; its per-node sweep loops split over the cores)."""
     import oracle as O
     cfg = O.Config(nx=nx, nz=NZ, Ra=RA, Pr=PR, gamma=GAMMA)
     X = O.init(cfg)
     t0 = time.perf_counter()
     O.step(cfg, X, steps)
     dt = time.perf_counter() - t0
-    return {"value": nx * NZ * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    cpu = host_cpu()
+    line = {"value": nx * NZ * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu,
             "sample": f"{steps} FP64 steps of the {nx}x{NZ} grid, single thread, {dt:.1f} s"}
+    path = O.build_omp()
+    if path is not None:
+        with O.library(path):
+            O.step(cfg, X, 1)  # thread pool start-up
+            t0 = time.perf_counter()
+            O.step(cfg, X, steps)
+            dto = time.perf_counter() - t0
+        line["all_cores"] = {"value": nx * NZ * steps / dto, "unit": UNIT, "cores": cpu["nproc"],
+                             "sample": f"{steps} FP64 steps of the {nx}x{NZ} grid, OpenMP build, {dto:.1f} s"}
+    return line
 
 
 def run_reference(args):
@@ -477,17 +581,25 @@ def run_reference(args):
         nx //= 2
     cfg = O.Config(nx=nx, nz=NZ, Ra=RA, Pr=PR, gamma=GAMMA)
     X = O.init(cfg)
-    X, _, _ = O.step(cfg, X, args.warmup)
-    t0 = time.perf_counter()
-    O.step(cfg, X, args.steps)
-    dt = time.perf_counter() - t0
+    # all host cores: the same oracle source built with OpenMP (bit-identical
+    # states), else the serial build on one core
+    cpu = host_cpu()
+    path = O.build_omp()
+    cores = cpu["nproc"] if path is not None else 1
+    with (O.library(path) if path is not None else contextlib.nullcontext()):
+        X, _, _ = O.step(cfg, X, args.warmup)
+        t0 = time.perf_counter()
+        O.step(cfg, X, args.steps)
+        dt = time.perf_counter() - t0
     value = nx * NZ * args.steps / dt
-    sample = f"{args.steps} FP64 steps of a {nx}x{NZ} slice of the workload (same per-node work), single thread"
+    how = f"OpenMP build on {cores} cores" if path is not None else "single thread"
+    sample = f"{args.steps} FP64 steps of a {nx}x{NZ} slice of the workload (same per-node work), {how}"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "nx": nx, "nz": NZ, "Ra": RA, "Pr": PR, "gamma": GAMMA},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu": cpu},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

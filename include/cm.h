@@ -268,6 +268,11 @@ typedef struct cm_ext {
     double F_n, F_p, F_b, F_v; /* averages over the interior planes (weights of the trapezoid rule) of
                           rho (u.grad) u_z, -dp/dz, rho g and d_i tau_iz (Sec. 6, z momentum) */
     double r_max;      /* max over nodes of K_e/I_e = (rho u^2/2)/(rho C_v T) */
+    double lambda_b_slope;   /* bottom layer read by the slope criterion of Sec. 4: the first distance
+                                from the plate where |d<T>_A/dz + D| = |d<T_sa>_A/dz| has fallen to
+                                0.1 D (slopes from the quadratic through three planes, the crossing
+                                interpolated linearly between planes); NaN if it never does */
+    double lambda_top_slope; /* the same from the top plate */
 } cm_ext;
 
 /* Plane means of F_n, F_p, F_b, F_v (0 on the plates), (rho u_z)^2 and

@@ -60,6 +60,24 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build_omp(force: bool = False) -> str | None:
+    """The same source with -fopenmp (liboracle_omp.so): the sweeps' per-node
+    loops run on all host cores, with the same values bit for bit.  None if
+    the compiler has no OpenMP."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        r = subprocess.run(
+            ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+             "-shared", "-o", tmp, _SRC, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
 class _Cfg(ctypes.Structure):
     _fields_ = [
         ("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
@@ -241,7 +259,8 @@ def diag(cfg: Config, X: np.ndarray) -> dict:
 
 
 EXT_PROFILE_KEYS = ("F_n", "F_p", "F_b", "F_v", "rho_uz_sq", "Tsa_sq", "Tsa", "rho_minus_rhoA", "U")
-EXT_KEYS = ("C", "rho_uz_sq", "Tsa_sq", "lambda_b", "lambda_t", "F_n", "F_p", "F_b", "F_v", "r_max")
+EXT_KEYS = ("C", "rho_uz_sq", "Tsa_sq", "lambda_b", "lambda_t", "F_n", "F_p", "F_b", "F_v", "r_max",
+            "lambda_b_slope", "lambda_t_slope")
 
 
 def ext_profiles(cfg: Config, X: np.ndarray) -> dict:

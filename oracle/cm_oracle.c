@@ -14,6 +14,11 @@
  * TVD fluxes) and plain nested loops, in the order the paper states the
  * scheme, so that it can be checked against the paper by eye.
  *
+ * The per-node loops of a sweep carry "omp parallel for" pragmas: every
+ * iteration writes its own nodes only, so a build with -fopenmp (the all-cores
+ * CPU baseline) computes the same values bit for bit; the default build
+ * ignores them.  Reductions (dt, diagnostics) stay serial.
+ *
  * Passages followed (paper sections / equations):
  *   Sec. 2, nondimensional continuity / momentum / energy equations and the
  *     closures for p, E and tau ........................ prims(), flux()
@@ -198,6 +203,7 @@ static size_t nbr(const P* p, int i, int j, int k, int d, int s)
 static void prims(const P* p, const double* X, double* U, double* T, double* Pr)
 {
     size_t N = p->n;
+    #pragma omp parallel for
     for (int k = 0; k < p->nz; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -313,6 +319,7 @@ static void tvd_flux(const P* p, const double* X, const double* A, double Delta,
 static void wave_speed(const P* p, int al, const double* U, const double* T, double* A)
 {
     size_t N = p->n;
+    #pragma omp parallel for
     for (size_t n = 0; n < N; n++) A[n] = fabs(U[al * N + n]) + sqrt(p->gam * p->a * T[n]);
 }
 
@@ -371,6 +378,7 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
     wave_speed(p, 2, w->U, w->T, w->A);
 
     /* predictor fluxes F^n_k, k = 0..nz-2 (forward z-derivatives) */
+    #pragma omp parallel for
     for (int k = 0; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -381,6 +389,7 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
             }
     /* predictor at interior nodes: X^P = X - (Delta/w_k)(F_k - F_{k-1}) + Delta S,
      * S = (0, 0, 0, -g rho, 0) */
+    #pragma omp parallel for
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -404,6 +413,7 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
     prims(p, w->XP, w->UP, w->TP, w->PP);
 
     /* corrector fluxes F^P_k, k = 1..nz-1 (backward z-derivatives) */
+    #pragma omp parallel for
     for (int k = 1; k < nz; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -414,6 +424,7 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
             }
     /* corrector at interior nodes: X^C = X - (Delta/w_k)(F^P_{k+1} - F^P_k) + Delta S^P;
      * then the average (X^P + X^C)/2 */
+    #pragma omp parallel for
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -437,6 +448,7 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
 
     /* TVD fluxes D_{k+1/2} for k = 1..nz-3 (zero at the two plate-adjacent interfaces) */
     memset(w->D, 0, 5 * N * sizeof(double));
+    #pragma omp parallel for
     for (int k = 1; k <= nz - 3; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -447,6 +459,7 @@ static void sweep_z(const P* p, double Delta, const double* X, double* Y, Work* 
                 for (int c = 0; c < 5; c++) w->D[c * N + n] = D[c];
             }
     /* X^{new} = (X^P + X^C)/2 + ((hp_k/w_k) D_{k+1/2} - (hp_{k-1}/w_k) D_{k-1/2}) */
+    #pragma omp parallel for
     for (int k = 1; k < K; k++) {
         double rp = p->hp[k] / p->w[k], rm = p->hp[k - 1] / p->w[k];
         for (int j = 0; j < p->ny; j++)
@@ -475,6 +488,7 @@ static void sweep_h(const P* p, int al, double Delta, const double* X, double* Y
     prims(p, X, w->U, w->T, w->Pr);
     wave_speed(p, al, w->U, w->T, w->A);
 
+    #pragma omp parallel for
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -484,6 +498,7 @@ static void sweep_h(const P* p, int al, double Delta, const double* X, double* Y
                 for (int c = 0; c < 5; c++) w->F[c * N + n] = F[c];
             }
     memcpy(w->XP, X, 5 * N * sizeof(double));
+    #pragma omp parallel for
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -494,6 +509,7 @@ static void sweep_h(const P* p, int al, double Delta, const double* X, double* Y
 
     prims(p, w->XP, w->UP, w->TP, w->PP);
 
+    #pragma omp parallel for
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -503,6 +519,7 @@ static void sweep_h(const P* p, int al, double Delta, const double* X, double* Y
                 for (int c = 0; c < 5; c++) w->FP[c * N + n] = F[c];
             }
     memcpy(Y, X, 5 * N * sizeof(double));
+    #pragma omp parallel for
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -513,6 +530,7 @@ static void sweep_h(const P* p, int al, double Delta, const double* X, double* Y
                 }
             }
     /* TVD flux D at interface n+1/2 stored at n; all interfaces of interior rows */
+    #pragma omp parallel for
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -526,6 +544,7 @@ static void sweep_h(const P* p, int al, double Delta, const double* X, double* Y
                 tvd_flux(p, X, w->A, Delta, p->h[al], nm, n0, n1, n2, D);
                 for (int c = 0; c < 5; c++) w->D[c * N + n0] = D[c];
             }
+    #pragma omp parallel for
     for (int k = 1; k < K; k++)
         for (int j = 0; j < p->ny; j++)
             for (int i = 0; i < p->nx; i++) {
@@ -957,9 +976,54 @@ void orc_ext_profiles(const orc_cfg* c, const double* ext, double* out)
  *   out[5..8] <F_n>, <F_p>, <F_b>, <F_v> over the interior planes (weights
  *          w_k of the interior planes, normalised by their sum)
  *   out[9] max over nodes of r = K_e / I_e = (rho u^2/2) / (rho C_v T) = b u^2 / (2 T)
+ *   out[10] lambda_b_slope, out[11] lambda_t_slope: the boundary layers by the
+ *          slope criterion of slope_lambda (tol 0.1), the second reading
  * hist[q] (q < nbins): nodes with log10 r in [lo + q w, lo + (q+1) w),
  *          w = (hi - lo)/nbins; below lo (or r = 0) in bin 0, at or above hi
  *          in bin nbins - 1. */
+/* slope of <T_sa>_A at plane k from the quadratic through three planes:
+ * one-sided (planes 0, 1, 2 or K, K-1, K-2) on the plates, central inside */
+static double tsa_slope(const P* p, const double* sa, int k)
+{
+    int K = p->nz - 1;
+    const double* z = p->z;
+    if (k == 0) {
+        double h1 = z[1] - z[0], h2 = z[2] - z[1];
+        return -(2.0 * h1 + h2) / (h1 * (h1 + h2)) * sa[0] + (h1 + h2) / (h1 * h2) * sa[1] - h1 / (h2 * (h1 + h2)) * sa[2];
+    }
+    if (k == K) {
+        double h1 = z[K] - z[K - 1], h2 = z[K - 1] - z[K - 2];
+        return (2.0 * h1 + h2) / (h1 * (h1 + h2)) * sa[K] - (h1 + h2) / (h1 * h2) * sa[K - 1] + h1 / (h2 * (h1 + h2)) * sa[K - 2];
+    }
+    double h1 = z[k] - z[k - 1], h2 = z[k + 1] - z[k];
+    return -h2 / (h1 * (h1 + h2)) * sa[k - 1] + (h2 - h1) / (h1 * h2) * sa[k] + h1 / (h2 * (h1 + h2)) * sa[k + 1];
+}
+
+/* Boundary layer by the words of Sec. 4 (the height where the slope of
+ * <T>_A approximates the adiabatic gradient -D), read with a tolerance: the
+ * first distance from the plate at which |d<T>_A/dz + D| = |d<T_sa>_A/dz|
+ * has fallen to tol * D, linearly interpolated between the two planes around
+ * the crossing; NaN if it never does (the conduction state) */
+static double slope_lambda(const P* p, const double* sa, int top, double tol)
+{
+    int K = p->nz - 1;
+    double target = tol * p->D, dprev = 0.0, sprev = 0.0;
+    for (int q = 0; q <= K; q++) {
+        int k = top ? K - q : q;
+        double s = fabs(tsa_slope(p, sa, k));
+        double d = top ? 1.0 - p->z[k] : p->z[k];
+        if (s <= target) {
+            if (q == 0) return 0.0;
+            return dprev + (sprev - target) / (sprev - s) * (d - dprev);
+        }
+        dprev = d;
+        sprev = s;
+    }
+    return NAN;
+}
+
+#define ORC_LAMBDA_SLOPE_TOL 0.1
+
 void orc_extended(const orc_cfg* c, const double* ext, double* out, long long* hist, int nbins, double lo, double hi)
 {
     P p;
@@ -1017,6 +1081,11 @@ void orc_extended(const orc_cfg* c, const double* ext, double* out, long long* h
         double dtp = (2.0 * h1 + h2) / (h1 * (h1 + h2)) * sb[0] - (h1 + h2) / (h1 * h2) * sb[1] + h1 / (h2 * (h1 + h2)) * sb[2];
         out[3] = (tb - sa[0]) / db;
         out[4] = (sb[0] - tb) / dtp;
+        double* sal = malloc((size_t)p.nz * sizeof(double));
+        for (int k = 0; k <= K; k++) sal[k] = TA[k] - (1.0 - p.D * p.z[k]);
+        out[10] = slope_lambda(&p, sal, 0, ORC_LAMBDA_SLOPE_TOL);
+        out[11] = slope_lambda(&p, sal, 1, ORC_LAMBDA_SLOPE_TOL);
+        free(sal);
     }
     for (int q = 0; q < 4; q++) out[5 + q] = f[q] / wsum;
     double rmax = 0.0, bw = (hi - lo) / nbins;

@@ -50,7 +50,7 @@ class cm_diag(ctypes.Structure):
 
 class cm_ext(ctypes.Structure):
     _fields_ = [(f, ctypes.c_double) for f in ("C", "rho_uz_sq", "Tsa_sq", "lambda_b", "lambda_top", "F_n", "F_p",
-                                               "F_b", "F_v", "r_max")]
+                                               "F_b", "F_v", "r_max", "lambda_b_slope", "lambda_top_slope")]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

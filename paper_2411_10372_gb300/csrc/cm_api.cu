@@ -938,6 +938,37 @@ int cm_extended(cm_ext* out, long long* hist_out, int nbins, double log10_lo, do
                            h1 / (h2 * (h1 + h2)) * sb[2];
         r.lambda_b = (tb - sa[0]) / db;
         r.lambda_top = (sb[0] - tb) / dtp;
+        // the slope reading: the first distance from a plate where the slope
+        // of <T_sa>_A (three-plane quadratic) has fallen to 0.1 D, interpolated
+        std::vector<double> s_sa(nz);
+        for (int k = 0; k <= K; ++k) s_sa[k] = TA[k] - (1.0 - D * z[k]);
+        auto slope = [&](int k) {
+            if (k == 0) {
+                const double a = z[1] - z[0], b = z[2] - z[1];
+                return -(2.0 * a + b) / (a * (a + b)) * s_sa[0] + (a + b) / (a * b) * s_sa[1] - a / (b * (a + b)) * s_sa[2];
+            }
+            if (k == K) {
+                const double a = z[K] - z[K - 1], b = z[K - 1] - z[K - 2];
+                return (2.0 * a + b) / (a * (a + b)) * s_sa[K] - (a + b) / (a * b) * s_sa[K - 1] +
+                       a / (b * (a + b)) * s_sa[K - 2];
+            }
+            const double a = z[k] - z[k - 1], b = z[k + 1] - z[k];
+            return -b / (a * (a + b)) * s_sa[k - 1] + (b - a) / (a * b) * s_sa[k] + a / (b * (a + b)) * s_sa[k + 1];
+        };
+        auto crossing = [&](bool top) {
+            const double target = 0.1 * D;
+            double dprev = 0.0, sprev = 0.0;
+            for (int q = 0; q <= K; ++q) {
+                const int k = top ? K - q : q;
+                const double sk = std::fabs(slope(k)), dk = top ? 1.0 - z[k] : z[k];
+                if (sk <= target) return q == 0 ? 0.0 : dprev + (sprev - target) / (sprev - sk) * (dk - dprev);
+                dprev = dk;
+                sprev = sk;
+            }
+            return std::nan("");
+        };
+        r.lambda_b_slope = crossing(false);
+        r.lambda_top_slope = crossing(true);
     }
     r.F_n = f[0] / wsum;
     r.F_p = f[1] / wsum;

@@ -64,6 +64,11 @@ struct Launch {
 cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
                             const SweepCtl& sc, int seg_rows, cudaStream_t s);
 
+// FP32 3D sweeps with two columns per lane (nx even, uniform z-grid);
+// defined in kernels_f32.cu.  seg_rows as for launch_sweep_x2 (march rows)
+cudaError_t launch_sweep3_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
+                             const SweepCtl& sc, int seg_rows, cudaStream_t s);
+
 // one batched sweep over every box of a batch (kernels_f32.cu); nblocks from
 // the work list; const_coefs: the boxes' coefficients were uploaded with
 // set_batch_coefs (batches of at most kConstBoxes boxes); stretched: every

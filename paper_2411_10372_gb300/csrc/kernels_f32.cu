@@ -2,6 +2,7 @@
 // FMA contraction allowed; the dt rule and all reductions stay FP64).
 #include "kernels_impl.cuh"
 #include "sweep2d_x2.cuh"
+#include "sweep3d_x2.cuh"
 
 namespace cm {
 
@@ -47,6 +48,51 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
                        : launch_pdl(true, sweep_x2d_x2, g, b, kRingBytes, s, io, C, sc);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int NW>
+static cudaError_t sweep3_x2_nw(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
+                                const SweepCtl& sc, int seg_rows, cudaStream_t s)
+{
+    Sweep3IO<float> io;
+    io.in = in;
+    io.out = out;
+    io.zt = zt;
+    io.nstrips = (C.nx + kOutW2 - 1) / kOutW2;
+    io.nmarch = (dir == 1) ? C.ny : C.nz;
+    io.nw = (dir == 1) ? C.nz : C.ny;
+    const int groups = (io.nw + NW - 5) / (NW - 4);
+    constexpr size_t ring = ring3_bytes(NW);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(sweep3d_march_x2<2, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+        cudaFuncSetAttribute(sweep3d_march_x2<1, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+        cudaFuncSetAttribute(sweep3d_x_x2<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+        attr = true;
+    }
+    if (dir < 0 || dir > 2) return cudaErrorInvalidValue;
+    io.seg = (seg_rows > 0 && !getenv("CM_SEG_ROWS"))
+                 ? seg_rows
+                 : pick_segment3((long long)io.nstrips * groups, io.nmarch, 1, sm_count());
+    const int nsegs = (io.nmarch + io.seg - 1) / io.seg;
+    const dim3 grid(io.nstrips, groups, nsegs), b(NW * 32);
+    if (dir == 2) return launch_pdl(false, sweep3d_march_x2<2, NW>, grid, b, ring, s, io, C, sc);
+    if (dir == 1) return launch_pdl(false, sweep3d_march_x2<1, NW>, grid, b, ring, s, io, C, sc);
+    return launch_pdl(false, sweep3d_x_x2<NW>, grid, b, ring, s, io, C, sc);
+}
+
+cudaError_t launch_sweep3_x2(int dir, const float* in, float* out, const float* zt, const Coef<float>& C,
+                             const SweepCtl& sc, int seg_rows, cudaStream_t s)
+{
+    static int nw = 0;
+    if (!nw) {
+        const char* e = getenv("CM_3D_NW");
+        nw = e ? atoi(e) : kNW3pDefault;  // CM_3D_NW: block height (measurement)
+        if (nw != 12 && nw != 14 && nw != 16) nw = kNW3pDefault;
+    }
+    if (nw == 12) return sweep3_x2_nw<12>(dir, in, out, zt, C, sc, seg_rows, s);
+    if (nw == 14) return sweep3_x2_nw<14>(dir, in, out, zt, C, sc, seg_rows, s);
+    return sweep3_x2_nw<16>(dir, in, out, zt, C, sc, seg_rows, s);
 }
 
 cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool const_coefs, bool stretched,

@@ -122,11 +122,21 @@ def test_config1_fp64_1000_steps():
     assert abs(t_gpu - t_cpu) <= 1e-12 * t_cpu
     for f in range(4):
         assert rel_l2(got[f], want[f]) <= 1e-12, f
+    # node by node: the FP64 kernels round every operation as the oracle
+    # does, so after 1000 steps every node is equal bit for bit
+    assert np.array_equal(got, want), [float(np.max(np.abs(got[f] - want[f]))) for f in range(4)]
     d_gpu = s.sample()
     d_cpu = O.diag(cfg, want)
     for k_gpu, k_cpu in (("Nu", "Nu"), ("Nu_bar", "Nu_bar"), ("Re", "Re"), ("KE", "KE"), ("mass", "mass")):
         assert abs(d_gpu[k_gpu] - d_cpu[k_cpu]) <= 1e-10 * max(abs(d_cpu[k_cpu]), 1e-6), k_gpu
     s.close()
+
+
+# FP32, 100 steps of the 256 x 64, Ra = 1e6 workload: relative L2 of m_x and
+# m_z against their own norms.  At step 100 the momentum is still only ~2e-5
+# of rho c, and its FP32 rounding (~3e-7 of rho c) is 1.8% / 1.7% of it
+# (measured); stated bar 5e-2
+FP32_MOMENTUM_OWN_BAR = 5e-2
 
 
 def test_fp32_100_steps():
@@ -142,6 +152,12 @@ def test_fp32_100_steps():
     scale = np.linalg.norm(want[0] * math.sqrt(cfg.gamma * cl["a"]))
     for f in (1, 2):
         assert np.linalg.norm(got[f] - want[f]) / scale <= 1e-5, f
+    # and against the momentum field itself (it grows from zero, so its own
+    # relative error is larger): stated per output
+    own = {f: rel_l2(got[f], want[f]) for f in (1, 2)}
+    print("FP32 100 steps: relative L2 of m_x, m_z against themselves", own,
+          "|m|/|rho c|", [float(np.linalg.norm(want[f]) / scale) for f in (1, 2)])
+    assert own[1] <= FP32_MOMENTUM_OWN_BAR and own[2] <= FP32_MOMENTUM_OWN_BAR, own
     s.close()
 
 

@@ -97,6 +97,10 @@ MUTANTS = [
     ("ext_r_missing_half", "double r = p.b * u2 / (2.0 * T[n]);", "double r = p.b * u2 / T[n];"),
     ("ext_rhoA_exponent", "pow(1.0 - p.D * z, 1.0 / (p.gam - 1.0))", "pow(1.0 - p.D * z, p.gam / (p.gam - 1.0))"),
     ("ext_rms_without_root", "out[(size_t)k * 9 + 8] = sqrt(usum / cells);", "out[(size_t)k * 9 + 8] = usum / cells;"),
+    ("ext_slope_bl_tolerance_unscaled", "double target = tol * p->D,", "double target = tol,"),
+    ("ext_slope_bl_no_interpolation", "return dprev + (sprev - target) / (sprev - s) * (d - dprev);", "return d;"),
+    ("ext_slope_bl_of_T_not_Tsa", "sal[k] = TA[k] - (1.0 - p.D * p.z[k]);", "sal[k] = TA[k];"),
+    ("ext_slope_central_weights", "+ (h2 - h1) / (h1 * h2) * sa[k] +", "+ (h1 - h2) / (h1 * h2) * sa[k] +"),
 ]
 
 

@@ -1014,6 +1014,36 @@ def test_ext_boundary_layers_of_built_profile():
     assert abs(e["lambda_b"] - 0.5) < 1e-12 and abs(e["lambda_t"] - 0.5) < 1e-12
 
 
+def test_ext_boundary_layers_by_the_slope_criterion():
+    """Boundary-layer reading by the words of Sec. 4 (slope of <T>_A within
+    tol * D of the adiabatic gradient -D, tol = 0.1): with <T_sa>_A quadratic
+    in each layer, A (1 - z/d)^2 above the bottom plate and -B (1 - (1-z)/e)^2
+    below the top one (constant bulk), |slope| = 2A/d (1 - z/d) falls to
+    tol D at z* = d (1 - tol D d / (2A)), and likewise at the top.  Slopes
+    from three planes are exact for a quadratic and the interpolation of a
+    linear |slope| is exact, so the crossing comes out to round-off on
+    uniform and tanh planes; the conduction state's slope (eps) never falls
+    to tol D, which gives NaN."""
+    tol = 0.1
+    for kw in ({"nz": 65}, {"nz": 97, "zstretch": 0.5}):
+        cfg = O.Config(nx=8, **kw)
+        z = O.znodes(cfg)
+        A, d, B, e = 0.021, 0.3, 0.03, 0.25
+        Tsa = np.where(z < d, A * (1 - z / d) ** 2, 0.0) - np.where(z > 1 - e, B * (1 - (1 - z) / e) ** 2, 0.0)
+        T = (1 - cfg.D * z) + Tsa - 0.05
+        X = state_from_prims(cfg, cols(cfg, 1 + 0 * z), cols(cfg, 0 * z), cols(cfg, 0 * z), cols(cfg, T), cols(cfg, z))
+        ext, _ = O.extended(cfg, X)
+        zb = d * (1 - tol * cfg.D * d / (2 * A))
+        zt = e * (1 - tol * cfg.D * e / (2 * B))
+        # the planes around each crossing and their stencils lie inside the layer
+        assert np.sum(z < zb) >= 2 and np.min(z[z > zb]) + 2 * np.max(np.diff(z)) < d
+        assert abs(ext["lambda_b_slope"] - zb) < 1e-12, (kw, ext["lambda_b_slope"], zb)
+        assert abs(ext["lambda_t_slope"] - zt) < 1e-12, (kw, ext["lambda_t_slope"], zt)
+    cfg = O.Config(nx=8, nz=17, pert_amp=0.0)
+    ext, _ = O.extended(cfg, O.init(cfg))
+    assert math.isnan(ext["lambda_b_slope"]) and math.isnan(ext["lambda_t_slope"])
+
+
 def test_ext_histogram_counts_are_exact():
     """r = K_e/I_e = b u^2/(2T) placed at bin centres of log10 r: the counts
     are the planted ones (nodes at rest, r = 0, in bin 0), r_max the largest."""
@@ -1031,3 +1061,59 @@ def test_ext_histogram_counts_are_exact():
     want = np.bincount(np.where(qs >= 0, qs, 0).ravel(), minlength=nb)
     assert np.array_equal(hist, want)
     assert abs(e["r_max"] / r.max() - 1) < 1e-12
+
+
+def _smooth_state(cfg, amp=0.02):
+    """The conduction profile with smooth temperature and velocity modes
+    (zero velocity on the plates)."""
+    T_c, p_c, _ = O.profile(cfg)
+    z = np.linspace(0, 1, cfg.nz)
+    x = np.arange(cfg.nx) * cfg.aspect / cfg.nx
+    Z, Xg = np.meshgrid(z, x, indexing="ij")
+    k = 2 * np.pi / cfg.aspect
+    T = T_c[:, None] * (1 + amp * np.sin(np.pi * Z) * np.cos(k * Xg))
+    ux = 3 * amp * np.sin(np.pi * Z) * np.sin(k * Xg)
+    uz = 3 * amp * np.sin(np.pi * Z) ** 2 * np.cos(2 * k * Xg)
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    return state_from_prims(cfg, p_c[:, None] / (cl["a"] * T), ux, uz, T, Z)
+
+
+def test_splitting_order_and_temporal_convergence():
+    """Reading A4 (Sec. 3.1, Eq. time_step).  One step of the oracle is the
+    literal composition L_x L_z L_x L_z (rightmost first) of its single sweeps
+    at dt/2 each, bit for bit.  At fixed grid spacing, halving dt from 0.4 of
+    the CFL step three times (16 .. 256 steps to the same time) from a smooth
+    state, the successive differences shrink at temporal order 1 (measured
+    0.95, 0.97, 0.985), with or without the TVD term.  The symmetric sequence
+    z, x, x, z built from the same sweeps converges alike: at fixed h a
+    MacCormack step carries a time error of order dt h^2 of its own (its
+    second-order time term uses the discrete spatial operator), which here
+    outweighs the splitting error, so the order measured at fixed h does not
+    tell the two splittings apart."""
+    base = O.Config(nx=48, nz=17, Ra=1e4, tvd_form=O.TVD_OFF)
+    X0 = _smooth_state(base)
+    dt0 = 0.4 * O.dt(base, X0)
+
+    def compose(cfg, X, dt, n, order):
+        for _ in range(n):
+            for d in order:
+                X = O.sweep(cfg, X, d, dt / 2)
+        return X
+
+    cfg = O.Config(nx=48, nz=17, Ra=1e4, tvd_form=O.TVD_OFF, dt_fixed=dt0)
+    A, _, _ = O.step(cfg, X0, 3)
+    assert np.array_equal(A, compose(cfg, X0, dt0, 3, (2, 0, 2, 0)))
+    for tvd in (O.TVD_OFF, O.TVD_SPLIT):
+        runs = {"literal": [], "symmetric": []}
+        for r in range(5):
+            c = O.Config(nx=48, nz=17, Ra=1e4, tvd_form=tvd, dt_fixed=dt0 / 2 ** r)
+            runs["literal"].append(O.step(c, X0, 16 * 2 ** r)[0])
+            if tvd == O.TVD_OFF:
+                runs["symmetric"].append(compose(c, X0, dt0 / 2 ** r, 16 * 2 ** r, (2, 0, 0, 2)))
+        for name, sols in runs.items():
+            if not sols:
+                continue
+            e = [np.linalg.norm(sols[i] - sols[i + 1]) for i in range(4)]
+            orders = [math.log2(e[i] / e[i + 1]) for i in range(3)]
+            assert all(0.9 <= p <= 1.1 for p in orders), (tvd, name, orders)
+            assert orders[2] > orders[0]  # approaching 1 from below
