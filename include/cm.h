@@ -98,7 +98,11 @@ typedef struct cm_params {
                             buffers (>= cm_state_bytes bytes, 256-byte aligned);
                             NULL = the library allocates.  Must outlive cm_finalize. */
     int adj_limiter;     /* CM_ADJ_PHI_*: derivative of the TVD limiter in cm_adj_backward */
-    int pad_;
+    int layout_exact;    /* FP32 2D sweeps (single box and batch): 0 (default) = fastest form,
+                            reproducible bit for bit for a given segment length (cm_tuning), but a
+                            node may round differently by an ulp with the segment length that the
+                            timing tuner at init picks; 1 = results bit for bit independent of the
+                            segment lengths (about 6% slower at 4096 x 1024).  No paper passage. */
 } cm_params;
 
 /* One diagnostics sample (Sec. 2, Eqs. volume_Nu, mean_Nu, Re), FP64.

@@ -33,7 +33,7 @@ class cm_params(ctypes.Structure):
                 ("t_top", ctypes.c_double), ("pert_amp", ctypes.c_double), ("stokes", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int), ("tvd_form", ctypes.c_int),
                 ("diag_every", ctypes.c_int), ("diag_capacity", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("state_buf", ctypes.c_void_p), ("adj_limiter", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("state_buf", ctypes.c_void_p), ("adj_limiter", ctypes.c_int), ("layout_exact", ctypes.c_int)]
 
 
 class cm_diag(ctypes.Structure):

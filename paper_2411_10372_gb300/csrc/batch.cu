@@ -124,7 +124,8 @@ int launch(Batch& B, int dir, int first, int last, double Delta)
     L.first = first;
     L.last = last;
     L.Delta = Delta;
-    CKB(launch_sweep_batch(dir, L, dir == 2 ? B.nblk_z : B.nblk_x, B.const_coefs, B.stretched, B.stream));
+    CKB(launch_sweep_batch(dir, L, dir == 2 ? B.nblk_z : B.nblk_x, B.const_coefs, B.stretched, B.prm.layout_exact != 0,
+                           B.stream));
     B.launches++;
     return CM_OK;
 }
@@ -235,6 +236,7 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
     if (params) P = *params;
     else cm_default_params(&P);
     if (P.precision != CM_FP32) return set_error(CM_EINVAL, "cm_batch_init: the batch steps FP32 states");
+    if (P.layout_exact != 0 && P.layout_exact != 1) return set_error(CM_EINVAL, "cm_batch_init: layout_exact must be 0 or 1");
     if (!(Pr > 0) || !(gamma > 1) || !(P.eps > 0) || !(P.D > 0) || !(P.cfl > 0) || P.cfl > 1.0)
         return set_error(CM_EINVAL, "cm_batch_init: bad physical parameters");
     for (int b = 0; b < nbox; ++b) {

@@ -605,6 +605,7 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     if (P.tvd_form < 0 || P.tvd_form > 2) return fail(CM_EINVAL, "tvd_form must be 0, 1 or 2");
     if (P.adj_limiter != CM_ADJ_PHI_EXACT && P.adj_limiter != CM_ADJ_PHI_FROZEN)
         return fail(CM_EINVAL, "adj_limiter must be CM_ADJ_PHI_EXACT or CM_ADJ_PHI_FROZEN");
+    if (P.layout_exact != 0 && P.layout_exact != 1) return fail(CM_EINVAL, "layout_exact must be 0 or 1");
     if (P.diag_capacity < 1) P.diag_capacity = 1024;
     if (P.state_buf && ((uintptr_t)P.state_buf & 255)) return fail(CM_EINVAL, "state_buf must be 256-byte aligned");
     std::vector<double> planes;

@@ -51,6 +51,8 @@ struct Coef {
     long long fstride;                 // elements between two fields
     int tvd_form, ndim;
     const Plane<R>* zp;                // per-plane metric of a stretched z-grid; nullptr = uniform planes
+    int layout_exact;                  // FP32 2D: layout-independent sweeps (cm_params.layout_exact)
+    int pad_;
 };
 
 // Device control block: dt slots (raw min of h/(|u|+c) as IEEE bits, so that

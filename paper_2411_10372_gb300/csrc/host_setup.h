@@ -58,6 +58,7 @@ void fill_coef(Coef<R>& C, const cm_grid& G, int ny, int pitch, long long fstrid
     C.fstride = fstride;
     C.tvd_form = P.tvd_form;
     C.ndim = G.ndim;
+    C.layout_exact = P.layout_exact;
     C.zp = nullptr;
 }
 

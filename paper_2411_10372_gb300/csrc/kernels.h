@@ -72,12 +72,13 @@ cudaError_t launch_sweep3_x2(int dir, const float* in, float* out, const float* 
 // one batched sweep over every box of a batch (kernels_f32.cu); nblocks from
 // the work list; const_coefs: the boxes' coefficients were uploaded with
 // set_batch_coefs (batches of at most kConstBoxes boxes); stretched: every
-// box has a plane table (C.zp) and no work item spans more than kBatchSegMax rows
+// box has a plane table (C.zp) and no work item spans more than kBatchSegMax
+// rows; layout_exact: the layout-independent form of the sweeps
 struct BatchLaunch;
 constexpr int kConstBoxes = 256;
 constexpr int kBatchSegMax = 128;
 cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool const_coefs, bool stretched,
-                               cudaStream_t s);
+                               bool layout_exact, cudaStream_t s);
 // copy the coefficients of n <= kConstBoxes boxes to constant memory (kernels_f32.cu)
 cudaError_t set_batch_coefs(const Coef<float>* C, int n, cudaStream_t s);
 

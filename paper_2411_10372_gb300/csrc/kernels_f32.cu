@@ -16,18 +16,23 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     io.out = out;
     io.zt = zt;
     io.nstrips = (C.nx + kOutW2 - 1) / kOutW2;
+    using K = void (*)(SweepIO2, Coef<float>, SweepCtl);
+    // [layout_exact][kernel]: z, x, x with dt, and the stretched-grid forms
+    static const K kern[2][6] = {
+        {pkf::sweep_z2d_x2, pkf::sweep_x2d_x2, pkf::sweep_x2d_x2_dt, pkf::sweep_z2d_x2s, pkf::sweep_x2d_x2s,
+         pkf::sweep_x2d_x2s_dt},
+        {pkx::sweep_z2d_x2, pkx::sweep_x2d_x2, pkx::sweep_x2d_x2_dt, pkx::sweep_z2d_x2s, pkx::sweep_x2d_x2s,
+         pkx::sweep_x2d_x2s_dt}};
     static int bz = 0, bx = 0;
     if (!bz) {
-        cudaFuncSetAttribute(sweep_z2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        cudaFuncSetAttribute(sweep_x2d_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        cudaFuncSetAttribute(sweep_x2d_x2_dt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        // stretched kernels: the ring plus the warps' plane caches
-        cudaFuncSetAttribute(sweep_z2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes + 96 * 1024);
-        cudaFuncSetAttribute(sweep_x2d_x2s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes + 96 * 1024);
-        cudaFuncSetAttribute(sweep_x2d_x2s_dt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes + 96 * 1024);
-        bz = blocks_per_sm(sweep_z2d_x2, kRingBytes);
-        bx = blocks_per_sm(sweep_x2d_x2, kRingBytes);
+        for (int v = 0; v < 2; ++v)
+            for (int q = 0; q < 6; ++q)  // stretched kernels: the ring plus the warps' plane caches
+                cudaFuncSetAttribute(kern[v][q], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRingBytes + (q >= 3 ? 96 * 1024 : 0));
+        bz = blocks_per_sm(pkf::sweep_z2d_x2, kRingBytes);
+        bx = blocks_per_sm(pkf::sweep_x2d_x2, kRingBytes);
     }
+    const K* k = kern[C.layout_exact ? 1 : 0];
     io.seg_rows = (seg_rows > 0 && !getenv("CM_SEG_ROWS")) ? seg_rows
                                                            : pick_segment(io.nstrips, C.nz, dir == 2 ? bz : bx, sm_count());
     const int nsegs = (C.nz + io.seg_rows - 1) / io.seg_rows;
@@ -36,16 +41,16 @@ cudaError_t launch_sweep_x2(int dir, const float* in, float* out, const float* z
     const dim3 g(blocks), b(kWarpsPerBlock * 32);
     const size_t cache = (size_t)kWarpsPerBlock * plane_cap2(io.seg_rows) * sizeof(float);
     if (dir == 2)
-        return C.zp ? launch_pdl(true, sweep_z2d_x2s, g, b, kRingBytes + 5 * cache, s, io, C, sc)
-                    : launch_pdl(true, sweep_z2d_x2, g, b, kRingBytes, s, io, C, sc);
+        return C.zp ? launch_pdl(true, k[3], g, b, kRingBytes + 5 * cache, s, io, C, sc)
+                    : launch_pdl(true, k[0], g, b, kRingBytes, s, io, C, sc);
     if (dir == 0) {
         // the last sweep of a step also reduces the next dt (separate kernels, so
         // that the other x sweeps carry none of that code)
         if (C.zp)
-            return sc.last ? launch_pdl(true, sweep_x2d_x2s_dt, g, b, kRingBytes + 2 * cache, s, io, C, sc)
-                           : launch_pdl(true, sweep_x2d_x2s, g, b, kRingBytes + 2 * cache, s, io, C, sc);
-        return sc.last ? launch_pdl(true, sweep_x2d_x2_dt, g, b, kRingBytes, s, io, C, sc)
-                       : launch_pdl(true, sweep_x2d_x2, g, b, kRingBytes, s, io, C, sc);
+            return sc.last ? launch_pdl(true, k[5], g, b, kRingBytes + 2 * cache, s, io, C, sc)
+                           : launch_pdl(true, k[4], g, b, kRingBytes + 2 * cache, s, io, C, sc);
+        return sc.last ? launch_pdl(true, k[2], g, b, kRingBytes, s, io, C, sc)
+                       : launch_pdl(true, k[1], g, b, kRingBytes, s, io, C, sc);
     }
     return cudaErrorInvalidValue;
 }
@@ -96,42 +101,32 @@ cudaError_t launch_sweep3_x2(int dir, const float* in, float* out, const float* 
 }
 
 cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool const_coefs, bool stretched,
-                               cudaStream_t s)
+                               bool layout_exact, cudaStream_t s)
 {
     // stretched: per-warp plane caches of 5 (z) or 2 (x) values per plane after the ring
     constexpr size_t kCacheZ = kRingBytes + (size_t)kWarpsPerBlock * plane_cap2(kBatchSegMax) * 5 * sizeof(float);
     constexpr size_t kCacheX = kRingBytes + (size_t)kWarpsPerBlock * plane_cap2(kBatchSegMax) * 2 * sizeof(float);
+    using K = void (*)(BatchLaunch);
+    // [layout_exact][dir z, x][stretched][const coefficients]
+    static const K kern[2][2][2][2] = {
+        {{{pkf::sweep_z2d_batch_smem, pkf::sweep_z2d_batch}, {pkf::sweep_z2d_batch_smem_s, pkf::sweep_z2d_batch_s}},
+         {{pkf::sweep_x2d_batch_smem, pkf::sweep_x2d_batch}, {pkf::sweep_x2d_batch_smem_s, pkf::sweep_x2d_batch_s}}},
+        {{{pkx::sweep_z2d_batch_smem, pkx::sweep_z2d_batch}, {pkx::sweep_z2d_batch_smem_s, pkx::sweep_z2d_batch_s}},
+         {{pkx::sweep_x2d_batch_smem, pkx::sweep_x2d_batch}, {pkx::sweep_x2d_batch_smem_s, pkx::sweep_x2d_batch_s}}}};
     static bool init = false;
     if (!init) {
-        cudaFuncSetAttribute(sweep_z2d_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        cudaFuncSetAttribute(sweep_x2d_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        cudaFuncSetAttribute(sweep_z2d_batch_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        cudaFuncSetAttribute(sweep_x2d_batch_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingBytes);
-        cudaFuncSetAttribute(sweep_z2d_batch_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheZ);
-        cudaFuncSetAttribute(sweep_x2d_batch_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheX);
-        cudaFuncSetAttribute(sweep_z2d_batch_smem_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheZ);
-        cudaFuncSetAttribute(sweep_x2d_batch_smem_s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCacheX);
+        for (int v = 0; v < 2; ++v)
+            for (int d = 0; d < 2; ++d)
+                for (int st = 0; st < 2; ++st)
+                    for (int cc = 0; cc < 2; ++cc)
+                        cudaFuncSetAttribute(kern[v][d][st][cc], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(st ? (d == 0 ? kCacheZ : kCacheX) : kRingBytes));
         init = true;
     }
-    if (dir == 2) {
-        if (stretched) {
-            if (const_coefs) sweep_z2d_batch_s<<<nblocks, kThreads2, kCacheZ, s>>>(L);
-            else sweep_z2d_batch_smem_s<<<nblocks, kThreads2, kCacheZ, s>>>(L);
-        } else {
-            if (const_coefs) sweep_z2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
-            else sweep_z2d_batch_smem<<<nblocks, kThreads2, kRingBytes, s>>>(L);
-        }
-    } else if (dir == 0) {
-        if (stretched) {
-            if (const_coefs) sweep_x2d_batch_s<<<nblocks, kThreads2, kCacheX, s>>>(L);
-            else sweep_x2d_batch_smem_s<<<nblocks, kThreads2, kCacheX, s>>>(L);
-        } else {
-            if (const_coefs) sweep_x2d_batch<<<nblocks, kThreads2, kRingBytes, s>>>(L);
-            else sweep_x2d_batch_smem<<<nblocks, kThreads2, kRingBytes, s>>>(L);
-        }
-    } else {
-        return cudaErrorInvalidValue;
-    }
+    if (dir != 2 && dir != 0) return cudaErrorInvalidValue;
+    const int d = dir == 2 ? 0 : 1;
+    const size_t smem = stretched ? (d == 0 ? kCacheZ : kCacheX) : kRingBytes;
+    kern[layout_exact ? 1 : 0][d][stretched ? 1 : 0][const_coefs ? 1 : 0]<<<nblocks, kThreads2, smem, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -51,15 +51,15 @@ __device__ __forceinline__ P5 p5_left(const P5& q)
 }
 __device__ __forceinline__ P5 p5_sub(const P5& a, const P5& b)
 {
-    return {sub2(a.r, b.r), {sub2(a.m[0], b.m[0]), sub2(a.m[1], b.m[1]), sub2(a.m[2], b.m[2])}, sub2(a.E, b.E)};
+    return {sub2f(a.r, b.r), {sub2f(a.m[0], b.m[0]), sub2f(a.m[1], b.m[1]), sub2f(a.m[2], b.m[2])}, sub2f(a.E, b.E)};
 }
 __device__ __forceinline__ f2 p5_dot(const P5& a, const P5& b)
 {
-    return fma2(a.E, b.E, fma2(a.m[2], b.m[2], fma2(a.m[1], b.m[1], fma2(a.m[0], b.m[0], mul2(a.r, b.r)))));
+    return fma2f(a.E, b.E, fma2f(a.m[2], b.m[2], fma2f(a.m[1], b.m[1], fma2f(a.m[0], b.m[0], mul2f(a.r, b.r)))));
 }
 __device__ __forceinline__ P5 p5_scale(f2 g, const P5& d)
 {
-    return {mul2(g, d.r), {mul2(g, d.m[0]), mul2(g, d.m[1]), mul2(g, d.m[2])}, mul2(g, d.E)};
+    return {mul2f(g, d.r), {mul2f(g, d.m[0]), mul2f(g, d.m[1]), mul2f(g, d.m[2])}, mul2f(g, d.E)};
 }
 __device__ __forceinline__ P5 p5_zero()
 {
@@ -116,13 +116,13 @@ struct Ring5 {
 __device__ __forceinline__ void prims5(const P5& q, f2 gz, const Coef<float>& C, f2 (&u)[3], f2& T, f2& p)
 {
     const f2 ri = rcp2(q.r);
-    u[0] = mul2(q.m[0], ri);
-    u[1] = mul2(q.m[1], ri);
-    u[2] = mul2(q.m[2], ri);
-    const f2 ke = fma2(u[2], u[2], fma2(u[1], u[1], mul2(u[0], u[0])));
-    const f2 e = fma2(q.E, ri, fma2(ke, bc(-0.5f), gz));
-    T = mul2(bc(C.b), e);
-    p = mul2(mul2(bc(C.a), q.r), T);
+    u[0] = mul2f(q.m[0], ri);
+    u[1] = mul2f(q.m[1], ri);
+    u[2] = mul2f(q.m[2], ri);
+    const f2 ke = fma2f(u[2], u[2], fma2f(u[1], u[1], mul2f(u[0], u[0])));
+    const f2 e = fma2f(q.E, ri, fma2f(ke, bc(-0.5f), gz));
+    T = mul2f(bc(C.b), e);
+    p = mul2f(mul2f(bc(C.a), q.r), T);
 }
 
 // F_AL of Sec. 3.1 for two columns, from the derivatives it uses:
@@ -134,19 +134,19 @@ __device__ __forceinline__ P5 flux5(const P5& q, const f2 (&u)[3], f2 p, const f
                                     const f2 (&cb)[3], const Coef<float>& C)
 {
     constexpr int B1 = AL == 0 ? 1 : 0, B2 = AL == 2 ? 1 : 2;  // the two directions across
-    const f2 div = add2(g[AL], add2(cb[B1], cb[B2]));
+    const f2 div = add2f(g[AL], add2f(cb[B1], cb[B2]));
     const f2 mu = bc(C.mu);
     f2 tau[3];
-    tau[AL] = mul2(mu, fma2(bc(C.stokes), div, add2(g[AL], g[AL])));
-    tau[B1] = mul2(mu, add2(g[B1], ca[B1]));
-    tau[B2] = mul2(mu, add2(g[B2], ca[B2]));
+    tau[AL] = mul2f(mu, fma2f(bc(C.stokes), div, add2f(g[AL], g[AL])));
+    tau[B1] = mul2f(mu, add2f(g[B1], ca[B1]));
+    tau[B2] = mul2f(mu, add2f(g[B2], ca[B2]));
     P5 F;
     F.r = q.m[AL];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) F.m[i] = fnma2(bc(1.f), tau[i], mul2(q.m[i], u[AL]));
-    F.m[AL] = add2(F.m[AL], p);
-    const f2 work = fma2(u[2], tau[2], fma2(u[1], tau[1], mul2(u[0], tau[0])));
-    F.E = sub2(fnma2(bc(C.kth), gT, mul2(u[AL], add2(q.E, p))), work);
+    for (int i = 0; i < 3; ++i) F.m[i] = fnma2f(bc(1.f), tau[i], mul2f(q.m[i], u[AL]));
+    F.m[AL] = add2f(F.m[AL], p);
+    const f2 work = fma2f(u[2], tau[2], fma2f(u[1], tau[1], mul2f(u[0], tau[0])));
+    F.E = sub2f(fnma2f(bc(C.kth), gT, mul2f(u[AL], add2f(q.E, p))), work);
     return F;
 }
 
@@ -236,7 +236,7 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
         const f2 gz0 = gz_of(j);
         f2 u0[3], T0, p0;
         prims5(X0, gz0, C, u0, T0, p0);
-        const f2 A0 = add2(abs2(u0[AL]), sqrt2(mul2(bc(C.cs2), T0)));
+        const f2 A0 = add2f(abs2(u0[AL]), sqrt2(mul2f(bc(C.cs2), T0)));
 
         // row m = j-1: F^n, X^P and its primitives (roles 1, 2)
         const int m = j - 1;
@@ -245,34 +245,34 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
         if (role >= 1) {
             f2 g[3], ca[3], cb[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) g[c] = mul2(sub2(u0[c], u1[c]), ia);
-            ca[0] = mul2(sub2(right_of(u1[AL]), left_of(u1[AL])), i2dx);
-            cb[0] = mul2(sub2(right_of(u1[0]), left_of(u1[0])), i2dx);
+            for (int c = 0; c < 3; ++c) g[c] = mul2f(sub2f(u0[c], u1[c]), ia);
+            ca[0] = mul2f(sub2f(right_of(u1[AL]), left_of(u1[AL])), i2dx);
+            cb[0] = mul2f(sub2f(right_of(u1[0]), left_of(u1[0])), i2dx);
             ca[WD] = dwa1;
             cb[WD] = dww1;
             ca[AL] = cb[AL] = z0;
-            F1 = flux5<AL>(Xm1, u1, p1, g, mul2(sub2(T0, T1), ia), ca, cb, C);
+            F1 = flux5<AL>(Xm1, u1, p1, g, mul2f(sub2f(T0, T1), ia), ca, cb, C);
             if (AL == 2) {
                 if (m >= 1 && m <= nz - 2) {
-                    XP1.r = fnma2(lam, sub2(F1.r, F2.r), Xm1.r);
+                    XP1.r = fnma2f(lam, sub2f(F1.r, F2.r), Xm1.r);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) XP1.m[c] = fnma2(lam, sub2(F1.m[c], F2.m[c]), Xm1.m[c]);
-                    XP1.m[2] = fma2(mDg, Xm1.r, XP1.m[2]);
-                    XP1.E = fnma2(lam, sub2(F1.E, F2.E), Xm1.E);
+                    for (int c = 0; c < 3; ++c) XP1.m[c] = fnma2f(lam, sub2f(F1.m[c], F2.m[c]), Xm1.m[c]);
+                    XP1.m[2] = fma2f(mDg, Xm1.r, XP1.m[2]);
+                    XP1.E = fnma2f(lam, sub2f(F1.E, F2.E), Xm1.E);
                 } else if (m <= 0) {
-                    XP1.r = fnma2(lam2, F1.r, Xm1.r);
+                    XP1.r = fnma2f(lam2, F1.r, Xm1.r);
                     XP1.m[0] = XP1.m[1] = XP1.m[2] = z0;
-                    XP1.E = mul2(XP1.r, bc(C.ebot));
+                    XP1.E = mul2f(XP1.r, bc(C.ebot));
                 } else {
-                    XP1.r = fma2(lam2, F2.r, Xm1.r);
+                    XP1.r = fma2f(lam2, F2.r, Xm1.r);
                     XP1.m[0] = XP1.m[1] = XP1.m[2] = z0;
-                    XP1.E = mul2(XP1.r, bc(C.etop));
+                    XP1.E = mul2f(XP1.r, bc(C.etop));
                 }
             } else if (!passthru) {
-                XP1.r = fnma2(lam, sub2(F1.r, F2.r), Xm1.r);
+                XP1.r = fnma2f(lam, sub2f(F1.r, F2.r), Xm1.r);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) XP1.m[c] = fnma2(lam, sub2(F1.m[c], F2.m[c]), Xm1.m[c]);
-                XP1.E = fnma2(lam, sub2(F1.E, F2.E), Xm1.E);
+                for (int c = 0; c < 3; ++c) XP1.m[c] = fnma2f(lam, sub2f(F1.m[c], F2.m[c]), Xm1.m[c]);
+                XP1.E = fnma2f(lam, sub2f(F1.E, F2.E), Xm1.E);
             }
             prims5(XP1, gz1, C, pp1, ppT1, ppp1);
         }
@@ -285,8 +285,8 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
         buf[3][w][lane] = pp1[WD];
         __syncthreads();
         const int wu = min(w + 1, kNW3p - 1), wd = max(w - 1, 0);
-        const f2 dwa0 = mul2(sub2(buf[0][wu][lane], buf[0][wd][lane]), i2dw);
-        const f2 dww0 = mul2(sub2(buf[1][wu][lane], buf[1][wd][lane]), i2dw);
+        const f2 dwa0 = mul2f(sub2f(buf[0][wu][lane], buf[0][wd][lane]), i2dw);
+        const f2 dww0 = mul2f(sub2f(buf[1][wu][lane], buf[1][wd][lane]), i2dw);
 
         P5 d0 = p5_zero();
         f2 dd0 = z0, ss1 = z0;
@@ -294,13 +294,13 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
             // F^P at row m (backward along the march)
             f2 g[3], ca[3], cb[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) g[c] = mul2(sub2(pp1[c], pp2[c]), ia);
-            ca[0] = mul2(sub2(right_of(pp1[AL]), left_of(pp1[AL])), i2dx);
-            cb[0] = mul2(sub2(right_of(pp1[0]), left_of(pp1[0])), i2dx);
-            ca[WD] = mul2(sub2(buf[2][wu][lane], buf[2][wd][lane]), i2dw);
-            cb[WD] = mul2(sub2(buf[3][wu][lane], buf[3][wd][lane]), i2dw);
+            for (int c = 0; c < 3; ++c) g[c] = mul2f(sub2f(pp1[c], pp2[c]), ia);
+            ca[0] = mul2f(sub2f(right_of(pp1[AL]), left_of(pp1[AL])), i2dx);
+            cb[0] = mul2f(sub2f(right_of(pp1[0]), left_of(pp1[0])), i2dx);
+            ca[WD] = mul2f(sub2f(buf[2][wu][lane], buf[2][wd][lane]), i2dw);
+            cb[WD] = mul2f(sub2f(buf[3][wu][lane], buf[3][wd][lane]), i2dw);
             ca[AL] = cb[AL] = z0;
-            const P5 FP1 = flux5<AL>(XP1, pp1, ppp1, g, mul2(sub2(ppT1, ppT2), ia), ca, cb, C);
+            const P5 FP1 = flux5<AL>(XP1, pp1, ppp1, g, mul2f(sub2f(ppT1, ppT2), ia), ca, cb, C);
 
             // TVD flux across (c, m), c = j-2, from the input state
             const int c = j - 2;
@@ -309,22 +309,22 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
             ss1 = p5_dot(d1, d0);
             P5 Dn = p5_zero();
             const bool tvd_on = (AL == 2) ? (c >= 1 && c <= nz - 3) : !passthru;
-            if (tvd_on) Dn = p5_scale(tvd_G2(ss2, ss1, dd1, mul2(lam, max2(A2, A1)), C.tvd_form), d1);
+            if (tvd_on) Dn = p5_scale(tvd_G2f(ss2, ss1, dd1, mul2f(lam, max2(A2, A1)), C.tvd_form), d1);
 
             // output row c
             if (own && c >= ks && c < ke) {
                 P5 Xn;
                 const bool interior = (AL == 2) ? (c >= 1 && c <= nz - 2) : !passthru;
                 if (interior) {
-                    Xn.r = add2(fnma2(hlam, sub2(FP1.r, FP2.r), H.r), Dn.r);
+                    Xn.r = add2f(fnma2f(hlam, sub2f(FP1.r, FP2.r), H.r), Dn.r);
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) Xn.m[q] = add2(fnma2(hlam, sub2(FP1.m[q], FP2.m[q]), H.m[q]), Dn.m[q]);
-                    Xn.E = add2(fnma2(hlam, sub2(FP1.E, FP2.E), H.E), Dn.E);
+                    for (int q = 0; q < 3; ++q) Xn.m[q] = add2f(fnma2f(hlam, sub2f(FP1.m[q], FP2.m[q]), H.m[q]), Dn.m[q]);
+                    Xn.E = add2f(fnma2f(hlam, sub2f(FP1.E, FP2.E), H.E), Dn.E);
                 } else if (AL == 2) {
                     // plates: rho = (rho^P + rho^C)/2 with the half-cell corrector
-                    Xn.r = (c == 0) ? fnma2(lam, FP1.r, H.r) : H.r;
+                    Xn.r = (c == 0) ? fnma2f(lam, FP1.r, H.r) : H.r;
                     Xn.m[0] = Xn.m[1] = Xn.m[2] = z0;
-                    Xn.E = mul2(Xn.r, bc(c == 0 ? C.ebot : C.etop));
+                    Xn.E = mul2f(Xn.r, bc(c == 0 ? C.ebot : C.etop));
                 } else {
                     Xn = H;  // plate planes of L_y: the input row
                 }
@@ -334,17 +334,17 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
             // H of row m for the next step
             const bool interior_m = (AL == 2) ? (m >= 1 && m <= nz - 2) : !passthru;
             if (interior_m) {
-                H.r = sub2(mul2(half, add2(XP1.r, Xm1.r)), Dn.r);
-                H.m[0] = sub2(mul2(half, add2(XP1.m[0], Xm1.m[0])), Dn.m[0]);
-                H.m[1] = sub2(mul2(half, add2(XP1.m[1], Xm1.m[1])), Dn.m[1]);
+                H.r = sub2f(mul2f(half, add2f(XP1.r, Xm1.r)), Dn.r);
+                H.m[0] = sub2f(mul2f(half, add2f(XP1.m[0], Xm1.m[0])), Dn.m[0]);
+                H.m[1] = sub2f(mul2f(half, add2f(XP1.m[1], Xm1.m[1])), Dn.m[1]);
                 if (AL == 2)
-                    H.m[2] = sub2(mul2(half, fma2(mDg, XP1.r, add2(XP1.m[2], Xm1.m[2]))), Dn.m[2]);
+                    H.m[2] = sub2f(mul2f(half, fma2f(mDg, XP1.r, add2f(XP1.m[2], Xm1.m[2]))), Dn.m[2]);
                 else
-                    H.m[2] = sub2(mul2(half, add2(XP1.m[2], Xm1.m[2])), Dn.m[2]);
-                H.E = sub2(mul2(half, add2(XP1.E, Xm1.E)), Dn.E);
+                    H.m[2] = sub2f(mul2f(half, add2f(XP1.m[2], Xm1.m[2])), Dn.m[2]);
+                H.E = sub2f(mul2f(half, add2f(XP1.E, Xm1.E)), Dn.E);
             } else if (AL == 2) {
                 H = p5_zero();
-                H.r = mul2(half, add2(XP1.r, Xm1.r));
+                H.r = mul2f(half, add2f(XP1.r, Xm1.r));
             } else {
                 H = Xm1;
             }
@@ -453,31 +453,31 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
             if (interior_m) {
                 f2 g[3], ca[3], cb[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) g[c] = mul2(sub2(right_of(u1[c]), u1[c]), idx_);
+                for (int c = 0; c < 3; ++c) g[c] = mul2f(sub2f(right_of(u1[c]), u1[c]), idx_);
                 ca[1] = dwx1;
                 cb[1] = dwy1;
-                ca[2] = mul2(sub2(u0[0], u2x), i2dz);
-                cb[2] = mul2(sub2(u0[2], u2z), i2dz);
+                ca[2] = mul2f(sub2f(u0[0], u2x), i2dz);
+                cb[2] = mul2f(sub2f(u0[2], u2z), i2dz);
                 ca[0] = cb[0] = z0;
-                const P5 F1 = flux5<0>(Xm1, u1, p1, g, mul2(sub2(right_of(T1), T1), idx_), ca, cb, C);
+                const P5 F1 = flux5<0>(Xm1, u1, p1, g, mul2f(sub2f(right_of(T1), T1), idx_), ca, cb, C);
                 const P5 Fl = p5_left(F1);
-                XP1.r = fnma2(lam, sub2(F1.r, Fl.r), Xm1.r);
+                XP1.r = fnma2f(lam, sub2f(F1.r, Fl.r), Xm1.r);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) XP1.m[c] = fnma2(lam, sub2(F1.m[c], Fl.m[c]), Xm1.m[c]);
-                XP1.E = fnma2(lam, sub2(F1.E, Fl.E), Xm1.E);
+                for (int c = 0; c < 3; ++c) XP1.m[c] = fnma2f(lam, sub2f(F1.m[c], Fl.m[c]), Xm1.m[c]);
+                XP1.E = fnma2f(lam, sub2f(F1.E, Fl.E), Xm1.E);
                 if (role == 2) {
                     // TVD along x on row m from the input state
                     const P5 dr = p5_sub(p5_right(Xm1), Xm1);
                     const f2 dd = p5_dot(dr, dr);
                     const f2 sp = p5_dot(p5_left(dr), dr);
-                    const f2 A = add2(abs2(u1[0]), sqrt2(mul2(bc(C.cs2), T1)));
-                    const f2 G = tvd_G2(sp, right_of(sp), dd, mul2(lam, max2(A, right_of(A))), C.tvd_form);
+                    const f2 A = add2f(abs2(u1[0]), sqrt2(mul2f(bc(C.cs2), T1)));
+                    const f2 G = tvd_G2f(sp, right_of(sp), dd, mul2f(lam, max2(A, right_of(A))), C.tvd_form);
                     const P5 Dn = p5_scale(G, dr);
                     const P5 Dl = p5_left(Dn);
-                    K1.r = fma2(half, add2(XP1.r, Xm1.r), sub2(Dn.r, Dl.r));
+                    K1.r = fma2f(half, add2f(XP1.r, Xm1.r), sub2f(Dn.r, Dl.r));
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) K1.m[c] = fma2(half, add2(XP1.m[c], Xm1.m[c]), sub2(Dn.m[c], Dl.m[c]));
-                    K1.E = fma2(half, add2(XP1.E, Xm1.E), sub2(Dn.E, Dl.E));
+                    for (int c = 0; c < 3; ++c) K1.m[c] = fma2f(half, add2f(XP1.m[c], Xm1.m[c]), sub2f(Dn.m[c], Dl.m[c]));
+                    K1.E = fma2f(half, add2f(XP1.E, Xm1.E), sub2f(Dn.E, Dl.E));
                 }
             }
             prims5(XP1, gz1, C, pp1, ppT1, ppp1);
@@ -491,10 +491,10 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
         buf[3][w][lane] = pp1[1];
         __syncthreads();
         const int wu = min(w + 1, kNW3p - 1), wd = max(w - 1, 0);
-        const f2 dwx0 = mul2(sub2(buf[0][wu][lane], buf[0][wd][lane]), i2dy);
-        const f2 dwy0 = mul2(sub2(buf[1][wu][lane], buf[1][wd][lane]), i2dy);
-        const f2 dwpx1 = mul2(sub2(buf[2][wu][lane], buf[2][wd][lane]), i2dy);
-        const f2 dwpy1 = mul2(sub2(buf[3][wu][lane], buf[3][wd][lane]), i2dy);
+        const f2 dwx0 = mul2f(sub2f(buf[0][wu][lane], buf[0][wd][lane]), i2dy);
+        const f2 dwy0 = mul2f(sub2f(buf[1][wu][lane], buf[1][wd][lane]), i2dy);
+        const f2 dwpx1 = mul2f(sub2f(buf[2][wu][lane], buf[2][wd][lane]), i2dy);
+        const f2 dwpy1 = mul2f(sub2f(buf[3][wu][lane], buf[3][wd][lane]), i2dy);
 
         if (role == 2) {
             // row c = j-2: F^P (backward x), corrector, output
@@ -503,28 +503,28 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
             if (c >= 1 && c <= nz - 2) {
                 f2 g[3], ca[3], cb[3];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) g[q] = mul2(sub2(pp2[q], left_of(pp2[q])), idx_);
+                for (int q = 0; q < 3; ++q) g[q] = mul2f(sub2f(pp2[q], left_of(pp2[q])), idx_);
                 ca[1] = dwpx2;
                 cb[1] = dwpy2;
-                ca[2] = mul2(sub2(pp1[0], pp3x), i2dz);
-                cb[2] = mul2(sub2(pp1[2], pp3z), i2dz);
+                ca[2] = mul2f(sub2f(pp1[0], pp3x), i2dz);
+                cb[2] = mul2f(sub2f(pp1[2], pp3z), i2dz);
                 ca[0] = cb[0] = z0;
-                const P5 FP = flux5<0>(XP2, pp2, ppp2, g, mul2(sub2(ppT2, left_of(ppT2)), idx_), ca, cb, C);
+                const P5 FP = flux5<0>(XP2, pp2, ppp2, g, mul2f(sub2f(ppT2, left_of(ppT2)), idx_), ca, cb, C);
                 const P5 FPr = p5_right(FP);
-                Xn.r = fnma2(hlam, sub2(FPr.r, FP.r), K2.r);
+                Xn.r = fnma2f(hlam, sub2f(FPr.r, FP.r), K2.r);
 #pragma unroll
-                for (int q = 0; q < 3; ++q) Xn.m[q] = fnma2(hlam, sub2(FPr.m[q], FP.m[q]), K2.m[q]);
-                Xn.E = fnma2(hlam, sub2(FPr.E, FP.E), K2.E);
+                for (int q = 0; q < 3; ++q) Xn.m[q] = fnma2f(hlam, sub2f(FPr.m[q], FP.m[q]), K2.m[q]);
+                Xn.E = fnma2f(hlam, sub2f(FPr.E, FP.E), K2.E);
             }
             if (own && c >= ks && c < ke) {
                 st5(io.out, fs, row_off(c), Xn);
                 if (want_dt) {
                     f2 un[3], Tn, pn;
                     prims5(Xn, gz2, C, un, Tn, pn);
-                    const f2 cs = sqrt2(mul2(bc(C.cs2), Tn));
-                    const f2 rx = mul2(add2(abs2(un[0]), cs), idx_);
-                    const f2 ry = mul2(add2(abs2(un[1]), cs), bc(C.inv_dy));
-                    const f2 rz = mul2(add2(abs2(un[2]), cs), bc(C.inv_dz));
+                    const f2 cs = sqrt2(mul2f(bc(C.cs2), Tn));
+                    const f2 rx = mul2f(add2f(abs2(un[0]), cs), idx_);
+                    const f2 ry = mul2f(add2f(abs2(un[1]), cs), bc(C.inv_dy));
+                    const f2 rz = mul2f(add2f(abs2(un[2]), cs), bc(C.inv_dz));
                     const f2 r2 = max2(max2(rx, ry), rz);
                     const float r = fmaxf(r2.x, r2.y);
                     if (!(r > 0.f) || !(r < 1e30f)) bad = 1;

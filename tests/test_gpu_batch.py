@@ -2,10 +2,11 @@
 boxes, graph-replayed steps): every box must agree with its own single-box
 run, and a box must match the FP64 oracle within the FP32 bar of
 tests/test_gpu_parity.py.  Batch and solo runs may split rows into segments
-differently (the autotuner), and the FP32 sweeps are reproducible only for a
-fixed split (at the FP32 noise level otherwise), which this unstable flow
-amplifies to ~2e-6 over 63 steps; 1e-5 is the bar, far below what a wrong
-work item, dt slot or graph replay would produce."""
+differently (the autotuner).  The default FP32 sweeps are reproducible bit
+for bit only for a fixed split (at the FP32 noise level otherwise), which this
+unstable flow amplifies to ~2e-6 over 63 steps, so 1e-5 is their bar, far
+below what a wrong work item, dt slot or graph replay would produce; with
+cm_params.layout_exact = 1 every box equals its solo run bit for bit."""
 import ctypes
 import math
 
@@ -57,6 +58,30 @@ def test_batch_boxes_equal_their_solo_runs():
         assert diags[b]["step"] == nsteps and d["step"] == nsteps
         for k in ("t", "dt", "mass"):
             assert abs(diags[b][k] - d[k]) <= 1e-5 * abs(d[k]), (b, k)
+
+
+def test_layout_exact_batch_boxes_equal_their_solo_runs_bit_for_bit():
+    """With cm_params.layout_exact = 1 the FP32 sweeps round alike whatever
+    the segment split, so every box of the batch (its own segment lengths
+    from the batch tuner, its own kernels) equals its single-box run bit for
+    bit, time and dt included."""
+    import paper_2411_10372_gb300 as cm
+    nsteps = 63
+    p = _params(cm)
+    p.layout_exact = 1
+    cm.cm_batch_init(_grids(cm), RAS, 1.0, 5.0 / 3.0, p)
+    cm.cm_batch_step(nsteps)
+    diags = cm.cm_batch_diagnostics()
+    batch_states = [cm.cm_batch_get_state(b, np.empty((4, nz, nx))) for b, (nx, nz) in enumerate(SIZES)]
+    cm.cm_batch_finalize()
+    for b, (nx, nz) in enumerate(SIZES):
+        s = cm.Solver(nx, nz, RAS[b], 1.0, 5.0 / 3.0, precision="fp32", seed=777 + b, layout_exact=1)
+        s.step(nsteps)
+        solo = s.state()
+        d = s.sample()
+        s.close()
+        assert np.array_equal(batch_states[b], solo), (b, float(np.max(np.abs(batch_states[b] - solo))))
+        assert diags[b]["t"] == d["t"] and diags[b]["dt"] == d["dt"]
 
 
 def test_batch_box_matches_oracle():
