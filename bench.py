@@ -171,6 +171,7 @@ def run_gpu(args):
         s.step(W)
         s.sync()
         barrier()
+        n_diag0 = len(s.diagnostics())
         launches0 = cm.cm_launch_count()
         clk = Clocks(local)
         # the value: events only at step boundaries, so the sweeps of a step
@@ -186,13 +187,15 @@ def run_gpu(args):
         barrier()
         launches = cm.cm_launch_count() - launches0
         s.sync()
+        n_diag_timed = len(s.diagnostics()) - n_diag0
         total_ms = max_ms(sum(step_ms))
         seg = cm.cm_tuning()
         # per-kernel durations for the roofline: a second timed pass with an
         # event pair around every sweep (each duration includes its launch gap)
         sweep_ms, _ = cm.cm_profile_steps(max(3, min(K, 500)), FLUSH_BYTES, per_sweep=True)
         ds = s.diagnostics()
-        diag = {"samples": len(ds), "all_finite": all(d["status"] == 0 for d in ds),
+        diag = {"samples": len(ds), "samples_in_timed_steps": n_diag_timed,
+                "all_finite": all(d["status"] == 0 for d in ds),
                 "last_Nu_bar": ds[-1]["Nu_bar"] if ds else None}
         out = dict(total_ms=total_ms, sweep_ms=sweep_ms, launches=launches, clocks=clk.summary() if clocks else None,
                    w=8 if precision == "fp64" else 4, segments={"z": seg[0], "x": seg[1]}, diag=diag)
@@ -485,7 +488,8 @@ def run_gpu(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD + "_fp32", "nx": NXr, "nz": NZr, "Ra": RA, "Pr": PR, "gamma": GAMMA,
                    "eps": 0.1, "D": 0.5, "cfl": 0.5, "state": "fp32, fp64 dt and reductions",
-                   "diagnostics": "sampled every 100 steps inside the timed region",
+                   "diagnostics": f"FP64 record every 100 steps ({r32['diag']['samples_in_timed_steps']} "
+                                  f"of them inside the {K} timed steps)",
                    "l2": "flushed before every timed step (256 MiB memset)", "parallelism": f"replicas x{world}",
                    "timing": "events at step boundaries for value; per-sweep events in a second pass for roofline"},
         "roofline": roofline(r32),
