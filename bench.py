@@ -171,7 +171,7 @@ def run_gpu(args):
         s.step(W)
         s.sync()
         barrier()
-        n_diag0 = len(s.diagnostics())
+        s.diagnostics()  # drain the warm-up's records
         launches0 = cm.cm_launch_count()
         clk = Clocks(local)
         # the value: events only at step boundaries, so the sweeps of a step
@@ -187,15 +187,13 @@ def run_gpu(args):
         barrier()
         launches = cm.cm_launch_count() - launches0
         s.sync()
-        n_diag_timed = len(s.diagnostics()) - n_diag0
+        ds = s.diagnostics()  # the records taken inside the timed steps
         total_ms = max_ms(sum(step_ms))
         seg = cm.cm_tuning()
         # per-kernel durations for the roofline: a second timed pass with an
         # event pair around every sweep (each duration includes its launch gap)
         sweep_ms, _ = cm.cm_profile_steps(max(3, min(K, 500)), FLUSH_BYTES, per_sweep=True)
-        ds = s.diagnostics()
-        diag = {"samples": len(ds), "samples_in_timed_steps": n_diag_timed,
-                "all_finite": all(d["status"] == 0 for d in ds),
+        diag = {"samples_in_timed_steps": len(ds), "all_finite": all(d["status"] == 0 for d in ds),
                 "last_Nu_bar": ds[-1]["Nu_bar"] if ds else None}
         out = dict(total_ms=total_ms, sweep_ms=sweep_ms, launches=launches, clocks=clk.summary() if clocks else None,
                    w=8 if precision == "fp64" else 4, segments={"z": seg[0], "x": seg[1]}, diag=diag)
