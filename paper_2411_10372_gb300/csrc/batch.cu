@@ -84,7 +84,10 @@ int ck(cudaError_t e, const char* what)
 #define CKB(call) do { int rc_ = ck((call), #call); if (rc_) return rc_; } while (0)
 
 // warp work items of one sweep for the given per-box segment lengths;
-// each box's items are padded to whole blocks of kWarpsPerBlock warps
+// each box's items are padded to whole blocks of kWarpsPerBlock warps.  The
+// blocks are then ordered by decreasing cost (rows stepped by their longest
+// warp, pipeline ramp included), so that the hardware's in-order block
+// dispatch schedules the longest first and short blocks fill the tail.
 std::vector<BatchWork> build_work(const Batch& B, bool zdir)
 {
     std::vector<BatchWork> w;
@@ -99,7 +102,21 @@ std::vector<BatchWork> build_work(const Batch& B, bool zdir)
         while ((w.size() - first) % kWarpsPerBlock) w.push_back({b, 0, 1 << 30, seg, 0, {0, 0, 0}});
         for (size_t q = first; q < first + kWarpsPerBlock; ++q) w[q].lead = 1;
     }
-    return w;
+    const size_t nblk = w.size() / kWarpsPerBlock;
+    std::vector<int> cost(nblk, 0), order(nblk);
+    for (size_t k = 0; k < nblk; ++k) {
+        for (int q = 0; q < kWarpsPerBlock; ++q) {
+            const BatchWork& it = w[k * kWarpsPerBlock + q];
+            const int nz = B.boxes[it.box].grid.nz;
+            if (it.ks < nz) cost[k] = std::max(cost[k], std::min(it.seg_rows, nz - it.ks) + 3);
+        }
+        order[k] = (int)k;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<BatchWork> sorted(w.size());
+    for (size_t k = 0; k < nblk; ++k)
+        for (int q = 0; q < kWarpsPerBlock; ++q) sorted[k * kWarpsPerBlock + q] = w[order[k] * kWarpsPerBlock + q];
+    return sorted;
 }
 
 int upload_work(Batch& B)

@@ -107,16 +107,24 @@ cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool 
     constexpr size_t kCacheZ = kRingBytes + (size_t)kWarpsPerBlock * plane_cap2(kBatchSegMax) * 5 * sizeof(float);
     constexpr size_t kCacheX = kRingBytes + (size_t)kWarpsPerBlock * plane_cap2(kBatchSegMax) * 2 * sizeof(float);
     using K = void (*)(BatchLaunch);
-    // [layout_exact][dir z, x][stretched][const coefficients]
-    static const K kern[2][2][2][2] = {
-        {{{pkf::sweep_z2d_batch_smem, pkf::sweep_z2d_batch}, {pkf::sweep_z2d_batch_smem_s, pkf::sweep_z2d_batch_s}},
-         {{pkf::sweep_x2d_batch_smem, pkf::sweep_x2d_batch}, {pkf::sweep_x2d_batch_smem_s, pkf::sweep_x2d_batch_s}}},
-        {{{pkx::sweep_z2d_batch_smem, pkx::sweep_z2d_batch}, {pkx::sweep_z2d_batch_smem_s, pkx::sweep_z2d_batch_s}},
-         {{pkx::sweep_x2d_batch_smem, pkx::sweep_x2d_batch}, {pkx::sweep_x2d_batch_smem_s, pkx::sweep_x2d_batch_s}}}};
+    // [layout_exact][kernel][stretched][const coefficients]; kernel: z, x, x with dt
+    static const K kern[2][3][2][2] = {
+        {{{pkf::sweep_z2d_batch_smem<false>, pkf::sweep_z2d_batch<false>},
+          {pkf::sweep_z2d_batch_smem<true>, pkf::sweep_z2d_batch<true>}},
+         {{pkf::sweep_x2d_batch_smem<false, 0>, pkf::sweep_x2d_batch<false, 0>},
+          {pkf::sweep_x2d_batch_smem<true, 0>, pkf::sweep_x2d_batch<true, 0>}},
+         {{pkf::sweep_x2d_batch_smem<false, 1>, pkf::sweep_x2d_batch<false, 1>},
+          {pkf::sweep_x2d_batch_smem<true, 1>, pkf::sweep_x2d_batch<true, 1>}}},
+        {{{pkx::sweep_z2d_batch_smem<false>, pkx::sweep_z2d_batch<false>},
+          {pkx::sweep_z2d_batch_smem<true>, pkx::sweep_z2d_batch<true>}},
+         {{pkx::sweep_x2d_batch_smem<false, 0>, pkx::sweep_x2d_batch<false, 0>},
+          {pkx::sweep_x2d_batch_smem<true, 0>, pkx::sweep_x2d_batch<true, 0>}},
+         {{pkx::sweep_x2d_batch_smem<false, 1>, pkx::sweep_x2d_batch<false, 1>},
+          {pkx::sweep_x2d_batch_smem<true, 1>, pkx::sweep_x2d_batch<true, 1>}}}};
     static bool init = false;
     if (!init) {
         for (int v = 0; v < 2; ++v)
-            for (int d = 0; d < 2; ++d)
+            for (int d = 0; d < 3; ++d)
                 for (int st = 0; st < 2; ++st)
                     for (int cc = 0; cc < 2; ++cc)
                         cudaFuncSetAttribute(kern[v][d][st][cc], cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -124,7 +132,7 @@ cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool 
         init = true;
     }
     if (dir != 2 && dir != 0) return cudaErrorInvalidValue;
-    const int d = dir == 2 ? 0 : 1;
+    const int d = dir == 2 ? 0 : (L.last ? 2 : 1);
     const size_t smem = stretched ? (d == 0 ? kCacheZ : kCacheX) : kRingBytes;
     kern[layout_exact ? 1 : 0][d][stretched ? 1 : 0][const_coefs ? 1 : 0]<<<nblocks, kThreads2, smem, s>>>(L);
     return cudaGetLastError();

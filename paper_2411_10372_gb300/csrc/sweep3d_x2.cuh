@@ -418,8 +418,10 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
     auto row_off = [&](int k) -> int { return (min(max(k, 0), nz - 1) * ny + cwr) * pitch + ic; };
     auto gz_of = [&](int k) -> f2 { return bc(-C.g * io.zt[min(max(k, 0), nz - 1)]); };
 
-    float rmax = 0.f;
-    int bad = 0;
+    // next dt: running maxima of |u_x| + c, |u_y| + c, |u_z| + c over the
+    // stored nodes (NaN-propagating), times 1/dx, 1/dy, 1/dz once at the end
+    // (equal to the maximum of the per-node products: rounding is monotone)
+    float ax = 0.f, ay = 0.f, az = 0.f;
     const Ring5<kNW3p * 32> ring{ring3_mem + threadIdx.x};
     const int j0 = ks - 2;
     for (int q = 0; q < kRing3 - 1; ++q) ring.request(q, io.in + row_off(j0 + q), fs);
@@ -516,19 +518,20 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
                 for (int q = 0; q < 3; ++q) Xn.m[q] = fnma2f(hlam, sub2f(FPr.m[q], FP.m[q]), K2.m[q]);
                 Xn.E = fnma2f(hlam, sub2f(FPr.E, FP.E), K2.E);
             }
-            if (own && c >= ks && c < ke) {
-                st5(io.out, fs, row_off(c), Xn);
-                if (want_dt) {
-                    f2 un[3], Tn, pn;
-                    prims5(Xn, gz2, C, un, Tn, pn);
-                    const f2 cs = sqrt2(mul2f(bc(C.cs2), Tn));
-                    const f2 rx = mul2f(add2f(abs2(un[0]), cs), idx_);
-                    const f2 ry = mul2f(add2f(abs2(un[1]), cs), bc(C.inv_dy));
-                    const f2 rz = mul2f(add2f(abs2(un[2]), cs), bc(C.inv_dz));
-                    const f2 r2 = max2(max2(rx, ry), rz);
-                    const float r = fmaxf(r2.x, r2.y);
-                    if (!(r > 0.f) || !(r < 1e30f)) bad = 1;
-                    rmax = fmaxf(rmax, r);
+            const bool keep = own && c >= ks && c < ke;
+            if (keep) st5(io.out, fs, row_off(c), Xn);
+            if (want_dt) {
+                // every lane of a storing warp evaluates; only kept nodes count
+                f2 un[3], Tn, pn;
+                prims5(Xn, gz2, C, un, Tn, pn);
+                const f2 cs = sqrt2(mul2f(bc(C.cs2), Tn));
+                const float vx = fmax_nan(fabsf(un[0].x) + cs.x, fabsf(un[0].y) + cs.y);
+                const float vy = fmax_nan(fabsf(un[1].x) + cs.x, fabsf(un[1].y) + cs.y);
+                const float vz = fmax_nan(fabsf(un[2].x) + cs.x, fabsf(un[2].y) + cs.y);
+                if (keep) {
+                    ax = fmax_nan(ax, vx);
+                    ay = fmax_nan(ay, vy);
+                    az = fmax_nan(az, vz);
                 }
             }
         }
@@ -556,7 +559,10 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
         dwpy2 = dwpy1;
     }
     cp_async_drain();
-    if (want_dt) block_dt_reduce(rmax > 0.f ? 1.0 / (double)rmax : 1e308, bad, sc.ctl, sc.slot_in ^ 1);
+    if (want_dt) {
+        const float r = fmax_nan(fmax_nan(ax * C.inv_dx, ay * C.inv_dy), az * C.inv_dz);
+        block_dt_reduce(r > 0.f ? 1.0 / (double)r : 1e308, !(r < 1e30f), sc.ctl, sc.slot_in ^ 1);
+    }
 }
 
 }  // namespace cm
