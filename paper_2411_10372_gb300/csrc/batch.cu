@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -192,11 +193,18 @@ int time_sweep(Batch& B, int dir, float* ms_out)
 
 // Autotuner: coordinate descent over the segment length of each box size
 // class (nz < 64, < 128, < 256, >= 256), per sweep direction, on the timed
-// batched sweep itself.
+// batched sweep itself; two passes over the classes, since the best length
+// of one class depends on how the others fill the GPU.
 int autotune(Batch& B)
 {
+    // CM_SEG_ROWS=n: every box runs n-row segments, untuned (profiling captures)
+    if (const char* e = getenv("CM_SEG_ROWS")) {
+        const int n = std::min(std::max(atoi(e), kBatchSegMin), kBatchSegMax);
+        for (Box& x : B.boxes) x.seg_z = x.seg_x = n;
+        return upload_work(B);
+    }
     // not only powers of two: the single-box sweeps ran fastest at 29 rows
-    const int cand[] = {8, 12, 16, 20, 24, 29, 32, 40, 48, 64, 96, 128};
+    const int cand[] = {kBatchSegMin, 8, 10, 12, 14, 16, 20, 24, 29, 32, 40, 48, 64, 96, 128};
     static_assert(kBatchSegMax >= 128, "the stretched batch kernels size their plane caches for kBatchSegMax rows");
     bool present[4] = {false, false, false, false};
     for (const Box& x : B.boxes) present[x.cls] = true;
@@ -210,17 +218,19 @@ int autotune(Batch& B)
         if (rc) return rc;
         float best = 0.f;
         if ((rc = time_sweep(B, dir, &best))) return rc;
-        for (int c = 0; c < 4; ++c) {
-            if (!present[c]) continue;
-            for (int v : cand) {
-                if (v == seg[c]) continue;
-                const int keep = seg[c];
-                seg[c] = v;
-                if ((rc = apply())) return rc;
-                float t = 0.f;
-                if ((rc = time_sweep(B, dir, &t))) return rc;
-                if (t < 0.99f * best) best = t;
-                else seg[c] = keep;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int c = 0; c < 4; ++c) {
+                if (!present[c]) continue;
+                for (int v : cand) {
+                    if (v == seg[c]) continue;
+                    const int keep = seg[c];
+                    seg[c] = v;
+                    if ((rc = apply())) return rc;
+                    float t = 0.f;
+                    if ((rc = time_sweep(B, dir, &t))) return rc;
+                    if (t < 0.99f * best) best = t;
+                    else seg[c] = keep;
+                }
             }
         }
         if ((rc = apply())) return rc;
@@ -316,7 +326,7 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
         x.buf_elems = 4 * (size_t)x.fstride;
         const int nz = x.grid.nz;
         x.cls = nz < 64 ? 0 : nz < 128 ? 1 : nz < 256 ? 2 : 3;
-        x.seg_z = x.seg_x = 8;  // smallest candidate: sizes the work buffers
+        x.seg_z = x.seg_x = kBatchSegMin;  // smallest candidate: sizes the work buffers
         off[kPieces * b + 0] = take(2 * x.buf_elems * sizeof(float));
         off[kPieces * b + 1] = take(nz * sizeof(float));
         off[kPieces * b + 2] = take(nz * sizeof(double));
@@ -326,7 +336,7 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
         off[kPieces * b + 6] = take(sizeof(DevCtl));
         off[kPieces * b + 7] = take(any_st ? nz * sizeof(Plane<float>) : 0);
         off[kPieces * b + 8] = take(any_st ? nz * sizeof(Plane<double>) : 0);
-        items += ((size_t)((x.grid.nx + kOutW2 - 1) / kOutW2) * ((nz + 7) / 8) + kWarpsPerBlock);
+        items += ((size_t)((x.grid.nx + kOutW2 - 1) / kOutW2) * ((nz + kBatchSegMin - 1) / kBatchSegMin) + kWarpsPerBlock);
     }
     B->work_cap = items;
     if (cudaMalloc(&B->pool, bytes) != cudaSuccess || cudaMalloc(&B->d_boxes, nbox * sizeof(BoxDesc)) != cudaSuccess ||

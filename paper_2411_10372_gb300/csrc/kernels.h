@@ -77,6 +77,7 @@ cudaError_t launch_sweep3_x2(int dir, const float* in, float* out, const float* 
 struct BatchLaunch;
 constexpr int kConstBoxes = 256;
 constexpr int kBatchSegMax = 128;
+constexpr int kBatchSegMin = 6;  // shortest segment the batch autotuner tries (sizes the work lists)
 cudaError_t launch_sweep_batch(int dir, const BatchLaunch& L, int nblocks, bool const_coefs, bool stretched,
                                bool layout_exact, cudaStream_t s);
 // copy the coefficients of n <= kConstBoxes boxes to constant memory (kernels_f32.cu)

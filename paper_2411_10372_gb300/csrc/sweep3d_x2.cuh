@@ -221,11 +221,13 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
     prims5(Xm1, gz1, C, u1, T1, p1);
     f2 A1 = z0, A2 = z0;        // |u_AL| + c of rows j-1, j-2
     f2 dwa1 = z0, dww1 = z0;    // d/dW of u_AL, u_W of X at row j-1 (exchanged one step earlier)
-    P5 F2 = p5_zero();          // F^n_{j-2}
-    P5 FP2 = p5_zero();         // F^P_{j-2}
+    // carried from row to row; each is replaced as soon as its new value
+    // exists (which shortens what is live across the exchange)
+    P5 F2 = p5_zero();   // F^n_{j-2}
+    P5 FP2 = p5_zero();  // F^P_{j-2}
+    P5 H = p5_zero();    // H_{j-2}
+    P5 d1 = p5_zero();   // X_{j-1} - X_{j-2}
     f2 pp2[3] = {u1[0], u1[1], u1[2]}, ppT2 = T1;  // primitives of X^P_{j-2}
-    P5 H = p5_zero();           // H_{j-2}
-    P5 d1 = p5_zero();          // X_{j-1} - X_{j-2}
     f2 dd1 = z0, ss2 = z0;      // <d1, d1>, <X_{j-2} - X_{j-3}, d1>
 
     for (int j = j0; j <= ke + 1; ++j) {
@@ -275,6 +277,7 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
                 XP1.E = fnma2f(lam, sub2f(F1.E, F2.E), Xm1.E);
             }
             prims5(XP1, gz1, C, pp1, ppT1, ppp1);
+            F2 = F1;
         }
 
         // exchange across W: u of X at row j and of X^P at row m
@@ -310,6 +313,7 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
             P5 Dn = p5_zero();
             const bool tvd_on = (AL == 2) ? (c >= 1 && c <= nz - 3) : !passthru;
             if (tvd_on) Dn = p5_scale(tvd_G2f(ss2, ss1, dd1, mul2f(lam, max2(A2, A1)), C.tvd_form), d1);
+            d1 = d0;
 
             // output row c
             if (own && c >= ks && c < ke) {
@@ -364,9 +368,7 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
         A1 = A0;
         dwa1 = dwa0;
         dww1 = dww0;
-        F2 = F1;
         ppT2 = ppT1;
-        d1 = d0;
         dd1 = dd0;
         ss2 = ss1;
     }

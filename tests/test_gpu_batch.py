@@ -38,7 +38,7 @@ def test_batch_boxes_equal_their_solo_runs():
     nsteps = 63  # one 50-step graph replay plus direct launches, odd count
     cm.cm_batch_init(_grids(cm), RAS, 1.0, 5.0 / 3.0, _params(cm))
     seg_z, seg_x = cm.cm_batch_tuning()
-    assert all(s in (8, 12, 16, 20, 24, 29, 32, 40, 48, 64, 96, 128) for s in seg_z + seg_x)
+    assert all(s in (6, 8, 10, 12, 14, 16, 20, 24, 29, 32, 40, 48, 64, 96, 128) for s in seg_z + seg_x)
     cm.cm_batch_step(nsteps)
     diags = cm.cm_batch_diagnostics()
     batch_states = []
