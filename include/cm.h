@@ -58,6 +58,10 @@ extern "C" {
 #define CM_ADJ_PHI_FROZEN 1 /* phi' = 0: no derivative through the ratios r (the limiter's
                                values held fixed; C(Co) still differentiated) */
 
+/* order of the half-step sweeps L_alpha(dt/2) within one step (Sec. 3.1, Eq. time_step) */
+#define CM_SPLIT_PRINTED 0   /* z, (y), x, z, (y), x: X^{n+1} = L_x L_y L_z L_x L_y L_z X^n as printed */
+#define CM_SPLIT_SYMMETRIC 1 /* x, (y), z, z, (y), x: the palindrome of the same half steps */
+
 typedef struct cm_grid {
     int ndim;       /* 2 or 3 */
     int nx, ny, nz; /* nodes; x (and y) periodic; nz counts both plates (ny ignored in 2D) */
@@ -103,6 +107,9 @@ typedef struct cm_params {
                             node may round differently by an ulp with the segment length that the
                             timing tuner at init picks; 1 = results bit for bit independent of the
                             segment lengths (about 6% slower at 4096 x 1024).  No paper passage. */
+    int split;           /* CM_SPLIT_* (default CM_SPLIT_PRINTED); single contexts and batches;
+                            the adjoint takes CM_SPLIT_PRINTED only (CM_EINVAL otherwise) */
+    int reserved_;       /* set to 0 */
 } cm_params;
 
 /* One diagnostics sample (Sec. 2, Eqs. volume_Nu, mean_Nu, Re), FP64.

@@ -81,7 +81,7 @@ def build_omp(force: bool = False) -> str | None:
 class _Cfg(ctypes.Structure):
     _fields_ = [
         ("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-        ("tvd_form", ctypes.c_int), ("pad_", ctypes.c_int),
+        ("tvd_form", ctypes.c_int), ("split", ctypes.c_int),
         ("aspect", ctypes.c_double), ("Ra", ctypes.c_double), ("Pr", ctypes.c_double),
         ("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("D", ctypes.c_double),
         ("cfl", ctypes.c_double), ("dt_fixed", ctypes.c_double), ("gravity", ctypes.c_double),
@@ -116,6 +116,7 @@ class Config:
     pert_amp: float = 1e-3
     seed: int = 12345
     tvd_form: int = TVD_SPLIT
+    split: int = 0                    # 0: Eq. time_step as printed; 1: palindrome x, (y), z, z, (y), x
     stokes: float = -2.0 / 3.0
     zstretch: float = 0.0             # beta of the tanh z-grid (Sec. 3); 0 = uniform
     znodes: "np.ndarray | None" = None  # explicit plane heights, overriding zstretch
@@ -137,7 +138,7 @@ class Config:
             zn = np.ascontiguousarray(self.znodes, dtype=np.float64)
             assert zn.shape == (self.nz,)
         c = _Cfg(self.ndim, self.nx, self.ny if self.ndim == 3 else 1, self.nz,
-                 self.tvd_form, 0, self.aspect, self.Ra, self.Pr, self.gamma, self.eps,
+                 self.tvd_form, self.split, self.aspect, self.Ra, self.Pr, self.gamma, self.eps,
                  self.D, self.cfl, self.dt_fixed, self.gravity, self.t_bot, t_top,
                  self.pert_amp, self.stokes, self.seed & 0xFFFFFFFFFFFFFFFF, self.zstretch,
                  zn.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if zn is not None else None)

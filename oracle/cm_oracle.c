@@ -67,7 +67,7 @@ typedef struct {
     int ndim;            /* 2 or 3 */
     int nx, ny, nz;      /* nodes; ny = 1 in 2D; nz counts both plates */
     int tvd_form;        /* 0: G(r+)+G(r-), 1: G(r+ + r-), 2: no TVD term */
-    int pad_;
+    int split;           /* 0: Eq. time_step as printed; 1: the palindrome of its half steps */
     double aspect;       /* Gamma = L/d */
     double Ra, Pr, gamma, eps, D;
     double cfl;          /* dt = cfl * min h/(|u|+c) */
@@ -83,7 +83,7 @@ typedef struct {
 
 /* derived constants */
 typedef struct {
-    int ndim, nx, ny, nz, tvd_form;
+    int ndim, nx, ny, nz, tvd_form, split;
     size_t n;
     double h[3];         /* dx, dy, dz */
     double a;            /* p = a rho T,        a = (gamma-1)/(gamma eps D) */
@@ -121,6 +121,7 @@ static void derive(const orc_cfg* c, P* p)
     p->ny = (c->ndim == 3) ? c->ny : 1;
     p->nz = c->nz;
     p->tvd_form = c->tvd_form;
+    p->split = c->split;
     p->n = (size_t)p->nx * p->ny * p->nz;
     p->h[0] = c->aspect / c->nx;
     p->h[1] = c->aspect / p->ny;
@@ -709,9 +710,12 @@ double orc_dt(const orc_cfg* c, const double* ext)
 }
 
 /* nsteps full steps of Eq. time_step:
- * X^{n+1} = L_x L_y L_z L_x L_y L_z X^n with every L at dt/2 (rightmost first);
- * dt from the state at the start of each step.  Writes each step's dt to dts
- * (if not NULL) and advances *t. */
+ * X^{n+1} = L_x L_y L_z L_x L_y L_z X^n with every L at dt/2 (rightmost first:
+ * z, y, x, z, y, x; 2D drops y); dt from the state at the start of each step.
+ * cfg->split = 1 applies the same half steps as the palindrome x, y, z, z, y, x
+ * instead (the symmetric ordering a second-order splitting would use; reading
+ * A4 takes the printed one).  Writes each step's dt to dts (if not NULL) and
+ * advances *t. */
 void orc_step(const orc_cfg* c, double* ext, int nsteps, double* t, double* dts)
 {
     P p;
@@ -722,18 +726,18 @@ void orc_step(const orc_cfg* c, double* ext, int nsteps, double* t, double* dts)
     Work w;
     work_alloc(&p, &w);
     to_internal(&p, ext, X);
+    /* sweep directions in the order applied: 0 = x, 1 = y, 2 = z */
+    static const int printed3[6] = {2, 1, 0, 2, 1, 0}, palindrome3[6] = {0, 1, 2, 2, 1, 0};
+    static const int printed2[4] = {2, 0, 2, 0}, palindrome2[4] = {0, 2, 2, 0};
+    const int* order = (p.ndim == 3) ? (p.split ? palindrome3 : printed3) : (p.split ? palindrome2 : printed2);
+    const int nsweeps = (p.ndim == 3) ? 6 : 4;
     for (int s = 0; s < nsteps; s++) {
         double dt = dt_of(&p, X, &w);
         double Delta = 0.5 * dt;
-        for (int half = 0; half < 2; half++) {
-            sweep_z(&p, Delta, X, Y, &w);              /* X -> Y */
-            if (p.ndim == 3) {
-                sweep_h(&p, 1, Delta, Y, X, &w);       /* Y -> X */
-                sweep_h(&p, 0, Delta, X, Y, &w);       /* X -> Y */
-                memcpy(X, Y, 5 * N * sizeof(double));
-            } else {
-                sweep_h(&p, 0, Delta, Y, X, &w);       /* Y -> X */
-            }
+        for (int q = 0; q < nsweeps; q++) {
+            if (order[q] == 2) sweep_z(&p, Delta, X, Y, &w);
+            else sweep_h(&p, order[q], Delta, X, Y, &w);
+            double* tmp = X; X = Y; Y = tmp;   /* the result is in X again */
         }
         if (dts) dts[s] = dt;
         if (t) *t += dt;

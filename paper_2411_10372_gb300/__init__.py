@@ -13,7 +13,7 @@ import ctypes
 import numpy as np
 
 from ._binding import (cm_adj_backward, cm_adj_forward, cm_adj_get_dts, cm_adj_set_dts, CM_ADJ_PHI_EXACT,
-                       CM_ADJ_PHI_FROZEN, cm_batch_diagnostics, cm_batch_finalize, cm_batch_get_state, cm_batch_init,
+                       CM_ADJ_PHI_FROZEN, CM_SPLIT_PRINTED, CM_SPLIT_SYMMETRIC, cm_batch_diagnostics, cm_batch_finalize, cm_batch_get_state, cm_batch_init,
                        cm_batch_launch_count, cm_batch_profile_steps, cm_batch_step, cm_batch_tuning,
                        CM_EBADCKPT, CM_ECUDA, CM_EINVAL, CM_ENAN, CM_ENOMEM, CM_ENOTINIT, CM_EUNSTABLE,
                        CM_FP32, CM_FP64, CM_OK, CM_TVD_DAVIS, CM_TVD_OFF, CM_TVD_SUM, CMError, cm_default_params,

@@ -19,6 +19,7 @@ CM_EUNSTABLE, CM_ENOMEM, CM_EBADCKPT = -7, -8, -9
 CM_FP64, CM_FP32 = 0, 1
 CM_TVD_DAVIS, CM_TVD_SUM, CM_TVD_OFF = 0, 1, 2
 CM_ADJ_PHI_EXACT, CM_ADJ_PHI_FROZEN = 0, 1
+CM_SPLIT_PRINTED, CM_SPLIT_SYMMETRIC = 0, 1
 
 
 class cm_grid(ctypes.Structure):
@@ -33,7 +34,8 @@ class cm_params(ctypes.Structure):
                 ("t_top", ctypes.c_double), ("pert_amp", ctypes.c_double), ("stokes", ctypes.c_double),
                 ("seed", ctypes.c_ulonglong), ("precision", ctypes.c_int), ("tvd_form", ctypes.c_int),
                 ("diag_every", ctypes.c_int), ("diag_capacity", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("state_buf", ctypes.c_void_p), ("adj_limiter", ctypes.c_int), ("layout_exact", ctypes.c_int)]
+                ("state_buf", ctypes.c_void_p), ("adj_limiter", ctypes.c_int), ("layout_exact", ctypes.c_int),
+                ("split", ctypes.c_int), ("reserved_", ctypes.c_int)]
 
 
 class cm_diag(ctypes.Structure):

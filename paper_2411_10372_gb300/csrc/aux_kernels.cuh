@@ -184,7 +184,6 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
 {
     const int k = blockIdx.x;
     const double z = A.zt[k];
-    const long long plane = (long long)C.nx * C.ny;
     const long long fs = C.fstride;
     double v[kDiagQ] = {0, 0, 0, 0, 0, 0, 0, 0};
     // FP32 states: per-thread compensated (Kahan) FP32 sums of the FP32
@@ -197,9 +196,10 @@ __global__ void __launch_bounds__(kDiagThreads) diag_planes(const R* X, Coef<R> 
     float kc[kDiagQ - 1] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float mach32 = 0.f;
     int bad = 0;
-    for (long long n = threadIdx.x; n < plane; n += kDiagThreads) {
-        const int i = (int)(n % C.nx);
-        const int j = (int)(n / C.nx);
+    // node (j, i) of the plane: rows j, columns i strided by the block (no
+    // division per node)
+    for (int j = 0; j < C.ny; ++j)
+    for (int i = threadIdx.x; i < C.nx; i += kDiagThreads) {
         const R* p = X + ((size_t)k * C.ny + j) * C.pitch + i;
         if constexpr (!kExact<R>) {
             const float rho = p[0], ri = 1.f / rho;

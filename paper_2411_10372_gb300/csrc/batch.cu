@@ -151,7 +151,9 @@ int launch(Batch& B, int dir, int first, int last, double Delta)
 int queue_steps(Batch& B, int n)
 {
     for (int s = 0; s < n; ++s) {
-        const int order[4] = {2, 0, 2, 0};  // z, x, z, x (Eq. time_step, rightmost operator first)
+        // z, x, z, x (Eq. time_step, rightmost operator first), or its palindrome x, z, z, x
+        static const int printed[4] = {2, 0, 2, 0}, symmetric[4] = {0, 2, 2, 0};
+        const int* order = B.prm.split == CM_SPLIT_SYMMETRIC ? symmetric : printed;
         for (int q = 0; q < 4; ++q) {
             int rc = launch(B, order[q], q == 0, q == 3, 0.0);
             if (rc) return rc;
@@ -264,6 +266,8 @@ int cm_batch_init(int nbox, const cm_grid* grids, const double* Ra, double Pr, d
     else cm_default_params(&P);
     if (P.precision != CM_FP32) return set_error(CM_EINVAL, "cm_batch_init: the batch steps FP32 states");
     if (P.layout_exact != 0 && P.layout_exact != 1) return set_error(CM_EINVAL, "cm_batch_init: layout_exact must be 0 or 1");
+    if (P.split != CM_SPLIT_PRINTED && P.split != CM_SPLIT_SYMMETRIC)
+        return set_error(CM_EINVAL, "cm_batch_init: split must be CM_SPLIT_PRINTED or CM_SPLIT_SYMMETRIC");
     if (!(Pr > 0) || !(gamma > 1) || !(P.eps > 0) || !(P.D > 0) || !(P.cfl > 0) || P.cfl > 1.0)
         return set_error(CM_EINVAL, "cm_batch_init: bad physical parameters");
     for (int b = 0; b < nbox; ++b) {

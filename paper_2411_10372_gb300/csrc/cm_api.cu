@@ -434,10 +434,14 @@ int sweeps_per_step(const Ctx* c) { return c->grid.ndim == 3 ? 6 : 4; }
 int queue_steps(Ctx* c, int n, cudaEvent_t* ev = nullptr, void* flush = nullptr, size_t flush_bytes = 0,
                 bool per_sweep = true)
 {
-    static const int order2[4] = {2, 0, 2, 0};
-    static const int order3[6] = {2, 1, 0, 2, 1, 0};
+    // sweep directions in the order applied (Eq. time_step, rightmost first;
+    // CM_SPLIT_SYMMETRIC: the palindrome); the last is always L_x, which
+    // reduces the next dt
+    static const int printed2[4] = {2, 0, 2, 0}, symmetric2[4] = {0, 2, 2, 0};
+    static const int printed3[6] = {2, 1, 0, 2, 1, 0}, symmetric3[6] = {0, 1, 2, 2, 1, 0};
     const int S = sweeps_per_step(c);
-    const int* order = S == 6 ? order3 : order2;
+    const bool sym = c->prm.split == CM_SPLIT_SYMMETRIC;
+    const int* order = S == 6 ? (sym ? symmetric3 : printed3) : (sym ? symmetric2 : printed2);
     for (int s = 0; s < n; ++s) {
         const int slot = (int)(c->step & 1);
         SweepCtl sc;
@@ -606,6 +610,8 @@ int cm_init(const cm_grid* grid, double Ra, double Pr, double gamma, const cm_pa
     if (P.adj_limiter != CM_ADJ_PHI_EXACT && P.adj_limiter != CM_ADJ_PHI_FROZEN)
         return fail(CM_EINVAL, "adj_limiter must be CM_ADJ_PHI_EXACT or CM_ADJ_PHI_FROZEN");
     if (P.layout_exact != 0 && P.layout_exact != 1) return fail(CM_EINVAL, "layout_exact must be 0 or 1");
+    if (P.split != CM_SPLIT_PRINTED && P.split != CM_SPLIT_SYMMETRIC)
+        return fail(CM_EINVAL, "split must be CM_SPLIT_PRINTED or CM_SPLIT_SYMMETRIC");
     if (P.diag_capacity < 1) P.diag_capacity = 1024;
     if (P.state_buf && ((uintptr_t)P.state_buf & 255)) return fail(CM_EINVAL, "state_buf must be 256-byte aligned");
     std::vector<double> planes;
@@ -1373,6 +1379,7 @@ int cm_adj_forward(int nsteps, int K, int win_begin, double* J)
     NEED_CTX();
     Ctx* c = g_ctx;
     if (c->prec != CM_FP64 || c->grid.ndim != 2) return fail(CM_EINVAL, "the adjoint needs a 2D FP64 context");
+    if (c->prm.split != CM_SPLIT_PRINTED) return fail(CM_EINVAL, "the adjoint needs split = CM_SPLIT_PRINTED");
     if (nsteps < 1 || K < 0 || win_begin < 1 || win_begin > nsteps)
         return fail(CM_EINVAL, "need nsteps >= 1, K >= 0, 1 <= win_begin <= nsteps");
     if (!c->adj) c->adj = new AdjCtx();

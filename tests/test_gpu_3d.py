@@ -178,12 +178,14 @@ def _nullcontext():
     return contextlib.nullcontext()
 
 
+@pytest.mark.parametrize("split", [0, 1])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
-def test_steps_3d(precision, tol):
+def test_steps_3d(precision, tol, split):
     """40 full steps with the CFL dt from the device reduction, from the
-    seeded initial state of the 3D workload recipe."""
-    cfg = O.Config(nx=40, ny=24, nz=17, ndim=3, Ra=1e6, seed=2024, pert_amp=1e-2)
-    s = solver_for(cfg, precision)
+    seeded initial state of the 3D workload recipe; split 1: the palindrome
+    x, y, z, z, y, x of the half steps (cm_params.split)."""
+    cfg = O.Config(nx=40, ny=24, nz=17, ndim=3, Ra=1e6, seed=2024, pert_amp=1e-2, split=split)
+    s = solver_for(cfg, precision, split=split)
     try:
         s.step(40)
         got = s.state()

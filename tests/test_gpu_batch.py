@@ -60,22 +60,25 @@ def test_batch_boxes_equal_their_solo_runs():
             assert abs(diags[b][k] - d[k]) <= 1e-5 * abs(d[k]), (b, k)
 
 
-def test_layout_exact_batch_boxes_equal_their_solo_runs_bit_for_bit():
+@pytest.mark.parametrize("split", [0, 1])
+def test_layout_exact_batch_boxes_equal_their_solo_runs_bit_for_bit(split):
     """With cm_params.layout_exact = 1 the FP32 sweeps round alike whatever
     the segment split, so every box of the batch (its own segment lengths
     from the batch tuner, its own kernels) equals its single-box run bit for
-    bit, time and dt included."""
+    bit, time and dt included; in either order of the half steps
+    (cm_params.split)."""
     import paper_2411_10372_gb300 as cm
     nsteps = 63
     p = _params(cm)
     p.layout_exact = 1
+    p.split = split
     cm.cm_batch_init(_grids(cm), RAS, 1.0, 5.0 / 3.0, p)
     cm.cm_batch_step(nsteps)
     diags = cm.cm_batch_diagnostics()
     batch_states = [cm.cm_batch_get_state(b, np.empty((4, nz, nx))) for b, (nx, nz) in enumerate(SIZES)]
     cm.cm_batch_finalize()
     for b, (nx, nz) in enumerate(SIZES):
-        s = cm.Solver(nx, nz, RAS[b], 1.0, 5.0 / 3.0, precision="fp32", seed=777 + b, layout_exact=1)
+        s = cm.Solver(nx, nz, RAS[b], 1.0, 5.0 / 3.0, precision="fp32", seed=777 + b, layout_exact=1, split=split)
         s.step(nsteps)
         solo = s.state()
         d = s.sample()
@@ -84,17 +87,20 @@ def test_layout_exact_batch_boxes_equal_their_solo_runs_bit_for_bit():
         assert diags[b]["t"] == d["t"] and diags[b]["dt"] == d["dt"]
 
 
-def test_batch_box_matches_oracle():
+@pytest.mark.parametrize("split", [0, 1])
+def test_batch_box_matches_oracle(split):
     import paper_2411_10372_gb300 as cm
     nsteps = 40
-    cm.cm_batch_init(_grids(cm), RAS, 1.0, 5.0 / 3.0, _params(cm, seed=5))
+    p = _params(cm, seed=5)
+    p.split = split
+    cm.cm_batch_init(_grids(cm), RAS, 1.0, 5.0 / 3.0, p)
     cm.cm_batch_step(nsteps)
     b = 3
     nx, nz = SIZES[b]
     got = cm.cm_batch_get_state(b, np.empty((4, nz, nx)))
     masses = [d["mass"] for d in cm.cm_batch_diagnostics()]
     cm.cm_batch_finalize()
-    cfg = O.Config(nx=nx, nz=nz, Ra=RAS[b], seed=5 + b)
+    cfg = O.Config(nx=nx, nz=nz, Ra=RAS[b], seed=5 + b, split=split)
     want, _, _ = O.step(cfg, O.init(cfg), nsteps)
     rel = lambda a, w: float(np.linalg.norm(a - w) / np.linalg.norm(w))
     assert rel(got[0], want[0]) <= 1e-5 and rel(got[3], want[3]) <= 1e-5

@@ -478,3 +478,54 @@ def test_profiles_match_plane_means_of_the_oracle_state():
             "mach_max": (np.sqrt(u2) / np.sqrt(cfg.gamma * cl["a"] * T)).max(1)}
     for k, w in want.items():
         assert np.max(np.abs(got[k] - w)) <= 1e-12 * max(np.max(np.abs(w)), 1e-3), k
+
+
+def test_symmetric_split_matches_oracle():
+    """cm_params.split = CM_SPLIT_SYMMETRIC (the palindrome x, z, z, x of the
+    half steps of Eq. time_step; reading A4 keeps the printed order by
+    default): FP64, 300 steps of the 256 x 64, Ra = 1e6 workload equal the
+    oracle's split = 1 run bit for bit, with t; FP32, 100 steps within the
+    FP32 bars of test_fp32_100_steps; the printed order gives another state."""
+    import paper_2411_10372_gb300 as cm
+    cfg = O.Config(split=1)
+    X0 = O.init(cfg)
+    want, t_cpu, _ = O.step(cfg, X0, 300)
+    s = solver_for(cfg, split=cm.CM_SPLIT_SYMMETRIC)
+    try:
+        s.step(300)
+        got = s.state()
+        t_gpu, steps = s.time()
+    finally:
+        s.close()
+    assert steps == 300 and abs(t_gpu - t_cpu) <= 1e-12 * t_cpu
+    assert np.array_equal(got, want), [float(np.max(np.abs(got[f] - want[f]))) for f in range(4)]
+    printed, _, _ = O.step(O.Config(), X0, 300)
+    assert not np.array_equal(printed, want)
+
+    want100, _, _ = O.step(cfg, X0, 100)
+    s = solver_for(cfg, "fp32", split=cm.CM_SPLIT_SYMMETRIC)
+    try:
+        s.step(100)
+        got = s.state()
+    finally:
+        s.close()
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    scale = np.linalg.norm(want100[0]) * math.sqrt(cfg.gamma * cl["a"])
+    assert rel_l2(got[0], want100[0]) <= 1e-5 and rel_l2(got[3], want100[3]) <= 1e-5
+    for f in (1, 2):
+        assert float(np.linalg.norm(got[f] - want100[f])) / scale <= 1e-5, f
+
+
+def test_split_switch_is_validated_and_the_adjoint_refuses_symmetric():
+    import paper_2411_10372_gb300 as cm
+    cfg = O.Config(nx=64, nz=17)
+    with pytest.raises(cm.CMError) as e:
+        solver_for(cfg, split=2)
+    assert e.value.code == cm.CM_EINVAL
+    s = solver_for(cfg, split=cm.CM_SPLIT_SYMMETRIC)
+    try:
+        with pytest.raises(cm.CMError) as e:
+            cm.cm_adj_forward(10, 5, 6)
+        assert e.value.code == cm.CM_EINVAL
+    finally:
+        s.close()

@@ -39,8 +39,9 @@ MUTANTS = [
     ("tvd_rminus_index", "dp[c] = X[c * N + n2] - X[c * N + n1];", "dp[c] = X[c * N + n0] - X[c * N + nm];"),
     ("courant_full_dt", "double Co = Delta * fmax(A[n0], A[n1]) / h;",
      "double Co = 2.0 * Delta * fmax(A[n0], A[n1]) / h;"),
-    ("split_order_x_first", "sweep_z(&p, Delta, X, Y, &w);              /* X -> Y */",
-     "sweep_h(&p, 0, Delta, X, Y, &w);"),
+    ("split_order_x_first", "printed2[4] = {2, 0, 2, 0}", "printed2[4] = {0, 2, 0, 2}"),
+    ("split_palindrome_is_printed_order", "palindrome2[4] = {0, 2, 2, 0}", "palindrome2[4] = {2, 0, 2, 0}"),
+    ("split_3d_order_y_last", "printed3[6] = {2, 1, 0, 2, 1, 0}", "printed3[6] = {2, 0, 1, 2, 0, 1}"),
     ("limiter_phi_no_factor2", "fmin(2.0 * r, 1.0)", "fmin(r, 1.0)"),
     ("nu_conv_coefficient", "out[1] = sRP / p.eps * (s_conv / vol);", "out[1] = sRP * (s_conv / vol);"),
     ("nu_k_coefficient", "out[2] = p.D * sRP / 2.0 * (s_k / vol);", "out[2] = p.D * sRP * (s_k / vol);"),

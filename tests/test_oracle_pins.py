@@ -1089,7 +1089,10 @@ def test_splitting_order_and_temporal_convergence():
     MacCormack step carries a time error of order dt h^2 of its own (its
     second-order time term uses the discrete spatial operator), which here
     outweighs the splitting error, so the order measured at fixed h does not
-    tell the two splittings apart."""
+    tell the two splittings apart.  The oracle's split = 1 (the palindrome
+    x, z, z, x of the same half steps) is that symmetric sequence bit for
+    bit; in 3D the printed step is z, y, x, z, y, x and split = 1 is
+    x, y, z, z, y, x, bit for bit."""
     base = O.Config(nx=48, nz=17, Ra=1e4, tvd_form=O.TVD_OFF)
     X0 = _smooth_state(base)
     dt0 = 0.4 * O.dt(base, X0)
@@ -1103,13 +1106,22 @@ def test_splitting_order_and_temporal_convergence():
     cfg = O.Config(nx=48, nz=17, Ra=1e4, tvd_form=O.TVD_OFF, dt_fixed=dt0)
     A, _, _ = O.step(cfg, X0, 3)
     assert np.array_equal(A, compose(cfg, X0, dt0, 3, (2, 0, 2, 0)))
+    cfg_s = O.Config(nx=48, nz=17, Ra=1e4, tvd_form=O.TVD_SPLIT, dt_fixed=dt0, split=1)
+    A, _, _ = O.step(cfg_s, X0, 3)
+    assert np.array_equal(A, compose(cfg_s, X0, dt0, 3, (0, 2, 2, 0)))
+    assert not np.array_equal(A, O.step(O.Config(nx=48, nz=17, Ra=1e4, tvd_form=O.TVD_SPLIT, dt_fixed=dt0), X0, 3)[0])
+    for split, order in ((0, (2, 1, 0, 2, 1, 0)), (1, (0, 1, 2, 2, 1, 0))):
+        cfg3 = O.Config(nx=12, ny=10, nz=9, ndim=3, Ra=1e4, dt_fixed=1e-4, split=split, pert_amp=0.05)
+        X3 = O.init(cfg3)
+        A3, _, _ = O.step(cfg3, X3, 2)
+        assert np.array_equal(A3, compose(cfg3, X3, 1e-4, 2, order)), split
     for tvd in (O.TVD_OFF, O.TVD_SPLIT):
         runs = {"literal": [], "symmetric": []}
         for r in range(5):
             c = O.Config(nx=48, nz=17, Ra=1e4, tvd_form=tvd, dt_fixed=dt0 / 2 ** r)
             runs["literal"].append(O.step(c, X0, 16 * 2 ** r)[0])
-            if tvd == O.TVD_OFF:
-                runs["symmetric"].append(compose(c, X0, dt0 / 2 ** r, 16 * 2 ** r, (2, 0, 0, 2)))
+            c.split = 1
+            runs["symmetric"].append(O.step(c, X0, 16 * 2 ** r)[0])
         for name, sols in runs.items():
             if not sols:
                 continue
