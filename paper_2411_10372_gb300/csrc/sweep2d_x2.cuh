@@ -89,9 +89,50 @@ __device__ __forceinline__ float fmax_nan(float a, float b)
     return r;
 }
 
+// Delta of a sweep (dt/2 from the step's dt slot, or the single-sweep
+// Delta) in FP32, with two FP64 multiplies and one conversion: equal to
+// (float)Delta of the FP64 rule.  FP64 issues at a small fraction of the
+// FP32 rate on this GPU and every thread of a sweep needs this value at its
+// start, where an FP64 division per thread held the warps back at each
+// launch.
+__device__ __forceinline__ float sweep_delta_f32(const SweepCtl& sc, const Coef<float>& C)
+{
+    if (sc.Delta > 0.0) return (float)sc.Delta;
+    if (C.dt_fixed > 0.0) return (float)(0.5 * C.dt_fixed);
+    return (float)(0.5 * (C.cfl * __longlong_as_double((long long)sc.ctl->dt_slot[sc.slot_in])));
+}
+
+// the step's advance of t and the step counter, and the reset of the other
+// dt slot, by one thread in the first sweep of a step (FP64)
+__device__ __forceinline__ void step_bookkeeping(const SweepCtl& sc, const Coef<float>& C)
+{
+    sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
+    sc.ctl->t += step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
+    sc.ctl->steps += 1.0;
+}
+
 __device__ __forceinline__ f2 abs2(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
 __device__ __forceinline__ f2 sqrt2(f2 a) { return make_float2(sqrt_fast(a.x), sqrt_fast(a.y)); }
+// next dt from the FP32 sweeps: the block's maximum of r = max (|u|+c)/h
+// over its nodes (NaN-propagating), then one thread stores 1/r in FP64 into
+// the dt slot; 1/r is monotone, so this is the minimum of h/(|u|+c) over the
+// nodes.  A non-finite maximum sets the sticky status instead.  Every thread
+// of the block calls it.
+__device__ __forceinline__ void block_rmax_dt(float r, DevCtl* ctl, int slot)
+{
+    __shared__ float sm[32];
+    for (int o = 16; o > 0; o >>= 1) r = fmax_nan(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = sm[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax_nan(m, sm[i]);
+        if (!(m < 1e30f)) atomicOr(&ctl->status, 1);
+        else if (m > 0.f) atomicMin(&ctl->dt_slot[slot], (unsigned long long)__double_as_longlong(1.0 / (double)m));
+    }
+}
+
 // TVD coefficient G of the flux G dX, both columns at once:
 //   C = c(1 - c), c = min(Co, 1/2);  phi(s) = clamp(2 s / dd, 0, 1)
 //   Davis form: G = C (2 - phi(sp) - phi(sm)) / 2;  printed form: C (1 - phi(sp + sm)) / 2

@@ -184,20 +184,15 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
     const bool own = lane >= 1 && lane <= 30 && i < nx && w >= 2 && w < kNW3p - 2 && cw >= 0 && cw < io.nw;
     const bool passthru = (AL == 1) && (cwr == 0 || cwr == nz - 1);  // L_y leaves the plate planes unchanged
 
-    const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
-    const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
-    const float lamf = (float)(Delta / ((AL == 2) ? C.dz : C.dy));
+    const float Df = sweep_delta_f32(sc, C);  // Delta = dt/2
+    const float lamf = Df * ((AL == 2) ? C.inv_dz : C.inv_dy);
     const f2 lam = bc(lamf), hlam = bc(0.5f * lamf), lam2 = bc(2.f * lamf);
-    const f2 mDg = bc(-(float)Delta * C.g);  // Delta times the source per unit density (L_z)
+    const f2 mDg = bc(-Df * C.g);  // Delta times the source per unit density (L_z)
     const f2 half = bc(0.5f), z0 = bc(0.f);
     const f2 ia = bc((AL == 2) ? C.inv_dz : C.inv_dy), i2dx = bc(C.inv_2dx);
     const f2 i2dw = bc((WD == 1) ? C.inv_2dy : C.inv_2dz);
 
-    if (sc.first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
-        sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
-        sc.ctl->t += dt;
-        sc.ctl->steps += 1.0;
-    }
+    if (sc.first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) step_bookkeeping(sc, C);
 
     // memory offset of march row j of this warp's W row
     auto row_off = [&](int j) -> int {
@@ -407,16 +402,10 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
     const bool own = lane >= 1 && lane <= 30 && i < nx && w >= 2 && w < kNW3p - 2 && cw < ny;
     const bool want_dt = sc.last != 0;
 
-    const double dt = step_dt(sc.ctl, sc.slot_in, C.cfl, C.dt_fixed);
-    const double Delta = sc.Delta > 0.0 ? sc.Delta : 0.5 * dt;
-    const float lamf = (float)(Delta / C.dx);
+    const float lamf = sweep_delta_f32(sc, C) * C.inv_dx;  // Delta / dx, Delta = dt/2
     const f2 lam = bc(lamf), hlam = bc(0.5f * lamf), half = bc(0.5f), z0 = bc(0.f);
     const f2 idx_ = bc(C.inv_dx), i2dy = bc(C.inv_2dy), i2dz = bc(C.inv_2dz);
-    if (sc.first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
-        sc.ctl->dt_slot[sc.slot_in ^ 1] = 0x7FF0000000000000ULL;
-        sc.ctl->t += dt;
-        sc.ctl->steps += 1.0;
-    }
+    if (sc.first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) step_bookkeeping(sc, C);
     auto row_off = [&](int k) -> int { return (min(max(k, 0), nz - 1) * ny + cwr) * pitch + ic; };
     auto gz_of = [&](int k) -> f2 { return bc(-C.g * io.zt[min(max(k, 0), nz - 1)]); };
 
@@ -563,7 +552,7 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
     cp_async_drain();
     if (want_dt) {
         const float r = fmax_nan(fmax_nan(ax * C.inv_dx, ay * C.inv_dy), az * C.inv_dz);
-        block_dt_reduce(r > 0.f ? 1.0 / (double)r : 1e308, !(r < 1e30f), sc.ctl, sc.slot_in ^ 1);
+        block_rmax_dt(r, sc.ctl, sc.slot_in ^ 1);
     }
 }
 
