@@ -68,19 +68,34 @@ static cudaError_t sweep3_x2_nw(int dir, const float* in, float* out, const floa
     io.nw = (dir == 1) ? C.nz : C.ny;
     const int groups = (io.nw + NW - 5) / (NW - 4);
     constexpr size_t ring = ring3_bytes(NW);
+    // stretched grids: the block's plane cache after the ring (4 values per
+    // plane for L_z, 2 for L_x, none for L_y), sized for the longest segment
+    constexpr int kSegMax = 256;
     static bool attr = false;
     if (!attr) {
+        const int ring_z = (int)(ring + plane_cache_bytes<float>(kSegMax, 4));
+        const int ring_x = (int)(ring + plane_cache_bytes<float>(kSegMax, 2));
         cudaFuncSetAttribute(sweep3d_march_x2<2, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
         cudaFuncSetAttribute(sweep3d_march_x2<1, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
         cudaFuncSetAttribute(sweep3d_x_x2<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+        cudaFuncSetAttribute(sweep3d_march_x2<2, NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ring_z);
+        cudaFuncSetAttribute(sweep3d_march_x2<1, NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring);
+        cudaFuncSetAttribute(sweep3d_x_x2<NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ring_x);
         attr = true;
     }
     if (dir < 0 || dir > 2) return cudaErrorInvalidValue;
     io.seg = (seg_rows > 0 && !getenv("CM_SEG_ROWS"))
                  ? seg_rows
                  : pick_segment3((long long)io.nstrips * groups, io.nmarch, 1, sm_count());
+    if (C.zp && io.seg > kSegMax) io.seg = kSegMax;
     const int nsegs = (io.nmarch + io.seg - 1) / io.seg;
     const dim3 grid(io.nstrips, groups, nsegs), b(NW * 32);
+    if (C.zp) {
+        const size_t ring_z = ring + plane_cache_bytes<float>(io.seg, 4), ring_x = ring + plane_cache_bytes<float>(io.seg, 2);
+        if (dir == 2) return launch_pdl(false, sweep3d_march_x2<2, NW, true>, grid, b, ring_z, s, io, C, sc);
+        if (dir == 1) return launch_pdl(false, sweep3d_march_x2<1, NW, true>, grid, b, ring, s, io, C, sc);
+        return launch_pdl(false, sweep3d_x_x2<NW, true>, grid, b, ring_x, s, io, C, sc);
+    }
     if (dir == 2) return launch_pdl(false, sweep3d_march_x2<2, NW>, grid, b, ring, s, io, C, sc);
     if (dir == 1) return launch_pdl(false, sweep3d_march_x2<1, NW>, grid, b, ring, s, io, C, sc);
     return launch_pdl(false, sweep3d_x_x2<NW>, grid, b, ring, s, io, C, sc);

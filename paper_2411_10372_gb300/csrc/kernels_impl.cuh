@@ -175,7 +175,7 @@ cudaError_t Launch<R>::sweep(int dir, const R* in, R* out, const R* zt, const Co
 {
     if (C.ndim == 3) {
         if constexpr (std::is_same<R, float>::value) {
-            if (C.nx % 2 == 0 && !C.zp && !getenv("CM_3D_SCALAR") && (long long)C.fstride * 5 < (1LL << 31))
+            if (C.nx % 2 == 0 && !getenv("CM_3D_SCALAR") && (long long)C.fstride * 5 < (1LL << 31))
                 return launch_sweep3_x2(dir, in, out, zt, C, sc, seg_rows, s);
         }
         return sweep3(dir, in, out, zt, C, sc, seg_rows, s);

@@ -158,7 +158,7 @@ __device__ __forceinline__ P5 flux5(const P5& q, const f2 (&u)[3], f2 p, const f
 // across (j-2, j-1) from the input state; output row j-2; H_{j-1}.  Plates:
 // for L_z at the ends of the march (half-cell density, m = 0, T = T_w); for
 // L_y the plate planes are W rows that pass through unchanged.
-template <int AL, int kNW3p>
+template <int AL, int kNW3p, bool ST = false>
 __global__ void __launch_bounds__(kNW3p * 32, 1)
 sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 {
@@ -190,7 +190,16 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
     const f2 mDg = bc(-Df * C.g);  // Delta times the source per unit density (L_z)
     const f2 half = bc(0.5f), z0 = bc(0.f);
     const f2 ia = bc((AL == 2) ? C.inv_dz : C.inv_dy), i2dx = bc(C.inv_2dx);
-    const f2 i2dw = bc((WD == 1) ? C.inv_2dy : C.inv_2dz);
+    // across W: uniform y (L_z); for L_y on a stretched grid the central span
+    // of the warp's own plane
+    const f2 i2dw = bc((WD == 1) ? C.inv_2dy : (ST ? C.zp[min(max(cw, 0), nz - 1)].isc : C.inv_2dz));
+    // stretched L_z: plate half cells Delta / w (predictor) and Delta / (2 w) (average)
+    f2 lam_bot = lam2, lam_top = lam2, hlam_bot = lam;
+    if constexpr (ST && AL == 2) {
+        lam_bot = bc(Df * C.zp[0].iw);
+        lam_top = bc(Df * C.zp[nz - 1].iw);
+        hlam_bot = bc(0.5f * Df * C.zp[0].iw);
+    }
 
     if (sc.first && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) step_bookkeeping(sc, C);
 
@@ -207,6 +216,11 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
     };
 
     const Ring5<kNW3p * 32> ring{ring3_mem + threadIdx.x};
+    // stretched L_z: the block's plane cache after the ring, {1/hp, 1/w, rp, rm}
+    // of planes ks - 4 .. ke (clamped); every warp marches the same rows
+    float* pz = reinterpret_cast<float*>(ring3_mem + ring3_bytes(kNW3p) / sizeof(f2));
+    if constexpr (ST && AL == 2) fill_planes<float, 4>(pz, C, ks, ke, true);
+    auto pl = [&](int k, int q) -> float { return pz[(k - (ks - kPlaneBack)) * 4 + q]; };
     const int j0 = ks - 2;  // first step; the first stored row is ks, at step ks + 2
     for (int q = 0; q < kRing3 - 1; ++q) ring.request(q, io.in + row_off(j0 + q), fs);
 
@@ -239,29 +253,36 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
         const int m = j - 1;
         P5 XP1 = Xm1, F1 = p5_zero();
         f2 pp1[3] = {u1[0], u1[1], u1[2]}, ppT1 = T1, ppp1 = p1;
+        // stretched L_z: 1/(spacing above m), 1/(spacing below m), Delta / w_m
+        f2 ia_f = ia, ia_b = ia, lam_m = lam;
+        if constexpr (ST && AL == 2) {
+            ia_f = bc(pl(m, 0));
+            ia_b = bc(pl(m - 1, 0));
+            lam_m = bc(Df * pl(m, 1));
+        }
         if (role >= 1) {
             f2 g[3], ca[3], cb[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) g[c] = mul2f(sub2f(u0[c], u1[c]), ia);
+            for (int c = 0; c < 3; ++c) g[c] = mul2f(sub2f(u0[c], u1[c]), ia_f);
             ca[0] = mul2f(sub2f(right_of(u1[AL]), left_of(u1[AL])), i2dx);
             cb[0] = mul2f(sub2f(right_of(u1[0]), left_of(u1[0])), i2dx);
             ca[WD] = dwa1;
             cb[WD] = dww1;
             ca[AL] = cb[AL] = z0;
-            F1 = flux5<AL>(Xm1, u1, p1, g, mul2f(sub2f(T0, T1), ia), ca, cb, C);
+            F1 = flux5<AL>(Xm1, u1, p1, g, mul2f(sub2f(T0, T1), ia_f), ca, cb, C);
             if (AL == 2) {
                 if (m >= 1 && m <= nz - 2) {
-                    XP1.r = fnma2f(lam, sub2f(F1.r, F2.r), Xm1.r);
+                    XP1.r = fnma2f(lam_m, sub2f(F1.r, F2.r), Xm1.r);
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) XP1.m[c] = fnma2f(lam, sub2f(F1.m[c], F2.m[c]), Xm1.m[c]);
+                    for (int c = 0; c < 3; ++c) XP1.m[c] = fnma2f(lam_m, sub2f(F1.m[c], F2.m[c]), Xm1.m[c]);
                     XP1.m[2] = fma2f(mDg, Xm1.r, XP1.m[2]);
-                    XP1.E = fnma2f(lam, sub2f(F1.E, F2.E), Xm1.E);
+                    XP1.E = fnma2f(lam_m, sub2f(F1.E, F2.E), Xm1.E);
                 } else if (m <= 0) {
-                    XP1.r = fnma2f(lam2, F1.r, Xm1.r);
+                    XP1.r = fnma2f(lam_bot, F1.r, Xm1.r);
                     XP1.m[0] = XP1.m[1] = XP1.m[2] = z0;
                     XP1.E = mul2f(XP1.r, bc(C.ebot));
                 } else {
-                    XP1.r = fma2f(lam2, F2.r, Xm1.r);
+                    XP1.r = fma2f(lam_top, F2.r, Xm1.r);
                     XP1.m[0] = XP1.m[1] = XP1.m[2] = z0;
                     XP1.E = mul2f(XP1.r, bc(C.etop));
                 }
@@ -292,13 +313,13 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
             // F^P at row m (backward along the march)
             f2 g[3], ca[3], cb[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) g[c] = mul2f(sub2f(pp1[c], pp2[c]), ia);
+            for (int c = 0; c < 3; ++c) g[c] = mul2f(sub2f(pp1[c], pp2[c]), ia_b);
             ca[0] = mul2f(sub2f(right_of(pp1[AL]), left_of(pp1[AL])), i2dx);
             cb[0] = mul2f(sub2f(right_of(pp1[0]), left_of(pp1[0])), i2dx);
             ca[WD] = mul2f(sub2f(buf[2][wu][lane], buf[2][wd][lane]), i2dw);
             cb[WD] = mul2f(sub2f(buf[3][wu][lane], buf[3][wd][lane]), i2dw);
             ca[AL] = cb[AL] = z0;
-            const P5 FP1 = flux5<AL>(XP1, pp1, ppp1, g, mul2f(sub2f(ppT1, ppT2), ia), ca, cb, C);
+            const P5 FP1 = flux5<AL>(XP1, pp1, ppp1, g, mul2f(sub2f(ppT1, ppT2), ia_b), ca, cb, C);
 
             // TVD flux across (c, m), c = j-2, from the input state
             const int c = j - 2;
@@ -307,7 +328,9 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
             ss1 = p5_dot(d1, d0);
             P5 Dn = p5_zero();
             const bool tvd_on = (AL == 2) ? (c >= 1 && c <= nz - 3) : !passthru;
-            if (tvd_on) Dn = p5_scale(tvd_G2f(ss2, ss1, dd1, mul2f(lam, max2(A2, A1)), C.tvd_form), d1);
+            // Courant number of interface (c, c+1): Delta over its spacing
+            const f2 lamh_c = (ST && AL == 2) ? bc(Df * pl(c, 0)) : lam;
+            if (tvd_on) Dn = p5_scale(tvd_G2f(ss2, ss1, dd1, mul2f(lamh_c, max2(A2, A1)), C.tvd_form), d1);
             d1 = d0;
 
             // output row c
@@ -315,13 +338,23 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
                 P5 Xn;
                 const bool interior = (AL == 2) ? (c >= 1 && c <= nz - 2) : !passthru;
                 if (interior) {
-                    Xn.r = add2f(fnma2f(hlam, sub2f(FP1.r, FP2.r), H.r), Dn.r);
+                    if constexpr (ST && AL == 2) {
+                        // Delta / (2 w_c) on the corrector's difference; the TVD flux
+                        // through (c, c+1) weighted by its spacing over w_c
+                        const f2 hl = bc(0.5f * Df * pl(c, 1)), rp = bc(pl(c, 2));
+                        Xn.r = fma2f(rp, Dn.r, fnma2f(hl, sub2f(FP1.r, FP2.r), H.r));
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) Xn.m[q] = add2f(fnma2f(hlam, sub2f(FP1.m[q], FP2.m[q]), H.m[q]), Dn.m[q]);
-                    Xn.E = add2f(fnma2f(hlam, sub2f(FP1.E, FP2.E), H.E), Dn.E);
+                        for (int q = 0; q < 3; ++q) Xn.m[q] = fma2f(rp, Dn.m[q], fnma2f(hl, sub2f(FP1.m[q], FP2.m[q]), H.m[q]));
+                        Xn.E = fma2f(rp, Dn.E, fnma2f(hl, sub2f(FP1.E, FP2.E), H.E));
+                    } else {
+                        Xn.r = add2f(fnma2f(hlam, sub2f(FP1.r, FP2.r), H.r), Dn.r);
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) Xn.m[q] = add2f(fnma2f(hlam, sub2f(FP1.m[q], FP2.m[q]), H.m[q]), Dn.m[q]);
+                        Xn.E = add2f(fnma2f(hlam, sub2f(FP1.E, FP2.E), H.E), Dn.E);
+                    }
                 } else if (AL == 2) {
                     // plates: rho = (rho^P + rho^C)/2 with the half-cell corrector
-                    Xn.r = (c == 0) ? fnma2f(lam, FP1.r, H.r) : H.r;
+                    Xn.r = (c == 0) ? fnma2f(hlam_bot, FP1.r, H.r) : H.r;
                     Xn.m[0] = Xn.m[1] = Xn.m[2] = z0;
                     Xn.E = mul2f(Xn.r, bc(c == 0 ? C.ebot : C.etop));
                 } else {
@@ -332,7 +365,15 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
 
             // H of row m for the next step
             const bool interior_m = (AL == 2) ? (m >= 1 && m <= nz - 2) : !passthru;
-            if (interior_m) {
+            if (interior_m && ST && AL == 2) {
+                // the TVD flux through (m-1, m) weighted by its spacing over w_m
+                const f2 rm = bc(pl(m, 3));
+                H.r = fnma2f(rm, Dn.r, mul2f(half, add2f(XP1.r, Xm1.r)));
+                H.m[0] = fnma2f(rm, Dn.m[0], mul2f(half, add2f(XP1.m[0], Xm1.m[0])));
+                H.m[1] = fnma2f(rm, Dn.m[1], mul2f(half, add2f(XP1.m[1], Xm1.m[1])));
+                H.m[2] = fnma2f(rm, Dn.m[2], mul2f(half, fma2f(mDg, XP1.r, add2f(XP1.m[2], Xm1.m[2]))));
+                H.E = fnma2f(rm, Dn.E, mul2f(half, add2f(XP1.E, Xm1.E)));
+            } else if (interior_m) {
                 H.r = sub2f(mul2f(half, add2f(XP1.r, Xm1.r)), Dn.r);
                 H.m[0] = sub2f(mul2f(half, add2f(XP1.m[0], Xm1.m[0])), Dn.m[0]);
                 H.m[1] = sub2f(mul2f(half, add2f(XP1.m[1], Xm1.m[1])), Dn.m[1]);
@@ -379,7 +420,7 @@ sweep3d_march_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, Swee
 // j-3; d/dy from the exchange of row j-2) and X_new_c = K_c - (lambda/2)
 // (F^P_{i+1} - F^P_i).  The last sweep of a step (sc.last) also reduces the
 // next dt from the stored nodes.
-template <int kNW3p>
+template <int kNW3p, bool ST = false>
 __global__ void __launch_bounds__(kNW3p * 32, 1)
 sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl sc)
 {
@@ -414,6 +455,11 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
     // (equal to the maximum of the per-node products: rounding is monotone)
     float ax = 0.f, ay = 0.f, az = 0.f;
     const Ring5<kNW3p * 32> ring{ring3_mem + threadIdx.x};
+    // stretched grid: the block's plane cache after the ring, {1/(central z
+    // span), 1/(smaller spacing)} of planes ks - 4 .. ke (clamped)
+    float* pz = reinterpret_cast<float*>(ring3_mem + ring3_bytes(kNW3p) / sizeof(f2));
+    if constexpr (ST) fill_planes<float, 2>(pz, C, ks, ke, false);
+    auto pl = [&](int k, int q) -> float { return pz[(k - (ks - kPlaneBack)) * 2 + q]; };
     const int j0 = ks - 2;
     for (int q = 0; q < kRing3 - 1; ++q) ring.request(q, io.in + row_off(j0 + q), fs);
 
@@ -449,8 +495,9 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
                 for (int c = 0; c < 3; ++c) g[c] = mul2f(sub2f(right_of(u1[c]), u1[c]), idx_);
                 ca[1] = dwx1;
                 cb[1] = dwy1;
-                ca[2] = mul2f(sub2f(u0[0], u2x), i2dz);
-                cb[2] = mul2f(sub2f(u0[2], u2z), i2dz);
+                const f2 i2dz_m = ST ? bc(pl(m, 0)) : i2dz;  // 1/(central z span) of plane m
+                ca[2] = mul2f(sub2f(u0[0], u2x), i2dz_m);
+                cb[2] = mul2f(sub2f(u0[2], u2z), i2dz_m);
                 ca[0] = cb[0] = z0;
                 const P5 F1 = flux5<0>(Xm1, u1, p1, g, mul2f(sub2f(right_of(T1), T1), idx_), ca, cb, C);
                 const P5 Fl = p5_left(F1);
@@ -499,8 +546,9 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
                 for (int q = 0; q < 3; ++q) g[q] = mul2f(sub2f(pp2[q], left_of(pp2[q])), idx_);
                 ca[1] = dwpx2;
                 cb[1] = dwpy2;
-                ca[2] = mul2f(sub2f(pp1[0], pp3x), i2dz);
-                cb[2] = mul2f(sub2f(pp1[2], pp3z), i2dz);
+                const f2 i2dz_c = ST ? bc(pl(c, 0)) : i2dz;  // 1/(central z span) of plane c
+                ca[2] = mul2f(sub2f(pp1[0], pp3x), i2dz_c);
+                cb[2] = mul2f(sub2f(pp1[2], pp3z), i2dz_c);
                 ca[0] = cb[0] = z0;
                 const P5 FP = flux5<0>(XP2, pp2, ppp2, g, mul2f(sub2f(ppT2, left_of(ppT2)), idx_), ca, cb, C);
                 const P5 FPr = p5_right(FP);
@@ -518,7 +566,8 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
                 const f2 cs = sqrt2(mul2f(bc(C.cs2), Tn));
                 const float vx = fmax_nan(fabsf(un[0].x) + cs.x, fabsf(un[0].y) + cs.y);
                 const float vy = fmax_nan(fabsf(un[1].x) + cs.x, fabsf(un[1].y) + cs.y);
-                const float vz = fmax_nan(fabsf(un[2].x) + cs.x, fabsf(un[2].y) + cs.y);
+                float vz = fmax_nan(fabsf(un[2].x) + cs.x, fabsf(un[2].y) + cs.y);
+                if constexpr (ST) vz *= pl(c, 1);  // the plane's CFL z step, 1/h_min
                 if (keep) {
                     ax = fmax_nan(ax, vx);
                     ay = fmax_nan(ay, vy);
@@ -551,7 +600,7 @@ sweep3d_x_x2(Sweep3IO<float> io, const __grid_constant__ Coef<float> C, SweepCtl
     }
     cp_async_drain();
     if (want_dt) {
-        const float r = fmax_nan(fmax_nan(ax * C.inv_dx, ay * C.inv_dy), az * C.inv_dz);
+        const float r = fmax_nan(fmax_nan(ax * C.inv_dx, ay * C.inv_dy), ST ? az : az * C.inv_dz);
         block_rmax_dt(r, sc.ctl, sc.slot_in ^ 1);
     }
 }

@@ -302,6 +302,32 @@ def test_steps_3d(name, grid):
             s.close()
 
 
+@pytest.mark.parametrize("name,grid", GRIDS, ids=[g[0] for g in GRIDS])
+def test_packed_3d_agrees_with_the_scalar_kernels_on_stretched_planes(monkeypatch, name, grid):
+    """The packed FP32 3D kernels (even nx) and the one-column FP32 kernels
+    (CM_3D_SCALAR) on the same stirred state on stretched planes: 6 full
+    steps, the dt reductions included, agree within the FP32 bar; the packed
+    kernels' plane caches hold the planes of segments of 32 rows (forced, so
+    that segments start and end inside the grid)."""
+    cfg = cfg3_for(122, 26, 71, grid, Ra=1e6)
+    z = O.znodes(cfg)
+    X = stirred_3d_on(cfg, z, seed=5, u_amp=0.1).astype(np.float32).astype(np.float64)
+    out = {}
+    for mode in ("packed", "scalar"):
+        monkeypatch.setenv("CM_SEG_ROWS", "32")
+        if mode == "scalar":
+            monkeypatch.setenv("CM_3D_SCALAR", "1")
+        s = solver3_for(cfg, "fp32")
+        try:
+            s.set_state(X)
+            s.step(6)
+            out[mode] = (s.state(), s.dt())
+        finally:
+            s.close()
+    check3(cfg, out["packed"][0], out["scalar"][0], 1e-5)
+    assert abs(out["packed"][1] - out["scalar"][1]) <= 1e-6 * out["scalar"][1]
+
+
 def test_full_size_3d_fp32_y_invariant_matches_2d_oracle():
     """The 512 x 512 x 128 FP32 box on the tanh grid (beta = 2) in the launch
     configuration the benchmark times, on y-independent data: 3 steps, y
