@@ -328,6 +328,37 @@ def test_packed_3d_agrees_with_the_scalar_kernels_on_stretched_planes(monkeypatc
     assert abs(out["packed"][1] - out["scalar"][1]) <= 1e-6 * out["scalar"][1]
 
 
+def test_full_size_3d_fp32_genuinely_3d_step_on_tanh_planes():
+    """The 512 x 512 x 128 FP32 box on the beta = 2 tanh grid in the
+    benchmark's launch shape (segment lengths tuned at init, packed kernels
+    with the blocks' plane caches) on a stirred, genuinely 3D state: one full
+    step against the FP64 oracle node by node, within 1e-5 of each field's
+    largest value (momenta: of rho c), the bar of the uniform full-size test."""
+    import contextlib
+    nx, ny, nz = 512, 512, 128
+    cfg = O.Config(nx=nx, ny=ny, nz=nz, ndim=3, Ra=1e9, dt_fixed=1e-4, zstretch=2.0)
+    z = O.znodes(cfg)
+    X = stirred_3d_on(cfg, z, seed=321, u_amp=0.05).astype(np.float32).astype(np.float64)
+    s = solver3_for(cfg, "fp32")
+    try:
+        s.set_state(X)
+        s.step(1)
+        got = s.state()
+    finally:
+        s.close()
+    path = O.build_omp()
+    with (O.library(path) if path else contextlib.nullcontext()):
+        want, _, _ = O.step(cfg, X, 1)
+    cl = closures(cfg.gamma, cfg.eps, cfg.D, cfg.Ra, cfg.Pr)
+    rc = np.max(np.abs(want[0])) * math.sqrt(cfg.gamma * cl["a"])
+    errs = []
+    for f in range(5):
+        scale = rc if f in (1, 2, 3) else np.max(np.abs(want[f]))
+        errs.append(float(np.max(np.abs(got[f] - want[f]))) / scale)
+    print("full-size 3D step on tanh planes, largest node difference per field / field scale:", errs)
+    assert max(errs) <= 1e-5, errs
+
+
 def test_full_size_3d_fp32_y_invariant_matches_2d_oracle():
     """The 512 x 512 x 128 FP32 box on the tanh grid (beta = 2) in the launch
     configuration the benchmark times, on y-independent data: 3 steps, y
