@@ -140,6 +140,8 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
+// the wait alone (a second wait returns at once)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 // dt as the kernels see it: fixed, or CFL times the slot's minimum
 __device__ __forceinline__ double step_dt(const DevCtl* c, int slot, double cfl, double dt_fixed)
