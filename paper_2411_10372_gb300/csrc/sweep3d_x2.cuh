@@ -1,5 +1,6 @@
-// sweep3d_x2.cuh -- FP32 3D sweeps with two columns per lane (even nx,
-// uniform z-grid): L_z and L_y (march kernel) and L_x of Sec. 3.1.
+// sweep3d_x2.cuh -- FP32 3D sweeps with two columns per lane (even nx;
+// uniform or, with ST, stretched z-grid): L_z and L_y (march kernel) and L_x
+// of Sec. 3.1.
 //
 // The 2.5D geometry of sweep3d.cuh -- lanes across x, the warps of a block
 // across the third direction W (y for L_z and L_x, z for L_y), all marching
@@ -22,6 +23,14 @@
 // corrector's flux difference is formed first, as the scheme writes it, so
 // that equal fluxes cancel exactly (y-independent data keep m_y = 0 through
 // L_y, whose y-momentum flux holds the pressure).
+//
+// Stretched z-grid (ST): the conservative metric form of the one-column
+// kernels.  L_z: flux differences of plane k over its cell width w_k, the
+// one-sided derivatives over the spacing they span, the TVD flux through
+// (k, k+1) weighted by its spacing over w_k and its Courant number over that
+// spacing; L_y: the central z span of the warp's plane; L_x: the central z
+// span of each row's plane and its CFL step 1/h_min.  The block copies the
+// metric of its segment's planes after the row ring once (fill_planes).
 #pragma once
 #include "sweep2d_x2.cuh"
 #include "sweep3d.cuh"
