@@ -43,6 +43,7 @@ MUTANTS = [
     ("split_palindrome_is_printed_order", "palindrome2[4] = {0, 2, 2, 0}", "palindrome2[4] = {2, 0, 2, 0}"),
     ("split_3d_order_y_last", "printed3[6] = {2, 1, 0, 2, 1, 0}", "printed3[6] = {2, 0, 1, 2, 0, 1}"),
     ("limiter_phi_no_factor2", "fmin(2.0 * r, 1.0)", "fmin(r, 1.0)"),
+    ("courant_coefficient_unclamped", "return Co <= 0.5 ? Co * (1.0 - Co) : 0.25;", "return Co * (1.0 - Co);"),
     ("nu_conv_coefficient", "out[1] = sRP / p.eps * (s_conv / vol);", "out[1] = sRP * (s_conv / vol);"),
     ("nu_k_coefficient", "out[2] = p.D * sRP / 2.0 * (s_k / vol);", "out[2] = p.D * sRP * (s_k / vol);"),
     ("tsa_sign", "double Tsa = T - (1.0 - p.D * z);", "double Tsa = T - (1.0 + p.D * z);"),
@@ -118,6 +119,8 @@ def _pin_calls():
             calls += [(f"{name}[{c}]", (lambda c=c, fn=fn: fn(c))) for c in (0.1, 0.2, 0.25, 0.4)]
         elif name == "test_xy_exchange_symmetry_3d":
             calls += [(f"{name}[{d}]", (lambda d=d, m=m, fn=fn: fn(d, m))) for d, m in ((1, 0), (0, 1), (2, 2))]
+        elif name == "test_single_sweep_on_contact_step_by_hand":
+            calls += [(f"{name}[{d}]", (lambda d=d, fn=fn: fn(d))) for d in (0.006, 0.012)]
         elif name == "test_sound_damping_pins_stokes_reading":
             calls += [(f"{name}[-]", lambda fn=fn: fn(-2.0 / 3.0, True)),
                       (f"{name}[+]", lambda fn=fn: fn(2.0 / 3.0, False))]

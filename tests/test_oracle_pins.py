@@ -517,25 +517,28 @@ def _contact(cfg, nx, i0, rhoL, rhoR, U):
     return X, cl
 
 
-def test_single_sweep_on_contact_step_by_hand():
+@pytest.mark.parametrize("Delta", [0.006, 0.012])
+def test_single_sweep_on_contact_step_by_hand(Delta):
     """One x-sweep on a contact step (uniform U and p) evaluated by hand from
     Sec. 3.1: for this data the predictor/corrector average is Lax-Wendroff at
     nu = U Delta/h, and at the step r+ = r- = 0, so phi = 0 and the TVD flux
     through the step interface is [G(0) + G(0)] dX = C dX with
-    C = Co (1 - Co), Co = Delta max(|u|+c)/h over the two nodes (A7 reading)."""
+    C = Co (1 - Co) for Co <= 1/2 and 1/4 above, Co = Delta max(|u|+c)/h over
+    the two nodes (A7 reading).  Delta = 0.006 gives Co = 0.28, Delta = 0.012
+    Co = 0.56 (the branch C = 1/4)."""
     nx, i0 = 32, 15
     cfg = O.Config(nx=nx, nz=3, gravity=0.0, t_top=1.0, pert_amp=0.0, Ra=1e14, tvd_form=O.TVD_SPLIT)
     rhoL, rhoR, U = 1.0, 0.5, 0.7
     X, cl = _contact(cfg, nx, i0, rhoL, rhoR, U)
     h = cfg.aspect / nx
-    Delta = 0.006
     Y = O.sweep(cfg, X, 0, Delta)
     r = X[0, 1]
     nu = U * Delta / h
     lw = r - nu / 2 * (np.roll(r, -1) - np.roll(r, 1)) + nu * nu / 2 * (np.roll(r, -1) - 2 * r + np.roll(r, 1))
     c_low = math.sqrt(cfg.gamma * cl["a"] / rhoR)   # c^2 = gamma p / rho, larger on the light side
     Co = Delta * (abs(U) + c_low) / h
-    C = Co * (1 - Co)
+    assert (Co < 0.5) == (Delta < 0.01)
+    C = Co * (1 - Co) if Co <= 0.5 else 0.25
     want = lw.copy()
     want[i0] += C * (rhoR - rhoL)
     want[i0 + 1] -= C * (rhoR - rhoL)
