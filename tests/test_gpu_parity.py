@@ -75,6 +75,35 @@ def test_single_sweeps_fp64(nx, nz, tvd):
     s.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_single_sweeps_with_courant_numbers_above_one_half(precision, tol):
+    """A sweep with Delta = 0.1 h puts the interface Courant numbers of this
+    stirred state at 0.37-0.55, across the switch of C(Co) (Sec. 3.1:
+    Co (1 - Co) up to 1/2, 1/4 above) that the CFL step never reaches (its
+    Courant numbers stay below 1/4)."""
+    nx, nz = 64, 33
+    cfg = O.Config(nx=nx, nz=nz, Ra=1e5, dt_fixed=1e-3)
+    X = stirred_state(cfg, seed=99)
+    if precision == "fp32":
+        X = X.astype(np.float32).astype(np.float64)
+    s = solver_for(cfg, precision)
+    try:
+        for direction in (2, 0):
+            h = cfg.aspect / nx if direction == 0 else 1.0 / (nz - 1)
+            Delta = 0.1 * h
+            s.set_state(X)
+            s.sweep(direction, Delta)
+            got = s.state()
+            want = O.sweep(cfg, X, direction, Delta)
+            for f in (0, 3):
+                assert rel_l2(got[f], want[f]) <= tol, (direction, f)
+            scale = np.linalg.norm(want[0]) * 3.65
+            for f in (1, 2):
+                assert np.linalg.norm(got[f] - want[f]) / scale <= tol, (direction, f)
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("nx,nz", [(8, 5), (29, 7), (30, 9), (64, 33), (122, 17), (256, 64), (250, 130)])
 def test_single_sweeps_fp32(nx, nz):
     """FP32 sweeps (two columns per lane for even nx, one for odd nx) on a
