@@ -75,6 +75,10 @@ MUTANTS = [
     ("stretched_tvd_unweighted", "(rp * w->D[c * N + n] - rm * w->D[c * N + nm])",
      "(w->D[c * N + n] - w->D[c * N + nm])"),
     ("stretched_width_one_sided", "p->w[k] = (p->hp[k - 1] + p->hp[k]) / 2.0;", "p->w[k] = p->hp[k];"),
+    ("stretched_courant_over_cell_width", "tvd_flux(p, X, w->A, Delta, p->hp[k], idx(p, i, j, k - 1)",
+     "tvd_flux(p, X, w->A, Delta, p->w[k], idx(p, i, j, k - 1)"),
+    ("stretched_courant_over_spacing_below", "tvd_flux(p, X, w->A, Delta, p->hp[k], idx(p, i, j, k - 1)",
+     "tvd_flux(p, X, w->A, Delta, p->hp[k - 1], idx(p, i, j, k - 1)"),
     ("stretched_cfl_largest_spacing", "return fmin(p->hp[k - 1], p->hp[k]);", "return fmax(p->hp[k - 1], p->hp[k]);"),
     ("stretched_diag_uniform_weights", "double wgt = p.stretched ? p.w[k] : ((k == 0 || k == p.nz - 1) ? 0.5 : 1.0);",
      "double wgt = (k == 0 || k == p.nz - 1) ? 0.5 : 1.0;"),
@@ -119,6 +123,8 @@ def _pin_calls():
             calls += [(f"{name}[{c}]", (lambda c=c, fn=fn: fn(c))) for c in (0.1, 0.2, 0.25, 0.4)]
         elif name == "test_xy_exchange_symmetry_3d":
             calls += [(f"{name}[{d}]", (lambda d=d, m=m, fn=fn: fn(d, m))) for d, m in ((1, 0), (0, 1), (2, 2))]
+        elif name == "test_stretched_z_contact_tvd_flux_by_hand":
+            calls += [(f"{name}[{b}]", (lambda b=b, fn=fn: fn(b))) for b in (1.5, 2.5)]
         elif name == "test_single_sweep_on_contact_step_by_hand":
             calls += [(f"{name}[{d}]", (lambda d=d, fn=fn: fn(d))) for d in (0.006, 0.012)]
         elif name == "test_sound_damping_pins_stokes_reading":

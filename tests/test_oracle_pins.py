@@ -548,6 +548,44 @@ def test_single_sweep_on_contact_step_by_hand(Delta):
     assert np.max(np.abs(Y[0, 1] - want)) < 1e-12
 
 
+@pytest.mark.parametrize("beta", [1.5, 2.5])
+def test_stretched_z_contact_tvd_flux_by_hand(beta):
+    """Reading A17 on tanh planes: a z-sweep of a contact step across the
+    interior interface (k, k+1) (uniform u_z and p, no gravity) differs with
+    and without the TVD term only at the step's two nodes, by
+    +(h/w_k) C dX and -(h/w_{k+1}) C dX, with h = z_{k+1} - z_k, w the cell
+    widths, dX the jump of the conserved state, and C = Co (1 - Co) at
+    Co = Delta max(|u_z| + c over k, k+1) / h: the Courant number over the
+    interface's own spacing."""
+    nx, nz, k0 = 8, 33, 15
+    kw = dict(nx=nx, nz=nz, gravity=0.0, t_top=1.0, pert_amp=0.0, Ra=1e14, zstretch=beta)
+    cfg_on = O.Config(tvd_form=O.TVD_SPLIT, **kw)
+    cfg_off = O.Config(tvd_form=O.TVD_OFF, **kw)
+    z = O.znodes(cfg_on)
+    k = np.arange(nz)
+    rho = np.where(k <= k0, 1.0, 0.6)[:, None] * np.ones((1, nx))
+    W = 0.3
+    uz = np.full_like(rho, W)
+    uz[0] = uz[-1] = 0.0
+    X = state_from_prims(cfg_on, rho, 0 * rho, uz, 1.0 / rho, np.repeat(z[:, None], nx, 1))
+    cl = closures(cfg_on.gamma, cfg_on.eps, cfg_on.D, cfg_on.Ra, cfg_on.Pr)
+    h = z[k0 + 1] - z[k0]
+    w = np.empty(nz)
+    w[1:-1] = (z[2:] - z[:-2]) / 2
+    w[0], w[-1] = (z[1] - z[0]) / 2, (z[-1] - z[-2]) / 2
+    c = np.sqrt(cl["a"] * cfg_on.gamma / rho[:, 0])          # c^2 = gamma p / rho with p = a
+    Delta = 0.3 * h / (W + max(c[k0], c[k0 + 1]))
+    Co = Delta * (W + max(c[k0], c[k0 + 1])) / h
+    C = Co * (1 - Co)
+    diff = O.sweep(cfg_on, X, 2, Delta) - O.sweep(cfg_off, X, 2, Delta)
+    dX = X[:, k0 + 1, 0] - X[:, k0, 0]
+    for q in range(4):
+        assert np.allclose(diff[q, k0], h / w[k0] * C * dX[q], rtol=1e-12, atol=1e-14), q
+        assert np.allclose(diff[q, k0 + 1], -h / w[k0 + 1] * C * dX[q], rtol=1e-12, atol=1e-14), q
+        others = np.delete(diff[q], [0, 1, k0, k0 + 1, nz - 2, nz - 1], axis=0)
+        assert np.max(np.abs(others)) <= 1e-14, q
+
+
 def test_mirror_symmetry_of_tvd_term():
     """The TVD term is symmetric under x -> -x (r+ and r- exchange roles): a
     contact moving right and its mirror image moving left stay mirror images."""
